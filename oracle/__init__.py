@@ -1,0 +1,219 @@
+"""FP64 CPU oracle for the shape-feature path (arXiv 2510.02894, Sec. 2).
+
+TEST INFRASTRUCTURE ONLY: tests/, the smoke check and the bench's CPU-baseline
+and reference legs are the only callers.  The product library never imports,
+links or runs anything here, and this package imports nothing from it.
+
+The C library (rad_oracle.c) holds all arithmetic; this module only marshals
+numpy arrays through ctypes.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        lib = ctypes.CDLL(path)
+        P = ctypes.c_void_p
+        I64 = ctypes.c_int64
+        D = ctypes.c_double
+        lib.orc_mesh_build.restype = P
+        lib.orc_mesh_build.argtypes = [P, ctypes.c_int, I64, I64, I64, P, ctypes.POINTER(ctypes.c_int)]
+        lib.orc_mesh_free.argtypes = [P]
+        for name in ("orc_mesh_nv", "orc_mesh_nt", "orc_mesh_nvox", "orc_mesh_n_ties"):
+            getattr(lib, name).restype = I64
+            getattr(lib, name).argtypes = [P]
+        for name in ("orc_mesh_volume", "orc_mesh_area"):
+            getattr(lib, name).restype = D
+            getattr(lib, name).argtypes = [P]
+        lib.orc_mesh_max_loop.restype = ctypes.c_int
+        lib.orc_mesh_max_loop.argtypes = [P]
+        lib.orc_mesh_copy.argtypes = [P, P, P, P, P, P]
+        lib.orc_diameters_bruteforce.argtypes = [P, I64, P, P, P, P]
+        lib.orc_diameter3d_pruned.argtypes = [P, I64, P, P, P, P, P]
+        lib.orc_diameter2d_grouped.argtypes = [P, I64, P, ctypes.c_int, P, P, P]
+        lib.orc_soft_grad.argtypes = [P, D, D, D, I64, I64, P]
+        lib.orc_pair_d2.restype = D
+        lib.orc_pair_d2.argtypes = [P, I64, I64, P]
+        lib.orc_num_threads.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class OracleMesh:
+    """Mesh of one mask: vertices in canonical (z, y, x, axis) order.
+
+    owner: (N, 3) int32 lower grid point of each crossing edge
+    axis:  (N,) int32 edge axis;  t: (N,) float64 crossing parameter
+    u:     (N, 3) float64 index-space position (owner + t along axis)
+    tri:   (T, 3) int32 vertex ids, outward counter-clockwise
+    """
+
+    def __init__(self, data, spacing):
+        lib = _load()
+        arr = np.ascontiguousarray(data)
+        if arr.ndim != 3:
+            raise ValueError("mask must be 3-D [nz][ny][nx]")
+        if arr.dtype == np.uint8 or arr.dtype == np.bool_:
+            arr = arr.astype(np.uint8, copy=False)
+            kind = 0
+        elif arr.dtype == np.float32:
+            kind = 1
+        elif arr.dtype == np.float64:
+            kind = 2
+        else:
+            raise TypeError(f"unsupported dtype {arr.dtype}")
+        nz, ny, nx = arr.shape
+        self.dims = (nx, ny, nz)
+        self.spacing = tuple(float(s) for s in spacing)
+        sp = np.array(self.spacing, dtype=np.float64)
+        st = ctypes.c_int(0)
+        h = lib.orc_mesh_build(_ptr(arr), kind, nx, ny, nz, _ptr(sp), ctypes.byref(st))
+        if not h:
+            raise RuntimeError(f"oracle mesh failed with status {st.value}")
+        try:
+            self.nv = int(lib.orc_mesh_nv(h))
+            self.nt = int(lib.orc_mesh_nt(h))
+            self.nvox = int(lib.orc_mesh_nvox(h))
+            self.volume = float(lib.orc_mesh_volume(h))
+            self.area = float(lib.orc_mesh_area(h))
+            self.max_loop = int(lib.orc_mesh_max_loop(h))
+            self.n_ties = int(lib.orc_mesh_n_ties(h))
+            self.owner = np.zeros((self.nv, 3), np.int32)
+            self.axis = np.zeros(self.nv, np.int32)
+            self.t = np.zeros(self.nv, np.float64)
+            self.u = np.zeros((self.nv, 3), np.float64)
+            self.tri = np.zeros((self.nt, 3), np.int32)
+            lib.orc_mesh_copy(h, _ptr(self.owner), _ptr(self.axis), _ptr(self.t), _ptr(self.u), _ptr(self.tri))
+            self._h = h
+            self._arr = arr
+        except Exception:
+            lib.orc_mesh_free(h)
+            raise
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.orc_mesh_free(h)
+            self._h = None
+
+    @property
+    def idx2(self):
+        """Doubled index coordinates (exact integers for a binary mask)."""
+        return np.rint(2.0 * self.u).astype(np.int64)
+
+    def rel_positions(self):
+        """O-relative physical positions, O = centre of the padded box."""
+        base = self.owner.astype(np.float64) - (np.array(self.dims, np.float64) - 1.0) * 0.5
+        tt = np.zeros((self.nv, 3))
+        tt[np.arange(self.nv), self.axis] = self.t
+        return (base + tt) * np.array(self.spacing)
+
+
+def pair_d2(u, i, j, spacing):
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    sp = np.array(spacing, dtype=np.float64)
+    return float(_load().orc_pair_d2(_ptr(u), int(i), int(j), _ptr(sp)))
+
+
+def diameters_bruteforce(u, spacing):
+    """All pairs: returns [(d2, i, j)] for 3D, Slice, Column, Row."""
+    lib = _load()
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    sp = np.array(spacing, dtype=np.float64)
+    d2 = np.zeros(4)
+    ii = np.zeros(4, np.int64)
+    jj = np.zeros(4, np.int64)
+    lib.orc_diameters_bruteforce(_ptr(u), u.shape[0], _ptr(sp), _ptr(d2), _ptr(ii), _ptr(jj))
+    return [(float(d2[q]), int(ii[q]), int(jj[q])) for q in range(4)]
+
+
+def diameter3d_pruned(u, spacing):
+    lib = _load()
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    sp = np.array(spacing, dtype=np.float64)
+    d2 = ctypes.c_double(0)
+    i = ctypes.c_int64(0)
+    j = ctypes.c_int64(0)
+    kept = ctypes.c_int64(0)
+    lib.orc_diameter3d_pruned(_ptr(u), u.shape[0], _ptr(sp), ctypes.byref(d2), ctypes.byref(i),
+                              ctypes.byref(j), ctypes.byref(kept))
+    return (d2.value, i.value, j.value), kept.value
+
+
+def diameter2d(u, spacing, axis):
+    lib = _load()
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    sp = np.array(spacing, dtype=np.float64)
+    d2 = ctypes.c_double(0)
+    i = ctypes.c_int64(0)
+    j = ctypes.c_int64(0)
+    lib.orc_diameter2d_grouped(_ptr(u), u.shape[0], _ptr(sp), int(axis), ctypes.byref(d2), ctypes.byref(i),
+                               ctypes.byref(j))
+    return (d2.value, i.value, j.value)
+
+
+def all_diameters(u, spacing, method="auto"):
+    """[(d2, i, j)] for 3D, Slice, Column, Row.
+
+    method "brute": one all-pairs pass; "fast": pruned 3D + grouped planes
+    (same results, checked against the brute force in the oracle tests)."""
+    n = u.shape[0]
+    if method == "brute" or (method == "auto" and n <= 20000):
+        return diameters_bruteforce(u, spacing)
+    d3, _ = diameter3d_pruned(u, spacing)
+    return [d3, diameter2d(u, spacing, 2), diameter2d(u, spacing, 1), diameter2d(u, spacing, 0)]
+
+
+FEATURE_NAMES = ("MeshVolume", "SurfaceArea", "VoxelVolume", "Maximum3DDiameter",
+                 "Maximum2DDiameterSlice", "Maximum2DDiameterColumn", "Maximum2DDiameterRow")
+
+
+def features(data, spacing, method="auto"):
+    """All shape features of one mask, with argmax pairs and counts."""
+    m = OracleMesh(data, spacing)
+    sp = m.spacing
+    diam = all_diameters(m.u, sp, method) if m.nv >= 2 else [(0.0, -1, -1)] * 4
+    out = {
+        "MeshVolume": m.volume,
+        "SurfaceArea": m.area,
+        "VoxelVolume": m.nvox * sp[0] * sp[1] * sp[2],
+        "Maximum3DDiameter": float(np.sqrt(diam[0][0])),
+        "Maximum2DDiameterSlice": float(np.sqrt(diam[1][0])),
+        "Maximum2DDiameterColumn": float(np.sqrt(diam[2][0])),
+        "Maximum2DDiameterRow": float(np.sqrt(diam[3][0])),
+        "n_vertices": m.nv,
+        "n_triangles": m.nt,
+        "n_voxels": m.nvox,
+        "argmax3d": diam[0][1:],
+        "argmax_slice": diam[1][1:],
+        "argmax_column": diam[2][1:],
+        "argmax_row": diam[3][1:],
+        "d2": [d[0] for d in diam],
+    }
+    return out, m
+
+
+def soft_grad(mesh, gA, gV, gD, argmax3d=(-1, -1)):
+    """Analytic FP64 gradient of gA*A + gV*V + gD*D3 w.r.t. every voxel."""
+    lib = _load()
+    nx, ny, nz = mesh.dims
+    grad = np.zeros((nz, ny, nx), np.float64)
+    lib.orc_soft_grad(mesh._h, float(gA), float(gV), float(gD), int(argmax3d[0]), int(argmax3d[1]), _ptr(grad))
+    return grad
+
+
+def num_threads():
+    return int(_load().orc_num_threads())
