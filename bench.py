@@ -1,0 +1,374 @@
+"""Benchmark of the shape-feature hot path on GB300.
+
+Workload (one step): marching cubes + all shape features (mesh volume,
+surface area, voxel volume, maximum 3D diameter and the three planar
+diameters) of one 512x512x256 uint8 CT-shaped mask (3 rotated ellipsoids,
+5 % boundary voxels flipped, spacing (0.7, 0.7, 2.5) mm), through the C ABI
+entry point rad_extract with the mask resident in HBM.  The L2 (129 MB) is
+flushed between steps by writing a 256 MB buffer (the mask itself is 67 MB).
+
+Metric: diameter vertex-pairs/s = N (N - 1) / 2 / step time, whole job over
+all ranks (replicas of the workload: the single-mask path does not shard).
+Also reported: the plain FP64 all-pairs kernel on the same mesh, batched
+crops per second, the end-to-end figure through host buffers, the roofline
+of the dominant kernel and the FP64 CPU oracle timed on a bounded sample.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "diameter vertex-pairs/s and batched ROIs/s vs plain FP64 kernel, 1 GB300, oracle-exact"
+UNIT = "vertex-pairs/s"
+WORKLOAD = ("ct_512x512x256: uint8 mask 512x512x256, spacing (0.7,0.7,2.5) mm, union of 3 rotated ellipsoids "
+            "(semi-axes 60-150 voxels), 5% boundary voxels flipped, seed 0; mesh + all shape features per step")
+FLOPS_PER_PAIR = 8  # 3 FADD + 1 FMUL + 2 FFMA (2 flops each) per evaluated pair
+L2_FLUSH_BYTES = 256 << 20
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.out,
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.flush()
+        rows = [r.split(",") for r in open(self.out.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.out.name)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.strip() == "Active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def kernel_work(name, ctx):
+    """Algorithmic work of one launch of `name`: (bound, amount, unit_scale)."""
+    nvox, words4, N, T, R = ctx["nvox"], ctx["bitset_bytes"], ctx["N"], ctx["T"], ctx["rows"]
+    if name == "mc_pack_u8":
+        return "hbm", nvox + words4
+    if name == "mc_count":
+        return "hbm", words4 + 12 * R
+    if name == "mc_emit":
+        return "hbm", words4 + 6 * N + 12 * T
+    if name == "diam_pairs_fp32":
+        return "alu", FLOPS_PER_PAIR * ctx["pairs_evaluated"]
+    if name == "diam_scatter":
+        return "hbm", 6 * N + 4 * 16 * N
+    return None, None
+
+
+def oracle_sample(mask, sp, n_slices, m_pairs_vertices):
+    """Time the FP64 oracle as it stands on a bounded sample: its mesh on a
+    central slab of z-slices (time scaled to all slices) and its brute-force
+    diameter over the pairs of the slab's first vertices."""
+    import oracle
+    nz = mask.shape[0]
+    z0 = max(0, nz // 2 - n_slices // 2)
+    slab = np.ascontiguousarray(mask[z0:z0 + n_slices])
+    t0 = time.perf_counter()
+    om = oracle.OracleMesh(slab, sp)
+    t_mesh = (time.perf_counter() - t0) * nz / slab.shape[0]
+    src = om if om.nv >= m_pairs_vertices else oracle.OracleMesh(mask, sp)
+    m = min(m_pairs_vertices, src.nv)
+    t0 = time.perf_counter()
+    oracle.diameters_bruteforce(src.u[:m], sp)
+    t_pairs = time.perf_counter() - t0
+    rate = m * (m - 1) / 2 / t_pairs
+    return t_mesh, rate, oracle.num_threads(), m
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2510_02894_gb300 import synth
+    mask, sp = synth.ct_512(0)
+    N = oracle.OracleMesh(mask, sp).nv
+    pairs = N * (N - 1) / 2
+    vals, times = [], []
+    for s in range(args.warmup + args.steps):
+        t_mesh, rate, cores, m = oracle_sample(mask, sp, 16, 30000)
+        full_s = t_mesh + pairs / rate
+        if s >= args.warmup:
+            vals.append(pairs / full_s)
+            times.append(full_s * 1e3)
+    value = statistics.mean(vals)
+    sample = (f"per step: oracle mesh of 16 central of 256 z-slices (time scaled x16) + brute-force pairs of "
+              f"{m} vertices ({m * (m - 1) // 2} pairs), extrapolated to N={N} ({pairs:.3e} pairs)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_vertices": N},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    from paper_2510_02894_gb300 import rad, synth
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    mask, sp = synth.ct_512(0)
+    dev = torch.from_numpy(mask).cuda()
+    pinned = torch.from_numpy(mask).pin_memory()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    ws = rad.Workspace()
+    ws_host = rad.Workspace()
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        feats = rad.extract(dev, sp, ws)
+        rad.extract_host(pinned.data_ptr(), mask.shape, sp, ws_host)
+    stats = rad.last_call_stats()
+    N, T = feats["n_vertices"], feats["n_triangles"]
+    pairs = N * (N - 1) / 2
+
+    # ---- timed region: device-resident inputs ------------------------------------
+    clocks = ClockSampler(local)
+    clocks.start()
+    rad.profile_reset()
+    rad.profile_enable(True)
+    launches0 = rad.launch_count()
+    barrier(world)
+    torch.cuda.synchronize()
+    step_ms = []
+    evaluated = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rad.extract(dev, sp, ws)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        evaluated.append(rad.last_call_stats()["pairs_evaluated"])
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = rad.launch_count() - launches0
+    rad.profile_enable(False)
+    prof = rad.profile_read()
+    clk = clocks.stop()
+    ms = max_over_ranks(statistics.mean(step_ms), world)
+    value = world * pairs / (ms / 1e3)
+
+    # ---- end to end through host buffers ------------------------------------------
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rad.extract_host(pinned.data_ptr(), mask.shape, sp, ws_host)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    hstats = rad.last_call_stats()
+    e2e = max_over_ranks(statistics.mean(e2e_ms), world)
+
+    # ---- roofline of the dominant kernel ---------------------------------------------
+    peaks, peak_kind = load_peaks()
+    props = torch.cuda.get_device_properties(local)
+    sm_max = float(peaks.get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0)
+    fp32_peak_tflops = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+    d = dict(nvox=int(mask.size), N=N, T=T, rows=(mask.shape[1] + 1) * (mask.shape[0] + 1),
+             bitset_bytes=4 * ((mask.shape[2] + 31) // 32) * (mask.shape[1] + 3) * (mask.shape[0] + 3),
+             pairs_evaluated=statistics.mean(evaluated))
+    kernels = {k: v for k, v in prof.items() if v["launches"] > 0}
+    total_ms = sum(v["total_ms"] for v in kernels.values()) or 1.0
+    dom = max(kernels, key=lambda k: kernels[k]["total_ms"])
+    bound, amount = kernel_work(dom, d)
+    per_launch_ms = kernels[dom]["total_ms"] / kernels[dom]["launches"]
+    roof = {"kernel": dom, "share": kernels[dom]["total_ms"] / total_ms, "launch_ms": per_launch_ms}
+    if bound == "hbm":
+        ach = amount / (per_launch_ms / 1e3) / 1e9
+        roof.update({"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": peak_kind,
+                     "algorithmic_bytes": amount})
+    elif bound == "alu":
+        ach = amount / (per_launch_ms / 1e3) / 1e12
+        roof.update({"bound": "alu", "achieved": ach, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
+                     "frac": ach / fp32_peak_tflops, "traffic": None,
+                     "peak_source": f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
+                     "algorithmic_flops": amount})
+    else:
+        roof.update({"bound": None, "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None})
+    kernel_table = {k: {"launches_per_step": v["launches"] / args.steps, "ms_per_step": v["total_ms"] / args.steps,
+                        "share": v["total_ms"] / total_ms} for k, v in sorted(kernels.items(),
+                                                                              key=lambda kv: -kv[1]["total_ms"])}
+
+    # ---- plain FP64 all-pairs kernel on the same mesh -------------------------------
+    plain = None
+    if not args.no_plain:
+        m = rad.mesh(dev, sp)
+        rad.shape(m)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fp = rad.shape_plain_fp64(m)
+        e1.record(stream)
+        e1.synchronize()
+        pms = e0.elapsed_time(e1)
+        e0.record(stream)
+        ff = rad.shape(m)
+        e1.record(stream)
+        e1.synchronize()
+        fms = e0.elapsed_time(e1)
+        same = all(fp[k] == ff[k] for k in ("Maximum3DDiameter", "Maximum2DDiameterSlice", "Maximum2DDiameterColumn",
+                                            "Maximum2DDiameterRow", "argmax3d", "argmax_slice", "argmax_column",
+                                            "argmax_row"))
+        plain = {"ms": pms, "pairs_per_s": pairs / (pms / 1e3), "fp32_filter_shape_ms": fms,
+                 "speedup_vs_plain": pms / fms, "identical_results": bool(same)}
+
+    # ---- batched crops (sequential calls until the batched launch lands) ----------
+    batch = None
+    if not args.no_batch:
+        crops = synth.batch_256(0)
+        devs = [(torch.from_numpy(c).cuda(), s) for c, s in crops]
+        wsb = rad.Workspace()
+        for c, s in devs[:8]:
+            rad.extract(c, s, wsb)
+        torch.cuda.synchronize()
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for c, s in devs:
+            rad.extract(c, s, wsb)
+        e1.record(stream)
+        e1.synchronize()
+        bms = e0.elapsed_time(e1)
+        batch = {"rois": len(devs), "ms": bms, "rois_per_s": len(devs) / (bms / 1e3),
+                 "mode": "one rad_extract call per crop"}
+
+    # ---- CPU baseline: the oracle on a bounded sample --------------------------------
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t_mesh, rate, cores, m = oracle_sample(mask, sp, 16, 60000)
+        full_s = t_mesh + pairs / rate
+        cpu = {"value": pairs / full_s, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": (f"oracle mesh of 16 central of 256 z-slices (time x16) + FP64 brute-force pairs of {m} "
+                          f"vertices, extrapolated to all {pairs:.3e} pairs (mesh {t_mesh:.2f} s, "
+                          f"{rate:.3e} pairs/s)")}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "u8+f32+f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "n_vertices": N, "n_triangles": T, "pairs": pairs,
+                           "pairs_evaluated_fp32": d["pairs_evaluated"], "l2": "flushed between steps (256 MB write)",
+                           "parallelism": f"replicas x{world}", "diam_stats": stats},
+                "roofline": roof, "kernels": kernel_table,
+                "e2e": {"value": world * pairs / (e2e / 1e3), "unit": UNIT, "ms_per_step": e2e,
+                        "h2d_bytes_per_step": hstats["h2d_bytes"], "d2h_bytes_per_step": hstats["d2h_bytes"]},
+                "plain_fp64": plain, "batched": batch, "cpu_baseline": cpu, "clocks": clk,
+                "gpu_launches": launches}
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,180 @@
+/*
+ * rad.h -- C ABI of the GB300 (sm_103a) shape-feature library.
+ *
+ * The library computes the 3D shape features that PyRadiomics-cuda
+ * accelerates (arXiv 2510.02894, Sec. 2 "PyRadiomics-cuda design"): a
+ * marching-cubes triangle mesh of a region-of-interest mask with its
+ * MeshVolume and SurfaceArea (first step, Sec. 2), then the maximum 3D
+ * diameter and the three planar diameters over the mesh vertices (second
+ * step, Sec. 2 "Parallel diameter calculation"), plus VoxelVolume.
+ *
+ * Conventions (all entry points):
+ *   - A mask is C-order [nz][ny][nx], x fastest; dims = {nx, ny, nz};
+ *     spacing = {sx, sy, sz} in mm (finite, > 0).  1 <= n_k <= 16383.
+ *   - The mask is implicitly padded with one outside voxel on every side.
+ *     A uint8 voxel is inside iff != 0; a float32 voxel iff > 0.5.
+ *   - Vertices: one per grid edge whose endpoints differ in inside-ness,
+ *     ids in canonical (z, y, x, axis) order of the edge's lower endpoint.
+ *     A vertex is stored as doubled index coordinates
+ *     (2 g_k + [k == axis]), int16 x 3, plus (soft maps) the iso crossing
+ *     parameter t from the lower endpoint, t = (0.5 - v0) / (v1 - v0).
+ *   - Triangles: int32 x 3 vertex ids, wound counter-clockwise seen from
+ *     outside.  Loops of 4+ vertices take the admissible triangulation of
+ *     minimum area (ties: larger enclosed volume, then the smallest sorted
+ *     list of canonical id triples).
+ *   - Diameters: d2 = ((Dx Dx + Dy Dy) + Dz Dz), D_k = (u_ik - u_jk) s_k in
+ *     FP64 (u = index position), D = sqrt(max d2); the argmax pair is the
+ *     smallest (i, j), i < j, attaining the maximum.  Slice = pairs of equal
+ *     z, Column = equal y, Row = equal x.  No pair: 0 and (-1, -1).
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Device
+ *     pointers must be device-accessible from the current device.
+ *   - No exception crosses the ABI.  Every call returns a rad_status; the
+ *     text of the last error of the calling thread is rad_last_error().
+ *   - Calls that return results to the host synchronise `stream`.
+ */
+#ifndef RAD_H_
+#define RAD_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RAD_OK = 0,
+  RAD_ERR_INVALID_ARG = 1, /* bad pointer, size or spacing; nothing launched */
+  RAD_ERR_CUDA = 2,        /* a CUDA runtime call failed (text in rad_last_error) */
+  RAD_ERR_CAPACITY = 3,    /* an output pool was too small; the needed sizes are reported */
+  RAD_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
+  RAD_ERR_OOM = 5,         /* device allocation failed */
+  RAD_ERR_INTERNAL = 6     /* a device-side consistency check failed */
+} rad_status;
+
+/* Features of one mask (names as in PyRadiomics' Shape class). */
+typedef struct {
+  double MeshVolume, SurfaceArea, VoxelVolume;
+  double Maximum3DDiameter, Maximum2DDiameterSlice, Maximum2DDiameterColumn, Maximum2DDiameterRow;
+  int64_t n_vertices, n_triangles, n_voxels;
+  int32_t argmax3d[2], argmax_slice[2], argmax_column[2], argmax_row[2];
+  int32_t status; /* rad_status of this mask (batched calls) */
+  int32_t _pad;
+} rad_features_t;
+
+/* A mesh on the device.  Zero-initialise before the first rad_mesh(); the
+ * library owns the buffers (grown as needed, reused by later calls) and
+ * frees them in rad_mesh_free().  The pointers stay valid until the next
+ * rad_mesh()/rad_soft_mesh() or rad_mesh_free() on the same struct. */
+typedef struct {
+  int64_t n_vertices, n_triangles, n_voxels;
+  int16_t* vtx_idx2; /* device, n_vertices x 3: doubled index coordinates */
+  double* vtx_t;     /* device, n_vertices: crossing parameter (soft meshes; NULL for masks) */
+  int32_t* tri;      /* device, n_triangles x 3 */
+  double mesh_volume, surface_area;
+  int64_t dims[3];
+  double spacing[3];
+  int32_t soft;
+  int32_t _pad;
+  void* _priv; /* library-owned state */
+} rad_mesh_t;
+
+/* Tuning knobs of the diameter kernels (see rad_set_tuning). */
+typedef struct {
+  int32_t tile;        /* vertices per tile: 64, 128 or 256 */
+  int32_t threads;     /* threads per CTA of the pair kernel: 64, 128 or 256 */
+  int32_t ctas_per_sm; /* persistent CTAs per SM for the pair kernel: 1..16 */
+  int32_t cell_shift;  /* spatial cell edge = 2^cell_shift doubled-index units (2..7) */
+} rad_tuning_t;
+
+/* ---- single mask --------------------------------------------------------- */
+
+/* Marching cubes (Sec. 2, "Marching cubes fused parallel kernels") on a
+ * device uint8 mask: fills mesh (vertices, triangles, MeshVolume,
+ * SurfaceArea, voxel count).  Synchronises `stream` (the vertex and triangle
+ * counts are returned in *mesh).  mask_dev: device, nx*ny*nz bytes, not
+ * modified. */
+rad_status rad_mesh(const uint8_t* mask_dev, const int64_t dims[3], const double spacing[3], rad_mesh_t* mesh,
+                    void* stream);
+
+/* Marching cubes on a device float32 probability map (iso level 0.5,
+ * linearly interpolated vertices); vtx_t is filled. */
+rad_status rad_soft_mesh(const float* prob_dev, const int64_t dims[3], const double spacing[3], rad_mesh_t* mesh,
+                         void* stream);
+
+/* Diameters of a mesh (Sec. 2, "Parallel diameter calculation"): FP32
+ * filter over tiled, bounding-box-culled vertex pairs, then FP64
+ * confirmation of every pair within the filter's error bound, so the result
+ * equals the FP64 all-pairs maximum.  Writes all features of the mesh to
+ * *out (host).  Synchronises `stream`. */
+rad_status rad_shape(const rad_mesh_t* mesh, rad_features_t* out, void* stream);
+
+/* The same diameters by a plain FP64 all-pairs kernel (one thread block per
+ * strip of pairs, no culling, no FP32 filter): the comparison kernel.
+ * Writes all features of the mesh to *out.  Synchronises `stream`. */
+rad_status rad_shape_plain_fp64(const rad_mesh_t* mesh, rad_features_t* out, void* stream);
+
+/* Whole path for one device mask: mesh + shape with library-owned buffers
+ * kept in `ws` between calls (one host synchronisation per call, none
+ * inside).  *ws must be NULL on the first call; free with
+ * rad_workspace_free(). */
+typedef struct rad_workspace rad_workspace_t;
+rad_status rad_extract(const uint8_t* mask_dev, const int64_t dims[3], const double spacing[3], rad_features_t* out,
+                       rad_workspace_t** ws, void* stream);
+
+/* Whole path for one HOST mask: the mask is copied to the device inside the
+ * call (pinned host memory gives full bandwidth), the features are copied
+ * back.  Same workspace rules as rad_extract. */
+rad_status rad_extract_host(const uint8_t* mask_host, const int64_t dims[3], const double spacing[3],
+                            rad_features_t* out, rad_workspace_t** ws, void* stream);
+
+void rad_workspace_free(rad_workspace_t* ws);
+void rad_mesh_free(rad_mesh_t* mesh);
+
+/* Copy a mesh's arrays to caller buffers (host or device; any may be NULL):
+ * idx2 n_vertices x 3 int16, t n_vertices doubles (soft meshes only), tri
+ * n_triangles x 3 int32.  Synchronises `stream`. */
+rad_status rad_mesh_copy(const rad_mesh_t* mesh, int16_t* idx2, double* t, int32_t* tri, void* stream);
+
+/* ---- configuration and introspection ----------------------------------- */
+
+/* Set (non-NULL) and/or read (get non-NULL) the diameter tuning of the
+ * calling process.  Invalid values return RAD_ERR_INVALID_ARG. */
+rad_status rad_set_tuning(const rad_tuning_t* set, rad_tuning_t* get);
+
+/* Per-kernel timing: when enabled, every kernel the library launches is
+ * bracketed by CUDA events on its launch stream.  rad_profile_read copies up
+ * to `cap` records (name, launches, total milliseconds) and returns how many
+ * exist; it synchronises the device.  rad_profile_reset clears them. */
+typedef struct {
+  char name[48];
+  int64_t launches;
+  double total_ms;
+} rad_kernel_stat_t;
+rad_status rad_profile_enable(int on);
+int rad_profile_read(rad_kernel_stat_t* out, int cap);
+void rad_profile_reset(void);
+
+/* Number of kernels this library has launched in this process. */
+int64_t rad_launch_count(void);
+
+/* Statistics of the calling thread's last rad_shape / rad_extract /
+ * rad_extract_host call (host copies; no device access). */
+typedef struct {
+  int64_t h2d_bytes, d2h_bytes;    /* host<->device bytes copied by the call */
+  int64_t problems;                /* diameter problems: 1 (3D) + planes with >= 2 vertices */
+  int64_t tiles, tile_pairs;       /* vertex tiles; tile pairs before culling */
+  int64_t work_items;              /* tile pairs that survived the first culling pass */
+  int64_t items_evaluated;         /* tile pairs evaluated in FP32 (after re-culling) */
+  int64_t pairs_evaluated;         /* vertex pairs evaluated in FP32 */
+  int64_t candidates;              /* pairs re-evaluated in FP64 */
+} rad_call_stats_t;
+rad_status rad_last_call_stats(rad_call_stats_t* out);
+
+const char* rad_status_str(rad_status s);
+const char* rad_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RAD_H_ */

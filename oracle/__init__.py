@@ -41,6 +41,7 @@ def _load():
         lib.orc_diameter3d_pruned.argtypes = [P, I64, P, P, P, P, P]
         lib.orc_diameter2d_grouped.argtypes = [P, I64, P, ctypes.c_int, P, P, P]
         lib.orc_soft_grad.argtypes = [P, D, D, D, I64, I64, P]
+        lib.orc_subset_max.argtypes = [P, P, I64, P, P, P, P]
         lib.orc_pair_d2.restype = D
         lib.orc_pair_d2.argtypes = [P, I64, I64, P]
         lib.orc_num_threads.restype = ctypes.c_int
@@ -165,14 +166,90 @@ def diameter2d(u, spacing, axis):
     return (d2.value, i.value, j.value)
 
 
+def subset_max(u, ids, spacing):
+    """Pinned brute force over the pairs of a vertex subset."""
+    lib = _load()
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    ids = np.ascontiguousarray(np.unique(np.asarray(ids, np.int64)))
+    sp = np.array(spacing, dtype=np.float64)
+    d2 = ctypes.c_double(0)
+    i = ctypes.c_int64(0)
+    j = ctypes.c_int64(0)
+    lib.orc_subset_max(_ptr(u), _ptr(ids), ids.size, _ptr(sp), ctypes.byref(d2), ctypes.byref(i), ctypes.byref(j))
+    return (d2.value, i.value, j.value)
+
+
+def _extreme_candidates(P):
+    """Indices of points that include every extreme point of their convex
+    hull: Qhull's vertices plus the points it reports as coplanar ('Qc'),
+    or, for sets of lower dimension, the per-coordinate extremes together
+    with a hull of the remaining coordinates."""
+    from scipy.spatial import ConvexHull
+    from scipy.spatial import QhullError
+    n, dim = P.shape
+    if n <= 64:
+        return np.arange(n)
+    try:
+        h = ConvexHull(P, qhull_options="Qc")
+        cand = [h.vertices]
+        if h.coplanar.size:
+            cand.append(h.coplanar[:, 0])
+        return np.unique(np.concatenate(cand))
+    except QhullError:
+        # flat (or collinear) set: drop a constant coordinate and retry
+        spread = P.max(axis=0) - P.min(axis=0)
+        keep = np.flatnonzero(spread > 0)
+        if keep.size < dim and keep.size >= 2:
+            return _extreme_candidates(P[:, keep])
+        ext = [np.flatnonzero(P[:, k] == P[:, k].min()) for k in range(dim)]
+        ext += [np.flatnonzero(P[:, k] == P[:, k].max()) for k in range(dim)]
+        return np.unique(np.concatenate(ext))
+
+
+def diameter_hull(u, spacing, axis=None):
+    """Exact maximum (d2, i, j) for very large vertex sets.
+
+    Every pair attaining the maximum consists of extreme points of the
+    convex hull (|p - q|^2 is strictly convex in p, so its maximum over the
+    hull is attained only at extreme points).  Qhull only shortlists them
+    (vertices plus coplanar points, a superset); the pinned FP64 brute force
+    over the shortlist decides.  axis None: 3D; 0/1/2: pairs of equal x/y/z,
+    one plane at a time (2D hull of the other two coordinates)."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    sp = np.asarray(spacing, np.float64)
+    if axis is None:
+        cand = _extreme_candidates(u * sp)
+        return subset_max(u, cand, spacing)
+    other = [k for k in range(3) if k != axis]
+    order = np.lexsort((np.arange(len(u)), u[:, axis]))
+    keys = u[order, axis]
+    cuts = np.flatnonzero(np.diff(keys)) + 1
+    best = (0.0, -1, -1)
+    for grp in np.split(order, cuts):
+        if grp.size < 2:
+            continue
+        loc = _extreme_candidates(u[grp][:, other] * sp[other])
+        d2, i, j = subset_max(u, grp[loc], spacing)
+        if i < 0:
+            continue
+        if best[1] < 0 or d2 > best[0] or (d2 == best[0] and (i, j) < (best[1], best[2])):
+            best = (d2, i, j)
+    return best
+
+
 def all_diameters(u, spacing, method="auto"):
     """[(d2, i, j)] for 3D, Slice, Column, Row.
 
-    method "brute": one all-pairs pass; "fast": pruned 3D + grouped planes
-    (same results, checked against the brute force in the oracle tests)."""
+    method "brute": one all-pairs pass; "fast": pruned 3D + grouped planes;
+    "hull": convex-hull shortlists + pinned brute force (very large sets).
+    All give the same results (checked against the brute force in the
+    oracle tests); "auto" picks by size."""
     n = u.shape[0]
     if method == "brute" or (method == "auto" and n <= 20000):
         return diameters_bruteforce(u, spacing)
+    if method == "hull" or (method == "auto" and n > 1500000):
+        return [diameter_hull(u, spacing), diameter_hull(u, spacing, 2), diameter_hull(u, spacing, 1),
+                diameter_hull(u, spacing, 0)]
     d3, _ = diameter3d_pruned(u, spacing)
     return [d3, diameter2d(u, spacing, 2), diameter2d(u, spacing, 1), diameter2d(u, spacing, 0)]
 

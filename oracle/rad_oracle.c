@@ -756,6 +756,19 @@ static void subset_max(const double* u, const int64_t* ids, int64_t m, const dou
   *out = gb;
 }
 
+/* Brute force over the pairs of a caller-given vertex subset (ids
+ * ascending); used with a candidate set that provably holds every vertex of
+ * every maximal pair (see oracle/__init__.py). */
+int orc_subset_max(const double* u, const int64_t* ids, int64_t m, const double s[3], double* d2_out,
+                   int64_t* i_out, int64_t* j_out) {
+  best_t bb;
+  subset_max(u, ids, m, s, &bb);
+  *d2_out = bb.i >= 0 ? bb.d2 : 0.0;
+  *i_out = bb.i;
+  *j_out = bb.j;
+  return ORC_OK;
+}
+
 /* Maximum 3D diameter with an exact pruning step (same result as the brute
  * force, for large meshes):
  *   1. L = d2 of an actual pair (two farthest-point sweeps from vertex 0):

@@ -1,0 +1,559 @@
+// C ABI of the shape-feature library (declared in include/rad.h): argument
+// validation, library-owned device buffers, the launch sequence of each entry
+// point, status words, per-kernel timing and error text.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "rad_internal.cuh"
+
+namespace rad {
+
+// ---- error text -----------------------------------------------------------------
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+rad_status cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
+  set_error("%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+  return e == cudaErrorMemoryAllocation ? RAD_ERR_OOM : RAD_ERR_CUDA;
+}
+
+// ---- launch bookkeeping ------------------------------------------------------------
+
+namespace {
+struct Pending {
+  int stat;
+  cudaEvent_t a, b;
+};
+struct Prof {
+  std::mutex mu;
+  bool on = false;
+  std::vector<rad_kernel_stat_t> stats;
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
+  long long launches = 0;
+};
+Prof& prof() {
+  static Prof* p = new Prof();
+  return *p;
+}
+cudaEvent_t get_event(Prof& p) {
+  if (!p.pool.empty()) {
+    cudaEvent_t e = p.pool.back();
+    p.pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+void flush_pending(Prof& p) {
+  for (auto& q : p.pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(q.b) == cudaSuccess && cudaEventElapsedTime(&ms, q.a, q.b) == cudaSuccess)
+      p.stats[q.stat].total_ms += ms;
+    p.pool.push_back(q.a);
+    p.pool.push_back(q.b);
+  }
+  p.pending.clear();
+}
+}  // namespace
+
+void launch_begin(const char* name, cudaStream_t s, void** token) {
+  Prof& p = prof();
+  std::lock_guard<std::mutex> g(p.mu);
+  p.launches++;
+  int idx = -1;
+  for (size_t i = 0; i < p.stats.size(); ++i)
+    if (strncmp(p.stats[i].name, name, sizeof(p.stats[i].name)) == 0) { idx = (int)i; break; }
+  if (idx < 0) {
+    rad_kernel_stat_t st;
+    memset(&st, 0, sizeof(st));
+    strncpy(st.name, name, sizeof(st.name) - 1);
+    p.stats.push_back(st);
+    idx = (int)p.stats.size() - 1;
+  }
+  p.stats[idx].launches++;
+  if (!p.on) {
+    *token = nullptr;
+    return;
+  }
+  if (p.pending.size() > 4096) flush_pending(p);
+  Pending q;
+  q.stat = idx;
+  q.a = get_event(p);
+  q.b = get_event(p);
+  cudaEventRecord(q.a, s);
+  p.pending.push_back(q);
+  *token = reinterpret_cast<void*>((intptr_t)p.pending.size());
+}
+
+void launch_end(void* token, cudaStream_t s) {
+  if (!token) return;
+  Prof& p = prof();
+  std::lock_guard<std::mutex> g(p.mu);
+  const size_t i = (size_t)(intptr_t)token - 1;
+  if (i < p.pending.size()) cudaEventRecord(p.pending[i].b, s);
+}
+
+int num_sms() {
+  static int cached[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return 132;
+  if (!cached[dev]) {
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    cached[dev] = n > 0 ? n : 132;
+  }
+  return cached[dev];
+}
+
+// ---- buffers -----------------------------------------------------------------------
+
+rad_status DevBuf::reserve(size_t need) {
+  if (need <= bytes && p) return RAD_OK;
+  if (p) {
+    cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  size_t n = std::max<size_t>(need + need / 4, 256);
+  cudaError_t e = cudaMalloc(&p, n);
+  if (e != cudaSuccess) {
+    p = nullptr;
+    cudaGetLastError();
+    set_error("cudaMalloc of %zu bytes failed: %s", n, cudaGetErrorString(e));
+    return RAD_ERR_OOM;
+  }
+  bytes = n;
+  return RAD_OK;
+}
+
+void DevBuf::release() {
+  if (p) cudaFree(p);
+  p = nullptr;
+  bytes = 0;
+}
+
+static rad_tuning_t g_tuning = {128, 128, 4, 4};
+const rad_tuning_t& tuning() { return g_tuning; }
+
+// ---- per-mesh / per-workspace state --------------------------------------------------
+
+struct Result {  // device, one copy per call
+  MeshTotals mt;
+  DiamResult dr;
+  unsigned int status;
+  unsigned int pad;
+};
+
+struct Work {
+  MeshScratch ms;
+  DiamScratch ds;
+  DevBuf result;   // Result
+  DevBuf idx2, vt, tri;
+  long long vcap = 0, tcap = 0;
+  Result* host = nullptr;  // pinned copy
+  DevBuf mask;     // device copy of a host mask (rad_extract_host)
+  int device = -1;
+  ~Work() {
+    ms.bits.release(); ms.counts.release(); ms.prefix.release(); ms.chunk.release(); ms.partial.release();
+    ms.bintab.release(); ds.misc.release(); ds.plain_part.release(); result.release(); idx2.release();
+    vt.release(); tri.release(); mask.release();
+    if (host) cudaFreeHost(host);
+  }
+  rad_status init() {
+    if (!host) RAD_CUDA(cudaMallocHost(&host, sizeof(Result)));
+    RAD_TRY(result.reserve(sizeof(Result)));
+    return RAD_OK;
+  }
+  Result* dres() const { return result.as<Result>(); }
+};
+
+}  // namespace rad
+
+namespace rad {
+static thread_local rad_call_stats_t g_stats;
+static void record_stats(const Result& r, long long h2d, bool have_diam) {
+  memset(&g_stats, 0, sizeof(g_stats));
+  g_stats.h2d_bytes = h2d;
+  g_stats.d2h_bytes = (long long)sizeof(Result);
+  if (!have_diam) return;
+  g_stats.problems = r.dr.problems;
+  g_stats.tiles = r.dr.tiles;
+  g_stats.tile_pairs = r.dr.tile_pairs;
+  g_stats.work_items = r.dr.work_items;
+  g_stats.items_evaluated = r.dr.items_evaluated;
+  g_stats.pairs_evaluated = r.dr.pairs_evaluated;
+  g_stats.candidates = r.dr.candidates;
+}
+}  // namespace rad
+
+struct rad_workspace {
+  rad::Work work;
+  rad_mesh_t mesh;
+};
+
+using namespace rad;
+
+namespace {
+
+rad_status check_geometry(const int64_t dims[3], const double spacing[3]) {
+  if (!dims || !spacing) {
+    set_error("dims and spacing must be non-NULL");
+    return RAD_ERR_INVALID_ARG;
+  }
+  for (int k = 0; k < 3; ++k) {
+    if (dims[k] < 1 || dims[k] > 16383) {
+      set_error("dims[%d] = %lld outside [1, 16383]", k, (long long)dims[k]);
+      return RAD_ERR_INVALID_ARG;
+    }
+    if (!(spacing[k] > 0.0) || !isfinite(spacing[k])) {
+      set_error("spacing[%d] = %g must be finite and > 0", k, spacing[k]);
+      return RAD_ERR_INVALID_ARG;
+    }
+  }
+  return RAD_OK;
+}
+
+rad_status check_device_ptr(const void* p, const char* what) {
+  if (!p) {
+    set_error("%s is NULL", what);
+    return RAD_ERR_INVALID_ARG;
+  }
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error("%s: cudaPointerGetAttributes failed: %s", what, cudaGetErrorString(e));
+    return RAD_ERR_INVALID_ARG;
+  }
+  if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) {
+    set_error("%s is not a device pointer", what);
+    return RAD_ERR_INVALID_ARG;
+  }
+  return RAD_OK;
+}
+
+rad_status status_from_dev(unsigned int st) {
+  if (st & (DEV_ERR_VCAP | DEV_ERR_TCAP | DEV_ERR_CANDCAP | DEV_ERR_WORKCAP | DEV_ERR_PROBCAP)) {
+    set_error("device pool too small (status 0x%x)", st);
+    return RAD_ERR_CAPACITY;
+  }
+  if (st & DEV_ERR_TIMEOUT) {
+    set_error("bounded device wait gave up (status 0x%x)", st);
+    return RAD_ERR_TIMEOUT;
+  }
+  if (st) {
+    set_error("device consistency check failed (status 0x%x)", st);
+    return RAD_ERR_INTERNAL;
+  }
+  return RAD_OK;
+}
+
+Work* work_of(rad_mesh_t* m) {
+  if (!m->_priv) m->_priv = new Work();
+  return static_cast<Work*>(m->_priv);
+}
+
+// Marching cubes into library-owned buffers of `w`; counts synchronously.
+rad_status run_mesh(const void* data, bool soft, const int64_t dims[3], const double sp[3], Work& w, rad_mesh_t* mesh,
+                    cudaStream_t st) {
+  RAD_TRY(w.init());
+  const MeshDims d = make_dims(dims);
+  Result* dr = w.dres();
+  RAD_TRY(mesh_count(data, soft, d, w.ms, &dr->mt, st));
+  RAD_CUDA(cudaMemcpyAsync(w.host, dr, sizeof(Result), cudaMemcpyDeviceToHost, st));
+  RAD_CUDA(cudaStreamSynchronize(st));
+  const long long nv = w.host->mt.nv, nt = w.host->mt.nt;
+  if (nv >= (1LL << 31) || nt >= (1LL << 31)) {
+    set_error("mesh too large: %lld vertices, %lld triangles", nv, nt);
+    return RAD_ERR_CAPACITY;
+  }
+  RAD_TRY(w.idx2.reserve(sizeof(int16_t) * 3 * std::max<long long>(nv, 1)));
+  if (soft) RAD_TRY(w.vt.reserve(sizeof(double) * std::max<long long>(nv, 1)));
+  RAD_TRY(w.tri.reserve(sizeof(int32_t) * 3 * std::max<long long>(nt, 1)));
+  w.vcap = (long long)(w.idx2.bytes / (3 * sizeof(int16_t)));
+  w.tcap = (long long)(w.tri.bytes / (3 * sizeof(int32_t)));
+  RAD_TRY(mesh_emit(data, soft, d, sp, w.ms, &dr->mt, w.idx2.as<int16_t>(), soft ? w.vt.as<double>() : nullptr,
+                    w.tri.as<int32_t>(), w.vcap, w.tcap, st));
+  RAD_CUDA(cudaMemcpyAsync(w.host, dr, sizeof(Result), cudaMemcpyDeviceToHost, st));
+  RAD_CUDA(cudaStreamSynchronize(st));
+  RAD_TRY(status_from_dev(w.host->mt.status));
+  mesh->n_vertices = nv;
+  mesh->n_triangles = nt;
+  mesh->n_voxels = w.host->mt.nvox;
+  mesh->vtx_idx2 = w.idx2.as<int16_t>();
+  mesh->vtx_t = soft ? w.vt.as<double>() : nullptr;
+  mesh->tri = w.tri.as<int32_t>();
+  mesh->mesh_volume = w.host->mt.vol6 / 6.0;
+  mesh->surface_area = w.host->mt.area2 * 0.5;
+  for (int k = 0; k < 3; ++k) {
+    mesh->dims[k] = dims[k];
+    mesh->spacing[k] = sp[k];
+  }
+  mesh->soft = soft ? 1 : 0;
+  return RAD_OK;
+}
+
+void fill_features(const Result& r, const int64_t dims[3], const double sp[3], bool have_diam, rad_features_t* out) {
+  (void)dims;
+  memset(out, 0, sizeof(*out));
+  out->MeshVolume = r.mt.vol6 / 6.0;
+  out->SurfaceArea = r.mt.area2 * 0.5;
+  out->VoxelVolume = (double)r.mt.nvox * sp[0] * sp[1] * sp[2];
+  out->n_vertices = r.mt.nv;
+  out->n_triangles = r.mt.nt;
+  out->n_voxels = r.mt.nvox;
+  double* D[4] = {&out->Maximum3DDiameter, &out->Maximum2DDiameterSlice, &out->Maximum2DDiameterColumn,
+                  &out->Maximum2DDiameterRow};
+  int32_t* A[4] = {out->argmax3d, out->argmax_slice, out->argmax_column, out->argmax_row};
+  for (int q = 0; q < 4; ++q) {
+    *D[q] = have_diam ? sqrt(r.dr.d2[q]) : 0.0;
+    A[q][0] = have_diam ? r.dr.i[q] : -1;
+    A[q][1] = have_diam ? r.dr.j[q] : -1;
+  }
+}
+
+// Diameters of a mesh held in `w` (vertex count known on the host).
+rad_status run_shape(const rad_mesh_t* mesh, Work& w, bool plain, rad_features_t* out, cudaStream_t st) {
+  RAD_TRY(w.init());
+  const MeshDims d = make_dims(mesh->dims);
+  Result* dr = w.dres();
+  const bool have = mesh->n_vertices >= 2;
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    RAD_CUDA(cudaMemsetAsync(&dr->dr, 0, sizeof(DiamResult) + 2 * sizeof(unsigned int), st));
+    if (have) {
+      if (plain)
+        RAD_TRY(diam_plain_fp64(mesh->vtx_idx2, mesh->vtx_t, mesh->n_vertices, d, mesh->spacing, w.ds, &dr->dr, st));
+      else
+        RAD_TRY(diam_run(mesh->vtx_idx2, mesh->vtx_t, mesh->n_vertices, &dr->mt.nv, d, mesh->spacing, w.ds, &dr->dr,
+                         &dr->status, st));
+    }
+    RAD_CUDA(cudaMemcpyAsync(w.host, dr, sizeof(Result), cudaMemcpyDeviceToHost, st));
+    RAD_CUDA(cudaStreamSynchronize(st));
+    const unsigned int s = w.host->status;
+    if (s & DEV_ERR_WORKCAP) { w.ds.work_cap *= 4; continue; }
+    if (s & DEV_ERR_CANDCAP) { w.ds.cand_cap *= 4; continue; }
+    RAD_TRY(status_from_dev(s));
+    Result r = *w.host;
+    record_stats(r, 0, have && !plain);
+    r.mt.nv = mesh->n_vertices;
+    r.mt.nt = mesh->n_triangles;
+    r.mt.nvox = mesh->n_voxels;
+    r.mt.vol6 = mesh->mesh_volume * 6.0;
+    r.mt.area2 = mesh->surface_area * 2.0;
+    fill_features(r, mesh->dims, mesh->spacing, have, out);
+    return RAD_OK;
+  }
+  return status_from_dev(w.host->status);
+}
+
+rad_status check_mesh(const rad_mesh_t* mesh) {
+  if (!mesh || !mesh->_priv) {
+    set_error("mesh is NULL or was not built by rad_mesh / rad_soft_mesh");
+    return RAD_ERR_INVALID_ARG;
+  }
+  return RAD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rad_status rad_mesh(const uint8_t* mask_dev, const int64_t dims[3], const double spacing[3], rad_mesh_t* mesh,
+                    void* stream) {
+  RAD_TRY(check_geometry(dims, spacing));
+  if (!mesh) { set_error("mesh is NULL"); return RAD_ERR_INVALID_ARG; }
+  RAD_TRY(check_device_ptr(mask_dev, "mask_dev"));
+  return run_mesh(mask_dev, false, dims, spacing, *work_of(mesh), mesh, (cudaStream_t)stream);
+}
+
+rad_status rad_soft_mesh(const float* prob_dev, const int64_t dims[3], const double spacing[3], rad_mesh_t* mesh,
+                         void* stream) {
+  RAD_TRY(check_geometry(dims, spacing));
+  if (!mesh) { set_error("mesh is NULL"); return RAD_ERR_INVALID_ARG; }
+  RAD_TRY(check_device_ptr(prob_dev, "prob_dev"));
+  return run_mesh(prob_dev, true, dims, spacing, *work_of(mesh), mesh, (cudaStream_t)stream);
+}
+
+rad_status rad_shape(const rad_mesh_t* mesh, rad_features_t* out, void* stream) {
+  RAD_TRY(check_mesh(mesh));
+  if (!out) { set_error("out is NULL"); return RAD_ERR_INVALID_ARG; }
+  return run_shape(mesh, *static_cast<Work*>(mesh->_priv), false, out, (cudaStream_t)stream);
+}
+
+rad_status rad_shape_plain_fp64(const rad_mesh_t* mesh, rad_features_t* out, void* stream) {
+  RAD_TRY(check_mesh(mesh));
+  if (!out) { set_error("out is NULL"); return RAD_ERR_INVALID_ARG; }
+  return run_shape(mesh, *static_cast<Work*>(mesh->_priv), true, out, (cudaStream_t)stream);
+}
+
+rad_status rad_mesh_copy(const rad_mesh_t* mesh, int16_t* idx2, double* t, int32_t* tri, void* stream) {
+  RAD_TRY(check_mesh(mesh));
+  cudaStream_t st = (cudaStream_t)stream;
+  if (idx2 && mesh->n_vertices)
+    RAD_CUDA(cudaMemcpyAsync(idx2, mesh->vtx_idx2, sizeof(int16_t) * 3 * mesh->n_vertices, cudaMemcpyDefault, st));
+  if (t && mesh->vtx_t && mesh->n_vertices)
+    RAD_CUDA(cudaMemcpyAsync(t, mesh->vtx_t, sizeof(double) * mesh->n_vertices, cudaMemcpyDefault, st));
+  if (tri && mesh->n_triangles)
+    RAD_CUDA(cudaMemcpyAsync(tri, mesh->tri, sizeof(int32_t) * 3 * mesh->n_triangles, cudaMemcpyDefault, st));
+  RAD_CUDA(cudaStreamSynchronize(st));
+  return RAD_OK;
+}
+
+void rad_mesh_free(rad_mesh_t* mesh) {
+  if (!mesh) return;
+  delete static_cast<Work*>(mesh->_priv);
+  memset(mesh, 0, sizeof(*mesh));
+}
+
+// Whole path with no host synchronisation inside: capacities come from the
+// previous call on this workspace (the first call sizes them with a counting
+// pass); an overflow is detected from the device status and the call re-runs
+// with grown pools.
+static rad_status extract_impl(const uint8_t* mask_dev, const int64_t dims[3], const double sp[3],
+                               rad_features_t* out, rad_workspace_t* ws, cudaStream_t st, long long h2d_bytes) {
+  Work& w = ws->work;
+  RAD_TRY(w.init());
+  const MeshDims d = make_dims(dims);
+  Result* dr = w.dres();
+  if (w.vcap == 0) {
+    RAD_TRY(run_mesh(mask_dev, false, dims, sp, w, &ws->mesh, st));
+  }
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    RAD_CUDA(cudaMemsetAsync(&dr->dr, 0, sizeof(DiamResult) + 2 * sizeof(unsigned int), st));
+    RAD_TRY(mesh_count(mask_dev, false, d, w.ms, &dr->mt, st));
+    RAD_TRY(mesh_emit(mask_dev, false, d, sp, w.ms, &dr->mt, w.idx2.as<int16_t>(), nullptr, w.tri.as<int32_t>(),
+                      w.vcap, w.tcap, st));
+    RAD_TRY(diam_run(w.idx2.as<int16_t>(), nullptr, w.vcap, &dr->mt.nv, d, sp, w.ds, &dr->dr, &dr->status, st));
+    RAD_CUDA(cudaMemcpyAsync(w.host, dr, sizeof(Result), cudaMemcpyDeviceToHost, st));
+    RAD_CUDA(cudaStreamSynchronize(st));
+    const Result& r = *w.host;
+    const unsigned int s = r.status | r.mt.status;
+    if (r.mt.nv > w.vcap || r.mt.nt > w.tcap || (s & (DEV_ERR_VCAP | DEV_ERR_TCAP))) {
+      RAD_TRY(run_mesh(mask_dev, false, dims, sp, w, &ws->mesh, st));
+      continue;
+    }
+    if (s & DEV_ERR_WORKCAP) { w.ds.work_cap *= 4; continue; }
+    if (s & DEV_ERR_CANDCAP) { w.ds.cand_cap *= 4; continue; }
+    RAD_TRY(status_from_dev(s));
+    fill_features(r, dims, sp, r.mt.nv >= 2, out);
+    record_stats(r, h2d_bytes, true);
+    return RAD_OK;
+  }
+  return status_from_dev(w.host->status | w.host->mt.status);
+}
+
+rad_status rad_extract(const uint8_t* mask_dev, const int64_t dims[3], const double spacing[3], rad_features_t* out,
+                       rad_workspace_t** ws, void* stream) {
+  RAD_TRY(check_geometry(dims, spacing));
+  if (!out || !ws) { set_error("out and ws must be non-NULL"); return RAD_ERR_INVALID_ARG; }
+  RAD_TRY(check_device_ptr(mask_dev, "mask_dev"));
+  if (!*ws) {
+    *ws = new rad_workspace();
+    memset(&(*ws)->mesh, 0, sizeof(rad_mesh_t));
+  }
+  return extract_impl(mask_dev, dims, spacing, out, *ws, (cudaStream_t)stream, 0);
+}
+
+rad_status rad_extract_host(const uint8_t* mask_host, const int64_t dims[3], const double spacing[3],
+                            rad_features_t* out, rad_workspace_t** ws, void* stream) {
+  RAD_TRY(check_geometry(dims, spacing));
+  if (!out || !ws || !mask_host) { set_error("mask_host, out and ws must be non-NULL"); return RAD_ERR_INVALID_ARG; }
+  if (!*ws) {
+    *ws = new rad_workspace();
+    memset(&(*ws)->mesh, 0, sizeof(rad_mesh_t));
+  }
+  Work& w = (*ws)->work;
+  const size_t bytes = (size_t)dims[0] * dims[1] * dims[2];
+  RAD_TRY(w.mask.reserve(bytes));
+  RAD_CUDA(cudaMemcpyAsync(w.mask.p, mask_host, bytes, cudaMemcpyHostToDevice, (cudaStream_t)stream));
+  return extract_impl(w.mask.as<uint8_t>(), dims, spacing, out, *ws, (cudaStream_t)stream, (long long)bytes);
+}
+
+void rad_workspace_free(rad_workspace_t* ws) { delete ws; }
+
+rad_status rad_set_tuning(const rad_tuning_t* set, rad_tuning_t* get) {
+  if (set) {
+    const bool ok_tile = set->tile == 64 || set->tile == 128 || set->tile == 256;
+    const bool ok_thr = (set->tile == 64 && (set->threads == 64 || set->threads == 128)) ||
+                        (set->tile == 128 && (set->threads == 64 || set->threads == 128 || set->threads == 256)) ||
+                        (set->tile == 256 && (set->threads == 128 || set->threads == 256));
+    if (!ok_tile || !ok_thr || set->ctas_per_sm < 1 || set->ctas_per_sm > 16 || set->cell_shift < 2 ||
+        set->cell_shift > 7) {
+      set_error("invalid tuning (tile %d, threads %d, ctas_per_sm %d, cell_shift %d)", set->tile, set->threads,
+                set->ctas_per_sm, set->cell_shift);
+      return RAD_ERR_INVALID_ARG;
+    }
+    g_tuning = *set;
+  }
+  if (get) *get = g_tuning;
+  return RAD_OK;
+}
+
+rad_status rad_profile_enable(int on) {
+  Prof& p = prof();
+  std::lock_guard<std::mutex> g(p.mu);
+  p.on = on != 0;
+  return RAD_OK;
+}
+
+int rad_profile_read(rad_kernel_stat_t* out, int cap) {
+  Prof& p = prof();
+  std::lock_guard<std::mutex> g(p.mu);
+  flush_pending(p);
+  const int n = (int)p.stats.size();
+  for (int i = 0; i < n && i < cap && out; ++i) out[i] = p.stats[i];
+  return n;
+}
+
+void rad_profile_reset(void) {
+  Prof& p = prof();
+  std::lock_guard<std::mutex> g(p.mu);
+  flush_pending(p);
+  p.stats.clear();
+}
+
+int64_t rad_launch_count(void) {
+  Prof& p = prof();
+  std::lock_guard<std::mutex> g(p.mu);
+  return p.launches;
+}
+
+const char* rad_status_str(rad_status s) {
+  switch (s) {
+    case RAD_OK: return "RAD_OK";
+    case RAD_ERR_INVALID_ARG: return "RAD_ERR_INVALID_ARG";
+    case RAD_ERR_CUDA: return "RAD_ERR_CUDA";
+    case RAD_ERR_CAPACITY: return "RAD_ERR_CAPACITY";
+    case RAD_ERR_TIMEOUT: return "RAD_ERR_TIMEOUT";
+    case RAD_ERR_OOM: return "RAD_ERR_OOM";
+    case RAD_ERR_INTERNAL: return "RAD_ERR_INTERNAL";
+  }
+  return "RAD_ERR_UNKNOWN";
+}
+
+const char* rad_last_error(void) { return g_err; }
+
+rad_status rad_last_call_stats(rad_call_stats_t* out) {
+  if (!out) { set_error("out is NULL"); return RAD_ERR_INVALID_ARG; }
+  *out = g_stats;
+  return RAD_OK;
+}
+
+}  // extern "C"

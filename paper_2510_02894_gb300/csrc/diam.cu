@@ -1,0 +1,910 @@
+// Maximum 3D and planar diameters over the mesh vertices (paper Sec. 2,
+// "Parallel diameter calculation": each thread scans a subset of vertex pairs
+// into a local maximum, then a reduction combines the local maxima).
+//
+// GB300 design (FP32 filter, FP64 confirmation):
+//   1. Every vertex gets four keys -- a spatial cell (3D problem) and its
+//      Slice (z), Column (y) and Row (x) plane -- and one counting sort lays
+//      the vertices out as float4 (x, y, z in FP32, centred and scaled; w =
+//      vertex id).  The 3D problem is the whole cell-sorted range; every plane
+//      with two or more vertices is its own problem.
+//   2. Each problem is cut into tiles of TS vertices; a tile gets its
+//      bounding box and 14 directional extremes.  The pairs of each
+//      problem's extremes seed its running maximum F.
+//   3. Tile pairs whose farthest-corner bound cannot reach the threshold
+//      T(F) are culled; the rest form a device work list.
+//   4. A persistent kernel evaluates the surviving tile pairs in FP32 from
+//      shared memory (6 FP32 operations per pair, warp max, one atomic max
+//      per tile pair on F), re-culling each item against the current F.
+//   5. Pairs with f >= T(F) become candidates and are re-evaluated in FP64
+//      with the pinned formula; max d2, then the smallest (i, j).
+//
+// FP32 error bound (per pair, binary or soft; u = 2^-24, positions a relative
+// to the grid centre, R = the grid's half extent in mm):
+//   P_k = fl32(a_k),  dx = fl(P_i - P_j),  f = fma(dz,dz, fma(dy,dy, dx*dx))
+//   |f - d2| <= 5.1u d2 + 4.1u |R| sqrt(d2) + 4.1u^2 |R|^2.
+// T(F) inverts this bound (with every coefficient doubled), so every pair
+// attaining the FP64 maximum has f >= T(F) for any F not above the largest
+// f; the culling bound uses the same monotone FP32 operations on box
+// distances, so it bounds f from above without any epsilon.
+#include <float.h>
+#include <math.h>
+#include <stdio.h>
+
+#include <algorithm>
+
+#include "rad_internal.cuh"
+
+namespace rad {
+
+namespace {
+
+constexpr int kNumDirs = 14;
+
+struct Problem {
+  int axis;  // -1: 3D, 0: Row (equal x), 1: Column (equal y), 2: Slice (equal z)
+  int beg, len;
+  int tile_beg;  // first tile
+  long long pair_beg;
+};
+
+struct Tile {
+  int problem, beg, len, pad;
+};
+
+struct WorkItem {
+  int problem, ta, tb, pad;
+};
+
+struct Cand {
+  int ea, eb, problem, pad;
+};
+
+struct ProblemState {
+  unsigned int F;  // float bits of the running FP32 maximum
+  unsigned int pad;
+  unsigned long long ext[kNumDirs];  // directional extremes: (ordered value << 32) | entry
+  unsigned long long best_d2;        // FP64 bits of the confirmed maximum
+  unsigned long long best_pair;      // (i << 32) | j, smallest among the maxima
+};
+
+struct Counters {
+  int n_problems;
+  int n_tiles;
+  long long n_pairs;
+  long long n_work;
+  long long n_cand;
+  int ticket;
+  int ticket2;
+  unsigned int status;
+  int pad;
+  unsigned long long items_evaluated, pairs_evaluated;
+};
+
+struct Params {
+  int nx, ny, nz;
+  int soft, planes;
+  int cell_shift, CX, CY, CZ;
+  long long C3, K;  // 3D cells; total keys
+  double sx, sy, sz;
+  double cx, cy, cz;  // centre (index units)
+  double alpha, beta, gamma;
+  int TS;
+  long long work_cap, cand_cap, max_problems, max_tiles;
+  long long nv_cap;  // vertex pool capacity: device counts are clamped to it
+};
+
+__device__ __forceinline__ unsigned int ord_float(float f) {
+  unsigned int b = __float_as_uint(f);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+__device__ __forceinline__ float pair_f(float4 a, float4 b) {
+  const float dx = __fsub_rn(a.x, b.x), dy = __fsub_rn(a.y, b.y), dz = __fsub_rn(a.z, b.z);
+  float f = __fmul_rn(dx, dx);
+  f = __fmaf_rn(dy, dy, f);
+  return __fmaf_rn(dz, dz, f);
+}
+
+// Threshold T(F): every pair attaining the FP64 maximum has f >= T(F).
+__device__ __forceinline__ float threshold(float F, const Params& p) {
+  const double f = (double)F;
+  if (!(f > p.gamma)) return 0.0f;
+  const double a1 = 1.0 + p.alpha;
+  const double s = (-p.beta + sqrt(p.beta * p.beta + 4.0 * a1 * (f - p.gamma))) / (2.0 * a1);
+  const double t = (1.0 - p.alpha) * s * s - p.beta * s - p.gamma;
+  return t > 0.0 ? __double2float_rd(t) : 0.0f;
+}
+
+// Upper bound of f over all pairs of two boxes (same monotone operations).
+__device__ __forceinline__ float box_ub(float4 alo, float4 ahi, float4 blo, float4 bhi) {
+  const float mx = fmaxf(__fsub_rn(bhi.x, alo.x), __fsub_rn(ahi.x, blo.x));
+  const float my = fmaxf(__fsub_rn(bhi.y, alo.y), __fsub_rn(ahi.y, blo.y));
+  const float mz = fmaxf(__fsub_rn(bhi.z, alo.z), __fsub_rn(ahi.z, blo.z));
+  float f = __fmul_rn(mx, mx);
+  f = __fmaf_rn(my, my, f);
+  return __fmaf_rn(mz, mz, f);
+}
+
+__device__ __forceinline__ void vertex_q(const int16_t* idx2, long long v, int q[3]) {
+  q[0] = idx2[3 * v];
+  q[1] = idx2[3 * v + 1];
+  q[2] = idx2[3 * v + 2];
+}
+
+// ---- 1. keys, histogram, scatter ------------------------------------------------
+
+__device__ __forceinline__ long long key_of(const Params& p, const int q[3], int kind) {
+  if (kind == 0) {
+    const int cx = (q[0] + 1) >> p.cell_shift, cy = (q[1] + 1) >> p.cell_shift, cz = (q[2] + 1) >> p.cell_shift;
+    return ((long long)cz * p.CY + cy) * p.CX + cx;
+  }
+  if (kind == 1) return p.C3 + (q[2] + 1);                                       // Slice: z plane
+  if (kind == 2) return p.C3 + (2LL * p.nz + 1) + (q[1] + 1);                    // Column: y plane
+  return p.C3 + (2LL * p.nz + 1) + (2LL * p.ny + 1) + (q[0] + 1);                // Row: x plane
+}
+
+__global__ void k_hist(const int16_t* __restrict__ idx2, const long long* __restrict__ nv_dev, Params p,
+                       int* __restrict__ hist) {
+  const long long n = min(*nv_dev, p.nv_cap);
+  const int kinds = p.planes ? 4 : 1;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
+    int q[3];
+    vertex_q(idx2, v, q);
+    for (int k = 0; k < kinds; ++k) atomicAdd(&hist[key_of(p, q, k)], 1);
+  }
+}
+
+__global__ void k_scatter(const int16_t* __restrict__ idx2, const double* __restrict__ vt,
+                          const long long* __restrict__ nv_dev, Params p, const long long* __restrict__ offs,
+                          int* __restrict__ cursor, float4* __restrict__ sorted) {
+  const long long n = min(*nv_dev, p.nv_cap);
+  const int kinds = p.planes ? 4 : 1;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
+    int q[3];
+    vertex_q(idx2, v, q);
+    double u[3];
+    vertex_u(idx2, vt, v, u);
+    const float4 e = make_float4(__double2float_rn((u[0] - p.cx) * p.sx), __double2float_rn((u[1] - p.cy) * p.sy),
+                                 __double2float_rn((u[2] - p.cz) * p.sz), __int_as_float((int)v));
+    for (int k = 0; k < kinds; ++k) {
+      const long long key = key_of(p, q, k);
+      const long long pos = offs[key] + atomicAdd(&cursor[key], 1);
+      sorted[pos] = e;
+    }
+  }
+}
+
+// Generic exclusive scan of int counts to long long offsets (3 kernels).
+constexpr int kScanBlock = 1024;
+__global__ void k_xscan_part(const int* __restrict__ in, long long n, long long* __restrict__ out,
+                             long long* __restrict__ part) {
+  __shared__ long long ws[32];
+  const long long i = blockIdx.x * (long long)kScanBlock + threadIdx.x;
+  long long v = i < n ? in[i] : 0;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  long long inc = v;
+  for (int off = 1; off < 32; off <<= 1) {
+    const long long o = __shfl_up_sync(0xffffffffu, inc, off);
+    if (lane >= off) inc += o;
+  }
+  if (lane == 31) ws[wid] = inc;
+  __syncthreads();
+  long long wb = 0, tot = 0;
+  for (int k = 0; k < kScanBlock / 32; ++k) {
+    if (k < wid) wb += ws[k];
+    tot += ws[k];
+  }
+  if (i < n) out[i] = wb + inc - v;
+  if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+__global__ void k_xscan_top(long long* __restrict__ part, int nparts, long long* __restrict__ total) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    long long s = 0;
+    for (int i = 0; i < nparts; ++i) {
+      const long long v = part[i];
+      part[i] = s;
+      s += v;
+    }
+    if (total) *total = s;
+  }
+}
+
+__global__ void k_xscan_add(long long* __restrict__ out, long long n, const long long* __restrict__ part) {
+  const long long i = blockIdx.x * (long long)kScanBlock + threadIdx.x;
+  if (i < n) out[i] += part[blockIdx.x];
+}
+
+// ---- 2. problems and tiles --------------------------------------------------------
+
+// Problem 0 is the 3D range [0, N).  Every plane bin with >= 2 vertices
+// becomes a problem.  Plane problems are appended in key order by a
+// single-pass compaction (one thread per key, atomic append; order does
+// not affect the result).
+__global__ void k_problems(const long long* __restrict__ nv_dev, Params p, const int* __restrict__ hist,
+                           const long long* __restrict__ offs, Problem* __restrict__ probs,
+                           Counters* __restrict__ cnt) {
+  const long long n = min(*nv_dev, p.nv_cap);
+  const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (gid == 0) {
+    Problem q;
+    q.axis = -1; q.beg = 0; q.len = (int)n; q.tile_beg = 0; q.pair_beg = 0;
+    probs[0] = q;
+  }
+  if (!p.planes) return;
+  const long long nplane = p.K - p.C3;
+  for (long long k = gid; k < nplane; k += (long long)gridDim.x * blockDim.x) {
+    const long long key = p.C3 + k;
+    const int c = hist[key];
+    if (c < 2) continue;
+    int axis;
+    if (k < 2LL * p.nz + 1) axis = 2;
+    else if (k < 2LL * p.nz + 1 + 2LL * p.ny + 1) axis = 1;
+    else axis = 0;
+    const int slot = 1 + atomicAdd(&cnt->n_problems, 1);
+    if (slot >= p.max_problems) { atomicOr(&cnt->status, DEV_ERR_PROBCAP); continue; }
+    Problem q;
+    q.axis = axis; q.beg = (int)offs[key]; q.len = c; q.tile_beg = 0; q.pair_beg = 0;
+    probs[slot] = q;
+  }
+}
+
+// One block: tile and pair prefixes over problems.
+__global__ void k_problem_scan(Problem* __restrict__ probs, Params p, Counters* __restrict__ cnt) {
+  __shared__ long long st[32], sp2[32];
+  const int np = 1 + min(cnt->n_problems, (int)p.max_problems - 1);
+  long long carry_t = 0, carry_p = 0;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int base = 0; base < np; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    long long nt = 0, npairs = 0;
+    if (i < np) {
+      nt = (probs[i].len + p.TS - 1) / p.TS;
+      npairs = probs[i].len >= 2 ? nt * (nt + 1) / 2 : 0;
+    }
+    long long it = nt, ip = npairs;
+    for (int off = 1; off < 32; off <<= 1) {
+      const long long a = __shfl_up_sync(0xffffffffu, it, off), b = __shfl_up_sync(0xffffffffu, ip, off);
+      if (lane >= off) { it += a; ip += b; }
+    }
+    if (lane == 31) { st[wid] = it; sp2[wid] = ip; }
+    __syncthreads();
+    long long wt = 0, wp = 0, bt = 0, bp = 0;
+    for (int k = 0; k < nw; ++k) {
+      if (k < wid) { wt += st[k]; wp += sp2[k]; }
+      bt += st[k]; bp += sp2[k];
+    }
+    if (i < np) {
+      probs[i].tile_beg = (int)(carry_t + wt + it - nt);
+      probs[i].pair_beg = carry_p + wp + ip - npairs;
+    }
+    carry_t += bt;
+    carry_p += bp;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    cnt->n_problems = np;
+    cnt->n_tiles = (int)carry_t;
+    cnt->n_pairs = carry_p;
+    if (carry_t > p.max_tiles) atomicOr(&cnt->status, DEV_ERR_PROBCAP);
+  }
+}
+
+__global__ void k_tiles(const Problem* __restrict__ probs, Params p, const Counters* __restrict__ cnt,
+                        Tile* __restrict__ tiles) {
+  const int np = cnt->n_problems;
+  const int lane = threadIdx.x & 31;
+  const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long i = warp; i < np; i += nwarps) {
+    const Problem q = probs[i];
+    const int nt = (q.len + p.TS - 1) / p.TS;
+    for (int t = lane; t < nt; t += 32) {
+      const long long ti = (long long)q.tile_beg + t;
+      if (ti >= p.max_tiles) break;
+      Tile tl;
+      tl.problem = (int)i;
+      tl.beg = q.beg + t * p.TS;
+      tl.len = min(p.TS, q.len - t * p.TS);
+      tl.pad = 0;
+      tiles[ti] = tl;
+    }
+  }
+}
+
+__constant__ float c_dirs[kNumDirs][3] = {{1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1},
+                                          {0, 0, -1}, {1, 1, 1}, {1, 1, -1}, {1, -1, 1}, {1, -1, -1},
+                                          {-1, 1, 1}, {-1, 1, -1}, {-1, -1, 1}, {-1, -1, -1}};
+
+// One block (128 threads) per tile: bounding box and directional extremes.
+__global__ void k_tile_box(const float4* __restrict__ sorted, const Tile* __restrict__ tiles, Params p,
+                           const Counters* __restrict__ cnt, float4* __restrict__ box,
+                           ProblemState* __restrict__ ps) {
+  const int nt = min(cnt->n_tiles, (int)p.max_tiles);
+  __shared__ float s_lo[3][4], s_hi[3][4];
+  __shared__ unsigned long long s_ext[kNumDirs][4];
+  for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
+    const Tile tl = tiles[ti];
+    float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+    unsigned long long ext[kNumDirs];
+    for (int k = 0; k < kNumDirs; ++k) ext[k] = 0ull;
+    for (int i = threadIdx.x; i < tl.len; i += blockDim.x) {
+      const int e = tl.beg + i;
+      const float4 v = sorted[e];
+      lo[0] = fminf(lo[0], v.x); lo[1] = fminf(lo[1], v.y); lo[2] = fminf(lo[2], v.z);
+      hi[0] = fmaxf(hi[0], v.x); hi[1] = fmaxf(hi[1], v.y); hi[2] = fmaxf(hi[2], v.z);
+      for (int k = 0; k < kNumDirs; ++k) {
+        const float pr = c_dirs[k][0] * v.x + c_dirs[k][1] * v.y + c_dirs[k][2] * v.z;
+        const unsigned long long key = ((unsigned long long)ord_float(pr) << 32) | (unsigned int)e;
+        ext[k] = max(ext[k], key);
+      }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      for (int k = 0; k < 3; ++k) {
+        lo[k] = fminf(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], off));
+        hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], off));
+      }
+      for (int k = 0; k < kNumDirs; ++k) ext[k] = max(ext[k], __shfl_xor_sync(0xffffffffu, ext[k], off));
+    }
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+      for (int k = 0; k < 3; ++k) { s_lo[k][wid] = lo[k]; s_hi[k][wid] = hi[k]; }
+      for (int k = 0; k < kNumDirs; ++k) s_ext[k][wid] = ext[k];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const int nw = blockDim.x >> 5;
+      for (int w = 1; w < nw; ++w) {
+        for (int k = 0; k < 3; ++k) { s_lo[k][0] = fminf(s_lo[k][0], s_lo[k][w]); s_hi[k][0] = fmaxf(s_hi[k][0], s_hi[k][w]); }
+        for (int k = 0; k < kNumDirs; ++k) s_ext[k][0] = max(s_ext[k][0], s_ext[k][w]);
+      }
+      box[2 * ti] = make_float4(s_lo[0][0], s_lo[1][0], s_lo[2][0], 0.f);
+      box[2 * ti + 1] = make_float4(s_hi[0][0], s_hi[1][0], s_hi[2][0], 0.f);
+      for (int k = 0; k < kNumDirs; ++k)
+        if (s_ext[k][0]) atomicMax(&ps[tl.problem].ext[k], s_ext[k][0]);
+    }
+    __syncthreads();
+  }
+}
+
+// One warp per problem: the pairs of its directional extremes seed F.
+__global__ void k_seed(const float4* __restrict__ sorted, Params p, const Counters* __restrict__ cnt,
+                       ProblemState* __restrict__ ps) {
+  const int np = cnt->n_problems;
+  const int lane = threadIdx.x & 31;
+  const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long i = warp; i < np; i += nwarps) {
+    float best = 0.0f;
+    for (int pr = lane; pr < kNumDirs * kNumDirs; pr += 32) {
+      const int a = pr / kNumDirs, b = pr % kNumDirs;
+      if (b <= a) continue;
+      const unsigned long long ka = ps[i].ext[a], kb = ps[i].ext[b];
+      if (!ka || !kb) continue;
+      const float4 va = sorted[(unsigned int)ka], vb = sorted[(unsigned int)kb];
+      best = fmaxf(best, pair_f(va, vb));
+    }
+    for (int off = 16; off > 0; off >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, off));
+    if (lane == 0) atomicMax(&ps[i].F, __float_as_uint(best));
+  }
+}
+
+// ---- 3. culling -------------------------------------------------------------------
+
+__device__ __forceinline__ int find_problem(const Problem* probs, int np, long long g) {
+  int lo = 0, hi = np - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (probs[mid].pair_beg <= g) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void k_cull(const Problem* __restrict__ probs, const float4* __restrict__ box, Params p,
+                       Counters* __restrict__ cnt, const ProblemState* __restrict__ ps,
+                       WorkItem* __restrict__ work) {
+  const int np = cnt->n_problems;
+  const long long total = cnt->n_pairs;
+  const int lane = threadIdx.x & 31;
+  for (long long g0 = blockIdx.x * (long long)blockDim.x; g0 < total; g0 += (long long)gridDim.x * blockDim.x) {
+    const long long g = g0 + threadIdx.x;
+    bool keep = false;
+    WorkItem w;
+    if (g < total) {
+      const int pi = find_problem(probs, np, g);
+      const Problem q = probs[pi];
+      const long long l = g - q.pair_beg;
+      long long b = (long long)((sqrt(8.0 * (double)l + 1.0) - 1.0) * 0.5);
+      while (b * (b + 1) / 2 > l) --b;
+      while ((b + 1) * (b + 2) / 2 <= l) ++b;
+      const long long a = l - b * (b + 1) / 2;
+      const int ta = q.tile_beg + (int)a, tb = q.tile_beg + (int)b;
+      if (tb < p.max_tiles) {
+        const float ub = box_ub(box[2 * ta], box[2 * ta + 1], box[2 * tb], box[2 * tb + 1]);
+        const float T = threshold(__uint_as_float(ps[pi].F), p);
+        keep = ub >= T;
+      }
+      w.problem = pi; w.ta = ta; w.tb = tb; w.pad = 0;
+    }
+    const unsigned int m = __ballot_sync(0xffffffffu, keep);
+    long long base = 0;
+    if (lane == 0 && m) base = atomicAdd((unsigned long long*)&cnt->n_work, (unsigned long long)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (keep) {
+      const long long slot = base + __popc(m & ((1u << lane) - 1u));
+      if (slot < p.work_cap) work[slot] = w;
+      else atomicOr(&cnt->status, DEV_ERR_WORKCAP);
+    }
+  }
+}
+
+// ---- 4./5. pair kernels ------------------------------------------------------------
+
+// Evaluates one tile pair from shared memory.  NT threads; lane l of every
+// warp holds the A entries l, l + 32, ...; warp w scans its slice of B.
+template <int TS, int NT, bool CAND>
+__device__ __forceinline__ float eval_pair_tile(const float4* __restrict__ sorted, const Tile& A, const Tile& B,
+                                                float4* sB, float T, int problem, Cand* cand, Counters* cnt,
+                                                long long cand_cap) {
+  constexpr int RA = TS / 32;
+  constexpr int NWARP = NT / 32;
+  constexpr int BSL = TS / NWARP;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < TS; i += NT) sB[i] = i < B.len ? sorted[B.beg + i] : sorted[B.beg];
+  float4 a[RA];
+  for (int r = 0; r < RA; ++r) {
+    const int ia = lane + 32 * r;
+    a[r] = sorted[A.beg + min(ia, A.len - 1)];
+  }
+  __syncthreads();
+  float mx[RA];
+  for (int r = 0; r < RA; ++r) mx[r] = 0.0f;
+  const int jb = wid * BSL;
+  const int je = min(jb + BSL, B.len);
+  if (!CAND) {
+#pragma unroll 4
+    for (int j = jb; j < je; ++j) {
+      const float4 b = sB[j];
+#pragma unroll
+      for (int r = 0; r < RA; ++r) mx[r] = fmaxf(mx[r], pair_f(a[r], b));
+    }
+  } else {
+    for (int j = jb; j < je; ++j) {
+      const float4 b = sB[j];
+      for (int r = 0; r < RA; ++r) {
+        const int ia = lane + 32 * r;
+        if (ia >= A.len) continue;
+        const int ea = A.beg + ia, eb = B.beg + j;
+        if (A.beg == B.beg && ea >= eb) continue;  // same tile: each unordered pair once
+        const float f = pair_f(a[r], b);
+        if (f >= T) {
+          const long long slot = atomicAdd((unsigned long long*)&cnt->n_cand, 1ull);
+          if (slot < cand_cap) {
+            Cand c;
+            c.ea = ea; c.eb = eb; c.problem = problem; c.pad = 0;
+            cand[slot] = c;
+          } else {
+            atomicOr(&cnt->status, DEV_ERR_CANDCAP);
+          }
+        }
+      }
+    }
+  }
+  float m = 0.0f;
+  for (int r = 0; r < RA; ++r)
+    if (lane + 32 * r < A.len) m = fmaxf(m, mx[r]);
+  return m;
+}
+
+template <int TS, int NT>
+__global__ void __launch_bounds__(NT) k_pairs_max(const float4* __restrict__ sorted, const Tile* __restrict__ tiles,
+                                                  const float4* __restrict__ box, const WorkItem* __restrict__ work,
+                                                  Params p, Counters* __restrict__ cnt, ProblemState* __restrict__ ps,
+                                                  float* __restrict__ itemmax) {
+  __shared__ float4 sB[TS];
+  __shared__ float sred[NT / 32];
+  __shared__ long long s_item;
+  const long long nwork = min(cnt->n_work, p.work_cap);
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(&cnt->ticket, 1);
+    __syncthreads();
+    const long long it = s_item;
+    if (it >= nwork) break;
+    const WorkItem w = work[it];
+    const float T = threshold(__uint_as_float(*(volatile unsigned int*)&ps[w.problem].F), p);
+    const float ub = box_ub(box[2 * w.ta], box[2 * w.ta + 1], box[2 * w.tb], box[2 * w.tb + 1]);
+    if (ub < T) {
+      if (threadIdx.x == 0) itemmax[it] = -1.0f;
+      __syncthreads();
+      continue;
+    }
+    const Tile A = tiles[w.ta], B = tiles[w.tb];
+    float m = eval_pair_tile<TS, NT, false>(sorted, A, B, sB, T, w.problem, nullptr, cnt, 0);
+    for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float bm = sred[0];
+      for (int k = 1; k < NT / 32; ++k) bm = fmaxf(bm, sred[k]);
+      itemmax[it] = bm;
+      atomicMax(&ps[w.problem].F, __float_as_uint(bm));
+      atomicAdd(&cnt->items_evaluated, 1ull);
+      atomicAdd(&cnt->pairs_evaluated, (unsigned long long)A.len * (unsigned long long)B.len);
+    }
+    __syncthreads();
+  }
+}
+
+template <int TS, int NT>
+__global__ void __launch_bounds__(NT) k_pairs_cand(const float4* __restrict__ sorted, const Tile* __restrict__ tiles,
+                                                   const WorkItem* __restrict__ work, Params p,
+                                                   Counters* __restrict__ cnt, const ProblemState* __restrict__ ps,
+                                                   const float* __restrict__ itemmax, Cand* __restrict__ cand) {
+  __shared__ float4 sB[TS];
+  __shared__ long long s_item;
+  const long long nwork = min(cnt->n_work, p.work_cap);
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(&cnt->ticket2, 1);
+    __syncthreads();
+    const long long it = s_item;
+    if (it >= nwork) break;
+    const WorkItem w = work[it];
+    const float T = threshold(__uint_as_float(ps[w.problem].F), p);
+    if (!(itemmax[it] >= T)) {
+      __syncthreads();
+      continue;
+    }
+    const Tile A = tiles[w.ta], B = tiles[w.tb];
+    eval_pair_tile<TS, NT, true>(sorted, A, B, sB, T, w.problem, cand, cnt, p.cand_cap);
+    __syncthreads();
+  }
+}
+
+// ---- 5. FP64 confirmation -------------------------------------------------------------
+
+__global__ void k_confirm(const float4* __restrict__ sorted, const int16_t* __restrict__ idx2,
+                          const double* __restrict__ vt, Params p, const Counters* __restrict__ cnt,
+                          const Cand* __restrict__ cand, ProblemState* __restrict__ ps) {
+  const long long nc = min(cnt->n_cand, p.cand_cap);
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nc; c += (long long)gridDim.x * blockDim.x) {
+    const Cand k = cand[c];
+    const int i = __float_as_int(sorted[k.ea].w), j = __float_as_int(sorted[k.eb].w);
+    double ui[3], uj[3];
+    vertex_u(idx2, vt, i, ui);
+    vertex_u(idx2, vt, j, uj);
+    const double d2 = pin_d2(ui[0], ui[1], ui[2], uj[0], uj[1], uj[2], p.sx, p.sy, p.sz);
+    atomicMax(&ps[k.problem].best_d2, (unsigned long long)__double_as_longlong(d2));
+  }
+}
+
+__global__ void k_tiebreak(const float4* __restrict__ sorted, const int16_t* __restrict__ idx2,
+                           const double* __restrict__ vt, Params p, const Counters* __restrict__ cnt,
+                           const Cand* __restrict__ cand, ProblemState* __restrict__ ps) {
+  const long long nc = min(cnt->n_cand, p.cand_cap);
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nc; c += (long long)gridDim.x * blockDim.x) {
+    const Cand k = cand[c];
+    int i = __float_as_int(sorted[k.ea].w), j = __float_as_int(sorted[k.eb].w);
+    double ui[3], uj[3];
+    vertex_u(idx2, vt, i, ui);
+    vertex_u(idx2, vt, j, uj);
+    const double d2 = pin_d2(ui[0], ui[1], ui[2], uj[0], uj[1], uj[2], p.sx, p.sy, p.sz);
+    if ((unsigned long long)__double_as_longlong(d2) == ps[k.problem].best_d2) {
+      if (i > j) { const int t = i; i = j; j = t; }
+      atomicMin(&ps[k.problem].best_pair, ((unsigned long long)(unsigned int)i << 32) | (unsigned int)j);
+    }
+  }
+}
+
+struct BestD {
+  double d2;
+  int i, j;
+};
+
+__device__ __forceinline__ bool better(double d2, int i, int j, const BestD& b) {
+  if (b.i < 0) return i >= 0;
+  if (i < 0) return false;
+  if (d2 != b.d2) return d2 > b.d2;
+  if (i != b.i) return i < b.i;
+  return j < b.j;
+}
+
+// One block: per category, the best problem result (max d2, smallest pair).
+__global__ void k_finalize(const Problem* __restrict__ probs, const Counters* __restrict__ cnt,
+                           const ProblemState* __restrict__ ps, DiamResult* __restrict__ out,
+                           unsigned int* __restrict__ status) {
+  __shared__ BestD s[4][32];
+  const int np = cnt->n_problems;
+  BestD b[4];
+  for (int q = 0; q < 4; ++q) { b[q].d2 = 0.0; b[q].i = -1; b[q].j = -1; }
+  for (int i = threadIdx.x; i < np; i += blockDim.x) {
+    const Problem pr = probs[i];
+    const int q = pr.axis < 0 ? 0 : (pr.axis == 2 ? 1 : (pr.axis == 1 ? 2 : 3));
+    const unsigned long long bp = ps[i].best_pair;
+    if (bp == ~0ull) continue;
+    const double d2 = __longlong_as_double((long long)ps[i].best_d2);
+    const int bi = (int)(bp >> 32), bj = (int)(bp & 0xffffffffu);
+    if (better(d2, bi, bj, b[q])) { b[q].d2 = d2; b[q].i = bi; b[q].j = bj; }
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int q = 0; q < 4; ++q) {
+    for (int off = 16; off > 0; off >>= 1) {
+      BestD o;
+      o.d2 = __shfl_xor_sync(0xffffffffu, b[q].d2, off);
+      o.i = __shfl_xor_sync(0xffffffffu, b[q].i, off);
+      o.j = __shfl_xor_sync(0xffffffffu, b[q].j, off);
+      if (better(o.d2, o.i, o.j, b[q])) b[q] = o;
+    }
+    if (lane == 0) s[q][wid] = b[q];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < 4; ++q) {
+      BestD r = s[q][0];
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+        if (better(s[q][w].d2, s[q][w].i, s[q][w].j, r)) r = s[q][w];
+      out->d2[q] = r.i >= 0 ? r.d2 : 0.0;
+      out->i[q] = r.i;
+      out->j[q] = r.j;
+    }
+    out->problems = cnt->n_problems;
+    out->tiles = cnt->n_tiles;
+    out->tile_pairs = cnt->n_pairs;
+    out->work_items = cnt->n_work;
+    out->items_evaluated = (long long)cnt->items_evaluated;
+    out->pairs_evaluated = (long long)cnt->pairs_evaluated;
+    out->candidates = cnt->n_cand;
+    if (cnt->status) atomicOr(status, cnt->status);
+  }
+}
+
+__global__ void k_init_states(ProblemState* __restrict__ ps, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    ProblemState s;
+    s.F = 0u;
+    s.pad = 0u;
+    for (int k = 0; k < kNumDirs; ++k) s.ext[k] = 0ull;
+    s.best_d2 = 0ull;
+    s.best_pair = ~0ull;
+    ps[i] = s;
+  }
+}
+
+template <class T>
+T* carve(char*& cur, size_t n) {
+  T* r = reinterpret_cast<T*>(cur);
+  cur += (n * sizeof(T) + 255) & ~size_t(255);
+  return r;
+}
+
+template <int TS, int NT>
+rad_status launch_pairs(const float4* sorted, const Tile* tiles, const float4* box, const WorkItem* work,
+                        const Params& p, Counters* cnt, ProblemState* ps, float* itemmax, Cand* cand, int ctas,
+                        cudaStream_t st) {
+  auto kmax = k_pairs_max<TS, NT>;
+  auto kcand = k_pairs_cand<TS, NT>;
+  RAD_LAUNCH("diam_pairs_fp32", kmax, ctas, NT, 0, st, sorted, tiles, box, work, p, cnt, ps, itemmax);
+  RAD_LAUNCH("diam_pairs_cand", kcand, ctas, NT, 0, st, sorted, tiles, work, p, cnt, ps, itemmax, cand);
+  return RAD_OK;
+}
+
+}  // namespace
+
+rad_status diam_run(const int16_t* idx2, const double* vt, long long nv_hint, const long long* nv_dev,
+                    const MeshDims& d, const double sp[3], DiamScratch& s, DiamResult* out_dev,
+                    unsigned int* status_dev, cudaStream_t st) {
+  const rad_tuning_t& tu = tuning();
+  Params p;
+  p.nx = d.nx; p.ny = d.ny; p.nz = d.nz;
+  p.soft = vt != nullptr;
+  p.planes = vt == nullptr;
+  p.cell_shift = tu.cell_shift;
+  p.CX = ((2 * d.nx) >> p.cell_shift) + 1;
+  p.CY = ((2 * d.ny) >> p.cell_shift) + 1;
+  p.CZ = ((2 * d.nz) >> p.cell_shift) + 1;
+  p.C3 = (long long)p.CX * p.CY * p.CZ;
+  p.K = p.C3 + (p.planes ? (2LL * d.nx + 1) + (2LL * d.ny + 1) + (2LL * d.nz + 1) : 0);
+  p.sx = sp[0]; p.sy = sp[1]; p.sz = sp[2];
+  p.cx = 0.5 * (d.nx - 1); p.cy = 0.5 * (d.ny - 1); p.cz = 0.5 * (d.nz - 1);
+  const double u = ldexp(1.0, -24);
+  double R2 = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    const int n = k == 0 ? d.nx : (k == 1 ? d.ny : d.nz);
+    const double r = 0.5 * (n + 1) * sp[k];
+    R2 += r * r;
+  }
+  p.alpha = 2.0 * 5.1 * u + 1e-14;
+  p.beta = 2.0 * 4.1 * u * sqrt(R2);
+  p.gamma = 2.0 * 4.1 * u * u * R2;
+  p.TS = tu.tile;
+  const long long nv = std::max<long long>(nv_hint, 2);
+  p.nv_cap = nv_hint;
+  const int kinds = p.planes ? 4 : 1;
+  const long long nsorted = nv * kinds;
+  p.max_problems = 2 + (p.planes ? (2LL * d.nx + 1) + (2LL * d.ny + 1) + (2LL * d.nz + 1) : 0);
+  p.max_tiles = nsorted / p.TS + p.max_problems + 1;
+  if (s.work_cap == 0) s.work_cap = 1 << 20;
+  if (s.cand_cap == 0) s.cand_cap = 1 << 20;
+  p.work_cap = s.work_cap;
+  p.cand_cap = s.cand_cap;
+
+  // scratch layout
+  const long long nparts = (p.K + kScanBlock - 1) / kScanBlock;
+  size_t bytes = 0;
+  auto add = [&](size_t n) { bytes += (n + 255) & ~size_t(255); };
+  add(sizeof(int) * p.K);              // hist
+  add(sizeof(int) * p.K);              // cursor
+  add(sizeof(long long) * p.K);        // offsets
+  add(sizeof(long long) * (nparts + 1));
+  add(sizeof(float4) * nsorted);
+  add(sizeof(Problem) * p.max_problems);
+  add(sizeof(Tile) * p.max_tiles);
+  add(sizeof(float4) * 2 * p.max_tiles);
+  add(sizeof(ProblemState) * p.max_problems);
+  add(sizeof(Counters));
+  add(sizeof(WorkItem) * p.work_cap);
+  add(sizeof(float) * p.work_cap);
+  add(sizeof(Cand) * p.cand_cap);
+  RAD_TRY(s.misc.reserve(bytes));
+  char* cur = s.misc.as<char>();
+  int* hist = carve<int>(cur, p.K);
+  int* cursor = carve<int>(cur, p.K);
+  long long* offs = carve<long long>(cur, p.K);
+  long long* parts = carve<long long>(cur, nparts + 1);
+  float4* sorted = carve<float4>(cur, nsorted);
+  Problem* probs = carve<Problem>(cur, p.max_problems);
+  Tile* tiles = carve<Tile>(cur, p.max_tiles);
+  float4* box = carve<float4>(cur, 2 * p.max_tiles);
+  ProblemState* ps = carve<ProblemState>(cur, p.max_problems);
+  Counters* cnt = carve<Counters>(cur, 1);
+  WorkItem* work = carve<WorkItem>(cur, p.work_cap);
+  float* itemmax = carve<float>(cur, p.work_cap);
+  Cand* cand = carve<Cand>(cur, p.cand_cap);
+
+  const int sms = num_sms();
+  RAD_CUDA(cudaMemsetAsync(hist, 0, sizeof(int) * p.K, st));
+  RAD_CUDA(cudaMemsetAsync(cursor, 0, sizeof(int) * p.K, st));
+  RAD_CUDA(cudaMemsetAsync(cnt, 0, sizeof(Counters), st));
+  RAD_LAUNCH("diam_init", k_init_states, std::min<long long>((p.max_problems + 255) / 256, sms * 4), 256, 0, st, ps,
+             p.max_problems);
+  const int vblocks = (int)std::min<long long>((nv + 255) / 256, (long long)sms * 8);
+  RAD_LAUNCH("diam_hist", k_hist, vblocks, 256, 0, st, idx2, nv_dev, p, hist);
+  RAD_LAUNCH("diam_scan_part", k_xscan_part, (int)nparts, kScanBlock, 0, st, hist, p.K, offs, parts);
+  RAD_LAUNCH("diam_scan_top", k_xscan_top, 1, 32, 0, st, parts, (int)nparts, (long long*)nullptr);
+  RAD_LAUNCH("diam_scan_add", k_xscan_add, (int)nparts, kScanBlock, 0, st, offs, p.K, parts);
+  RAD_LAUNCH("diam_scatter", k_scatter, vblocks, 256, 0, st, idx2, vt, nv_dev, p, offs, cursor, sorted);
+  RAD_LAUNCH("diam_problems", k_problems, (int)std::max<long long>(1, std::min<long long>((p.K - p.C3 + 255) / 256, sms * 4)),
+             256, 0, st, nv_dev, p, hist, offs, probs, cnt);
+  RAD_LAUNCH("diam_problem_scan", k_problem_scan, 1, 1024, 0, st, probs, p, cnt);
+  RAD_LAUNCH("diam_tiles", k_tiles, sms * 4, 256, 0, st, probs, p, cnt, tiles);
+  RAD_LAUNCH("diam_tile_box", k_tile_box, sms * 8, 128, 0, st, sorted, tiles, p, cnt, box, ps);
+  RAD_LAUNCH("diam_seed", k_seed, sms * 2, 256, 0, st, sorted, p, cnt, ps);
+  RAD_LAUNCH("diam_cull", k_cull, sms * 16, 256, 0, st, probs, box, p, cnt, ps, work);
+  const int ctas = sms * tu.ctas_per_sm;
+  if (tu.tile == 64) {
+    if (tu.threads == 64) RAD_TRY((launch_pairs<64, 64>(sorted, tiles, box, work, p, cnt, ps, itemmax, cand, ctas, st)));
+    else RAD_TRY((launch_pairs<64, 128>(sorted, tiles, box, work, p, cnt, ps, itemmax, cand, ctas, st)));
+  } else if (tu.tile == 128) {
+    if (tu.threads == 64) RAD_TRY((launch_pairs<128, 64>(sorted, tiles, box, work, p, cnt, ps, itemmax, cand, ctas, st)));
+    else if (tu.threads == 128) RAD_TRY((launch_pairs<128, 128>(sorted, tiles, box, work, p, cnt, ps, itemmax, cand, ctas, st)));
+    else RAD_TRY((launch_pairs<128, 256>(sorted, tiles, box, work, p, cnt, ps, itemmax, cand, ctas, st)));
+  } else {
+    if (tu.threads == 128) RAD_TRY((launch_pairs<256, 128>(sorted, tiles, box, work, p, cnt, ps, itemmax, cand, ctas, st)));
+    else RAD_TRY((launch_pairs<256, 256>(sorted, tiles, box, work, p, cnt, ps, itemmax, cand, ctas, st)));
+  }
+  RAD_LAUNCH("diam_confirm", k_confirm, sms * 4, 256, 0, st, sorted, idx2, vt, p, cnt, cand, ps);
+  RAD_LAUNCH("diam_tiebreak", k_tiebreak, sms * 4, 256, 0, st, sorted, idx2, vt, p, cnt, cand, ps);
+  RAD_LAUNCH("diam_finalize", k_finalize, 1, 1024, 0, st, probs, cnt, ps, out_dev, status_dev);
+  return RAD_OK;
+}
+
+// ---- plain FP64 all-pairs (comparison kernel) ------------------------------------
+
+namespace {
+
+constexpr int kPlainTile = 256;
+
+__device__ __forceinline__ void take_best(BestD& b, double d2, int i, int j) {
+  if (better(d2, i, j, b)) { b.d2 = d2; b.i = i; b.j = j; }
+}
+
+// Persistent grid over the upper-triangular tile pairs; each CTA keeps its
+// running (d2, i, j) for 3D, Slice, Column, Row and writes them to scratch.
+__global__ void __launch_bounds__(kPlainTile) k_plain(const int16_t* __restrict__ idx2, const double* __restrict__ vt,
+                                                      int n, double sx, double sy, double sz,
+                                                      BestD* __restrict__ part) {
+  __shared__ double su[3][kPlainTile];
+  __shared__ int sq[3][kPlainTile];
+  __shared__ BestD sred[4][kPlainTile / 32];
+  const int nt = (n + kPlainTile - 1) / kPlainTile;
+  const long long npairs = (long long)nt * (nt + 1) / 2;
+  BestD b[4];
+  for (int q = 0; q < 4; ++q) { b[q].d2 = 0.0; b[q].i = -1; b[q].j = -1; }
+  for (long long l = blockIdx.x; l < npairs; l += gridDim.x) {
+    long long tb = (long long)((sqrt(8.0 * (double)l + 1.0) - 1.0) * 0.5);
+    while (tb * (tb + 1) / 2 > l) --tb;
+    while ((tb + 1) * (tb + 2) / 2 <= l) ++tb;
+    const long long ta = l - tb * (tb + 1) / 2;
+    const int jb = (int)tb * kPlainTile;
+    __syncthreads();
+    {
+      const int j = jb + threadIdx.x;
+      if (j < n) {
+        double u[3];
+        vertex_u(idx2, vt, j, u);
+        for (int k = 0; k < 3; ++k) { su[k][threadIdx.x] = u[k]; sq[k][threadIdx.x] = idx2[3 * j + k]; }
+      }
+    }
+    __syncthreads();
+    const int i = (int)ta * kPlainTile + threadIdx.x;
+    if (i < n) {
+      double ui[3];
+      vertex_u(idx2, vt, i, ui);
+      const int qi0 = idx2[3 * i], qi1 = idx2[3 * i + 1], qi2 = idx2[3 * i + 2];
+      const int jend = min(kPlainTile, n - jb);
+      for (int jj = 0; jj < jend; ++jj) {
+        const int j = jb + jj;
+        if (j <= i) continue;
+        const double d2 = pin_d2(ui[0], ui[1], ui[2], su[0][jj], su[1][jj], su[2][jj], sx, sy, sz);
+        take_best(b[0], d2, i, j);
+        if (vt == nullptr) {
+          if (qi2 == sq[2][jj]) take_best(b[1], d2, i, j);
+          if (qi1 == sq[1][jj]) take_best(b[2], d2, i, j);
+          if (qi0 == sq[0][jj]) take_best(b[3], d2, i, j);
+        } else {
+          if (ui[2] == su[2][jj]) take_best(b[1], d2, i, j);
+          if (ui[1] == su[1][jj]) take_best(b[2], d2, i, j);
+          if (ui[0] == su[0][jj]) take_best(b[3], d2, i, j);
+        }
+      }
+    }
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int q = 0; q < 4; ++q) {
+    for (int off = 16; off > 0; off >>= 1) {
+      BestD o;
+      o.d2 = __shfl_xor_sync(0xffffffffu, b[q].d2, off);
+      o.i = __shfl_xor_sync(0xffffffffu, b[q].i, off);
+      o.j = __shfl_xor_sync(0xffffffffu, b[q].j, off);
+      if (better(o.d2, o.i, o.j, b[q])) b[q] = o;
+    }
+    if (lane == 0) sred[q][wid] = b[q];
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    const int q = threadIdx.x;
+    BestD r = sred[q][0];
+    for (int w = 1; w < kPlainTile / 32; ++w)
+      if (better(sred[q][w].d2, sred[q][w].i, sred[q][w].j, r)) r = sred[q][w];
+    part[4 * blockIdx.x + q] = r;
+  }
+}
+
+__global__ void k_plain_final(const BestD* __restrict__ part, int nparts, DiamResult* __restrict__ out) {
+  if (threadIdx.x < 4) {
+    const int q = threadIdx.x;
+    BestD r;
+    r.d2 = 0.0; r.i = -1; r.j = -1;
+    for (int b = 0; b < nparts; ++b)
+      if (better(part[4 * b + q].d2, part[4 * b + q].i, part[4 * b + q].j, r)) r = part[4 * b + q];
+    out->d2[q] = r.i >= 0 ? r.d2 : 0.0;
+    out->i[q] = r.i;
+    out->j[q] = r.j;
+  }
+}
+
+}  // namespace
+
+rad_status diam_plain_fp64(const int16_t* idx2, const double* vt, long long nv, const MeshDims& d, const double sp[3],
+                           DiamScratch& s, DiamResult* out_dev, cudaStream_t st) {
+  (void)d;
+  const int ctas = num_sms() * 4;
+  RAD_TRY(s.plain_part.reserve(sizeof(BestD) * 4 * ctas));
+  RAD_LAUNCH("plain_fp64_pairs", k_plain, ctas, kPlainTile, 0, st, idx2, vt, (int)nv, sp[0], sp[1], sp[2],
+             s.plain_part.as<BestD>());
+  RAD_LAUNCH("plain_fp64_final", k_plain_final, 1, 32, 0, st, s.plain_part.as<BestD>(), ctas, out_dev);
+  return RAD_OK;
+}
+
+}  // namespace rad

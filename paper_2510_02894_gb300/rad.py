@@ -1,0 +1,276 @@
+"""Thin Python binding of librad (include/rad.h): argument marshalling only.
+
+Every step of the shape-feature path runs in the library's CUDA kernels; this
+module passes device pointers of torch tensors, the current CUDA stream and
+plain structs through ctypes.  There is no CPU fallback: if librad.so is
+missing the first call raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librad.so")
+
+RAD_OK = 0
+STATUS = {0: "RAD_OK", 1: "RAD_ERR_INVALID_ARG", 2: "RAD_ERR_CUDA", 3: "RAD_ERR_CAPACITY", 4: "RAD_ERR_TIMEOUT",
+          5: "RAD_ERR_OOM", 6: "RAD_ERR_INTERNAL"}
+
+
+class RadError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Features(ctypes.Structure):
+    _fields_ = [("MeshVolume", ctypes.c_double), ("SurfaceArea", ctypes.c_double), ("VoxelVolume", ctypes.c_double),
+                ("Maximum3DDiameter", ctypes.c_double), ("Maximum2DDiameterSlice", ctypes.c_double),
+                ("Maximum2DDiameterColumn", ctypes.c_double), ("Maximum2DDiameterRow", ctypes.c_double),
+                ("n_vertices", ctypes.c_int64), ("n_triangles", ctypes.c_int64), ("n_voxels", ctypes.c_int64),
+                ("argmax3d", ctypes.c_int32 * 2), ("argmax_slice", ctypes.c_int32 * 2),
+                ("argmax_column", ctypes.c_int32 * 2), ("argmax_row", ctypes.c_int32 * 2),
+                ("status", ctypes.c_int32), ("_pad", ctypes.c_int32)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k in ("MeshVolume", "SurfaceArea", "VoxelVolume", "Maximum3DDiameter",
+                                           "Maximum2DDiameterSlice", "Maximum2DDiameterColumn",
+                                           "Maximum2DDiameterRow", "n_vertices", "n_triangles", "n_voxels")}
+        for k in ("argmax3d", "argmax_slice", "argmax_column", "argmax_row"):
+            a = getattr(self, k)
+            d[k] = (int(a[0]), int(a[1]))
+        d["status"] = int(self.status)
+        return d
+
+
+class MeshT(ctypes.Structure):
+    _fields_ = [("n_vertices", ctypes.c_int64), ("n_triangles", ctypes.c_int64), ("n_voxels", ctypes.c_int64),
+                ("vtx_idx2", ctypes.c_void_p), ("vtx_t", ctypes.c_void_p), ("tri", ctypes.c_void_p),
+                ("mesh_volume", ctypes.c_double), ("surface_area", ctypes.c_double),
+                ("dims", ctypes.c_int64 * 3), ("spacing", ctypes.c_double * 3), ("soft", ctypes.c_int32),
+                ("_pad", ctypes.c_int32), ("_priv", ctypes.c_void_p)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("tile", ctypes.c_int32), ("threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("cell_shift", ctypes.c_int32)]
+
+
+class CallStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("h2d_bytes", "d2h_bytes", "problems", "tiles", "tile_pairs",
+                                               "work_items", "items_evaluated", "pairs_evaluated", "candidates")]
+
+
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
+
+
+_lib = None
+EXPORTS = ("rad_mesh", "rad_soft_mesh", "rad_shape", "rad_shape_plain_fp64", "rad_extract", "rad_extract_host",
+           "rad_workspace_free", "rad_mesh_free", "rad_mesh_copy", "rad_set_tuning", "rad_profile_enable",
+           "rad_profile_read", "rad_profile_reset", "rad_launch_count", "rad_status_str", "rad_last_error",
+           "rad_last_call_stats")
+
+
+def lib():
+    """Load librad.so (built in-tree by __graft_entry__.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build the CUDA library first (__graft_entry__.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        for name in ("rad_mesh", "rad_soft_mesh"):
+            getattr(L, name).argtypes = [P, P, P, ctypes.POINTER(MeshT), P]
+            getattr(L, name).restype = I
+        for name in ("rad_shape", "rad_shape_plain_fp64"):
+            getattr(L, name).argtypes = [ctypes.POINTER(MeshT), ctypes.POINTER(Features), P]
+            getattr(L, name).restype = I
+        for name in ("rad_extract", "rad_extract_host"):
+            getattr(L, name).argtypes = [P, P, P, ctypes.POINTER(Features), ctypes.POINTER(P), P]
+            getattr(L, name).restype = I
+        L.rad_workspace_free.argtypes = [P]
+        L.rad_workspace_free.restype = None
+        L.rad_mesh_free.argtypes = [ctypes.POINTER(MeshT)]
+        L.rad_mesh_free.restype = None
+        L.rad_mesh_copy.argtypes = [ctypes.POINTER(MeshT), P, P, P, P]
+        L.rad_mesh_copy.restype = I
+        L.rad_set_tuning.argtypes = [ctypes.POINTER(Tuning), ctypes.POINTER(Tuning)]
+        L.rad_set_tuning.restype = I
+        L.rad_profile_enable.argtypes = [I]
+        L.rad_profile_enable.restype = I
+        L.rad_profile_read.argtypes = [ctypes.POINTER(KernelStat), I]
+        L.rad_profile_read.restype = I
+        L.rad_profile_reset.argtypes = []
+        L.rad_profile_reset.restype = None
+        L.rad_launch_count.argtypes = []
+        L.rad_launch_count.restype = ctypes.c_int64
+        L.rad_status_str.argtypes = [I]
+        L.rad_status_str.restype = ctypes.c_char_p
+        L.rad_last_call_stats.argtypes = [ctypes.POINTER(CallStats)]
+        L.rad_last_call_stats.restype = I
+        L.rad_last_error.argtypes = []
+        L.rad_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != RAD_OK:
+        raise RadError(status, lib().rad_last_error().decode(errors="replace"))
+
+
+def _stream(stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _geometry(shape_zyx, spacing):
+    nz, ny, nx = (int(v) for v in shape_zyx)
+    dims = (ctypes.c_int64 * 3)(nx, ny, nz)
+    sp = (ctypes.c_double * 3)(*(float(s) for s in spacing))
+    return dims, sp
+
+
+def _device_tensor(t, dtype_name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA torch.Tensor")
+    if str(t.dtype) != dtype_name:
+        raise TypeError(f"expected {dtype_name}, got {t.dtype}")
+    if t.dim() != 3 or not t.is_contiguous():
+        raise ValueError("expected a contiguous [nz][ny][nx] tensor")
+    return t
+
+
+class Mesh:
+    """A device mesh owned by the library (freed with the object)."""
+
+    def __init__(self):
+        self.m = MeshT()
+
+    def __del__(self):
+        if _lib is not None and self.m._priv:
+            _lib.rad_mesh_free(ctypes.byref(self.m))
+
+    @property
+    def n_vertices(self):
+        return int(self.m.n_vertices)
+
+    @property
+    def n_triangles(self):
+        return int(self.m.n_triangles)
+
+    def to_host(self, stream=None):
+        """(idx2 int16 [N,3], t float64 [N] or None, tri int32 [T,3]) on the host."""
+        idx2 = np.zeros((self.n_vertices, 3), np.int16)
+        tri = np.zeros((self.n_triangles, 3), np.int32)
+        t = np.zeros(self.n_vertices, np.float64) if self.m.soft else None
+        _check(lib().rad_mesh_copy(ctypes.byref(self.m), idx2.ctypes.data_as(ctypes.c_void_p),
+                                   t.ctypes.data_as(ctypes.c_void_p) if t is not None else None,
+                                   tri.ctypes.data_as(ctypes.c_void_p), _stream(stream)))
+        return idx2, t, tri
+
+
+def mesh(mask, spacing, stream=None, out=None):
+    """rad_mesh on a CUDA uint8 tensor [nz][ny][nx]."""
+    _device_tensor(mask, "torch.uint8")
+    dims, sp = _geometry(mask.shape, spacing)
+    m = out if out is not None else Mesh()
+    _check(lib().rad_mesh(ctypes.c_void_p(mask.data_ptr()), dims, sp, ctypes.byref(m.m), _stream(stream)))
+    return m
+
+
+def soft_mesh(prob, spacing, stream=None, out=None):
+    """rad_soft_mesh on a CUDA float32 tensor [nz][ny][nx]."""
+    _device_tensor(prob, "torch.float32")
+    dims, sp = _geometry(prob.shape, spacing)
+    m = out if out is not None else Mesh()
+    _check(lib().rad_soft_mesh(ctypes.c_void_p(prob.data_ptr()), dims, sp, ctypes.byref(m.m), _stream(stream)))
+    return m
+
+
+def shape(m, stream=None):
+    f = Features()
+    _check(lib().rad_shape(ctypes.byref(m.m), ctypes.byref(f), _stream(stream)))
+    return f.as_dict()
+
+
+def shape_plain_fp64(m, stream=None):
+    f = Features()
+    _check(lib().rad_shape_plain_fp64(ctypes.byref(m.m), ctypes.byref(f), _stream(stream)))
+    return f.as_dict()
+
+
+class Workspace:
+    """Library-owned buffers reused by extract()/extract_host() calls."""
+
+    def __init__(self):
+        self.h = ctypes.c_void_p(None)
+
+    def __del__(self):
+        if _lib is not None and self.h.value:
+            _lib.rad_workspace_free(self.h)
+            self.h = ctypes.c_void_p(None)
+
+
+def extract(mask, spacing, ws, stream=None):
+    """Whole path (mesh + all features) for a CUDA uint8 mask."""
+    _device_tensor(mask, "torch.uint8")
+    dims, sp = _geometry(mask.shape, spacing)
+    f = Features()
+    _check(lib().rad_extract(ctypes.c_void_p(mask.data_ptr()), dims, sp, ctypes.byref(f), ctypes.byref(ws.h),
+                             _stream(stream)))
+    return f.as_dict()
+
+
+def extract_host(mask_ptr, shape_zyx, spacing, ws, stream=None):
+    """Whole path for a HOST mask given by address (pinned memory gives full
+    copy bandwidth) and shape [nz, ny, nx]."""
+    dims, sp = _geometry(shape_zyx, spacing)
+    f = Features()
+    _check(lib().rad_extract_host(ctypes.c_void_p(int(mask_ptr)), dims, sp, ctypes.byref(f), ctypes.byref(ws.h),
+                                  _stream(stream)))
+    return f.as_dict()
+
+
+def set_tuning(tile=None, threads=None, ctas_per_sm=None, cell_shift=None):
+    cur = get_tuning()
+    t = Tuning(tile or cur["tile"], threads or cur["threads"], ctas_per_sm or cur["ctas_per_sm"],
+               cell_shift or cur["cell_shift"])
+    _check(lib().rad_set_tuning(ctypes.byref(t), None))
+
+
+def get_tuning():
+    t = Tuning()
+    _check(lib().rad_set_tuning(None, ctypes.byref(t)))
+    return {"tile": t.tile, "threads": t.threads, "ctas_per_sm": t.ctas_per_sm, "cell_shift": t.cell_shift}
+
+
+def profile_enable(on=True):
+    _check(lib().rad_profile_enable(1 if on else 0))
+
+
+def profile_reset():
+    lib().rad_profile_reset()
+
+
+def profile_read():
+    n = lib().rad_profile_read(None, 0)
+    arr = (KernelStat * max(n, 1))()
+    n = lib().rad_profile_read(arr, n)
+    return {arr[i].name.decode(): {"launches": int(arr[i].launches), "total_ms": float(arr[i].total_ms)}
+            for i in range(n)}
+
+
+def last_call_stats():
+    st = CallStats()
+    _check(lib().rad_last_call_stats(ctypes.byref(st)))
+    return {n: int(getattr(st, n)) for n, _ in CallStats._fields_}
+
+
+def launch_count():
+    return int(lib().rad_launch_count())
