@@ -136,6 +136,31 @@ void rad_mesh_free(rad_mesh_t* mesh);
  * n_triangles x 3 int32.  Synchronises `stream`. */
 rad_status rad_mesh_copy(const rad_mesh_t* mesh, int16_t* idx2, double* t, int32_t* tri, void* stream);
 
+/* ---- diameters without device allocation --------------------------------- */
+
+/* The paper has no counterpart of this entry point; it exists for callers
+ * that cannot call cudaMalloc (device memory owned by a framework's fixed
+ * pool, services that forbid allocation after start-up, code that must avoid
+ * the implicit synchronisation of cudaMalloc/cudaFree).  It computes the
+ * same diameters as rad_shape_plain_fp64 (plain FP64 all pairs, same pinned
+ * formula and tie-break) and allocates nothing: its only scratch is a static
+ * device array of 256 KB built into the library, which every GPU that loads
+ * the library keeps until the process exits.
+ *   idx2_dev   device, n_vertices x 3 int16 doubled index coordinates
+ *   t_dev      device, n_vertices doubles (soft meshes) or NULL (masks)
+ *   n_vertices 0 .. 1048576 (4096 tiles of 256 vertices); larger counts are
+ *              rejected with RAD_ERR_INVALID_ARG before any launch
+ *   d2_dev     device, 4 doubles out: squared 3D, Slice, Column, Row diameter
+ *   pairs_dev  device, 8 int32 out: (i, j) of each, (-1, -1) if no pair
+ * Asynchronous on `stream` (nothing is copied to the host).  The first call
+ * on a device looks up the device address of the static array with that
+ * device current; make that first call before any stream capture.  All calls
+ * share the one array: calls that overlap on the GPU (other streams or
+ * threads) race and must be serialised by the caller. */
+rad_status rad_diameters_plain_fp64_noalloc(const int16_t* idx2_dev, const double* t_dev, int64_t n_vertices,
+                                            const double spacing[3], double* d2_dev, int32_t* pairs_dev,
+                                            void* stream);
+
 /* ---- configuration and introspection ----------------------------------- */
 
 /* Set (non-NULL) and/or read (get non-NULL) the diameter tuning of the
