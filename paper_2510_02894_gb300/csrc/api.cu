@@ -171,7 +171,8 @@ struct Work {
   DevBuf mask;     // device copy of a host mask (rad_extract_host)
   int device = -1;
   ~Work() {
-    ms.bits.release(); ms.counts.release(); ms.prefix.release(); ms.chunk.release(); ms.partial.release();
+    ms.bits.release(); ms.counts.release(); ms.wpre.release(); ms.prefix.release(); ms.chunk.release();
+    ms.cubes.release(); ms.hist.release(); ms.partial.release();
     ms.bintab.release(); ds.misc.release(); ds.plain_part.release(); result.release(); idx2.release();
     vt.release(); tri.release(); mask.release();
     if (host) cudaFreeHost(host);

@@ -14,10 +14,15 @@
 //            counts.
 //   k_scan_* chunked exclusive scan of the row counts (vertex and triangle
 //            ids follow the canonical (z, y, x, axis) order).
-//   k_emit   re-derives the bits of the 3 x 3 neighbouring rows, ranks every
-//            crossing edge with popc + group scans, writes vertices and
-//            triangles, and reduces 6V and 2A in FP64 with a fixed-order tree
-//            (deterministic).
+//   k_rows   per row: writes the row's vertices (ids = row base + popc ranks)
+//            and a compact list of its active cubes with their triangle ids.
+//   k_cubes  one thread per active cube: vertex ids of its crossing edges
+//            (bitset words + per-word prefixes), its triangles, and the volume
+//            and area sums.  For a mask the volume is an exact int64 sum in
+//            half-voxel units (6V = det(diag(s/2)) * sum A.(B x C)) and the
+//            area comes from a per-case table and a per-case histogram, so
+//            both are deterministic; a soft map sums FP64 per triangle with a
+//            fixed-order reduction.
 #include <stdio.h>
 
 #include <algorithm>
@@ -30,8 +35,16 @@ namespace rad {
 namespace {
 
 constexpr int kScanChunk = 2048;  // rows per scan chunk (256 threads x 8)
-constexpr int kEmitBlocksPerSM = 4;
-constexpr int kEmitThreads = 256;
+constexpr int kCubeBlocksPerSM = 8;
+
+// Per-case data of a binary mask for one spacing (built by k_binary_table).
+struct BinCase {
+  int ntri;
+  unsigned char tri[MC_MAX_TRI][3];  // local edge triples
+  int nsum[3];                        // sum of (B - A) x (C - A), local doubled positions
+  int tsum;                           // sum of A . (B x C)
+  double area2;                       // sum of twice the physical triangle areas
+};
 
 __device__ __forceinline__ const uint32_t* brow(const uint32_t* bits, const MeshDims& d, int y, int z) {
   return bits + ((long long)(z + 1) * d.BY + (y + 1)) * d.W;
@@ -114,139 +127,182 @@ __device__ __forceinline__ int cube_case(uint32_t r00, uint32_t r00n, uint32_t r
 
 __device__ __forceinline__ uint32_t shift1(uint32_t w, uint32_t wn) { return (w >> 1) | (wn << 31); }
 
-__global__ void k_count(const uint32_t* __restrict__ bits, MeshDims d, int L, int* __restrict__ counts) {
+// Per-word view of one cube row (y, z): the four mask rows of its cubes and
+// the crossing bits of owner row (y, z).
+struct WordView {
+  uint32_t a, as, b, bs, c, cs, e, es;  // rows (y,z) (y+1,z) (y,z+1) (y+1,z+1), plain and shifted
+  uint32_t ex, ey, ez;                  // crossing edges owned by row (y, z)
+  uint32_t act;                         // cubes whose corners differ
+};
+
+__device__ __forceinline__ WordView word_view(const uint32_t* R00, const uint32_t* R10, const uint32_t* R01,
+                                              const uint32_t* R11, int w, int W) {
+  WordView v;
+  const uint32_t an = ldw(R00, w + 1, W), bn = ldw(R10, w + 1, W), cn = ldw(R01, w + 1, W), en = ldw(R11, w + 1, W);
+  v.a = ldw(R00, w, W);
+  v.b = ldw(R10, w, W);
+  v.c = ldw(R01, w, W);
+  v.e = ldw(R11, w, W);
+  v.as = shift1(v.a, an);
+  v.bs = shift1(v.b, bn);
+  v.cs = shift1(v.c, cn);
+  v.es = shift1(v.e, en);
+  v.ex = v.a ^ v.as;
+  v.ey = v.a ^ v.b;
+  v.ez = v.a ^ v.c;
+  v.act = (v.a | v.b | v.c | v.e | v.as | v.bs | v.cs | v.es) & ~(v.a & v.b & v.c & v.e & v.as & v.bs & v.cs & v.es);
+  return v;
+}
+
+// Group (L lanes) inclusive scan.
+__device__ __forceinline__ int group_incl(int v, int sub, int L) {
+  for (int off = 1; off < L; off <<= 1) {
+    const int o = __shfl_up_sync(0xffffffffu, v, off, L);
+    if (sub >= off) v += o;
+  }
+  return v;
+}
+
+// One group of L lanes per row item (y, z) in [-1, ny-1] x [-1, nz-1]:
+//   counts = (vertices owned by row, triangles of cube row, inside voxels, active cubes)
+//   wpre[row][w] = vertices of the row owned by x < 32 w (row-local prefix)
+__global__ void k_count(const uint32_t* __restrict__ bits, MeshDims d, int L, int4* __restrict__ counts,
+                        int* __restrict__ wpre) {
   const int lane = threadIdx.x & 31, sub = lane % L, gpw = 32 / L;
   const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const int Wc = d.W + ((L - d.W % L) % L);
   for (long long base = warp * gpw; base < d.R; base += nwarps * gpw) {
-    long long item = base + lane / L;
-    bool valid = item < d.R;
-    int y = valid ? (int)(item % (d.ny + 1)) - 1 : -1;
-    int z = valid ? (int)(item / (d.ny + 1)) - 1 : -1;
+    const long long item = base + lane / L;
+    const bool valid = item < d.R;
+    const int y = valid ? (int)(item % (d.ny + 1)) - 1 : -1;
+    const int z = valid ? (int)(item / (d.ny + 1)) - 1 : -1;
     const uint32_t* R00 = brow(bits, d, y, z);
     const uint32_t* R10 = brow(bits, d, y + 1, z);
     const uint32_t* R01 = brow(bits, d, y, z + 1);
     const uint32_t* R11 = brow(bits, d, y + 1, z + 1);
-    int nv = 0, nt = 0, nvox = 0;
-    for (int w = sub; w < d.W + ((L - d.W % L) % L); w += L) {
-      uint32_t a = ldw(R00, w, d.W), an = ldw(R00, w + 1, d.W);
-      uint32_t b = ldw(R10, w, d.W), bn = ldw(R10, w + 1, d.W);
-      uint32_t c = ldw(R01, w, d.W), cn = ldw(R01, w + 1, d.W);
-      uint32_t e = ldw(R11, w, d.W), en = ldw(R11, w + 1, d.W);
-      uint32_t ex = a ^ shift1(a, an), ey = a ^ b, ez = a ^ c;
-      nv += __popc(ex) + __popc(ey) + __popc(ez);
-      if (y >= 0 && z >= 0) nvox += __popc(a);
-      uint32_t as = shift1(a, an), bs = shift1(b, bn), cs = shift1(c, cn), es = shift1(e, en);
-      uint32_t o = a | b | c | e | as | bs | cs | es;
-      uint32_t n = a & b & c & e & as & bs & cs & es;
-      uint32_t act = o & ~n;
-      while (act) {
-        int bit = __ffs(act) - 1;
-        act &= act - 1;
-        nt += MC_CASE_NTRI[cube_case(a, as, b, bs, c, cs, e, es, bit)];
-      }
-    }
-    if (sub == 0) {
-      // owner x = -1 (x-edge into voxel 0) and cube x = -1 (corners cx = 1 at x = 0)
-      uint32_t a0 = ldw(R00, 0, d.W) & 1u, b0 = ldw(R10, 0, d.W) & 1u, c0 = ldw(R01, 0, d.W) & 1u,
-               e0 = ldw(R11, 0, d.W) & 1u;
-      nv += (int)a0;
-      int cs = (int)((a0 << 1) | (b0 << 3) | (c0 << 5) | (e0 << 7));
-      nt += MC_CASE_NTRI[cs];
+    // owner x = -1 and cube x = -1 (corners cx = 1 at voxel x = 0)
+    const uint32_t a0 = ldw(R00, 0, d.W) & 1u, b0 = ldw(R10, 0, d.W) & 1u, c0 = ldw(R01, 0, d.W) & 1u,
+                   e0 = ldw(R11, 0, d.W) & 1u;
+    const int case_m1 = (int)((a0 << 1) | (b0 << 3) | (c0 << 5) | (e0 << 7));
+    int carry = (int)a0;
+    int nt = sub == 0 ? MC_CASE_NTRI[case_m1] : 0;
+    int na = (sub == 0 && case_m1) ? 1 : 0;
+    int nvox = 0;
+    for (int w = sub; w < Wc; w += L) {
+      const WordView v = word_view(R00, R10, R01, R11, w, d.W);
+      const int cnt = __popc(v.ex) + __popc(v.ey) + __popc(v.ez);
+      const int incl = group_incl(cnt, sub, L);
+      if (valid && w < d.W) wpre[item * d.W + w] = carry + incl - cnt;
+      carry += __shfl_sync(0xffffffffu, incl, L - 1, L);
+      if (y >= 0 && z >= 0) nvox += __popc(v.a);
+      na += __popc(v.act);
+      for (uint32_t act = v.act; act; act &= act - 1)
+        nt += MC_CASE_NTRI[cube_case(v.a, v.as, v.b, v.bs, v.c, v.cs, v.e, v.es, __ffs(act) - 1)];
     }
     for (int off = L / 2; off > 0; off >>= 1) {
-      nv += __shfl_xor_sync(0xffffffffu, nv, off, L);
       nt += __shfl_xor_sync(0xffffffffu, nt, off, L);
       nvox += __shfl_xor_sync(0xffffffffu, nvox, off, L);
+      na += __shfl_xor_sync(0xffffffffu, na, off, L);
     }
-    if (valid && sub == 0) {
-      counts[3 * item] = nv;
-      counts[3 * item + 1] = nt;
-      counts[3 * item + 2] = nvox;
-    }
+    if (valid && sub == 0) counts[item] = make_int4(carry, nt, nvox, na);
   }
 }
 
 // ---- scan of row counts -------------------------------------------------------------
+// prefix[row] = chunk-local exclusive prefixes of (vertices, triangles, cubes);
+// chunk[c] = totals of chunk c, turned into chunk offsets by k_scan_top.
 
-__global__ void k_scan_chunks(const int* __restrict__ counts, long long R, long long* __restrict__ prefix,
+__global__ void k_scan_chunks(const int4* __restrict__ counts, long long R, long long* __restrict__ prefix,
                               long long* __restrict__ chunk) {
-  __shared__ long long sv[8], st[8], sx[8];
+  __shared__ long long sw[3][8], sx[8];
   const long long beg = (long long)blockIdx.x * kScanChunk;
-  const int per = kScanChunk / 256;
-  long long v[per], t[per];
-  long long lv = 0, lt = 0, lx = 0;
+  constexpr int per = kScanChunk / 256;
+  long long own[3] = {0, 0, 0}, lx = 0;
+  int4 c[per];
   for (int i = 0; i < per; ++i) {
-    long long r = beg + threadIdx.x * per + i;
-    int cv = 0, ct = 0, cx = 0;
-    if (r < R) { cv = counts[3 * r]; ct = counts[3 * r + 1]; cx = counts[3 * r + 2]; }
-    v[i] = lv; t[i] = lt;
-    lv += cv; lt += ct; lx += cx;
+    const long long r = beg + threadIdx.x * per + i;
+    c[i] = r < R ? counts[r] : make_int4(0, 0, 0, 0);
+    own[0] += c[i].x; own[1] += c[i].y; own[2] += c[i].w; lx += c[i].z;
   }
-  // block exclusive scan of (lv, lt); sum of lx
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  long long iv = lv, it = lt, ix = lx;
-  for (int off = 1; off < 32; off <<= 1) {
-    long long a = __shfl_up_sync(0xffffffffu, iv, off), b = __shfl_up_sync(0xffffffffu, it, off);
-    if (lane >= off) { iv += a; it += b; }
-  }
-  for (int off = 16; off > 0; off >>= 1) ix += __shfl_xor_sync(0xffffffffu, ix, off);
-  if (lane == 31) { sv[wid] = iv; st[wid] = it; }
-  if (lane == 0) sx[wid] = ix;
+  long long inc[3] = {own[0], own[1], own[2]};
+  for (int off = 1; off < 32; off <<= 1)
+    for (int q = 0; q < 3; ++q) {
+      const long long o = __shfl_up_sync(0xffffffffu, inc[q], off);
+      if (lane >= off) inc[q] += o;
+    }
+  for (int off = 16; off > 0; off >>= 1) lx += __shfl_xor_sync(0xffffffffu, lx, off);
+  if (lane == 31)
+    for (int q = 0; q < 3; ++q) sw[q][wid] = inc[q];
+  if (lane == 0) sx[wid] = lx;
   __syncthreads();
-  long long wv = 0, wt = 0;
-  for (int k = 0; k < wid; ++k) { wv += sv[k]; wt += st[k]; }
-  long long ev = wv + iv - lv, et = wt + it - lt;
+  long long ex[3];
+  for (int q = 0; q < 3; ++q) {
+    long long wb = 0;
+    for (int k = 0; k < wid; ++k) wb += sw[q][k];
+    ex[q] = wb + inc[q] - own[q];
+  }
   for (int i = 0; i < per; ++i) {
-    long long r = beg + threadIdx.x * per + i;
-    if (r < R) { prefix[2 * r] = ev + v[i]; prefix[2 * r + 1] = et + t[i]; }
+    const long long r = beg + threadIdx.x * per + i;
+    if (r < R) {
+      prefix[3 * r] = ex[0];
+      prefix[3 * r + 1] = ex[1];
+      prefix[3 * r + 2] = ex[2];
+    }
+    ex[0] += c[i].x; ex[1] += c[i].y; ex[2] += c[i].w;
   }
   if (threadIdx.x == 255) {
     long long tx = 0;
     for (int k = 0; k < 8; ++k) tx += sx[k];
-    chunk[3 * blockIdx.x] = ev + lv;
-    chunk[3 * blockIdx.x + 1] = et + lt;
-    chunk[3 * blockIdx.x + 2] = tx;
+    chunk[4 * blockIdx.x] = ex[0];
+    chunk[4 * blockIdx.x + 1] = ex[1];
+    chunk[4 * blockIdx.x + 2] = ex[2];
+    chunk[4 * blockIdx.x + 3] = tx;
   }
 }
 
-// Single block: exclusive scan of the chunk totals in place; totals to *tot.
 __global__ void k_scan_top(long long* __restrict__ chunk, int nchunks, MeshTotals* __restrict__ tot) {
-  __shared__ long long sv[32], st[32], sx[32];
-  long long carry_v = 0, carry_t = 0, carry_x = 0;
+  __shared__ long long sw[3][32], sx[32];
+  long long carry[3] = {0, 0, 0}, carry_x = 0;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int base = 0; base < nchunks; base += blockDim.x) {
     const int c = base + threadIdx.x;
-    long long v = 0, t = 0, x = 0;
-    if (c < nchunks) { v = chunk[3 * c]; t = chunk[3 * c + 1]; x = chunk[3 * c + 2]; }
-    long long iv = v, it = t, ix = x;
-    for (int off = 1; off < 32; off <<= 1) {
-      const long long a = __shfl_up_sync(0xffffffffu, iv, off), b = __shfl_up_sync(0xffffffffu, it, off);
-      if (lane >= off) { iv += a; it += b; }
-    }
-    for (int off = 16; off > 0; off >>= 1) ix += __shfl_xor_sync(0xffffffffu, ix, off);
-    if (lane == 31) { sv[wid] = iv; st[wid] = it; }
-    if (lane == 0) sx[wid] = ix;
+    long long v[3] = {0, 0, 0}, x = 0;
+    if (c < nchunks) { v[0] = chunk[4 * c]; v[1] = chunk[4 * c + 1]; v[2] = chunk[4 * c + 2]; x = chunk[4 * c + 3]; }
+    long long inc[3] = {v[0], v[1], v[2]};
+    for (int off = 1; off < 32; off <<= 1)
+      for (int q = 0; q < 3; ++q) {
+        const long long o = __shfl_up_sync(0xffffffffu, inc[q], off);
+        if (lane >= off) inc[q] += o;
+      }
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+    if (lane == 31)
+      for (int q = 0; q < 3; ++q) sw[q][wid] = inc[q];
+    if (lane == 0) sx[wid] = x;
     __syncthreads();
-    long long wv = 0, wt = 0, bv = 0, bt = 0, bx = 0;
-    for (int k = 0; k < nw; ++k) {
-      if (k < wid) { wv += sv[k]; wt += st[k]; }
-      bv += sv[k]; bt += st[k]; bx += sx[k];
+    for (int q = 0; q < 3; ++q) {
+      long long wb = 0, bt = 0;
+      for (int k = 0; k < nw; ++k) {
+        if (k < wid) wb += sw[q][k];
+        bt += sw[q][k];
+      }
+      if (c < nchunks) chunk[4 * c + q] = carry[q] + wb + inc[q] - v[q];
+      carry[q] += bt;
     }
-    if (c < nchunks) {
-      chunk[3 * c] = carry_v + wv + iv - v;
-      chunk[3 * c + 1] = carry_t + wt + it - t;
-    }
-    carry_v += bv;
-    carry_t += bt;
-    carry_x += bx;
+    for (int k = 0; k < nw; ++k) carry_x += sx[k];
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    tot->nv = carry_v;
-    tot->nt = carry_t;
+    tot->nv = carry[0];
+    tot->nt = carry[1];
+    tot->na = carry[2];
     tot->nvox = carry_x;
   }
+}
+
+__device__ __forceinline__ long long row_base(const long long* prefix, const long long* chunk, long long r, int q) {
+  return prefix[3 * r + q] + chunk[4 * (r / kScanChunk) + q];
 }
 
 // ---- triangulation choice -----------------------------------------------------------
@@ -284,43 +340,58 @@ __device__ int select_candidate(int loop, const double (*w)[3], const double* sp
 }
 
 // Binary masks: every crossing sits at an edge midpoint, so the choice depends
-// only on (case, spacing).  One thread per case writes MC_MAX_TRI triples.
-__global__ void k_binary_table(double sx, double sy, double sz, unsigned char* __restrict__ tab) {
+// only on (case, spacing).  One thread per case writes its triangles (local
+// edge triples) and the per-case sums used for volume and area:
+//   nsum = sum over the case's triangles of (B - A) x (C - A),
+//   tsum = sum of A . (B x C),
+// with A, B, C the local doubled positions (integers 0..2), and area2 = sum of
+// |cof(H) ((B - A) x (C - A))| with H = diag(s / 2).
+__global__ void k_binary_table(double sx, double sy, double sz, BinCase* __restrict__ tab) {
   const int cs = blockIdx.x * blockDim.x + threadIdx.x;
   if (cs >= 256) return;
   const double sp[3] = {sx, sy, sz};
   double w[12][3];
+  int lp[12][3];
   for (int e = 0; e < 12; ++e) {
     const int c = MC_EDGE_CORNER[e], a = MC_EDGE_AXIS[e];
-    for (int k = 0; k < 3; ++k)
+    for (int k = 0; k < 3; ++k) {
       w[e][k] = __dmul_rn(__dadd_rn((double)((c >> k) & 1), k == a ? 0.5 : 0.0), sp[k]);
+      lp[e][k] = 2 * ((c >> k) & 1) + (k == a);
+    }
   }
-  int n = 0;
+  BinCase out;
+  out.ntri = 0;
+  out.nsum[0] = out.nsum[1] = out.nsum[2] = 0;
+  out.tsum = 0;
+  out.area2 = 0.0;
+  const double hx = 0.5 * sx, hy = 0.5 * sy, hz = 0.5 * sz;
+  const double cof[3] = {hy * hz, hx * hz, hx * hy};
   for (int l = MC_CASE_LOOP_BEGIN[cs]; l < MC_CASE_LOOP_BEGIN[cs + 1]; ++l) {
     const int c = select_candidate(l, w, sp);
     const int tb = MC_CAND_TRI_BEGIN[c];
-    for (int t = 0; t < MC_LOOP_K[l] - 2; ++t, ++n)
-      for (int q = 0; q < 3; ++q) tab[(cs * MC_MAX_TRI + n) * 3 + q] = MC_CAND_TRIPLES[3 * (tb + t) + q];
+    for (int t = 0; t < MC_LOOP_K[l] - 2; ++t) {
+      const int e0 = MC_CAND_TRIPLES[3 * (tb + t)], e1 = MC_CAND_TRIPLES[3 * (tb + t) + 1],
+                e2 = MC_CAND_TRIPLES[3 * (tb + t) + 2];
+      out.tri[out.ntri][0] = (unsigned char)e0;
+      out.tri[out.ntri][1] = (unsigned char)e1;
+      out.tri[out.ntri][2] = (unsigned char)e2;
+      out.ntri++;
+      const int* A = lp[e0];
+      const int* B = lp[e1];
+      const int* C = lp[e2];
+      const int u[3] = {B[0] - A[0], B[1] - A[1], B[2] - A[2]}, v[3] = {C[0] - A[0], C[1] - A[1], C[2] - A[2]};
+      const int n[3] = {u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2], u[0] * v[1] - u[1] * v[0]};
+      for (int k = 0; k < 3; ++k) out.nsum[k] += n[k];
+      out.tsum += A[0] * (B[1] * C[2] - B[2] * C[1]) + A[1] * (B[2] * C[0] - B[0] * C[2]) +
+                  A[2] * (B[0] * C[1] - B[1] * C[0]);
+      const double fx = cof[0] * n[0], fy = cof[1] * n[1], fz = cof[2] * n[2];
+      out.area2 += sqrt(fx * fx + fy * fy + fz * fz);
+    }
   }
+  tab[cs] = out;
 }
 
-// ---- emit ----------------------------------------------------------------------------
-
-struct OwnerRow {
-  uint32_t ex, ey, ez;  // crossing bits of this word (owner x = 32 w + bit)
-  int cnt;              // crossings in this word
-  long long pre;        // id of the first crossing of this word
-  int exn, eyn;         // crossings at bit 0 of the next word (x-edge, y-edge)
-};
-
-__device__ __forceinline__ long long owner_rank(const OwnerRow& o, int bit, int a) {
-  if (bit == 32) return o.pre + o.cnt + (a >= 1 ? o.exn : 0) + (a >= 2 ? o.eyn : 0);
-  const uint32_t low = (1u << bit) - 1u;
-  long long r = o.pre + __popc(o.ex & low) + __popc(o.ey & low) + __popc(o.ez & low);
-  if (a >= 1) r += (o.ex >> bit) & 1u;
-  if (a >= 2) r += (o.ey >> bit) & 1u;
-  return r;
-}
+// ---- rows: vertices and the active-cube list --------------------------------------------
 
 __device__ __forceinline__ float value_at(const float* p, const MeshDims& d, int x, int y, int z) {
   if (x < 0 || y < 0 || z < 0 || x >= d.nx || y >= d.ny || z >= d.nz) return 0.0f;
@@ -332,255 +403,258 @@ __device__ __forceinline__ double crossing_t(double v0, double v1) {
 }
 
 template <bool SOFT>
-__global__ void __launch_bounds__(kEmitThreads) k_emit(const uint32_t* __restrict__ bits, const float* __restrict__ prob,
-                                                       MeshDims d, int L, double sx, double sy, double sz,
-                                                       const long long* __restrict__ prefix,
-                                                       const long long* __restrict__ chunk,
-                                                       const unsigned char* __restrict__ bintab,
-                                                       int16_t* __restrict__ idx2, double* __restrict__ vt,
-                                                       int32_t* __restrict__ tri, long long vcap, long long tcap,
-                                                       MeshTotals* __restrict__ tot, double* __restrict__ partial) {
+__global__ void k_rows(const uint32_t* __restrict__ bits, const float* __restrict__ prob, MeshDims d, int L,
+                       const int* __restrict__ wpre, const long long* __restrict__ prefix,
+                       const long long* __restrict__ chunk, int16_t* __restrict__ idx2, double* __restrict__ vt,
+                       int4* __restrict__ cubes, long long vcap, long long ccap, MeshTotals* __restrict__ tot) {
   const int lane = threadIdx.x & 31, sub = lane % L, gpw = 32 / L;
   const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  const double sp[3] = {sx, sy, sz};
-  const double hs[3] = {0.5 * sx, 0.5 * sy, 0.5 * sz};
-  const int nn[3] = {d.nx, d.ny, d.nz};
-  double acc_v6 = 0.0, acc_a2 = 0.0;
+  const int Wc = d.W + ((L - d.W % L) % L);
   unsigned int err = 0;
-  const int Wc = d.W + ((L - d.W % L) % L);  // word loop bound, uniform across groups
-
   for (long long base = warp * gpw; base < d.R; base += nwarps * gpw) {
     const long long item = base + lane / L;
     const bool valid = item < d.R;
     const int y = valid ? (int)(item % (d.ny + 1)) - 1 : -1;
     const int z = valid ? (int)(item / (d.ny + 1)) - 1 : -1;
-    // bitset rows (y + dy, z + dz), dy, dz in 0..2
-    const uint32_t* rows[3][3];
-    for (int dz = 0; dz < 3; ++dz)
-      for (int dy = 0; dy < 3; ++dy) rows[dz][dy] = brow(bits, d, y + dy, z + dz);
-    // owner rows o = (oy, oz) in {0,1}^2: base vertex ids
-    long long vb[2][2];
-    bool orow_ok[2][2];
-    for (int oz = 0; oz < 2; ++oz)
-      for (int oy = 0; oy < 2; ++oy) {
-        const bool ok = valid && (y + oy) <= d.ny - 1 && (z + oz) <= d.nz - 1;
-        orow_ok[oz][oy] = ok;
-        long long r = ok ? (long long)(z + oz + 1) * (d.ny + 1) + (y + oy + 1) : 0;
-        vb[oz][oy] = ok ? prefix[2 * r] + chunk[3 * (r / kScanChunk)] : 0;
+    const uint32_t* R00 = brow(bits, d, y, z);
+    const uint32_t* R10 = brow(bits, d, y + 1, z);
+    const uint32_t* R01 = brow(bits, d, y, z + 1);
+    const uint32_t* R11 = brow(bits, d, y + 1, z + 1);
+    const long long vb = valid ? row_base(prefix, chunk, item, 0) : 0;
+    const long long tb = valid ? row_base(prefix, chunk, item, 1) : 0;
+    const long long cb = valid ? row_base(prefix, chunk, item, 2) : 0;
+    const uint32_t a0 = ldw(R00, 0, d.W) & 1u, b0 = ldw(R10, 0, d.W) & 1u, c0 = ldw(R01, 0, d.W) & 1u,
+                   e0 = ldw(R11, 0, d.W) & 1u;
+    const int case_m1 = (int)((a0 << 1) | (b0 << 3) | (c0 << 5) | (e0 << 7));
+    const int nt_m1 = MC_CASE_NTRI[case_m1], na_m1 = case_m1 ? 1 : 0;
+    if (valid && sub == 0) {
+      if (a0) {  // owner x = -1: x-edge into voxel 0, the row's first vertex
+        if (vb < vcap) {
+          idx2[3 * vb] = (int16_t)(-1);
+          idx2[3 * vb + 1] = (int16_t)(2 * y);
+          idx2[3 * vb + 2] = (int16_t)(2 * z);
+          if (SOFT) vt[vb] = crossing_t(0.0, (double)value_at(prob, d, 0, y, z));
+        } else {
+          err |= DEV_ERR_VCAP;
+        }
       }
-    const long long tb = valid ? prefix[2 * item + 1] + chunk[3 * (item / kScanChunk) + 1] : 0;
-    // ex_m1 of each owner row: x-edge from x = -1 into voxel 0
-    int exm1[2][2];
-    for (int oz = 0; oz < 2; ++oz)
-      for (int oy = 0; oy < 2; ++oy) exm1[oz][oy] = (int)(ldw(rows[oz][oy], 0, d.W) & 1u);
-    // cube x = -1: corners with cx = 1 are voxels x = 0
-    const int case_m1 = (int)((exm1[0][0] << 1) | (exm1[0][1] << 3) | (exm1[1][0] << 5) | (exm1[1][1] << 7));
-    const int ntri_m1 = MC_CASE_NTRI[case_m1];
-
-    long long carry_o[2][2] = {{0, 0}, {0, 0}};
-    long long carry_t = 0;
+      if (na_m1) {
+        if (cb < ccap) cubes[cb] = make_int4(-1, (int)item, case_m1, (int)tb);
+        else err |= DEV_ERR_TCAP;
+      }
+    }
+    int carry_t = nt_m1, carry_c = na_m1;
     for (int w = sub; w < Wc; w += L) {
-      // words of the 8 rows needed, at w, w + 1, w + 2
-      uint32_t m[3][3][3];
-      for (int dz = 0; dz < 3; ++dz)
-        for (int dy = 0; dy < 3; ++dy)
-          for (int s = 0; s < 3; ++s)
-            m[dz][dy][s] = (dz == 2 && dy == 2) ? 0u : ldw(rows[dz][dy], w + s, d.W);
-      OwnerRow o[2][2];
-      for (int oz = 0; oz < 2; ++oz)
-        for (int oy = 0; oy < 2; ++oy) {
-          const uint32_t a = m[oz][oy][0], an = m[oz][oy][1], ann = m[oz][oy][2];
-          const uint32_t b = m[oz][oy + 1][0], bn = m[oz][oy + 1][1];
-          const uint32_t c = m[oz + 1][oy][0];
-          OwnerRow& r = o[oz][oy];
-          r.ex = a ^ shift1(a, an);
-          r.ey = a ^ b;
-          r.ez = a ^ c;
-          r.cnt = __popc(r.ex) + __popc(r.ey) + __popc(r.ez);
-          r.exn = (int)((an ^ shift1(an, ann)) & 1u);
-          r.eyn = (int)((an ^ bn) & 1u);
-        }
-      // group scans of the four owner-row counts and of the triangle counts
-      const uint32_t A = m[0][0][0], An = m[0][0][1], B = m[0][1][0], Bn = m[0][1][1];
-      const uint32_t C = m[1][0][0], Cn = m[1][0][1], E = m[1][1][0], En = m[1][1][1];
-      const uint32_t As = shift1(A, An), Bs = shift1(B, Bn), Cs = shift1(C, Cn), Es = shift1(E, En);
-      const uint32_t act = (A | B | C | E | As | Bs | Cs | Es) & ~(A & B & C & E & As & Bs & Cs & Es);
+      const WordView v = word_view(R00, R10, R01, R11, w, d.W);
       int tcnt = 0;
-      for (uint32_t a2 = act; a2; a2 &= a2 - 1) tcnt += MC_CASE_NTRI[cube_case(A, As, B, Bs, C, Cs, E, Es, __ffs(a2) - 1)];
-      int incl[5] = {o[0][0].cnt, o[0][1].cnt, o[1][0].cnt, o[1][1].cnt, tcnt};
-      const int own[5] = {incl[0], incl[1], incl[2], incl[3], incl[4]};
-      for (int off = 1; off < L; off <<= 1)
-        for (int q = 0; q < 5; ++q) {
-          int v = __shfl_up_sync(0xffffffffu, incl[q], off, L);
-          if (sub >= off) incl[q] += v;
-        }
-      int tot5[5];
-      for (int q = 0; q < 5; ++q) tot5[q] = __shfl_sync(0xffffffffu, incl[q], L - 1, L);
-      o[0][0].pre = carry_o[0][0] + exm1[0][0] + incl[0] - own[0];
-      o[0][1].pre = carry_o[0][1] + exm1[0][1] + incl[1] - own[1];
-      o[1][0].pre = carry_o[1][0] + exm1[1][0] + incl[2] - own[2];
-      o[1][1].pre = carry_o[1][1] + exm1[1][1] + incl[3] - own[3];
-      long long tpre = carry_t + ntri_m1 + incl[4] - own[4];
-
-      if (valid && w < d.W) {
-        // vertices owned by row (y, z), canonical order within the word
-        if (orow_ok[0][0]) {
-          long long id = vb[0][0] + o[0][0].pre;
-          const OwnerRow& r = o[0][0];
-          for (uint32_t u = r.ex | r.ey | r.ez; u; u &= u - 1) {
-            const int bit = __ffs(u) - 1;
-            const int x = w * 32 + bit;
-            for (int a = 0; a < 3; ++a) {
-              const uint32_t eb = a == 0 ? r.ex : (a == 1 ? r.ey : r.ez);
-              if (!((eb >> bit) & 1u)) continue;
-              if (id < vcap) {
-                idx2[3 * id] = (int16_t)(2 * x + (a == 0));
-                idx2[3 * id + 1] = (int16_t)(2 * y + (a == 1));
-                idx2[3 * id + 2] = (int16_t)(2 * z + (a == 2));
-                if (SOFT) {
-                  double v0 = (double)value_at(prob, d, x, y, z);
-                  double v1 = (double)value_at(prob, d, x + (a == 0), y + (a == 1), z + (a == 2));
-                  vt[id] = crossing_t(v0, v1);
-                }
-              } else {
-                err |= DEV_ERR_VCAP;
-              }
-              ++id;
-            }
-          }
-          if (w == 0 && exm1[0][0]) {
-            const long long id0 = vb[0][0];
-            if (id0 < vcap) {
-              idx2[3 * id0] = (int16_t)(-1);
-              idx2[3 * id0 + 1] = (int16_t)(2 * y);
-              idx2[3 * id0 + 2] = (int16_t)(2 * z);
-              if (SOFT) vt[id0] = crossing_t(0.0, (double)value_at(prob, d, 0, y, z));
-            } else {
-              err |= DEV_ERR_VCAP;
-            }
-          }
-        }
-        // triangles of cube row (y, z): cube x = -1 first (lane of word 0), then ascending x
-        long long tid = tb + tpre;
-        int first_bit = (w == 0) ? -1 : 0;
-        uint32_t cubes = act;
-        for (int cb = first_bit; cb < 32; ++cb) {
-          int cs;
-          if (cb < 0) {
-            if (!ntri_m1) continue;
-            cs = case_m1;
-            tid = tb;  // cube x = -1 comes first in the row
-          } else {
-            if (!((cubes >> cb) & 1u)) continue;
-            cs = cube_case(A, As, B, Bs, C, Cs, E, Es, cb);
-          }
-          const int x = w * 32 + cb;  // cube lower corner x (may be -1)
-          // vertex ids and positions of the cube's crossing edges
-          const unsigned int emask = MC_CASE_EDGES[cs];
-          long long vid[12];
-          double P[12][3];
-          double wl[12][3];
-          for (int e = 0; e < 12; ++e) {
-            if (!((emask >> e) & 1u)) continue;
-            const int c = MC_EDGE_CORNER[e], a = MC_EDGE_AXIS[e];
-            const int cx = c & 1, cy = (c >> 1) & 1, cz = (c >> 2) & 1;
-            const int ox = x + cx;
-            long long r;
-            if (ox < 0) r = 0;  // the x-edge of owner x = -1 is the row's first vertex
-            else r = owner_rank(o[cz][cy], ox - w * 32, a);
-            vid[e] = vb[cz][cy] + r;
-            const int g[3] = {ox, y + cy, z + cz};
-            double t = 0.5;
+      for (uint32_t act = v.act; act; act &= act - 1)
+        tcnt += MC_CASE_NTRI[cube_case(v.a, v.as, v.b, v.bs, v.c, v.cs, v.e, v.es, __ffs(act) - 1)];
+      const int ccnt = __popc(v.act);
+      const int ti = group_incl(tcnt, sub, L), ci = group_incl(ccnt, sub, L);
+      long long tid = tb + carry_t + ti - tcnt;
+      long long cid = cb + carry_c + ci - ccnt;
+      carry_t += __shfl_sync(0xffffffffu, ti, L - 1, L);
+      carry_c += __shfl_sync(0xffffffffu, ci, L - 1, L);
+      if (!valid || w >= d.W) continue;
+      // vertices owned by (x, y, z), x in this word, canonical (x, axis) order
+      long long id = vb + wpre[item * d.W + w];
+      for (uint32_t u = v.ex | v.ey | v.ez; u; u &= u - 1) {
+        const int bit = __ffs(u) - 1, x = 32 * w + bit;
+        for (int a = 0; a < 3; ++a) {
+          const uint32_t eb = a == 0 ? v.ex : (a == 1 ? v.ey : v.ez);
+          if (!((eb >> bit) & 1u)) continue;
+          if (id < vcap) {
+            idx2[3 * id] = (int16_t)(2 * x + (a == 0));
+            idx2[3 * id + 1] = (int16_t)(2 * y + (a == 1));
+            idx2[3 * id + 2] = (int16_t)(2 * z + (a == 2));
             if (SOFT) {
-              const double v0 = (double)value_at(prob, d, g[0], g[1], g[2]);
-              const double v1 = (double)value_at(prob, d, g[0] + (a == 0), g[1] + (a == 1), g[2] + (a == 2));
-              t = crossing_t(v0, v1);
-            }
-            for (int k = 0; k < 3; ++k) {
-              if (SOFT) {
-                P[e][k] = ((double)g[k] - 0.5 * (double)(nn[k] - 1) + (k == a ? t : 0.0)) * sp[k];
-                wl[e][k] = __dmul_rn(__dadd_rn((double)((c >> k) & 1), k == a ? t : 0.0), sp[k]);
-              } else {
-                P[e][k] = (double)(2 * g[k] + (k == a) - (nn[k] - 1)) * hs[k];
-              }
-            }
-          }
-          // triangles of the cube
-          int nt = 0;
-          unsigned char trs[MC_MAX_TRI][3];
-          if (SOFT) {
-            for (int l = MC_CASE_LOOP_BEGIN[cs]; l < MC_CASE_LOOP_BEGIN[cs + 1]; ++l) {
-              const int cand = select_candidate(l, wl, sp);
-              const int tb2 = MC_CAND_TRI_BEGIN[cand];
-              for (int t = 0; t < MC_LOOP_K[l] - 2; ++t, ++nt)
-                for (int q = 0; q < 3; ++q) trs[nt][q] = MC_CAND_TRIPLES[3 * (tb2 + t) + q];
+              const double v0 = (double)value_at(prob, d, x, y, z);
+              const double v1 = (double)value_at(prob, d, x + (a == 0), y + (a == 1), z + (a == 2));
+              vt[id] = crossing_t(v0, v1);
             }
           } else {
-            nt = MC_CASE_NTRI[cs];
-            for (int t = 0; t < nt; ++t)
-              for (int q = 0; q < 3; ++q) trs[t][q] = bintab[(cs * MC_MAX_TRI + t) * 3 + q];
+            err |= DEV_ERR_VCAP;
           }
-          for (int t = 0; t < nt; ++t, ++tid) {
-            const int e0 = trs[t][0], e1 = trs[t][1], e2 = trs[t][2];
-            if (tid < tcap) {
-              tri[3 * tid] = (int32_t)vid[e0];
-              tri[3 * tid + 1] = (int32_t)vid[e1];
-              tri[3 * tid + 2] = (int32_t)vid[e2];
-            } else {
-              err |= DEV_ERR_TCAP;
-            }
-            const double* a = P[e0];
-            const double* b = P[e1];
-            const double* c = P[e2];
-            acc_v6 += a[0] * (b[1] * c[2] - b[2] * c[1]) + a[1] * (b[2] * c[0] - b[0] * c[2]) +
-                      a[2] * (b[0] * c[1] - b[1] * c[0]);
-            const double ux = b[0] - a[0], uy = b[1] - a[1], uz = b[2] - a[2];
-            const double vx = c[0] - a[0], vy = c[1] - a[1], vz = c[2] - a[2];
-            const double nx = uy * vz - uz * vy, ny = uz * vx - ux * vz, nz = ux * vy - uy * vx;
-            acc_a2 += sqrt(nx * nx + ny * ny + nz * nz);
-          }
-          if (cb < 0) tid = tb + tpre;  // resume at this lane's first cube of the word
+          ++id;
         }
       }
-      for (int oz = 0; oz < 2; ++oz)
-        for (int oy = 0; oy < 2; ++oy) carry_o[oz][oy] += tot5[oz * 2 + oy];
-      carry_t += tot5[4];
+      // active cubes of this word, ascending x
+      for (uint32_t act = v.act; act; act &= act - 1) {
+        const int bit = __ffs(act) - 1;
+        const int cs = cube_case(v.a, v.as, v.b, v.bs, v.c, v.cs, v.e, v.es, bit);
+        if (cid < ccap) cubes[cid] = make_int4(32 * w + bit, (int)item, cs, (int)tid);
+        else err |= DEV_ERR_TCAP;
+        ++cid;
+        tid += MC_CASE_NTRI[cs];
+      }
     }
   }
-  // deterministic reduction: warp tree, then block, then the last CTA
+  if (err) atomicOr(&tot->status, err);
+}
+
+// ---- cubes: triangles, volume, area -------------------------------------------------------
+
+// Vertex id of the crossing edge (owner (xo, yo, zo), axis a).
+__device__ __forceinline__ long long vertex_id(const uint32_t* bits, const MeshDims& d, const int* wpre,
+                                               const long long* prefix, const long long* chunk, int xo, int yo,
+                                               int zo, int a) {
+  const long long r = (long long)(zo + 1) * (d.ny + 1) + (yo + 1);
+  const long long base = row_base(prefix, chunk, r, 0);
+  if (xo < 0) return base;  // the row's first vertex (x-edge into voxel 0)
+  const int w = xo >> 5, bit = xo & 31;
+  const uint32_t* R0 = brow(bits, d, yo, zo);
+  const uint32_t b = R0[w], bn = ldw(R0, w + 1, d.W);
+  const uint32_t by = brow(bits, d, yo + 1, zo)[w], bz = brow(bits, d, yo, zo + 1)[w];
+  const uint32_t ex = b ^ shift1(b, bn), ey = b ^ by, ez = b ^ bz;
+  const uint32_t low = (1u << bit) - 1u;
+  long long rank = wpre[r * d.W + w] + __popc(ex & low) + __popc(ey & low) + __popc(ez & low);
+  if (a >= 1) rank += (ex >> bit) & 1u;
+  if (a >= 2) rank += (ey >> bit) & 1u;
+  return base + rank;
+}
+
+constexpr int kCubeThreads = 256;
+
+template <bool SOFT>
+__global__ void __launch_bounds__(kCubeThreads) k_cubes(const uint32_t* __restrict__ bits, const float* __restrict__ prob,
+                                                        MeshDims d, double sx, double sy, double sz,
+                                                        const int* __restrict__ wpre, const long long* __restrict__ prefix,
+                                                        const long long* __restrict__ chunk,
+                                                        const int4* __restrict__ cubes, const BinCase* __restrict__ tab,
+                                                        int32_t* __restrict__ tri, long long ccap, long long tcap,
+                                                        MeshTotals* __restrict__ tot,
+                                                        unsigned long long* __restrict__ case_hist,
+                                                        double* __restrict__ partial) {
+  __shared__ unsigned int s_hist[256];
+  if (!SOFT)
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) s_hist[i] = 0;
+  __syncthreads();
+  const long long ncubes = min(tot->na, ccap);
+  const double sp[3] = {sx, sy, sz};
+  const int nn[3] = {d.nx, d.ny, d.nz};
+  long long vsum = 0;
+  double acc_v6 = 0.0, acc_a2 = 0.0;
+  unsigned int err = 0;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < ncubes;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int4 cu = cubes[k];
+    const int x = cu.x, cs = cu.z;
+    const long long item = cu.y;
+    const int y = (int)(item % (d.ny + 1)) - 1, z = (int)(item / (d.ny + 1)) - 1;
+    const unsigned int emask = MC_CASE_EDGES[cs];
+    int vid[12];
+    double P[12][3], wl[12][3];
+    for (int e = 0; e < 12; ++e) {
+      if (!((emask >> e) & 1u)) continue;
+      const int c = MC_EDGE_CORNER[e], a = MC_EDGE_AXIS[e];
+      const int g[3] = {x + (c & 1), y + ((c >> 1) & 1), z + ((c >> 2) & 1)};
+      vid[e] = (int)vertex_id(bits, d, wpre, prefix, chunk, g[0], g[1], g[2], a);
+      if (SOFT) {
+        const double v0 = (double)value_at(prob, d, g[0], g[1], g[2]);
+        const double v1 = (double)value_at(prob, d, g[0] + (a == 0), g[1] + (a == 1), g[2] + (a == 2));
+        const double t = crossing_t(v0, v1);
+        for (int q = 0; q < 3; ++q) {
+          P[e][q] = ((double)g[q] - 0.5 * (double)(nn[q] - 1) + (q == a ? t : 0.0)) * sp[q];
+          wl[e][q] = __dmul_rn(__dadd_rn((double)((c >> q) & 1), q == a ? t : 0.0), sp[q]);
+        }
+      }
+    }
+    long long tid = cu.w;
+    if (SOFT) {
+      for (int l = MC_CASE_LOOP_BEGIN[cs]; l < MC_CASE_LOOP_BEGIN[cs + 1]; ++l) {
+        const int cand = select_candidate(l, wl, sp);
+        const int tb2 = MC_CAND_TRI_BEGIN[cand];
+        for (int t = 0; t < MC_LOOP_K[l] - 2; ++t, ++tid) {
+          const int e0 = MC_CAND_TRIPLES[3 * (tb2 + t)], e1 = MC_CAND_TRIPLES[3 * (tb2 + t) + 1],
+                    e2 = MC_CAND_TRIPLES[3 * (tb2 + t) + 2];
+          if (tid < tcap) {
+            tri[3 * tid] = vid[e0];
+            tri[3 * tid + 1] = vid[e1];
+            tri[3 * tid + 2] = vid[e2];
+          } else {
+            err |= DEV_ERR_TCAP;
+          }
+          const double* A = P[e0];
+          const double* B = P[e1];
+          const double* C = P[e2];
+          acc_v6 += A[0] * (B[1] * C[2] - B[2] * C[1]) + A[1] * (B[2] * C[0] - B[0] * C[2]) +
+                    A[2] * (B[0] * C[1] - B[1] * C[0]);
+          const double ux = B[0] - A[0], uy = B[1] - A[1], uz = B[2] - A[2];
+          const double vx = C[0] - A[0], vy = C[1] - A[1], vz = C[2] - A[2];
+          const double nx = uy * vz - uz * vy, ny = uz * vx - ux * vz, nz = ux * vy - uy * vx;
+          acc_a2 += sqrt(nx * nx + ny * ny + nz * nz);
+        }
+      }
+    } else {
+      const BinCase& bc = tab[cs];
+      for (int t = 0; t < bc.ntri; ++t, ++tid) {
+        if (tid < tcap) {
+          tri[3 * tid] = vid[bc.tri[t][0]];
+          tri[3 * tid + 1] = vid[bc.tri[t][1]];
+          tri[3 * tid + 2] = vid[bc.tri[t][2]];
+        } else {
+          err |= DEV_ERR_TCAP;
+        }
+      }
+      // exact volume: positions in half-voxel units relative to the padded-box
+      // centre, P = o + local; sum A.(B x C) = o . nsum + tsum
+      const long long ox = 2LL * x - (d.nx - 1), oy = 2LL * y - (d.ny - 1), oz = 2LL * z - (d.nz - 1);
+      vsum += ox * bc.nsum[0] + oy * bc.nsum[1] + oz * bc.nsum[2] + bc.tsum;
+      atomicAdd(&s_hist[cs], 1u);
+    }
+  }
+  // block reduction (fixed order), then the last CTA finishes
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int off = 16; off > 0; off >>= 1) {
+    vsum += __shfl_xor_sync(0xffffffffu, vsum, off);
     acc_v6 += __shfl_xor_sync(0xffffffffu, acc_v6, off);
     acc_a2 += __shfl_xor_sync(0xffffffffu, acc_a2, off);
     err |= __shfl_xor_sync(0xffffffffu, err, off);
   }
-  __shared__ double sv[kEmitThreads / 32], sa[kEmitThreads / 32];
-  __shared__ unsigned int se[kEmitThreads / 32];
+  __shared__ long long s_vs[kCubeThreads / 32];
+  __shared__ double s_v6[kCubeThreads / 32], s_a2[kCubeThreads / 32];
+  __shared__ unsigned int s_err[kCubeThreads / 32];
   __shared__ bool last;
-  const int wid = threadIdx.x >> 5;
-  if (lane == 0) { sv[wid] = acc_v6; sa[wid] = acc_a2; se[wid] = err; }
+  if (lane == 0) { s_vs[wid] = vsum; s_v6[wid] = acc_v6; s_a2[wid] = acc_a2; s_err[wid] = err; }
   __syncthreads();
+  if (!SOFT)
+    for (int i = threadIdx.x; i < 256; i += blockDim.x)
+      if (s_hist[i]) atomicAdd(&case_hist[i], (unsigned long long)s_hist[i]);
   if (threadIdx.x == 0) {
-    double bv = 0.0, ba = 0.0;
+    long long bv = 0;
+    double b6 = 0.0, b2 = 0.0;
     unsigned int be = 0;
-    for (int k = 0; k < kEmitThreads / 32; ++k) { bv += sv[k]; ba += sa[k]; be |= se[k]; }
-    partial[2 * blockIdx.x] = bv;
-    partial[2 * blockIdx.x + 1] = ba;
+    for (int k2 = 0; k2 < kCubeThreads / 32; ++k2) { bv += s_vs[k2]; b6 += s_v6[k2]; b2 += s_a2[k2]; be |= s_err[k2]; }
+    if (!SOFT && bv) atomicAdd((unsigned long long*)&tot->vsum, (unsigned long long)bv);
+    partial[2 * blockIdx.x] = b6;
+    partial[2 * blockIdx.x + 1] = b2;
     if (be) atomicOr(&tot->status, be);
     __threadfence();
-    const unsigned int ticket = atomicAdd(&tot->done_ctas, 1u);
-    last = ticket == gridDim.x - 1;
+    last = atomicAdd(&tot->done_ctas, 1u) == gridDim.x - 1;
   }
   __syncthreads();
   if (last && threadIdx.x == 0) {
     __threadfence();
-    double v = 0.0, a = 0.0;
-    for (unsigned int b = 0; b < gridDim.x; ++b) {
-      v += __ldcg(&partial[2 * b]);
-      a += __ldcg(&partial[2 * b + 1]);
+    if (SOFT) {
+      double v = 0.0, a = 0.0;
+      for (unsigned int b = 0; b < gridDim.x; ++b) {
+        v += __ldcg(&partial[2 * b]);
+        a += __ldcg(&partial[2 * b + 1]);
+      }
+      tot->vol6 = v;
+      tot->area2 = a;
+    } else {
+      // V = det(diag(s / 2)) * sum / 6;  A = sum over cases of count * area of the case
+      const double h3 = (0.5 * sx) * (0.5 * sy) * (0.5 * sz);
+      tot->vol6 = (double)__ldcg((const long long*)&tot->vsum) * h3;
+      double a = 0.0;
+      for (int c = 0; c < 256; ++c) {
+        const unsigned long long n = __ldcg(&case_hist[c]);
+        if (n) a += (double)n * tab[c].area2;
+      }
+      tot->area2 = a;
     }
-    tot->vol6 = v;
-    tot->area2 = a;
     tot->done_ctas = 0;
   }
 }
@@ -610,11 +684,14 @@ rad_status mesh_count(const void* data, bool soft, const MeshDims& d, MeshScratc
   const long long words = (long long)d.BY * d.BZ * d.W;
   const long long nchunks = (d.R + kScanChunk - 1) / kScanChunk;
   RAD_TRY(s.bits.reserve(sizeof(uint32_t) * words));
-  RAD_TRY(s.counts.reserve(sizeof(int) * 3 * d.R));
-  RAD_TRY(s.prefix.reserve(sizeof(long long) * 2 * d.R));
-  RAD_TRY(s.chunk.reserve(sizeof(long long) * 3 * nchunks));
-  RAD_TRY(s.partial.reserve(sizeof(double) * 2 * num_sms() * kEmitBlocksPerSM));
+  RAD_TRY(s.counts.reserve(sizeof(int4) * d.R));
+  RAD_TRY(s.wpre.reserve(sizeof(int) * d.R * d.W));
+  RAD_TRY(s.prefix.reserve(sizeof(long long) * 3 * d.R));
+  RAD_TRY(s.chunk.reserve(sizeof(long long) * 4 * nchunks));
+  RAD_TRY(s.hist.reserve(sizeof(unsigned long long) * 256));
+  RAD_TRY(s.partial.reserve(sizeof(double) * 2 * num_sms() * kCubeBlocksPerSM));
   RAD_CUDA(cudaMemsetAsync(tot, 0, sizeof(MeshTotals), st));
+  RAD_CUDA(cudaMemsetAsync(s.hist.p, 0, sizeof(unsigned long long) * 256, st));
   const int sms = num_sms();
   const bool vec16 = soft ? ((d.nx % 4) == 0 && (((uintptr_t)data) & 15) == 0)
                           : ((d.nx % 16) == 0 && (((uintptr_t)data) & 15) == 0);
@@ -626,14 +703,13 @@ rad_status mesh_count(const void* data, bool soft, const MeshDims& d, MeshScratc
     RAD_LAUNCH("mc_pack_u8", k_pack_u8, pack_blocks, 256, 0, st, (const uint8_t*)data, d, vec16,
                s.bits.as<uint32_t>());
   const int L = group_lanes(d.W);
-  const long long groups_needed = d.R;
-  const long long warps_needed = (groups_needed + (32 / L) - 1) / (32 / L);
-  const int cblocks = (int)std::max<long long>(1, std::min<long long>((warps_needed + 7) / 8, (long long)sms * 8));
-  RAD_LAUNCH("mc_count", k_count, cblocks, 256, 0, st, s.bits.as<uint32_t>(), d, L, s.counts.as<int>());
-  RAD_LAUNCH("mc_scan_chunks", k_scan_chunks, (int)nchunks, 256, 0, st, s.counts.as<int>(), d.R,
+  const long long warps_needed = (d.R + (32 / L) - 1) / (32 / L);
+  const int rblocks = (int)std::max<long long>(1, std::min<long long>((warps_needed + 7) / 8, (long long)sms * 8));
+  RAD_LAUNCH("mc_count", k_count, rblocks, 256, 0, st, s.bits.as<uint32_t>(), d, L, s.counts.as<int4>(),
+             s.wpre.as<int>());
+  RAD_LAUNCH("mc_scan_chunks", k_scan_chunks, (int)nchunks, 256, 0, st, s.counts.as<int4>(), d.R,
              s.prefix.as<long long>(), s.chunk.as<long long>());
-  RAD_LAUNCH("mc_scan_top", k_scan_top, 1, 1024, 0, st, s.chunk.as<long long>(), (int)nchunks,
-             tot);
+  RAD_LAUNCH("mc_scan_top", k_scan_top, 1, 1024, 0, st, s.chunk.as<long long>(), (int)nchunks, tot);
   return RAD_OK;
 }
 
@@ -641,26 +717,38 @@ rad_status mesh_emit(const void* data, bool soft, const MeshDims& d, const doubl
                      MeshTotals* tot, int16_t* idx2, double* vt, int32_t* tri, long long vcap, long long tcap,
                      cudaStream_t st) {
   if (!soft) {
-    RAD_TRY(s.bintab.reserve(256 * MC_MAX_TRI * 3));
+    RAD_TRY(s.bintab.reserve(sizeof(BinCase) * 256));
     if (!s.tab_valid || s.tab_spacing[0] != sp[0] || s.tab_spacing[1] != sp[1] || s.tab_spacing[2] != sp[2]) {
-      RAD_LAUNCH("mc_binary_table", k_binary_table, 1, 256, 0, st, sp[0], sp[1], sp[2],
-                 s.bintab.as<unsigned char>());
+      RAD_LAUNCH("mc_binary_table", k_binary_table, 1, 256, 0, st, sp[0], sp[1], sp[2], s.bintab.as<BinCase>());
       s.tab_valid = true;
       for (int k = 0; k < 3; ++k) s.tab_spacing[k] = sp[k];
     }
   }
+  // every active cube has at least one triangle: the cube list fits in tcap
+  const long long ccap = std::max<long long>(tcap, 1);
+  RAD_TRY(s.cubes.reserve(sizeof(int4) * ccap));
+  const int sms = num_sms();
   const int L = group_lanes(d.W);
-  const int blocks = num_sms() * kEmitBlocksPerSM;
-  if (soft)
-    RAD_LAUNCH("mc_emit_soft", k_emit<true>, blocks, kEmitThreads, 0, st, s.bits.as<uint32_t>(),
-               (const float*)data, d, L, sp[0], sp[1], sp[2], s.prefix.as<long long>(), s.chunk.as<long long>(),
-               (const unsigned char*)nullptr, idx2, vt, tri, vcap, tcap, tot,
+  const long long warps_needed = (d.R + (32 / L) - 1) / (32 / L);
+  const int rblocks = (int)std::max<long long>(1, std::min<long long>((warps_needed + 7) / 8, (long long)sms * 8));
+  const int cblocks = sms * kCubeBlocksPerSM;
+  if (soft) {
+    RAD_LAUNCH("mc_rows_soft", k_rows<true>, rblocks, 256, 0, st, s.bits.as<uint32_t>(), (const float*)data, d, L,
+               s.wpre.as<int>(), s.prefix.as<long long>(), s.chunk.as<long long>(), idx2, vt, s.cubes.as<int4>(),
+               vcap, ccap, tot);
+    RAD_LAUNCH("mc_cubes_soft", k_cubes<true>, cblocks, kCubeThreads, 0, st, s.bits.as<uint32_t>(),
+               (const float*)data, d, sp[0], sp[1], sp[2], s.wpre.as<int>(), s.prefix.as<long long>(),
+               s.chunk.as<long long>(), s.cubes.as<int4>(), (const BinCase*)nullptr, tri, ccap, tcap, tot,
+               s.hist.as<unsigned long long>(), s.partial.as<double>());
+  } else {
+    RAD_LAUNCH("mc_rows", k_rows<false>, rblocks, 256, 0, st, s.bits.as<uint32_t>(), (const float*)nullptr, d, L,
+               s.wpre.as<int>(), s.prefix.as<long long>(), s.chunk.as<long long>(), idx2, (double*)nullptr,
+               s.cubes.as<int4>(), vcap, ccap, tot);
+    RAD_LAUNCH("mc_cubes", k_cubes<false>, cblocks, kCubeThreads, 0, st, s.bits.as<uint32_t>(), (const float*)nullptr,
+               d, sp[0], sp[1], sp[2], s.wpre.as<int>(), s.prefix.as<long long>(), s.chunk.as<long long>(),
+               s.cubes.as<int4>(), s.bintab.as<BinCase>(), tri, ccap, tcap, tot, s.hist.as<unsigned long long>(),
                s.partial.as<double>());
-  else
-    RAD_LAUNCH("mc_emit", k_emit<false>, blocks, kEmitThreads, 0, st, s.bits.as<uint32_t>(), (const float*)nullptr,
-               d, L, sp[0], sp[1], sp[2], s.prefix.as<long long>(), s.chunk.as<long long>(),
-               s.bintab.as<unsigned char>(), idx2, vt, tri, vcap, tcap, tot,
-               s.partial.as<double>());
+  }
   return RAD_OK;
 }
 

@@ -77,21 +77,25 @@ MeshDims make_dims(const int64_t dims[3]);
 
 // Scratch of the marching-cubes pass, reused between calls.
 struct MeshScratch {
-  DevBuf bits;    // packed inside bits
-  DevBuf counts;  // int32 x 3 per row: vertices, triangles, inside voxels
-  DevBuf prefix;  // int64 x 2 per row: exclusive prefixes (chunk-local)
-  DevBuf chunk;   // int64 x 3 per scan chunk; chunk offsets
-  DevBuf partial; // per-CTA FP64 partial sums of 6V and 2A
-  DevBuf bintab;  // per-spacing binary triangle table
+  DevBuf bits;    // packed inside bits, (ny + 3) (nz + 3) rows of W words
+  DevBuf counts;  // int4 per row: vertices, triangles, inside voxels, active cubes
+  DevBuf wpre;    // int per (row, word): row-local vertex prefix
+  DevBuf prefix;  // int64 x 3 per row: chunk-local exclusive prefixes (vertices, triangles, cubes)
+  DevBuf chunk;   // int64 x 4 per scan chunk: chunk offsets (and inside voxels)
+  DevBuf cubes;   // int4 per active cube: x, row, case, first triangle id
+  DevBuf hist;    // uint64 x 256: active cubes per case (mask area)
+  DevBuf partial; // per-CTA FP64 partial sums of 6V and 2A (soft maps)
+  DevBuf bintab;  // per-spacing binary case table
   double tab_spacing[3] = {0, 0, 0};
   bool tab_valid = false;
 };
 
 struct MeshTotals {  // device counts and sums of one marching-cubes pass
-  long long nv, nt, nvox;
+  long long nv, nt, nvox, na;
   double vol6, area2;
+  long long vsum;          // exact sum of A.(B x C) in half-voxel units (masks)
   unsigned int status;
-  unsigned int done_ctas;  // last-CTA ticket of the emit kernel
+  unsigned int done_ctas;  // last-CTA ticket of the cube kernel
 };
 
 // Phase 1: pack + count + scan; the counts land in *tot (device).
