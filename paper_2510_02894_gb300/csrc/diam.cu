@@ -39,7 +39,6 @@ namespace rad {
 
 namespace {
 
-constexpr int kNumDirs = 14;
 
 struct Problem {
   int axis;  // -1: 3D, 0: Row (equal x), 1: Column (equal y), 2: Slice (equal z)
@@ -49,7 +48,7 @@ struct Problem {
 };
 
 struct Tile {
-  int problem, beg, len, pad;
+  int problem, beg, len, tile_end;  // tile_end: one past the problem's last tile
 };
 
 struct WorkItem {
@@ -63,9 +62,8 @@ struct Cand {
 struct ProblemState {
   unsigned int F;  // float bits of the running FP32 maximum
   unsigned int pad;
-  unsigned long long ext[kNumDirs];  // directional extremes: (ordered value << 32) | entry
-  unsigned long long best_d2;        // FP64 bits of the confirmed maximum
-  unsigned long long best_pair;      // (i << 32) | j, smallest among the maxima
+  unsigned long long best_d2;    // FP64 bits of the confirmed maximum
+  unsigned long long best_pair;  // (i << 32) | j, smallest among the maxima
 };
 
 struct Counters {
@@ -79,13 +77,15 @@ struct Counters {
   unsigned int status;
   int pad;
   unsigned long long items_evaluated, pairs_evaluated;
+  long long n_work2;  // items re-evaluated for candidates
 };
 
 struct Params {
   int nx, ny, nz;
   int soft, planes;
-  int cell_shift, CX, CY, CZ;
-  long long C3, K;  // 3D cells; total keys
+  int cell_shift, CX, CY, CZ;     // 3D cells
+  int plane_shift, PX, PY, PZ;    // in-plane 2D cells
+  long long C3, S0, S1, S2, K;    // key blocks: 3D cells, Slice, Column, Row; total
   double sx, sy, sz;
   double cx, cy, cz;  // centre (index units)
   double alpha, beta, gamma;
@@ -93,11 +93,6 @@ struct Params {
   long long work_cap, cand_cap, max_problems, max_tiles;
   long long nv_cap;  // vertex pool capacity: device counts are clamped to it
 };
-
-__device__ __forceinline__ unsigned int ord_float(float f) {
-  unsigned int b = __float_as_uint(f);
-  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
-}
 
 __device__ __forceinline__ float pair_f(float4 a, float4 b) {
   const float dx = __fsub_rn(a.x, b.x), dy = __fsub_rn(a.y, b.y), dz = __fsub_rn(a.z, b.z);
@@ -133,25 +128,39 @@ __device__ __forceinline__ void vertex_q(const int16_t* idx2, long long v, int q
 }
 
 // ---- 1. keys, histogram, scatter ------------------------------------------------
+// kind 0: 3D cell (z, y, x order); kinds 1..3: (plane, 2D cell) for Slice
+// (equal z), Column (equal y) and Row (equal x).  Sorting by these keys gives
+// the 3D problem spatially compact tiles and every plane compact 2D tiles.
 
 __device__ __forceinline__ long long key_of(const Params& p, const int q[3], int kind) {
+  const int x1 = q[0] + 1, y1 = q[1] + 1, z1 = q[2] + 1;  // 0 .. 2n
   if (kind == 0) {
-    const int cx = (q[0] + 1) >> p.cell_shift, cy = (q[1] + 1) >> p.cell_shift, cz = (q[2] + 1) >> p.cell_shift;
+    const int cx = x1 >> p.cell_shift, cy = y1 >> p.cell_shift, cz = z1 >> p.cell_shift;
     return ((long long)cz * p.CY + cy) * p.CX + cx;
   }
-  if (kind == 1) return p.C3 + (q[2] + 1);                                       // Slice: z plane
-  if (kind == 2) return p.C3 + (2LL * p.nz + 1) + (q[1] + 1);                    // Column: y plane
-  return p.C3 + (2LL * p.nz + 1) + (2LL * p.ny + 1) + (q[0] + 1);                // Row: x plane
+  const int px = x1 >> p.plane_shift, py = y1 >> p.plane_shift, pz = z1 >> p.plane_shift;
+  if (kind == 1) return p.S0 + (long long)z1 * p.PX * p.PY + (long long)py * p.PX + px;
+  if (kind == 2) return p.S1 + (long long)y1 * p.PX * p.PZ + (long long)pz * p.PX + px;
+  return p.S2 + (long long)x1 * p.PY * p.PZ + (long long)pz * p.PY + py;
 }
 
+// Warp-aggregated: lanes with equal keys (consecutive vertices share cells and
+// planes) make one atomic.
 __global__ void k_hist(const int16_t* __restrict__ idx2, const long long* __restrict__ nv_dev, Params p,
                        int* __restrict__ hist) {
   const long long n = min(*nv_dev, p.nv_cap);
   const int kinds = p.planes ? 4 : 1;
-  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
-    int q[3];
-    vertex_q(idx2, v, q);
-    for (int k = 0; k < kinds; ++k) atomicAdd(&hist[key_of(p, q, k)], 1);
+  const int lane = threadIdx.x & 31;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long v0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) - lane; v0 < n; v0 += stride) {
+    const long long v = v0 + lane;
+    int q[3] = {0, 0, 0};
+    if (v < n) vertex_q(idx2, v, q);
+    for (int k = 0; k < kinds; ++k) {
+      const long long key = v < n ? key_of(p, q, k) : -1;
+      const unsigned int peers = __match_any_sync(0xffffffffu, key);
+      if (key >= 0 && lane == __ffs(peers) - 1) atomicAdd(&hist[key], __popc(peers));
+    }
   }
 }
 
@@ -160,17 +169,27 @@ __global__ void k_scatter(const int16_t* __restrict__ idx2, const double* __rest
                           int* __restrict__ cursor, float4* __restrict__ sorted) {
   const long long n = min(*nv_dev, p.nv_cap);
   const int kinds = p.planes ? 4 : 1;
-  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
-    int q[3];
-    vertex_q(idx2, v, q);
-    double u[3];
-    vertex_u(idx2, vt, v, u);
-    const float4 e = make_float4(__double2float_rn((u[0] - p.cx) * p.sx), __double2float_rn((u[1] - p.cy) * p.sy),
-                                 __double2float_rn((u[2] - p.cz) * p.sz), __int_as_float((int)v));
+  const int lane = threadIdx.x & 31;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long v0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) - lane; v0 < n; v0 += stride) {
+    const long long v = v0 + lane;
+    int q[3] = {0, 0, 0};
+    float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (v < n) {
+      vertex_q(idx2, v, q);
+      double u[3];
+      vertex_u(idx2, vt, v, u);
+      e = make_float4(__double2float_rn((u[0] - p.cx) * p.sx), __double2float_rn((u[1] - p.cy) * p.sy),
+                      __double2float_rn((u[2] - p.cz) * p.sz), __int_as_float((int)v));
+    }
     for (int k = 0; k < kinds; ++k) {
-      const long long key = key_of(p, q, k);
-      const long long pos = offs[key] + atomicAdd(&cursor[key], 1);
-      sorted[pos] = e;
+      const long long key = v < n ? key_of(p, q, k) : -1;
+      const unsigned int peers = __match_any_sync(0xffffffffu, key);
+      const int leader = __ffs(peers) - 1;
+      int base = 0;
+      if (key >= 0 && lane == leader) base = atomicAdd(&cursor[key], __popc(peers));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (key >= 0) sorted[offs[key] + base + __popc(peers & ((1u << lane) - 1u))] = e;
     }
   }
 }
@@ -199,15 +218,28 @@ __global__ void k_xscan_part(const int* __restrict__ in, long long n, long long*
   if (threadIdx.x == 0) part[blockIdx.x] = tot;
 }
 
-__global__ void k_xscan_top(long long* __restrict__ part, int nparts, long long* __restrict__ total) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    long long s = 0;
-    for (int i = 0; i < nparts; ++i) {
-      const long long v = part[i];
-      part[i] = s;
-      s += v;
+__global__ void k_xscan_top(long long* __restrict__ part, int nparts) {
+  __shared__ long long ws[32];
+  long long carry = 0;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int base = 0; base < nparts; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    const long long v = i < nparts ? part[i] : 0;
+    long long inc = v;
+    for (int off = 1; off < 32; off <<= 1) {
+      const long long o = __shfl_up_sync(0xffffffffu, inc, off);
+      if (lane >= off) inc += o;
     }
-    if (total) *total = s;
+    if (lane == 31) ws[wid] = inc;
+    __syncthreads();
+    long long wb = 0, tot = 0;
+    for (int k = 0; k < nw; ++k) {
+      if (k < wid) wb += ws[k];
+      tot += ws[k];
+    }
+    if (i < nparts) part[i] = carry + wb + inc - v;
+    carry += tot;
+    __syncthreads();
   }
 }
 
@@ -218,13 +250,10 @@ __global__ void k_xscan_add(long long* __restrict__ out, long long n, const long
 
 // ---- 2. problems and tiles --------------------------------------------------------
 
-// Problem 0 is the 3D range [0, N).  Every plane bin with >= 2 vertices
-// becomes a problem.  Plane problems are appended in key order by a
-// single-pass compaction (one thread per key, atomic append; order does
-// not affect the result).
-__global__ void k_problems(const long long* __restrict__ nv_dev, Params p, const int* __restrict__ hist,
-                           const long long* __restrict__ offs, Problem* __restrict__ probs,
-                           Counters* __restrict__ cnt) {
+// Problem 0 is the 3D range [0, N).  Every plane with >= 2 vertices becomes
+// a problem (appended in any order: the result does not depend on it).
+__global__ void k_problems(const long long* __restrict__ nv_dev, Params p, const long long* __restrict__ offs,
+                           Problem* __restrict__ probs, Counters* __restrict__ cnt) {
   const long long n = min(*nv_dev, p.nv_cap);
   const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (gid == 0) {
@@ -233,19 +262,30 @@ __global__ void k_problems(const long long* __restrict__ nv_dev, Params p, const
     probs[0] = q;
   }
   if (!p.planes) return;
-  const long long nplane = p.K - p.C3;
-  for (long long k = gid; k < nplane; k += (long long)gridDim.x * blockDim.x) {
-    const long long key = p.C3 + k;
-    const int c = hist[key];
-    if (c < 2) continue;
+  const long long nz2 = 2LL * p.nz + 1, ny2 = 2LL * p.ny + 1, nx2 = 2LL * p.nx + 1;
+  const long long nplanes = nz2 + ny2 + nx2;
+  for (long long k = gid; k < nplanes; k += (long long)gridDim.x * blockDim.x) {
     int axis;
-    if (k < 2LL * p.nz + 1) axis = 2;
-    else if (k < 2LL * p.nz + 1 + 2LL * p.ny + 1) axis = 1;
-    else axis = 0;
+    long long k0, k1;
+    if (k < nz2) {
+      axis = 2;
+      k0 = p.S0 + k * p.PX * p.PY;
+      k1 = k0 + (long long)p.PX * p.PY;
+    } else if (k < nz2 + ny2) {
+      axis = 1;
+      k0 = p.S1 + (k - nz2) * p.PX * p.PZ;
+      k1 = k0 + (long long)p.PX * p.PZ;
+    } else {
+      axis = 0;
+      k0 = p.S2 + (k - nz2 - ny2) * p.PY * p.PZ;
+      k1 = k0 + (long long)p.PY * p.PZ;
+    }
+    const long long beg = offs[k0], len = offs[k1] - beg;
+    if (len < 2) continue;
     const int slot = 1 + atomicAdd(&cnt->n_problems, 1);
     if (slot >= p.max_problems) { atomicOr(&cnt->status, DEV_ERR_PROBCAP); continue; }
     Problem q;
-    q.axis = axis; q.beg = (int)offs[key]; q.len = c; q.tile_beg = 0; q.pair_beg = 0;
+    q.axis = axis; q.beg = (int)beg; q.len = (int)len; q.tile_beg = 0; q.pair_beg = 0;
     probs[slot] = q;
   }
 }
@@ -285,7 +325,7 @@ __global__ void k_problem_scan(Problem* __restrict__ probs, Params p, Counters* 
   }
   if (threadIdx.x == 0) {
     cnt->n_problems = np;
-    cnt->n_tiles = (int)carry_t;
+    cnt->n_tiles = (int)min(carry_t, p.max_tiles);
     cnt->n_pairs = carry_p;
     if (carry_t > p.max_tiles) atomicOr(&cnt->status, DEV_ERR_PROBCAP);
   }
@@ -307,136 +347,112 @@ __global__ void k_tiles(const Problem* __restrict__ probs, Params p, const Count
       tl.problem = (int)i;
       tl.beg = q.beg + t * p.TS;
       tl.len = min(p.TS, q.len - t * p.TS);
-      tl.pad = 0;
+      tl.tile_end = (int)min((long long)q.tile_beg + nt, p.max_tiles);
       tiles[ti] = tl;
     }
   }
 }
 
-__constant__ float c_dirs[kNumDirs][3] = {{1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1},
-                                          {0, 0, -1}, {1, 1, 1}, {1, 1, -1}, {1, -1, 1}, {1, -1, -1},
-                                          {-1, 1, 1}, {-1, 1, -1}, {-1, -1, 1}, {-1, -1, -1}};
-
-// One block (128 threads) per tile: bounding box and directional extremes.
-__global__ void k_tile_box(const float4* __restrict__ sorted, const Tile* __restrict__ tiles, Params p,
-                           const Counters* __restrict__ cnt, float4* __restrict__ box,
-                           ProblemState* __restrict__ ps) {
-  const int nt = min(cnt->n_tiles, (int)p.max_tiles);
-  __shared__ float s_lo[3][4], s_hi[3][4];
-  __shared__ unsigned long long s_ext[kNumDirs][4];
-  for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
+// One warp per tile: bounding box of its FP32 positions.
+__global__ void k_tile_box(const float4* __restrict__ sorted, const Tile* __restrict__ tiles,
+                           const Counters* __restrict__ cnt, float4* __restrict__ box) {
+  const int nt = cnt->n_tiles;
+  const int lane = threadIdx.x & 31;
+  const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long ti = warp; ti < nt; ti += nwarps) {
     const Tile tl = tiles[ti];
     float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
-    unsigned long long ext[kNumDirs];
-    for (int k = 0; k < kNumDirs; ++k) ext[k] = 0ull;
-    for (int i = threadIdx.x; i < tl.len; i += blockDim.x) {
-      const int e = tl.beg + i;
-      const float4 v = sorted[e];
+    for (int i = lane; i < tl.len; i += 32) {
+      const float4 v = sorted[tl.beg + i];
       lo[0] = fminf(lo[0], v.x); lo[1] = fminf(lo[1], v.y); lo[2] = fminf(lo[2], v.z);
       hi[0] = fmaxf(hi[0], v.x); hi[1] = fmaxf(hi[1], v.y); hi[2] = fmaxf(hi[2], v.z);
-      for (int k = 0; k < kNumDirs; ++k) {
-        const float pr = c_dirs[k][0] * v.x + c_dirs[k][1] * v.y + c_dirs[k][2] * v.z;
-        const unsigned long long key = ((unsigned long long)ord_float(pr) << 32) | (unsigned int)e;
-        ext[k] = max(ext[k], key);
-      }
     }
-    for (int off = 16; off > 0; off >>= 1) {
+    for (int off = 16; off > 0; off >>= 1)
       for (int k = 0; k < 3; ++k) {
         lo[k] = fminf(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], off));
         hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], off));
       }
-      for (int k = 0; k < kNumDirs; ++k) ext[k] = max(ext[k], __shfl_xor_sync(0xffffffffu, ext[k], off));
-    }
-    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane == 0) {
-      for (int k = 0; k < 3; ++k) { s_lo[k][wid] = lo[k]; s_hi[k][wid] = hi[k]; }
-      for (int k = 0; k < kNumDirs; ++k) s_ext[k][wid] = ext[k];
+      box[2 * ti] = make_float4(lo[0], lo[1], lo[2], 0.f);
+      box[2 * ti + 1] = make_float4(hi[0], hi[1], hi[2], 0.f);
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      const int nw = blockDim.x >> 5;
-      for (int w = 1; w < nw; ++w) {
-        for (int k = 0; k < 3; ++k) { s_lo[k][0] = fminf(s_lo[k][0], s_lo[k][w]); s_hi[k][0] = fmaxf(s_hi[k][0], s_hi[k][w]); }
-        for (int k = 0; k < kNumDirs; ++k) s_ext[k][0] = max(s_ext[k][0], s_ext[k][w]);
-      }
-      box[2 * ti] = make_float4(s_lo[0][0], s_lo[1][0], s_lo[2][0], 0.f);
-      box[2 * ti + 1] = make_float4(s_hi[0][0], s_hi[1][0], s_hi[2][0], 0.f);
-      for (int k = 0; k < kNumDirs; ++k)
-        if (s_ext[k][0]) atomicMax(&ps[tl.problem].ext[k], s_ext[k][0]);
-    }
-    __syncthreads();
   }
 }
 
-// One warp per problem: the pairs of its directional extremes seed F.
-__global__ void k_seed(const float4* __restrict__ sorted, Params p, const Counters* __restrict__ cnt,
-                       ProblemState* __restrict__ ps) {
-  const int np = cnt->n_problems;
+// Seed: one warp per tile row a.  The pairs of tile representatives (first
+// vertex of each tile) of one problem, plus each tile's first-last pair, are
+// actual vertex pairs, so their largest f is a valid starting F.
+__global__ void k_seed_rows(const float4* __restrict__ sorted, const Tile* __restrict__ tiles,
+                            const Counters* __restrict__ cnt, ProblemState* __restrict__ ps) {
+  const int nt = cnt->n_tiles;
   const int lane = threadIdx.x & 31;
   const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long i = warp; i < np; i += nwarps) {
-    float best = 0.0f;
-    for (int pr = lane; pr < kNumDirs * kNumDirs; pr += 32) {
-      const int a = pr / kNumDirs, b = pr % kNumDirs;
-      if (b <= a) continue;
-      const unsigned long long ka = ps[i].ext[a], kb = ps[i].ext[b];
-      if (!ka || !kb) continue;
-      const float4 va = sorted[(unsigned int)ka], vb = sorted[(unsigned int)kb];
-      best = fmaxf(best, pair_f(va, vb));
-    }
+  for (long long a = warp; a < nt; a += nwarps) {
+    const Tile ta = tiles[a];
+    const float4 ra = sorted[ta.beg];
+    float best = lane == 0 ? pair_f(ra, sorted[ta.beg + ta.len - 1]) : 0.0f;
+    for (long long b = a + 1 + lane; b < ta.tile_end; b += 32) best = fmaxf(best, pair_f(ra, sorted[tiles[b].beg]));
     for (int off = 16; off > 0; off >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, off));
-    if (lane == 0) atomicMax(&ps[i].F, __float_as_uint(best));
+    if (lane == 0 && best > 0.0f) atomicMax(&ps[ta.problem].F, __float_as_uint(best));
   }
 }
 
 // ---- 3. culling -------------------------------------------------------------------
-
-__device__ __forceinline__ int find_problem(const Problem* probs, int np, long long g) {
-  int lo = 0, hi = np - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (probs[mid].pair_beg <= g) lo = mid;
-    else hi = mid - 1;
+// One warp per tile row a: every tile pair (a, b >= a) of the same problem
+// whose box bound reaches T(F) goes to the work list.
+__global__ void k_cull_rows(const Tile* __restrict__ tiles, const float4* __restrict__ box, Params p,
+                            Counters* __restrict__ cnt, const ProblemState* __restrict__ ps,
+                            WorkItem* __restrict__ work) {
+  const int nt = cnt->n_tiles;
+  const int lane = threadIdx.x & 31;
+  const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long a = warp; a < nt; a += nwarps) {
+    const Tile ta = tiles[a];
+    const float T = threshold(__uint_as_float(ps[ta.problem].F), p);
+    const float4 alo = box[2 * a], ahi = box[2 * a + 1];
+    for (long long b0 = a; b0 < ta.tile_end; b0 += 32) {
+      const long long b = b0 + lane;
+      bool keep = false;
+      if (b < ta.tile_end) keep = box_ub(alo, ahi, box[2 * b], box[2 * b + 1]) >= T;
+      const unsigned int m = __ballot_sync(0xffffffffu, keep);
+      if (!m) continue;
+      long long base = 0;
+      if (lane == 0) base = atomicAdd((unsigned long long*)&cnt->n_work, (unsigned long long)__popc(m));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (keep) {
+        const long long slot = base + __popc(m & ((1u << lane) - 1u));
+        if (slot < p.work_cap) {
+          WorkItem w;
+          w.problem = ta.problem; w.ta = (int)a; w.tb = (int)b; w.pad = 0;
+          work[slot] = w;
+        } else {
+          atomicOr(&cnt->status, DEV_ERR_WORKCAP);
+        }
+      }
+    }
   }
-  return lo;
 }
 
-__global__ void k_cull(const Problem* __restrict__ probs, const float4* __restrict__ box, Params p,
-                       Counters* __restrict__ cnt, const ProblemState* __restrict__ ps,
-                       WorkItem* __restrict__ work) {
-  const int np = cnt->n_problems;
-  const long long total = cnt->n_pairs;
+// Items whose FP32 maximum reaches the final threshold of their problem are
+// re-evaluated for candidates; list them compactly.
+__global__ void k_compact_items(const WorkItem* __restrict__ work, const float* __restrict__ itemmax, Params p,
+                                Counters* __restrict__ cnt, const ProblemState* __restrict__ ps,
+                                int* __restrict__ work2) {
+  const long long nwork = min(cnt->n_work, p.work_cap);
   const int lane = threadIdx.x & 31;
-  for (long long g0 = blockIdx.x * (long long)blockDim.x; g0 < total; g0 += (long long)gridDim.x * blockDim.x) {
-    const long long g = g0 + threadIdx.x;
+  for (long long i0 = blockIdx.x * (long long)blockDim.x; i0 < nwork; i0 += (long long)gridDim.x * blockDim.x) {
+    const long long i = i0 + threadIdx.x;
     bool keep = false;
-    WorkItem w;
-    if (g < total) {
-      const int pi = find_problem(probs, np, g);
-      const Problem q = probs[pi];
-      const long long l = g - q.pair_beg;
-      long long b = (long long)((sqrt(8.0 * (double)l + 1.0) - 1.0) * 0.5);
-      while (b * (b + 1) / 2 > l) --b;
-      while ((b + 1) * (b + 2) / 2 <= l) ++b;
-      const long long a = l - b * (b + 1) / 2;
-      const int ta = q.tile_beg + (int)a, tb = q.tile_beg + (int)b;
-      if (tb < p.max_tiles) {
-        const float ub = box_ub(box[2 * ta], box[2 * ta + 1], box[2 * tb], box[2 * tb + 1]);
-        const float T = threshold(__uint_as_float(ps[pi].F), p);
-        keep = ub >= T;
-      }
-      w.problem = pi; w.ta = ta; w.tb = tb; w.pad = 0;
-    }
+    if (i < nwork) keep = itemmax[i] >= threshold(__uint_as_float(ps[work[i].problem].F), p);
     const unsigned int m = __ballot_sync(0xffffffffu, keep);
+    if (!m) continue;
     long long base = 0;
-    if (lane == 0 && m) base = atomicAdd((unsigned long long*)&cnt->n_work, (unsigned long long)__popc(m));
+    if (lane == 0) base = atomicAdd((unsigned long long*)&cnt->n_work2, (unsigned long long)__popc(m));
     base = __shfl_sync(0xffffffffu, base, 0);
-    if (keep) {
-      const long long slot = base + __popc(m & ((1u << lane) - 1u));
-      if (slot < p.work_cap) work[slot] = w;
-      else atomicOr(&cnt->status, DEV_ERR_WORKCAP);
-    }
+    if (keep) work2[base + __popc(m & ((1u << lane) - 1u))] = (int)i;
   }
 }
 
@@ -539,23 +555,14 @@ __global__ void __launch_bounds__(NT) k_pairs_max(const float4* __restrict__ sor
 
 template <int TS, int NT>
 __global__ void __launch_bounds__(NT) k_pairs_cand(const float4* __restrict__ sorted, const Tile* __restrict__ tiles,
-                                                   const WorkItem* __restrict__ work, Params p,
-                                                   Counters* __restrict__ cnt, const ProblemState* __restrict__ ps,
-                                                   const float* __restrict__ itemmax, Cand* __restrict__ cand) {
+                                                   const WorkItem* __restrict__ work, const int* __restrict__ work2,
+                                                   Params p, Counters* __restrict__ cnt,
+                                                   const ProblemState* __restrict__ ps, Cand* __restrict__ cand) {
   __shared__ float4 sB[TS];
-  __shared__ long long s_item;
-  const long long nwork = min(cnt->n_work, p.work_cap);
-  for (;;) {
-    if (threadIdx.x == 0) s_item = atomicAdd(&cnt->ticket2, 1);
-    __syncthreads();
-    const long long it = s_item;
-    if (it >= nwork) break;
-    const WorkItem w = work[it];
+  const long long n2 = cnt->n_work2;
+  for (long long k = blockIdx.x; k < n2; k += gridDim.x) {
+    const WorkItem w = work[work2[k]];
     const float T = threshold(__uint_as_float(ps[w.problem].F), p);
-    if (!(itemmax[it] >= T)) {
-      __syncthreads();
-      continue;
-    }
     const Tile A = tiles[w.ta], B = tiles[w.tb];
     eval_pair_tile<TS, NT, true>(sorted, A, B, sB, T, w.problem, cand, cnt, p.cand_cap);
     __syncthreads();
@@ -664,7 +671,6 @@ __global__ void k_init_states(ProblemState* __restrict__ ps, long long n) {
     ProblemState s;
     s.F = 0u;
     s.pad = 0u;
-    for (int k = 0; k < kNumDirs; ++k) s.ext[k] = 0ull;
     s.best_d2 = 0ull;
     s.best_pair = ~0ull;
     ps[i] = s;
@@ -679,13 +685,15 @@ T* carve(char*& cur, size_t n) {
 }
 
 template <int TS, int NT>
-rad_status launch_pairs(const float4* sorted, const Tile* tiles, const float4* box, const WorkItem* work,
+rad_status launch_pairs(const float4* sorted, const Tile* tiles, const float4* box, const WorkItem* work, int* work2,
                         const Params& p, Counters* cnt, ProblemState* ps, float* itemmax, Cand* cand, int ctas,
                         cudaStream_t st) {
   auto kmax = k_pairs_max<TS, NT>;
   auto kcand = k_pairs_cand<TS, NT>;
+  const int sms = num_sms();
   RAD_LAUNCH("diam_pairs_fp32", kmax, ctas, NT, 0, st, sorted, tiles, box, work, p, cnt, ps, itemmax);
-  RAD_LAUNCH("diam_pairs_cand", kcand, ctas, NT, 0, st, sorted, tiles, work, p, cnt, ps, itemmax, cand);
+  RAD_LAUNCH("diam_compact", k_compact_items, sms * 4, 256, 0, st, work, itemmax, p, cnt, ps, work2);
+  RAD_LAUNCH("diam_pairs_cand", kcand, ctas, NT, 0, st, sorted, tiles, work, work2, p, cnt, ps, cand);
   return RAD_OK;
 }
 
@@ -703,8 +711,15 @@ rad_status diam_run(const int16_t* idx2, const double* vt, long long nv_hint, co
   p.CX = ((2 * d.nx) >> p.cell_shift) + 1;
   p.CY = ((2 * d.ny) >> p.cell_shift) + 1;
   p.CZ = ((2 * d.nz) >> p.cell_shift) + 1;
+  p.plane_shift = tu.cell_shift + 1;
+  p.PX = ((2 * d.nx) >> p.plane_shift) + 1;
+  p.PY = ((2 * d.ny) >> p.plane_shift) + 1;
+  p.PZ = ((2 * d.nz) >> p.plane_shift) + 1;
   p.C3 = (long long)p.CX * p.CY * p.CZ;
-  p.K = p.C3 + (p.planes ? (2LL * d.nx + 1) + (2LL * d.ny + 1) + (2LL * d.nz + 1) : 0);
+  p.S0 = p.C3;
+  p.S1 = p.S0 + (p.planes ? (2LL * d.nz + 1) * p.PX * p.PY : 0);
+  p.S2 = p.S1 + (p.planes ? (2LL * d.ny + 1) * p.PX * p.PZ : 0);
+  p.K = p.S2 + (p.planes ? (2LL * d.nx + 1) * p.PY * p.PZ : 0);
   p.sx = sp[0]; p.sy = sp[1]; p.sz = sp[2];
   p.cx = 0.5 * (d.nx - 1); p.cy = 0.5 * (d.ny - 1); p.cz = 0.5 * (d.nz - 1);
   const double u = ldexp(1.0, -24);
@@ -729,13 +744,14 @@ rad_status diam_run(const int16_t* idx2, const double* vt, long long nv_hint, co
   p.work_cap = s.work_cap;
   p.cand_cap = s.cand_cap;
 
-  // scratch layout
-  const long long nparts = (p.K + kScanBlock - 1) / kScanBlock;
+  // scratch layout (hist/offsets carry one extra entry: offs[K] = total)
+  const long long K1 = p.K + 1;
+  const long long nparts = (K1 + kScanBlock - 1) / kScanBlock;
   size_t bytes = 0;
   auto add = [&](size_t n) { bytes += (n + 255) & ~size_t(255); };
-  add(sizeof(int) * p.K);              // hist
-  add(sizeof(int) * p.K);              // cursor
-  add(sizeof(long long) * p.K);        // offsets
+  add(sizeof(int) * K1);             // hist
+  add(sizeof(int) * K1);             // cursor
+  add(sizeof(long long) * K1);       // offsets
   add(sizeof(long long) * (nparts + 1));
   add(sizeof(float4) * nsorted);
   add(sizeof(Problem) * p.max_problems);
@@ -745,12 +761,13 @@ rad_status diam_run(const int16_t* idx2, const double* vt, long long nv_hint, co
   add(sizeof(Counters));
   add(sizeof(WorkItem) * p.work_cap);
   add(sizeof(float) * p.work_cap);
+  add(sizeof(int) * p.work_cap);
   add(sizeof(Cand) * p.cand_cap);
   RAD_TRY(s.misc.reserve(bytes));
   char* cur = s.misc.as<char>();
-  int* hist = carve<int>(cur, p.K);
-  int* cursor = carve<int>(cur, p.K);
-  long long* offs = carve<long long>(cur, p.K);
+  int* hist = carve<int>(cur, K1);
+  int* cursor = carve<int>(cur, K1);
+  long long* offs = carve<long long>(cur, K1);
   long long* parts = carve<long long>(cur, nparts + 1);
   float4* sorted = carve<float4>(cur, nsorted);
   Problem* probs = carve<Problem>(cur, p.max_problems);
@@ -760,38 +777,40 @@ rad_status diam_run(const int16_t* idx2, const double* vt, long long nv_hint, co
   Counters* cnt = carve<Counters>(cur, 1);
   WorkItem* work = carve<WorkItem>(cur, p.work_cap);
   float* itemmax = carve<float>(cur, p.work_cap);
+  int* work2 = carve<int>(cur, p.work_cap);
   Cand* cand = carve<Cand>(cur, p.cand_cap);
 
   const int sms = num_sms();
-  RAD_CUDA(cudaMemsetAsync(hist, 0, sizeof(int) * p.K, st));
-  RAD_CUDA(cudaMemsetAsync(cursor, 0, sizeof(int) * p.K, st));
+  RAD_CUDA(cudaMemsetAsync(hist, 0, sizeof(int) * K1, st));
+  RAD_CUDA(cudaMemsetAsync(cursor, 0, sizeof(int) * K1, st));
   RAD_CUDA(cudaMemsetAsync(cnt, 0, sizeof(Counters), st));
   RAD_LAUNCH("diam_init", k_init_states, std::min<long long>((p.max_problems + 255) / 256, sms * 4), 256, 0, st, ps,
              p.max_problems);
   const int vblocks = (int)std::min<long long>((nv + 255) / 256, (long long)sms * 8);
   RAD_LAUNCH("diam_hist", k_hist, vblocks, 256, 0, st, idx2, nv_dev, p, hist);
-  RAD_LAUNCH("diam_scan_part", k_xscan_part, (int)nparts, kScanBlock, 0, st, hist, p.K, offs, parts);
-  RAD_LAUNCH("diam_scan_top", k_xscan_top, 1, 32, 0, st, parts, (int)nparts, (long long*)nullptr);
-  RAD_LAUNCH("diam_scan_add", k_xscan_add, (int)nparts, kScanBlock, 0, st, offs, p.K, parts);
+  RAD_LAUNCH("diam_scan_part", k_xscan_part, (int)nparts, kScanBlock, 0, st, hist, K1, offs, parts);
+  RAD_LAUNCH("diam_scan_top", k_xscan_top, 1, 1024, 0, st, parts, (int)nparts);
+  RAD_LAUNCH("diam_scan_add", k_xscan_add, (int)nparts, kScanBlock, 0, st, offs, K1, parts);
   RAD_LAUNCH("diam_scatter", k_scatter, vblocks, 256, 0, st, idx2, vt, nv_dev, p, offs, cursor, sorted);
-  RAD_LAUNCH("diam_problems", k_problems, (int)std::max<long long>(1, std::min<long long>((p.K - p.C3 + 255) / 256, sms * 4)),
-             256, 0, st, nv_dev, p, hist, offs, probs, cnt);
+  const long long nplanes = p.planes ? (2LL * d.nx + 1) + (2LL * d.ny + 1) + (2LL * d.nz + 1) : 1;
+  RAD_LAUNCH("diam_problems", k_problems, (int)std::max<long long>(1, std::min<long long>((nplanes + 255) / 256, sms * 4)),
+             256, 0, st, nv_dev, p, offs, probs, cnt);
   RAD_LAUNCH("diam_problem_scan", k_problem_scan, 1, 1024, 0, st, probs, p, cnt);
   RAD_LAUNCH("diam_tiles", k_tiles, sms * 4, 256, 0, st, probs, p, cnt, tiles);
-  RAD_LAUNCH("diam_tile_box", k_tile_box, sms * 8, 128, 0, st, sorted, tiles, p, cnt, box, ps);
-  RAD_LAUNCH("diam_seed", k_seed, sms * 2, 256, 0, st, sorted, p, cnt, ps);
-  RAD_LAUNCH("diam_cull", k_cull, sms * 16, 256, 0, st, probs, box, p, cnt, ps, work);
+  RAD_LAUNCH("diam_tile_box", k_tile_box, sms * 8, 256, 0, st, sorted, tiles, cnt, box);
+  RAD_LAUNCH("diam_seed", k_seed_rows, sms * 8, 256, 0, st, sorted, tiles, cnt, ps);
+  RAD_LAUNCH("diam_cull", k_cull_rows, sms * 8, 256, 0, st, tiles, box, p, cnt, ps, work);
   const int ctas = sms * tu.ctas_per_sm;
   if (tu.tile == 64) {
-    if (tu.threads == 64) RAD_TRY((launch_pairs<64, 64>(sorted, tiles, box, work, p, cnt, ps, itemmax, cand, ctas, st)));
-    else RAD_TRY((launch_pairs<64, 128>(sorted, tiles, box, work, p, cnt, ps, itemmax, cand, ctas, st)));
+    if (tu.threads == 64) RAD_TRY((launch_pairs<64, 64>(sorted, tiles, box, work, work2, p, cnt, ps, itemmax, cand, ctas, st)));
+    else RAD_TRY((launch_pairs<64, 128>(sorted, tiles, box, work, work2, p, cnt, ps, itemmax, cand, ctas, st)));
   } else if (tu.tile == 128) {
-    if (tu.threads == 64) RAD_TRY((launch_pairs<128, 64>(sorted, tiles, box, work, p, cnt, ps, itemmax, cand, ctas, st)));
-    else if (tu.threads == 128) RAD_TRY((launch_pairs<128, 128>(sorted, tiles, box, work, p, cnt, ps, itemmax, cand, ctas, st)));
-    else RAD_TRY((launch_pairs<128, 256>(sorted, tiles, box, work, p, cnt, ps, itemmax, cand, ctas, st)));
+    if (tu.threads == 64) RAD_TRY((launch_pairs<128, 64>(sorted, tiles, box, work, work2, p, cnt, ps, itemmax, cand, ctas, st)));
+    else if (tu.threads == 128) RAD_TRY((launch_pairs<128, 128>(sorted, tiles, box, work, work2, p, cnt, ps, itemmax, cand, ctas, st)));
+    else RAD_TRY((launch_pairs<128, 256>(sorted, tiles, box, work, work2, p, cnt, ps, itemmax, cand, ctas, st)));
   } else {
-    if (tu.threads == 128) RAD_TRY((launch_pairs<256, 128>(sorted, tiles, box, work, p, cnt, ps, itemmax, cand, ctas, st)));
-    else RAD_TRY((launch_pairs<256, 256>(sorted, tiles, box, work, p, cnt, ps, itemmax, cand, ctas, st)));
+    if (tu.threads == 128) RAD_TRY((launch_pairs<256, 128>(sorted, tiles, box, work, work2, p, cnt, ps, itemmax, cand, ctas, st)));
+    else RAD_TRY((launch_pairs<256, 256>(sorted, tiles, box, work, work2, p, cnt, ps, itemmax, cand, ctas, st)));
   }
   RAD_LAUNCH("diam_confirm", k_confirm, sms * 4, 256, 0, st, sorted, idx2, vt, p, cnt, cand, ps);
   RAD_LAUNCH("diam_tiebreak", k_tiebreak, sms * 4, 256, 0, st, sorted, idx2, vt, p, cnt, cand, ps);
