@@ -226,8 +226,6 @@ def main():
     # ---- timed region: device-resident inputs ------------------------------------
     clocks = ClockSampler(local)
     clocks.start()
-    rad.profile_reset()
-    rad.profile_enable(True)
     launches0 = rad.launch_count()
     barrier(world)
     torch.cuda.synchronize()
@@ -246,11 +244,28 @@ def main():
     torch.cuda.synchronize()
     barrier(world)
     launches = rad.launch_count() - launches0
-    rad.profile_enable(False)
-    prof = rad.profile_read()
     clk = clocks.stop()
     ms = max_over_ranks(statistics.mean(step_ms), world)
     value = world * pairs / (ms / 1e3)
+
+    # ---- per-kernel durations: the same steps with CUDA events around every
+    # kernel (event-record nodes inside the replayed graph) --------------------
+    rad.profile_enable(True)
+    rad.extract(dev, sp, ws)  # re-capture with the event nodes
+    rad.profile_reset()
+    prof_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rad.extract(dev, sp, ws)
+        e1.record(stream)
+        e1.synchronize()
+        prof_ms.append(e0.elapsed_time(e1))
+    rad.profile_enable(False)
+    prof = rad.profile_read()
+    rad.extract(dev, sp, ws)  # back to the graph without event nodes
 
     # ---- end to end through host buffers ------------------------------------------
     e2e_ms = []
@@ -358,11 +373,11 @@ def main():
                 "config": {"workload": WORKLOAD, "n_vertices": N, "n_triangles": T, "pairs": pairs,
                            "pairs_evaluated_fp32": d["pairs_evaluated"], "l2": "flushed between steps (256 MB write)",
                            "parallelism": f"replicas x{world}", "diam_stats": stats},
-                "roofline": roof, "kernels": kernel_table,
+                "roofline": roof, "kernels": kernel_table, "ms_per_step_with_kernel_events": statistics.mean(prof_ms),
                 "e2e": {"value": world * pairs / (e2e / 1e3), "unit": UNIT, "ms_per_step": e2e,
                         "h2d_bytes_per_step": hstats["h2d_bytes"], "d2h_bytes_per_step": hstats["d2h_bytes"]},
                 "plain_fp64": plain, "batched": batch, "cpu_baseline": cpu, "clocks": clk,
-                "gpu_launches": launches}
+                "gpu_launches": launches, "gpu_launches_per_step": launches / args.steps}
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

@@ -116,8 +116,9 @@ rad_status rad_shape_plain_fp64(const rad_mesh_t* mesh, rad_features_t* out, voi
 
 /* Whole path for one device mask: mesh + shape with library-owned buffers
  * kept in `ws` between calls (one host synchronisation per call, none
- * inside).  *ws must be NULL on the first call; free with
- * rad_workspace_free(). */
+ * inside).  From the second call with the same (mask_dev, dims, spacing) and
+ * unchanged pool sizes the whole pass is replayed as one captured CUDA graph.
+ * *ws must be NULL on the first call; free with rad_workspace_free(). */
 typedef struct rad_workspace rad_workspace_t;
 rad_status rad_extract(const uint8_t* mask_dev, const int64_t dims[3], const double spacing[3], rad_features_t* out,
                        rad_workspace_t** ws, void* stream);
@@ -168,7 +169,8 @@ rad_status rad_diameters_plain_fp64_noalloc(const int16_t* idx2_dev, const doubl
 rad_status rad_set_tuning(const rad_tuning_t* set, rad_tuning_t* get);
 
 /* Per-kernel timing: when enabled, every kernel the library launches is
- * bracketed by CUDA events on its launch stream.  rad_profile_read copies up
+ * bracketed by CUDA events on its launch stream (inside a replayed graph the
+ * event pairs are graph nodes, read after each replay).  rad_profile_read copies up
  * to `cap` records (name, launches, total milliseconds) and returns how many
  * exist; it synchronises the device.  rad_profile_reset clears them. */
 typedef struct {

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -65,12 +66,23 @@ void flush_pending(Prof& p) {
     float ms = 0.f;
     if (cudaEventSynchronize(q.b) == cudaSuccess && cudaEventElapsedTime(&ms, q.a, q.b) == cudaSuccess)
       p.stats[q.stat].total_ms += ms;
+    else
+      cudaGetLastError();  // a timing failure must not surface in the caller's next CUDA call
     p.pool.push_back(q.a);
     p.pool.push_back(q.b);
   }
   p.pending.clear();
 }
 }  // namespace
+
+// While a CUDA graph is being captured on this thread, launches are collected
+// here: their kernel-stat slots (counted per replay) and, with profiling on,
+// the event pair around each kernel (recorded by every replay).
+struct CaptureSink {
+  std::vector<int> stats;
+  std::vector<Pending> slots;
+};
+static thread_local CaptureSink* g_sink = nullptr;
 
 void launch_begin(const char* name, cudaStream_t s, void** token) {
   Prof& p = prof();
@@ -87,26 +99,85 @@ void launch_begin(const char* name, cudaStream_t s, void** token) {
     idx = (int)p.stats.size() - 1;
   }
   p.stats[idx].launches++;
+  if (g_sink) g_sink->stats.push_back(idx);
   if (!p.on) {
     *token = nullptr;
     return;
   }
-  if (p.pending.size() > 4096) flush_pending(p);
   Pending q;
   q.stat = idx;
   q.a = get_event(p);
   q.b = get_event(p);
+  if (g_sink) {
+    // inside a capture only an external record becomes a node that records
+    // the event at every replay
+    cudaEventRecordWithFlags(q.a, s, cudaEventRecordExternal);
+    g_sink->slots.push_back(q);
+    *token = reinterpret_cast<void*>((intptr_t)(-(intptr_t)g_sink->slots.size()));
+    return;
+  }
   cudaEventRecord(q.a, s);
+  if (p.pending.size() > 4096) flush_pending(p);
   p.pending.push_back(q);
   *token = reinterpret_cast<void*>((intptr_t)p.pending.size());
+}
+
+bool profiling_on() {
+  Prof& p = prof();
+  std::lock_guard<std::mutex> g(p.mu);
+  return p.on;
 }
 
 void launch_end(void* token, cudaStream_t s) {
   if (!token) return;
   Prof& p = prof();
   std::lock_guard<std::mutex> g(p.mu);
-  const size_t i = (size_t)(intptr_t)token - 1;
+  const intptr_t t = (intptr_t)token;
+  if (t < 0) {
+    if (g_sink && (size_t)(-t - 1) < g_sink->slots.size())
+      cudaEventRecordWithFlags(g_sink->slots[-t - 1].b, s, cudaEventRecordExternal);
+    return;
+  }
+  const size_t i = (size_t)t - 1;
   if (i < p.pending.size()) cudaEventRecord(p.pending[i].b, s);
+}
+
+// Bookkeeping of a captured graph: undo the counts made while capturing, then
+// add one launch per captured kernel at every replay and, after the replay has
+// finished, the elapsed time of each captured event pair.
+void graph_undo_capture(const CaptureSink& k) {
+  Prof& p = prof();
+  std::lock_guard<std::mutex> g(p.mu);
+  p.launches -= (long long)k.stats.size();
+  for (int i : k.stats) p.stats[i].launches--;
+}
+
+void graph_replayed(const CaptureSink& k) {
+  Prof& p = prof();
+  std::lock_guard<std::mutex> g(p.mu);
+  p.launches += (long long)k.stats.size();
+  for (int i : k.stats) p.stats[i].launches++;
+}
+
+void graph_timed(const CaptureSink& k) {
+  Prof& p = prof();
+  std::lock_guard<std::mutex> g(p.mu);
+  for (const Pending& q : k.slots) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, q.a, q.b) == cudaSuccess) p.stats[q.stat].total_ms += ms;
+    else cudaGetLastError();
+  }
+}
+
+void graph_release(CaptureSink& k) {
+  Prof& p = prof();
+  std::lock_guard<std::mutex> g(p.mu);
+  for (const Pending& q : k.slots) {
+    p.pool.push_back(q.a);
+    p.pool.push_back(q.b);
+  }
+  k.slots.clear();
+  k.stats.clear();
 }
 
 int num_sms() {
@@ -124,8 +195,12 @@ int num_sms() {
 
 // ---- buffers -----------------------------------------------------------------------
 
+static std::atomic<long long> g_alloc_epoch{0};
+long long alloc_epoch() { return g_alloc_epoch.load(); }
+
 rad_status DevBuf::reserve(size_t need) {
   if (need <= bytes && p) return RAD_OK;
+  g_alloc_epoch++;
   if (p) {
     cudaFree(p);
     p = nullptr;
@@ -170,7 +245,23 @@ struct Work {
   Result* host = nullptr;  // pinned copy
   DevBuf mask;     // device copy of a host mask (rad_extract_host)
   int device = -1;
+  // CUDA graph of the whole rad_extract sequence, valid for one key
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  long long g_epoch = -1;
+  bool g_prof = false;
+  CaptureSink g_sink_data;
+  const void* g_mask = nullptr;
+  int64_t g_dims[3] = {0, 0, 0};
+  double g_sp[3] = {0, 0, 0};
+  void drop_graph() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    gexec = nullptr;
+    graph_release(g_sink_data);
+  }
   ~Work() {
+    drop_graph();
+    if (cap_stream) cudaStreamDestroy(cap_stream);
     ms.bits.release(); ms.counts.release(); ms.wpre.release(); ms.prefix.release(); ms.chunk.release();
     ms.cubes.release(); ms.hist.release(); ms.partial.release();
     ms.bintab.release(); ds.misc.release(); ds.plain_part.release(); result.release(); idx2.release();
@@ -423,38 +514,103 @@ void rad_mesh_free(rad_mesh_t* mesh) {
   memset(mesh, 0, sizeof(*mesh));
 }
 
+// The launch sequence of one whole-path pass (no host synchronisation): mesh,
+// diameters, copy of the result block to pinned host memory.
+static rad_status enqueue_extract(const uint8_t* mask_dev, const MeshDims& d, const double sp[3], Work& w,
+                                  cudaStream_t st) {
+  Result* dr = w.dres();
+  RAD_CUDA(cudaMemsetAsync(&dr->dr, 0, sizeof(DiamResult) + 2 * sizeof(unsigned int), st));
+  RAD_TRY(mesh_count(mask_dev, false, d, w.ms, &dr->mt, st));
+  RAD_TRY(mesh_emit(mask_dev, false, d, sp, w.ms, &dr->mt, w.idx2.as<int16_t>(), nullptr, w.tri.as<int32_t>(),
+                    w.vcap, w.tcap, st));
+  RAD_TRY(diam_run(w.idx2.as<int16_t>(), nullptr, w.vcap, &dr->mt.nv, d, sp, w.ds, &dr->dr, &dr->status, st));
+  RAD_CUDA(cudaMemcpyAsync(w.host, dr, sizeof(Result), cudaMemcpyDeviceToHost, st));
+  return RAD_OK;
+}
+
+// Capture the pass into a CUDA graph on an internal stream (the caller's
+// stream may be the legacy default stream, which cannot be captured).  Every
+// buffer is already sized by an eager pass, so nothing is allocated inside.
+static rad_status capture_extract(const uint8_t* mask_dev, const int64_t dims[3], const double sp[3], Work& w) {
+  w.drop_graph();
+  if (!w.cap_stream) RAD_CUDA(cudaStreamCreateWithFlags(&w.cap_stream, cudaStreamNonBlocking));
+  const MeshDims d = make_dims(dims);
+  const long long epoch0 = alloc_epoch();
+  RAD_CUDA(cudaStreamBeginCapture(w.cap_stream, cudaStreamCaptureModeThreadLocal));
+  g_sink = &w.g_sink_data;
+  rad_status s = enqueue_extract(mask_dev, d, sp, w, w.cap_stream);
+  g_sink = nullptr;
+  graph_undo_capture(w.g_sink_data);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(w.cap_stream, &graph);
+  if (s != RAD_OK || e != cudaSuccess || alloc_epoch() != epoch0) {
+    // failed, or a buffer moved while capturing: keep running eagerly
+    if (graph) cudaGraphDestroy(graph);
+    graph_release(w.g_sink_data);
+    if (s != RAD_OK) return s;
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+    return RAD_OK;
+  }
+  e = cudaGraphInstantiate(&w.gexec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    w.gexec = nullptr;
+    graph_release(w.g_sink_data);
+    return cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__);
+  }
+  w.g_prof = profiling_on();
+  w.g_epoch = alloc_epoch();
+  w.g_mask = mask_dev;
+  for (int k = 0; k < 3; ++k) { w.g_dims[k] = dims[k]; w.g_sp[k] = sp[k]; }
+  return RAD_OK;
+}
+
+static bool graph_matches(const Work& w, const uint8_t* mask_dev, const int64_t dims[3], const double sp[3]) {
+  if (!w.gexec || w.g_epoch != alloc_epoch() || w.g_mask != mask_dev || w.g_prof != profiling_on()) return false;
+  for (int k = 0; k < 3; ++k)
+    if (w.g_dims[k] != dims[k] || w.g_sp[k] != sp[k]) return false;
+  return true;
+}
+
 // Whole path with no host synchronisation inside: capacities come from the
 // previous call on this workspace (the first call sizes them with a counting
 // pass); an overflow is detected from the device status and the call re-runs
-// with grown pools.
+// with grown pools.  From the second call on the same (mask, dims, spacing)
+// the pass is replayed as one CUDA graph (with per-kernel event pairs inside it
+// when profiling is on).
 static rad_status extract_impl(const uint8_t* mask_dev, const int64_t dims[3], const double sp[3],
                                rad_features_t* out, rad_workspace_t* ws, cudaStream_t st, long long h2d_bytes) {
   Work& w = ws->work;
   RAD_TRY(w.init());
   const MeshDims d = make_dims(dims);
-  Result* dr = w.dres();
   if (w.vcap == 0) {
     RAD_TRY(run_mesh(mask_dev, false, dims, sp, w, &ws->mesh, st));
   }
+  const bool use_graph = true;
   for (int attempt = 0; attempt < 4; ++attempt) {
-    RAD_CUDA(cudaMemsetAsync(&dr->dr, 0, sizeof(DiamResult) + 2 * sizeof(unsigned int), st));
-    RAD_TRY(mesh_count(mask_dev, false, d, w.ms, &dr->mt, st));
-    RAD_TRY(mesh_emit(mask_dev, false, d, sp, w.ms, &dr->mt, w.idx2.as<int16_t>(), nullptr, w.tri.as<int32_t>(),
-                      w.vcap, w.tcap, st));
-    RAD_TRY(diam_run(w.idx2.as<int16_t>(), nullptr, w.vcap, &dr->mt.nv, d, sp, w.ds, &dr->dr, &dr->status, st));
-    RAD_CUDA(cudaMemcpyAsync(w.host, dr, sizeof(Result), cudaMemcpyDeviceToHost, st));
+    bool replayed = false;
+    if (use_graph && graph_matches(w, mask_dev, dims, sp)) {
+      RAD_CUDA(cudaGraphLaunch(w.gexec, st));
+      graph_replayed(w.g_sink_data);
+      replayed = true;
+    } else {
+      RAD_TRY(enqueue_extract(mask_dev, d, sp, w, st));
+    }
     RAD_CUDA(cudaStreamSynchronize(st));
+    if (replayed) graph_timed(w.g_sink_data);
     const Result& r = *w.host;
     const unsigned int s = r.status | r.mt.status;
     if (r.mt.nv > w.vcap || r.mt.nt > w.tcap || (s & (DEV_ERR_VCAP | DEV_ERR_TCAP))) {
+      w.drop_graph();
       RAD_TRY(run_mesh(mask_dev, false, dims, sp, w, &ws->mesh, st));
       continue;
     }
-    if (s & DEV_ERR_WORKCAP) { w.ds.work_cap *= 4; continue; }
-    if (s & DEV_ERR_CANDCAP) { w.ds.cand_cap *= 4; continue; }
+    if (s & DEV_ERR_WORKCAP) { w.drop_graph(); w.ds.work_cap *= 4; continue; }
+    if (s & DEV_ERR_CANDCAP) { w.drop_graph(); w.ds.cand_cap *= 4; continue; }
     RAD_TRY(status_from_dev(s));
     fill_features(r, dims, sp, r.mt.nv >= 2, out);
     record_stats(r, h2d_bytes, true);
+    if (use_graph && !graph_matches(w, mask_dev, dims, sp)) RAD_TRY(capture_extract(mask_dev, dims, sp, w));
     return RAD_OK;
   }
   return status_from_dev(w.host->status | w.host->mt.status);
@@ -527,7 +683,10 @@ void rad_profile_reset(void) {
   Prof& p = prof();
   std::lock_guard<std::mutex> g(p.mu);
   flush_pending(p);
-  p.stats.clear();
+  for (auto& st : p.stats) {  // keep the entries: captured graphs refer to them
+    st.launches = 0;
+    st.total_ms = 0.0;
+  }
 }
 
 int64_t rad_launch_count(void) {

@@ -42,6 +42,8 @@ void launch_end(void* token, cudaStream_t s);
   } while (0)
 
 int num_sms();
+bool profiling_on();
+long long alloc_epoch();           // bumps whenever a library buffer is reallocated
 
 // ---- device buffers ----------------------------------------------------------
 // A grow-only device buffer owned by the library.

@@ -161,3 +161,43 @@ def test_invalid_arguments():
     big = (ctypes.c_int64 * 3)(4, 4, 20000)
     st = rad.lib().rad_mesh(ctypes.c_void_p(dev.data_ptr()), big, sp, ctypes.byref(mt), None)
     assert st == 1
+
+
+def test_graph_replay_follows_new_contents():
+    """From the second call the whole pass is a replayed CUDA graph bound to
+    the buffer, not to its contents: new contents in the same buffer give the
+    new features, and a mask with more vertices than the pools hold makes the
+    call fall back, grow the pools and re-capture."""
+    rng = np.random.default_rng(13)
+    shape = (24, 40, 48)
+    masks = [(synth._noise_blob(rng, shape, s) > 0.5).astype(np.uint8) for s in (4.0, 3.0, 1.2)]
+    sp = (0.8, 0.8, 3.0)
+    buf = torch.zeros(shape, dtype=torch.uint8, device="cuda")
+    ws = rad.Workspace()
+    for m in masks + masks[:1]:
+        buf.copy_(torch.from_numpy(m))
+        ref, _ = oracle.features(m, sp)
+        for _ in range(3):
+            assert_features(rad.extract(buf, sp, ws), ref)
+
+
+def test_kernel_timing_inside_replayed_graph():
+    m, sp = synth.ellipsoid_32(5)
+    dev = torch.from_numpy(m).cuda()
+    ws = rad.Workspace()
+    rad.profile_enable(True)
+    try:
+        rad.extract(dev, sp, ws)
+        rad.extract(dev, sp, ws)  # captured with event nodes
+        rad.profile_reset()
+        n0 = rad.launch_count()
+        for _ in range(3):
+            rad.extract(dev, sp, ws)
+        prof = rad.profile_read()
+        per_call = (rad.launch_count() - n0) / 3
+    finally:
+        rad.profile_enable(False)
+    assert prof["mc_pack_u8"]["launches"] == 3 and prof["mc_pack_u8"]["total_ms"] > 0
+    assert prof["diam_pairs_fp32"]["launches"] == 3 and prof["diam_pairs_fp32"]["total_ms"] > 0
+    assert per_call == sum(v["launches"] for v in prof.values()) / 3
+    torch.zeros(8, device="cuda").sum().item()  # no CUDA error left behind
