@@ -123,18 +123,25 @@ def max_over_ranks(x, world):
 
 
 def kernel_work(name, ctx):
-    """Algorithmic work of one launch of `name`: (bound, amount, unit_scale)."""
-    nvox, words4, N, T, R = ctx["nvox"], ctx["bitset_bytes"], ctx["N"], ctx["T"], ctx["rows"]
-    if name == "mc_pack_u8":
-        return "hbm", nvox + words4
-    if name == "mc_count":
-        return "hbm", words4 + 12 * R
-    if name == "mc_emit":
-        return "hbm", words4 + 6 * N + 12 * T
+    """Algorithmic work of one launch of `name`: ("hbm", bytes) or ("alu", FP32 flops).
+
+    Bytes count what the kernel must move at least once (its inputs read, its
+    outputs written); flops count the evaluated vertex pairs of the FP32
+    filter at 8 flops each."""
+    nvox, words4, N, T, R, na = (ctx[k] for k in ("nvox", "bitset_bytes", "N", "T", "rows", "cubes"))
+    W = ctx["words_per_row"]
+    table = {
+        "mc_pack_u8": nvox + words4,                    # mask in, bitset out
+        "mc_count": words4 + 16 * R + 4 * R * W,        # bitset in, row counts + word prefixes out
+        "mc_rows": 6 * N + 16 * na,                     # vertices + active-cube list out
+        "mc_cubes": 16 * na + 12 * T,                   # cube list in, triangles out
+        "diam_hist": 6 * N,                             # vertices in
+        "diam_scatter": 6 * N + 4 * 16 * N,             # vertices in, sorted entries out
+    }
     if name == "diam_pairs_fp32":
         return "alu", FLOPS_PER_PAIR * ctx["pairs_evaluated"]
-    if name == "diam_scatter":
-        return "hbm", 6 * N + 4 * 16 * N
+    if name in table:
+        return "hbm", table[name]
     return None, None
 
 
@@ -287,8 +294,9 @@ def main():
     sm_max = float(peaks.get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0)
     fp32_peak_tflops = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
     d = dict(nvox=int(mask.size), N=N, T=T, rows=(mask.shape[1] + 1) * (mask.shape[0] + 1),
+             words_per_row=(mask.shape[2] + 31) // 32,
              bitset_bytes=4 * ((mask.shape[2] + 31) // 32) * (mask.shape[1] + 3) * (mask.shape[0] + 3),
-             pairs_evaluated=statistics.mean(evaluated))
+             cubes=stats.get("cubes", T // 2), pairs_evaluated=statistics.mean(evaluated))
     kernels = {k: v for k, v in prof.items() if v["launches"] > 0}
     total_ms = sum(v["total_ms"] for v in kernels.values()) or 1.0
     dom = max(kernels, key=lambda k: kernels[k]["total_ms"])

@@ -137,6 +137,27 @@ void rad_mesh_free(rad_mesh_t* mesh);
  * n_triangles x 3 int32.  Synchronises `stream`. */
 rad_status rad_mesh_copy(const rad_mesh_t* mesh, int16_t* idx2, double* t, int32_t* tri, void* stream);
 
+/* ---- soft probability maps: forward and adjoint ------------------------------ */
+
+/* Forward pass on a device float32 probability map [nz][ny][nx] (iso level
+ * 0.5, linearly interpolated vertices; a 0/1 map gives the mask's mesh):
+ * out[0] = SurfaceArea, out[1] = MeshVolume, out[2] = Maximum3DDiameter
+ * (host doubles); argmax = the diameter's vertex pair (host).  Uses and
+ * keeps the buffers of *ws (NULL on first use).  Synchronises `stream`. */
+rad_status rad_soft_forward(const float* prob_dev, const int64_t dims[3], const double spacing[3], double out[3],
+                            int32_t argmax[2], rad_workspace_t** ws, void* stream);
+
+/* Adjoint: grad_dev (device, nx*ny*nz doubles, overwritten) receives the
+ * gradient of gout[0]*SurfaceArea + gout[1]*MeshVolume +
+ * gout[2]*Maximum3DDiameter with respect to every voxel value.  The mesh is
+ * recomputed from prob_dev (nothing of the forward pass is stored but the
+ * argmax pair it returned, passed back here).  Mesh topology, triangulation
+ * and the argmax pair are held fixed (the features are piecewise smooth).
+ * Voxels away from the iso-surface get 0.  Synchronises `stream`. */
+rad_status rad_soft_backward(const float* prob_dev, const int64_t dims[3], const double spacing[3],
+                             const double gout[3], const int32_t argmax[2], double* grad_dev, rad_workspace_t** ws,
+                             void* stream);
+
 /* ---- diameters without device allocation --------------------------------- */
 
 /* The paper has no counterpart of this entry point; it exists for callers

@@ -224,7 +224,7 @@ void DevBuf::release() {
   bytes = 0;
 }
 
-static rad_tuning_t g_tuning = {128, 128, 4, 4};
+static rad_tuning_t g_tuning = {128, 128, 8, 4};
 const rad_tuning_t& tuning() { return g_tuning; }
 
 // ---- per-mesh / per-workspace state --------------------------------------------------
@@ -244,6 +244,7 @@ struct Work {
   long long vcap = 0, tcap = 0;
   Result* host = nullptr;  // pinned copy
   DevBuf mask;     // device copy of a host mask (rad_extract_host)
+  DevBuf gvtx;     // per-vertex position gradients (soft adjoint)
   int device = -1;
   // CUDA graph of the whole rad_extract sequence, valid for one key
   cudaStream_t cap_stream = nullptr;
@@ -265,7 +266,7 @@ struct Work {
     ms.bits.release(); ms.counts.release(); ms.wpre.release(); ms.prefix.release(); ms.chunk.release();
     ms.cubes.release(); ms.hist.release(); ms.partial.release();
     ms.bintab.release(); ds.misc.release(); ds.plain_part.release(); result.release(); idx2.release();
-    vt.release(); tri.release(); mask.release();
+    vt.release(); tri.release(); mask.release(); gvtx.release();
     if (host) cudaFreeHost(host);
   }
   rad_status init() {
@@ -644,6 +645,61 @@ rad_status rad_extract_host(const uint8_t* mask_host, const int64_t dims[3], con
 }
 
 void rad_workspace_free(rad_workspace_t* ws) { delete ws; }
+
+static rad_workspace_t* ensure_ws(rad_workspace_t** ws) {
+  if (!*ws) {
+    *ws = new rad_workspace();
+    memset(&(*ws)->mesh, 0, sizeof(rad_mesh_t));
+  }
+  return *ws;
+}
+
+rad_status rad_soft_forward(const float* prob_dev, const int64_t dims[3], const double spacing[3], double out[3],
+                            int32_t argmax[2], rad_workspace_t** ws, void* stream) {
+  RAD_TRY(check_geometry(dims, spacing));
+  if (!out || !argmax || !ws) { set_error("out, argmax and ws must be non-NULL"); return RAD_ERR_INVALID_ARG; }
+  RAD_TRY(check_device_ptr(prob_dev, "prob_dev"));
+  rad_workspace_t* w = ensure_ws(ws);
+  cudaStream_t st = (cudaStream_t)stream;
+  RAD_TRY(run_mesh(prob_dev, true, dims, spacing, w->work, &w->mesh, st));
+  rad_features_t f;
+  RAD_TRY(run_shape(&w->mesh, w->work, false, &f, st));
+  out[0] = f.SurfaceArea;
+  out[1] = f.MeshVolume;
+  out[2] = f.Maximum3DDiameter;
+  argmax[0] = f.argmax3d[0];
+  argmax[1] = f.argmax3d[1];
+  return RAD_OK;
+}
+
+rad_status rad_soft_backward(const float* prob_dev, const int64_t dims[3], const double spacing[3],
+                             const double gout[3], const int32_t argmax[2], double* grad_dev, rad_workspace_t** ws,
+                             void* stream) {
+  RAD_TRY(check_geometry(dims, spacing));
+  if (!gout || !argmax || !ws) { set_error("gout, argmax and ws must be non-NULL"); return RAD_ERR_INVALID_ARG; }
+  RAD_TRY(check_device_ptr(prob_dev, "prob_dev"));
+  RAD_TRY(check_device_ptr(grad_dev, "grad_dev"));
+  rad_workspace_t* w = ensure_ws(ws);
+  Work& wk = w->work;
+  cudaStream_t st = (cudaStream_t)stream;
+  // recompute the mesh instead of keeping it from the forward pass
+  RAD_TRY(run_mesh(prob_dev, true, dims, spacing, wk, &w->mesh, st));
+  const long long nv = w->mesh.n_vertices;
+  if ((argmax[0] >= 0 || argmax[1] >= 0) &&
+      (argmax[0] < 0 || argmax[1] < 0 || argmax[0] >= nv || argmax[1] >= nv || argmax[0] == argmax[1])) {
+    set_error("argmax pair (%d, %d) is not a vertex pair of this map's mesh (%lld vertices)", argmax[0], argmax[1],
+              nv);
+    return RAD_ERR_INVALID_ARG;
+  }
+  RAD_TRY(wk.gvtx.reserve(sizeof(double) * 3 * std::max<long long>(wk.vcap, 1)));
+  const MeshDims d = make_dims(dims);
+  Result* dr = wk.dres();
+  RAD_TRY(soft_adjoint(wk.idx2.as<int16_t>(), wk.vt.as<double>(), wk.tri.as<int32_t>(), &dr->mt.nv, &dr->mt.nt,
+                       wk.vcap, wk.tcap, prob_dev, d, spacing, gout, argmax[0], argmax[1], wk.gvtx.as<double>(),
+                       grad_dev, st));
+  RAD_CUDA(cudaStreamSynchronize(st));
+  return RAD_OK;
+}
 
 rad_status rad_set_tuning(const rad_tuning_t* set, rad_tuning_t* get) {
   if (set) {

@@ -61,7 +61,7 @@ struct Cand {
 
 struct ProblemState {
   unsigned int F;  // float bits of the running FP32 maximum
-  unsigned int pad;
+  unsigned int T;  // float bits of T(F), raised with F
   unsigned long long best_d2;    // FP64 bits of the confirmed maximum
   unsigned long long best_pair;  // (i << 32) | j, smallest among the maxima
 };
@@ -78,6 +78,8 @@ struct Counters {
   int pad;
   unsigned long long items_evaluated, pairs_evaluated;
   long long n_work2;  // items re-evaluated for candidates
+  unsigned int done;  // last-block ticket of the tie-break kernel
+  unsigned int pad2;
 };
 
 struct Params {
@@ -164,9 +166,12 @@ __global__ void k_hist(const int16_t* __restrict__ idx2, const long long* __rest
   }
 }
 
+__device__ __forceinline__ long long key_offset(const long long* offs, const long long* parts, long long key);
+
 __global__ void k_scatter(const int16_t* __restrict__ idx2, const double* __restrict__ vt,
                           const long long* __restrict__ nv_dev, Params p, const long long* __restrict__ offs,
-                          int* __restrict__ cursor, float4* __restrict__ sorted) {
+                          const long long* __restrict__ parts, int* __restrict__ cursor,
+                          float4* __restrict__ sorted) {
   const long long n = min(*nv_dev, p.nv_cap);
   const int kinds = p.planes ? 4 : 1;
   const int lane = threadIdx.x & 31;
@@ -189,7 +194,7 @@ __global__ void k_scatter(const int16_t* __restrict__ idx2, const double* __rest
       int base = 0;
       if (key >= 0 && lane == leader) base = atomicAdd(&cursor[key], __popc(peers));
       base = __shfl_sync(0xffffffffu, base, leader);
-      if (key >= 0) sorted[offs[key] + base + __popc(peers & ((1u << lane) - 1u))] = e;
+      if (key >= 0) sorted[key_offset(offs, parts, key) + base + __popc(peers & ((1u << lane) - 1u))] = e;
     }
   }
 }
@@ -243,59 +248,78 @@ __global__ void k_xscan_top(long long* __restrict__ part, int nparts) {
   }
 }
 
-__global__ void k_xscan_add(long long* __restrict__ out, long long n, const long long* __restrict__ part) {
-  const long long i = blockIdx.x * (long long)kScanBlock + threadIdx.x;
-  if (i < n) out[i] += part[blockIdx.x];
+// Offset of a key: block-local exclusive prefix + the scanned block total.
+__device__ __forceinline__ long long key_offset(const long long* offs, const long long* parts, long long key) {
+  return offs[key] + parts[key / kScanBlock];
 }
 
 // ---- 2. problems and tiles --------------------------------------------------------
-
-// Problem 0 is the 3D range [0, N).  Every plane with >= 2 vertices becomes
-// a problem (appended in any order: the result does not depend on it).
-__global__ void k_problems(const long long* __restrict__ nv_dev, Params p, const long long* __restrict__ offs,
-                           Problem* __restrict__ probs, Counters* __restrict__ cnt) {
+// One block builds the problem list: problem 0 is the 3D range [0, N); every
+// plane with >= 2 vertices follows in plane order.  It then scans tile and
+// pair counts and resets the per-problem state (k_tiles writes the tiles).
+__global__ void __launch_bounds__(1024) k_setup_problems(const long long* __restrict__ nv_dev, Params p,
+                                                         const long long* __restrict__ offs,
+                                                         const long long* __restrict__ parts,
+                                                         Problem* __restrict__ probs, Tile* __restrict__ tiles,
+                                                         ProblemState* __restrict__ ps, Counters* __restrict__ cnt) {
+  __shared__ long long s_a[32], s_b[32];
+  __shared__ long long s_np;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const long long n = min(*nv_dev, p.nv_cap);
-  const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (gid == 0) {
+  const long long nz2 = 2LL * p.nz + 1, ny2 = 2LL * p.ny + 1, nx2 = 2LL * p.nx + 1;
+  const long long n_planes = p.planes ? nz2 + ny2 + nx2 : 0;
+  if (threadIdx.x == 0) {
     Problem q;
     q.axis = -1; q.beg = 0; q.len = (int)n; q.tile_beg = 0; q.pair_beg = 0;
     probs[0] = q;
+    s_np = 1;
   }
-  if (!p.planes) return;
-  const long long nz2 = 2LL * p.nz + 1, ny2 = 2LL * p.ny + 1, nx2 = 2LL * p.nx + 1;
-  const long long nplanes = nz2 + ny2 + nx2;
-  for (long long k = gid; k < nplanes; k += (long long)gridDim.x * blockDim.x) {
-    int axis;
-    long long k0, k1;
-    if (k < nz2) {
-      axis = 2;
-      k0 = p.S0 + k * p.PX * p.PY;
-      k1 = k0 + (long long)p.PX * p.PY;
-    } else if (k < nz2 + ny2) {
-      axis = 1;
-      k0 = p.S1 + (k - nz2) * p.PX * p.PZ;
-      k1 = k0 + (long long)p.PX * p.PZ;
-    } else {
-      axis = 0;
-      k0 = p.S2 + (k - nz2 - ny2) * p.PY * p.PZ;
-      k1 = k0 + (long long)p.PY * p.PZ;
+  __syncthreads();
+  // planes with >= 2 vertices, compacted in plane order
+  for (long long base = 0; base < n_planes; base += blockDim.x) {
+    const long long k = base + threadIdx.x;
+    int axis = 0;
+    long long beg = 0, len = 0;
+    if (k < n_planes) {
+      long long k0, k1;
+      if (k < nz2) {
+        axis = 2; k0 = p.S0 + k * p.PX * p.PY; k1 = k0 + (long long)p.PX * p.PY;
+      } else if (k < nz2 + ny2) {
+        axis = 1; k0 = p.S1 + (k - nz2) * p.PX * p.PZ; k1 = k0 + (long long)p.PX * p.PZ;
+      } else {
+        axis = 0; k0 = p.S2 + (k - nz2 - ny2) * p.PY * p.PZ; k1 = k0 + (long long)p.PY * p.PZ;
+      }
+      beg = key_offset(offs, parts, k0);
+      len = key_offset(offs, parts, k1) - beg;
     }
-    const long long beg = offs[k0], len = offs[k1] - beg;
-    if (len < 2) continue;
-    const int slot = 1 + atomicAdd(&cnt->n_problems, 1);
-    if (slot >= p.max_problems) { atomicOr(&cnt->status, DEV_ERR_PROBCAP); continue; }
-    Problem q;
-    q.axis = axis; q.beg = (int)beg; q.len = (int)len; q.tile_beg = 0; q.pair_beg = 0;
-    probs[slot] = q;
+    const int keep = len >= 2 ? 1 : 0;
+    int inc = keep;
+    for (int off = 1; off < 32; off <<= 1) {
+      const int o = __shfl_up_sync(0xffffffffu, inc, off);
+      if (lane >= off) inc += o;
+    }
+    if (lane == 31) s_a[wid] = inc;
+    __syncthreads();
+    long long wb = 0, tot = 0;
+    for (int w = 0; w < nw; ++w) {
+      if (w < wid) wb += s_a[w];
+      tot += s_a[w];
+    }
+    if (keep) {
+      const long long slot = s_np + wb + inc - 1;
+      if (slot < p.max_problems) {
+        Problem q;
+        q.axis = axis; q.beg = (int)beg; q.len = (int)len; q.tile_beg = 0; q.pair_beg = 0;
+        probs[slot] = q;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) s_np += tot;
+    __syncthreads();
   }
-}
-
-// One block: tile and pair prefixes over problems.
-__global__ void k_problem_scan(Problem* __restrict__ probs, Params p, Counters* __restrict__ cnt) {
-  __shared__ long long st[32], sp2[32];
-  const int np = 1 + min(cnt->n_problems, (int)p.max_problems - 1);
+  const int np = (int)min(s_np, p.max_problems);
+  // tile and pair prefixes over problems; per-problem state reset
   long long carry_t = 0, carry_p = 0;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int base = 0; base < np; base += blockDim.x) {
     const int i = base + threadIdx.x;
     long long nt = 0, npairs = 0;
@@ -305,19 +329,22 @@ __global__ void k_problem_scan(Problem* __restrict__ probs, Params p, Counters* 
     }
     long long it = nt, ip = npairs;
     for (int off = 1; off < 32; off <<= 1) {
-      const long long a = __shfl_up_sync(0xffffffffu, it, off), b = __shfl_up_sync(0xffffffffu, ip, off);
-      if (lane >= off) { it += a; ip += b; }
+      const long long a2 = __shfl_up_sync(0xffffffffu, it, off), b2 = __shfl_up_sync(0xffffffffu, ip, off);
+      if (lane >= off) { it += a2; ip += b2; }
     }
-    if (lane == 31) { st[wid] = it; sp2[wid] = ip; }
+    if (lane == 31) { s_a[wid] = it; s_b[wid] = ip; }
     __syncthreads();
     long long wt = 0, wp = 0, bt = 0, bp = 0;
-    for (int k = 0; k < nw; ++k) {
-      if (k < wid) { wt += st[k]; wp += sp2[k]; }
-      bt += st[k]; bp += sp2[k];
+    for (int w = 0; w < nw; ++w) {
+      if (w < wid) { wt += s_a[w]; wp += s_b[w]; }
+      bt += s_a[w]; bp += s_b[w];
     }
     if (i < np) {
       probs[i].tile_beg = (int)(carry_t + wt + it - nt);
       probs[i].pair_beg = carry_p + wp + ip - npairs;
+      ProblemState z;
+      z.F = 0u; z.T = 0u; z.best_d2 = 0ull; z.best_pair = ~0ull;
+      ps[i] = z;
     }
     carry_t += bt;
     carry_p += bp;
@@ -327,7 +354,7 @@ __global__ void k_problem_scan(Problem* __restrict__ probs, Params p, Counters* 
     cnt->n_problems = np;
     cnt->n_tiles = (int)min(carry_t, p.max_tiles);
     cnt->n_pairs = carry_p;
-    if (carry_t > p.max_tiles) atomicOr(&cnt->status, DEV_ERR_PROBCAP);
+    if (carry_t > p.max_tiles || s_np > p.max_problems) atomicOr(&cnt->status, DEV_ERR_PROBCAP);
   }
 }
 
@@ -355,7 +382,7 @@ __global__ void k_tiles(const Problem* __restrict__ probs, Params p, const Count
 
 // One warp per tile: bounding box of its FP32 positions.
 __global__ void k_tile_box(const float4* __restrict__ sorted, const Tile* __restrict__ tiles,
-                           const Counters* __restrict__ cnt, float4* __restrict__ box) {
+                           const Counters* __restrict__ cnt, float4* __restrict__ box, float4* __restrict__ rep) {
   const int nt = cnt->n_tiles;
   const int lane = threadIdx.x & 31;
   const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
@@ -376,6 +403,7 @@ __global__ void k_tile_box(const float4* __restrict__ sorted, const Tile* __rest
     if (lane == 0) {
       box[2 * ti] = make_float4(lo[0], lo[1], lo[2], 0.f);
       box[2 * ti + 1] = make_float4(hi[0], hi[1], hi[2], 0.f);
+      rep[ti] = sorted[tl.beg];
     }
   }
 }
@@ -383,19 +411,37 @@ __global__ void k_tile_box(const float4* __restrict__ sorted, const Tile* __rest
 // Seed: one warp per tile row a.  The pairs of tile representatives (first
 // vertex of each tile) of one problem, plus each tile's first-last pair, are
 // actual vertex pairs, so their largest f is a valid starting F.
-__global__ void k_seed_rows(const float4* __restrict__ sorted, const Tile* __restrict__ tiles,
-                            const Counters* __restrict__ cnt, ProblemState* __restrict__ ps) {
+__global__ void k_seed_rows(const float4* __restrict__ sorted, const float4* __restrict__ rep, Params p,
+                            const Tile* __restrict__ tiles, Counters* __restrict__ cnt,
+                            ProblemState* __restrict__ ps) {
   const int nt = cnt->n_tiles;
   const int lane = threadIdx.x & 31;
   const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   for (long long a = warp; a < nt; a += nwarps) {
     const Tile ta = tiles[a];
-    const float4 ra = sorted[ta.beg];
+    const float4 ra = rep[a];
     float best = lane == 0 ? pair_f(ra, sorted[ta.beg + ta.len - 1]) : 0.0f;
-    for (long long b = a + 1 + lane; b < ta.tile_end; b += 32) best = fmaxf(best, pair_f(ra, sorted[tiles[b].beg]));
+    for (long long b = a + 1 + lane; b < ta.tile_end; b += 32) best = fmaxf(best, pair_f(ra, rep[b]));
     for (int off = 16; off > 0; off >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, off));
     if (lane == 0 && best > 0.0f) atomicMax(&ps[ta.problem].F, __float_as_uint(best));
+  }
+  // the last block turns every seeded F into its threshold T(F) (FP64 math
+  // once per problem instead of once per tile row)
+  __shared__ bool last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(&cnt->done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    const int np = cnt->n_problems;
+    for (int i = threadIdx.x; i < np; i += blockDim.x)
+      ps[i].T = __float_as_uint(threshold(__uint_as_float(__ldcg(&ps[i].F)), p));
+    __syncthreads();
+    if (threadIdx.x == 0) cnt->done = 0;
   }
 }
 
@@ -403,15 +449,14 @@ __global__ void k_seed_rows(const float4* __restrict__ sorted, const Tile* __res
 // One warp per tile row a: every tile pair (a, b >= a) of the same problem
 // whose box bound reaches T(F) goes to the work list.
 __global__ void k_cull_rows(const Tile* __restrict__ tiles, const float4* __restrict__ box, Params p,
-                            Counters* __restrict__ cnt, const ProblemState* __restrict__ ps,
-                            WorkItem* __restrict__ work) {
+                            Counters* __restrict__ cnt, ProblemState* __restrict__ ps, WorkItem* __restrict__ work) {
   const int nt = cnt->n_tiles;
   const int lane = threadIdx.x & 31;
   const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   for (long long a = warp; a < nt; a += nwarps) {
     const Tile ta = tiles[a];
-    const float T = threshold(__uint_as_float(ps[ta.problem].F), p);
+    const float T = __uint_as_float(ps[ta.problem].T);
     const float4 alo = box[2 * a], ahi = box[2 * a + 1];
     for (long long b0 = a; b0 < ta.tile_end; b0 += 32) {
       const long long b = b0 + lane;
@@ -446,7 +491,7 @@ __global__ void k_compact_items(const WorkItem* __restrict__ work, const float* 
   for (long long i0 = blockIdx.x * (long long)blockDim.x; i0 < nwork; i0 += (long long)gridDim.x * blockDim.x) {
     const long long i = i0 + threadIdx.x;
     bool keep = false;
-    if (i < nwork) keep = itemmax[i] >= threshold(__uint_as_float(ps[work[i].problem].F), p);
+    if (i < nwork) keep = itemmax[i] >= __uint_as_float(ps[work[i].problem].T);
     const unsigned int m = __ballot_sync(0xffffffffu, keep);
     if (!m) continue;
     long long base = 0;
@@ -521,19 +566,16 @@ __global__ void __launch_bounds__(NT) k_pairs_max(const float4* __restrict__ sor
                                                   float* __restrict__ itemmax) {
   __shared__ float4 sB[TS];
   __shared__ float sred[NT / 32];
-  __shared__ long long s_item;
   const long long nwork = min(cnt->n_work, p.work_cap);
-  for (;;) {
-    if (threadIdx.x == 0) s_item = atomicAdd(&cnt->ticket, 1);
-    __syncthreads();
-    const long long it = s_item;
-    if (it >= nwork) break;
+  unsigned long long n_items = 0, n_pairs = 0;
+  for (long long it = blockIdx.x; it < nwork; it += gridDim.x) {
     const WorkItem w = work[it];
-    const float T = threshold(__uint_as_float(*(volatile unsigned int*)&ps[w.problem].F), p);
+    // re-cull against the problem's current threshold (raised by other CTAs);
+    // threads may read different values, so the decision is block-wide
+    const float T = __uint_as_float(*(volatile unsigned int*)&ps[w.problem].T);
     const float ub = box_ub(box[2 * w.ta], box[2 * w.ta + 1], box[2 * w.tb], box[2 * w.tb + 1]);
-    if (ub < T) {
+    if (__syncthreads_and(ub < T)) {
       if (threadIdx.x == 0) itemmax[it] = -1.0f;
-      __syncthreads();
       continue;
     }
     const Tile A = tiles[w.ta], B = tiles[w.tb];
@@ -545,11 +587,16 @@ __global__ void __launch_bounds__(NT) k_pairs_max(const float4* __restrict__ sor
       float bm = sred[0];
       for (int k = 1; k < NT / 32; ++k) bm = fmaxf(bm, sred[k]);
       itemmax[it] = bm;
-      atomicMax(&ps[w.problem].F, __float_as_uint(bm));
-      atomicAdd(&cnt->items_evaluated, 1ull);
-      atomicAdd(&cnt->pairs_evaluated, (unsigned long long)A.len * (unsigned long long)B.len);
+      const unsigned int old = atomicMax(&ps[w.problem].F, __float_as_uint(bm));
+      if (__float_as_uint(bm) > old) atomicMax(&ps[w.problem].T, __float_as_uint(threshold(bm, p)));
+      n_items++;
+      n_pairs += (unsigned long long)A.len * (unsigned long long)B.len;
     }
     __syncthreads();
+  }
+  if (threadIdx.x == 0 && n_items) {
+    atomicAdd(&cnt->items_evaluated, n_items);
+    atomicAdd(&cnt->pairs_evaluated, n_pairs);
   }
 }
 
@@ -562,7 +609,7 @@ __global__ void __launch_bounds__(NT) k_pairs_cand(const float4* __restrict__ so
   const long long n2 = cnt->n_work2;
   for (long long k = blockIdx.x; k < n2; k += gridDim.x) {
     const WorkItem w = work[work2[k]];
-    const float T = threshold(__uint_as_float(ps[w.problem].F), p);
+    const float T = __uint_as_float(ps[w.problem].T);
     const Tile A = tiles[w.ta], B = tiles[w.tb];
     eval_pair_tile<TS, NT, true>(sorted, A, B, sB, T, w.problem, cand, cnt, p.cand_cap);
     __syncthreads();
@@ -586,24 +633,6 @@ __global__ void k_confirm(const float4* __restrict__ sorted, const int16_t* __re
   }
 }
 
-__global__ void k_tiebreak(const float4* __restrict__ sorted, const int16_t* __restrict__ idx2,
-                           const double* __restrict__ vt, Params p, const Counters* __restrict__ cnt,
-                           const Cand* __restrict__ cand, ProblemState* __restrict__ ps) {
-  const long long nc = min(cnt->n_cand, p.cand_cap);
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nc; c += (long long)gridDim.x * blockDim.x) {
-    const Cand k = cand[c];
-    int i = __float_as_int(sorted[k.ea].w), j = __float_as_int(sorted[k.eb].w);
-    double ui[3], uj[3];
-    vertex_u(idx2, vt, i, ui);
-    vertex_u(idx2, vt, j, uj);
-    const double d2 = pin_d2(ui[0], ui[1], ui[2], uj[0], uj[1], uj[2], p.sx, p.sy, p.sz);
-    if ((unsigned long long)__double_as_longlong(d2) == ps[k.problem].best_d2) {
-      if (i > j) { const int t = i; i = j; j = t; }
-      atomicMin(&ps[k.problem].best_pair, ((unsigned long long)(unsigned int)i << 32) | (unsigned int)j);
-    }
-  }
-}
-
 struct BestD {
   double d2;
   int i, j;
@@ -617,10 +646,11 @@ __device__ __forceinline__ bool better(double d2, int i, int j, const BestD& b) 
   return j < b.j;
 }
 
-// One block: per category, the best problem result (max d2, smallest pair).
-__global__ void k_finalize(const Problem* __restrict__ probs, const Counters* __restrict__ cnt,
-                           const ProblemState* __restrict__ ps, DiamResult* __restrict__ out,
-                           unsigned int* __restrict__ status) {
+// Per category (3D, Slice, Column, Row), the best problem result: max d2,
+// then the smallest pair.  Run by one block.
+__device__ void finalize_block(const Problem* __restrict__ probs, const Counters* __restrict__ cnt,
+                               const ProblemState* __restrict__ ps, DiamResult* __restrict__ out,
+                               unsigned int* __restrict__ status) {
   __shared__ BestD s[4][32];
   const int np = cnt->n_problems;
   BestD b[4];
@@ -628,9 +658,9 @@ __global__ void k_finalize(const Problem* __restrict__ probs, const Counters* __
   for (int i = threadIdx.x; i < np; i += blockDim.x) {
     const Problem pr = probs[i];
     const int q = pr.axis < 0 ? 0 : (pr.axis == 2 ? 1 : (pr.axis == 1 ? 2 : 3));
-    const unsigned long long bp = ps[i].best_pair;
+    const unsigned long long bp = __ldcg(&ps[i].best_pair);
     if (bp == ~0ull) continue;
-    const double d2 = __longlong_as_double((long long)ps[i].best_d2);
+    const double d2 = __longlong_as_double((long long)__ldcg(&ps[i].best_d2));
     const int bi = (int)(bp >> 32), bj = (int)(bp & 0xffffffffu);
     if (better(d2, bi, bj, b[q])) { b[q].d2 = d2; b[q].i = bi; b[q].j = bj; }
   }
@@ -666,14 +696,36 @@ __global__ void k_finalize(const Problem* __restrict__ probs, const Counters* __
   }
 }
 
-__global__ void k_init_states(ProblemState* __restrict__ ps, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    ProblemState s;
-    s.F = 0u;
-    s.pad = 0u;
-    s.best_d2 = 0ull;
-    s.best_pair = ~0ull;
-    ps[i] = s;
+// Candidates attaining their problem's maximum take the smallest (i, j); the
+// last block to finish writes the per-category results.
+__global__ void k_tiebreak(const float4* __restrict__ sorted, const int16_t* __restrict__ idx2,
+                           const double* __restrict__ vt, Params p, Counters* __restrict__ cnt,
+                           const Cand* __restrict__ cand, ProblemState* __restrict__ ps,
+                           const Problem* __restrict__ probs, DiamResult* __restrict__ out,
+                           unsigned int* __restrict__ status) {
+  const long long nc = min(cnt->n_cand, p.cand_cap);
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nc; c += (long long)gridDim.x * blockDim.x) {
+    const Cand k = cand[c];
+    int i = __float_as_int(sorted[k.ea].w), j = __float_as_int(sorted[k.eb].w);
+    double ui[3], uj[3];
+    vertex_u(idx2, vt, i, ui);
+    vertex_u(idx2, vt, j, uj);
+    const double d2 = pin_d2(ui[0], ui[1], ui[2], uj[0], uj[1], uj[2], p.sx, p.sy, p.sz);
+    if ((unsigned long long)__double_as_longlong(d2) == __ldcg(&ps[k.problem].best_d2)) {
+      if (i > j) { const int t = i; i = j; j = t; }
+      atomicMin(&ps[k.problem].best_pair, ((unsigned long long)(unsigned int)i << 32) | (unsigned int)j);
+    }
+  }
+  __shared__ bool last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(&cnt->done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    finalize_block(probs, cnt, ps, out, status);
   }
 }
 
@@ -711,7 +763,7 @@ rad_status diam_run(const int16_t* idx2, const double* vt, long long nv_hint, co
   p.CX = ((2 * d.nx) >> p.cell_shift) + 1;
   p.CY = ((2 * d.ny) >> p.cell_shift) + 1;
   p.CZ = ((2 * d.nz) >> p.cell_shift) + 1;
-  p.plane_shift = tu.cell_shift + 1;
+  p.plane_shift = tu.cell_shift + 2;
   p.PX = ((2 * d.nx) >> p.plane_shift) + 1;
   p.PY = ((2 * d.ny) >> p.plane_shift) + 1;
   p.PZ = ((2 * d.nz) >> p.plane_shift) + 1;
@@ -757,6 +809,7 @@ rad_status diam_run(const int16_t* idx2, const double* vt, long long nv_hint, co
   add(sizeof(Problem) * p.max_problems);
   add(sizeof(Tile) * p.max_tiles);
   add(sizeof(float4) * 2 * p.max_tiles);
+  add(sizeof(float4) * p.max_tiles);
   add(sizeof(ProblemState) * p.max_problems);
   add(sizeof(Counters));
   add(sizeof(WorkItem) * p.work_cap);
@@ -773,6 +826,7 @@ rad_status diam_run(const int16_t* idx2, const double* vt, long long nv_hint, co
   Problem* probs = carve<Problem>(cur, p.max_problems);
   Tile* tiles = carve<Tile>(cur, p.max_tiles);
   float4* box = carve<float4>(cur, 2 * p.max_tiles);
+  float4* rep = carve<float4>(cur, p.max_tiles);
   ProblemState* ps = carve<ProblemState>(cur, p.max_problems);
   Counters* cnt = carve<Counters>(cur, 1);
   WorkItem* work = carve<WorkItem>(cur, p.work_cap);
@@ -784,21 +838,15 @@ rad_status diam_run(const int16_t* idx2, const double* vt, long long nv_hint, co
   RAD_CUDA(cudaMemsetAsync(hist, 0, sizeof(int) * K1, st));
   RAD_CUDA(cudaMemsetAsync(cursor, 0, sizeof(int) * K1, st));
   RAD_CUDA(cudaMemsetAsync(cnt, 0, sizeof(Counters), st));
-  RAD_LAUNCH("diam_init", k_init_states, std::min<long long>((p.max_problems + 255) / 256, sms * 4), 256, 0, st, ps,
-             p.max_problems);
   const int vblocks = (int)std::min<long long>((nv + 255) / 256, (long long)sms * 8);
   RAD_LAUNCH("diam_hist", k_hist, vblocks, 256, 0, st, idx2, nv_dev, p, hist);
   RAD_LAUNCH("diam_scan_part", k_xscan_part, (int)nparts, kScanBlock, 0, st, hist, K1, offs, parts);
   RAD_LAUNCH("diam_scan_top", k_xscan_top, 1, 1024, 0, st, parts, (int)nparts);
-  RAD_LAUNCH("diam_scan_add", k_xscan_add, (int)nparts, kScanBlock, 0, st, offs, K1, parts);
-  RAD_LAUNCH("diam_scatter", k_scatter, vblocks, 256, 0, st, idx2, vt, nv_dev, p, offs, cursor, sorted);
-  const long long nplanes = p.planes ? (2LL * d.nx + 1) + (2LL * d.ny + 1) + (2LL * d.nz + 1) : 1;
-  RAD_LAUNCH("diam_problems", k_problems, (int)std::max<long long>(1, std::min<long long>((nplanes + 255) / 256, sms * 4)),
-             256, 0, st, nv_dev, p, offs, probs, cnt);
-  RAD_LAUNCH("diam_problem_scan", k_problem_scan, 1, 1024, 0, st, probs, p, cnt);
+  RAD_LAUNCH("diam_scatter", k_scatter, vblocks, 256, 0, st, idx2, vt, nv_dev, p, offs, parts, cursor, sorted);
+  RAD_LAUNCH("diam_setup", k_setup_problems, 1, 1024, 0, st, nv_dev, p, offs, parts, probs, tiles, ps, cnt);
   RAD_LAUNCH("diam_tiles", k_tiles, sms * 4, 256, 0, st, probs, p, cnt, tiles);
-  RAD_LAUNCH("diam_tile_box", k_tile_box, sms * 8, 256, 0, st, sorted, tiles, cnt, box);
-  RAD_LAUNCH("diam_seed", k_seed_rows, sms * 8, 256, 0, st, sorted, tiles, cnt, ps);
+  RAD_LAUNCH("diam_tile_box", k_tile_box, sms * 8, 256, 0, st, sorted, tiles, cnt, box, rep);
+  RAD_LAUNCH("diam_seed", k_seed_rows, sms * 8, 256, 0, st, sorted, rep, p, tiles, cnt, ps);
   RAD_LAUNCH("diam_cull", k_cull_rows, sms * 8, 256, 0, st, tiles, box, p, cnt, ps, work);
   const int ctas = sms * tu.ctas_per_sm;
   if (tu.tile == 64) {
@@ -813,8 +861,8 @@ rad_status diam_run(const int16_t* idx2, const double* vt, long long nv_hint, co
     else RAD_TRY((launch_pairs<256, 256>(sorted, tiles, box, work, work2, p, cnt, ps, itemmax, cand, ctas, st)));
   }
   RAD_LAUNCH("diam_confirm", k_confirm, sms * 4, 256, 0, st, sorted, idx2, vt, p, cnt, cand, ps);
-  RAD_LAUNCH("diam_tiebreak", k_tiebreak, sms * 4, 256, 0, st, sorted, idx2, vt, p, cnt, cand, ps);
-  RAD_LAUNCH("diam_finalize", k_finalize, 1, 1024, 0, st, probs, cnt, ps, out_dev, status_dev);
+  RAD_LAUNCH("diam_tiebreak", k_tiebreak, sms * 4, 256, 0, st, sorted, idx2, vt, p, cnt, cand, ps, probs, out_dev,
+             status_dev);
   return RAD_OK;
 }
 

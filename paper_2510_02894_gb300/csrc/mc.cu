@@ -35,7 +35,7 @@ namespace rad {
 namespace {
 
 constexpr int kScanChunk = 2048;  // rows per scan chunk (256 threads x 8)
-constexpr int kCubeBlocksPerSM = 8;
+constexpr int kCubeBlocksPerSM = 2;
 
 // Per-case data of a binary mask for one spacing (built by k_binary_table).
 struct BinCase {
@@ -175,8 +175,9 @@ __global__ void k_count(const uint32_t* __restrict__ bits, MeshDims d, int L, in
   for (long long base = warp * gpw; base < d.R; base += nwarps * gpw) {
     const long long item = base + lane / L;
     const bool valid = item < d.R;
-    const int y = valid ? (int)(item % (d.ny + 1)) - 1 : -1;
-    const int z = valid ? (int)(item / (d.ny + 1)) - 1 : -1;
+    const int item32 = valid ? (int)item : 0;  // R < 2^31 (dims <= 16383)
+    const int y = valid ? item32 % (d.ny + 1) - 1 : -1;
+    const int z = valid ? item32 / (d.ny + 1) - 1 : -1;
     const uint32_t* R00 = brow(bits, d, y, z);
     const uint32_t* R10 = brow(bits, d, y + 1, z);
     const uint32_t* R01 = brow(bits, d, y, z + 1);
@@ -404,7 +405,8 @@ __device__ __forceinline__ double crossing_t(double v0, double v1) {
 
 template <bool SOFT>
 __global__ void k_rows(const uint32_t* __restrict__ bits, const float* __restrict__ prob, MeshDims d, int L,
-                       const int* __restrict__ wpre, const long long* __restrict__ prefix,
+                       const int4* __restrict__ counts, const int* __restrict__ wpre,
+                       const long long* __restrict__ prefix,
                        const long long* __restrict__ chunk, int16_t* __restrict__ idx2, double* __restrict__ vt,
                        int4* __restrict__ cubes, long long vcap, long long ccap, MeshTotals* __restrict__ tot) {
   const int lane = threadIdx.x & 31, sub = lane % L, gpw = 32 / L;
@@ -415,8 +417,13 @@ __global__ void k_rows(const uint32_t* __restrict__ bits, const float* __restric
   for (long long base = warp * gpw; base < d.R; base += nwarps * gpw) {
     const long long item = base + lane / L;
     const bool valid = item < d.R;
-    const int y = valid ? (int)(item % (d.ny + 1)) - 1 : -1;
-    const int z = valid ? (int)(item / (d.ny + 1)) - 1 : -1;
+    const int item32 = valid ? (int)item : 0;  // R < 2^31 (dims <= 16383)
+    const int y = valid ? item32 % (d.ny + 1) - 1 : -1;
+    const int z = valid ? item32 / (d.ny + 1) - 1 : -1;
+    // rows without vertices and active cubes have nothing to write; skip
+    // them when the whole warp agrees (the group scans below are warp-wide)
+    const int4 rc = valid ? counts[item] : make_int4(0, 0, 0, 0);
+    if (__all_sync(0xffffffffu, rc.x == 0 && rc.w == 0)) continue;
     const uint32_t* R00 = brow(bits, d, y, z);
     const uint32_t* R10 = brow(bits, d, y + 1, z);
     const uint32_t* R01 = brow(bits, d, y, z + 1);
@@ -495,23 +502,54 @@ __global__ void k_rows(const uint32_t* __restrict__ bits, const float* __restric
 
 // ---- cubes: triangles, volume, area -------------------------------------------------------
 
-// Vertex id of the crossing edge (owner (xo, yo, zo), axis a).
-__device__ __forceinline__ long long vertex_id(const uint32_t* bits, const MeshDims& d, const int* wpre,
-                                               const long long* prefix, const long long* chunk, int xo, int yo,
-                                               int zo, int a) {
-  const long long r = (long long)(zo + 1) * (d.ny + 1) + (yo + 1);
-  const long long base = row_base(prefix, chunk, r, 0);
-  if (xo < 0) return base;  // the row's first vertex (x-edge into voxel 0)
-  const int w = xo >> 5, bit = xo & 31;
+// Crossing-edge info of one owner row at one word: crossing bits and the
+// row-local vertex prefix of the word, plus the row's first vertex id.
+struct OwnerWord {
+  long long base;
+  int pre;
+  uint32_t ex, ey;
+  uint32_t ez;
+};
+
+__device__ __forceinline__ OwnerWord owner_word(const uint32_t* bits, const MeshDims& d, const int* wpre,
+                                                const long long* prefix, const long long* chunk, int xo, int yo,
+                                                int zo) {
+  OwnerWord o;
+  const int r = (zo + 1) * (d.ny + 1) + (yo + 1);
+  o.base = row_base(prefix, chunk, r, 0);
+  if (xo < 0) {
+    o.pre = 0; o.ex = o.ey = o.ez = 0u;
+    return o;
+  }
+  const int w = xo >> 5;
   const uint32_t* R0 = brow(bits, d, yo, zo);
   const uint32_t b = R0[w], bn = ldw(R0, w + 1, d.W);
-  const uint32_t by = brow(bits, d, yo + 1, zo)[w], bz = brow(bits, d, yo, zo + 1)[w];
-  const uint32_t ex = b ^ shift1(b, bn), ey = b ^ by, ez = b ^ bz;
+  o.ex = b ^ shift1(b, bn);
+  o.ey = b ^ brow(bits, d, yo + 1, zo)[w];
+  o.ez = b ^ brow(bits, d, yo, zo + 1)[w];
+  o.pre = wpre[(long long)r * d.W + w];
+  return o;
+}
+
+__device__ __forceinline__ int owner_rank(const OwnerWord& o, int xo, int a) {
+  if (xo < 0) return 0;  // the x-edge into voxel 0 is the row's first vertex
+  const int bit = xo & 31;
   const uint32_t low = (1u << bit) - 1u;
-  long long rank = wpre[r * d.W + w] + __popc(ex & low) + __popc(ey & low) + __popc(ez & low);
-  if (a >= 1) rank += (ex >> bit) & 1u;
-  if (a >= 2) rank += (ey >> bit) & 1u;
-  return base + rank;
+  int r = o.pre + __popc(o.ex & low) + __popc(o.ey & low) + __popc(o.ez & low);
+  if (a >= 1) r += (o.ex >> bit) & 1u;
+  if (a >= 2) r += (o.ey >> bit) & 1u;
+  return r;
+}
+
+// Local edge e = (corner, axis) in canonical (cz, cy, cx, axis) order.
+__device__ __forceinline__ int edge_corner(int e) {
+  return e < 3 ? 0 : (e < 5 ? 1 : (e < 7 ? 2 : (e < 8 ? 3 : (e < 10 ? 4 : (e < 11 ? 5 : 6)))));
+}
+__device__ __forceinline__ int edge_axis(int e) {
+  constexpr unsigned long long kAxes = 0ull | (0ull << 0) | (1ull << 2) | (2ull << 4) | (1ull << 6) | (2ull << 8) |
+                                      (0ull << 10) | (2ull << 12) | (2ull << 14) | (0ull << 16) | (1ull << 18) |
+                                      (1ull << 20) | (0ull << 22);
+  return (int)((kAxes >> (2 * e)) & 3ull);
 }
 
 constexpr int kCubeThreads = 256;
@@ -540,16 +578,26 @@ __global__ void __launch_bounds__(kCubeThreads) k_cubes(const uint32_t* __restri
        k += (long long)gridDim.x * blockDim.x) {
     const int4 cu = cubes[k];
     const int x = cu.x, cs = cu.z;
-    const long long item = cu.y;
-    const int y = (int)(item % (d.ny + 1)) - 1, z = (int)(item / (d.ny + 1)) - 1;
+    const int y = cu.y % (d.ny + 1) - 1, z = cu.y / (d.ny + 1) - 1;
     const unsigned int emask = MC_CASE_EDGES[cs];
+    // owner rows (cy, cz) at the word of x (cx = 0) or of x + 1 (cx = 1),
+    // each loaded once per cube
+    OwnerWord ow[8];
+    unsigned int have = 0;
     int vid[12];
     double P[12][3], wl[12][3];
+#pragma unroll
     for (int e = 0; e < 12; ++e) {
       if (!((emask >> e) & 1u)) continue;
-      const int c = MC_EDGE_CORNER[e], a = MC_EDGE_AXIS[e];
-      const int g[3] = {x + (c & 1), y + ((c >> 1) & 1), z + ((c >> 2) & 1)};
-      vid[e] = (int)vertex_id(bits, d, wpre, prefix, chunk, g[0], g[1], g[2], a);
+      const int c = edge_corner(e), a = edge_axis(e);
+      const int cx = c & 1, cy = (c >> 1) & 1, cz = (c >> 2) & 1;
+      const int slot = cz * 4 + cy * 2 + cx;
+      const int g[3] = {x + cx, y + cy, z + cz};
+      if (!((have >> slot) & 1u)) {
+        ow[slot] = owner_word(bits, d, wpre, prefix, chunk, g[0], g[1], g[2]);
+        have |= 1u << slot;
+      }
+      vid[e] = (int)(ow[slot].base + owner_rank(ow[slot], g[0], a));
       if (SOFT) {
         const double v0 = (double)value_at(prob, d, g[0], g[1], g[2]);
         const double v1 = (double)value_at(prob, d, g[0] + (a == 0), g[1] + (a == 1), g[2] + (a == 2));
@@ -734,7 +782,7 @@ rad_status mesh_emit(const void* data, bool soft, const MeshDims& d, const doubl
   const int cblocks = sms * kCubeBlocksPerSM;
   if (soft) {
     RAD_LAUNCH("mc_rows_soft", k_rows<true>, rblocks, 256, 0, st, s.bits.as<uint32_t>(), (const float*)data, d, L,
-               s.wpre.as<int>(), s.prefix.as<long long>(), s.chunk.as<long long>(), idx2, vt, s.cubes.as<int4>(),
+               s.counts.as<int4>(), s.wpre.as<int>(), s.prefix.as<long long>(), s.chunk.as<long long>(), idx2, vt, s.cubes.as<int4>(),
                vcap, ccap, tot);
     RAD_LAUNCH("mc_cubes_soft", k_cubes<true>, cblocks, kCubeThreads, 0, st, s.bits.as<uint32_t>(),
                (const float*)data, d, sp[0], sp[1], sp[2], s.wpre.as<int>(), s.prefix.as<long long>(),
@@ -742,7 +790,7 @@ rad_status mesh_emit(const void* data, bool soft, const MeshDims& d, const doubl
                s.hist.as<unsigned long long>(), s.partial.as<double>());
   } else {
     RAD_LAUNCH("mc_rows", k_rows<false>, rblocks, 256, 0, st, s.bits.as<uint32_t>(), (const float*)nullptr, d, L,
-               s.wpre.as<int>(), s.prefix.as<long long>(), s.chunk.as<long long>(), idx2, (double*)nullptr,
+               s.counts.as<int4>(), s.wpre.as<int>(), s.prefix.as<long long>(), s.chunk.as<long long>(), idx2, (double*)nullptr,
                s.cubes.as<int4>(), vcap, ccap, tot);
     RAD_LAUNCH("mc_cubes", k_cubes<false>, cblocks, kCubeThreads, 0, st, s.bits.as<uint32_t>(), (const float*)nullptr,
                d, sp[0], sp[1], sp[2], s.wpre.as<int>(), s.prefix.as<long long>(), s.chunk.as<long long>(),

@@ -131,6 +131,12 @@ rad_status diam_plain_fp64(const int16_t* idx2, const double* vt, long long nv, 
 
 const rad_tuning_t& tuning();
 
+// Adjoint of the soft-map features (grad: dense FP64, nx*ny*nz; gvtx: 3 x vcap).
+rad_status soft_adjoint(const int16_t* idx2, const double* vt, const int32_t* tri, const long long* nv_dev,
+                        const long long* nt_dev, long long vcap, long long tcap, const float* prob, const MeshDims& d,
+                        const double sp[3], const double gout[3], int ai, int aj, double* gvtx, double* grad,
+                        cudaStream_t st);
+
 }  // namespace rad
 
 // ---- pinned FP64 arithmetic (no contraction) ------------------------------------

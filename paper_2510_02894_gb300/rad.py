@@ -70,7 +70,7 @@ _lib = None
 EXPORTS = ("rad_mesh", "rad_soft_mesh", "rad_shape", "rad_shape_plain_fp64", "rad_extract", "rad_extract_host",
            "rad_workspace_free", "rad_mesh_free", "rad_mesh_copy", "rad_set_tuning", "rad_profile_enable",
            "rad_profile_read", "rad_profile_reset", "rad_launch_count", "rad_status_str", "rad_last_error",
-           "rad_last_call_stats")
+           "rad_last_call_stats", "rad_soft_forward", "rad_soft_backward")
 
 
 def lib():
@@ -110,6 +110,10 @@ def lib():
         L.rad_status_str.restype = ctypes.c_char_p
         L.rad_last_call_stats.argtypes = [ctypes.POINTER(CallStats)]
         L.rad_last_call_stats.restype = I
+        L.rad_soft_forward.argtypes = [P, P, P, P, P, ctypes.POINTER(P), P]
+        L.rad_soft_forward.restype = I
+        L.rad_soft_backward.argtypes = [P, P, P, P, P, P, ctypes.POINTER(P), P]
+        L.rad_soft_backward.restype = I
         L.rad_last_error.argtypes = []
         L.rad_last_error.restype = ctypes.c_char_p
         _lib = L
@@ -235,6 +239,32 @@ def extract_host(mask_ptr, shape_zyx, spacing, ws, stream=None):
     _check(lib().rad_extract_host(ctypes.c_void_p(int(mask_ptr)), dims, sp, ctypes.byref(f), ctypes.byref(ws.h),
                                   _stream(stream)))
     return f.as_dict()
+
+
+def soft_forward(prob, spacing, ws, stream=None):
+    """(SurfaceArea, MeshVolume, Maximum3DDiameter), argmax pair of a CUDA
+    float32 probability map."""
+    _device_tensor(prob, "torch.float32")
+    dims, sp = _geometry(prob.shape, spacing)
+    out = (ctypes.c_double * 3)()
+    am = (ctypes.c_int32 * 2)()
+    _check(lib().rad_soft_forward(ctypes.c_void_p(prob.data_ptr()), dims, sp, out, am, ctypes.byref(ws.h),
+                                  _stream(stream)))
+    return (out[0], out[1], out[2]), (int(am[0]), int(am[1]))
+
+
+def soft_backward(prob, spacing, gout, argmax, grad, ws, stream=None):
+    """Writes d(gout . (A, V, D3)) / d prob into `grad` (CUDA float64 tensor of
+    prob's shape); the mesh is recomputed."""
+    _device_tensor(prob, "torch.float32")
+    _device_tensor(grad, "torch.float64")
+    if tuple(grad.shape) != tuple(prob.shape):
+        raise ValueError("grad must have prob's shape")
+    dims, sp = _geometry(prob.shape, spacing)
+    g = (ctypes.c_double * 3)(*(float(v) for v in gout))
+    am = (ctypes.c_int32 * 2)(int(argmax[0]), int(argmax[1]))
+    _check(lib().rad_soft_backward(ctypes.c_void_p(prob.data_ptr()), dims, sp, g, am,
+                                   ctypes.c_void_p(grad.data_ptr()), ctypes.byref(ws.h), _stream(stream)))
 
 
 def set_tuning(tile=None, threads=None, ctas_per_sm=None, cell_shift=None):
