@@ -343,26 +343,31 @@ def main():
         plain = {"ms": pms, "pairs_per_s": pairs / (pms / 1e3), "fp32_filter_shape_ms": fms,
                  "speedup_vs_plain": pms / fms, "identical_results": bool(same)}
 
-    # ---- batched crops (sequential calls until the batched launch lands) ----------
+    # ---- batched crops: 256 ROIs in one set of launches (one CUDA graph) -----------
     batch = None
     if not args.no_batch:
         crops = synth.batch_256(0)
-        devs = [(torch.from_numpy(c).cuda(), s) for c, s in crops]
-        wsb = rad.Workspace()
-        for c, s in devs[:8]:
-            rad.extract(c, s, wsb)
-        torch.cuda.synchronize()
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for c, s in devs:
-            rad.extract(c, s, wsb)
-        e1.record(stream)
-        e1.synchronize()
-        bms = e0.elapsed_time(e1)
-        batch = {"rois": len(devs), "ms": bms, "rois_per_s": len(devs) / (bms / 1e3),
-                 "mode": "one rad_extract call per crop"}
+        devs = [torch.from_numpy(c).cuda() for c, _ in crops]
+        b = rad.Batch(devs, [s for _, s in crops])
+        for _ in range(args.warmup):
+            b.run()
+        bms = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.run()
+            e1.record(stream)
+            e1.synchronize()
+            bms.append(e0.elapsed_time(e1))
+        bs = rad.last_call_stats()
+        bm = statistics.mean(bms)
+        total_pairs = sum(f["n_vertices"] * (f["n_vertices"] - 1) / 2 for f in b.run())
+        batch = {"rois": len(devs), "ms": bm, "rois_per_s": len(devs) / (bm / 1e3),
+                 "vertex_pairs_per_s": total_pairs / (bm / 1e3), "voxels": int(sum(c.size for c, _ in crops)),
+                 "mode": "rad_batch_run: one launch per stage over all 256 ROIs, replayed as one CUDA graph",
+                 "pairs_evaluated_fp32": bs["pairs_evaluated"]}
 
     # ---- CPU baseline: the oracle on a bounded sample --------------------------------
     cpu = None

@@ -132,6 +132,27 @@ rad_status rad_extract_host(const uint8_t* mask_host, const int64_t dims[3], con
 void rad_workspace_free(rad_workspace_t* ws);
 void rad_mesh_free(rad_mesh_t* mesh);
 
+/* ---- batches of regions of interest ------------------------------------------ */
+
+/* A batch of n_rois device uint8 masks of any sizes and spacings (ROI i:
+ * masks_dev[i], dims[3 i .. 3 i + 2], spacing[3 i .. 3 i + 2]) processed
+ * together: every stage of the mesh and of the diameters is one launch over
+ * all ROIs (rows, vertices, tiles and tile pairs of every ROI share one
+ * device work space), and the whole pass is captured once as a CUDA graph.
+ * rad_batch_create validates the ROIs, sizes the pools with one counting
+ * pass and runs + captures the pass (synchronises `stream`).  The masks are
+ * read at every rad_batch_run (their contents may change; their addresses
+ * and sizes may not).  Pool overflows after content changes are detected and
+ * the pass re-runs with grown pools. */
+typedef struct rad_batch rad_batch_t;
+rad_status rad_batch_create(int n_rois, const uint8_t* const* masks_dev, const int64_t* dims, const double* spacing,
+                            rad_batch_t** out, void* stream);
+
+/* Replay the batch: out (host, n_rois entries) receives every ROI's
+ * features.  Synchronises `stream`. */
+rad_status rad_batch_run(rad_batch_t* batch, rad_features_t* out, void* stream);
+void rad_batch_destroy(rad_batch_t* batch);
+
 /* Copy a mesh's arrays to caller buffers (host or device; any may be NULL):
  * idx2 n_vertices x 3 int16, t n_vertices doubles (soft meshes only), tri
  * n_triangles x 3 int32.  Synchronises `stream`. */

@@ -227,34 +227,70 @@ void DevBuf::release() {
 static rad_tuning_t g_tuning = {128, 128, 8, 4};
 const rad_tuning_t& tuning() { return g_tuning; }
 
-// ---- per-mesh / per-workspace state --------------------------------------------------
+// ---- per-workspace state --------------------------------------------------------------
 
-struct Result {  // device, one copy per call
-  MeshTotals mt;
-  DiamResult dr;
-  unsigned int status;
-  unsigned int pad;
+struct ResultBlock {  // device; copied to pinned host memory after every pass
+  MeshTotals tot;
+  DiamStats stats;
 };
+
+// Features of every ROI from the mesh and diameter results (one thread per ROI).
+__global__ void k_assemble(const Roi* __restrict__ rois, const RoiOut* __restrict__ ro,
+                           const DiamOut* __restrict__ dout, int n, int have_diam, rad_features_t* __restrict__ f) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const Roi& r = rois[i];
+    const RoiOut& o = ro[i];
+    rad_features_t x;
+    x.MeshVolume = o.vol6 / 6.0;
+    x.SurfaceArea = o.area2 * 0.5;
+    x.VoxelVolume = (double)o.nvox * r.sx * r.sy * r.sz;
+    x.n_vertices = o.nv;
+    x.n_triangles = o.nt;
+    x.n_voxels = o.nvox;
+    double* D[4] = {&x.Maximum3DDiameter, &x.Maximum2DDiameterSlice, &x.Maximum2DDiameterColumn,
+                    &x.Maximum2DDiameterRow};
+    int32_t* A[4] = {x.argmax3d, x.argmax_slice, x.argmax_column, x.argmax_row};
+    for (int q = 0; q < 4; ++q) {
+      const unsigned long long pr = have_diam ? dout[i].pair[q] : ~0ull;
+      const bool ok = pr != ~0ull;
+      *D[q] = ok ? sqrt(__longlong_as_double((long long)dout[i].d2[q])) : 0.0;
+      A[q][0] = ok ? (int32_t)(pr >> 32) : -1;
+      A[q][1] = ok ? (int32_t)(pr & 0xffffffffu) : -1;
+    }
+    x.status = 0;
+    x._pad = 0;
+    f[i] = x;
+  }
+}
 
 struct Work {
   MeshScratch ms;
   DiamScratch ds;
-  DevBuf result;   // Result
+  DevBuf result;            // ResultBlock
+  DevBuf ro, dout, feats;   // per ROI: RoiOut, DiamOut, rad_features_t
+  DevBuf rois_dev, rd_dev;  // per ROI: Roi, RoiDiam
   DevBuf idx2, vt, tri;
   long long vcap = 0, tcap = 0;
-  Result* host = nullptr;  // pinned copy
-  DevBuf mask;     // device copy of a host mask (rad_extract_host)
-  DevBuf gvtx;     // per-vertex position gradients (soft adjoint)
-  int device = -1;
-  // CUDA graph of the whole rad_extract sequence, valid for one key
+  ResultBlock* host = nullptr;       // pinned copies
+  rad_features_t* hfeats = nullptr;
+  int hfeats_cap = 0;
+  DevBuf mask;  // device copy of a host mask (rad_extract_host)
+  DevBuf gvtx;  // per-vertex position gradients (soft adjoint)
+  DevBuf plain; // result of the plain FP64 kernel
+  // plan of the current batch
+  std::vector<Roi> rois, up_rois;     // planned / last uploaded
+  std::vector<RoiDiam> rd, up_rd;
+  std::vector<double> tab_sp;         // spacings of the uploaded case tables
+  MeshBatch mb;
+  long long nkeys = 0, nplanes = 0;
+  bool soft = false;
+  // CUDA graph of the whole pass, valid for the ROI table it was captured with
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t gexec = nullptr;
   long long g_epoch = -1;
   bool g_prof = false;
+  std::vector<Roi> g_rois;
   CaptureSink g_sink_data;
-  const void* g_mask = nullptr;
-  int64_t g_dims[3] = {0, 0, 0};
-  double g_sp[3] = {0, 0, 0};
   void drop_graph() {
     if (gexec) cudaGraphExecDestroy(gexec);
     gexec = nullptr;
@@ -263,42 +299,247 @@ struct Work {
   ~Work() {
     drop_graph();
     if (cap_stream) cudaStreamDestroy(cap_stream);
-    ms.bits.release(); ms.counts.release(); ms.wpre.release(); ms.prefix.release(); ms.chunk.release();
-    ms.cubes.release(); ms.hist.release(); ms.partial.release();
-    ms.bintab.release(); ds.misc.release(); ds.plain_part.release(); result.release(); idx2.release();
-    vt.release(); tri.release(); mask.release(); gvtx.release();
+    for (DevBuf* b : {&ms.bits, &ms.counts, &ms.wpre, &ms.prefix, &ms.chunk, &ms.cubes, &ms.hist, &ms.partial,
+                      &ms.bintab, &ms.tabsp, &ds.misc, &ds.plain_part, &result, &ro, &dout, &feats, &rois_dev,
+                      &rd_dev, &idx2, &vt, &tri, &mask, &gvtx, &plain})
+      b->release();
     if (host) cudaFreeHost(host);
+    if (hfeats) cudaFreeHost(hfeats);
   }
-  rad_status init() {
-    if (!host) RAD_CUDA(cudaMallocHost(&host, sizeof(Result)));
-    RAD_TRY(result.reserve(sizeof(Result)));
-    return RAD_OK;
-  }
-  Result* dres() const { return result.as<Result>(); }
+  ResultBlock* dres() const { return result.as<ResultBlock>(); }
+  RoiOut* dro() const { return ro.as<RoiOut>(); }
 };
 
-}  // namespace rad
+static bool same_bytes(const void* a, const void* b, size_t n) { return memcmp(a, b, n) == 0; }
 
-namespace rad {
+// Plan a batch (ROI table, case tables, diameter parameters) and upload what
+// changed.  All uploads happen here, outside any graph capture.
+static rad_status prepare(Work& w, int n, const void* const* data, const int64_t* dims, const double* sp, bool soft,
+                          cudaStream_t st) {
+  if (!w.host) RAD_CUDA(cudaMallocHost(&w.host, sizeof(ResultBlock)));
+  if (w.hfeats_cap < n) {
+    if (w.hfeats) cudaFreeHost(w.hfeats);
+    w.hfeats = nullptr;
+    RAD_CUDA(cudaMallocHost(&w.hfeats, sizeof(rad_features_t) * n));
+    w.hfeats_cap = n;
+  }
+  RAD_TRY(w.result.reserve(sizeof(ResultBlock)));
+  RAD_TRY(w.ro.reserve(sizeof(RoiOut) * n));
+  RAD_TRY(w.dout.reserve(sizeof(DiamOut) * n));
+  RAD_TRY(w.feats.reserve(sizeof(rad_features_t) * n));
+  // case tables: one per distinct spacing (binary masks)
+  std::vector<int> tab(n, 0);
+  std::vector<double> tsp;
+  if (!soft) {
+    for (int i = 0; i < n; ++i) {
+      int k = 0;
+      for (; k < (int)tsp.size() / 3; ++k)
+        if (tsp[3 * k] == sp[3 * i] && tsp[3 * k + 1] == sp[3 * i + 1] && tsp[3 * k + 2] == sp[3 * i + 2]) break;
+      if (k == (int)tsp.size() / 3) tsp.insert(tsp.end(), {sp[3 * i], sp[3 * i + 1], sp[3 * i + 2]});
+      tab[i] = k;
+    }
+    if (tsp != w.tab_sp) {
+      RAD_TRY(mesh_tables(tsp.data(), (int)tsp.size() / 3, w.ms, st));
+      w.tab_sp = tsp;
+    }
+  }
+  plan_batch(dims, data, tab.data(), sp, n, soft, w.rois, w.mb);
+  plan_diam(w.rois, soft, w.rd, w.nkeys, w.nplanes);
+  w.soft = soft;
+  RAD_TRY(w.rois_dev.reserve(sizeof(Roi) * n));
+  RAD_TRY(w.rd_dev.reserve(sizeof(RoiDiam) * n));
+  if (w.up_rois.size() != w.rois.size() || !same_bytes(w.up_rois.data(), w.rois.data(), sizeof(Roi) * n) ||
+      w.up_rd.size() != w.rd.size() || !same_bytes(w.up_rd.data(), w.rd.data(), sizeof(RoiDiam) * n) ||
+      w.rois_dev.p != w.mb.rois) {
+    RAD_CUDA(cudaMemcpyAsync(w.rois_dev.p, w.rois.data(), sizeof(Roi) * n, cudaMemcpyHostToDevice, st));
+    RAD_CUDA(cudaMemcpyAsync(w.rd_dev.p, w.rd.data(), sizeof(RoiDiam) * n, cudaMemcpyHostToDevice, st));
+    RAD_CUDA(cudaStreamSynchronize(st));  // the host vectors may change before the copy runs
+    w.up_rois = w.rois;
+    w.up_rd = w.rd;
+  }
+  w.mb.rois = w.rois_dev.as<Roi>();
+  return RAD_OK;
+}
+
+// Counting pass + exact pool sizing (synchronises).
+static rad_status size_pools(Work& w, cudaStream_t st) {
+  ResultBlock* dr = w.dres();
+  RAD_TRY(mesh_count(w.mb, w.ms, &dr->tot, w.dro(), st));
+  RAD_CUDA(cudaMemcpyAsync(w.host, dr, sizeof(ResultBlock), cudaMemcpyDeviceToHost, st));
+  RAD_CUDA(cudaStreamSynchronize(st));
+  const long long nv = w.host->tot.nv, nt = w.host->tot.nt;
+  if (nv >= (1LL << 31) || nt >= (1LL << 31)) {
+    set_error("mesh too large: %lld vertices, %lld triangles", nv, nt);
+    return RAD_ERR_CAPACITY;
+  }
+  RAD_TRY(w.idx2.reserve(sizeof(int16_t) * 3 * std::max<long long>(nv, 1)));
+  if (w.soft) RAD_TRY(w.vt.reserve(sizeof(double) * std::max<long long>(nv, 1)));
+  RAD_TRY(w.tri.reserve(sizeof(int32_t) * 3 * std::max<long long>(nt, 1)));
+  w.vcap = (long long)(w.idx2.bytes / (3 * sizeof(int16_t)));
+  w.tcap = (long long)(w.tri.bytes / (3 * sizeof(int32_t)));
+  if (w.soft) w.vcap = std::min<long long>(w.vcap, (long long)(w.vt.bytes / sizeof(double)));
+  return RAD_OK;
+}
+
+static rad_status enqueue_mesh(Work& w, cudaStream_t st, bool count) {
+  ResultBlock* dr = w.dres();
+  if (count) RAD_TRY(mesh_count(w.mb, w.ms, &dr->tot, w.dro(), st));
+  return mesh_emit(w.mb, w.ms, &dr->tot, w.dro(), w.idx2.as<int16_t>(), w.soft ? w.vt.as<double>() : nullptr,
+                   w.tri.as<int32_t>(), w.vcap, w.tcap, st);
+}
+
+static rad_status enqueue_shape(Work& w, cudaStream_t st) {
+  ResultBlock* dr = w.dres();
+  RAD_CUDA(cudaMemsetAsync(&dr->stats, 0, sizeof(DiamStats), st));
+  RAD_TRY(diam_run(w.mb.n, w.rd_dev.as<RoiDiam>(), w.dro(), &dr->tot.nv, w.vcap, w.nkeys, w.nplanes, !w.soft,
+                   w.idx2.as<int16_t>(), w.soft ? w.vt.as<double>() : nullptr, w.ds, w.dout.as<DiamOut>(),
+                   &dr->stats, st));
+  return RAD_OK;
+}
+
+static rad_status enqueue_finish(Work& w, bool have_diam, cudaStream_t st) {
+  const int n = w.mb.n;
+  RAD_LAUNCH("assemble", k_assemble, std::max(1, (n + 127) / 128), 128, 0, st, w.mb.rois, w.dro(),
+             w.dout.as<DiamOut>(), n, have_diam ? 1 : 0, w.feats.as<rad_features_t>());
+  RAD_CUDA(cudaMemcpyAsync(w.host, w.dres(), sizeof(ResultBlock), cudaMemcpyDeviceToHost, st));
+  RAD_CUDA(cudaMemcpyAsync(w.hfeats, w.feats.p, sizeof(rad_features_t) * n, cudaMemcpyDeviceToHost, st));
+  return RAD_OK;
+}
+
+// One whole pass (mesh, diameters, features to pinned host memory).
+static rad_status enqueue_pass(Work& w, cudaStream_t st) {
+  RAD_TRY(enqueue_mesh(w, st, true));
+  RAD_TRY(enqueue_shape(w, st));
+  return enqueue_finish(w, true, st);
+}
+
+// Capture the pass into a CUDA graph on an internal stream (the caller's
+// stream may be the legacy default stream, which cannot be captured).  Every
+// buffer is already sized by an eager pass, so nothing is allocated inside.
+static rad_status capture_pass(Work& w) {
+  w.drop_graph();
+  if (!w.cap_stream) RAD_CUDA(cudaStreamCreateWithFlags(&w.cap_stream, cudaStreamNonBlocking));
+  const long long epoch0 = alloc_epoch();
+  RAD_CUDA(cudaStreamBeginCapture(w.cap_stream, cudaStreamCaptureModeThreadLocal));
+  g_sink = &w.g_sink_data;
+  rad_status s = enqueue_pass(w, w.cap_stream);
+  g_sink = nullptr;
+  graph_undo_capture(w.g_sink_data);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(w.cap_stream, &graph);
+  if (s != RAD_OK || e != cudaSuccess || alloc_epoch() != epoch0) {
+    // failed, or a buffer moved while capturing: keep running eagerly
+    if (graph) cudaGraphDestroy(graph);
+    graph_release(w.g_sink_data);
+    if (s != RAD_OK) return s;
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+    return RAD_OK;
+  }
+  e = cudaGraphInstantiate(&w.gexec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    w.gexec = nullptr;
+    graph_release(w.g_sink_data);
+    return cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__);
+  }
+  w.g_prof = profiling_on();
+  w.g_epoch = alloc_epoch();
+  w.g_rois = w.rois;
+  return RAD_OK;
+}
+
+static bool graph_matches(const Work& w) {
+  return w.gexec && w.g_epoch == alloc_epoch() && w.g_prof == profiling_on() && w.g_rois.size() == w.rois.size() &&
+         same_bytes(w.g_rois.data(), w.rois.data(), sizeof(Roi) * w.rois.size());
+}
+
+rad_status status_from_dev(unsigned int st) {
+  if (st & (DEV_ERR_VCAP | DEV_ERR_TCAP | DEV_ERR_CANDCAP | DEV_ERR_WORKCAP | DEV_ERR_PROBCAP)) {
+    set_error("device pool too small (status 0x%x)", st);
+    return RAD_ERR_CAPACITY;
+  }
+  if (st & DEV_ERR_TIMEOUT) {
+    set_error("bounded device wait gave up (status 0x%x)", st);
+    return RAD_ERR_TIMEOUT;
+  }
+  if (st) {
+    set_error("device consistency check failed (status 0x%x)", st);
+    return RAD_ERR_INTERNAL;
+  }
+  return RAD_OK;
+}
+
 static thread_local rad_call_stats_t g_stats;
-static void record_stats(const Result& r, long long h2d, bool have_diam) {
+static void record_stats(const ResultBlock& r, long long h2d, long long d2h, bool have_diam) {
   memset(&g_stats, 0, sizeof(g_stats));
   g_stats.h2d_bytes = h2d;
-  g_stats.d2h_bytes = (long long)sizeof(Result);
+  g_stats.d2h_bytes = d2h;
   if (!have_diam) return;
-  g_stats.problems = r.dr.problems;
-  g_stats.tiles = r.dr.tiles;
-  g_stats.tile_pairs = r.dr.tile_pairs;
-  g_stats.work_items = r.dr.work_items;
-  g_stats.items_evaluated = r.dr.items_evaluated;
-  g_stats.pairs_evaluated = r.dr.pairs_evaluated;
-  g_stats.candidates = r.dr.candidates;
+  g_stats.problems = r.stats.problems;
+  g_stats.tiles = r.stats.tiles;
+  g_stats.tile_pairs = r.stats.tile_pairs;
+  g_stats.work_items = r.stats.work_items;
+  g_stats.items_evaluated = r.stats.items_evaluated;
+  g_stats.pairs_evaluated = r.stats.pairs_evaluated;
+  g_stats.candidates = r.stats.candidates;
 }
+
+// Whole pass on the prepared batch.  Capacities come from the previous call
+// (the first call sizes them with a counting pass); an overflow is detected
+// from the device status and the pass re-runs with grown pools.  From the
+// second call on the same ROI table the pass is replayed as one CUDA graph
+// (with per-kernel event pairs inside it when profiling is on).
+static rad_status run_pass(Work& w, cudaStream_t st, bool use_graph, long long h2d_bytes) {
+  if (w.vcap == 0) RAD_TRY(size_pools(w, st));
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    bool replayed = false;
+    if (use_graph && graph_matches(w)) {
+      RAD_CUDA(cudaGraphLaunch(w.gexec, st));
+      graph_replayed(w.g_sink_data);
+      replayed = true;
+    } else {
+      RAD_TRY(enqueue_pass(w, st));
+    }
+    RAD_CUDA(cudaStreamSynchronize(st));
+    if (replayed) graph_timed(w.g_sink_data);
+    const ResultBlock& r = *w.host;
+    const unsigned int s = r.stats.status | r.tot.status;
+    if (r.tot.nv > w.vcap || r.tot.nt > w.tcap || (s & (DEV_ERR_VCAP | DEV_ERR_TCAP))) {
+      w.drop_graph();
+      RAD_TRY(size_pools(w, st));
+      continue;
+    }
+    if (s & DEV_ERR_WORKCAP) { w.drop_graph(); w.ds.work_cap *= 4; continue; }
+    if (s & DEV_ERR_CANDCAP) { w.drop_graph(); w.ds.cand_cap *= 4; continue; }
+    RAD_TRY(status_from_dev(s));
+    record_stats(r, h2d_bytes, (long long)(sizeof(ResultBlock) + sizeof(rad_features_t) * w.mb.n), true);
+    if (use_graph && !graph_matches(w)) RAD_TRY(capture_pass(w));
+    return RAD_OK;
+  }
+  return status_from_dev(w.host->stats.status | w.host->tot.status);
+}
+
+// Mesh only (rad_mesh / rad_soft_mesh / the soft adjoint): exact sizing, then
+// vertices and triangles; the per-ROI results are read back.
+static rad_status run_mesh_only(Work& w, cudaStream_t st, RoiOut* ro_host) {
+  RAD_TRY(size_pools(w, st));
+  RAD_TRY(enqueue_mesh(w, st, false));
+  RAD_CUDA(cudaMemcpyAsync(w.host, w.dres(), sizeof(ResultBlock), cudaMemcpyDeviceToHost, st));
+  if (ro_host) RAD_CUDA(cudaMemcpyAsync(ro_host, w.dro(), sizeof(RoiOut), cudaMemcpyDeviceToHost, st));
+  RAD_CUDA(cudaStreamSynchronize(st));
+  return status_from_dev(w.host->tot.status);
+}
+
 }  // namespace rad
 
 struct rad_workspace {
   rad::Work work;
   rad_mesh_t mesh;
+};
+
+struct rad_batch {
+  rad::Work work;
+  int n = 0;
 };
 
 using namespace rad;
@@ -342,59 +583,34 @@ rad_status check_device_ptr(const void* p, const char* what) {
   return RAD_OK;
 }
 
-rad_status status_from_dev(unsigned int st) {
-  if (st & (DEV_ERR_VCAP | DEV_ERR_TCAP | DEV_ERR_CANDCAP | DEV_ERR_WORKCAP | DEV_ERR_PROBCAP)) {
-    set_error("device pool too small (status 0x%x)", st);
-    return RAD_ERR_CAPACITY;
-  }
-  if (st & DEV_ERR_TIMEOUT) {
-    set_error("bounded device wait gave up (status 0x%x)", st);
-    return RAD_ERR_TIMEOUT;
-  }
-  if (st) {
-    set_error("device consistency check failed (status 0x%x)", st);
-    return RAD_ERR_INTERNAL;
-  }
-  return RAD_OK;
-}
-
 Work* work_of(rad_mesh_t* m) {
   if (!m->_priv) m->_priv = new Work();
   return static_cast<Work*>(m->_priv);
 }
 
-// Marching cubes into library-owned buffers of `w`; counts synchronously.
-rad_status run_mesh(const void* data, bool soft, const int64_t dims[3], const double sp[3], Work& w, rad_mesh_t* mesh,
-                    cudaStream_t st) {
-  RAD_TRY(w.init());
-  const MeshDims d = make_dims(dims);
-  Result* dr = w.dres();
-  RAD_TRY(mesh_count(data, soft, d, w.ms, &dr->mt, st));
-  RAD_CUDA(cudaMemcpyAsync(w.host, dr, sizeof(Result), cudaMemcpyDeviceToHost, st));
-  RAD_CUDA(cudaStreamSynchronize(st));
-  const long long nv = w.host->mt.nv, nt = w.host->mt.nt;
-  if (nv >= (1LL << 31) || nt >= (1LL << 31)) {
-    set_error("mesh too large: %lld vertices, %lld triangles", nv, nt);
-    return RAD_ERR_CAPACITY;
+rad_workspace_t* ensure_ws(rad_workspace_t** ws) {
+  if (!*ws) {
+    *ws = new rad_workspace();
+    memset(&(*ws)->mesh, 0, sizeof(rad_mesh_t));
   }
-  RAD_TRY(w.idx2.reserve(sizeof(int16_t) * 3 * std::max<long long>(nv, 1)));
-  if (soft) RAD_TRY(w.vt.reserve(sizeof(double) * std::max<long long>(nv, 1)));
-  RAD_TRY(w.tri.reserve(sizeof(int32_t) * 3 * std::max<long long>(nt, 1)));
-  w.vcap = (long long)(w.idx2.bytes / (3 * sizeof(int16_t)));
-  w.tcap = (long long)(w.tri.bytes / (3 * sizeof(int32_t)));
-  RAD_TRY(mesh_emit(data, soft, d, sp, w.ms, &dr->mt, w.idx2.as<int16_t>(), soft ? w.vt.as<double>() : nullptr,
-                    w.tri.as<int32_t>(), w.vcap, w.tcap, st));
-  RAD_CUDA(cudaMemcpyAsync(w.host, dr, sizeof(Result), cudaMemcpyDeviceToHost, st));
-  RAD_CUDA(cudaStreamSynchronize(st));
-  RAD_TRY(status_from_dev(w.host->mt.status));
-  mesh->n_vertices = nv;
-  mesh->n_triangles = nt;
-  mesh->n_voxels = w.host->mt.nvox;
+  return *ws;
+}
+
+// Marching cubes of one grid into the buffers of `w`, described in *mesh.
+rad_status build_mesh(const void* data, bool soft, const int64_t dims[3], const double sp[3], Work& w,
+                      rad_mesh_t* mesh, cudaStream_t st) {
+  const void* ptrs[1] = {data};
+  RAD_TRY(prepare(w, 1, ptrs, dims, sp, soft, st));
+  RoiOut ro;
+  RAD_TRY(run_mesh_only(w, st, &ro));
+  mesh->n_vertices = ro.nv;
+  mesh->n_triangles = ro.nt;
+  mesh->n_voxels = ro.nvox;
   mesh->vtx_idx2 = w.idx2.as<int16_t>();
   mesh->vtx_t = soft ? w.vt.as<double>() : nullptr;
   mesh->tri = w.tri.as<int32_t>();
-  mesh->mesh_volume = w.host->mt.vol6 / 6.0;
-  mesh->surface_area = w.host->mt.area2 * 0.5;
+  mesh->mesh_volume = ro.vol6 / 6.0;
+  mesh->surface_area = ro.area2 * 0.5;
   for (int k = 0; k < 3; ++k) {
     mesh->dims[k] = dims[k];
     mesh->spacing[k] = sp[k];
@@ -403,65 +619,53 @@ rad_status run_mesh(const void* data, bool soft, const int64_t dims[3], const do
   return RAD_OK;
 }
 
-void fill_features(const Result& r, const int64_t dims[3], const double sp[3], bool have_diam, rad_features_t* out) {
-  (void)dims;
-  memset(out, 0, sizeof(*out));
-  out->MeshVolume = r.mt.vol6 / 6.0;
-  out->SurfaceArea = r.mt.area2 * 0.5;
-  out->VoxelVolume = (double)r.mt.nvox * sp[0] * sp[1] * sp[2];
-  out->n_vertices = r.mt.nv;
-  out->n_triangles = r.mt.nt;
-  out->n_voxels = r.mt.nvox;
-  double* D[4] = {&out->Maximum3DDiameter, &out->Maximum2DDiameterSlice, &out->Maximum2DDiameterColumn,
-                  &out->Maximum2DDiameterRow};
-  int32_t* A[4] = {out->argmax3d, out->argmax_slice, out->argmax_column, out->argmax_row};
-  for (int q = 0; q < 4; ++q) {
-    *D[q] = have_diam ? sqrt(r.dr.d2[q]) : 0.0;
-    A[q][0] = have_diam ? r.dr.i[q] : -1;
-    A[q][1] = have_diam ? r.dr.j[q] : -1;
-  }
-}
-
-// Diameters of a mesh held in `w` (vertex count known on the host).
-rad_status run_shape(const rad_mesh_t* mesh, Work& w, bool plain, rad_features_t* out, cudaStream_t st) {
-  RAD_TRY(w.init());
-  const MeshDims d = make_dims(mesh->dims);
-  Result* dr = w.dres();
-  const bool have = mesh->n_vertices >= 2;
-  for (int attempt = 0; attempt < 4; ++attempt) {
-    RAD_CUDA(cudaMemsetAsync(&dr->dr, 0, sizeof(DiamResult) + 2 * sizeof(unsigned int), st));
-    if (have) {
-      if (plain)
-        RAD_TRY(diam_plain_fp64(mesh->vtx_idx2, mesh->vtx_t, mesh->n_vertices, d, mesh->spacing, w.ds, &dr->dr, st));
-      else
-        RAD_TRY(diam_run(mesh->vtx_idx2, mesh->vtx_t, mesh->n_vertices, &dr->mt.nv, d, mesh->spacing, w.ds, &dr->dr,
-                         &dr->status, st));
-    }
-    RAD_CUDA(cudaMemcpyAsync(w.host, dr, sizeof(Result), cudaMemcpyDeviceToHost, st));
-    RAD_CUDA(cudaStreamSynchronize(st));
-    const unsigned int s = w.host->status;
-    if (s & DEV_ERR_WORKCAP) { w.ds.work_cap *= 4; continue; }
-    if (s & DEV_ERR_CANDCAP) { w.ds.cand_cap *= 4; continue; }
-    RAD_TRY(status_from_dev(s));
-    Result r = *w.host;
-    record_stats(r, 0, have && !plain);
-    r.mt.nv = mesh->n_vertices;
-    r.mt.nt = mesh->n_triangles;
-    r.mt.nvox = mesh->n_voxels;
-    r.mt.vol6 = mesh->mesh_volume * 6.0;
-    r.mt.area2 = mesh->surface_area * 2.0;
-    fill_features(r, mesh->dims, mesh->spacing, have, out);
-    return RAD_OK;
-  }
-  return status_from_dev(w.host->status);
-}
-
 rad_status check_mesh(const rad_mesh_t* mesh) {
   if (!mesh || !mesh->_priv) {
     set_error("mesh is NULL or was not built by rad_mesh / rad_soft_mesh");
     return RAD_ERR_INVALID_ARG;
   }
   return RAD_OK;
+}
+
+// Diameters of the mesh held by `w` (built by build_mesh on the same Work).
+rad_status shape_of_mesh(const rad_mesh_t* mesh, Work& w, bool plain, rad_features_t* out, cudaStream_t st) {
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    if (plain) {
+      RAD_TRY(w.plain.reserve(sizeof(DiamResult)));
+      RAD_TRY(enqueue_finish(w, false, st));
+      if (mesh->n_vertices >= 2)
+        RAD_TRY(diam_plain_fp64(mesh->vtx_idx2, mesh->vtx_t, mesh->n_vertices, make_dims(mesh->dims), mesh->spacing,
+                                w.ds, w.plain.as<DiamResult>(), st));
+      DiamResult pr;
+      memset(&pr, 0, sizeof(pr));
+      if (mesh->n_vertices >= 2)
+        RAD_CUDA(cudaMemcpyAsync(&pr, w.plain.p, sizeof(DiamResult), cudaMemcpyDeviceToHost, st));
+      RAD_CUDA(cudaStreamSynchronize(st));
+      *out = w.hfeats[0];
+      double* D[4] = {&out->Maximum3DDiameter, &out->Maximum2DDiameterSlice, &out->Maximum2DDiameterColumn,
+                      &out->Maximum2DDiameterRow};
+      int32_t* A[4] = {out->argmax3d, out->argmax_slice, out->argmax_column, out->argmax_row};
+      for (int q = 0; q < 4; ++q) {
+        const bool ok = mesh->n_vertices >= 2 && pr.i[q] >= 0;
+        *D[q] = ok ? sqrt(pr.d2[q]) : 0.0;
+        A[q][0] = ok ? pr.i[q] : -1;
+        A[q][1] = ok ? pr.j[q] : -1;
+      }
+      record_stats(*w.host, 0, (long long)sizeof(DiamResult), false);
+      return RAD_OK;
+    }
+    RAD_TRY(enqueue_shape(w, st));
+    RAD_TRY(enqueue_finish(w, true, st));
+    RAD_CUDA(cudaStreamSynchronize(st));
+    const unsigned int s = w.host->stats.status;
+    if (s & DEV_ERR_WORKCAP) { w.ds.work_cap *= 4; continue; }
+    if (s & DEV_ERR_CANDCAP) { w.ds.cand_cap *= 4; continue; }
+    RAD_TRY(status_from_dev(s));
+    *out = w.hfeats[0];
+    record_stats(*w.host, 0, (long long)(sizeof(ResultBlock) + sizeof(rad_features_t)), true);
+    return RAD_OK;
+  }
+  return status_from_dev(w.host->stats.status);
 }
 
 }  // namespace
@@ -473,7 +677,7 @@ rad_status rad_mesh(const uint8_t* mask_dev, const int64_t dims[3], const double
   RAD_TRY(check_geometry(dims, spacing));
   if (!mesh) { set_error("mesh is NULL"); return RAD_ERR_INVALID_ARG; }
   RAD_TRY(check_device_ptr(mask_dev, "mask_dev"));
-  return run_mesh(mask_dev, false, dims, spacing, *work_of(mesh), mesh, (cudaStream_t)stream);
+  return build_mesh(mask_dev, false, dims, spacing, *work_of(mesh), mesh, (cudaStream_t)stream);
 }
 
 rad_status rad_soft_mesh(const float* prob_dev, const int64_t dims[3], const double spacing[3], rad_mesh_t* mesh,
@@ -481,19 +685,19 @@ rad_status rad_soft_mesh(const float* prob_dev, const int64_t dims[3], const dou
   RAD_TRY(check_geometry(dims, spacing));
   if (!mesh) { set_error("mesh is NULL"); return RAD_ERR_INVALID_ARG; }
   RAD_TRY(check_device_ptr(prob_dev, "prob_dev"));
-  return run_mesh(prob_dev, true, dims, spacing, *work_of(mesh), mesh, (cudaStream_t)stream);
+  return build_mesh(prob_dev, true, dims, spacing, *work_of(mesh), mesh, (cudaStream_t)stream);
 }
 
 rad_status rad_shape(const rad_mesh_t* mesh, rad_features_t* out, void* stream) {
   RAD_TRY(check_mesh(mesh));
   if (!out) { set_error("out is NULL"); return RAD_ERR_INVALID_ARG; }
-  return run_shape(mesh, *static_cast<Work*>(mesh->_priv), false, out, (cudaStream_t)stream);
+  return shape_of_mesh(mesh, *static_cast<Work*>(mesh->_priv), false, out, (cudaStream_t)stream);
 }
 
 rad_status rad_shape_plain_fp64(const rad_mesh_t* mesh, rad_features_t* out, void* stream) {
   RAD_TRY(check_mesh(mesh));
   if (!out) { set_error("out is NULL"); return RAD_ERR_INVALID_ARG; }
-  return run_shape(mesh, *static_cast<Work*>(mesh->_priv), true, out, (cudaStream_t)stream);
+  return shape_of_mesh(mesh, *static_cast<Work*>(mesh->_priv), true, out, (cudaStream_t)stream);
 }
 
 rad_status rad_mesh_copy(const rad_mesh_t* mesh, int16_t* idx2, double* t, int32_t* tri, void* stream) {
@@ -515,106 +719,14 @@ void rad_mesh_free(rad_mesh_t* mesh) {
   memset(mesh, 0, sizeof(*mesh));
 }
 
-// The launch sequence of one whole-path pass (no host synchronisation): mesh,
-// diameters, copy of the result block to pinned host memory.
-static rad_status enqueue_extract(const uint8_t* mask_dev, const MeshDims& d, const double sp[3], Work& w,
-                                  cudaStream_t st) {
-  Result* dr = w.dres();
-  RAD_CUDA(cudaMemsetAsync(&dr->dr, 0, sizeof(DiamResult) + 2 * sizeof(unsigned int), st));
-  RAD_TRY(mesh_count(mask_dev, false, d, w.ms, &dr->mt, st));
-  RAD_TRY(mesh_emit(mask_dev, false, d, sp, w.ms, &dr->mt, w.idx2.as<int16_t>(), nullptr, w.tri.as<int32_t>(),
-                    w.vcap, w.tcap, st));
-  RAD_TRY(diam_run(w.idx2.as<int16_t>(), nullptr, w.vcap, &dr->mt.nv, d, sp, w.ds, &dr->dr, &dr->status, st));
-  RAD_CUDA(cudaMemcpyAsync(w.host, dr, sizeof(Result), cudaMemcpyDeviceToHost, st));
-  return RAD_OK;
-}
-
-// Capture the pass into a CUDA graph on an internal stream (the caller's
-// stream may be the legacy default stream, which cannot be captured).  Every
-// buffer is already sized by an eager pass, so nothing is allocated inside.
-static rad_status capture_extract(const uint8_t* mask_dev, const int64_t dims[3], const double sp[3], Work& w) {
-  w.drop_graph();
-  if (!w.cap_stream) RAD_CUDA(cudaStreamCreateWithFlags(&w.cap_stream, cudaStreamNonBlocking));
-  const MeshDims d = make_dims(dims);
-  const long long epoch0 = alloc_epoch();
-  RAD_CUDA(cudaStreamBeginCapture(w.cap_stream, cudaStreamCaptureModeThreadLocal));
-  g_sink = &w.g_sink_data;
-  rad_status s = enqueue_extract(mask_dev, d, sp, w, w.cap_stream);
-  g_sink = nullptr;
-  graph_undo_capture(w.g_sink_data);
-  cudaGraph_t graph = nullptr;
-  cudaError_t e = cudaStreamEndCapture(w.cap_stream, &graph);
-  if (s != RAD_OK || e != cudaSuccess || alloc_epoch() != epoch0) {
-    // failed, or a buffer moved while capturing: keep running eagerly
-    if (graph) cudaGraphDestroy(graph);
-    graph_release(w.g_sink_data);
-    if (s != RAD_OK) return s;
-    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
-    return RAD_OK;
-  }
-  e = cudaGraphInstantiate(&w.gexec, graph, 0);
-  cudaGraphDestroy(graph);
-  if (e != cudaSuccess) {
-    w.gexec = nullptr;
-    graph_release(w.g_sink_data);
-    return cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__);
-  }
-  w.g_prof = profiling_on();
-  w.g_epoch = alloc_epoch();
-  w.g_mask = mask_dev;
-  for (int k = 0; k < 3; ++k) { w.g_dims[k] = dims[k]; w.g_sp[k] = sp[k]; }
-  return RAD_OK;
-}
-
-static bool graph_matches(const Work& w, const uint8_t* mask_dev, const int64_t dims[3], const double sp[3]) {
-  if (!w.gexec || w.g_epoch != alloc_epoch() || w.g_mask != mask_dev || w.g_prof != profiling_on()) return false;
-  for (int k = 0; k < 3; ++k)
-    if (w.g_dims[k] != dims[k] || w.g_sp[k] != sp[k]) return false;
-  return true;
-}
-
-// Whole path with no host synchronisation inside: capacities come from the
-// previous call on this workspace (the first call sizes them with a counting
-// pass); an overflow is detected from the device status and the call re-runs
-// with grown pools.  From the second call on the same (mask, dims, spacing)
-// the pass is replayed as one CUDA graph (with per-kernel event pairs inside it
-// when profiling is on).
 static rad_status extract_impl(const uint8_t* mask_dev, const int64_t dims[3], const double sp[3],
                                rad_features_t* out, rad_workspace_t* ws, cudaStream_t st, long long h2d_bytes) {
   Work& w = ws->work;
-  RAD_TRY(w.init());
-  const MeshDims d = make_dims(dims);
-  if (w.vcap == 0) {
-    RAD_TRY(run_mesh(mask_dev, false, dims, sp, w, &ws->mesh, st));
-  }
-  const bool use_graph = true;
-  for (int attempt = 0; attempt < 4; ++attempt) {
-    bool replayed = false;
-    if (use_graph && graph_matches(w, mask_dev, dims, sp)) {
-      RAD_CUDA(cudaGraphLaunch(w.gexec, st));
-      graph_replayed(w.g_sink_data);
-      replayed = true;
-    } else {
-      RAD_TRY(enqueue_extract(mask_dev, d, sp, w, st));
-    }
-    RAD_CUDA(cudaStreamSynchronize(st));
-    if (replayed) graph_timed(w.g_sink_data);
-    const Result& r = *w.host;
-    const unsigned int s = r.status | r.mt.status;
-    if (r.mt.nv > w.vcap || r.mt.nt > w.tcap || (s & (DEV_ERR_VCAP | DEV_ERR_TCAP))) {
-      w.drop_graph();
-      RAD_TRY(run_mesh(mask_dev, false, dims, sp, w, &ws->mesh, st));
-      continue;
-    }
-    if (s & DEV_ERR_WORKCAP) { w.drop_graph(); w.ds.work_cap *= 4; continue; }
-    if (s & DEV_ERR_CANDCAP) { w.drop_graph(); w.ds.cand_cap *= 4; continue; }
-    RAD_TRY(status_from_dev(s));
-    fill_features(r, dims, sp, r.mt.nv >= 2, out);
-    record_stats(r, h2d_bytes, true);
-    if (use_graph && !graph_matches(w, mask_dev, dims, sp)) RAD_TRY(capture_extract(mask_dev, dims, sp, w));
-    return RAD_OK;
-  }
-  return status_from_dev(w.host->status | w.host->mt.status);
+  const void* ptrs[1] = {mask_dev};
+  RAD_TRY(prepare(w, 1, ptrs, dims, sp, false, st));
+  RAD_TRY(run_pass(w, st, true, h2d_bytes));
+  *out = w.hfeats[0];
+  return RAD_OK;
 }
 
 rad_status rad_extract(const uint8_t* mask_dev, const int64_t dims[3], const double spacing[3], rad_features_t* out,
@@ -622,37 +734,54 @@ rad_status rad_extract(const uint8_t* mask_dev, const int64_t dims[3], const dou
   RAD_TRY(check_geometry(dims, spacing));
   if (!out || !ws) { set_error("out and ws must be non-NULL"); return RAD_ERR_INVALID_ARG; }
   RAD_TRY(check_device_ptr(mask_dev, "mask_dev"));
-  if (!*ws) {
-    *ws = new rad_workspace();
-    memset(&(*ws)->mesh, 0, sizeof(rad_mesh_t));
-  }
-  return extract_impl(mask_dev, dims, spacing, out, *ws, (cudaStream_t)stream, 0);
+  return extract_impl(mask_dev, dims, spacing, out, ensure_ws(ws), (cudaStream_t)stream, 0);
 }
 
 rad_status rad_extract_host(const uint8_t* mask_host, const int64_t dims[3], const double spacing[3],
                             rad_features_t* out, rad_workspace_t** ws, void* stream) {
   RAD_TRY(check_geometry(dims, spacing));
   if (!out || !ws || !mask_host) { set_error("mask_host, out and ws must be non-NULL"); return RAD_ERR_INVALID_ARG; }
-  if (!*ws) {
-    *ws = new rad_workspace();
-    memset(&(*ws)->mesh, 0, sizeof(rad_mesh_t));
-  }
-  Work& w = (*ws)->work;
+  rad_workspace_t* w = ensure_ws(ws);
   const size_t bytes = (size_t)dims[0] * dims[1] * dims[2];
-  RAD_TRY(w.mask.reserve(bytes));
-  RAD_CUDA(cudaMemcpyAsync(w.mask.p, mask_host, bytes, cudaMemcpyHostToDevice, (cudaStream_t)stream));
-  return extract_impl(w.mask.as<uint8_t>(), dims, spacing, out, *ws, (cudaStream_t)stream, (long long)bytes);
+  RAD_TRY(w->work.mask.reserve(bytes));
+  RAD_CUDA(cudaMemcpyAsync(w->work.mask.p, mask_host, bytes, cudaMemcpyHostToDevice, (cudaStream_t)stream));
+  return extract_impl(w->work.mask.as<uint8_t>(), dims, spacing, out, w, (cudaStream_t)stream, (long long)bytes);
 }
 
 void rad_workspace_free(rad_workspace_t* ws) { delete ws; }
 
-static rad_workspace_t* ensure_ws(rad_workspace_t** ws) {
-  if (!*ws) {
-    *ws = new rad_workspace();
-    memset(&(*ws)->mesh, 0, sizeof(rad_mesh_t));
+rad_status rad_batch_create(int n_rois, const uint8_t* const* masks_dev, const int64_t* dims, const double* spacing,
+                            rad_batch_t** out, void* stream) {
+  if (!out || !masks_dev || !dims || !spacing || n_rois < 1) {
+    set_error("n_rois >= 1 and non-NULL masks_dev, dims, spacing, out required");
+    return RAD_ERR_INVALID_ARG;
   }
-  return *ws;
+  for (int i = 0; i < n_rois; ++i) {
+    RAD_TRY(check_geometry(dims + 3 * i, spacing + 3 * i));
+    RAD_TRY(check_device_ptr(masks_dev[i], "masks_dev[i]"));
+  }
+  rad_batch_t* b = new rad_batch();
+  b->n = n_rois;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<const void*> ptrs(masks_dev, masks_dev + n_rois);
+  rad_status s = prepare(b->work, n_rois, ptrs.data(), dims, spacing, false, st);
+  if (s == RAD_OK) s = run_pass(b->work, st, true, 0);  // sizes the pools and captures the graph
+  if (s != RAD_OK) {
+    delete b;
+    return s;
+  }
+  *out = b;
+  return RAD_OK;
 }
+
+rad_status rad_batch_run(rad_batch_t* b, rad_features_t* out, void* stream) {
+  if (!b || !out) { set_error("batch and out must be non-NULL"); return RAD_ERR_INVALID_ARG; }
+  RAD_TRY(run_pass(b->work, (cudaStream_t)stream, true, 0));
+  memcpy(out, b->work.hfeats, sizeof(rad_features_t) * b->n);
+  return RAD_OK;
+}
+
+void rad_batch_destroy(rad_batch_t* b) { delete b; }
 
 rad_status rad_soft_forward(const float* prob_dev, const int64_t dims[3], const double spacing[3], double out[3],
                             int32_t argmax[2], rad_workspace_t** ws, void* stream) {
@@ -661,9 +790,9 @@ rad_status rad_soft_forward(const float* prob_dev, const int64_t dims[3], const 
   RAD_TRY(check_device_ptr(prob_dev, "prob_dev"));
   rad_workspace_t* w = ensure_ws(ws);
   cudaStream_t st = (cudaStream_t)stream;
-  RAD_TRY(run_mesh(prob_dev, true, dims, spacing, w->work, &w->mesh, st));
+  RAD_TRY(build_mesh(prob_dev, true, dims, spacing, w->work, &w->mesh, st));
   rad_features_t f;
-  RAD_TRY(run_shape(&w->mesh, w->work, false, &f, st));
+  RAD_TRY(shape_of_mesh(&w->mesh, w->work, false, &f, st));
   out[0] = f.SurfaceArea;
   out[1] = f.MeshVolume;
   out[2] = f.Maximum3DDiameter;
@@ -683,7 +812,7 @@ rad_status rad_soft_backward(const float* prob_dev, const int64_t dims[3], const
   Work& wk = w->work;
   cudaStream_t st = (cudaStream_t)stream;
   // recompute the mesh instead of keeping it from the forward pass
-  RAD_TRY(run_mesh(prob_dev, true, dims, spacing, wk, &w->mesh, st));
+  RAD_TRY(build_mesh(prob_dev, true, dims, spacing, wk, &w->mesh, st));
   const long long nv = w->mesh.n_vertices;
   if ((argmax[0] >= 0 || argmax[1] >= 0) &&
       (argmax[0] < 0 || argmax[1] < 0 || argmax[0] >= nv || argmax[1] >= nv || argmax[0] == argmax[1])) {
@@ -693,8 +822,8 @@ rad_status rad_soft_backward(const float* prob_dev, const int64_t dims[3], const
   }
   RAD_TRY(wk.gvtx.reserve(sizeof(double) * 3 * std::max<long long>(wk.vcap, 1)));
   const MeshDims d = make_dims(dims);
-  Result* dr = wk.dres();
-  RAD_TRY(soft_adjoint(wk.idx2.as<int16_t>(), wk.vt.as<double>(), wk.tri.as<int32_t>(), &dr->mt.nv, &dr->mt.nt,
+  ResultBlock* dr = wk.dres();
+  RAD_TRY(soft_adjoint(wk.idx2.as<int16_t>(), wk.vt.as<double>(), wk.tri.as<int32_t>(), &dr->tot.nv, &dr->tot.nt,
                        wk.vcap, wk.tcap, prob_dev, d, spacing, gout, argmax[0], argmax[1], wk.gvtx.as<double>(),
                        grad_dev, st));
   RAD_CUDA(cudaStreamSynchronize(st));

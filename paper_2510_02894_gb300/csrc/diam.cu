@@ -2,6 +2,10 @@
 // "Parallel diameter calculation": each thread scans a subset of vertex pairs
 // into a local maximum, then a reduction combines the local maxima).
 //
+// A batch of regions of interest (ROIs) runs as one set of launches: every
+// problem carries its ROI, whose spacing, centre and error-bound coefficients
+// live in a small device table.
+//
 // GB300 design (FP32 filter, FP64 confirmation):
 //   1. Every vertex gets four keys -- a spatial cell (3D problem) and its
 //      Slice (z), Column (y) and Row (x) plane -- and one counting sort lays
@@ -32,6 +36,7 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "rad_internal.cuh"
 
@@ -44,7 +49,8 @@ struct Problem {
   int axis;  // -1: 3D, 0: Row (equal x), 1: Column (equal y), 2: Slice (equal z)
   int beg, len;
   int tile_beg;  // first tile
-  long long pair_beg;
+  int roi;
+  int pad;
 };
 
 struct Tile {
@@ -52,11 +58,11 @@ struct Tile {
 };
 
 struct WorkItem {
-  int problem, ta, tb, pad;
+  int problem, ta, tb, roi;
 };
 
 struct Cand {
-  int ea, eb, problem, pad;
+  int ea, eb, problem, roi;
 };
 
 struct ProblemState {
@@ -78,22 +84,17 @@ struct Counters {
   int pad;
   unsigned long long items_evaluated, pairs_evaluated;
   long long n_work2;  // items re-evaluated for candidates
-  unsigned int done;  // last-block ticket of the tie-break kernel
+  unsigned int done;  // last-block ticket
   unsigned int pad2;
 };
 
+// Batch-wide parameters of one run.
 struct Params {
-  int nx, ny, nz;
-  int soft, planes;
-  int cell_shift, CX, CY, CZ;     // 3D cells
-  int plane_shift, PX, PY, PZ;    // in-plane 2D cells
-  long long C3, S0, S1, S2, K;    // key blocks: 3D cells, Slice, Column, Row; total
-  double sx, sy, sz;
-  double cx, cy, cz;  // centre (index units)
-  double alpha, beta, gamma;
+  int n;              // ROIs
   int TS;
+  long long nplanes;  // planes of all ROIs
   long long work_cap, cand_cap, max_problems, max_tiles;
-  long long nv_cap;  // vertex pool capacity: device counts are clamped to it
+  long long nv_cap;   // vertex pool capacity: device counts are clamped to it
 };
 
 __device__ __forceinline__ float pair_f(float4 a, float4 b) {
@@ -104,7 +105,7 @@ __device__ __forceinline__ float pair_f(float4 a, float4 b) {
 }
 
 // Threshold T(F): every pair attaining the FP64 maximum has f >= T(F).
-__device__ __forceinline__ float threshold(float F, const Params& p) {
+__device__ __forceinline__ float threshold(float F, const RoiDiam& p) {
   const double f = (double)F;
   if (!(f > p.gamma)) return 0.0f;
   const double a1 = 1.0 + p.alpha;
@@ -131,35 +132,53 @@ __device__ __forceinline__ void vertex_q(const int16_t* idx2, long long v, int q
 
 // ---- 1. keys, histogram, scatter ------------------------------------------------
 // kind 0: 3D cell (z, y, x order); kinds 1..3: (plane, 2D cell) for Slice
-// (equal z), Column (equal y) and Row (equal x).  Sorting by these keys gives
-// the 3D problem spatially compact tiles and every plane compact 2D tiles.
+// (equal z), Column (equal y) and Row (equal x), all offset by the ROI's
+// first key.  Sorting by these keys gives every 3D problem spatially compact
+// tiles and every plane compact 2D tiles.
 
-__device__ __forceinline__ long long key_of(const Params& p, const int q[3], int kind) {
+__device__ __forceinline__ long long key_of(const RoiDiam& p, const int q[3], int kind) {
   const int x1 = q[0] + 1, y1 = q[1] + 1, z1 = q[2] + 1;  // 0 .. 2n
   if (kind == 0) {
     const int cx = x1 >> p.cell_shift, cy = y1 >> p.cell_shift, cz = z1 >> p.cell_shift;
-    return ((long long)cz * p.CY + cy) * p.CX + cx;
+    return p.key0 + ((long long)cz * p.CY + cy) * p.CX + cx;
   }
   const int px = x1 >> p.plane_shift, py = y1 >> p.plane_shift, pz = z1 >> p.plane_shift;
-  if (kind == 1) return p.S0 + (long long)z1 * p.PX * p.PY + (long long)py * p.PX + px;
-  if (kind == 2) return p.S1 + (long long)y1 * p.PX * p.PZ + (long long)pz * p.PX + px;
-  return p.S2 + (long long)x1 * p.PY * p.PZ + (long long)pz * p.PY + py;
+  if (kind == 1) return p.key0 + p.S0 + (long long)z1 * p.PX * p.PY + (long long)py * p.PX + px;
+  if (kind == 2) return p.key0 + p.S1 + (long long)y1 * p.PX * p.PZ + (long long)pz * p.PX + px;
+  return p.key0 + p.S2 + (long long)x1 * p.PY * p.PZ + (long long)pz * p.PY + py;
+}
+
+// ROI of a global vertex id (last ROI whose first vertex is <= v).
+__device__ __forceinline__ int roi_of_vertex(const RoiOut* ro, int n, long long v) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (ro[mid].v0 <= v) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
 }
 
 // Warp-aggregated: lanes with equal keys (consecutive vertices share cells and
 // planes) make one atomic.
-__global__ void k_hist(const int16_t* __restrict__ idx2, const long long* __restrict__ nv_dev, Params p,
+__global__ void k_hist(const int16_t* __restrict__ idx2, const long long* __restrict__ nv_dev,
+                       const RoiDiam* __restrict__ rd, const RoiOut* __restrict__ ro, Params p,
                        int* __restrict__ hist) {
   const long long n = min(*nv_dev, p.nv_cap);
-  const int kinds = p.planes ? 4 : 1;
   const int lane = threadIdx.x & 31;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long v0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) - lane; v0 < n; v0 += stride) {
     const long long v = v0 + lane;
     int q[3] = {0, 0, 0};
-    if (v < n) vertex_q(idx2, v, q);
-    for (int k = 0; k < kinds; ++k) {
-      const long long key = v < n ? key_of(p, q, k) : -1;
+    int roi = 0;
+    if (v < n) {
+      vertex_q(idx2, v, q);
+      roi = p.n == 1 ? 0 : roi_of_vertex(ro, p.n, v);
+    }
+    const RoiDiam& r = rd[roi];
+    for (int k = 0; k < 4; ++k) {
+      const bool use = v < n && (k == 0 || r.planes);
+      const long long key = use ? key_of(r, q, k) : -1;
       const unsigned int peers = __match_any_sync(0xffffffffu, key);
       if (key >= 0 && lane == __ffs(peers) - 1) atomicAdd(&hist[key], __popc(peers));
     }
@@ -169,26 +188,31 @@ __global__ void k_hist(const int16_t* __restrict__ idx2, const long long* __rest
 __device__ __forceinline__ long long key_offset(const long long* offs, const long long* parts, long long key);
 
 __global__ void k_scatter(const int16_t* __restrict__ idx2, const double* __restrict__ vt,
-                          const long long* __restrict__ nv_dev, Params p, const long long* __restrict__ offs,
+                          const long long* __restrict__ nv_dev, const RoiDiam* __restrict__ rd,
+                          const RoiOut* __restrict__ ro, Params p, const long long* __restrict__ offs,
                           const long long* __restrict__ parts, int* __restrict__ cursor,
                           float4* __restrict__ sorted) {
   const long long n = min(*nv_dev, p.nv_cap);
-  const int kinds = p.planes ? 4 : 1;
   const int lane = threadIdx.x & 31;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long v0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) - lane; v0 < n; v0 += stride) {
     const long long v = v0 + lane;
     int q[3] = {0, 0, 0};
+    int roi = 0;
     float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
     if (v < n) {
       vertex_q(idx2, v, q);
+      roi = p.n == 1 ? 0 : roi_of_vertex(ro, p.n, v);
+      const RoiDiam& r = rd[roi];
       double u[3];
       vertex_u(idx2, vt, v, u);
-      e = make_float4(__double2float_rn((u[0] - p.cx) * p.sx), __double2float_rn((u[1] - p.cy) * p.sy),
-                      __double2float_rn((u[2] - p.cz) * p.sz), __int_as_float((int)v));
+      e = make_float4(__double2float_rn((u[0] - r.cx) * r.sx), __double2float_rn((u[1] - r.cy) * r.sy),
+                      __double2float_rn((u[2] - r.cz) * r.sz), __int_as_float((int)v));
     }
-    for (int k = 0; k < kinds; ++k) {
-      const long long key = v < n ? key_of(p, q, k) : -1;
+    const RoiDiam& r = rd[roi];
+    for (int k = 0; k < 4; ++k) {
+      const bool use = v < n && (k == 0 || r.planes);
+      const long long key = use ? key_of(r, q, k) : -1;
       const unsigned int peers = __match_any_sync(0xffffffffu, key);
       const int leader = __ffs(peers) - 1;
       int base = 0;
@@ -254,136 +278,90 @@ __device__ __forceinline__ long long key_offset(const long long* offs, const lon
 }
 
 // ---- 2. problems and tiles --------------------------------------------------------
-// One block builds the problem list: problem 0 is the 3D range [0, N); every
-// plane with >= 2 vertices follows in plane order.  It then scans tile and
-// pair counts and resets the per-problem state (k_tiles writes the tiles).
-__global__ void __launch_bounds__(1024) k_setup_problems(const long long* __restrict__ nv_dev, Params p,
-                                                         const long long* __restrict__ offs,
-                                                         const long long* __restrict__ parts,
-                                                         Problem* __restrict__ probs, Tile* __restrict__ tiles,
-                                                         ProblemState* __restrict__ ps, Counters* __restrict__ cnt) {
-  __shared__ long long s_a[32], s_b[32];
-  __shared__ long long s_np;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const long long n = min(*nv_dev, p.nv_cap);
-  const long long nz2 = 2LL * p.nz + 1, ny2 = 2LL * p.ny + 1, nx2 = 2LL * p.nx + 1;
-  const long long n_planes = p.planes ? nz2 + ny2 + nx2 : 0;
-  if (threadIdx.x == 0) {
-    Problem q;
-    q.axis = -1; q.beg = 0; q.len = (int)n; q.tile_beg = 0; q.pair_beg = 0;
-    probs[0] = q;
-    s_np = 1;
+// One warp per candidate problem: the 3D problem of every ROI (items 0..n-1)
+// and every plane of every ROI (items n..).  A problem with >= 2 vertices
+// takes a slot and a contiguous run of tiles with atomics (the order of
+// problems does not affect any result), resets its state and writes its
+// tiles.
+__device__ __forceinline__ int roi_of_plane(const RoiDiam* rd, int n, long long g) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (rd[mid].plane0 <= g) lo = mid;
+    else hi = mid - 1;
   }
-  __syncthreads();
-  // planes with >= 2 vertices, compacted in plane order
-  for (long long base = 0; base < n_planes; base += blockDim.x) {
-    const long long k = base + threadIdx.x;
-    int axis = 0;
-    long long beg = 0, len = 0;
-    if (k < n_planes) {
-      long long k0, k1;
-      if (k < nz2) {
-        axis = 2; k0 = p.S0 + k * p.PX * p.PY; k1 = k0 + (long long)p.PX * p.PY;
-      } else if (k < nz2 + ny2) {
-        axis = 1; k0 = p.S1 + (k - nz2) * p.PX * p.PZ; k1 = k0 + (long long)p.PX * p.PZ;
-      } else {
-        axis = 0; k0 = p.S2 + (k - nz2 - ny2) * p.PY * p.PZ; k1 = k0 + (long long)p.PY * p.PZ;
-      }
-      beg = key_offset(offs, parts, k0);
-      len = key_offset(offs, parts, k1) - beg;
-    }
-    const int keep = len >= 2 ? 1 : 0;
-    int inc = keep;
-    for (int off = 1; off < 32; off <<= 1) {
-      const int o = __shfl_up_sync(0xffffffffu, inc, off);
-      if (lane >= off) inc += o;
-    }
-    if (lane == 31) s_a[wid] = inc;
-    __syncthreads();
-    long long wb = 0, tot = 0;
-    for (int w = 0; w < nw; ++w) {
-      if (w < wid) wb += s_a[w];
-      tot += s_a[w];
-    }
-    if (keep) {
-      const long long slot = s_np + wb + inc - 1;
-      if (slot < p.max_problems) {
-        Problem q;
-        q.axis = axis; q.beg = (int)beg; q.len = (int)len; q.tile_beg = 0; q.pair_beg = 0;
-        probs[slot] = q;
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) s_np += tot;
-    __syncthreads();
-  }
-  const int np = (int)min(s_np, p.max_problems);
-  // tile and pair prefixes over problems; per-problem state reset
-  long long carry_t = 0, carry_p = 0;
-  for (int base = 0; base < np; base += blockDim.x) {
-    const int i = base + threadIdx.x;
-    long long nt = 0, npairs = 0;
-    if (i < np) {
-      nt = (probs[i].len + p.TS - 1) / p.TS;
-      npairs = probs[i].len >= 2 ? nt * (nt + 1) / 2 : 0;
-    }
-    long long it = nt, ip = npairs;
-    for (int off = 1; off < 32; off <<= 1) {
-      const long long a2 = __shfl_up_sync(0xffffffffu, it, off), b2 = __shfl_up_sync(0xffffffffu, ip, off);
-      if (lane >= off) { it += a2; ip += b2; }
-    }
-    if (lane == 31) { s_a[wid] = it; s_b[wid] = ip; }
-    __syncthreads();
-    long long wt = 0, wp = 0, bt = 0, bp = 0;
-    for (int w = 0; w < nw; ++w) {
-      if (w < wid) { wt += s_a[w]; wp += s_b[w]; }
-      bt += s_a[w]; bp += s_b[w];
-    }
-    if (i < np) {
-      probs[i].tile_beg = (int)(carry_t + wt + it - nt);
-      probs[i].pair_beg = carry_p + wp + ip - npairs;
-      ProblemState z;
-      z.F = 0u; z.T = 0u; z.best_d2 = 0ull; z.best_pair = ~0ull;
-      ps[i] = z;
-    }
-    carry_t += bt;
-    carry_p += bp;
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    cnt->n_problems = np;
-    cnt->n_tiles = (int)min(carry_t, p.max_tiles);
-    cnt->n_pairs = carry_p;
-    if (carry_t > p.max_tiles || s_np > p.max_problems) atomicOr(&cnt->status, DEV_ERR_PROBCAP);
-  }
+  return lo;
 }
 
-__global__ void k_tiles(const Problem* __restrict__ probs, Params p, const Counters* __restrict__ cnt,
-                        Tile* __restrict__ tiles) {
-  const int np = cnt->n_problems;
+__global__ void k_setup(const RoiDiam* __restrict__ rd, Params p, const long long* __restrict__ offs,
+                        const long long* __restrict__ parts, Problem* __restrict__ probs, Tile* __restrict__ tiles,
+                        ProblemState* __restrict__ ps, Counters* __restrict__ cnt) {
   const int lane = threadIdx.x & 31;
   const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long i = warp; i < np; i += nwarps) {
-    const Problem q = probs[i];
-    const int nt = (q.len + p.TS - 1) / p.TS;
+  const long long items = p.n + p.nplanes;
+  for (long long it = warp; it < items; it += nwarps) {
+    int roi, axis;
+    long long k0, k1;
+    if (it < p.n) {
+      roi = (int)it;
+      const RoiDiam& r = rd[roi];
+      axis = -1;
+      k0 = r.key0;
+      k1 = r.key0 + r.C3;
+    } else {
+      const long long g = it - p.n;
+      roi = roi_of_plane(rd, p.n, g);
+      const RoiDiam& r = rd[roi];
+      const long long l = g - r.plane0;
+      const long long nz2 = 2LL * r.nz + 1, ny2 = 2LL * r.ny + 1;
+      if (l < nz2) {
+        axis = 2; k0 = r.key0 + r.S0 + l * r.PX * r.PY; k1 = k0 + (long long)r.PX * r.PY;
+      } else if (l < nz2 + ny2) {
+        axis = 1; k0 = r.key0 + r.S1 + (l - nz2) * r.PX * r.PZ; k1 = k0 + (long long)r.PX * r.PZ;
+      } else {
+        axis = 0; k0 = r.key0 + r.S2 + (l - nz2 - ny2) * r.PY * r.PZ; k1 = k0 + (long long)r.PY * r.PZ;
+      }
+    }
+    const long long beg = key_offset(offs, parts, k0);
+    const long long len = key_offset(offs, parts, k1) - beg;
+    if (len < 2) continue;  // warp-uniform
+    const int nt = (int)((len + p.TS - 1) / p.TS);
+    int slot = 0, tb = 0;
+    if (lane == 0) {
+      slot = atomicAdd(&cnt->n_problems, 1);
+      tb = atomicAdd(&cnt->n_tiles, nt);
+      atomicAdd((unsigned long long*)&cnt->n_pairs, (unsigned long long)nt * (nt + 1) / 2);
+    }
+    slot = __shfl_sync(0xffffffffu, slot, 0);
+    tb = __shfl_sync(0xffffffffu, tb, 0);
+    if (slot >= p.max_problems || (long long)tb + nt > p.max_tiles) {
+      if (lane == 0) atomicOr(&cnt->status, DEV_ERR_PROBCAP);
+      continue;
+    }
+    if (lane == 0) {
+      Problem q;
+      q.axis = axis; q.beg = (int)beg; q.len = (int)len; q.tile_beg = tb; q.roi = roi; q.pad = 0;
+      probs[slot] = q;
+      ProblemState z;
+      z.F = 0u; z.T = 0u; z.best_d2 = 0ull; z.best_pair = ~0ull;
+      ps[slot] = z;
+    }
     for (int t = lane; t < nt; t += 32) {
-      const long long ti = (long long)q.tile_beg + t;
-      if (ti >= p.max_tiles) break;
       Tile tl;
-      tl.problem = (int)i;
-      tl.beg = q.beg + t * p.TS;
-      tl.len = min(p.TS, q.len - t * p.TS);
-      tl.tile_end = (int)min((long long)q.tile_beg + nt, p.max_tiles);
-      tiles[ti] = tl;
+      tl.problem = slot;
+      tl.beg = (int)beg + t * p.TS;
+      tl.len = min(p.TS, (int)len - t * p.TS);
+      tl.tile_end = tb + nt;
+      tiles[tb + t] = tl;
     }
   }
 }
 
 // One warp per tile: bounding box of its FP32 positions.
-__global__ void k_tile_box(const float4* __restrict__ sorted, const Tile* __restrict__ tiles,
+__global__ void k_tile_box(const float4* __restrict__ sorted, const Tile* __restrict__ tiles, Params p,
                            const Counters* __restrict__ cnt, float4* __restrict__ box, float4* __restrict__ rep) {
-  const int nt = cnt->n_tiles;
+  const int nt = (int)min((long long)cnt->n_tiles, p.max_tiles);
   const int lane = threadIdx.x & 31;
   const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -412,9 +390,10 @@ __global__ void k_tile_box(const float4* __restrict__ sorted, const Tile* __rest
 // vertex of each tile) of one problem, plus each tile's first-last pair, are
 // actual vertex pairs, so their largest f is a valid starting F.
 __global__ void k_seed_rows(const float4* __restrict__ sorted, const float4* __restrict__ rep, Params p,
+                            const RoiDiam* __restrict__ rd, const Problem* __restrict__ probs,
                             const Tile* __restrict__ tiles, Counters* __restrict__ cnt,
                             ProblemState* __restrict__ ps) {
-  const int nt = cnt->n_tiles;
+  const int nt = (int)min((long long)cnt->n_tiles, p.max_tiles);
   const int lane = threadIdx.x & 31;
   const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -437,9 +416,9 @@ __global__ void k_seed_rows(const float4* __restrict__ sorted, const float4* __r
   __syncthreads();
   if (last) {
     __threadfence();
-    const int np = cnt->n_problems;
+    const int np = (int)min((long long)cnt->n_problems, p.max_problems);
     for (int i = threadIdx.x; i < np; i += blockDim.x)
-      ps[i].T = __float_as_uint(threshold(__uint_as_float(__ldcg(&ps[i].F)), p));
+      ps[i].T = __float_as_uint(threshold(__uint_as_float(__ldcg(&ps[i].F)), rd[probs[i].roi]));
     __syncthreads();
     if (threadIdx.x == 0) cnt->done = 0;
   }
@@ -449,14 +428,16 @@ __global__ void k_seed_rows(const float4* __restrict__ sorted, const float4* __r
 // One warp per tile row a: every tile pair (a, b >= a) of the same problem
 // whose box bound reaches T(F) goes to the work list.
 __global__ void k_cull_rows(const Tile* __restrict__ tiles, const float4* __restrict__ box, Params p,
-                            Counters* __restrict__ cnt, ProblemState* __restrict__ ps, WorkItem* __restrict__ work) {
-  const int nt = cnt->n_tiles;
+                            const Problem* __restrict__ probs, Counters* __restrict__ cnt,
+                            ProblemState* __restrict__ ps, WorkItem* __restrict__ work) {
+  const int nt = (int)min((long long)cnt->n_tiles, p.max_tiles);
   const int lane = threadIdx.x & 31;
   const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   for (long long a = warp; a < nt; a += nwarps) {
     const Tile ta = tiles[a];
     const float T = __uint_as_float(ps[ta.problem].T);
+    const int roi = probs[ta.problem].roi;
     const float4 alo = box[2 * a], ahi = box[2 * a + 1];
     for (long long b0 = a; b0 < ta.tile_end; b0 += 32) {
       const long long b = b0 + lane;
@@ -471,7 +452,7 @@ __global__ void k_cull_rows(const Tile* __restrict__ tiles, const float4* __rest
         const long long slot = base + __popc(m & ((1u << lane) - 1u));
         if (slot < p.work_cap) {
           WorkItem w;
-          w.problem = ta.problem; w.ta = (int)a; w.tb = (int)b; w.pad = 0;
+          w.problem = ta.problem; w.ta = (int)a; w.tb = (int)b; w.roi = roi;
           work[slot] = w;
         } else {
           atomicOr(&cnt->status, DEV_ERR_WORKCAP);
@@ -507,7 +488,7 @@ __global__ void k_compact_items(const WorkItem* __restrict__ work, const float* 
 // warp holds the A entries l, l + 32, ...; warp w scans its slice of B.
 template <int TS, int NT, bool CAND>
 __device__ __forceinline__ float eval_pair_tile(const float4* __restrict__ sorted, const Tile& A, const Tile& B,
-                                                float4* sB, float T, int problem, Cand* cand, Counters* cnt,
+                                                float4* sB, float T, int problem, int roi, Cand* cand, Counters* cnt,
                                                 long long cand_cap) {
   constexpr int RA = TS / 32;
   constexpr int NWARP = NT / 32;
@@ -544,7 +525,7 @@ __device__ __forceinline__ float eval_pair_tile(const float4* __restrict__ sorte
           const long long slot = atomicAdd((unsigned long long*)&cnt->n_cand, 1ull);
           if (slot < cand_cap) {
             Cand c;
-            c.ea = ea; c.eb = eb; c.problem = problem; c.pad = 0;
+            c.ea = ea; c.eb = eb; c.problem = problem; c.roi = roi;
             cand[slot] = c;
           } else {
             atomicOr(&cnt->status, DEV_ERR_CANDCAP);
@@ -562,7 +543,8 @@ __device__ __forceinline__ float eval_pair_tile(const float4* __restrict__ sorte
 template <int TS, int NT>
 __global__ void __launch_bounds__(NT) k_pairs_max(const float4* __restrict__ sorted, const Tile* __restrict__ tiles,
                                                   const float4* __restrict__ box, const WorkItem* __restrict__ work,
-                                                  Params p, Counters* __restrict__ cnt, ProblemState* __restrict__ ps,
+                                                  Params p, const RoiDiam* __restrict__ rd,
+                                                  Counters* __restrict__ cnt, ProblemState* __restrict__ ps,
                                                   float* __restrict__ itemmax) {
   __shared__ float4 sB[TS];
   __shared__ float sred[NT / 32];
@@ -579,7 +561,7 @@ __global__ void __launch_bounds__(NT) k_pairs_max(const float4* __restrict__ sor
       continue;
     }
     const Tile A = tiles[w.ta], B = tiles[w.tb];
-    float m = eval_pair_tile<TS, NT, false>(sorted, A, B, sB, T, w.problem, nullptr, cnt, 0);
+    float m = eval_pair_tile<TS, NT, false>(sorted, A, B, sB, T, w.problem, w.roi, nullptr, cnt, 0);
     for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
     if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = m;
     __syncthreads();
@@ -588,7 +570,7 @@ __global__ void __launch_bounds__(NT) k_pairs_max(const float4* __restrict__ sor
       for (int k = 1; k < NT / 32; ++k) bm = fmaxf(bm, sred[k]);
       itemmax[it] = bm;
       const unsigned int old = atomicMax(&ps[w.problem].F, __float_as_uint(bm));
-      if (__float_as_uint(bm) > old) atomicMax(&ps[w.problem].T, __float_as_uint(threshold(bm, p)));
+      if (__float_as_uint(bm) > old) atomicMax(&ps[w.problem].T, __float_as_uint(threshold(bm, rd[w.roi])));
       n_items++;
       n_pairs += (unsigned long long)A.len * (unsigned long long)B.len;
     }
@@ -611,7 +593,7 @@ __global__ void __launch_bounds__(NT) k_pairs_cand(const float4* __restrict__ so
     const WorkItem w = work[work2[k]];
     const float T = __uint_as_float(ps[w.problem].T);
     const Tile A = tiles[w.ta], B = tiles[w.tb];
-    eval_pair_tile<TS, NT, true>(sorted, A, B, sB, T, w.problem, cand, cnt, p.cand_cap);
+    eval_pair_tile<TS, NT, true>(sorted, A, B, sB, T, w.problem, w.roi, cand, cnt, p.cand_cap);
     __syncthreads();
   }
 }
@@ -619,18 +601,91 @@ __global__ void __launch_bounds__(NT) k_pairs_cand(const float4* __restrict__ so
 // ---- 5. FP64 confirmation -------------------------------------------------------------
 
 __global__ void k_confirm(const float4* __restrict__ sorted, const int16_t* __restrict__ idx2,
-                          const double* __restrict__ vt, Params p, const Counters* __restrict__ cnt,
-                          const Cand* __restrict__ cand, ProblemState* __restrict__ ps) {
+                          const double* __restrict__ vt, Params p, const RoiDiam* __restrict__ rd,
+                          const Counters* __restrict__ cnt, const Cand* __restrict__ cand,
+                          ProblemState* __restrict__ ps) {
   const long long nc = min(cnt->n_cand, p.cand_cap);
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nc; c += (long long)gridDim.x * blockDim.x) {
     const Cand k = cand[c];
+    const RoiDiam& r = rd[k.roi];
     const int i = __float_as_int(sorted[k.ea].w), j = __float_as_int(sorted[k.eb].w);
     double ui[3], uj[3];
     vertex_u(idx2, vt, i, ui);
     vertex_u(idx2, vt, j, uj);
-    const double d2 = pin_d2(ui[0], ui[1], ui[2], uj[0], uj[1], uj[2], p.sx, p.sy, p.sz);
+    const double d2 = pin_d2(ui[0], ui[1], ui[2], uj[0], uj[1], uj[2], r.sx, r.sy, r.sz);
     atomicMax(&ps[k.problem].best_d2, (unsigned long long)__double_as_longlong(d2));
   }
+}
+
+// Candidates attaining their problem's maximum take the smallest (i, j)
+// (ids local to the ROI).  The last block to finish then reduces the
+// problems to one result per ROI and category (3D, Slice, Column, Row): first
+// the largest d2, then the smallest pair among the problems attaining it.
+__global__ void k_tiebreak(const float4* __restrict__ sorted, const int16_t* __restrict__ idx2,
+                           const double* __restrict__ vt, Params p, const RoiDiam* __restrict__ rd,
+                           const RoiOut* __restrict__ ro, Counters* __restrict__ cnt, const Cand* __restrict__ cand,
+                           ProblemState* __restrict__ ps, const Problem* __restrict__ probs,
+                           DiamOut* __restrict__ out, DiamStats* __restrict__ stats) {
+  const long long nc = min(cnt->n_cand, p.cand_cap);
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nc; c += (long long)gridDim.x * blockDim.x) {
+    const Cand k = cand[c];
+    const RoiDiam& r = rd[k.roi];
+    int i = __float_as_int(sorted[k.ea].w), j = __float_as_int(sorted[k.eb].w);
+    double ui[3], uj[3];
+    vertex_u(idx2, vt, i, ui);
+    vertex_u(idx2, vt, j, uj);
+    const double d2 = pin_d2(ui[0], ui[1], ui[2], uj[0], uj[1], uj[2], r.sx, r.sy, r.sz);
+    if ((unsigned long long)__double_as_longlong(d2) == __ldcg(&ps[k.problem].best_d2)) {
+      const long long v0 = ro[k.roi].v0;
+      i -= (int)v0;
+      j -= (int)v0;
+      if (i > j) { const int t = i; i = j; j = t; }
+      atomicMin(&ps[k.problem].best_pair, ((unsigned long long)(unsigned int)i << 32) | (unsigned int)j);
+    }
+  }
+  __shared__ bool last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(&cnt->done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const int np = (int)min((long long)cnt->n_problems, p.max_problems);
+  for (int i = threadIdx.x; i < np; i += blockDim.x) {
+    const Problem pr = probs[i];
+    if (__ldcg(&ps[i].best_pair) == ~0ull) continue;
+    const int q = pr.axis < 0 ? 0 : (pr.axis == 2 ? 1 : (pr.axis == 1 ? 2 : 3));
+    atomicMax(&out[pr.roi].d2[q], __ldcg(&ps[i].best_d2));
+  }
+  __threadfence();  // phase-1 atomics of every thread visible before phase 2
+  __syncthreads();
+  for (int i = threadIdx.x; i < np; i += blockDim.x) {
+    const Problem pr = probs[i];
+    const unsigned long long bp = __ldcg(&ps[i].best_pair);
+    if (bp == ~0ull) continue;
+    const int q = pr.axis < 0 ? 0 : (pr.axis == 2 ? 1 : (pr.axis == 1 ? 2 : 3));
+    if (__ldcg(&ps[i].best_d2) == __ldcg(&out[pr.roi].d2[q])) atomicMin(&out[pr.roi].pair[q], bp);
+  }
+  if (threadIdx.x == 0) {
+    stats->problems = cnt->n_problems;
+    stats->tiles = cnt->n_tiles;
+    stats->tile_pairs = cnt->n_pairs;
+    stats->work_items = cnt->n_work;
+    stats->items_evaluated = (long long)cnt->items_evaluated;
+    stats->pairs_evaluated = (long long)cnt->pairs_evaluated;
+    stats->candidates = cnt->n_cand;
+    stats->status |= cnt->status;
+  }
+}
+
+__global__ void k_diam_init(DiamOut* __restrict__ out, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    for (int q = 0; q < 4; ++q) {
+      out[i].d2[q] = 0ull;
+      out[i].pair[q] = ~0ull;
+    }
 }
 
 struct BestD {
@@ -646,89 +701,6 @@ __device__ __forceinline__ bool better(double d2, int i, int j, const BestD& b) 
   return j < b.j;
 }
 
-// Per category (3D, Slice, Column, Row), the best problem result: max d2,
-// then the smallest pair.  Run by one block.
-__device__ void finalize_block(const Problem* __restrict__ probs, const Counters* __restrict__ cnt,
-                               const ProblemState* __restrict__ ps, DiamResult* __restrict__ out,
-                               unsigned int* __restrict__ status) {
-  __shared__ BestD s[4][32];
-  const int np = cnt->n_problems;
-  BestD b[4];
-  for (int q = 0; q < 4; ++q) { b[q].d2 = 0.0; b[q].i = -1; b[q].j = -1; }
-  for (int i = threadIdx.x; i < np; i += blockDim.x) {
-    const Problem pr = probs[i];
-    const int q = pr.axis < 0 ? 0 : (pr.axis == 2 ? 1 : (pr.axis == 1 ? 2 : 3));
-    const unsigned long long bp = __ldcg(&ps[i].best_pair);
-    if (bp == ~0ull) continue;
-    const double d2 = __longlong_as_double((long long)__ldcg(&ps[i].best_d2));
-    const int bi = (int)(bp >> 32), bj = (int)(bp & 0xffffffffu);
-    if (better(d2, bi, bj, b[q])) { b[q].d2 = d2; b[q].i = bi; b[q].j = bj; }
-  }
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int q = 0; q < 4; ++q) {
-    for (int off = 16; off > 0; off >>= 1) {
-      BestD o;
-      o.d2 = __shfl_xor_sync(0xffffffffu, b[q].d2, off);
-      o.i = __shfl_xor_sync(0xffffffffu, b[q].i, off);
-      o.j = __shfl_xor_sync(0xffffffffu, b[q].j, off);
-      if (better(o.d2, o.i, o.j, b[q])) b[q] = o;
-    }
-    if (lane == 0) s[q][wid] = b[q];
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int q = 0; q < 4; ++q) {
-      BestD r = s[q][0];
-      for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
-        if (better(s[q][w].d2, s[q][w].i, s[q][w].j, r)) r = s[q][w];
-      out->d2[q] = r.i >= 0 ? r.d2 : 0.0;
-      out->i[q] = r.i;
-      out->j[q] = r.j;
-    }
-    out->problems = cnt->n_problems;
-    out->tiles = cnt->n_tiles;
-    out->tile_pairs = cnt->n_pairs;
-    out->work_items = cnt->n_work;
-    out->items_evaluated = (long long)cnt->items_evaluated;
-    out->pairs_evaluated = (long long)cnt->pairs_evaluated;
-    out->candidates = cnt->n_cand;
-    if (cnt->status) atomicOr(status, cnt->status);
-  }
-}
-
-// Candidates attaining their problem's maximum take the smallest (i, j); the
-// last block to finish writes the per-category results.
-__global__ void k_tiebreak(const float4* __restrict__ sorted, const int16_t* __restrict__ idx2,
-                           const double* __restrict__ vt, Params p, Counters* __restrict__ cnt,
-                           const Cand* __restrict__ cand, ProblemState* __restrict__ ps,
-                           const Problem* __restrict__ probs, DiamResult* __restrict__ out,
-                           unsigned int* __restrict__ status) {
-  const long long nc = min(cnt->n_cand, p.cand_cap);
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nc; c += (long long)gridDim.x * blockDim.x) {
-    const Cand k = cand[c];
-    int i = __float_as_int(sorted[k.ea].w), j = __float_as_int(sorted[k.eb].w);
-    double ui[3], uj[3];
-    vertex_u(idx2, vt, i, ui);
-    vertex_u(idx2, vt, j, uj);
-    const double d2 = pin_d2(ui[0], ui[1], ui[2], uj[0], uj[1], uj[2], p.sx, p.sy, p.sz);
-    if ((unsigned long long)__double_as_longlong(d2) == __ldcg(&ps[k.problem].best_d2)) {
-      if (i > j) { const int t = i; i = j; j = t; }
-      atomicMin(&ps[k.problem].best_pair, ((unsigned long long)(unsigned int)i << 32) | (unsigned int)j);
-    }
-  }
-  __shared__ bool last;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    last = atomicAdd(&cnt->done, 1u) == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (last) {
-    __threadfence();
-    finalize_block(probs, cnt, ps, out, status);
-  }
-}
-
 template <class T>
 T* carve(char*& cur, size_t n) {
   T* r = reinterpret_cast<T*>(cur);
@@ -738,12 +710,12 @@ T* carve(char*& cur, size_t n) {
 
 template <int TS, int NT>
 rad_status launch_pairs(const float4* sorted, const Tile* tiles, const float4* box, const WorkItem* work, int* work2,
-                        const Params& p, Counters* cnt, ProblemState* ps, float* itemmax, Cand* cand, int ctas,
-                        cudaStream_t st) {
+                        const Params& p, const RoiDiam* rd, Counters* cnt, ProblemState* ps, float* itemmax,
+                        Cand* cand, int ctas, cudaStream_t st) {
   auto kmax = k_pairs_max<TS, NT>;
   auto kcand = k_pairs_cand<TS, NT>;
   const int sms = num_sms();
-  RAD_LAUNCH("diam_pairs_fp32", kmax, ctas, NT, 0, st, sorted, tiles, box, work, p, cnt, ps, itemmax);
+  RAD_LAUNCH("diam_pairs_fp32", kmax, ctas, NT, 0, st, sorted, tiles, box, work, p, rd, cnt, ps, itemmax);
   RAD_LAUNCH("diam_compact", k_compact_items, sms * 4, 256, 0, st, work, itemmax, p, cnt, ps, work2);
   RAD_LAUNCH("diam_pairs_cand", kcand, ctas, NT, 0, st, sorted, tiles, work, work2, p, cnt, ps, cand);
   return RAD_OK;
@@ -751,45 +723,63 @@ rad_status launch_pairs(const float4* sorted, const Tile* tiles, const float4* b
 
 }  // namespace
 
-rad_status diam_run(const int16_t* idx2, const double* vt, long long nv_hint, const long long* nv_dev,
-                    const MeshDims& d, const double sp[3], DiamScratch& s, DiamResult* out_dev,
-                    unsigned int* status_dev, cudaStream_t st) {
+// Host-side per-ROI parameters of the diameter problems.
+void plan_diam(const std::vector<Roi>& rois, bool soft, std::vector<RoiDiam>& rd, long long& nkeys,
+               long long& nplanes) {
+  const rad_tuning_t& tu = tuning();
+  rd.resize(rois.size());
+  nkeys = 0;
+  nplanes = 0;
+  const double u = ldexp(1.0, -24);
+  for (size_t i = 0; i < rois.size(); ++i) {
+    const Roi& g = rois[i];
+    RoiDiam& p = rd[i];
+    p.nx = g.nx; p.ny = g.ny; p.nz = g.nz;
+    p.planes = soft ? 0 : 1;
+    p.cell_shift = tu.cell_shift;
+    p.CX = ((2 * g.nx) >> p.cell_shift) + 1;
+    p.CY = ((2 * g.ny) >> p.cell_shift) + 1;
+    p.CZ = ((2 * g.nz) >> p.cell_shift) + 1;
+    p.plane_shift = tu.cell_shift + 2;
+    p.PX = ((2 * g.nx) >> p.plane_shift) + 1;
+    p.PY = ((2 * g.ny) >> p.plane_shift) + 1;
+    p.PZ = ((2 * g.nz) >> p.plane_shift) + 1;
+    p.C3 = (long long)p.CX * p.CY * p.CZ;
+    p.S0 = p.C3;
+    p.S1 = p.S0 + (p.planes ? (2LL * g.nz + 1) * p.PX * p.PY : 0);
+    p.S2 = p.S1 + (p.planes ? (2LL * g.ny + 1) * p.PX * p.PZ : 0);
+    p.K = p.S2 + (p.planes ? (2LL * g.nx + 1) * p.PY * p.PZ : 0);
+    p.key0 = nkeys;
+    p.plane0 = nplanes;
+    nkeys += p.K;
+    nplanes += p.planes ? (2LL * g.nx + 1) + (2LL * g.ny + 1) + (2LL * g.nz + 1) : 0;
+    p.sx = g.sx; p.sy = g.sy; p.sz = g.sz;
+    p.cx = 0.5 * (g.nx - 1); p.cy = 0.5 * (g.ny - 1); p.cz = 0.5 * (g.nz - 1);
+    double R2 = 0.0;
+    const int nn[3] = {g.nx, g.ny, g.nz};
+    const double sp[3] = {g.sx, g.sy, g.sz};
+    for (int k = 0; k < 3; ++k) {
+      const double r = 0.5 * (nn[k] + 1) * sp[k];
+      R2 += r * r;
+    }
+    p.alpha = 2.0 * 5.1 * u + 1e-14;
+    p.beta = 2.0 * 4.1 * u * sqrt(R2);
+    p.gamma = 2.0 * 4.1 * u * u * R2;
+  }
+}
+
+rad_status diam_run(int n, const RoiDiam* rd, const RoiOut* ro, const long long* nv_dev, long long nv_cap,
+                    long long nkeys, long long nplanes, bool planes, const int16_t* idx2, const double* vt,
+                    DiamScratch& s, DiamOut* out, DiamStats* stats, cudaStream_t st) {
   const rad_tuning_t& tu = tuning();
   Params p;
-  p.nx = d.nx; p.ny = d.ny; p.nz = d.nz;
-  p.soft = vt != nullptr;
-  p.planes = vt == nullptr;
-  p.cell_shift = tu.cell_shift;
-  p.CX = ((2 * d.nx) >> p.cell_shift) + 1;
-  p.CY = ((2 * d.ny) >> p.cell_shift) + 1;
-  p.CZ = ((2 * d.nz) >> p.cell_shift) + 1;
-  p.plane_shift = tu.cell_shift + 2;
-  p.PX = ((2 * d.nx) >> p.plane_shift) + 1;
-  p.PY = ((2 * d.ny) >> p.plane_shift) + 1;
-  p.PZ = ((2 * d.nz) >> p.plane_shift) + 1;
-  p.C3 = (long long)p.CX * p.CY * p.CZ;
-  p.S0 = p.C3;
-  p.S1 = p.S0 + (p.planes ? (2LL * d.nz + 1) * p.PX * p.PY : 0);
-  p.S2 = p.S1 + (p.planes ? (2LL * d.ny + 1) * p.PX * p.PZ : 0);
-  p.K = p.S2 + (p.planes ? (2LL * d.nx + 1) * p.PY * p.PZ : 0);
-  p.sx = sp[0]; p.sy = sp[1]; p.sz = sp[2];
-  p.cx = 0.5 * (d.nx - 1); p.cy = 0.5 * (d.ny - 1); p.cz = 0.5 * (d.nz - 1);
-  const double u = ldexp(1.0, -24);
-  double R2 = 0.0;
-  for (int k = 0; k < 3; ++k) {
-    const int n = k == 0 ? d.nx : (k == 1 ? d.ny : d.nz);
-    const double r = 0.5 * (n + 1) * sp[k];
-    R2 += r * r;
-  }
-  p.alpha = 2.0 * 5.1 * u + 1e-14;
-  p.beta = 2.0 * 4.1 * u * sqrt(R2);
-  p.gamma = 2.0 * 4.1 * u * u * R2;
+  p.n = n;
   p.TS = tu.tile;
-  const long long nv = std::max<long long>(nv_hint, 2);
-  p.nv_cap = nv_hint;
-  const int kinds = p.planes ? 4 : 1;
-  const long long nsorted = nv * kinds;
-  p.max_problems = 2 + (p.planes ? (2LL * d.nx + 1) + (2LL * d.ny + 1) + (2LL * d.nz + 1) : 0);
+  p.nplanes = nplanes;
+  const long long nv = std::max<long long>(nv_cap, 2);
+  p.nv_cap = nv_cap;
+  const long long nsorted = nv * (planes ? 4 : 1);
+  p.max_problems = n + nplanes + 1;
   p.max_tiles = nsorted / p.TS + p.max_problems + 1;
   if (s.work_cap == 0) s.work_cap = 1 << 20;
   if (s.cand_cap == 0) s.cand_cap = 1 << 20;
@@ -797,10 +787,10 @@ rad_status diam_run(const int16_t* idx2, const double* vt, long long nv_hint, co
   p.cand_cap = s.cand_cap;
 
   // scratch layout (hist/offsets carry one extra entry: offs[K] = total)
-  const long long K1 = p.K + 1;
+  const long long K1 = nkeys + 1;
   const long long nparts = (K1 + kScanBlock - 1) / kScanBlock;
   size_t bytes = 0;
-  auto add = [&](size_t n) { bytes += (n + 255) & ~size_t(255); };
+  auto add = [&](size_t m) { bytes += (m + 255) & ~size_t(255); };
   add(sizeof(int) * K1);             // hist
   add(sizeof(int) * K1);             // cursor
   add(sizeof(long long) * K1);       // offsets
@@ -838,31 +828,31 @@ rad_status diam_run(const int16_t* idx2, const double* vt, long long nv_hint, co
   RAD_CUDA(cudaMemsetAsync(hist, 0, sizeof(int) * K1, st));
   RAD_CUDA(cudaMemsetAsync(cursor, 0, sizeof(int) * K1, st));
   RAD_CUDA(cudaMemsetAsync(cnt, 0, sizeof(Counters), st));
+  RAD_LAUNCH("diam_init", k_diam_init, std::max(1, std::min((n + 255) / 256, sms * 4)), 256, 0, st, out, n);
   const int vblocks = (int)std::min<long long>((nv + 255) / 256, (long long)sms * 8);
-  RAD_LAUNCH("diam_hist", k_hist, vblocks, 256, 0, st, idx2, nv_dev, p, hist);
+  RAD_LAUNCH("diam_hist", k_hist, vblocks, 256, 0, st, idx2, nv_dev, rd, ro, p, hist);
   RAD_LAUNCH("diam_scan_part", k_xscan_part, (int)nparts, kScanBlock, 0, st, hist, K1, offs, parts);
   RAD_LAUNCH("diam_scan_top", k_xscan_top, 1, 1024, 0, st, parts, (int)nparts);
-  RAD_LAUNCH("diam_scatter", k_scatter, vblocks, 256, 0, st, idx2, vt, nv_dev, p, offs, parts, cursor, sorted);
-  RAD_LAUNCH("diam_setup", k_setup_problems, 1, 1024, 0, st, nv_dev, p, offs, parts, probs, tiles, ps, cnt);
-  RAD_LAUNCH("diam_tiles", k_tiles, sms * 4, 256, 0, st, probs, p, cnt, tiles);
-  RAD_LAUNCH("diam_tile_box", k_tile_box, sms * 8, 256, 0, st, sorted, tiles, cnt, box, rep);
-  RAD_LAUNCH("diam_seed", k_seed_rows, sms * 8, 256, 0, st, sorted, rep, p, tiles, cnt, ps);
-  RAD_LAUNCH("diam_cull", k_cull_rows, sms * 8, 256, 0, st, tiles, box, p, cnt, ps, work);
+  RAD_LAUNCH("diam_scatter", k_scatter, vblocks, 256, 0, st, idx2, vt, nv_dev, rd, ro, p, offs, parts, cursor, sorted);
+  RAD_LAUNCH("diam_setup", k_setup, sms * 4, 256, 0, st, rd, p, offs, parts, probs, tiles, ps, cnt);
+  RAD_LAUNCH("diam_tile_box", k_tile_box, sms * 8, 256, 0, st, sorted, tiles, p, cnt, box, rep);
+  RAD_LAUNCH("diam_seed", k_seed_rows, sms * 8, 256, 0, st, sorted, rep, p, rd, probs, tiles, cnt, ps);
+  RAD_LAUNCH("diam_cull", k_cull_rows, sms * 8, 256, 0, st, tiles, box, p, probs, cnt, ps, work);
   const int ctas = sms * tu.ctas_per_sm;
   if (tu.tile == 64) {
-    if (tu.threads == 64) RAD_TRY((launch_pairs<64, 64>(sorted, tiles, box, work, work2, p, cnt, ps, itemmax, cand, ctas, st)));
-    else RAD_TRY((launch_pairs<64, 128>(sorted, tiles, box, work, work2, p, cnt, ps, itemmax, cand, ctas, st)));
+    if (tu.threads == 64) RAD_TRY((launch_pairs<64, 64>(sorted, tiles, box, work, work2, p, rd, cnt, ps, itemmax, cand, ctas, st)));
+    else RAD_TRY((launch_pairs<64, 128>(sorted, tiles, box, work, work2, p, rd, cnt, ps, itemmax, cand, ctas, st)));
   } else if (tu.tile == 128) {
-    if (tu.threads == 64) RAD_TRY((launch_pairs<128, 64>(sorted, tiles, box, work, work2, p, cnt, ps, itemmax, cand, ctas, st)));
-    else if (tu.threads == 128) RAD_TRY((launch_pairs<128, 128>(sorted, tiles, box, work, work2, p, cnt, ps, itemmax, cand, ctas, st)));
-    else RAD_TRY((launch_pairs<128, 256>(sorted, tiles, box, work, work2, p, cnt, ps, itemmax, cand, ctas, st)));
+    if (tu.threads == 64) RAD_TRY((launch_pairs<128, 64>(sorted, tiles, box, work, work2, p, rd, cnt, ps, itemmax, cand, ctas, st)));
+    else if (tu.threads == 128) RAD_TRY((launch_pairs<128, 128>(sorted, tiles, box, work, work2, p, rd, cnt, ps, itemmax, cand, ctas, st)));
+    else RAD_TRY((launch_pairs<128, 256>(sorted, tiles, box, work, work2, p, rd, cnt, ps, itemmax, cand, ctas, st)));
   } else {
-    if (tu.threads == 128) RAD_TRY((launch_pairs<256, 128>(sorted, tiles, box, work, work2, p, cnt, ps, itemmax, cand, ctas, st)));
-    else RAD_TRY((launch_pairs<256, 256>(sorted, tiles, box, work, work2, p, cnt, ps, itemmax, cand, ctas, st)));
+    if (tu.threads == 128) RAD_TRY((launch_pairs<256, 128>(sorted, tiles, box, work, work2, p, rd, cnt, ps, itemmax, cand, ctas, st)));
+    else RAD_TRY((launch_pairs<256, 256>(sorted, tiles, box, work, work2, p, rd, cnt, ps, itemmax, cand, ctas, st)));
   }
-  RAD_LAUNCH("diam_confirm", k_confirm, sms * 4, 256, 0, st, sorted, idx2, vt, p, cnt, cand, ps);
-  RAD_LAUNCH("diam_tiebreak", k_tiebreak, sms * 4, 256, 0, st, sorted, idx2, vt, p, cnt, cand, ps, probs, out_dev,
-             status_dev);
+  RAD_LAUNCH("diam_confirm", k_confirm, sms * 4, 256, 0, st, sorted, idx2, vt, p, rd, cnt, cand, ps);
+  RAD_LAUNCH("diam_tiebreak", k_tiebreak, sms * 4, 256, 0, st, sorted, idx2, vt, p, rd, ro, cnt, cand, ps, probs, out,
+             stats);
   return RAD_OK;
 }
 

@@ -1,31 +1,38 @@
-// Marching cubes on a padded mask (paper Sec. 2, "Marching cubes fused
+// Marching cubes on padded masks (paper Sec. 2, "Marching cubes fused
 // parallel kernels"): every cube of the implicitly zero-padded grid is tested
 // against the iso level, crossing edges become vertices, the cube's case
 // selects its polygons, and the mesh volume and surface area are summed.
 //
+// Every kernel covers a whole batch of regions of interest (ROIs) in one
+// launch: the rows, bitset words and outputs of all ROIs are concatenated and
+// each item finds its ROI in a small device table (binary search over start
+// offsets).  A single mask is the one-ROI case.
+//
 // GB300 layout of the pass:
-//   k_pack   the mask (uint8 or float32) is read once, coalesced and
-//            vectorised (16-byte loads), and packed to one bit per voxel
-//            (32 voxels per word) with zero rows around it; the packed grid
-//            is 1/8 (1/32) of the input and stays in L2 for the passes below.
+//   k_pack   each mask is read once, coalesced and vectorised (16-byte loads),
+//            and packed to one bit per voxel (32 voxels per word) with zero
+//            rows around it; the packed grid is 1/8 of the input and stays in
+//            L2 for the passes below.
 //   k_count  one group of lanes per x-row (y, z): crossing-edge bits by XOR of
 //            neighbouring rows, counted with popc; active cubes by OR/AND of
-//            the four rows of a cube row; per-row vertex, triangle and voxel
-//            counts.
-//   k_scan_* chunked exclusive scan of the row counts (vertex and triangle
-//            ids follow the canonical (z, y, x, axis) order).
-//   k_rows   per row: writes the row's vertices (ids = row base + popc ranks)
-//            and a compact list of its active cubes with their triangle ids.
-//   k_cubes  one thread per active cube: vertex ids of its crossing edges
-//            (bitset words + per-word prefixes), its triangles, and the volume
-//            and area sums.  For a mask the volume is an exact int64 sum in
-//            half-voxel units (6V = det(diag(s/2)) * sum A.(B x C)) and the
-//            area comes from a per-case table and a per-case histogram, so
-//            both are deterministic; a soft map sums FP64 per triangle with a
-//            fixed-order reduction.
+//            the four rows of a cube row; per-row vertex, triangle, voxel and
+//            active-cube counts, and per-word vertex prefixes.
+//   k_scan_* chunked exclusive scan of the row counts over the whole batch:
+//            vertex and triangle ids follow the canonical (z, y, x, axis)
+//            order inside each ROI, ROIs one after the other.
+//   k_rows   per row: the row's vertices (ids = row base + popc ranks) and a
+//            compact list of its active cubes with their first triangle id.
+//   k_cubes  one thread per active cube: vertex ids of its crossing edges, its
+//            triangles, and the volume and area sums.  For a mask the volume
+//            is an exact int64 sum in half-voxel units
+//            (6V = det(diag(s/2)) * sum A.(B x C)) and the area comes from a
+//            per-case table and a per-ROI, per-case histogram, so both are
+//            deterministic; a soft map (one ROI) sums FP64 per triangle with
+//            a fixed-order reduction.
 #include <stdio.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "mc_tables.inc"
 #include "rad_internal.cuh"
@@ -36,6 +43,7 @@ namespace {
 
 constexpr int kScanChunk = 2048;  // rows per scan chunk (256 threads x 8)
 constexpr int kCubeBlocksPerSM = 2;
+constexpr int kCubeThreads = 256;
 
 // Per-case data of a binary mask for one spacing (built by k_binary_table).
 struct BinCase {
@@ -46,8 +54,29 @@ struct BinCase {
   double area2;                       // sum of twice the physical triangle areas
 };
 
-__device__ __forceinline__ const uint32_t* brow(const uint32_t* bits, const MeshDims& d, int y, int z) {
-  return bits + ((long long)(z + 1) * d.BY + (y + 1)) * d.W;
+// ROI of a global row / word: last ROI whose start is <= g.
+__device__ __forceinline__ int roi_of_row(const Roi* rois, int n, long long g) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (rois[mid].row0 <= g) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int roi_of_word(const Roi* rois, int n, long long g) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (rois[mid].word0 <= g) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ const uint32_t* brow(const uint32_t* bits, const Roi& r, int y, int z) {
+  return bits + r.word0 + ((long long)(z + 1) * r.BY + (y + 1)) * r.W;
 }
 
 __device__ __forceinline__ uint32_t ldw(const uint32_t* row, int w, int W) { return w < W ? row[w] : 0u; }
@@ -61,54 +90,44 @@ __device__ __forceinline__ uint32_t nz4(uint32_t v) {
   return (((t >> 7) * 0x00204081u) >> 21) & 0xFu;
 }
 
-__global__ void k_pack_u8(const uint8_t* __restrict__ mask, MeshDims d, bool vec16, uint32_t* __restrict__ bits) {
-  long long total = (long long)d.BY * d.BZ * d.W;
+// One thread per bitset word of the whole batch (padding rows included).
+template <bool SOFT>
+__global__ void k_pack(const Roi* __restrict__ rois, int n, long long total, uint32_t* __restrict__ bits) {
   for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
        id += (long long)gridDim.x * blockDim.x) {
-    int w = (int)(id % d.W);
-    long long br = id / d.W;
-    int y = (int)(br % d.BY) - 1, z = (int)(br / d.BY) - 1;
+    const Roi& r = rois[n == 1 ? 0 : roi_of_word(rois, n, id)];
+    const long long local = id - r.word0;
+    const int w = (int)(local % r.W);
+    const long long br = local / r.W;
+    const int y = (int)(br % r.BY) - 1, z = (int)(br / r.BY) - 1;
     uint32_t word = 0;
-    if (y >= 0 && y < d.ny && z >= 0 && z < d.nz) {
-      const uint8_t* row = mask + ((long long)z * d.ny + y) * d.nx;
-      int x0 = w * 32;
-      int n = min(32, d.nx - x0);
-      if (vec16 && n == 32) {
-        uint4 a = __ldg(reinterpret_cast<const uint4*>(row + x0));
-        uint4 b = __ldg(reinterpret_cast<const uint4*>(row + x0 + 16));
-        word = nz4(a.x) | (nz4(a.y) << 4) | (nz4(a.z) << 8) | (nz4(a.w) << 12) | (nz4(b.x) << 16) |
-               (nz4(b.y) << 20) | (nz4(b.z) << 24) | (nz4(b.w) << 28);
-      } else if (vec16 && n == 16) {
-        uint4 a = __ldg(reinterpret_cast<const uint4*>(row + x0));
-        word = nz4(a.x) | (nz4(a.y) << 4) | (nz4(a.z) << 8) | (nz4(a.w) << 12);
-      } else {
-        for (int i = 0; i < n; ++i) word |= (uint32_t)(row[x0 + i] != 0) << i;
-      }
-    }
-    bits[id] = word;
-  }
-}
-
-__global__ void k_pack_f32(const float* __restrict__ prob, MeshDims d, bool vec16, uint32_t* __restrict__ bits) {
-  long long total = (long long)d.BY * d.BZ * d.W;
-  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
-       id += (long long)gridDim.x * blockDim.x) {
-    int w = (int)(id % d.W);
-    long long br = id / d.W;
-    int y = (int)(br % d.BY) - 1, z = (int)(br / d.BY) - 1;
-    uint32_t word = 0;
-    if (y >= 0 && y < d.ny && z >= 0 && z < d.nz) {
-      const float* row = prob + ((long long)z * d.ny + y) * d.nx;
-      int x0 = w * 32;
-      int n = min(32, d.nx - x0);
-      if (vec16 && (n & 3) == 0) {
-        for (int i = 0; i < n; i += 4) {
-          float4 v = __ldg(reinterpret_cast<const float4*>(row + x0 + i));
-          word |= ((uint32_t)(v.x > 0.5f) << i) | ((uint32_t)(v.y > 0.5f) << (i + 1)) |
-                  ((uint32_t)(v.z > 0.5f) << (i + 2)) | ((uint32_t)(v.w > 0.5f) << (i + 3));
+    if (y >= 0 && y < r.ny && z >= 0 && z < r.nz) {
+      const int x0 = w * 32;
+      const int cnt = min(32, r.nx - x0);
+      if (!SOFT) {
+        const uint8_t* row = (const uint8_t*)r.data + ((long long)z * r.ny + y) * r.nx;
+        if (r.vec16 && cnt == 32) {
+          const uint4 a = __ldg(reinterpret_cast<const uint4*>(row + x0));
+          const uint4 b = __ldg(reinterpret_cast<const uint4*>(row + x0 + 16));
+          word = nz4(a.x) | (nz4(a.y) << 4) | (nz4(a.z) << 8) | (nz4(a.w) << 12) | (nz4(b.x) << 16) |
+                 (nz4(b.y) << 20) | (nz4(b.z) << 24) | (nz4(b.w) << 28);
+        } else if (r.vec16 && cnt == 16) {
+          const uint4 a = __ldg(reinterpret_cast<const uint4*>(row + x0));
+          word = nz4(a.x) | (nz4(a.y) << 4) | (nz4(a.z) << 8) | (nz4(a.w) << 12);
+        } else {
+          for (int i = 0; i < cnt; ++i) word |= (uint32_t)(row[x0 + i] != 0) << i;
         }
       } else {
-        for (int i = 0; i < n; ++i) word |= (uint32_t)(row[x0 + i] > 0.5f) << i;
+        const float* row = (const float*)r.data + ((long long)z * r.ny + y) * r.nx;
+        if (r.vec16 && (cnt & 3) == 0) {
+          for (int i = 0; i < cnt; i += 4) {
+            const float4 v = __ldg(reinterpret_cast<const float4*>(row + x0 + i));
+            word |= ((uint32_t)(v.x > 0.5f) << i) | ((uint32_t)(v.y > 0.5f) << (i + 1)) |
+                    ((uint32_t)(v.z > 0.5f) << (i + 2)) | ((uint32_t)(v.w > 0.5f) << (i + 3));
+          }
+        } else {
+          for (int i = 0; i < cnt; ++i) word |= (uint32_t)(row[x0 + i] > 0.5f) << i;
+        }
       }
     }
     bits[id] = word;
@@ -163,38 +182,55 @@ __device__ __forceinline__ int group_incl(int v, int sub, int L) {
   return v;
 }
 
-// One group of L lanes per row item (y, z) in [-1, ny-1] x [-1, nz-1]:
-//   counts = (vertices owned by row, triangles of cube row, inside voxels, active cubes)
+// Row item of a group: global row g, its ROI and (y, z) inside it.
+struct RowItem {
+  long long g;
+  int roi, y, z;
+  bool valid;
+};
+
+__device__ __forceinline__ RowItem row_item(const Roi* rois, int n, long long total_rows, long long g) {
+  RowItem it;
+  it.g = g;
+  it.valid = g < total_rows;
+  it.roi = it.valid ? (n == 1 ? 0 : roi_of_row(rois, n, g)) : 0;
+  const Roi& r = rois[it.roi];
+  const int local = it.valid ? (int)(g - r.row0) : 0;  // rows of one ROI < 2^31
+  it.y = it.valid ? local % (r.ny + 1) - 1 : -1;
+  it.z = it.valid ? local / (r.ny + 1) - 1 : -1;
+  return it;
+}
+
+// One group of L lanes per row item (y, z) in [-1, ny-1] x [-1, nz-1] of each ROI:
+//   counts = (vertices owned by the row, triangles of the cube row, inside voxels, active cubes)
 //   wpre[row][w] = vertices of the row owned by x < 32 w (row-local prefix)
-__global__ void k_count(const uint32_t* __restrict__ bits, MeshDims d, int L, int4* __restrict__ counts,
-                        int* __restrict__ wpre) {
+__global__ void k_count(const uint32_t* __restrict__ bits, const Roi* __restrict__ rois, int n, long long total_rows,
+                        int L, int Wc, int4* __restrict__ counts, int* __restrict__ wpre) {
   const int lane = threadIdx.x & 31, sub = lane % L, gpw = 32 / L;
   const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  const int Wc = d.W + ((L - d.W % L) % L);
-  for (long long base = warp * gpw; base < d.R; base += nwarps * gpw) {
-    const long long item = base + lane / L;
-    const bool valid = item < d.R;
-    const int item32 = valid ? (int)item : 0;  // R < 2^31 (dims <= 16383)
-    const int y = valid ? item32 % (d.ny + 1) - 1 : -1;
-    const int z = valid ? item32 / (d.ny + 1) - 1 : -1;
-    const uint32_t* R00 = brow(bits, d, y, z);
-    const uint32_t* R10 = brow(bits, d, y + 1, z);
-    const uint32_t* R01 = brow(bits, d, y, z + 1);
-    const uint32_t* R11 = brow(bits, d, y + 1, z + 1);
+  for (long long base = warp * gpw; base < total_rows; base += nwarps * gpw) {
+    const RowItem it = row_item(rois, n, total_rows, base + lane / L);
+    const Roi& r = rois[it.roi];
+    const int y = it.y, z = it.z, W = r.W;
+    const uint32_t* R00 = brow(bits, r, y, z);
+    const uint32_t* R10 = brow(bits, r, y + 1, z);
+    const uint32_t* R01 = brow(bits, r, y, z + 1);
+    const uint32_t* R11 = brow(bits, r, y + 1, z + 1);
     // owner x = -1 and cube x = -1 (corners cx = 1 at voxel x = 0)
-    const uint32_t a0 = ldw(R00, 0, d.W) & 1u, b0 = ldw(R10, 0, d.W) & 1u, c0 = ldw(R01, 0, d.W) & 1u,
-                   e0 = ldw(R11, 0, d.W) & 1u;
+    const uint32_t a0 = ldw(R00, 0, W) & 1u, b0 = ldw(R10, 0, W) & 1u, c0 = ldw(R01, 0, W) & 1u,
+                   e0 = ldw(R11, 0, W) & 1u;
     const int case_m1 = (int)((a0 << 1) | (b0 << 3) | (c0 << 5) | (e0 << 7));
     int carry = (int)a0;
     int nt = sub == 0 ? MC_CASE_NTRI[case_m1] : 0;
     int na = (sub == 0 && case_m1) ? 1 : 0;
     int nvox = 0;
+    const long long wbase = r.wpre0 + (it.g - r.row0) * (long long)W;
     for (int w = sub; w < Wc; w += L) {
-      const WordView v = word_view(R00, R10, R01, R11, w, d.W);
+      const WordView v = word_view(R00, R10, R01, R11, w, W);
       const int cnt = __popc(v.ex) + __popc(v.ey) + __popc(v.ez);
       const int incl = group_incl(cnt, sub, L);
-      if (valid && w < d.W) wpre[item * d.W + w] = carry + incl - cnt;
+      if (it.valid && w < W) wpre[wbase + w] = carry + incl - cnt;
       carry += __shfl_sync(0xffffffffu, incl, L - 1, L);
       if (y >= 0 && z >= 0) nvox += __popc(v.a);
       na += __popc(v.act);
@@ -206,83 +242,71 @@ __global__ void k_count(const uint32_t* __restrict__ bits, MeshDims d, int L, in
       nvox += __shfl_xor_sync(0xffffffffu, nvox, off, L);
       na += __shfl_xor_sync(0xffffffffu, na, off, L);
     }
-    if (valid && sub == 0) counts[item] = make_int4(carry, nt, nvox, na);
+    if (it.valid && sub == 0) counts[it.g] = make_int4(carry, nt, nvox, na);
   }
 }
 
 // ---- scan of row counts -------------------------------------------------------------
-// prefix[row] = chunk-local exclusive prefixes of (vertices, triangles, cubes);
+// prefix[row] = chunk-local exclusive prefixes of (vertices, triangles, cubes, voxels);
 // chunk[c] = totals of chunk c, turned into chunk offsets by k_scan_top.
 
 __global__ void k_scan_chunks(const int4* __restrict__ counts, long long R, long long* __restrict__ prefix,
                               long long* __restrict__ chunk) {
-  __shared__ long long sw[3][8], sx[8];
+  __shared__ long long sw[4][8];
   const long long beg = (long long)blockIdx.x * kScanChunk;
   constexpr int per = kScanChunk / 256;
-  long long own[3] = {0, 0, 0}, lx = 0;
+  long long own[4] = {0, 0, 0, 0};
   int4 c[per];
   for (int i = 0; i < per; ++i) {
     const long long r = beg + threadIdx.x * per + i;
     c[i] = r < R ? counts[r] : make_int4(0, 0, 0, 0);
-    own[0] += c[i].x; own[1] += c[i].y; own[2] += c[i].w; lx += c[i].z;
+    own[0] += c[i].x; own[1] += c[i].y; own[2] += c[i].w; own[3] += c[i].z;
   }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  long long inc[3] = {own[0], own[1], own[2]};
+  long long inc[4] = {own[0], own[1], own[2], own[3]};
   for (int off = 1; off < 32; off <<= 1)
-    for (int q = 0; q < 3; ++q) {
+    for (int q = 0; q < 4; ++q) {
       const long long o = __shfl_up_sync(0xffffffffu, inc[q], off);
       if (lane >= off) inc[q] += o;
     }
-  for (int off = 16; off > 0; off >>= 1) lx += __shfl_xor_sync(0xffffffffu, lx, off);
   if (lane == 31)
-    for (int q = 0; q < 3; ++q) sw[q][wid] = inc[q];
-  if (lane == 0) sx[wid] = lx;
+    for (int q = 0; q < 4; ++q) sw[q][wid] = inc[q];
   __syncthreads();
-  long long ex[3];
-  for (int q = 0; q < 3; ++q) {
+  long long ex[4];
+  for (int q = 0; q < 4; ++q) {
     long long wb = 0;
     for (int k = 0; k < wid; ++k) wb += sw[q][k];
     ex[q] = wb + inc[q] - own[q];
   }
   for (int i = 0; i < per; ++i) {
     const long long r = beg + threadIdx.x * per + i;
-    if (r < R) {
-      prefix[3 * r] = ex[0];
-      prefix[3 * r + 1] = ex[1];
-      prefix[3 * r + 2] = ex[2];
-    }
-    ex[0] += c[i].x; ex[1] += c[i].y; ex[2] += c[i].w;
+    if (r < R)
+      for (int q = 0; q < 4; ++q) prefix[4 * r + q] = ex[q];
+    ex[0] += c[i].x; ex[1] += c[i].y; ex[2] += c[i].w; ex[3] += c[i].z;
   }
-  if (threadIdx.x == 255) {
-    long long tx = 0;
-    for (int k = 0; k < 8; ++k) tx += sx[k];
-    chunk[4 * blockIdx.x] = ex[0];
-    chunk[4 * blockIdx.x + 1] = ex[1];
-    chunk[4 * blockIdx.x + 2] = ex[2];
-    chunk[4 * blockIdx.x + 3] = tx;
-  }
+  if (threadIdx.x == 255)
+    for (int q = 0; q < 4; ++q) chunk[4 * blockIdx.x + q] = ex[q];
 }
 
 __global__ void k_scan_top(long long* __restrict__ chunk, int nchunks, MeshTotals* __restrict__ tot) {
-  __shared__ long long sw[3][32], sx[32];
-  long long carry[3] = {0, 0, 0}, carry_x = 0;
+  __shared__ long long sw[4][32];
+  long long carry[4] = {0, 0, 0, 0};
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int base = 0; base < nchunks; base += blockDim.x) {
     const int c = base + threadIdx.x;
-    long long v[3] = {0, 0, 0}, x = 0;
-    if (c < nchunks) { v[0] = chunk[4 * c]; v[1] = chunk[4 * c + 1]; v[2] = chunk[4 * c + 2]; x = chunk[4 * c + 3]; }
-    long long inc[3] = {v[0], v[1], v[2]};
+    long long v[4] = {0, 0, 0, 0};
+    if (c < nchunks)
+      for (int q = 0; q < 4; ++q) v[q] = chunk[4 * c + q];
+    long long inc[4] = {v[0], v[1], v[2], v[3]};
     for (int off = 1; off < 32; off <<= 1)
-      for (int q = 0; q < 3; ++q) {
+      for (int q = 0; q < 4; ++q) {
         const long long o = __shfl_up_sync(0xffffffffu, inc[q], off);
         if (lane >= off) inc[q] += o;
       }
-    for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
     if (lane == 31)
-      for (int q = 0; q < 3; ++q) sw[q][wid] = inc[q];
-    if (lane == 0) sx[wid] = x;
+      for (int q = 0; q < 4; ++q) sw[q][wid] = inc[q];
     __syncthreads();
-    for (int q = 0; q < 3; ++q) {
+    for (int q = 0; q < 4; ++q) {
       long long wb = 0, bt = 0;
       for (int k = 0; k < nw; ++k) {
         if (k < wid) wb += sw[q][k];
@@ -291,19 +315,40 @@ __global__ void k_scan_top(long long* __restrict__ chunk, int nchunks, MeshTotal
       if (c < nchunks) chunk[4 * c + q] = carry[q] + wb + inc[q] - v[q];
       carry[q] += bt;
     }
-    for (int k = 0; k < nw; ++k) carry_x += sx[k];
     __syncthreads();
   }
   if (threadIdx.x == 0) {
     tot->nv = carry[0];
     tot->nt = carry[1];
     tot->na = carry[2];
-    tot->nvox = carry_x;
+    tot->nvox = carry[3];
   }
 }
 
+// q: 0 vertices, 1 triangles, 2 active cubes, 3 inside voxels
 __device__ __forceinline__ long long row_base(const long long* prefix, const long long* chunk, long long r, int q) {
-  return prefix[3 * r + q] + chunk[4 * (r / kScanChunk) + q];
+  return prefix[4 * r + q] + chunk[4 * (r / kScanChunk) + q];
+}
+
+// Per-ROI ranges of the batch's vertex, triangle and cube ids (one thread per ROI).
+__global__ void k_roi_ranges(const Roi* __restrict__ rois, int n, const long long* __restrict__ prefix,
+                             const long long* __restrict__ chunk, const MeshTotals* __restrict__ tot,
+                             RoiOut* __restrict__ out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const Roi& r = rois[i];
+    const bool last = i == n - 1;
+    const long long e = r.row0 + r.R;
+    RoiOut o = out[i];
+    o.v0 = row_base(prefix, chunk, r.row0, 0);
+    o.t0 = row_base(prefix, chunk, r.row0, 1);
+    o.c0 = row_base(prefix, chunk, r.row0, 2);
+    const long long x0 = row_base(prefix, chunk, r.row0, 3);
+    o.nv = (last ? tot->nv : row_base(prefix, chunk, e, 0)) - o.v0;
+    o.nt = (last ? tot->nt : row_base(prefix, chunk, e, 1)) - o.t0;
+    o.na = (last ? tot->na : row_base(prefix, chunk, e, 2)) - o.c0;
+    o.nvox = (last ? tot->nvox : row_base(prefix, chunk, e, 3)) - x0;
+    out[i] = o;
+  }
 }
 
 // ---- triangulation choice -----------------------------------------------------------
@@ -347,9 +392,10 @@ __device__ int select_candidate(int loop, const double (*w)[3], const double* sp
 //   tsum = sum of A . (B x C),
 // with A, B, C the local doubled positions (integers 0..2), and area2 = sum of
 // |cof(H) ((B - A) x (C - A))| with H = diag(s / 2).
-__global__ void k_binary_table(double sx, double sy, double sz, BinCase* __restrict__ tab) {
-  const int cs = blockIdx.x * blockDim.x + threadIdx.x;
-  if (cs >= 256) return;
+__global__ void k_binary_table(const double* __restrict__ spacings, BinCase* __restrict__ tabs) {
+  const int cs = threadIdx.x;
+  const double sx = spacings[3 * blockIdx.x], sy = spacings[3 * blockIdx.x + 1], sz = spacings[3 * blockIdx.x + 2];
+  BinCase* tab = tabs + 256 * blockIdx.x;
   const double sp[3] = {sx, sy, sz};
   double w[12][3];
   int lp[12][3];
@@ -392,68 +438,66 @@ __global__ void k_binary_table(double sx, double sy, double sz, BinCase* __restr
   tab[cs] = out;
 }
 
-// ---- rows: vertices and the active-cube list --------------------------------------------
-
-__device__ __forceinline__ float value_at(const float* p, const MeshDims& d, int x, int y, int z) {
-  if (x < 0 || y < 0 || z < 0 || x >= d.nx || y >= d.ny || z >= d.nz) return 0.0f;
-  return __ldg(p + ((long long)z * d.ny + y) * d.nx + x);
+__device__ __forceinline__ float value_at(const Roi& r, int x, int y, int z) {
+  if (x < 0 || y < 0 || z < 0 || x >= r.nx || y >= r.ny || z >= r.nz) return 0.0f;
+  return __ldg((const float*)r.data + ((long long)z * r.ny + y) * r.nx + x);
 }
 
 __device__ __forceinline__ double crossing_t(double v0, double v1) {
   return __ddiv_rn(__dsub_rn(0.5, v0), __dsub_rn(v1, v0));
 }
 
+// ---- rows: vertices and the active-cube list --------------------------------------------
+
 template <bool SOFT>
-__global__ void k_rows(const uint32_t* __restrict__ bits, const float* __restrict__ prob, MeshDims d, int L,
-                       const int4* __restrict__ counts, const int* __restrict__ wpre,
-                       const long long* __restrict__ prefix,
-                       const long long* __restrict__ chunk, int16_t* __restrict__ idx2, double* __restrict__ vt,
-                       int4* __restrict__ cubes, long long vcap, long long ccap, MeshTotals* __restrict__ tot) {
+__global__ void k_rows(const uint32_t* __restrict__ bits, const Roi* __restrict__ rois, int n, long long total_rows,
+                       int L, int Wc, const int4* __restrict__ counts, const int* __restrict__ wpre,
+                       const long long* __restrict__ prefix, const long long* __restrict__ chunk,
+                       int16_t* __restrict__ idx2, double* __restrict__ vt, int4* __restrict__ cubes, long long vcap,
+                       long long ccap, MeshTotals* __restrict__ tot) {
   const int lane = threadIdx.x & 31, sub = lane % L, gpw = 32 / L;
   const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  const int Wc = d.W + ((L - d.W % L) % L);
   unsigned int err = 0;
-  for (long long base = warp * gpw; base < d.R; base += nwarps * gpw) {
-    const long long item = base + lane / L;
-    const bool valid = item < d.R;
-    const int item32 = valid ? (int)item : 0;  // R < 2^31 (dims <= 16383)
-    const int y = valid ? item32 % (d.ny + 1) - 1 : -1;
-    const int z = valid ? item32 / (d.ny + 1) - 1 : -1;
+  for (long long base = warp * gpw; base < total_rows; base += nwarps * gpw) {
+    const RowItem it = row_item(rois, n, total_rows, base + lane / L);
     // rows without vertices and active cubes have nothing to write; skip
     // them when the whole warp agrees (the group scans below are warp-wide)
-    const int4 rc = valid ? counts[item] : make_int4(0, 0, 0, 0);
+    const int4 rc = it.valid ? counts[it.g] : make_int4(0, 0, 0, 0);
     if (__all_sync(0xffffffffu, rc.x == 0 && rc.w == 0)) continue;
-    const uint32_t* R00 = brow(bits, d, y, z);
-    const uint32_t* R10 = brow(bits, d, y + 1, z);
-    const uint32_t* R01 = brow(bits, d, y, z + 1);
-    const uint32_t* R11 = brow(bits, d, y + 1, z + 1);
-    const long long vb = valid ? row_base(prefix, chunk, item, 0) : 0;
-    const long long tb = valid ? row_base(prefix, chunk, item, 1) : 0;
-    const long long cb = valid ? row_base(prefix, chunk, item, 2) : 0;
-    const uint32_t a0 = ldw(R00, 0, d.W) & 1u, b0 = ldw(R10, 0, d.W) & 1u, c0 = ldw(R01, 0, d.W) & 1u,
-                   e0 = ldw(R11, 0, d.W) & 1u;
+    const Roi& r = rois[it.roi];
+    const int y = it.y, z = it.z, W = r.W;
+    const uint32_t* R00 = brow(bits, r, y, z);
+    const uint32_t* R10 = brow(bits, r, y + 1, z);
+    const uint32_t* R01 = brow(bits, r, y, z + 1);
+    const uint32_t* R11 = brow(bits, r, y + 1, z + 1);
+    const long long vb = it.valid ? row_base(prefix, chunk, it.g, 0) : 0;
+    const long long tb = it.valid ? row_base(prefix, chunk, it.g, 1) : 0;
+    const long long cb = it.valid ? row_base(prefix, chunk, it.g, 2) : 0;
+    const uint32_t a0 = ldw(R00, 0, W) & 1u, b0 = ldw(R10, 0, W) & 1u, c0 = ldw(R01, 0, W) & 1u,
+                   e0 = ldw(R11, 0, W) & 1u;
     const int case_m1 = (int)((a0 << 1) | (b0 << 3) | (c0 << 5) | (e0 << 7));
     const int nt_m1 = MC_CASE_NTRI[case_m1], na_m1 = case_m1 ? 1 : 0;
-    if (valid && sub == 0) {
+    if (it.valid && sub == 0) {
       if (a0) {  // owner x = -1: x-edge into voxel 0, the row's first vertex
         if (vb < vcap) {
           idx2[3 * vb] = (int16_t)(-1);
           idx2[3 * vb + 1] = (int16_t)(2 * y);
           idx2[3 * vb + 2] = (int16_t)(2 * z);
-          if (SOFT) vt[vb] = crossing_t(0.0, (double)value_at(prob, d, 0, y, z));
+          if (SOFT) vt[vb] = crossing_t(0.0, (double)value_at(r, 0, y, z));
         } else {
           err |= DEV_ERR_VCAP;
         }
       }
       if (na_m1) {
-        if (cb < ccap) cubes[cb] = make_int4(-1, (int)item, case_m1, (int)tb);
+        if (cb < ccap) cubes[cb] = make_int4(-1, (int)it.g, case_m1, (int)tb);
         else err |= DEV_ERR_TCAP;
       }
     }
     int carry_t = nt_m1, carry_c = na_m1;
+    const long long wbase = r.wpre0 + (it.g - r.row0) * (long long)W;
     for (int w = sub; w < Wc; w += L) {
-      const WordView v = word_view(R00, R10, R01, R11, w, d.W);
+      const WordView v = word_view(R00, R10, R01, R11, w, W);
       int tcnt = 0;
       for (uint32_t act = v.act; act; act &= act - 1)
         tcnt += MC_CASE_NTRI[cube_case(v.a, v.as, v.b, v.bs, v.c, v.cs, v.e, v.es, __ffs(act) - 1)];
@@ -463,9 +507,9 @@ __global__ void k_rows(const uint32_t* __restrict__ bits, const float* __restric
       long long cid = cb + carry_c + ci - ccnt;
       carry_t += __shfl_sync(0xffffffffu, ti, L - 1, L);
       carry_c += __shfl_sync(0xffffffffu, ci, L - 1, L);
-      if (!valid || w >= d.W) continue;
+      if (!it.valid || w >= W) continue;
       // vertices owned by (x, y, z), x in this word, canonical (x, axis) order
-      long long id = vb + wpre[item * d.W + w];
+      long long id = vb + wpre[wbase + w];
       for (uint32_t u = v.ex | v.ey | v.ez; u; u &= u - 1) {
         const int bit = __ffs(u) - 1, x = 32 * w + bit;
         for (int a = 0; a < 3; ++a) {
@@ -476,8 +520,8 @@ __global__ void k_rows(const uint32_t* __restrict__ bits, const float* __restric
             idx2[3 * id + 1] = (int16_t)(2 * y + (a == 1));
             idx2[3 * id + 2] = (int16_t)(2 * z + (a == 2));
             if (SOFT) {
-              const double v0 = (double)value_at(prob, d, x, y, z);
-              const double v1 = (double)value_at(prob, d, x + (a == 0), y + (a == 1), z + (a == 2));
+              const double v0 = (double)value_at(r, x, y, z);
+              const double v1 = (double)value_at(r, x + (a == 0), y + (a == 1), z + (a == 2));
               vt[id] = crossing_t(v0, v1);
             }
           } else {
@@ -490,7 +534,7 @@ __global__ void k_rows(const uint32_t* __restrict__ bits, const float* __restric
       for (uint32_t act = v.act; act; act &= act - 1) {
         const int bit = __ffs(act) - 1;
         const int cs = cube_case(v.a, v.as, v.b, v.bs, v.c, v.cs, v.e, v.es, bit);
-        if (cid < ccap) cubes[cid] = make_int4(32 * w + bit, (int)item, cs, (int)tid);
+        if (cid < ccap) cubes[cid] = make_int4(32 * w + bit, (int)it.g, cs, (int)tid);
         else err |= DEV_ERR_TCAP;
         ++cid;
         tid += MC_CASE_NTRI[cs];
@@ -507,27 +551,26 @@ __global__ void k_rows(const uint32_t* __restrict__ bits, const float* __restric
 struct OwnerWord {
   long long base;
   int pre;
-  uint32_t ex, ey;
-  uint32_t ez;
+  uint32_t ex, ey, ez;
 };
 
-__device__ __forceinline__ OwnerWord owner_word(const uint32_t* bits, const MeshDims& d, const int* wpre,
+__device__ __forceinline__ OwnerWord owner_word(const uint32_t* bits, const Roi& r, const int* wpre,
                                                 const long long* prefix, const long long* chunk, int xo, int yo,
                                                 int zo) {
   OwnerWord o;
-  const int r = (zo + 1) * (d.ny + 1) + (yo + 1);
-  o.base = row_base(prefix, chunk, r, 0);
+  const long long g = r.row0 + (long long)(zo + 1) * (r.ny + 1) + (yo + 1);
+  o.base = row_base(prefix, chunk, g, 0);
   if (xo < 0) {
     o.pre = 0; o.ex = o.ey = o.ez = 0u;
     return o;
   }
   const int w = xo >> 5;
-  const uint32_t* R0 = brow(bits, d, yo, zo);
-  const uint32_t b = R0[w], bn = ldw(R0, w + 1, d.W);
+  const uint32_t* R0 = brow(bits, r, yo, zo);
+  const uint32_t b = R0[w], bn = ldw(R0, w + 1, r.W);
   o.ex = b ^ shift1(b, bn);
-  o.ey = b ^ brow(bits, d, yo + 1, zo)[w];
-  o.ez = b ^ brow(bits, d, yo, zo + 1)[w];
-  o.pre = wpre[(long long)r * d.W + w];
+  o.ey = b ^ brow(bits, r, yo + 1, zo)[w];
+  o.ez = b ^ brow(bits, r, yo, zo + 1)[w];
+  o.pre = wpre[r.wpre0 + (g - r.row0) * (long long)r.W + w];
   return o;
 }
 
@@ -535,10 +578,10 @@ __device__ __forceinline__ int owner_rank(const OwnerWord& o, int xo, int a) {
   if (xo < 0) return 0;  // the x-edge into voxel 0 is the row's first vertex
   const int bit = xo & 31;
   const uint32_t low = (1u << bit) - 1u;
-  int r = o.pre + __popc(o.ex & low) + __popc(o.ey & low) + __popc(o.ez & low);
-  if (a >= 1) r += (o.ex >> bit) & 1u;
-  if (a >= 2) r += (o.ey >> bit) & 1u;
-  return r;
+  int rk = o.pre + __popc(o.ex & low) + __popc(o.ey & low) + __popc(o.ez & low);
+  if (a >= 1) rk += (o.ex >> bit) & 1u;
+  if (a >= 2) rk += (o.ey >> bit) & 1u;
+  return rk;
 }
 
 // Local edge e = (corner, axis) in canonical (cz, cy, cx, axis) order.
@@ -546,164 +589,185 @@ __device__ __forceinline__ int edge_corner(int e) {
   return e < 3 ? 0 : (e < 5 ? 1 : (e < 7 ? 2 : (e < 8 ? 3 : (e < 10 ? 4 : (e < 11 ? 5 : 6)))));
 }
 __device__ __forceinline__ int edge_axis(int e) {
-  constexpr unsigned long long kAxes = 0ull | (0ull << 0) | (1ull << 2) | (2ull << 4) | (1ull << 6) | (2ull << 8) |
+  constexpr unsigned long long kAxes = (0ull << 0) | (1ull << 2) | (2ull << 4) | (1ull << 6) | (2ull << 8) |
                                       (0ull << 10) | (2ull << 12) | (2ull << 14) | (0ull << 16) | (1ull << 18) |
                                       (1ull << 20) | (0ull << 22);
   return (int)((kAxes >> (2 * e)) & 3ull);
 }
 
-constexpr int kCubeThreads = 256;
-
 template <bool SOFT>
-__global__ void __launch_bounds__(kCubeThreads) k_cubes(const uint32_t* __restrict__ bits, const float* __restrict__ prob,
-                                                        MeshDims d, double sx, double sy, double sz,
-                                                        const int* __restrict__ wpre, const long long* __restrict__ prefix,
+__global__ void __launch_bounds__(kCubeThreads) k_cubes(const uint32_t* __restrict__ bits, const Roi* __restrict__ rois,
+                                                        int n, const int* __restrict__ wpre,
+                                                        const long long* __restrict__ prefix,
                                                         const long long* __restrict__ chunk,
                                                         const int4* __restrict__ cubes, const BinCase* __restrict__ tab,
                                                         int32_t* __restrict__ tri, long long ccap, long long tcap,
-                                                        MeshTotals* __restrict__ tot,
+                                                        MeshTotals* __restrict__ tot, RoiOut* __restrict__ out,
                                                         unsigned long long* __restrict__ case_hist,
                                                         double* __restrict__ partial) {
-  __shared__ unsigned int s_hist[256];
-  if (!SOFT)
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) s_hist[i] = 0;
-  __syncthreads();
   const long long ncubes = min(tot->na, ccap);
-  const double sp[3] = {sx, sy, sz};
-  const int nn[3] = {d.nx, d.ny, d.nz};
   long long vsum = 0;
   double acc_v6 = 0.0, acc_a2 = 0.0;
   unsigned int err = 0;
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < ncubes;
-       k += (long long)gridDim.x * blockDim.x) {
-    const int4 cu = cubes[k];
-    const int x = cu.x, cs = cu.z;
-    const int y = cu.y % (d.ny + 1) - 1, z = cu.y / (d.ny + 1) - 1;
-    const unsigned int emask = MC_CASE_EDGES[cs];
-    // owner rows (cy, cz) at the word of x (cx = 0) or of x + 1 (cx = 1),
-    // each loaded once per cube
-    OwnerWord ow[8];
-    unsigned int have = 0;
-    int vid[12];
-    double P[12][3], wl[12][3];
+  const int lane = threadIdx.x & 31;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  // warp-uniform loop: lanes past the end take part in the aggregation below
+  for (long long k0 = blockIdx.x * (long long)blockDim.x + threadIdx.x - lane; k0 < ncubes; k0 += stride) {
+    const long long k = k0 + lane;
+    const bool valid = k < ncubes;
+    const int4 cu = valid ? cubes[k] : make_int4(0, 0, 0, 0);
+    const int roi = valid ? (n == 1 ? 0 : roi_of_row(rois, n, cu.y)) : 0;
+    int cs = cu.z;
+    if (valid) {
+      const Roi& r = rois[roi];
+      const int x = cu.x;
+      const int local = (int)(cu.y - r.row0);
+      const int y = local % (r.ny + 1) - 1, z = local / (r.ny + 1) - 1;
+      const double sp[3] = {r.sx, r.sy, r.sz};
+      const int nn[3] = {r.nx, r.ny, r.nz};
+      const unsigned int emask = MC_CASE_EDGES[cs];
+      // owner rows (cy, cz) at the word of x (cx = 0) or of x + 1 (cx = 1), each loaded once
+      OwnerWord ow[8];
+      unsigned int have = 0;
+      int vid[12];
+      double P[12][3], wl[12][3];
 #pragma unroll
-    for (int e = 0; e < 12; ++e) {
-      if (!((emask >> e) & 1u)) continue;
-      const int c = edge_corner(e), a = edge_axis(e);
-      const int cx = c & 1, cy = (c >> 1) & 1, cz = (c >> 2) & 1;
-      const int slot = cz * 4 + cy * 2 + cx;
-      const int g[3] = {x + cx, y + cy, z + cz};
-      if (!((have >> slot) & 1u)) {
-        ow[slot] = owner_word(bits, d, wpre, prefix, chunk, g[0], g[1], g[2]);
-        have |= 1u << slot;
-      }
-      vid[e] = (int)(ow[slot].base + owner_rank(ow[slot], g[0], a));
-      if (SOFT) {
-        const double v0 = (double)value_at(prob, d, g[0], g[1], g[2]);
-        const double v1 = (double)value_at(prob, d, g[0] + (a == 0), g[1] + (a == 1), g[2] + (a == 2));
-        const double t = crossing_t(v0, v1);
-        for (int q = 0; q < 3; ++q) {
-          P[e][q] = ((double)g[q] - 0.5 * (double)(nn[q] - 1) + (q == a ? t : 0.0)) * sp[q];
-          wl[e][q] = __dmul_rn(__dadd_rn((double)((c >> q) & 1), q == a ? t : 0.0), sp[q]);
+      for (int e = 0; e < 12; ++e) {
+        if (!((emask >> e) & 1u)) continue;
+        const int c = edge_corner(e), a = edge_axis(e);
+        const int cx = c & 1, cy = (c >> 1) & 1, cz = (c >> 2) & 1;
+        const int slot = cz * 4 + cy * 2 + cx;
+        const int g[3] = {x + cx, y + cy, z + cz};
+        if (!((have >> slot) & 1u)) {
+          ow[slot] = owner_word(bits, r, wpre, prefix, chunk, g[0], g[1], g[2]);
+          have |= 1u << slot;
+        }
+        vid[e] = (int)(ow[slot].base + owner_rank(ow[slot], g[0], a));
+        if (SOFT) {
+          const double v0 = (double)value_at(r, g[0], g[1], g[2]);
+          const double v1 = (double)value_at(r, g[0] + (a == 0), g[1] + (a == 1), g[2] + (a == 2));
+          const double t = crossing_t(v0, v1);
+          for (int q = 0; q < 3; ++q) {
+            P[e][q] = ((double)g[q] - 0.5 * (double)(nn[q] - 1) + (q == a ? t : 0.0)) * sp[q];
+            wl[e][q] = __dmul_rn(__dadd_rn((double)((c >> q) & 1), q == a ? t : 0.0), sp[q]);
+          }
         }
       }
-    }
-    long long tid = cu.w;
-    if (SOFT) {
-      for (int l = MC_CASE_LOOP_BEGIN[cs]; l < MC_CASE_LOOP_BEGIN[cs + 1]; ++l) {
-        const int cand = select_candidate(l, wl, sp);
-        const int tb2 = MC_CAND_TRI_BEGIN[cand];
-        for (int t = 0; t < MC_LOOP_K[l] - 2; ++t, ++tid) {
-          const int e0 = MC_CAND_TRIPLES[3 * (tb2 + t)], e1 = MC_CAND_TRIPLES[3 * (tb2 + t) + 1],
-                    e2 = MC_CAND_TRIPLES[3 * (tb2 + t) + 2];
+      long long tid = cu.w;
+      if (SOFT) {
+        for (int l = MC_CASE_LOOP_BEGIN[cs]; l < MC_CASE_LOOP_BEGIN[cs + 1]; ++l) {
+          const int cand = select_candidate(l, wl, sp);
+          const int tb2 = MC_CAND_TRI_BEGIN[cand];
+          for (int t = 0; t < MC_LOOP_K[l] - 2; ++t, ++tid) {
+            const int e0 = MC_CAND_TRIPLES[3 * (tb2 + t)], e1 = MC_CAND_TRIPLES[3 * (tb2 + t) + 1],
+                      e2 = MC_CAND_TRIPLES[3 * (tb2 + t) + 2];
+            if (tid < tcap) {
+              tri[3 * tid] = vid[e0];
+              tri[3 * tid + 1] = vid[e1];
+              tri[3 * tid + 2] = vid[e2];
+            } else {
+              err |= DEV_ERR_TCAP;
+            }
+            const double* A = P[e0];
+            const double* B = P[e1];
+            const double* C = P[e2];
+            acc_v6 += A[0] * (B[1] * C[2] - B[2] * C[1]) + A[1] * (B[2] * C[0] - B[0] * C[2]) +
+                      A[2] * (B[0] * C[1] - B[1] * C[0]);
+            const double ux = B[0] - A[0], uy = B[1] - A[1], uz = B[2] - A[2];
+            const double vx = C[0] - A[0], vy = C[1] - A[1], vz = C[2] - A[2];
+            const double nx = uy * vz - uz * vy, ny = uz * vx - ux * vz, nz = ux * vy - uy * vx;
+            acc_a2 += sqrt(nx * nx + ny * ny + nz * nz);
+          }
+        }
+      } else {
+        const BinCase& bc = tab[r.tab * 256 + cs];
+        for (int t = 0; t < bc.ntri; ++t, ++tid) {
           if (tid < tcap) {
-            tri[3 * tid] = vid[e0];
-            tri[3 * tid + 1] = vid[e1];
-            tri[3 * tid + 2] = vid[e2];
+            tri[3 * tid] = vid[bc.tri[t][0]];
+            tri[3 * tid + 1] = vid[bc.tri[t][1]];
+            tri[3 * tid + 2] = vid[bc.tri[t][2]];
           } else {
             err |= DEV_ERR_TCAP;
           }
-          const double* A = P[e0];
-          const double* B = P[e1];
-          const double* C = P[e2];
-          acc_v6 += A[0] * (B[1] * C[2] - B[2] * C[1]) + A[1] * (B[2] * C[0] - B[0] * C[2]) +
-                    A[2] * (B[0] * C[1] - B[1] * C[0]);
-          const double ux = B[0] - A[0], uy = B[1] - A[1], uz = B[2] - A[2];
-          const double vx = C[0] - A[0], vy = C[1] - A[1], vz = C[2] - A[2];
-          const double nx = uy * vz - uz * vy, ny = uz * vx - ux * vz, nz = ux * vy - uy * vx;
-          acc_a2 += sqrt(nx * nx + ny * ny + nz * nz);
         }
+        // exact volume: positions in half-voxel units relative to the padded-box
+        // centre, P = o + local; sum A.(B x C) = o . nsum + tsum
+        const long long ox = 2LL * x - (r.nx - 1), oy = 2LL * y - (r.ny - 1), oz = 2LL * z - (r.nz - 1);
+        vsum = ox * bc.nsum[0] + oy * bc.nsum[1] + oz * bc.nsum[2] + bc.tsum;
       }
-    } else {
-      const BinCase& bc = tab[cs];
-      for (int t = 0; t < bc.ntri; ++t, ++tid) {
-        if (tid < tcap) {
-          tri[3 * tid] = vid[bc.tri[t][0]];
-          tri[3 * tid + 1] = vid[bc.tri[t][1]];
-          tri[3 * tid + 2] = vid[bc.tri[t][2]];
-        } else {
-          err |= DEV_ERR_TCAP;
-        }
-      }
-      // exact volume: positions in half-voxel units relative to the padded-box
-      // centre, P = o + local; sum A.(B x C) = o . nsum + tsum
-      const long long ox = 2LL * x - (d.nx - 1), oy = 2LL * y - (d.ny - 1), oz = 2LL * z - (d.nz - 1);
-      vsum += ox * bc.nsum[0] + oy * bc.nsum[1] + oz * bc.nsum[2] + bc.tsum;
-      atomicAdd(&s_hist[cs], 1u);
+    }
+    if (!SOFT) {
+      // lanes of one ROI add their volume sums with one atomic; lanes of one
+      // (ROI, case) add their count with one atomic
+      // |vsum| of one cube < 5e6, so a warp's sum fits in 32 bits
+      const unsigned int same_roi = __match_any_sync(0xffffffffu, valid ? roi : -1);
+      const int vs = __reduce_add_sync(same_roi, (int)vsum);
+      if (valid && lane == __ffs(same_roi) - 1 && vs)
+        atomicAdd((unsigned long long*)&out[roi].vsum, (unsigned long long)(long long)vs);
+      const long long key = valid ? (long long)roi * 256 + cs : -1;
+      const unsigned int same_case = __match_any_sync(0xffffffffu, key);
+      if (valid && lane == __ffs(same_case) - 1) atomicAdd(&case_hist[key], (unsigned long long)__popc(same_case));
+      vsum = 0;
     }
   }
-  // block reduction (fixed order), then the last CTA finishes
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (err) atomicOr(&tot->status, err);
+  if (!SOFT) return;
+  // soft map (one ROI): fixed-order block reduction, then the last CTA finishes
+  const int wid = threadIdx.x >> 5;
   for (int off = 16; off > 0; off >>= 1) {
-    vsum += __shfl_xor_sync(0xffffffffu, vsum, off);
     acc_v6 += __shfl_xor_sync(0xffffffffu, acc_v6, off);
     acc_a2 += __shfl_xor_sync(0xffffffffu, acc_a2, off);
-    err |= __shfl_xor_sync(0xffffffffu, err, off);
   }
-  __shared__ long long s_vs[kCubeThreads / 32];
   __shared__ double s_v6[kCubeThreads / 32], s_a2[kCubeThreads / 32];
-  __shared__ unsigned int s_err[kCubeThreads / 32];
   __shared__ bool last;
-  if (lane == 0) { s_vs[wid] = vsum; s_v6[wid] = acc_v6; s_a2[wid] = acc_a2; s_err[wid] = err; }
+  if (lane == 0) { s_v6[wid] = acc_v6; s_a2[wid] = acc_a2; }
   __syncthreads();
-  if (!SOFT)
-    for (int i = threadIdx.x; i < 256; i += blockDim.x)
-      if (s_hist[i]) atomicAdd(&case_hist[i], (unsigned long long)s_hist[i]);
   if (threadIdx.x == 0) {
-    long long bv = 0;
     double b6 = 0.0, b2 = 0.0;
-    unsigned int be = 0;
-    for (int k2 = 0; k2 < kCubeThreads / 32; ++k2) { bv += s_vs[k2]; b6 += s_v6[k2]; b2 += s_a2[k2]; be |= s_err[k2]; }
-    if (!SOFT && bv) atomicAdd((unsigned long long*)&tot->vsum, (unsigned long long)bv);
+    for (int k2 = 0; k2 < kCubeThreads / 32; ++k2) { b6 += s_v6[k2]; b2 += s_a2[k2]; }
     partial[2 * blockIdx.x] = b6;
     partial[2 * blockIdx.x + 1] = b2;
-    if (be) atomicOr(&tot->status, be);
     __threadfence();
     last = atomicAdd(&tot->done_ctas, 1u) == gridDim.x - 1;
   }
   __syncthreads();
   if (last && threadIdx.x == 0) {
     __threadfence();
-    if (SOFT) {
-      double v = 0.0, a = 0.0;
-      for (unsigned int b = 0; b < gridDim.x; ++b) {
-        v += __ldcg(&partial[2 * b]);
-        a += __ldcg(&partial[2 * b + 1]);
-      }
-      tot->vol6 = v;
-      tot->area2 = a;
-    } else {
-      // V = det(diag(s / 2)) * sum / 6;  A = sum over cases of count * area of the case
-      const double h3 = (0.5 * sx) * (0.5 * sy) * (0.5 * sz);
-      tot->vol6 = (double)__ldcg((const long long*)&tot->vsum) * h3;
-      double a = 0.0;
-      for (int c = 0; c < 256; ++c) {
-        const unsigned long long n = __ldcg(&case_hist[c]);
-        if (n) a += (double)n * tab[c].area2;
-      }
-      tot->area2 = a;
+    double v = 0.0, a = 0.0;
+    for (unsigned int b = 0; b < gridDim.x; ++b) {
+      v += __ldcg(&partial[2 * b]);
+      a += __ldcg(&partial[2 * b + 1]);
     }
+    out[0].vol6 = v;
+    out[0].area2 = a;
     tot->done_ctas = 0;
+  }
+}
+
+// Mask volume and area per ROI (one block per ROI, fixed order):
+//   6V = det(diag(s / 2)) * vsum,  2A = sum over cases of count * area2 of the case.
+__global__ void k_mask_totals(const Roi* __restrict__ rois, int n, const BinCase* __restrict__ tab,
+                              const unsigned long long* __restrict__ case_hist, RoiOut* __restrict__ out) {
+  __shared__ double s[256];
+  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+    const Roi& r = rois[i];
+    double a = 0.0;
+    for (int c = threadIdx.x; c < 256; c += blockDim.x) {
+      const unsigned long long cnt = case_hist[(long long)i * 256 + c];
+      if (cnt) a += (double)cnt * tab[r.tab * 256 + c].area2;
+    }
+    s[threadIdx.x] = a;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+      if ((int)threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      const double h3 = (0.5 * r.sx) * (0.5 * r.sy) * (0.5 * r.sz);
+      out[i].vol6 = (double)out[i].vsum * h3;
+      out[i].area2 = s[0];
+    }
+    __syncthreads();
   }
 }
 
@@ -715,89 +779,114 @@ int group_lanes(int W) {
 
 }  // namespace
 
-MeshDims make_dims(const int64_t dims[3]) {
-  MeshDims d;
-  d.nx = (int)dims[0];
-  d.ny = (int)dims[1];
-  d.nz = (int)dims[2];
-  d.W = (d.nx + 31) / 32;
-  d.BY = d.ny + 3;
-  d.BZ = d.nz + 3;
-  d.R = (long long)(d.ny + 1) * (d.nz + 1);
-  return d;
-}
+// ---- host ---------------------------------------------------------------------------
 
-rad_status mesh_count(const void* data, bool soft, const MeshDims& d, MeshScratch& s, MeshTotals* tot,
-                      cudaStream_t st) {
-  const long long words = (long long)d.BY * d.BZ * d.W;
-  const long long nchunks = (d.R + kScanChunk - 1) / kScanChunk;
-  RAD_TRY(s.bits.reserve(sizeof(uint32_t) * words));
-  RAD_TRY(s.counts.reserve(sizeof(int4) * d.R));
-  RAD_TRY(s.wpre.reserve(sizeof(int) * d.R * d.W));
-  RAD_TRY(s.prefix.reserve(sizeof(long long) * 3 * d.R));
-  RAD_TRY(s.chunk.reserve(sizeof(long long) * 4 * nchunks));
-  RAD_TRY(s.hist.reserve(sizeof(unsigned long long) * 256));
-  RAD_TRY(s.partial.reserve(sizeof(double) * 2 * num_sms() * kCubeBlocksPerSM));
-  RAD_CUDA(cudaMemsetAsync(tot, 0, sizeof(MeshTotals), st));
-  RAD_CUDA(cudaMemsetAsync(s.hist.p, 0, sizeof(unsigned long long) * 256, st));
-  const int sms = num_sms();
-  const bool vec16 = soft ? ((d.nx % 4) == 0 && (((uintptr_t)data) & 15) == 0)
-                          : ((d.nx % 16) == 0 && (((uintptr_t)data) & 15) == 0);
-  const int pack_blocks = (int)std::min<long long>((words + 255) / 256, (long long)sms * 16);
-  if (soft)
-    RAD_LAUNCH("mc_pack_f32", k_pack_f32, pack_blocks, 256, 0, st, (const float*)data, d, vec16,
-               s.bits.as<uint32_t>());
-  else
-    RAD_LAUNCH("mc_pack_u8", k_pack_u8, pack_blocks, 256, 0, st, (const uint8_t*)data, d, vec16,
-               s.bits.as<uint32_t>());
-  const int L = group_lanes(d.W);
-  const long long warps_needed = (d.R + (32 / L) - 1) / (32 / L);
-  const int rblocks = (int)std::max<long long>(1, std::min<long long>((warps_needed + 7) / 8, (long long)sms * 8));
-  RAD_LAUNCH("mc_count", k_count, rblocks, 256, 0, st, s.bits.as<uint32_t>(), d, L, s.counts.as<int4>(),
-             s.wpre.as<int>());
-  RAD_LAUNCH("mc_scan_chunks", k_scan_chunks, (int)nchunks, 256, 0, st, s.counts.as<int4>(), d.R,
-             s.prefix.as<long long>(), s.chunk.as<long long>());
-  RAD_LAUNCH("mc_scan_top", k_scan_top, 1, 1024, 0, st, s.chunk.as<long long>(), (int)nchunks, tot);
+rad_status mesh_tables(const double* spacings_host, int n_tabs, MeshScratch& s, cudaStream_t st) {
+  RAD_TRY(s.bintab.reserve(sizeof(BinCase) * 256 * std::max(n_tabs, 1)));
+  RAD_TRY(s.tabsp.reserve(sizeof(double) * 3 * std::max(n_tabs, 1)));
+  RAD_CUDA(cudaMemcpyAsync(s.tabsp.p, spacings_host, sizeof(double) * 3 * n_tabs, cudaMemcpyHostToDevice, st));
+  RAD_LAUNCH("mc_binary_table", k_binary_table, n_tabs, 256, 0, st, s.tabsp.as<double>(), s.bintab.as<BinCase>());
   return RAD_OK;
 }
 
-rad_status mesh_emit(const void* data, bool soft, const MeshDims& d, const double sp[3], MeshScratch& s,
-                     MeshTotals* tot, int16_t* idx2, double* vt, int32_t* tri, long long vcap, long long tcap,
-                     cudaStream_t st) {
-  if (!soft) {
-    RAD_TRY(s.bintab.reserve(sizeof(BinCase) * 256));
-    if (!s.tab_valid || s.tab_spacing[0] != sp[0] || s.tab_spacing[1] != sp[1] || s.tab_spacing[2] != sp[2]) {
-      RAD_LAUNCH("mc_binary_table", k_binary_table, 1, 256, 0, st, sp[0], sp[1], sp[2], s.bintab.as<BinCase>());
-      s.tab_valid = true;
-      for (int k = 0; k < 3; ++k) s.tab_spacing[k] = sp[k];
-    }
-  }
+rad_status mesh_count(const MeshBatch& b, MeshScratch& s, MeshTotals* tot, RoiOut* out, cudaStream_t st) {
+  const long long nchunks = (b.rows + kScanChunk - 1) / kScanChunk;
+  RAD_TRY(s.bits.reserve(sizeof(uint32_t) * b.words));
+  RAD_TRY(s.counts.reserve(sizeof(int4) * b.rows));
+  RAD_TRY(s.wpre.reserve(sizeof(int) * b.wpre));
+  RAD_TRY(s.prefix.reserve(sizeof(long long) * 4 * b.rows));
+  RAD_TRY(s.chunk.reserve(sizeof(long long) * 4 * nchunks));
+  RAD_TRY(s.hist.reserve(sizeof(unsigned long long) * 256 * b.n));
+  RAD_TRY(s.partial.reserve(sizeof(double) * 2 * num_sms() * kCubeBlocksPerSM));
+  RAD_CUDA(cudaMemsetAsync(tot, 0, sizeof(MeshTotals), st));
+  RAD_CUDA(cudaMemsetAsync(out, 0, sizeof(RoiOut) * b.n, st));
+  RAD_CUDA(cudaMemsetAsync(s.hist.p, 0, sizeof(unsigned long long) * 256 * b.n, st));
+  const int sms = num_sms();
+  const int pack_blocks = (int)std::max<long long>(1, std::min<long long>((b.words + 255) / 256, (long long)sms * 16));
+  if (b.soft)
+    RAD_LAUNCH("mc_pack_f32", k_pack<true>, pack_blocks, 256, 0, st, b.rois, b.n, b.words, s.bits.as<uint32_t>());
+  else
+    RAD_LAUNCH("mc_pack_u8", k_pack<false>, pack_blocks, 256, 0, st, b.rois, b.n, b.words, s.bits.as<uint32_t>());
+  const long long warps_needed = (b.rows + (32 / b.L) - 1) / (32 / b.L);
+  const int rblocks = (int)std::max<long long>(1, std::min<long long>((warps_needed + 7) / 8, (long long)sms * 8));
+  RAD_LAUNCH("mc_count", k_count, rblocks, 256, 0, st, s.bits.as<uint32_t>(), b.rois, b.n, b.rows, b.L, b.Wc,
+             s.counts.as<int4>(), s.wpre.as<int>());
+  RAD_LAUNCH("mc_scan_chunks", k_scan_chunks, (int)nchunks, 256, 0, st, s.counts.as<int4>(), b.rows,
+             s.prefix.as<long long>(), s.chunk.as<long long>());
+  RAD_LAUNCH("mc_scan_top", k_scan_top, 1, 1024, 0, st, s.chunk.as<long long>(), (int)nchunks, tot);
+  RAD_LAUNCH("mc_roi_ranges", k_roi_ranges, (b.n + 255) / 256, 256, 0, st, b.rois, b.n, s.prefix.as<long long>(),
+             s.chunk.as<long long>(), tot, out);
+  return RAD_OK;
+}
+
+rad_status mesh_emit(const MeshBatch& b, MeshScratch& s, MeshTotals* tot, RoiOut* out, int16_t* idx2, double* vt,
+                     int32_t* tri, long long vcap, long long tcap, cudaStream_t st) {
   // every active cube has at least one triangle: the cube list fits in tcap
   const long long ccap = std::max<long long>(tcap, 1);
   RAD_TRY(s.cubes.reserve(sizeof(int4) * ccap));
   const int sms = num_sms();
-  const int L = group_lanes(d.W);
-  const long long warps_needed = (d.R + (32 / L) - 1) / (32 / L);
+  const long long warps_needed = (b.rows + (32 / b.L) - 1) / (32 / b.L);
   const int rblocks = (int)std::max<long long>(1, std::min<long long>((warps_needed + 7) / 8, (long long)sms * 8));
   const int cblocks = sms * kCubeBlocksPerSM;
-  if (soft) {
-    RAD_LAUNCH("mc_rows_soft", k_rows<true>, rblocks, 256, 0, st, s.bits.as<uint32_t>(), (const float*)data, d, L,
-               s.counts.as<int4>(), s.wpre.as<int>(), s.prefix.as<long long>(), s.chunk.as<long long>(), idx2, vt, s.cubes.as<int4>(),
-               vcap, ccap, tot);
-    RAD_LAUNCH("mc_cubes_soft", k_cubes<true>, cblocks, kCubeThreads, 0, st, s.bits.as<uint32_t>(),
-               (const float*)data, d, sp[0], sp[1], sp[2], s.wpre.as<int>(), s.prefix.as<long long>(),
-               s.chunk.as<long long>(), s.cubes.as<int4>(), (const BinCase*)nullptr, tri, ccap, tcap, tot,
-               s.hist.as<unsigned long long>(), s.partial.as<double>());
-  } else {
-    RAD_LAUNCH("mc_rows", k_rows<false>, rblocks, 256, 0, st, s.bits.as<uint32_t>(), (const float*)nullptr, d, L,
-               s.counts.as<int4>(), s.wpre.as<int>(), s.prefix.as<long long>(), s.chunk.as<long long>(), idx2, (double*)nullptr,
-               s.cubes.as<int4>(), vcap, ccap, tot);
-    RAD_LAUNCH("mc_cubes", k_cubes<false>, cblocks, kCubeThreads, 0, st, s.bits.as<uint32_t>(), (const float*)nullptr,
-               d, sp[0], sp[1], sp[2], s.wpre.as<int>(), s.prefix.as<long long>(), s.chunk.as<long long>(),
-               s.cubes.as<int4>(), s.bintab.as<BinCase>(), tri, ccap, tcap, tot, s.hist.as<unsigned long long>(),
+  if (b.soft) {
+    RAD_LAUNCH("mc_rows_soft", k_rows<true>, rblocks, 256, 0, st, s.bits.as<uint32_t>(), b.rois, b.n, b.rows, b.L,
+               b.Wc, s.counts.as<int4>(), s.wpre.as<int>(), s.prefix.as<long long>(), s.chunk.as<long long>(), idx2,
+               vt, s.cubes.as<int4>(), vcap, ccap, tot);
+    RAD_LAUNCH("mc_cubes_soft", k_cubes<true>, cblocks, kCubeThreads, 0, st, s.bits.as<uint32_t>(), b.rois, b.n,
+               s.wpre.as<int>(), s.prefix.as<long long>(), s.chunk.as<long long>(), s.cubes.as<int4>(),
+               (const BinCase*)nullptr, tri, ccap, tcap, tot, out, s.hist.as<unsigned long long>(),
                s.partial.as<double>());
+  } else {
+    RAD_LAUNCH("mc_rows", k_rows<false>, rblocks, 256, 0, st, s.bits.as<uint32_t>(), b.rois, b.n, b.rows, b.L, b.Wc,
+               s.counts.as<int4>(), s.wpre.as<int>(), s.prefix.as<long long>(), s.chunk.as<long long>(), idx2,
+               (double*)nullptr, s.cubes.as<int4>(), vcap, ccap, tot);
+    RAD_LAUNCH("mc_cubes", k_cubes<false>, cblocks, kCubeThreads, 0, st, s.bits.as<uint32_t>(), b.rois, b.n,
+               s.wpre.as<int>(), s.prefix.as<long long>(), s.chunk.as<long long>(), s.cubes.as<int4>(),
+               s.bintab.as<BinCase>(), tri, ccap, tcap, tot, out, s.hist.as<unsigned long long>(),
+               s.partial.as<double>());
+    RAD_LAUNCH("mc_mask_totals", k_mask_totals, std::min(b.n, sms * 8), 256, 0, st, b.rois, b.n,
+               s.bintab.as<BinCase>(), s.hist.as<unsigned long long>(), out);
   }
   return RAD_OK;
+}
+
+// Host description of a batch: ROI table entries, offsets and the group shape.
+void plan_batch(const int64_t* dims, const void* const* data, const int* tab, const double* spacing, int n, bool soft,
+                std::vector<Roi>& rois, MeshBatch& b) {
+  rois.resize(n);
+  long long rows = 0, words = 0, wpre = 0;
+  int maxW = 1;
+  for (int i = 0; i < n; ++i) {
+    Roi& r = rois[i];
+    r.data = data[i];
+    r.nx = (int)dims[3 * i];
+    r.ny = (int)dims[3 * i + 1];
+    r.nz = (int)dims[3 * i + 2];
+    r.W = (r.nx + 31) / 32;
+    r.BY = r.ny + 3;
+    r.BZ = r.nz + 3;
+    r.vec16 = soft ? ((r.nx % 4) == 0 && (((uintptr_t)r.data) & 15) == 0)
+                   : ((r.nx % 16) == 0 && (((uintptr_t)r.data) & 15) == 0);
+    r.tab = tab ? tab[i] : 0;
+    r.R = (long long)(r.ny + 1) * (r.nz + 1);
+    r.row0 = rows;
+    r.word0 = words;
+    r.wpre0 = wpre;
+    r.sx = spacing[3 * i];
+    r.sy = spacing[3 * i + 1];
+    r.sz = spacing[3 * i + 2];
+    rows += r.R;
+    words += (long long)r.BY * r.BZ * r.W;
+    wpre += r.R * r.W;
+    maxW = std::max(maxW, r.W);
+  }
+  b.n = n;
+  b.soft = soft;
+  b.rows = rows;
+  b.words = words;
+  b.wpre = wpre;
+  b.L = group_lanes(maxW);
+  b.Wc = ((maxW + b.L - 1) / b.L) * b.L;
 }
 
 }  // namespace rad

@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "rad.h"
 
@@ -69,45 +70,63 @@ enum : uint32_t {
 };
 
 // ---- marching cubes -----------------------------------------------------------
-struct MeshDims {
-  int nx, ny, nz;
-  int W;       // 32-bit words per bitset row
-  int BY, BZ;  // bitset rows per axis (ny + 3, nz + 3)
-  int64_t R;   // owner / cube rows: (ny + 1) * (nz + 1)
+// One region of interest of a batch (host-computed, uploaded as a table).
+struct Roi {
+  const void* data;       // device mask (uint8) or probability map (float32)
+  int nx, ny, nz, W;      // W: 32-bit words per bitset row
+  int BY, BZ;             // bitset rows per axis: ny + 3, nz + 3 (zero padding)
+  int vec16, tab;         // 16-byte loads possible; index of its case table
+  long long R;            // owner / cube rows: (ny + 1) (nz + 1)
+  long long row0, word0;  // first row and first bitset word in the batch
+  long long wpre0;        // first per-word prefix slot
+  double sx, sy, sz;
 };
-MeshDims make_dims(const int64_t dims[3]);
+
+// Per-ROI results of a pass (device).
+struct RoiOut {
+  long long v0, nv, t0, nt, c0, na, nvox;  // id ranges of vertices, triangles, cubes; inside voxels
+  long long vsum;                          // exact sum of A.(B x C) in half-voxel units (masks)
+  double vol6, area2;                      // 6 V and 2 A
+};
+
+struct MeshTotals {  // batch-wide counts and status of one marching-cubes pass
+  long long nv, nt, nvox, na;
+  unsigned int status;
+  unsigned int done_ctas;  // last-CTA ticket of the soft cube kernel
+};
+
+// Host view of a batch.
+struct MeshBatch {
+  int n = 0;
+  bool soft = false;
+  const Roi* rois = nullptr;  // device table
+  long long rows = 0, words = 0, wpre = 0;
+  int L = 1, Wc = 1;          // lanes per row group; word-loop bound
+};
 
 // Scratch of the marching-cubes pass, reused between calls.
 struct MeshScratch {
-  DevBuf bits;    // packed inside bits, (ny + 3) (nz + 3) rows of W words
+  DevBuf bits;    // packed inside bits of every ROI
   DevBuf counts;  // int4 per row: vertices, triangles, inside voxels, active cubes
   DevBuf wpre;    // int per (row, word): row-local vertex prefix
-  DevBuf prefix;  // int64 x 3 per row: chunk-local exclusive prefixes (vertices, triangles, cubes)
-  DevBuf chunk;   // int64 x 4 per scan chunk: chunk offsets (and inside voxels)
-  DevBuf cubes;   // int4 per active cube: x, row, case, first triangle id
-  DevBuf hist;    // uint64 x 256: active cubes per case (mask area)
+  DevBuf prefix;  // int64 x 4 per row: chunk-local exclusive prefixes
+  DevBuf chunk;   // int64 x 4 per scan chunk: chunk offsets
+  DevBuf cubes;   // int4 per active cube: x, global row, case, first triangle id
+  DevBuf hist;    // uint64 x 256 per ROI: active cubes per case (mask area)
   DevBuf partial; // per-CTA FP64 partial sums of 6V and 2A (soft maps)
-  DevBuf bintab;  // per-spacing binary case table
-  double tab_spacing[3] = {0, 0, 0};
-  bool tab_valid = false;
+  DevBuf bintab;  // case tables, one per spacing
+  DevBuf tabsp;   // spacings of the case tables
 };
 
-struct MeshTotals {  // device counts and sums of one marching-cubes pass
-  long long nv, nt, nvox, na;
-  double vol6, area2;
-  long long vsum;          // exact sum of A.(B x C) in half-voxel units (masks)
-  unsigned int status;
-  unsigned int done_ctas;  // last-CTA ticket of the cube kernel
-};
-
-// Phase 1: pack + count + scan; the counts land in *tot (device).
-rad_status mesh_count(const void* data, bool soft, const MeshDims& d, MeshScratch& s, MeshTotals* tot,
-                      cudaStream_t st);
-// Phase 2: emit vertices / triangles (up to the given capacities) and reduce
-// 6V and 2A into *tot.
-rad_status mesh_emit(const void* data, bool soft, const MeshDims& d, const double sp[3], MeshScratch& s,
-                     MeshTotals* tot, int16_t* idx2, double* vt, int32_t* tri, long long vcap, long long tcap,
-                     cudaStream_t st);
+void plan_batch(const int64_t* dims, const void* const* data, const int* tab, const double* spacing, int n, bool soft,
+                std::vector<Roi>& rois, MeshBatch& b);
+// Case tables of binary masks, one per spacing (n_tabs x 3 doubles, host).
+rad_status mesh_tables(const double* spacings_host, int n_tabs, MeshScratch& s, cudaStream_t st);
+// Phase 1: pack + count + scan; batch totals in *tot, per-ROI id ranges in out[].
+rad_status mesh_count(const MeshBatch& b, MeshScratch& s, MeshTotals* tot, RoiOut* out, cudaStream_t st);
+// Phase 2: vertices / triangles (up to the capacities) and per-ROI 6V, 2A.
+rad_status mesh_emit(const MeshBatch& b, MeshScratch& s, MeshTotals* tot, RoiOut* out, int16_t* idx2, double* vt,
+                     int32_t* tri, long long vcap, long long tcap, cudaStream_t st);
 
 // ---- diameters ----------------------------------------------------------------
 struct DiamScratch {
@@ -116,16 +135,47 @@ struct DiamScratch {
   long long work_cap = 0, cand_cap = 0;
 };
 
-// Device result of one diameter run: for 3D, Slice, Column, Row.
+// Per-ROI parameters of the diameter problems (host-computed, uploaded).
+struct RoiDiam {
+  int nx, ny, nz, planes;         // planes: also the planar diameters (masks)
+  int cell_shift, CX, CY, CZ;     // 3D cells
+  int plane_shift, PX, PY, PZ;    // in-plane 2D cells
+  long long key0;                 // first sort key of the ROI
+  long long C3, S0, S1, S2, K;    // key blocks (relative): 3D cells, Slice, Column, Row; total
+  long long plane0;               // first plane of the ROI in the batch
+  double sx, sy, sz;
+  double cx, cy, cz;              // centre (index units)
+  double alpha, beta, gamma;      // FP32 error-bound coefficients
+};
+
+// Per-ROI result (device): FP64 bits of the squared diameters and the
+// (i << 32 | j) argmax pairs (ROI-local ids) for 3D, Slice, Column, Row.
+struct DiamOut {
+  unsigned long long d2[4];
+  unsigned long long pair[4];
+};
+
+struct DiamStats {
+  long long problems, tiles, tile_pairs, work_items, items_evaluated, pairs_evaluated, candidates;
+  unsigned int status, pad;
+};
+
+// Result of the plain FP64 kernel (one mask).
 struct DiamResult {
   double d2[4];
   int i[4], j[4];
-  long long problems, tiles, tile_pairs, work_items, items_evaluated, pairs_evaluated, candidates;
 };
 
-rad_status diam_run(const int16_t* idx2, const double* vt, long long nv_hint, const long long* nv_dev,
-                    const MeshDims& d, const double sp[3], DiamScratch& s, DiamResult* out_dev,
-                    unsigned int* status_dev, cudaStream_t st);
+struct MeshDims {  // size of one grid
+  int nx, ny, nz;
+};
+inline MeshDims make_dims(const int64_t dims[3]) { return MeshDims{(int)dims[0], (int)dims[1], (int)dims[2]}; }
+
+void plan_diam(const std::vector<Roi>& rois, bool soft, std::vector<RoiDiam>& rd, long long& nkeys,
+               long long& nplanes);
+rad_status diam_run(int n, const RoiDiam* rd, const RoiOut* ro, const long long* nv_dev, long long nv_cap,
+                    long long nkeys, long long nplanes, bool planes, const int16_t* idx2, const double* vt,
+                    DiamScratch& s, DiamOut* out, DiamStats* stats, cudaStream_t st);
 rad_status diam_plain_fp64(const int16_t* idx2, const double* vt, long long nv, const MeshDims& d, const double sp[3],
                            DiamScratch& s, DiamResult* out_dev, cudaStream_t st);
 

@@ -70,7 +70,8 @@ _lib = None
 EXPORTS = ("rad_mesh", "rad_soft_mesh", "rad_shape", "rad_shape_plain_fp64", "rad_extract", "rad_extract_host",
            "rad_workspace_free", "rad_mesh_free", "rad_mesh_copy", "rad_set_tuning", "rad_profile_enable",
            "rad_profile_read", "rad_profile_reset", "rad_launch_count", "rad_status_str", "rad_last_error",
-           "rad_last_call_stats", "rad_soft_forward", "rad_soft_backward")
+           "rad_last_call_stats", "rad_soft_forward", "rad_soft_backward", "rad_batch_create", "rad_batch_run",
+           "rad_batch_destroy")
 
 
 def lib():
@@ -114,6 +115,12 @@ def lib():
         L.rad_soft_forward.restype = I
         L.rad_soft_backward.argtypes = [P, P, P, P, P, P, ctypes.POINTER(P), P]
         L.rad_soft_backward.restype = I
+        L.rad_batch_create.argtypes = [I, P, P, P, ctypes.POINTER(P), P]
+        L.rad_batch_create.restype = I
+        L.rad_batch_run.argtypes = [P, ctypes.POINTER(Features), P]
+        L.rad_batch_run.restype = I
+        L.rad_batch_destroy.argtypes = [P]
+        L.rad_batch_destroy.restype = None
         L.rad_last_error.argtypes = []
         L.rad_last_error.restype = ctypes.c_char_p
         _lib = L
@@ -265,6 +272,35 @@ def soft_backward(prob, spacing, gout, argmax, grad, ws, stream=None):
     am = (ctypes.c_int32 * 2)(int(argmax[0]), int(argmax[1]))
     _check(lib().rad_soft_backward(ctypes.c_void_p(prob.data_ptr()), dims, sp, g, am,
                                    ctypes.c_void_p(grad.data_ptr()), ctypes.byref(ws.h), _stream(stream)))
+
+
+class Batch:
+    """A batch of CUDA uint8 masks (tensors [nz][ny][nx]) with their spacings,
+    processed in one set of launches and replayed as one CUDA graph."""
+
+    def __init__(self, masks, spacings, stream=None):
+        if len(masks) != len(spacings) or not masks:
+            raise ValueError("need one spacing per mask")
+        for m in masks:
+            _device_tensor(m, "torch.uint8")
+        self.masks = list(masks)  # keep the tensors alive
+        n = len(masks)
+        ptrs = (ctypes.c_void_p * n)(*[m.data_ptr() for m in masks])
+        dims = (ctypes.c_int64 * (3 * n))(*[v for m in masks for v in (m.shape[2], m.shape[1], m.shape[0])])
+        sp = (ctypes.c_double * (3 * n))(*[float(v) for s in spacings for v in s])
+        self.h = ctypes.c_void_p(None)
+        _check(lib().rad_batch_create(n, ptrs, dims, sp, ctypes.byref(self.h), _stream(stream)))
+        self.n = n
+
+    def run(self, stream=None):
+        out = (Features * self.n)()
+        _check(lib().rad_batch_run(self.h, out, _stream(stream)))
+        return [f.as_dict() for f in out]
+
+    def __del__(self):
+        if _lib is not None and getattr(self, "h", None) is not None and self.h.value:
+            _lib.rad_batch_destroy(self.h)
+            self.h = ctypes.c_void_p(None)
 
 
 def set_tuning(tile=None, threads=None, ctas_per_sm=None, cell_shift=None):
