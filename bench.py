@@ -204,6 +204,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -211,7 +212,7 @@ def main():
 
     import torch
 
-    from paper_2510_02894_gb300 import rad, synth
+    from paper_2510_02894_gb300 import autotune, rad, synth
 
     world, rank, local = dist_setup()
     torch.cuda.set_device(local)
@@ -229,6 +230,13 @@ def main():
     stats = rad.last_call_stats()
     N, T = feats["n_vertices"], feats["n_triangles"]
     pairs = N * (N - 1) / 2
+    tuned = {}
+    if not args.no_autotune:  # pick tile / block shapes on this workload (a second or so)
+        cache = os.path.join(tempfile.gettempdir(), "rad_bench_tuning.json")
+        cfg, table = autotune.tune(lambda: rad.extract(dev, sp, ws), autotune.bucket(1, N), cache_path=cache)
+        tuned["ct_512"] = {"config": cfg, "candidates": len(table),
+                           "best_ms": min(ms for _, ms in table), "default_ms": table[0][1]}
+    tuning_main = rad.get_tuning()
 
     # ---- timed region: device-resident inputs ------------------------------------
     clocks = ClockSampler(local)
@@ -349,6 +357,12 @@ def main():
         crops = synth.batch_256(0)
         devs = [torch.from_numpy(c).cuda() for c, _ in crops]
         b = rad.Batch(devs, [s for _, s in crops])
+        if not args.no_autotune:
+            nb = sum(f["n_vertices"] for f in b.run())
+            cache = os.path.join(tempfile.gettempdir(), "rad_bench_tuning.json")
+            cfg, table = autotune.tune(b.run, autotune.bucket(len(devs), nb), cache_path=cache)
+            tuned["batch_256"] = {"config": cfg, "candidates": len(table),
+                                  "best_ms": min(ms for _, ms in table), "default_ms": table[0][1]}
         for _ in range(args.warmup):
             b.run()
         bms = []
@@ -367,7 +381,8 @@ def main():
         batch = {"rois": len(devs), "ms": bm, "rois_per_s": len(devs) / (bm / 1e3),
                  "vertex_pairs_per_s": total_pairs / (bm / 1e3), "voxels": int(sum(c.size for c, _ in crops)),
                  "mode": "rad_batch_run: one launch per stage over all 256 ROIs, replayed as one CUDA graph",
-                 "pairs_evaluated_fp32": bs["pairs_evaluated"]}
+                 "pairs_evaluated_fp32": bs["pairs_evaluated"], "tuning": rad.get_tuning()}
+        rad.set_tuning(**tuning_main)
 
     # ---- CPU baseline: the oracle on a bounded sample --------------------------------
     cpu = None
@@ -385,7 +400,8 @@ def main():
                 "vs_baseline": None, "dtype": "u8+f32+f64", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "n_vertices": N, "n_triangles": T, "pairs": pairs,
                            "pairs_evaluated_fp32": d["pairs_evaluated"], "l2": "flushed between steps (256 MB write)",
-                           "parallelism": f"replicas x{world}", "diam_stats": stats},
+                           "parallelism": f"replicas x{world}", "diam_stats": stats, "tuning": tuning_main,
+                           "autotune": tuned},
                 "roofline": roof, "kernels": kernel_table, "ms_per_step_with_kernel_events": statistics.mean(prof_ms),
                 "e2e": {"value": world * pairs / (e2e / 1e3), "unit": UNIT, "ms_per_step": e2e,
                         "h2d_bytes_per_step": hstats["h2d_bytes"], "d2h_bytes_per_step": hstats["d2h_bytes"]},

@@ -290,6 +290,8 @@ struct Work {
   long long g_epoch = -1;
   bool g_prof = false;
   std::vector<Roi> g_rois;
+  std::vector<RoiDiam> g_rd;
+  rad_tuning_t g_tuning = {0, 0, 0, 0};
   CaptureSink g_sink_data;
   void drop_graph() {
     if (gexec) cudaGraphExecDestroy(gexec);
@@ -445,12 +447,18 @@ static rad_status capture_pass(Work& w) {
   w.g_prof = profiling_on();
   w.g_epoch = alloc_epoch();
   w.g_rois = w.rois;
+  w.g_rd = w.rd;
+  w.g_tuning = tuning();
   return RAD_OK;
 }
 
+// A graph stays valid while the ROI table, the diameter parameters, the
+// tuning (kernel shapes), the profiling mode and every buffer are unchanged.
 static bool graph_matches(const Work& w) {
+  const rad_tuning_t& t = tuning();
   return w.gexec && w.g_epoch == alloc_epoch() && w.g_prof == profiling_on() && w.g_rois.size() == w.rois.size() &&
-         same_bytes(w.g_rois.data(), w.rois.data(), sizeof(Roi) * w.rois.size());
+         same_bytes(w.g_rois.data(), w.rois.data(), sizeof(Roi) * w.rois.size()) && w.g_rd.size() == w.rd.size() &&
+         same_bytes(w.g_rd.data(), w.rd.data(), sizeof(RoiDiam) * w.rd.size()) && same_bytes(&w.g_tuning, &t, sizeof(t));
 }
 
 rad_status status_from_dev(unsigned int st) {
@@ -540,6 +548,9 @@ struct rad_workspace {
 struct rad_batch {
   rad::Work work;
   int n = 0;
+  std::vector<const void*> masks;
+  std::vector<int64_t> dims;
+  std::vector<double> spacing;
 };
 
 using namespace rad;
@@ -762,9 +773,11 @@ rad_status rad_batch_create(int n_rois, const uint8_t* const* masks_dev, const i
   }
   rad_batch_t* b = new rad_batch();
   b->n = n_rois;
+  b->masks.assign(masks_dev, masks_dev + n_rois);
+  b->dims.assign(dims, dims + 3 * n_rois);
+  b->spacing.assign(spacing, spacing + 3 * n_rois);
   cudaStream_t st = (cudaStream_t)stream;
-  std::vector<const void*> ptrs(masks_dev, masks_dev + n_rois);
-  rad_status s = prepare(b->work, n_rois, ptrs.data(), dims, spacing, false, st);
+  rad_status s = prepare(b->work, n_rois, b->masks.data(), dims, spacing, false, st);
   if (s == RAD_OK) s = run_pass(b->work, st, true, 0);  // sizes the pools and captures the graph
   if (s != RAD_OK) {
     delete b;
@@ -776,6 +789,8 @@ rad_status rad_batch_create(int n_rois, const uint8_t* const* masks_dev, const i
 
 rad_status rad_batch_run(rad_batch_t* b, rad_features_t* out, void* stream) {
   if (!b || !out) { set_error("batch and out must be non-NULL"); return RAD_ERR_INVALID_ARG; }
+  // re-plan (host only; uploads only if the tuning changed the parameters)
+  RAD_TRY(prepare(b->work, b->n, b->masks.data(), b->dims.data(), b->spacing.data(), false, (cudaStream_t)stream));
   RAD_TRY(run_pass(b->work, (cudaStream_t)stream, true, 0));
   memcpy(out, b->work.hfeats, sizeof(rad_features_t) * b->n);
   return RAD_OK;
