@@ -92,16 +92,20 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def dist_setup():
+def dist_setup(backend="nccl"):
+    """Read the torchrun environment; for N > 1 join the process group (one
+    rank per GPU; the ranks are independent replicas, the group only carries
+    the barriers and the max over ranks of the step time)."""
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    elif torch.cuda.is_available():
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    elif backend == "nccl" and torch.cuda.is_available():
         torch.cuda.set_device(0)
     return world, rank, local
 
@@ -113,13 +117,20 @@ def barrier(world):
 
 
 def max_over_ranks(x, world):
+    """Maximum of a per-rank float over all ranks (the whole-job step time)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_throughput(units_per_rank, ms_max, world):
+    """Whole-job rate: the units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank / (ms_max / 1e3)
 
 
 def kernel_work(name, ctx):
@@ -261,7 +272,7 @@ def main():
     launches = rad.launch_count() - launches0
     clk = clocks.stop()
     ms = max_over_ranks(statistics.mean(step_ms), world)
-    value = world * pairs / (ms / 1e3)
+    value = job_throughput(pairs, ms, world)
 
     # ---- per-kernel durations: the same steps with CUDA events around every
     # kernel (event-record nodes inside the replayed graph) --------------------
@@ -403,7 +414,7 @@ def main():
                            "parallelism": f"replicas x{world}", "diam_stats": stats, "tuning": tuning_main,
                            "autotune": tuned},
                 "roofline": roof, "kernels": kernel_table, "ms_per_step_with_kernel_events": statistics.mean(prof_ms),
-                "e2e": {"value": world * pairs / (e2e / 1e3), "unit": UNIT, "ms_per_step": e2e,
+                "e2e": {"value": job_throughput(pairs, e2e, world), "unit": UNIT, "ms_per_step": e2e,
                         "h2d_bytes_per_step": hstats["h2d_bytes"], "d2h_bytes_per_step": hstats["d2h_bytes"]},
                 "plain_fp64": plain, "batched": batch, "cpu_baseline": cpu, "clocks": clk,
                 "gpu_launches": launches, "gpu_launches_per_step": launches / args.steps}
