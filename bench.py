@@ -388,11 +388,26 @@ def main():
             bms.append(e0.elapsed_time(e1))
         bs = rad.last_call_stats()
         bm = statistics.mean(bms)
+        # per-kernel durations of the batch (event nodes in its graph)
+        rad.profile_enable(True)
+        b.run()
+        rad.profile_reset()
+        for _ in range(args.steps):
+            flush.zero_()
+            b.run()
+        torch.cuda.synchronize()
+        rad.profile_enable(False)
+        bprof = {k: v for k, v in rad.profile_read().items() if v["launches"] > 0}
+        b.run()
+        btot = sum(v["total_ms"] for v in bprof.values()) or 1.0
+        batch_kernels = {k: {"ms_per_run": v["total_ms"] / args.steps, "share": v["total_ms"] / btot}
+                         for k, v in sorted(bprof.items(), key=lambda kv: -kv[1]["total_ms"])}
         total_pairs = sum(f["n_vertices"] * (f["n_vertices"] - 1) / 2 for f in b.run())
         batch = {"rois": len(devs), "ms": bm, "rois_per_s": len(devs) / (bm / 1e3),
                  "vertex_pairs_per_s": total_pairs / (bm / 1e3), "voxels": int(sum(c.size for c, _ in crops)),
                  "mode": "rad_batch_run: one launch per stage over all 256 ROIs, replayed as one CUDA graph",
-                 "pairs_evaluated_fp32": bs["pairs_evaluated"], "tuning": rad.get_tuning()}
+                 "pairs_evaluated_fp32": bs["pairs_evaluated"], "tuning": rad.get_tuning(),
+                 "diam_stats": bs, "kernels": batch_kernels}
         rad.set_tuning(**tuning_main)
 
     # ---- CPU baseline: the oracle on a bounded sample --------------------------------

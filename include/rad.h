@@ -82,7 +82,8 @@ typedef struct {
 /* Tuning knobs of the diameter kernels (see rad_set_tuning). */
 typedef struct {
   int32_t tile;        /* vertices per tile: 64, 128 or 256 */
-  int32_t threads;     /* threads per CTA of the pair kernel: 64, 128 or 256 */
+  int32_t threads;     /* threads per CTA of the pair kernel: 64 or 128, also 256 with
+                          tiles of 128 vertices */
   int32_t ctas_per_sm; /* persistent CTAs per SM for the pair kernel: 1..16 */
   int32_t cell_shift;  /* spatial cell edge = 2^cell_shift doubled-index units (2..7) */
 } rad_tuning_t;

@@ -16,7 +16,7 @@ import statistics
 from . import rad
 
 # (tile, threads) pairs the library instantiates
-SHAPES = ((64, 64), (64, 128), (128, 64), (128, 128), (128, 256), (256, 128), (256, 256))
+SHAPES = ((64, 64), (64, 128), (128, 64), (128, 128), (128, 256), (256, 64), (256, 128))
 CELL_SHIFTS = (3, 4, 5)
 CTAS_PER_SM = (2, 4, 8, 16)
 

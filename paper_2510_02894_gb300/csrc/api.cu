@@ -850,7 +850,7 @@ rad_status rad_set_tuning(const rad_tuning_t* set, rad_tuning_t* get) {
     const bool ok_tile = set->tile == 64 || set->tile == 128 || set->tile == 256;
     const bool ok_thr = (set->tile == 64 && (set->threads == 64 || set->threads == 128)) ||
                         (set->tile == 128 && (set->threads == 64 || set->threads == 128 || set->threads == 256)) ||
-                        (set->tile == 256 && (set->threads == 128 || set->threads == 256));
+                        (set->tile == 256 && (set->threads == 64 || set->threads == 128));
     if (!ok_tile || !ok_thr || set->ctas_per_sm < 1 || set->ctas_per_sm > 16 || set->cell_shift < 2 ||
         set->cell_shift > 7) {
       set_error("invalid tuning (tile %d, threads %d, ctas_per_sm %d, cell_shift %d)", set->tile, set->threads,

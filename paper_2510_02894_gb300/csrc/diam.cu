@@ -12,16 +12,21 @@
 //      the vertices out as float4 (x, y, z in FP32, centred and scaled; w =
 //      vertex id).  The 3D problem is the whole cell-sorted range; every plane
 //      with two or more vertices is its own problem.
-//   2. Each problem is cut into tiles of TS vertices; a tile gets its
-//      bounding box and 14 directional extremes.  The pairs of each
-//      problem's extremes seed its running maximum F.
-//   3. Tile pairs whose farthest-corner bound cannot reach the threshold
-//      T(F) are culled; the rest form a device work list.
-//   4. A persistent kernel evaluates the surviving tile pairs in FP32 from
-//      shared memory (6 FP32 operations per pair, warp max, one atomic max
-//      per tile pair on F), re-culling each item against the current F.
-//   5. Pairs with f >= T(F) become candidates and are re-evaluated in FP64
-//      with the pinned formula; max d2, then the smallest (i, j).
+//   2. Each problem is cut into tiles of TS vertices with bounding boxes and
+//      a representative vertex.  The upper triangle of a problem's tile pairs
+//      is walked as (tile row, 128-column chunk) items spread evenly over all
+//      warps: the representative pairs seed the running maximum F, then the
+//      tile pairs whose farthest-corner bound reaches T(F) form the work list.
+//   3. The surviving tile pairs are split into (tile pair, 32-entry B slice)
+//      warp items.  Every warp takes items from a ticket and evaluates them in
+//      FP32 from its own shared-memory buffers (the next item is staged with
+//      cp.async while the current one is evaluated, no block barriers); it
+//      re-culls against the current F, keeps the slice maximum and raises F
+//      with one atomic when it beats F.  Slices whose maximum reaches the
+//      final T(F) are rescanned and their pairs with f >= T(F) become
+//      candidates.
+//   4. The candidates are re-evaluated in FP64 with the pinned formula: the
+//      largest d2 per ROI and category, then the smallest (i, j) attaining it.
 //
 // FP32 error bound (per pair, binary or soft; u = 2^-24, positions a relative
 // to the grid centre, R = the grid's half extent in mm):
@@ -30,8 +35,10 @@
 // T(F) inverts this bound (with every coefficient doubled), so every pair
 // attaining the FP64 maximum has f >= T(F) for any F not above the largest
 // f; the culling bound uses the same monotone FP32 operations on box
-// distances, so it bounds f from above without any epsilon.
+// distances, so it bounds f from above without any epsilon.  T only grows, so
+// a pair culled or left out against an earlier T is also below the final one.
 #include <float.h>
+#include <limits.h>
 #include <math.h>
 #include <stdio.h>
 
@@ -44,48 +51,49 @@ namespace rad {
 
 namespace {
 
+constexpr int kChunk = 128;  // tile columns per seed / cull item (4 per lane)
 
 struct Problem {
   int axis;  // -1: 3D, 0: Row (equal x), 1: Column (equal y), 2: Slice (equal z)
   int beg, len;
   int tile_beg;  // first tile
   int roi;
-  int pad;
+  int q;  // result slot: 0 3D, 1 Slice, 2 Column, 3 Row
 };
 
-struct Tile {
+struct __align__(16) Tile {
   int problem, beg, len, tile_end;  // tile_end: one past the problem's last tile
+  int roi, q, pad0, pad1;           // ROI and result slot of the problem
 };
 
+// A surviving tile pair: both vertex ranges, its box bound and its result slot.
 struct WorkItem {
-  int problem, ta, tb, roi;
+  int problem, roi;
+  int abeg, alen, bbeg, blen;
+  float ub;
+  int q;
 };
 
 struct Cand {
-  int ea, eb, problem, roi;
+  int ea, eb, roi, q;  // sorted-entry indices of the pair, ROI, result slot
 };
 
-struct ProblemState {
+struct __align__(8) ProblemState {  // read as one 64-bit word by the pair kernel
   unsigned int F;  // float bits of the running FP32 maximum
   unsigned int T;  // float bits of T(F), raised with F
-  unsigned long long best_d2;    // FP64 bits of the confirmed maximum
-  unsigned long long best_pair;  // (i << 32) | j, smallest among the maxima
 };
 
 struct Counters {
   int n_problems;
-  int n_tiles;
-  long long n_pairs;
+  unsigned int pad1;
+  unsigned long long alloc;  // (seed/cull chunks << 32) + tiles, one atomic per problem
+  long long n_pairs;         // tile pairs (upper triangles)
   long long n_work;
   long long n_cand;
-  int ticket;
-  int ticket2;
-  unsigned int status;
-  int pad;
+  long long n_hits;  // slices to rescan for candidates
   unsigned long long items_evaluated, pairs_evaluated;
-  long long n_work2;  // items re-evaluated for candidates
-  unsigned int done;  // last-block ticket
-  unsigned int pad2;
+  unsigned int status;
+  unsigned int pad;
 };
 
 // Batch-wide parameters of one run.
@@ -129,6 +137,8 @@ __device__ __forceinline__ void vertex_q(const int16_t* idx2, long long v, int q
   q[1] = idx2[3 * v + 1];
   q[2] = idx2[3 * v + 2];
 }
+
+__device__ __forceinline__ int slot_of_axis(int axis) { return axis < 0 ? 0 : (axis == 2 ? 1 : (axis == 1 ? 2 : 3)); }
 
 // ---- 1. keys, histogram, scatter ------------------------------------------------
 // kind 0: 3D cell (z, y, x order); kinds 1..3: (plane, 2D cell) for Slice
@@ -187,6 +197,8 @@ __global__ void k_hist(const int16_t* __restrict__ idx2, const long long* __rest
 
 __device__ __forceinline__ long long key_offset(const long long* offs, const long long* parts, long long key);
 
+// The four slot reservations of a warp are issued back to back, so one
+// round trip covers all of them.
 __global__ void k_scatter(const int16_t* __restrict__ idx2, const double* __restrict__ vt,
                           const long long* __restrict__ nv_dev, const RoiDiam* __restrict__ rd,
                           const RoiOut* __restrict__ ro, Params p, const long long* __restrict__ offs,
@@ -210,20 +222,30 @@ __global__ void k_scatter(const int16_t* __restrict__ idx2, const double* __rest
                       __double2float_rn((u[2] - r.cz) * r.sz), __int_as_float((int)v));
     }
     const RoiDiam& r = rd[roi];
+    long long key[4];
+    unsigned int peers[4];
+    int base[4];
+#pragma unroll
     for (int k = 0; k < 4; ++k) {
       const bool use = v < n && (k == 0 || r.planes);
-      const long long key = use ? key_of(r, q, k) : -1;
-      const unsigned int peers = __match_any_sync(0xffffffffu, key);
-      const int leader = __ffs(peers) - 1;
-      int base = 0;
-      if (key >= 0 && lane == leader) base = atomicAdd(&cursor[key], __popc(peers));
-      base = __shfl_sync(0xffffffffu, base, leader);
-      if (key >= 0) sorted[key_offset(offs, parts, key) + base + __popc(peers & ((1u << lane) - 1u))] = e;
+      key[k] = use ? key_of(r, q, k) : -1;
+      peers[k] = __match_any_sync(0xffffffffu, key[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      base[k] = 0;
+      if (key[k] >= 0 && lane == __ffs(peers[k]) - 1) base[k] = atomicAdd(&cursor[key[k]], __popc(peers[k]));
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int b = __shfl_sync(0xffffffffu, base[k], __ffs(peers[k]) - 1);
+      if (key[k] >= 0)
+        sorted[key_offset(offs, parts, key[k]) + b + __popc(peers[k] & ((1u << lane) - 1u))] = e;
     }
   }
 }
 
-// Generic exclusive scan of int counts to long long offsets (3 kernels).
+// Generic exclusive scan of int counts to long long offsets (2 kernels).
 constexpr int kScanBlock = 1024;
 __global__ void k_xscan_part(const int* __restrict__ in, long long n, long long* __restrict__ out,
                              long long* __restrict__ part) {
@@ -280,9 +302,10 @@ __device__ __forceinline__ long long key_offset(const long long* offs, const lon
 // ---- 2. problems and tiles --------------------------------------------------------
 // One warp per candidate problem: the 3D problem of every ROI (items 0..n-1)
 // and every plane of every ROI (items n..).  A problem with >= 2 vertices
-// takes a slot and a contiguous run of tiles with atomics (the order of
-// problems does not affect any result), resets its state and writes its
-// tiles.
+// takes a slot, and -- in one 64-bit atomic, so both ranges follow the same
+// order -- a contiguous run of tiles and of seed/cull chunks (the order of
+// problems does not affect any result).  Row i of a problem with nt tiles
+// scans tiles i..nt-1 in ceil((nt - i) / kChunk) chunks.
 __device__ __forceinline__ int roi_of_plane(const RoiDiam* rd, int n, long long g) {
   int lo = 0, hi = n - 1;
   while (lo < hi) {
@@ -293,75 +316,127 @@ __device__ __forceinline__ int roi_of_plane(const RoiDiam* rd, int n, long long 
   return lo;
 }
 
+// sum over k = 1..m of ceil(k / kChunk): the chunks of the last m rows.
+__device__ __forceinline__ long long chunks_upto(long long m) {
+  const long long q = m / kChunk, r = m % kChunk;
+  return kChunk * q * (q + 1) / 2 + r * (q + 1);
+}
+
 __global__ void k_setup(const RoiDiam* __restrict__ rd, Params p, const long long* __restrict__ offs,
                         const long long* __restrict__ parts, Problem* __restrict__ probs, Tile* __restrict__ tiles,
-                        ProblemState* __restrict__ ps, Counters* __restrict__ cnt) {
+                        int* __restrict__ chunk0, ProblemState* __restrict__ ps, Counters* __restrict__ cnt) {
   const int lane = threadIdx.x & 31;
   const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   const long long items = p.n + p.nplanes;
-  for (long long it = warp; it < items; it += nwarps) {
-    int roi, axis;
-    long long k0, k1;
-    if (it < p.n) {
-      roi = (int)it;
-      const RoiDiam& r = rd[roi];
-      axis = -1;
-      k0 = r.key0;
-      k1 = r.key0 + r.C3;
-    } else {
-      const long long g = it - p.n;
-      roi = roi_of_plane(rd, p.n, g);
-      const RoiDiam& r = rd[roi];
-      const long long l = g - r.plane0;
-      const long long nz2 = 2LL * r.nz + 1, ny2 = 2LL * r.ny + 1;
-      if (l < nz2) {
-        axis = 2; k0 = r.key0 + r.S0 + l * r.PX * r.PY; k1 = k0 + (long long)r.PX * r.PY;
-      } else if (l < nz2 + ny2) {
-        axis = 1; k0 = r.key0 + r.S1 + (l - nz2) * r.PX * r.PZ; k1 = k0 + (long long)r.PX * r.PZ;
+  for (long long base = warp * 32; base < items; base += nwarps * 32) {
+    // one lane per candidate problem
+    const long long it = base + lane;
+    int roi = 0, axis = -1;
+    long long beg = 0, len = 0;
+    if (it < items) {
+      long long k0, k1;
+      if (it < p.n) {
+        roi = (int)it;
+        const RoiDiam& r = rd[roi];
+        k0 = r.key0;
+        k1 = r.key0 + r.C3;
       } else {
-        axis = 0; k0 = r.key0 + r.S2 + (l - nz2 - ny2) * r.PY * r.PZ; k1 = k0 + (long long)r.PY * r.PZ;
+        const long long g = it - p.n;
+        roi = roi_of_plane(rd, p.n, g);
+        const RoiDiam& r = rd[roi];
+        const long long l = g - r.plane0;
+        const long long nz2 = 2LL * r.nz + 1, ny2 = 2LL * r.ny + 1;
+        if (l < nz2) {
+          axis = 2; k0 = r.key0 + r.S0 + l * r.PX * r.PY; k1 = k0 + (long long)r.PX * r.PY;
+        } else if (l < nz2 + ny2) {
+          axis = 1; k0 = r.key0 + r.S1 + (l - nz2) * r.PX * r.PZ; k1 = k0 + (long long)r.PX * r.PZ;
+        } else {
+          axis = 0; k0 = r.key0 + r.S2 + (l - nz2 - ny2) * r.PY * r.PZ; k1 = k0 + (long long)r.PY * r.PZ;
+        }
       }
+      beg = key_offset(offs, parts, k0);
+      len = key_offset(offs, parts, k1) - beg;
     }
-    const long long beg = key_offset(offs, parts, k0);
-    const long long len = key_offset(offs, parts, k1) - beg;
-    if (len < 2) continue;  // warp-uniform
-    const int nt = (int)((len + p.TS - 1) / p.TS);
-    int slot = 0, tb = 0;
+    const bool use = len >= 2;
+    const unsigned int um = __ballot_sync(0xffffffffu, use);
+    if (um == 0) continue;  // warp-uniform
+    // warp-aggregated allocation of slots, tiles and chunks
+    const int nt = use ? (int)((len + p.TS - 1) / p.TS) : 0;
+    const long long S = use ? chunks_upto(nt) : 0;
+    const unsigned long long add = use ? ((unsigned long long)S << 32) + (unsigned long long)nt : 0ull;
+    unsigned long long inc = add;
+    for (int off = 1; off < 32; off <<= 1) {
+      const unsigned long long o = __shfl_up_sync(0xffffffffu, inc, off);
+      if (lane >= off) inc += o;
+    }
+    const unsigned long long total = __shfl_sync(0xffffffffu, inc, 31);
+    int slot0 = 0;
+    unsigned long long old0 = 0;
     if (lane == 0) {
-      slot = atomicAdd(&cnt->n_problems, 1);
-      tb = atomicAdd(&cnt->n_tiles, nt);
-      atomicAdd((unsigned long long*)&cnt->n_pairs, (unsigned long long)nt * (nt + 1) / 2);
+      slot0 = atomicAdd(&cnt->n_problems, __popc(um));
+      old0 = atomicAdd(&cnt->alloc, total);
     }
-    slot = __shfl_sync(0xffffffffu, slot, 0);
-    tb = __shfl_sync(0xffffffffu, tb, 0);
-    if (slot >= p.max_problems || (long long)tb + nt > p.max_tiles) {
-      if (lane == 0) atomicOr(&cnt->status, DEV_ERR_PROBCAP);
-      continue;
-    }
-    if (lane == 0) {
-      Problem q;
-      q.axis = axis; q.beg = (int)beg; q.len = (int)len; q.tile_beg = tb; q.roi = roi; q.pad = 0;
-      probs[slot] = q;
+    slot0 = __shfl_sync(0xffffffffu, slot0, 0);
+    old0 = __shfl_sync(0xffffffffu, old0, 0);
+    if (use) atomicAdd((unsigned long long*)&cnt->n_pairs, (unsigned long long)nt * (nt + 1) / 2);
+    const int slot = slot0 + __popc(um & ((1u << lane) - 1u));
+    const unsigned long long old = old0 + (inc - add);
+    const long long tb = (long long)(old & 0xffffffffull);
+    const long long cb = (long long)(old >> 32);
+    const bool ok = use && slot < p.max_problems && tb + nt <= p.max_tiles;
+    // more than 2^31 chunks in one batch (about 740k tiles in one problem):
+    // reported, and the chunk walk stays inside the tile array
+    const bool ovf = ok && cb + S > (long long)INT_MAX;
+    if ((use && !ok) || ovf) atomicOr(&cnt->status, DEV_ERR_PROBCAP);
+    const int q = slot_of_axis(axis);
+    if (ok) {
+      Problem pr;
+      pr.axis = axis; pr.beg = (int)beg; pr.len = (int)len; pr.tile_beg = (int)tb; pr.roi = roi; pr.q = q;
+      probs[slot] = pr;
       ProblemState z;
-      z.F = 0u; z.T = 0u; z.best_d2 = 0ull; z.best_pair = ~0ull;
+      z.F = 0u; z.T = 0u;
       ps[slot] = z;
     }
-    for (int t = lane; t < nt; t += 32) {
-      Tile tl;
-      tl.problem = slot;
-      tl.beg = (int)beg + t * p.TS;
-      tl.len = min(p.TS, (int)len - t * p.TS);
-      tl.tile_end = tb + nt;
-      tiles[tb + t] = tl;
+    // the warp writes the tiles of each accepted problem together
+    unsigned int wm = __ballot_sync(0xffffffffu, ok);
+    while (wm) {
+      const int src = __ffs(wm) - 1;
+      wm &= wm - 1;
+      const int s_slot = __shfl_sync(0xffffffffu, slot, src), s_nt = __shfl_sync(0xffffffffu, nt, src);
+      const int s_roi = __shfl_sync(0xffffffffu, roi, src), s_q = __shfl_sync(0xffffffffu, q, src);
+      const long long s_tb = __shfl_sync(0xffffffffu, tb, src), s_cb = __shfl_sync(0xffffffffu, cb, src);
+      const long long s_beg = __shfl_sync(0xffffffffu, beg, src), s_len = __shfl_sync(0xffffffffu, len, src);
+      const long long s_S = __shfl_sync(0xffffffffu, S, src);
+      const bool s_ovf = __shfl_sync(0xffffffffu, (int)ovf, src) != 0;
+      for (int t = lane; t < s_nt; t += 32) {
+        Tile tl;
+        tl.problem = s_slot;
+        tl.beg = (int)s_beg + t * p.TS;
+        tl.len = min(p.TS, (int)s_len - t * p.TS);
+        tl.tile_end = (int)s_tb + s_nt;
+        tl.roi = s_roi;
+        tl.q = s_q;
+        tl.pad0 = tl.pad1 = 0;
+        tiles[s_tb + t] = tl;
+        chunk0[s_tb + t] = s_ovf ? INT_MAX : (int)(s_cb + s_S - chunks_upto(s_nt - t));
+      }
     }
   }
 }
 
-// One warp per tile: bounding box of its FP32 positions.
+// T(F) of every problem from its seeded F (FP64, one thread per problem).
+__global__ void k_thresh(const RoiDiam* __restrict__ rd, const Problem* __restrict__ probs, Params p,
+                         const Counters* __restrict__ cnt, ProblemState* __restrict__ ps) {
+  const int np = (int)min((long long)cnt->n_problems, p.max_problems);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x)
+    ps[i].T = __float_as_uint(threshold(__uint_as_float(ps[i].F), rd[probs[i].roi]));
+}
+
+// One warp per tile: bounding box of its FP32 positions and its first vertex.
 __global__ void k_tile_box(const float4* __restrict__ sorted, const Tile* __restrict__ tiles, Params p,
                            const Counters* __restrict__ cnt, float4* __restrict__ box, float4* __restrict__ rep) {
-  const int nt = (int)min((long long)cnt->n_tiles, p.max_tiles);
+  const int nt = (int)min((long long)(cnt->alloc & 0xffffffffull), p.max_tiles);
   const int lane = threadIdx.x & 31;
   const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -386,147 +461,368 @@ __global__ void k_tile_box(const float4* __restrict__ sorted, const Tile* __rest
   }
 }
 
-// Seed: one warp per tile row a.  The pairs of tile representatives (first
-// vertex of each tile) of one problem, plus each tile's first-last pair, are
-// actual vertex pairs, so their largest f is a valid starting F.
-__global__ void k_seed_rows(const float4* __restrict__ sorted, const float4* __restrict__ rep, Params p,
-                            const RoiDiam* __restrict__ rd, const Problem* __restrict__ probs,
-                            const Tile* __restrict__ tiles, Counters* __restrict__ cnt,
-                            ProblemState* __restrict__ ps) {
-  const int nt = (int)min((long long)cnt->n_tiles, p.max_tiles);
+// ---- 3. seed and cull over (tile row, chunk) items ----------------------------------
+// The items of all problems are numbered 0..K-1 in tile order (chunk0[t] is
+// the first item of tile row t, non-decreasing).  Each warp takes an equal
+// contiguous range of items, finds its first row with a 32-way search and
+// then walks forward.
+
+__device__ __forceinline__ int warp_find_row(const int* chunk0, int nt, long long k) {
   const int lane = threadIdx.x & 31;
+  int lo = 0, hi = nt - 1;  // chunk0[lo] <= k; the row is in [lo, hi]
+  while (hi > lo) {         // warp-uniform; the range shrinks every step
+    const long long span = hi - lo;
+    const int pos = lo + (int)((span * (lane + 1) + 31) / 32);  // lane 31 probes hi
+    const unsigned int m = __ballot_sync(0xffffffffu, (long long)chunk0[pos] <= k);
+    if (m == 0) {
+      hi = __shfl_sync(0xffffffffu, pos, 0) - 1;
+    } else {
+      const int l = 31 - __clz(m);
+      const int plo = __shfl_sync(0xffffffffu, pos, l);
+      const int pnext = __shfl_sync(0xffffffffu, pos, l < 31 ? l + 1 : 31);
+      lo = plo;
+      if (l < 31) hi = pnext - 1;
+    }
+  }
+  return lo;
+}
+
+struct ChunkWalk {
+  long long k, kend;    // this warp's items
+  int a;                // current tile row
+  long long c0, next0;  // first item of row a and of row a + 1
+};
+
+__device__ __forceinline__ bool walk_begin(ChunkWalk& w, const int* chunk0, int nt, long long K) {
   const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long a = warp; a < nt; a += nwarps) {
-    const Tile ta = tiles[a];
-    const float4 ra = rep[a];
-    float best = lane == 0 ? pair_f(ra, sorted[ta.beg + ta.len - 1]) : 0.0f;
-    for (long long b = a + 1 + lane; b < ta.tile_end; b += 32) best = fmaxf(best, pair_f(ra, rep[b]));
-    for (int off = 16; off > 0; off >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, off));
-    if (lane == 0 && best > 0.0f) atomicMax(&ps[ta.problem].F, __float_as_uint(best));
-  }
-  // the last block turns every seeded F into its threshold T(F) (FP64 math
-  // once per problem instead of once per tile row)
-  __shared__ bool last;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    last = atomicAdd(&cnt->done, 1u) == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (last) {
-    __threadfence();
-    const int np = (int)min((long long)cnt->n_problems, p.max_problems);
-    for (int i = threadIdx.x; i < np; i += blockDim.x)
-      ps[i].T = __float_as_uint(threshold(__uint_as_float(__ldcg(&ps[i].F)), rd[probs[i].roi]));
-    __syncthreads();
-    if (threadIdx.x == 0) cnt->done = 0;
+  const long long per = (K + nwarps - 1) / nwarps;
+  w.k = warp * per;
+  w.kend = min(K, w.k + per);
+  if (nt <= 0 || w.k >= w.kend) return false;
+  w.a = warp_find_row(chunk0, nt, w.k);
+  w.c0 = chunk0[w.a];
+  w.next0 = w.a + 1 < nt ? (long long)chunk0[w.a + 1] : LLONG_MAX;
+  return true;
+}
+
+// Next row's entries, loaded one row ahead (every row has at least one item,
+// so the walk moves at most one row per item).
+struct RowAhead {
+  Tile t;
+  float4 v0, v1;    // seed: representative; cull: box
+  long long next1;  // first item of the row after it
+};
+
+__device__ __forceinline__ void row_ahead(RowAhead& r, const Tile* tiles, const float4* v, int stride,
+                                          const int* chunk0, int nt, int a) {
+  if (a + 1 < nt) {
+    r.t = tiles[a + 1];
+    r.v0 = v[stride * (a + 1)];
+    if (stride == 2) r.v1 = v[2 * (a + 1) + 1];
+    r.next1 = a + 2 < nt ? (long long)chunk0[a + 2] : LLONG_MAX;
   }
 }
 
-// ---- 3. culling -------------------------------------------------------------------
-// One warp per tile row a: every tile pair (a, b >= a) of the same problem
-// whose box bound reaches T(F) goes to the work list.
-__global__ void k_cull_rows(const Tile* __restrict__ tiles, const float4* __restrict__ box, Params p,
-                            const Problem* __restrict__ probs, Counters* __restrict__ cnt,
-                            ProblemState* __restrict__ ps, WorkItem* __restrict__ work) {
-  const int nt = (int)min((long long)cnt->n_tiles, p.max_tiles);
+__device__ __forceinline__ void seed_flush(float m, int problem, ProblemState* ps) {
+  for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+  if ((threadIdx.x & 31) == 0 && m > 0.0f) atomicMax(&ps[problem].F, __float_as_uint(m));
+}
+
+// Seed: the pairs of tile representatives (first vertices) in every tile
+// pair of a problem, plus each tile's first-last pair, are actual vertex
+// pairs, so their largest f is a valid starting F.
+__global__ void k_seed(const float4* __restrict__ sorted, const float4* __restrict__ rep, Params p,
+                       const Tile* __restrict__ tiles, const int* __restrict__ chunk0, const Counters* __restrict__ cnt,
+                       ProblemState* __restrict__ ps) {
+  const unsigned long long alloc = cnt->alloc;
+  const int nt = (int)min((long long)(alloc & 0xffffffffull), p.max_tiles);
+  const long long K = min((long long)(alloc >> 32), (long long)INT_MAX);
   const int lane = threadIdx.x & 31;
-  const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long a = warp; a < nt; a += nwarps) {
-    const Tile ta = tiles[a];
-    const float T = __uint_as_float(ps[ta.problem].T);
-    const int roi = probs[ta.problem].roi;
-    const float4 alo = box[2 * a], ahi = box[2 * a + 1];
-    for (long long b0 = a; b0 < ta.tile_end; b0 += 32) {
-      const long long b = b0 + lane;
-      bool keep = false;
-      if (b < ta.tile_end) keep = box_ub(alo, ahi, box[2 * b], box[2 * b + 1]) >= T;
-      const unsigned int m = __ballot_sync(0xffffffffu, keep);
-      if (!m) continue;
-      long long base = 0;
-      if (lane == 0) base = atomicAdd((unsigned long long*)&cnt->n_work, (unsigned long long)__popc(m));
-      base = __shfl_sync(0xffffffffu, base, 0);
-      if (keep) {
-        const long long slot = base + __popc(m & ((1u << lane) - 1u));
+  ChunkWalk w;
+  if (!walk_begin(w, chunk0, nt, K)) return;
+  Tile ta = tiles[w.a];
+  float4 ra = rep[w.a];
+  RowAhead nx;
+  row_ahead(nx, tiles, rep, 1, chunk0, nt, w.a);
+  float m = 0.0f;
+  for (; w.k < w.kend; ++w.k) {
+    if (w.k >= w.next0 && w.a + 1 < nt) {  // warp-uniform
+      seed_flush(m, ta.problem, ps);
+      m = 0.0f;
+      ++w.a;
+      ta = nx.t;
+      ra = nx.v0;
+      w.c0 = w.next0;
+      w.next0 = nx.next1;
+      row_ahead(nx, tiles, rep, 1, chunk0, nt, w.a);
+    }
+    const long long c = w.k - w.c0;
+    const long long b0 = w.a + c * kChunk;
+    if (c == 0 && lane == 0) m = fmaxf(m, pair_f(ra, sorted[ta.beg + ta.len - 1]));
+#pragma unroll
+    for (int u = 0; u < kChunk / 32; ++u) {
+      const long long b = b0 + 32 * u + lane;
+      if (b < ta.tile_end) m = fmaxf(m, pair_f(ra, rep[b]));
+    }
+  }
+  seed_flush(m, ta.problem, ps);
+}
+
+// Cull: every tile pair (a, b >= a) of a problem whose box bound reaches
+// T(F) goes to the work list, with both vertex ranges and the bound.
+__global__ void k_cull(const Tile* __restrict__ tiles, const float4* __restrict__ box, Params p,
+                       const int* __restrict__ chunk0, Counters* __restrict__ cnt, const ProblemState* __restrict__ ps,
+                       WorkItem* __restrict__ work) {
+  const unsigned long long alloc = cnt->alloc;
+  const int nt = (int)min((long long)(alloc & 0xffffffffull), p.max_tiles);
+  const long long K = min((long long)(alloc >> 32), (long long)INT_MAX);
+  const int lane = threadIdx.x & 31;
+  constexpr int U = kChunk / 32;
+  ChunkWalk w;
+  if (!walk_begin(w, chunk0, nt, K)) return;
+  Tile ta = tiles[w.a];
+  float4 alo = box[2 * w.a], ahi = box[2 * w.a + 1];
+  int problem = ta.problem;
+  float T = __uint_as_float(ps[problem].T);
+  RowAhead nx;
+  row_ahead(nx, tiles, box, 2, chunk0, nt, w.a);
+  for (; w.k < w.kend; ++w.k) {
+    if (w.k >= w.next0 && w.a + 1 < nt) {  // warp-uniform
+      ++w.a;
+      ta = nx.t;
+      alo = nx.v0;
+      ahi = nx.v1;
+      w.c0 = w.next0;
+      w.next0 = nx.next1;
+      row_ahead(nx, tiles, box, 2, chunk0, nt, w.a);
+      if (ta.problem != problem) {
+        problem = ta.problem;
+        T = __uint_as_float(ps[problem].T);
+      }
+    }
+    const long long b0 = w.a + (w.k - w.c0) * kChunk;
+    bool keep[U];
+    float ub[U];
+    unsigned int m[U];
+    int total = 0;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const long long b = b0 + 32 * u + lane;
+      keep[u] = false;
+      ub[u] = 0.0f;
+      if (b < ta.tile_end) {
+        ub[u] = box_ub(alo, ahi, box[2 * b], box[2 * b + 1]);
+        keep[u] = ub[u] >= T;
+      }
+      m[u] = __ballot_sync(0xffffffffu, keep[u]);
+      total += __popc(m[u]);
+    }
+    if (total == 0) continue;  // warp-uniform
+    long long base = 0;
+    if (lane == 0) base = (long long)atomicAdd((unsigned long long*)&cnt->n_work, (unsigned long long)total);
+    base = __shfl_sync(0xffffffffu, base, 0);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (keep[u]) {
+        const long long slot = base + __popc(m[u] & ((1u << lane) - 1u));
         if (slot < p.work_cap) {
-          WorkItem w;
-          w.problem = ta.problem; w.ta = (int)a; w.tb = (int)b; w.roi = roi;
-          work[slot] = w;
+          const Tile tb = tiles[b0 + 32 * u + lane];
+          WorkItem it;
+          it.problem = ta.problem; it.roi = ta.roi; it.q = ta.q;
+          it.abeg = ta.beg; it.alen = ta.len; it.bbeg = tb.beg; it.blen = tb.len;
+          it.ub = ub[u];
+          work[slot] = it;
         } else {
           atomicOr(&cnt->status, DEV_ERR_WORKCAP);
         }
       }
+      base += __popc(m[u]);
     }
   }
 }
 
-// Items whose FP32 maximum reaches the final threshold of their problem are
-// re-evaluated for candidates; list them compactly.
-__global__ void k_compact_items(const WorkItem* __restrict__ work, const float* __restrict__ itemmax, Params p,
-                                Counters* __restrict__ cnt, const ProblemState* __restrict__ ps,
-                                int* __restrict__ work2) {
-  const long long nwork = min(cnt->n_work, p.work_cap);
+// ---- 4. pair kernel -----------------------------------------------------------------
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned int s = (unsigned int)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// One warp item: tile A and the 32-entry slice s of tile B of a work item,
+// into the warp's own shared-memory buffers.  Entries past a tile's length
+// repeat its last vertex (a real vertex, so maxima are unaffected).
+template <int TS>
+__device__ __forceinline__ void stage_slice(float4* sA, float4* sB, const float4* sorted, const WorkItem& w, int s) {
   const int lane = threadIdx.x & 31;
-  for (long long i0 = blockIdx.x * (long long)blockDim.x; i0 < nwork; i0 += (long long)gridDim.x * blockDim.x) {
-    const long long i = i0 + threadIdx.x;
-    bool keep = false;
-    if (i < nwork) keep = itemmax[i] >= __uint_as_float(ps[work[i].problem].T);
-    const unsigned int m = __ballot_sync(0xffffffffu, keep);
-    if (!m) continue;
-    long long base = 0;
-    if (lane == 0) base = atomicAdd((unsigned long long*)&cnt->n_work2, (unsigned long long)__popc(m));
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (keep) work2[base + __popc(m & ((1u << lane) - 1u))] = (int)i;
+#pragma unroll
+  for (int r = 0; r < TS / 32; ++r) cp_async16(&sA[lane + 32 * r], &sorted[w.abeg + min(lane + 32 * r, w.alen - 1)]);
+  cp_async16(&sB[lane], &sorted[w.bbeg + min(32 * s + lane, w.blen - 1)]);
+}
+
+// Every warp works on its own over (tile pair, 32-entry B slice) warp items
+// g, g + W, g + 2W, ... (g its global warp index, W the number of warps; the
+// warps of one CTA take the slices of the same tile pair, which share tile A
+// in L1).  It stages the next item with cp.async while it evaluates the
+// current one (no block barrier anywhere), skips an item whose bound is below
+// the current T, and otherwise stores the slice maximum (lane l holds the A
+// entries l, l + 32, ...) and raises F (and T) when it beats F.
+// slicemax[warp item] < 0 marks a skipped or empty slice.
+template <int TS, int NT>
+__global__ void __launch_bounds__(NT) k_pairs(const float4* __restrict__ sorted, const WorkItem* __restrict__ work,
+                                              Params p, const RoiDiam* __restrict__ rd, Counters* __restrict__ cnt,
+                                              ProblemState* __restrict__ ps, float* __restrict__ slicemax) {
+  constexpr int RA = TS / 32;  // A entries per lane, and B slices per tile pair
+  constexpr int NWARP = NT / 32;
+  __shared__ __align__(16) float4 sA[NWARP][2][TS];
+  __shared__ __align__(16) float4 sB[NWARP][2][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const long long nws = min(cnt->n_work, p.work_cap) * RA;
+  const long long W = (long long)gridDim.x * NWARP;
+  long long t_cur = (long long)blockIdx.x * NWARP + wid;
+  if (t_cur >= nws) return;  // warp-uniform
+  WorkItem w_cur = work[t_cur / RA];
+  stage_slice<TS>(sA[wid][0], sB[wid][0], sorted, w_cur, (int)(t_cur % RA));
+  cp_async_commit();
+  unsigned long long ft_cur = *(volatile unsigned long long*)&ps[w_cur.problem];
+  long long t_nxt = t_cur + W;
+  WorkItem w_nxt = t_nxt < nws ? work[t_nxt / RA] : w_cur;
+  int buf = 0;
+  unsigned long long n_items = 0, n_pairs = 0;
+  while (true) {
+    const bool has_next = t_nxt < nws;
+    __syncwarp();  // every lane is done with the other buffer
+    unsigned long long ft_nxt = ft_cur;
+    if (has_next) {
+      stage_slice<TS>(sA[wid][buf ^ 1], sB[wid][buf ^ 1], sorted, w_nxt, (int)(t_nxt % RA));
+      ft_nxt = *(volatile unsigned long long*)&ps[w_nxt.problem];
+    }
+    cp_async_commit();
+    const long long t_nn = t_nxt + W;
+    const WorkItem w_nn = t_nn < nws ? work[t_nn / RA] : w_nxt;
+    cp_async_wait<1>();  // this lane's copies of the current item have landed
+    __syncwarp();        // ... and every lane's
+    const float F = __uint_as_float((unsigned int)ft_cur), T = __uint_as_float((unsigned int)(ft_cur >> 32));
+    const int s = (int)(t_cur % RA);
+    float m = -1.0f;
+    if (!(w_cur.ub < T) && 32 * s < w_cur.blen) {
+      float4 a[RA];
+#pragma unroll
+      for (int r = 0; r < RA; ++r) a[r] = sA[wid][buf][lane + 32 * r];
+      float mx[RA];
+#pragma unroll
+      for (int r = 0; r < RA; ++r) mx[r] = 0.0f;
+      const float4* sb = sB[wid][buf];
+#pragma unroll 8
+      for (int j = 0; j < 32; ++j) {
+        const float4 b = sb[j];
+#pragma unroll
+        for (int r = 0; r < RA; ++r) mx[r] = fmaxf(mx[r], pair_f(a[r], b));
+      }
+      m = mx[0];
+#pragma unroll
+      for (int r = 1; r < RA; ++r) m = fmaxf(m, mx[r]);
+      for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+      if (lane == 0) {
+        if (m > F) {
+          const unsigned int old = atomicMax(&ps[w_cur.problem].F, __float_as_uint(m));
+          if (__float_as_uint(m) > old) atomicMax(&ps[w_cur.problem].T, __float_as_uint(threshold(m, rd[w_cur.roi])));
+        }
+        n_items += s == 0;
+        n_pairs += (unsigned long long)w_cur.alen * (unsigned long long)min(32, w_cur.blen - 32 * s);
+      }
+    }
+    if (lane == 0) slicemax[t_cur] = m;
+    if (!has_next) break;
+    t_cur = t_nxt;
+    w_cur = w_nxt;
+    ft_cur = ft_nxt;
+    t_nxt = t_nn;
+    w_nxt = w_nn;
+    buf ^= 1;
+  }
+  cp_async_wait<0>();
+  if (lane == 0 && n_pairs) {
+    atomicAdd(&cnt->items_evaluated, n_items);
+    atomicAdd(&cnt->pairs_evaluated, n_pairs);
   }
 }
 
-// ---- 4./5. pair kernels ------------------------------------------------------------
-
-// Evaluates one tile pair from shared memory.  NT threads; lane l of every
-// warp holds the A entries l, l + 32, ...; warp w scans its slice of B.
-template <int TS, int NT, bool CAND>
-__device__ __forceinline__ float eval_pair_tile(const float4* __restrict__ sorted, const Tile& A, const Tile& B,
-                                                float4* sB, float T, int problem, int roi, Cand* cand, Counters* cnt,
-                                                long long cand_cap) {
+// Slices whose maximum reaches their problem's final T, listed compactly
+// (one lane per slice).
+template <int TS>
+__global__ void k_cand_list(const WorkItem* __restrict__ work, const float* __restrict__ slicemax, Params p,
+                            Counters* __restrict__ cnt, const ProblemState* __restrict__ ps, int* __restrict__ hits) {
   constexpr int RA = TS / 32;
-  constexpr int NWARP = NT / 32;
-  constexpr int BSL = TS / NWARP;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int i = threadIdx.x; i < TS; i += NT) sB[i] = i < B.len ? sorted[B.beg + i] : sorted[B.beg];
-  float4 a[RA];
-  for (int r = 0; r < RA; ++r) {
-    const int ia = lane + 32 * r;
-    a[r] = sorted[A.beg + min(ia, A.len - 1)];
-  }
-  __syncthreads();
-  float mx[RA];
-  for (int r = 0; r < RA; ++r) mx[r] = 0.0f;
-  const int jb = wid * BSL;
-  const int je = min(jb + BSL, B.len);
-  if (!CAND) {
-#pragma unroll 4
-    for (int j = jb; j < je; ++j) {
-      const float4 b = sB[j];
-#pragma unroll
-      for (int r = 0; r < RA; ++r) mx[r] = fmaxf(mx[r], pair_f(a[r], b));
+  const long long nslices = min(cnt->n_work, p.work_cap) * RA;
+  const int lane = threadIdx.x & 31;
+  for (long long s0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) - lane; s0 < nslices;
+       s0 += (long long)gridDim.x * blockDim.x) {
+    const long long sl = s0 + lane;
+    bool hit = false;
+    if (sl < nslices) {
+      const float m = slicemax[sl];
+      if (m >= 0.0f) hit = m >= __uint_as_float(ps[work[sl / RA].problem].T);
     }
-  } else {
-    for (int j = jb; j < je; ++j) {
-      const float4 b = sB[j];
+    const unsigned int hm = __ballot_sync(0xffffffffu, hit);
+    if (hm == 0) continue;
+    long long base = 0;
+    if (lane == 0) base = (long long)atomicAdd((unsigned long long*)&cnt->n_hits, (unsigned long long)__popc(hm));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (hit) hits[base + __popc(hm & ((1u << lane) - 1u))] = (int)sl;
+  }
+}
+
+// Candidates: one warp per listed slice rescans it (A entries in registers,
+// the 32 B entries one per lane, broadcast by shuffles) and lists its pairs
+// with f >= T.
+template <int TS>
+__global__ void k_cand(const float4* __restrict__ sorted, const WorkItem* __restrict__ work,
+                       const int* __restrict__ hits, Params p, Counters* __restrict__ cnt,
+                       const ProblemState* __restrict__ ps, Cand* __restrict__ cand) {
+  constexpr int RA = TS / 32;
+  const long long nh = cnt->n_hits;
+  const int lane = threadIdx.x & 31;
+  const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long h = warp; h < nh; h += nwarps) {
+    const int sl = hits[h];
+    const WorkItem w = work[sl / RA];
+    const float T = __uint_as_float(ps[w.problem].T);
+    const int jb = (sl % RA) * 32;
+    const bool same = w.abeg == w.bbeg;
+    float4 a[RA];
+#pragma unroll
+    for (int r = 0; r < RA; ++r) a[r] = sorted[w.abeg + min(lane + 32 * r, w.alen - 1)];
+    const float4 bl = sorted[w.bbeg + min(jb + lane, w.blen - 1)];
+    const int nj = min(32, w.blen - jb);
+    for (int jj = 0; jj < nj; ++jj) {
+      float4 b;
+      b.x = __shfl_sync(0xffffffffu, bl.x, jj);
+      b.y = __shfl_sync(0xffffffffu, bl.y, jj);
+      b.z = __shfl_sync(0xffffffffu, bl.z, jj);
+      b.w = 0.0f;
+      const int j = jb + jj;
+#pragma unroll
       for (int r = 0; r < RA; ++r) {
         const int ia = lane + 32 * r;
-        if (ia >= A.len) continue;
-        const int ea = A.beg + ia, eb = B.beg + j;
-        if (A.beg == B.beg && ea >= eb) continue;  // same tile: each unordered pair once
-        const float f = pair_f(a[r], b);
-        if (f >= T) {
-          const long long slot = atomicAdd((unsigned long long*)&cnt->n_cand, 1ull);
-          if (slot < cand_cap) {
-            Cand c;
-            c.ea = ea; c.eb = eb; c.problem = problem; c.roi = roi;
-            cand[slot] = c;
+        const bool c = ia < w.alen && (!same || ia < j) && pair_f(a[r], b) >= T;
+        const unsigned int cm = __ballot_sync(0xffffffffu, c);
+        if (cm == 0) continue;
+        long long base = 0;
+        if (lane == 0) base = (long long)atomicAdd((unsigned long long*)&cnt->n_cand, (unsigned long long)__popc(cm));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (c) {
+          const long long slot = base + __popc(cm & ((1u << lane) - 1u));
+          if (slot < p.cand_cap) {
+            Cand k;
+            k.ea = w.abeg + ia; k.eb = w.bbeg + j; k.roi = w.roi; k.q = w.q;
+            cand[slot] = k;
           } else {
             atomicOr(&cnt->status, DEV_ERR_CANDCAP);
           }
@@ -534,76 +830,16 @@ __device__ __forceinline__ float eval_pair_tile(const float4* __restrict__ sorte
       }
     }
   }
-  float m = 0.0f;
-  for (int r = 0; r < RA; ++r)
-    if (lane + 32 * r < A.len) m = fmaxf(m, mx[r]);
-  return m;
-}
-
-template <int TS, int NT>
-__global__ void __launch_bounds__(NT) k_pairs_max(const float4* __restrict__ sorted, const Tile* __restrict__ tiles,
-                                                  const float4* __restrict__ box, const WorkItem* __restrict__ work,
-                                                  Params p, const RoiDiam* __restrict__ rd,
-                                                  Counters* __restrict__ cnt, ProblemState* __restrict__ ps,
-                                                  float* __restrict__ itemmax) {
-  __shared__ float4 sB[TS];
-  __shared__ float sred[NT / 32];
-  const long long nwork = min(cnt->n_work, p.work_cap);
-  unsigned long long n_items = 0, n_pairs = 0;
-  for (long long it = blockIdx.x; it < nwork; it += gridDim.x) {
-    const WorkItem w = work[it];
-    // re-cull against the problem's current threshold (raised by other CTAs);
-    // threads may read different values, so the decision is block-wide
-    const float T = __uint_as_float(*(volatile unsigned int*)&ps[w.problem].T);
-    const float ub = box_ub(box[2 * w.ta], box[2 * w.ta + 1], box[2 * w.tb], box[2 * w.tb + 1]);
-    if (__syncthreads_and(ub < T)) {
-      if (threadIdx.x == 0) itemmax[it] = -1.0f;
-      continue;
-    }
-    const Tile A = tiles[w.ta], B = tiles[w.tb];
-    float m = eval_pair_tile<TS, NT, false>(sorted, A, B, sB, T, w.problem, w.roi, nullptr, cnt, 0);
-    for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
-    if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = m;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      float bm = sred[0];
-      for (int k = 1; k < NT / 32; ++k) bm = fmaxf(bm, sred[k]);
-      itemmax[it] = bm;
-      const unsigned int old = atomicMax(&ps[w.problem].F, __float_as_uint(bm));
-      if (__float_as_uint(bm) > old) atomicMax(&ps[w.problem].T, __float_as_uint(threshold(bm, rd[w.roi])));
-      n_items++;
-      n_pairs += (unsigned long long)A.len * (unsigned long long)B.len;
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0 && n_items) {
-    atomicAdd(&cnt->items_evaluated, n_items);
-    atomicAdd(&cnt->pairs_evaluated, n_pairs);
-  }
-}
-
-template <int TS, int NT>
-__global__ void __launch_bounds__(NT) k_pairs_cand(const float4* __restrict__ sorted, const Tile* __restrict__ tiles,
-                                                   const WorkItem* __restrict__ work, const int* __restrict__ work2,
-                                                   Params p, Counters* __restrict__ cnt,
-                                                   const ProblemState* __restrict__ ps, Cand* __restrict__ cand) {
-  __shared__ float4 sB[TS];
-  const long long n2 = cnt->n_work2;
-  for (long long k = blockIdx.x; k < n2; k += gridDim.x) {
-    const WorkItem w = work[work2[k]];
-    const float T = __uint_as_float(ps[w.problem].T);
-    const Tile A = tiles[w.ta], B = tiles[w.tb];
-    eval_pair_tile<TS, NT, true>(sorted, A, B, sB, T, w.problem, w.roi, cand, cnt, p.cand_cap);
-    __syncthreads();
-  }
 }
 
 // ---- 5. FP64 confirmation -------------------------------------------------------------
 
+// Largest pinned FP64 d2 per ROI and category.  Every pair attaining it is a
+// candidate of its problem, so the maximum over candidates is the maximum.
 __global__ void k_confirm(const float4* __restrict__ sorted, const int16_t* __restrict__ idx2,
                           const double* __restrict__ vt, Params p, const RoiDiam* __restrict__ rd,
                           const Counters* __restrict__ cnt, const Cand* __restrict__ cand,
-                          ProblemState* __restrict__ ps) {
+                          DiamOut* __restrict__ out) {
   const long long nc = min(cnt->n_cand, p.cand_cap);
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nc; c += (long long)gridDim.x * blockDim.x) {
     const Cand k = cand[c];
@@ -613,19 +849,26 @@ __global__ void k_confirm(const float4* __restrict__ sorted, const int16_t* __re
     vertex_u(idx2, vt, i, ui);
     vertex_u(idx2, vt, j, uj);
     const double d2 = pin_d2(ui[0], ui[1], ui[2], uj[0], uj[1], uj[2], r.sx, r.sy, r.sz);
-    atomicMax(&ps[k.problem].best_d2, (unsigned long long)__double_as_longlong(d2));
+    atomicMax(&out[k.roi].d2[k.q], (unsigned long long)__double_as_longlong(d2));
   }
 }
 
-// Candidates attaining their problem's maximum take the smallest (i, j)
-// (ids local to the ROI).  The last block to finish then reduces the
-// problems to one result per ROI and category (3D, Slice, Column, Row): first
-// the largest d2, then the smallest pair among the problems attaining it.
+// Candidates attaining their ROI's maximum in their category take the
+// smallest (i, j) (ids local to the ROI).  Block 0 also copies the counters.
 __global__ void k_tiebreak(const float4* __restrict__ sorted, const int16_t* __restrict__ idx2,
                            const double* __restrict__ vt, Params p, const RoiDiam* __restrict__ rd,
-                           const RoiOut* __restrict__ ro, Counters* __restrict__ cnt, const Cand* __restrict__ cand,
-                           ProblemState* __restrict__ ps, const Problem* __restrict__ probs,
-                           DiamOut* __restrict__ out, DiamStats* __restrict__ stats) {
+                           const RoiOut* __restrict__ ro, const Counters* __restrict__ cnt,
+                           const Cand* __restrict__ cand, DiamOut* __restrict__ out, DiamStats* __restrict__ stats) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    stats->problems = cnt->n_problems;
+    stats->tiles = (long long)(cnt->alloc & 0xffffffffull);
+    stats->tile_pairs = cnt->n_pairs;
+    stats->work_items = cnt->n_work;
+    stats->items_evaluated = (long long)cnt->items_evaluated;
+    stats->pairs_evaluated = (long long)cnt->pairs_evaluated;
+    stats->candidates = cnt->n_cand;
+    stats->status |= cnt->status;
+  }
   const long long nc = min(cnt->n_cand, p.cand_cap);
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nc; c += (long long)gridDim.x * blockDim.x) {
     const Cand k = cand[c];
@@ -635,48 +878,13 @@ __global__ void k_tiebreak(const float4* __restrict__ sorted, const int16_t* __r
     vertex_u(idx2, vt, i, ui);
     vertex_u(idx2, vt, j, uj);
     const double d2 = pin_d2(ui[0], ui[1], ui[2], uj[0], uj[1], uj[2], r.sx, r.sy, r.sz);
-    if ((unsigned long long)__double_as_longlong(d2) == __ldcg(&ps[k.problem].best_d2)) {
+    if ((unsigned long long)__double_as_longlong(d2) == __ldcg(&out[k.roi].d2[k.q])) {
       const long long v0 = ro[k.roi].v0;
       i -= (int)v0;
       j -= (int)v0;
       if (i > j) { const int t = i; i = j; j = t; }
-      atomicMin(&ps[k.problem].best_pair, ((unsigned long long)(unsigned int)i << 32) | (unsigned int)j);
+      atomicMin(&out[k.roi].pair[k.q], ((unsigned long long)(unsigned int)i << 32) | (unsigned int)j);
     }
-  }
-  __shared__ bool last;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    last = atomicAdd(&cnt->done, 1u) == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  const int np = (int)min((long long)cnt->n_problems, p.max_problems);
-  for (int i = threadIdx.x; i < np; i += blockDim.x) {
-    const Problem pr = probs[i];
-    if (__ldcg(&ps[i].best_pair) == ~0ull) continue;
-    const int q = pr.axis < 0 ? 0 : (pr.axis == 2 ? 1 : (pr.axis == 1 ? 2 : 3));
-    atomicMax(&out[pr.roi].d2[q], __ldcg(&ps[i].best_d2));
-  }
-  __threadfence();  // phase-1 atomics of every thread visible before phase 2
-  __syncthreads();
-  for (int i = threadIdx.x; i < np; i += blockDim.x) {
-    const Problem pr = probs[i];
-    const unsigned long long bp = __ldcg(&ps[i].best_pair);
-    if (bp == ~0ull) continue;
-    const int q = pr.axis < 0 ? 0 : (pr.axis == 2 ? 1 : (pr.axis == 1 ? 2 : 3));
-    if (__ldcg(&ps[i].best_d2) == __ldcg(&out[pr.roi].d2[q])) atomicMin(&out[pr.roi].pair[q], bp);
-  }
-  if (threadIdx.x == 0) {
-    stats->problems = cnt->n_problems;
-    stats->tiles = cnt->n_tiles;
-    stats->tile_pairs = cnt->n_pairs;
-    stats->work_items = cnt->n_work;
-    stats->items_evaluated = (long long)cnt->items_evaluated;
-    stats->pairs_evaluated = (long long)cnt->pairs_evaluated;
-    stats->candidates = cnt->n_cand;
-    stats->status |= cnt->status;
   }
 }
 
@@ -709,15 +917,14 @@ T* carve(char*& cur, size_t n) {
 }
 
 template <int TS, int NT>
-rad_status launch_pairs(const float4* sorted, const Tile* tiles, const float4* box, const WorkItem* work, int* work2,
-                        const Params& p, const RoiDiam* rd, Counters* cnt, ProblemState* ps, float* itemmax,
-                        Cand* cand, int ctas, cudaStream_t st) {
-  auto kmax = k_pairs_max<TS, NT>;
-  auto kcand = k_pairs_cand<TS, NT>;
-  const int sms = num_sms();
-  RAD_LAUNCH("diam_pairs_fp32", kmax, ctas, NT, 0, st, sorted, tiles, box, work, p, rd, cnt, ps, itemmax);
-  RAD_LAUNCH("diam_compact", k_compact_items, sms * 4, 256, 0, st, work, itemmax, p, cnt, ps, work2);
-  RAD_LAUNCH("diam_pairs_cand", kcand, ctas, NT, 0, st, sorted, tiles, work, work2, p, cnt, ps, cand);
+rad_status launch_pairs(const float4* sorted, const WorkItem* work, const Params& p, const RoiDiam* rd, Counters* cnt,
+                        ProblemState* ps, float* slicemax, int* hits, Cand* cand, int ctas, cudaStream_t st) {
+  auto kp = k_pairs<TS, NT>;
+  auto kl = k_cand_list<TS>;
+  auto kc = k_cand<TS>;
+  RAD_LAUNCH("diam_pairs_fp32", kp, ctas, NT, 0, st, sorted, work, p, rd, cnt, ps, slicemax);
+  RAD_LAUNCH("diam_cand_list", kl, num_sms() * 4, 256, 0, st, work, slicemax, p, cnt, ps, hits);
+  RAD_LAUNCH("diam_pairs_cand", kc, num_sms() * 4, 256, 0, st, sorted, work, hits, p, cnt, ps, cand);
   return RAD_OK;
 }
 
@@ -798,13 +1005,14 @@ rad_status diam_run(int n, const RoiDiam* rd, const RoiOut* ro, const long long*
   add(sizeof(float4) * nsorted);
   add(sizeof(Problem) * p.max_problems);
   add(sizeof(Tile) * p.max_tiles);
+  add(sizeof(int) * p.max_tiles);    // chunk0
   add(sizeof(float4) * 2 * p.max_tiles);
   add(sizeof(float4) * p.max_tiles);
   add(sizeof(ProblemState) * p.max_problems);
   add(sizeof(Counters));
   add(sizeof(WorkItem) * p.work_cap);
-  add(sizeof(float) * p.work_cap);
-  add(sizeof(int) * p.work_cap);
+  add(sizeof(float) * 8 * p.work_cap);  // slice maxima (up to 8 slices per item)
+  add(sizeof(int) * 8 * p.work_cap);    // slices to rescan
   add(sizeof(Cand) * p.cand_cap);
   RAD_TRY(s.misc.reserve(bytes));
   char* cur = s.misc.as<char>();
@@ -815,13 +1023,14 @@ rad_status diam_run(int n, const RoiDiam* rd, const RoiOut* ro, const long long*
   float4* sorted = carve<float4>(cur, nsorted);
   Problem* probs = carve<Problem>(cur, p.max_problems);
   Tile* tiles = carve<Tile>(cur, p.max_tiles);
+  int* chunk0 = carve<int>(cur, p.max_tiles);
   float4* box = carve<float4>(cur, 2 * p.max_tiles);
   float4* rep = carve<float4>(cur, p.max_tiles);
   ProblemState* ps = carve<ProblemState>(cur, p.max_problems);
   Counters* cnt = carve<Counters>(cur, 1);
   WorkItem* work = carve<WorkItem>(cur, p.work_cap);
-  float* itemmax = carve<float>(cur, p.work_cap);
-  int* work2 = carve<int>(cur, p.work_cap);
+  float* slicemax = carve<float>(cur, 8 * p.work_cap);
+  int* hits = carve<int>(cur, 8 * p.work_cap);
   Cand* cand = carve<Cand>(cur, p.cand_cap);
 
   const int sms = num_sms();
@@ -834,25 +1043,25 @@ rad_status diam_run(int n, const RoiDiam* rd, const RoiOut* ro, const long long*
   RAD_LAUNCH("diam_scan_part", k_xscan_part, (int)nparts, kScanBlock, 0, st, hist, K1, offs, parts);
   RAD_LAUNCH("diam_scan_top", k_xscan_top, 1, 1024, 0, st, parts, (int)nparts);
   RAD_LAUNCH("diam_scatter", k_scatter, vblocks, 256, 0, st, idx2, vt, nv_dev, rd, ro, p, offs, parts, cursor, sorted);
-  RAD_LAUNCH("diam_setup", k_setup, sms * 4, 256, 0, st, rd, p, offs, parts, probs, tiles, ps, cnt);
+  RAD_LAUNCH("diam_setup", k_setup, sms * 4, 256, 0, st, rd, p, offs, parts, probs, tiles, chunk0, ps, cnt);
   RAD_LAUNCH("diam_tile_box", k_tile_box, sms * 8, 256, 0, st, sorted, tiles, p, cnt, box, rep);
-  RAD_LAUNCH("diam_seed", k_seed_rows, sms * 8, 256, 0, st, sorted, rep, p, rd, probs, tiles, cnt, ps);
-  RAD_LAUNCH("diam_cull", k_cull_rows, sms * 8, 256, 0, st, tiles, box, p, probs, cnt, ps, work);
+  RAD_LAUNCH("diam_seed", k_seed, sms * 8, 256, 0, st, sorted, rep, p, tiles, chunk0, cnt, ps);
+  RAD_LAUNCH("diam_thresh", k_thresh, sms * 2, 256, 0, st, rd, probs, p, cnt, ps);
+  RAD_LAUNCH("diam_cull", k_cull, sms * 8, 256, 0, st, tiles, box, p, chunk0, cnt, ps, work);
   const int ctas = sms * tu.ctas_per_sm;
   if (tu.tile == 64) {
-    if (tu.threads == 64) RAD_TRY((launch_pairs<64, 64>(sorted, tiles, box, work, work2, p, rd, cnt, ps, itemmax, cand, ctas, st)));
-    else RAD_TRY((launch_pairs<64, 128>(sorted, tiles, box, work, work2, p, rd, cnt, ps, itemmax, cand, ctas, st)));
+    if (tu.threads == 64) RAD_TRY((launch_pairs<64, 64>(sorted, work, p, rd, cnt, ps, slicemax, hits, cand, ctas, st)));
+    else RAD_TRY((launch_pairs<64, 128>(sorted, work, p, rd, cnt, ps, slicemax, hits, cand, ctas, st)));
   } else if (tu.tile == 128) {
-    if (tu.threads == 64) RAD_TRY((launch_pairs<128, 64>(sorted, tiles, box, work, work2, p, rd, cnt, ps, itemmax, cand, ctas, st)));
-    else if (tu.threads == 128) RAD_TRY((launch_pairs<128, 128>(sorted, tiles, box, work, work2, p, rd, cnt, ps, itemmax, cand, ctas, st)));
-    else RAD_TRY((launch_pairs<128, 256>(sorted, tiles, box, work, work2, p, rd, cnt, ps, itemmax, cand, ctas, st)));
+    if (tu.threads == 64) RAD_TRY((launch_pairs<128, 64>(sorted, work, p, rd, cnt, ps, slicemax, hits, cand, ctas, st)));
+    else if (tu.threads == 128) RAD_TRY((launch_pairs<128, 128>(sorted, work, p, rd, cnt, ps, slicemax, hits, cand, ctas, st)));
+    else RAD_TRY((launch_pairs<128, 256>(sorted, work, p, rd, cnt, ps, slicemax, hits, cand, ctas, st)));
   } else {
-    if (tu.threads == 128) RAD_TRY((launch_pairs<256, 128>(sorted, tiles, box, work, work2, p, rd, cnt, ps, itemmax, cand, ctas, st)));
-    else RAD_TRY((launch_pairs<256, 256>(sorted, tiles, box, work, work2, p, rd, cnt, ps, itemmax, cand, ctas, st)));
+    if (tu.threads == 64) RAD_TRY((launch_pairs<256, 64>(sorted, work, p, rd, cnt, ps, slicemax, hits, cand, ctas, st)));
+    else RAD_TRY((launch_pairs<256, 128>(sorted, work, p, rd, cnt, ps, slicemax, hits, cand, ctas, st)));
   }
-  RAD_LAUNCH("diam_confirm", k_confirm, sms * 4, 256, 0, st, sorted, idx2, vt, p, rd, cnt, cand, ps);
-  RAD_LAUNCH("diam_tiebreak", k_tiebreak, sms * 4, 256, 0, st, sorted, idx2, vt, p, rd, ro, cnt, cand, ps, probs, out,
-             stats);
+  RAD_LAUNCH("diam_confirm", k_confirm, sms, 256, 0, st, sorted, idx2, vt, p, rd, cnt, cand, out);
+  RAD_LAUNCH("diam_tiebreak", k_tiebreak, sms, 256, 0, st, sorted, idx2, vt, p, rd, ro, cnt, cand, out, stats);
   return RAD_OK;
 }
 

@@ -133,7 +133,8 @@ def test_extract_paths_agree():
     assert_features(rad.extract(torch.from_numpy(m2).cuda(), (0.5, 0.5, 1.0), ws), ref2)
 
 
-@pytest.mark.parametrize("tuning", [dict(tile=64, threads=64, cell_shift=3), dict(tile=256, threads=256, cell_shift=5),
+@pytest.mark.parametrize("tuning", [dict(tile=64, threads=64, cell_shift=3), dict(tile=256, threads=128, cell_shift=5),
+                                    dict(tile=256, threads=64, ctas_per_sm=2, cell_shift=4),
                                     dict(tile=128, threads=64, ctas_per_sm=1, cell_shift=2)])
 def test_tuning_variants_same_result(tuning):
     rng = np.random.default_rng(10)
