@@ -51,6 +51,7 @@ struct BinCase {
   unsigned char tri[MC_MAX_TRI][3];  // local edge triples
   int nsum[3];                        // sum of (B - A) x (C - A), local doubled positions
   int tsum;                           // sum of A . (B x C)
+  unsigned long long tri4;            // the same triples, 4 bits per edge (nibble 3 t + k)
   double area2;                       // sum of twice the physical triangle areas
 };
 
@@ -408,6 +409,7 @@ __global__ void k_binary_table(const double* __restrict__ spacings, BinCase* __r
   }
   BinCase out;
   out.ntri = 0;
+  out.tri4 = 0ull;
   out.nsum[0] = out.nsum[1] = out.nsum[2] = 0;
   out.tsum = 0;
   out.area2 = 0.0;
@@ -422,6 +424,8 @@ __global__ void k_binary_table(const double* __restrict__ spacings, BinCase* __r
       out.tri[out.ntri][0] = (unsigned char)e0;
       out.tri[out.ntri][1] = (unsigned char)e1;
       out.tri[out.ntri][2] = (unsigned char)e2;
+      out.tri4 |= ((unsigned long long)e0 | ((unsigned long long)e1 << 4) | ((unsigned long long)e2 << 8))
+                  << (12 * out.ntri);
       out.ntri++;
       const int* A = lp[e0];
       const int* B = lp[e1];
@@ -744,6 +748,249 @@ __global__ void __launch_bounds__(kCubeThreads) k_cubes(const uint32_t* __restri
   }
 }
 
+// ---- binary masks: vertices and triangles in one pass -------------------------------
+// One warp per row group, as in k_count.  Every lane keeps, for its word, the
+// eight corner rows of its cubes and the crossing masks and row-local vertex
+// prefixes of the four owner rows (y, z), (y+1, z), (y, z+1), (y+1, z+1) in
+// shared memory (one array per quantity, so lanes hit distinct banks).  Each
+// lane writes the vertices of its own word (ids: the first row's base plus a
+// warp prefix).  The active cubes are listed in canonical order and taken 32
+// at a time, one per lane, so a long run of surface in one word is shared by
+// the whole warp; a cube's vertex ids come from the owner-row masks of its
+// word (or the next word) and its triangle ids from a running prefix.
+constexpr int kEmitThreads = 128;
+constexpr int kEmitWarps = kEmitThreads / 32;
+constexpr int kListCap = 32 * 32 + 32;  // 32 words x 32 bits + one x = -1 entry per row
+
+struct __align__(16) EmitRow {
+  long long vb[4];      // first vertex id of the four owner rows (0 where the row does not exist)
+  int y, z, roi, tab;
+  int ox0, oy0, oz0, pad;  // -(n - 1) per axis: half-voxel offsets to the padded-box centre
+};
+
+struct __align__(16) EmitShared {
+  uint32_t cw[8][32];  // per lane: rows (y,z) (y+1,z) (y,z+1) (y+1,z+1) at x and x + 1: a, as, b, bs, c, cs, e, es
+  int4 own[4][32];     // per owner row, per lane: ex, ey, ez, row-local vertex prefix
+  EmitRow row[32];     // per row of the warp
+  unsigned short list[kListCap];
+};
+
+__device__ __forceinline__ int warp_incl(int v, int lane) {
+  for (int off = 1; off < 32; off <<= 1) {
+    const int o = __shfl_up_sync(0xffffffffu, v, off);
+    if (lane >= off) v += o;
+  }
+  return v;
+}
+
+// Crossing masks and row-local vertex prefix of owner row (yo, zo) at word wo
+// straight from global memory (the next word of a lane that holds the last
+// word of an iteration; only rows wider than 32 words).
+__device__ int4 owner_global(const uint32_t* bits, const Roi& r, const int* wpre, int yo, int zo, int wo) {
+  const uint32_t* R0 = brow(bits, r, yo, zo);
+  const uint32_t b = R0[wo], bn = ldw(R0, wo + 1, r.W);
+  int4 o;
+  o.x = (int)(b ^ shift1(b, bn));
+  o.y = (int)(b ^ brow(bits, r, yo + 1, zo)[wo]);
+  o.z = (int)(b ^ brow(bits, r, yo, zo + 1)[wo]);
+  const long long g = r.row0 + (long long)(zo + 1) * (r.ny + 1) + (yo + 1);
+  o.w = wpre[r.wpre0 + (g - r.row0) * (long long)r.W + wo];
+  return o;
+}
+
+// Local edge e = (corner, axis) in canonical (cz, cy, cx, axis) order, as packed constants.
+constexpr unsigned long long kEdgeCorner = 0ull | (0ull << 3) | (0ull << 6) | (1ull << 9) | (1ull << 12) |
+                                           (2ull << 15) | (2ull << 18) | (3ull << 21) | (4ull << 24) |
+                                           (4ull << 27) | (5ull << 30) | (6ull << 33);
+constexpr unsigned int kEdgeAxis = (0u << 0) | (1u << 2) | (2u << 4) | (1u << 6) | (2u << 8) | (0u << 10) |
+                                   (2u << 12) | (2u << 14) | (0u << 16) | (1u << 18) | (1u << 20) | (0u << 22);
+
+__global__ void __launch_bounds__(kEmitThreads, 8)
+    k_emit(const uint32_t* __restrict__ bits, const Roi* __restrict__ rois, int n, long long total_rows, int L, int Wc,
+           const int4* __restrict__ counts, const int* __restrict__ wpre, const long long* __restrict__ prefix,
+           const long long* __restrict__ chunk, const BinCase* __restrict__ tab, int16_t* __restrict__ idx2,
+           int32_t* __restrict__ tri, long long vcap, long long tcap, MeshTotals* __restrict__ tot,
+           RoiOut* __restrict__ out, unsigned long long* __restrict__ case_hist) {
+  __shared__ EmitShared sh[kEmitWarps];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, sub = lane % L, grp = lane / L, gpw = 32 / L;
+  const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  EmitShared& S = sh[wid];
+  unsigned int err = 0;
+  for (long long base = warp * gpw; base < total_rows; base += nwarps * gpw) {
+    const RowItem it = row_item(rois, n, total_rows, base + grp);
+    const int4 rc = it.valid ? counts[it.g] : make_int4(0, 0, 0, 0);
+    if (__all_sync(0xffffffffu, rc.x == 0 && rc.w == 0)) continue;
+    const Roi& r = rois[it.roi];
+    const int y = it.y, z = it.z, W = r.W;
+    // owner row k = cy + 2 cz exists for y + cy <= ny - 1 and z + cz <= nz - 1
+    const bool oky = y + 1 <= r.ny - 1, okz = z + 1 <= r.nz - 1;
+    if (sub == 0) {
+      EmitRow er;
+      er.vb[0] = it.valid ? row_base(prefix, chunk, it.g, 0) : 0;
+      er.vb[1] = it.valid && oky ? row_base(prefix, chunk, it.g + 1, 0) : 0;
+      er.vb[2] = it.valid && okz ? row_base(prefix, chunk, it.g + r.ny + 1, 0) : 0;
+      er.vb[3] = it.valid && oky && okz ? row_base(prefix, chunk, it.g + r.ny + 2, 0) : 0;
+      er.y = y; er.z = z; er.roi = it.roi; er.tab = r.tab;
+      er.ox0 = -(r.nx - 1); er.oy0 = -(r.ny - 1); er.oz0 = -(r.nz - 1); er.pad = 0;
+      S.row[grp] = er;
+    }
+    long long trun = row_base(prefix, chunk, base, 1);  // triangle ids continue over the warp's rows
+    const long long vfirst = row_base(prefix, chunk, base, 0);
+    const uint32_t* R0 = brow(bits, r, y, z);  // bit row (y + dy, z + dz) = R0 + (dz * BY + dy) * W
+    const long long BW = (long long)r.BY * W;
+    const long long wrow = r.wpre0 + (it.g - r.row0) * (long long)W;  // wpre row (y, z); (y+1) + W; (z+1) + (ny+1) W
+    const long long WZ = (long long)(r.ny + 1) * W;
+    long long vcarry = 0;  // vertices of the warp's earlier words
+    for (int w0 = 0; w0 < Wc; w0 += L) {
+      const int w = w0 + sub;
+      const bool live = it.valid && w < W;
+      uint32_t a = 0, as = 0, b = 0, bs = 0, c = 0, cs = 0, e = 0, es = 0, u = 0, act = 0;
+      if (live) {
+        a = R0[w]; b = R0[W + w]; c = R0[BW + w]; e = R0[BW + W + w];
+        as = shift1(a, ldw(R0, w + 1, W)); bs = shift1(b, ldw(R0 + W, w + 1, W));
+        cs = shift1(c, ldw(R0 + BW, w + 1, W)); es = shift1(e, ldw(R0 + BW + W, w + 1, W));
+        const uint32_t f = R0[2 * W + w], g = R0[2 * BW + w], h = R0[BW + 2 * W + w], i2 = R0[2 * BW + W + w];
+        S.own[0][lane] = make_int4((int)(a ^ as), (int)(a ^ b), (int)(a ^ c), wpre[wrow + w]);
+        S.own[1][lane] = make_int4((int)(b ^ bs), (int)(b ^ f), (int)(b ^ e), oky ? wpre[wrow + W + w] : 0);
+        S.own[2][lane] = make_int4((int)(c ^ cs), (int)(c ^ e), (int)(c ^ g), okz ? wpre[wrow + WZ + w] : 0);
+        S.own[3][lane] =
+            make_int4((int)(e ^ es), (int)(e ^ h), (int)(e ^ i2), oky && okz ? wpre[wrow + WZ + W + w] : 0);
+        u = (a ^ as) | (a ^ b) | (a ^ c);
+        act = (a | as | b | bs | c | cs | e | es) & ~(a & as & b & bs & c & cs & e & es);
+      }
+      S.cw[0][lane] = a; S.cw[1][lane] = as; S.cw[2][lane] = b; S.cw[3][lane] = bs;
+      S.cw[4][lane] = c; S.cw[5][lane] = cs; S.cw[6][lane] = e; S.cw[7][lane] = es;
+      // the x = -1 vertex (x-edge into voxel 0) and cube (corners at voxel 0) open the row
+      const bool first = w0 == 0 && sub == 0 && live;
+      const bool m1v = first && (a & 1u);
+      const int case_m1 = first ? (int)(((a & 1u) << 1) | ((b & 1u) << 3) | ((c & 1u) << 5) | ((e & 1u) << 7)) : 0;
+
+      // ---- vertices of owner row (y, z): each lane writes its own word's ----------
+      {
+        const uint32_t ex = a ^ as, ey = a ^ b, ez = a ^ c;
+        const int nv = __popc(ex) + __popc(ey) + __popc(ez) + (m1v ? 1 : 0);
+        const int vin = warp_incl(nv, lane);
+        long long id = vfirst + vcarry + vin - nv;
+        vcarry += __shfl_sync(0xffffffffu, vin, 31);
+        const int16_t qy = (int16_t)(2 * y), qz = (int16_t)(2 * z);
+        if (m1v) {
+          if (id < vcap) {
+            idx2[3 * id] = (int16_t)(-1); idx2[3 * id + 1] = qy; idx2[3 * id + 2] = qz;
+          } else {
+            err |= DEV_ERR_VCAP;
+          }
+          ++id;
+        }
+        for (uint32_t m = u; m; m &= m - 1) {
+          const int bit = __ffs(m) - 1, x = 32 * w + bit;
+          const int16_t qx = (int16_t)(2 * x);
+#pragma unroll
+          for (int ax = 0; ax < 3; ++ax) {
+            if (!((((ax == 0 ? ex : (ax == 1 ? ey : ez)) >> bit) & 1u))) continue;
+            if (id < vcap) {
+              idx2[3 * id] = (int16_t)(qx + (ax == 0));
+              idx2[3 * id + 1] = (int16_t)(qy + (ax == 1));
+              idx2[3 * id + 2] = (int16_t)(qz + (ax == 2));
+            } else {
+              err |= DEV_ERR_VCAP;
+            }
+            ++id;
+          }
+        }
+      }
+
+      // ---- active cubes: triangles, volume and case counts ------------------------
+      const int cc = __popc(act) + (case_m1 ? 1 : 0);
+      const int cin = warp_incl(cc, lane);
+      const int ctot = __shfl_sync(0xffffffffu, cin, 31);
+      if (ctot == 0) continue;  // warp-uniform
+      {
+        int o = cin - cc;
+        if (case_m1) S.list[o++] = (unsigned short)((lane << 6) | 32);
+        for (uint32_t m = act; m; m &= m - 1) S.list[o++] = (unsigned short)((lane << 6) | (__ffs(m) - 1));
+      }
+      __syncwarp();
+      for (int j0 = 0; j0 < ctot; j0 += 32) {
+        const int j = j0 + lane;
+        int src = 0, bit = 0, cs = 0, ntri = 0, roi = -1;
+        const BinCase* bc = nullptr;
+        if (j < ctot) {
+          const unsigned short en = S.list[j];
+          src = en >> 6;
+          bit = en & 63;
+          const int bq = bit == 32 ? 0 : bit;
+          const uint32_t k0 = S.cw[0][src] >> bq, k1 = S.cw[1][src] >> bq, k2 = S.cw[2][src] >> bq,
+                         k3 = S.cw[3][src] >> bq, k4 = S.cw[4][src] >> bq, k5 = S.cw[5][src] >> bq,
+                         k6 = S.cw[6][src] >> bq, k7 = S.cw[7][src] >> bq;
+          cs = bit == 32 ? (int)(((k0 & 1u) << 1) | ((k2 & 1u) << 3) | ((k4 & 1u) << 5) | ((k6 & 1u) << 7))
+                         : (int)((k0 & 1u) | ((k1 & 1u) << 1) | ((k2 & 1u) << 2) | ((k3 & 1u) << 3) |
+                                 ((k4 & 1u) << 4) | ((k5 & 1u) << 5) | ((k6 & 1u) << 6) | ((k7 & 1u) << 7));
+          const EmitRow& er = S.row[src / L];
+          roi = er.roi;
+          bc = &tab[er.tab * 256 + cs];
+          ntri = bc->ntri;
+        }
+        const int tin = warp_incl(ntri, lane);
+        const int ttot = __shfl_sync(0xffffffffu, tin, 31);
+        long long vsum = 0;
+        if (j < ctot) {
+          const EmitRow& er = S.row[src / L];
+          const int ws = w0 + src % L;
+          const int x = bit == 32 ? -1 : 32 * ws + bit;
+          const unsigned long long t4 = bc->tri4;
+          long long tid = trun + tin - ntri;
+          for (int t = 0; t < ntri; ++t, ++tid) {
+            int vid[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+              const int ed = (int)((t4 >> (12 * t + 4 * k)) & 15ull);
+              const int corner = (int)((kEdgeCorner >> (3 * ed)) & 7ull), ax = (int)((kEdgeAxis >> (2 * ed)) & 3u);
+              const int orow = ((corner >> 1) & 1) + 2 * (corner >> 2);
+              const int xo = x + (corner & 1);
+              int rank = 0;  // owner x = -1: the row's first vertex
+              if (xo >= 0) {
+                const int wo = xo >> 5, bo = xo & 31;
+                int4 ow;
+                if (wo == ws) ow = S.own[orow][src];
+                else if (src % L + 1 < L) ow = S.own[orow][src + 1];
+                else ow = owner_global(bits, rois[roi], wpre, er.y + (orow & 1), er.z + (orow >> 1), wo);
+                const uint32_t low = (1u << bo) - 1u;
+                rank = ow.w + __popc((uint32_t)ow.x & low) + __popc((uint32_t)ow.y & low) +
+                       __popc((uint32_t)ow.z & low);
+                if (ax >= 1) rank += ((uint32_t)ow.x >> bo) & 1u;
+                if (ax >= 2) rank += ((uint32_t)ow.y >> bo) & 1u;
+              }
+              vid[k] = (int)(er.vb[orow] + rank);
+            }
+            if (tid < tcap) {
+              tri[3 * tid] = vid[0];
+              tri[3 * tid + 1] = vid[1];
+              tri[3 * tid + 2] = vid[2];
+            } else {
+              err |= DEV_ERR_TCAP;
+            }
+          }
+          // exact volume in half-voxel units relative to the padded-box centre
+          const long long ox = 2LL * x + er.ox0, oy = 2LL * er.y + er.oy0, oz = 2LL * er.z + er.oz0;
+          vsum = ox * bc->nsum[0] + oy * bc->nsum[1] + oz * bc->nsum[2] + bc->tsum;
+        }
+        // |vsum| of one cube < 5e6, so a warp's sum fits in 32 bits
+        const unsigned int same_roi = __match_any_sync(0xffffffffu, roi);
+        const int vs = __reduce_add_sync(same_roi, (int)vsum);
+        if (roi >= 0 && lane == __ffs(same_roi) - 1 && vs)
+          atomicAdd((unsigned long long*)&out[roi].vsum, (unsigned long long)(long long)vs);
+        const long long key = roi >= 0 ? (long long)roi * 256 + cs : -1;
+        const unsigned int same_case = __match_any_sync(0xffffffffu, key);
+        if (roi >= 0 && lane == __ffs(same_case) - 1) atomicAdd(&case_hist[key], (unsigned long long)__popc(same_case));
+        trun += ttot;
+      }
+      __syncwarp();
+    }
+  }
+  if (err) atomicOr(&tot->status, err);
+}
+
 // Mask volume and area per ROI (one block per ROI, fixed order):
 //   6V = det(diag(s / 2)) * vsum,  2A = sum over cases of count * area2 of the case.
 __global__ void k_mask_totals(const Roi* __restrict__ rois, int n, const BinCase* __restrict__ tab,
@@ -823,7 +1070,7 @@ rad_status mesh_emit(const MeshBatch& b, MeshScratch& s, MeshTotals* tot, RoiOut
                      int32_t* tri, long long vcap, long long tcap, cudaStream_t st) {
   // every active cube has at least one triangle: the cube list fits in tcap
   const long long ccap = std::max<long long>(tcap, 1);
-  RAD_TRY(s.cubes.reserve(sizeof(int4) * ccap));
+  if (b.soft) RAD_TRY(s.cubes.reserve(sizeof(int4) * ccap));
   const int sms = num_sms();
   const long long warps_needed = (b.rows + (32 / b.L) - 1) / (32 / b.L);
   const int rblocks = (int)std::max<long long>(1, std::min<long long>((warps_needed + 7) / 8, (long long)sms * 8));
@@ -837,13 +1084,12 @@ rad_status mesh_emit(const MeshBatch& b, MeshScratch& s, MeshTotals* tot, RoiOut
                (const BinCase*)nullptr, tri, ccap, tcap, tot, out, s.hist.as<unsigned long long>(),
                s.partial.as<double>());
   } else {
-    RAD_LAUNCH("mc_rows", k_rows<false>, rblocks, 256, 0, st, s.bits.as<uint32_t>(), b.rois, b.n, b.rows, b.L, b.Wc,
-               s.counts.as<int4>(), s.wpre.as<int>(), s.prefix.as<long long>(), s.chunk.as<long long>(), idx2,
-               (double*)nullptr, s.cubes.as<int4>(), vcap, ccap, tot);
-    RAD_LAUNCH("mc_cubes", k_cubes<false>, cblocks, kCubeThreads, 0, st, s.bits.as<uint32_t>(), b.rois, b.n,
-               s.wpre.as<int>(), s.prefix.as<long long>(), s.chunk.as<long long>(), s.cubes.as<int4>(),
-               s.bintab.as<BinCase>(), tri, ccap, tcap, tot, out, s.hist.as<unsigned long long>(),
-               s.partial.as<double>());
+    const long long ewarps = (b.rows + (32 / b.L) - 1) / (32 / b.L);
+    const int eblocks =
+        (int)std::max<long long>(1, std::min<long long>((ewarps + kEmitWarps - 1) / kEmitWarps, (long long)sms * 16));
+    RAD_LAUNCH("mc_emit", k_emit, eblocks, kEmitThreads, 0, st, s.bits.as<uint32_t>(), b.rois, b.n, b.rows, b.L, b.Wc,
+               s.counts.as<int4>(), s.wpre.as<int>(), s.prefix.as<long long>(), s.chunk.as<long long>(),
+               s.bintab.as<BinCase>(), idx2, tri, vcap, tcap, tot, out, s.hist.as<unsigned long long>());
     RAD_LAUNCH("mc_mask_totals", k_mask_totals, std::min(b.n, sms * 8), 256, 0, st, b.rois, b.n,
                s.bintab.as<BinCase>(), s.hist.as<unsigned long long>(), out);
   }
