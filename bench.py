@@ -144,8 +144,9 @@ def kernel_work(name, ctx):
     table = {
         "mc_pack_u8": nvox + words4,                    # mask in, bitset out
         "mc_count": words4 + 16 * R + 4 * R * W,        # bitset in, row counts + word prefixes out
-        "mc_rows": 6 * N + 16 * na,                     # vertices + active-cube list out
-        "mc_cubes": 16 * na + 12 * T,                   # cube list in, triangles out
+        "mc_emit": words4 + 4 * R * W + 32 * R + 6 * N + 12 * T,  # bitset, word prefixes, row bases in;
+                                                                    # vertices and triangles out
+        "mc_scan_chunks": 16 * R + 32 * R,              # row counts in, row prefixes out
         "diam_hist": 6 * N,                             # vertices in
         "diam_scatter": 6 * N + 4 * 16 * N,             # vertices in, sorted entries out
     }

@@ -301,7 +301,7 @@ struct Work {
   ~Work() {
     drop_graph();
     if (cap_stream) cudaStreamDestroy(cap_stream);
-    for (DevBuf* b : {&ms.bits, &ms.counts, &ms.wpre, &ms.prefix, &ms.chunk, &ms.cubes, &ms.hist, &ms.partial,
+    for (DevBuf* b : {&ms.bits, &ms.counts, &ms.wpre, &ms.tpre, &ms.wlist, &ms.prefix, &ms.chunk, &ms.cubes, &ms.hist, &ms.partial,
                       &ms.bintab, &ms.tabsp, &ds.misc, &ds.plain_part, &result, &ro, &dout, &feats, &rois_dev,
                       &rd_dev, &idx2, &vt, &tri, &mask, &gvtx, &plain})
       b->release();

@@ -205,11 +205,30 @@ __device__ __forceinline__ RowItem row_item(const Roi* rois, int n, long long to
 // One group of L lanes per row item (y, z) in [-1, ny-1] x [-1, nz-1] of each ROI:
 //   counts = (vertices owned by the row, triangles of the cube row, inside voxels, active cubes)
 //   wpre[row][w] = vertices of the row owned by x < 32 w (row-local prefix)
-__global__ void k_count(const uint32_t* __restrict__ bits, const Roi* __restrict__ rois, int n, long long total_rows,
-                        int L, int Wc, int4* __restrict__ counts, int* __restrict__ wpre) {
+//   tpre[row][w] = triangles of the cube row's cubes x < 32 w (row-local prefix)
+// and every word with crossings or active cubes (word 0 also for the x = -1
+// vertex and cube) is appended to wlist (any order: the prefixes fix the ids).
+constexpr int kCountThreads = 256;
+__global__ void __launch_bounds__(kCountThreads) k_count(const uint32_t* __restrict__ bits, const Roi* __restrict__ rois, int n, long long total_rows,
+                        int L, int Wc, int4* __restrict__ counts, int* __restrict__ wpre, int* __restrict__ tpre,
+                        int2* __restrict__ wlist, long long wlist_cap, MeshTotals* __restrict__ tot) {
   const int lane = threadIdx.x & 31, sub = lane % L, gpw = 32 / L;
   const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  // list entries are staged per warp and reserved 33..64 at a time
+  __shared__ int2 s_lb[kCountThreads / 32][64];
+  int2* lb = s_lb[threadIdx.x >> 5];
+  int lbn = 0;
+  auto list_flush = [&]() {
+    __syncwarp();
+    long long lbase = 0;
+    if (lane == 0) lbase = (long long)atomicAdd((unsigned long long*)&tot->nwords, (unsigned long long)lbn);
+    lbase = __shfl_sync(0xffffffffu, lbase, 0);
+    for (int i = lane; i < lbn; i += 32)
+      if (lbase + i < wlist_cap) wlist[lbase + i] = lb[i];
+    __syncwarp();
+    lbn = 0;
+  };
   for (long long base = warp * gpw; base < total_rows; base += nwarps * gpw) {
     const RowItem it = row_item(rois, n, total_rows, base + lane / L);
     const Roi& r = rois[it.roi];
@@ -223,20 +242,36 @@ __global__ void k_count(const uint32_t* __restrict__ bits, const Roi* __restrict
                    e0 = ldw(R11, 0, W) & 1u;
     const int case_m1 = (int)((a0 << 1) | (b0 << 3) | (c0 << 5) | (e0 << 7));
     int carry = (int)a0;
-    int nt = sub == 0 ? MC_CASE_NTRI[case_m1] : 0;
+    int tcarry = MC_CASE_NTRI[case_m1];
+    int nt = sub == 0 ? tcarry : 0;
     int na = (sub == 0 && case_m1) ? 1 : 0;
     int nvox = 0;
     const long long wbase = r.wpre0 + (it.g - r.row0) * (long long)W;
     for (int w = sub; w < Wc; w += L) {
       const WordView v = word_view(R00, R10, R01, R11, w, W);
       const int cnt = __popc(v.ex) + __popc(v.ey) + __popc(v.ez);
-      const int incl = group_incl(cnt, sub, L);
-      if (it.valid && w < W) wpre[wbase + w] = carry + incl - cnt;
+      int tw = 0;
+      for (uint32_t act = v.act; act; act &= act - 1)
+        tw += MC_CASE_NTRI[cube_case(v.a, v.as, v.b, v.bs, v.c, v.cs, v.e, v.es, __ffs(act) - 1)];
+      const int incl = group_incl(cnt, sub, L), tincl = group_incl(tw, sub, L);
+      const bool live = it.valid && w < W;
+      if (live) {
+        wpre[wbase + w] = carry + incl - cnt;
+        tpre[wbase + w] = tcarry + tincl - tw;
+      }
       carry += __shfl_sync(0xffffffffu, incl, L - 1, L);
+      tcarry += __shfl_sync(0xffffffffu, tincl, L - 1, L);
       if (y >= 0 && z >= 0) nvox += __popc(v.a);
       na += __popc(v.act);
-      for (uint32_t act = v.act; act; act &= act - 1)
-        nt += MC_CASE_NTRI[cube_case(v.a, v.as, v.b, v.bs, v.c, v.cs, v.e, v.es, __ffs(act) - 1)];
+      nt += tw;
+      // words with surface go to the emit list
+      const bool surf = live && ((v.ex | v.ey | v.ez | v.act) != 0u || (w == 0 && (a0 || case_m1)));
+      const unsigned int sm = __ballot_sync(0xffffffffu, surf);
+      if (sm) {
+        if (surf) lb[lbn + __popc(sm & ((1u << lane) - 1u))] = make_int2((int)(it.g), w);
+        lbn += __popc(sm);
+        if (lbn > 32) list_flush();
+      }
     }
     for (int off = L / 2; off > 0; off >>= 1) {
       nt += __shfl_xor_sync(0xffffffffu, nt, off, L);
@@ -245,6 +280,7 @@ __global__ void k_count(const uint32_t* __restrict__ bits, const Roi* __restrict
     }
     if (it.valid && sub == 0) counts[it.g] = make_int4(carry, nt, nvox, na);
   }
+  if (lbn) list_flush();
 }
 
 // ---- scan of row counts -------------------------------------------------------------
@@ -748,30 +784,31 @@ __global__ void __launch_bounds__(kCubeThreads) k_cubes(const uint32_t* __restri
   }
 }
 
-// ---- binary masks: vertices and triangles in one pass -------------------------------
-// One warp per row group, as in k_count.  Every lane keeps, for its word, the
-// eight corner rows of its cubes and the crossing masks and row-local vertex
-// prefixes of the four owner rows (y, z), (y+1, z), (y, z+1), (y+1, z+1) in
-// shared memory (one array per quantity, so lanes hit distinct banks).  Each
-// lane writes the vertices of its own word (ids: the first row's base plus a
-// warp prefix).  The active cubes are listed in canonical order and taken 32
-// at a time, one per lane, so a long run of surface in one word is shared by
-// the whole warp; a cube's vertex ids come from the owner-row masks of its
-// word (or the next word) and its triangle ids from a running prefix.
+// ---- binary masks: vertices and triangles of the words with surface ----------------
+// One lane per listed word (any order: the row bases and the row-local word
+// prefixes fix every id).  Each lane loads its word's cube rows and the
+// crossing masks and vertex prefixes of the four owner rows (y, z), (y+1, z),
+// (y, z+1), (y+1, z+1) into shared memory (one array per quantity, so lanes
+// hit distinct banks), plus the bit-0 crossings and prefixes of the next word
+// for cubes at bit 31.  The warp then lists the crossing positions and the
+// active cubes of its 32 words and works through each list 32 entries at a
+// time, every lane taking one entry, so a word with a long run of surface is
+// shared by the whole warp.  A vertex id is its row base + word prefix + rank
+// in the word; a cube's triangle ids are its word's base + the triangles of
+// the word's earlier cubes (a prefix over the cube's run in the list plus a
+// per-word carry between rounds).
 constexpr int kEmitThreads = 128;
 constexpr int kEmitWarps = kEmitThreads / 32;
-constexpr int kListCap = 32 * 32 + 32;  // 32 words x 32 bits + one x = -1 entry per row
-
-struct __align__(16) EmitRow {
-  long long vb[4];      // first vertex id of the four owner rows (0 where the row does not exist)
-  int y, z, roi, tab;
-  int ox0, oy0, oz0, pad;  // -(n - 1) per axis: half-voxel offsets to the padded-box centre
-};
+constexpr int kEmitBlocksPerSM = 6;  // 35 KB of shared memory per block
+constexpr int kListCap = 32 * 33;  // 32 words x (32 bits + the x = -1 entry)
 
 struct __align__(16) EmitShared {
   uint32_t cw[8][32];  // per lane: rows (y,z) (y+1,z) (y,z+1) (y+1,z+1) at x and x + 1: a, as, b, bs, c, cs, e, es
-  int4 own[4][32];     // per owner row, per lane: ex, ey, ez, row-local vertex prefix
-  EmitRow row[32];     // per row of the warp
+  int4 own[4][32];     // per owner row, per lane: ex, ey, ez, row-local vertex prefix of the word
+  int onx[4][32];      // per owner row: next word's prefix << 2 | ey bit 0 << 1 | ex bit 0
+  long long vb[4][32]; // first vertex id of the owner rows
+  long long tb[32];    // first triangle id of the word's cubes
+  int y[32], z[32], wd[32], roi[32], tab[32], tcar[32];
   unsigned short list[kListCap];
 };
 
@@ -783,21 +820,6 @@ __device__ __forceinline__ int warp_incl(int v, int lane) {
   return v;
 }
 
-// Crossing masks and row-local vertex prefix of owner row (yo, zo) at word wo
-// straight from global memory (the next word of a lane that holds the last
-// word of an iteration; only rows wider than 32 words).
-__device__ int4 owner_global(const uint32_t* bits, const Roi& r, const int* wpre, int yo, int zo, int wo) {
-  const uint32_t* R0 = brow(bits, r, yo, zo);
-  const uint32_t b = R0[wo], bn = ldw(R0, wo + 1, r.W);
-  int4 o;
-  o.x = (int)(b ^ shift1(b, bn));
-  o.y = (int)(b ^ brow(bits, r, yo + 1, zo)[wo]);
-  o.z = (int)(b ^ brow(bits, r, yo, zo + 1)[wo]);
-  const long long g = r.row0 + (long long)(zo + 1) * (r.ny + 1) + (yo + 1);
-  o.w = wpre[r.wpre0 + (g - r.row0) * (long long)r.W + wo];
-  return o;
-}
-
 // Local edge e = (corner, axis) in canonical (cz, cy, cx, axis) order, as packed constants.
 constexpr unsigned long long kEdgeCorner = 0ull | (0ull << 3) | (0ull << 6) | (1ull << 9) | (1ull << 12) |
                                            (2ull << 15) | (2ull << 18) | (3ull << 21) | (4ull << 24) |
@@ -805,189 +827,256 @@ constexpr unsigned long long kEdgeCorner = 0ull | (0ull << 3) | (0ull << 6) | (1
 constexpr unsigned int kEdgeAxis = (0u << 0) | (1u << 2) | (2u << 4) | (1u << 6) | (2u << 8) | (0u << 10) |
                                    (2u << 12) | (2u << 14) | (0u << 16) | (1u << 18) | (1u << 20) | (0u << 22);
 
-__global__ void __launch_bounds__(kEmitThreads, 8)
-    k_emit(const uint32_t* __restrict__ bits, const Roi* __restrict__ rois, int n, long long total_rows, int L, int Wc,
-           const int4* __restrict__ counts, const int* __restrict__ wpre, const long long* __restrict__ prefix,
-           const long long* __restrict__ chunk, const BinCase* __restrict__ tab, int16_t* __restrict__ idx2,
-           int32_t* __restrict__ tri, long long vcap, long long tcap, MeshTotals* __restrict__ tot,
-           RoiOut* __restrict__ out, unsigned long long* __restrict__ case_hist) {
+__global__ void __launch_bounds__(kEmitThreads, kEmitBlocksPerSM)
+    k_emit(const uint32_t* __restrict__ bits, const Roi* __restrict__ rois, int n, const int2* __restrict__ wlist,
+           long long wlist_cap, const int* __restrict__ wpre, const int* __restrict__ tpre,
+           const long long* __restrict__ prefix, const long long* __restrict__ chunk, const BinCase* __restrict__ tab,
+           int16_t* __restrict__ idx2, int32_t* __restrict__ tri, long long vcap, long long tcap,
+           MeshTotals* __restrict__ tot, RoiOut* __restrict__ out, unsigned long long* __restrict__ case_hist) {
   __shared__ EmitShared sh[kEmitWarps];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, sub = lane % L, grp = lane / L, gpw = 32 / L;
+  __shared__ unsigned int s_hist[kEmitWarps][256];  // case counts of the warp's current ROI
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   EmitShared& S = sh[wid];
+  unsigned int* hist = s_hist[wid];
+  const long long nlist = min(tot->nwords, wlist_cap);
   unsigned int err = 0;
-  for (long long base = warp * gpw; base < total_rows; base += nwarps * gpw) {
-    const RowItem it = row_item(rois, n, total_rows, base + grp);
-    const int4 rc = it.valid ? counts[it.g] : make_int4(0, 0, 0, 0);
-    if (__all_sync(0xffffffffu, rc.x == 0 && rc.w == 0)) continue;
-    const Roi& r = rois[it.roi];
-    const int y = it.y, z = it.z, W = r.W;
-    // owner row k = cy + 2 cz exists for y + cy <= ny - 1 and z + cz <= nz - 1
-    const bool oky = y + 1 <= r.ny - 1, okz = z + 1 <= r.nz - 1;
-    if (sub == 0) {
-      EmitRow er;
-      er.vb[0] = it.valid ? row_base(prefix, chunk, it.g, 0) : 0;
-      er.vb[1] = it.valid && oky ? row_base(prefix, chunk, it.g + 1, 0) : 0;
-      er.vb[2] = it.valid && okz ? row_base(prefix, chunk, it.g + r.ny + 1, 0) : 0;
-      er.vb[3] = it.valid && oky && okz ? row_base(prefix, chunk, it.g + r.ny + 2, 0) : 0;
-      er.y = y; er.z = z; er.roi = it.roi; er.tab = r.tab;
-      er.ox0 = -(r.nx - 1); er.oy0 = -(r.ny - 1); er.oz0 = -(r.nz - 1); er.pad = 0;
-      S.row[grp] = er;
+  // volume sum and case counts of one ROI (tag) stay in the warp until the ROI changes
+  int tag = -1;
+  long long vacc = 0;
+  for (int c = lane; c < 256; c += 32) hist[c] = 0u;
+  auto flush = [&]() {
+    __syncwarp();
+    if (tag >= 0) {
+      for (int c = lane; c < 256; c += 32) {
+        const unsigned int h = hist[c];
+        if (h) atomicAdd(&case_hist[(long long)tag * 256 + c], (unsigned long long)h);
+        hist[c] = 0u;
+      }
+      long long v = vacc;  // the leader of the tagged run differs between rounds
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+      if (lane == 0 && v) atomicAdd((unsigned long long*)&out[tag].vsum, (unsigned long long)v);
     }
-    long long trun = row_base(prefix, chunk, base, 1);  // triangle ids continue over the warp's rows
-    const long long vfirst = row_base(prefix, chunk, base, 0);
-    const uint32_t* R0 = brow(bits, r, y, z);  // bit row (y + dy, z + dz) = R0 + (dz * BY + dy) * W
-    const long long BW = (long long)r.BY * W;
-    const long long wrow = r.wpre0 + (it.g - r.row0) * (long long)W;  // wpre row (y, z); (y+1) + W; (z+1) + (ny+1) W
-    const long long WZ = (long long)(r.ny + 1) * W;
-    long long vcarry = 0;  // vertices of the warp's earlier words
-    for (int w0 = 0; w0 < Wc; w0 += L) {
-      const int w = w0 + sub;
-      const bool live = it.valid && w < W;
-      uint32_t a = 0, as = 0, b = 0, bs = 0, c = 0, cs = 0, e = 0, es = 0, u = 0, act = 0;
-      if (live) {
+    vacc = 0;
+    __syncwarp();
+  };
+  for (long long k0 = warp * 32; k0 < nlist; k0 += nwarps * 32) {
+    const long long k = k0 + lane;
+    const bool valid = k < nlist;
+    uint32_t u = 0, act = 0;
+    bool m1v = false;
+    int case_m1 = 0;
+    {
+      const int2 en = valid ? wlist[k] : make_int2(0, 0);
+      const long long g = en.x;
+      const int w = en.y;
+      const int roi = valid ? (n == 1 ? 0 : roi_of_row(rois, n, g)) : 0;
+      const Roi& r = rois[roi];
+      const int W = r.W;
+      const int local = (int)(g - r.row0);
+      const int y = local % (r.ny + 1) - 1, z = local / (r.ny + 1) - 1;
+      const bool oky = y + 1 <= r.ny - 1, okz = z + 1 <= r.nz - 1;
+      uint32_t a = 0, as = 0, b = 0, bs = 0, c = 0, cs = 0, e = 0, es = 0;
+      if (valid) {
+        const uint32_t* R0 = brow(bits, r, y, z);  // bit row (y + dy, z + dz) = R0 + (dz * BY + dy) * W
+        const long long BW = (long long)r.BY * W;
+        const long long wrow = r.wpre0 + (g - r.row0) * (long long)W;  // word prefixes of row (y, z)
+        const long long WZ = (long long)(r.ny + 1) * W;
+        const bool nx1 = w + 1 < W;
         a = R0[w]; b = R0[W + w]; c = R0[BW + w]; e = R0[BW + W + w];
-        as = shift1(a, ldw(R0, w + 1, W)); bs = shift1(b, ldw(R0 + W, w + 1, W));
-        cs = shift1(c, ldw(R0 + BW, w + 1, W)); es = shift1(e, ldw(R0 + BW + W, w + 1, W));
-        const uint32_t f = R0[2 * W + w], g = R0[2 * BW + w], h = R0[BW + 2 * W + w], i2 = R0[2 * BW + W + w];
+        const uint32_t an = nx1 ? R0[w + 1] : 0u, bn = nx1 ? R0[W + w + 1] : 0u;
+        const uint32_t cn = nx1 ? R0[BW + w + 1] : 0u, en2 = nx1 ? R0[BW + W + w + 1] : 0u;
+        as = shift1(a, an); bs = shift1(b, bn); cs = shift1(c, cn); es = shift1(e, en2);
+        const uint32_t f = R0[2 * W + w], gg = R0[2 * BW + w], h = R0[BW + 2 * W + w], i2 = R0[2 * BW + W + w];
         S.own[0][lane] = make_int4((int)(a ^ as), (int)(a ^ b), (int)(a ^ c), wpre[wrow + w]);
         S.own[1][lane] = make_int4((int)(b ^ bs), (int)(b ^ f), (int)(b ^ e), oky ? wpre[wrow + W + w] : 0);
-        S.own[2][lane] = make_int4((int)(c ^ cs), (int)(c ^ e), (int)(c ^ g), okz ? wpre[wrow + WZ + w] : 0);
+        S.own[2][lane] = make_int4((int)(c ^ cs), (int)(c ^ e), (int)(c ^ gg), okz ? wpre[wrow + WZ + w] : 0);
         S.own[3][lane] =
             make_int4((int)(e ^ es), (int)(e ^ h), (int)(e ^ i2), oky && okz ? wpre[wrow + WZ + W + w] : 0);
+        // next word, bit 0: crossings along x and y of the owner rows, and their prefixes
+        int o0 = 0, o1 = 0, o2 = 0, o3 = 0;
+        if (nx1) {
+          const uint32_t fn = R0[2 * W + w + 1], hn = R0[BW + 2 * W + w + 1];
+          o0 = (wpre[wrow + w + 1] << 2) | (int)((((an ^ bn) & 1u) << 1) | ((an ^ (an >> 1)) & 1u));
+          o1 = ((oky ? wpre[wrow + W + w + 1] : 0) << 2) | (int)((((bn ^ fn) & 1u) << 1) | ((bn ^ (bn >> 1)) & 1u));
+          o2 = ((okz ? wpre[wrow + WZ + w + 1] : 0) << 2) | (int)((((cn ^ en2) & 1u) << 1) | ((cn ^ (cn >> 1)) & 1u));
+          o3 = ((oky && okz ? wpre[wrow + WZ + W + w + 1] : 0) << 2) |
+               (int)((((en2 ^ hn) & 1u) << 1) | ((en2 ^ (en2 >> 1)) & 1u));
+        }
+        S.onx[0][lane] = o0; S.onx[1][lane] = o1; S.onx[2][lane] = o2; S.onx[3][lane] = o3;
+        S.vb[0][lane] = row_base(prefix, chunk, g, 0);
+        S.vb[1][lane] = oky ? row_base(prefix, chunk, g + 1, 0) : 0;
+        S.vb[2][lane] = okz ? row_base(prefix, chunk, g + r.ny + 1, 0) : 0;
+        S.vb[3][lane] = oky && okz ? row_base(prefix, chunk, g + r.ny + 2, 0) : 0;
+        S.tb[lane] = row_base(prefix, chunk, g, 1) + (w == 0 ? 0 : tpre[wrow + w]);
         u = (a ^ as) | (a ^ b) | (a ^ c);
         act = (a | as | b | bs | c | cs | e | es) & ~(a & as & b & bs & c & cs & e & es);
+        m1v = w == 0 && (a & 1u);
+        case_m1 = w == 0 ? (int)(((a & 1u) << 1) | ((b & 1u) << 3) | ((c & 1u) << 5) | ((e & 1u) << 7)) : 0;
       }
       S.cw[0][lane] = a; S.cw[1][lane] = as; S.cw[2][lane] = b; S.cw[3][lane] = bs;
       S.cw[4][lane] = c; S.cw[5][lane] = cs; S.cw[6][lane] = e; S.cw[7][lane] = es;
-      // the x = -1 vertex (x-edge into voxel 0) and cube (corners at voxel 0) open the row
-      const bool first = w0 == 0 && sub == 0 && live;
-      const bool m1v = first && (a & 1u);
-      const int case_m1 = first ? (int)(((a & 1u) << 1) | ((b & 1u) << 3) | ((c & 1u) << 5) | ((e & 1u) << 7)) : 0;
+      S.y[lane] = y; S.z[lane] = z; S.wd[lane] = w; S.roi[lane] = roi; S.tab[lane] = r.tab; S.tcar[lane] = 0;
+    }
 
-      // ---- vertices of owner row (y, z): each lane writes its own word's ----------
-      {
-        const uint32_t ex = a ^ as, ey = a ^ b, ez = a ^ c;
-        const int nv = __popc(ex) + __popc(ey) + __popc(ez) + (m1v ? 1 : 0);
-        const int vin = warp_incl(nv, lane);
-        long long id = vfirst + vcarry + vin - nv;
-        vcarry += __shfl_sync(0xffffffffu, vin, 31);
-        const int16_t qy = (int16_t)(2 * y), qz = (int16_t)(2 * z);
-        if (m1v) {
+    {
+      const int t0 = __shfl_sync(0xffffffffu, S.roi[0], 0);  // lane 0's entry is always valid
+      if (t0 != tag) {
+        flush();
+        tag = t0;
+      }
+    }
+
+    // ---- vertices: the x = -1 vertex opens word 0, then the positions by x --------
+    {
+      const int pc = __popc(u) + (m1v ? 1 : 0);
+      const int pin = warp_incl(pc, lane);
+      const int ptot = __shfl_sync(0xffffffffu, pin, 31);
+      int o = pin - pc;
+      if (m1v) S.list[o++] = (unsigned short)((lane << 6) | 32);
+      for (uint32_t m = u; m; m &= m - 1) S.list[o++] = (unsigned short)((lane << 6) | (__ffs(m) - 1));
+      __syncwarp();
+      for (int j = lane; j < ptot; j += 32) {
+        const unsigned short en = S.list[j];
+        const int src = en >> 6, bit = en & 63;
+        const int16_t qy = (int16_t)(2 * S.y[src]), qz = (int16_t)(2 * S.z[src]);
+        long long id = S.vb[0][src];
+        if (bit == 32) {
           if (id < vcap) {
             idx2[3 * id] = (int16_t)(-1); idx2[3 * id + 1] = qy; idx2[3 * id + 2] = qz;
           } else {
             err |= DEV_ERR_VCAP;
           }
+          continue;
+        }
+        const int4 o0 = S.own[0][src];
+        const uint32_t ex = (uint32_t)o0.x, ey = (uint32_t)o0.y, ez = (uint32_t)o0.z, low = (1u << bit) - 1u;
+        id += o0.w + __popc(ex & low) + __popc(ey & low) + __popc(ez & low);
+        const int16_t qx = (int16_t)(2 * (32 * S.wd[src] + bit));
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+          if (!((((ax == 0 ? ex : (ax == 1 ? ey : ez)) >> bit) & 1u))) continue;
+          if (id < vcap) {
+            idx2[3 * id] = (int16_t)(qx + (ax == 0));
+            idx2[3 * id + 1] = (int16_t)(qy + (ax == 1));
+            idx2[3 * id + 2] = (int16_t)(qz + (ax == 2));
+          } else {
+            err |= DEV_ERR_VCAP;
+          }
           ++id;
         }
-        for (uint32_t m = u; m; m &= m - 1) {
-          const int bit = __ffs(m) - 1, x = 32 * w + bit;
-          const int16_t qx = (int16_t)(2 * x);
-#pragma unroll
-          for (int ax = 0; ax < 3; ++ax) {
-            if (!((((ax == 0 ? ex : (ax == 1 ? ey : ez)) >> bit) & 1u))) continue;
-            if (id < vcap) {
-              idx2[3 * id] = (int16_t)(qx + (ax == 0));
-              idx2[3 * id + 1] = (int16_t)(qy + (ax == 1));
-              idx2[3 * id + 2] = (int16_t)(qz + (ax == 2));
-            } else {
-              err |= DEV_ERR_VCAP;
-            }
-            ++id;
-          }
-        }
-      }
-
-      // ---- active cubes: triangles, volume and case counts ------------------------
-      const int cc = __popc(act) + (case_m1 ? 1 : 0);
-      const int cin = warp_incl(cc, lane);
-      const int ctot = __shfl_sync(0xffffffffu, cin, 31);
-      if (ctot == 0) continue;  // warp-uniform
-      {
-        int o = cin - cc;
-        if (case_m1) S.list[o++] = (unsigned short)((lane << 6) | 32);
-        for (uint32_t m = act; m; m &= m - 1) S.list[o++] = (unsigned short)((lane << 6) | (__ffs(m) - 1));
       }
       __syncwarp();
-      for (int j0 = 0; j0 < ctot; j0 += 32) {
-        const int j = j0 + lane;
-        int src = 0, bit = 0, cs = 0, ntri = 0, roi = -1;
-        const BinCase* bc = nullptr;
-        if (j < ctot) {
-          const unsigned short en = S.list[j];
-          src = en >> 6;
-          bit = en & 63;
-          const int bq = bit == 32 ? 0 : bit;
-          const uint32_t k0 = S.cw[0][src] >> bq, k1 = S.cw[1][src] >> bq, k2 = S.cw[2][src] >> bq,
-                         k3 = S.cw[3][src] >> bq, k4 = S.cw[4][src] >> bq, k5 = S.cw[5][src] >> bq,
-                         k6 = S.cw[6][src] >> bq, k7 = S.cw[7][src] >> bq;
-          cs = bit == 32 ? (int)(((k0 & 1u) << 1) | ((k2 & 1u) << 3) | ((k4 & 1u) << 5) | ((k6 & 1u) << 7))
-                         : (int)((k0 & 1u) | ((k1 & 1u) << 1) | ((k2 & 1u) << 2) | ((k3 & 1u) << 3) |
-                                 ((k4 & 1u) << 4) | ((k5 & 1u) << 5) | ((k6 & 1u) << 6) | ((k7 & 1u) << 7));
-          const EmitRow& er = S.row[src / L];
-          roi = er.roi;
-          bc = &tab[er.tab * 256 + cs];
-          ntri = bc->ntri;
-        }
-        const int tin = warp_incl(ntri, lane);
-        const int ttot = __shfl_sync(0xffffffffu, tin, 31);
-        long long vsum = 0;
-        if (j < ctot) {
-          const EmitRow& er = S.row[src / L];
-          const int ws = w0 + src % L;
-          const int x = bit == 32 ? -1 : 32 * ws + bit;
-          const unsigned long long t4 = bc->tri4;
-          long long tid = trun + tin - ntri;
-          for (int t = 0; t < ntri; ++t, ++tid) {
-            int vid[3];
+    }
+
+    // ---- active cubes: triangles, volume and case counts ---------------------------
+    const int cc = __popc(act) + (case_m1 ? 1 : 0);
+    const int cin = warp_incl(cc, lane);
+    const int ctot = __shfl_sync(0xffffffffu, cin, 31);
+    if (ctot == 0) continue;  // warp-uniform
+    {
+      int o = cin - cc;
+      if (case_m1) S.list[o++] = (unsigned short)((lane << 6) | 32);
+      for (uint32_t m = act; m; m &= m - 1) S.list[o++] = (unsigned short)((lane << 6) | (__ffs(m) - 1));
+    }
+    __syncwarp();
+    for (int j0 = 0; j0 < ctot; j0 += 32) {
+      const int j = j0 + lane;
+      const bool on = j < ctot;
+      int src = -1, bit = 0, cs = 0, ntri = 0, roi = -1;
+      const BinCase* bc = nullptr;
+      if (on) {
+        const unsigned short en = S.list[j];
+        src = en >> 6;
+        bit = en & 63;
+        const int bq = bit == 32 ? 0 : bit;
+        const uint32_t k0w = S.cw[0][src] >> bq, k1 = S.cw[1][src] >> bq, k2 = S.cw[2][src] >> bq,
+                       k3 = S.cw[3][src] >> bq, k4 = S.cw[4][src] >> bq, k5 = S.cw[5][src] >> bq,
+                       k6 = S.cw[6][src] >> bq, k7 = S.cw[7][src] >> bq;
+        cs = bit == 32 ? (int)(((k0w & 1u) << 1) | ((k2 & 1u) << 3) | ((k4 & 1u) << 5) | ((k6 & 1u) << 7))
+                       : (int)((k0w & 1u) | ((k1 & 1u) << 1) | ((k2 & 1u) << 2) | ((k3 & 1u) << 3) |
+                               ((k4 & 1u) << 4) | ((k5 & 1u) << 5) | ((k6 & 1u) << 6) | ((k7 & 1u) << 7));
+        roi = S.roi[src];
+        bc = &tab[S.tab[src] * 256 + cs];
+        ntri = bc->ntri;
+      }
+      // triangle ids: the word's base + its triangles already written + the
+      // triangles of the word's earlier cubes in this round (runs of equal src)
+      const int tin = warp_incl(ntri, lane);
+      const int tex = tin - ntri;
+      const unsigned int peers = __match_any_sync(0xffffffffu, src);
+      const int seg0 = __shfl_sync(0xffffffffu, tex, __ffs(peers) - 1);
+      const int seglast = 31 - __clz(peers);
+      long long vsum = 0;
+      if (on) {
+        const int w = S.wd[src];
+        const int x = bit == 32 ? -1 : 32 * w + bit;
+        const unsigned long long t4 = bc->tri4;
+        long long tid = S.tb[src] + S.tcar[src] + (tex - seg0);
+        for (int t = 0; t < ntri; ++t, ++tid) {
+          int vid[3];
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-              const int ed = (int)((t4 >> (12 * t + 4 * k)) & 15ull);
-              const int corner = (int)((kEdgeCorner >> (3 * ed)) & 7ull), ax = (int)((kEdgeAxis >> (2 * ed)) & 3u);
-              const int orow = ((corner >> 1) & 1) + 2 * (corner >> 2);
-              const int xo = x + (corner & 1);
-              int rank = 0;  // owner x = -1: the row's first vertex
-              if (xo >= 0) {
-                const int wo = xo >> 5, bo = xo & 31;
-                int4 ow;
-                if (wo == ws) ow = S.own[orow][src];
-                else if (src % L + 1 < L) ow = S.own[orow][src + 1];
-                else ow = owner_global(bits, rois[roi], wpre, er.y + (orow & 1), er.z + (orow >> 1), wo);
+          for (int kk = 0; kk < 3; ++kk) {
+            const int ed = (int)((t4 >> (12 * t + 4 * kk)) & 15ull);
+            const int corner = (int)((kEdgeCorner >> (3 * ed)) & 7ull), ax = (int)((kEdgeAxis >> (2 * ed)) & 3u);
+            const int orow = ((corner >> 1) & 1) + 2 * (corner >> 2);
+            const int xo = x + (corner & 1);
+            int rank = 0;  // owner x = -1: the row's first vertex
+            if (xo >= 0) {
+              if ((xo >> 5) == w) {
+                const int4 ow = S.own[orow][src];
+                const int bo = xo & 31;
                 const uint32_t low = (1u << bo) - 1u;
                 rank = ow.w + __popc((uint32_t)ow.x & low) + __popc((uint32_t)ow.y & low) +
                        __popc((uint32_t)ow.z & low);
                 if (ax >= 1) rank += ((uint32_t)ow.x >> bo) & 1u;
                 if (ax >= 2) rank += ((uint32_t)ow.y >> bo) & 1u;
+              } else {  // bit 0 of the next word
+                const int on2 = S.onx[orow][src];
+                rank = on2 >> 2;
+                if (ax >= 1) rank += on2 & 1;
+                if (ax >= 2) rank += (on2 >> 1) & 1;
               }
-              vid[k] = (int)(er.vb[orow] + rank);
             }
-            if (tid < tcap) {
-              tri[3 * tid] = vid[0];
-              tri[3 * tid + 1] = vid[1];
-              tri[3 * tid + 2] = vid[2];
-            } else {
-              err |= DEV_ERR_TCAP;
-            }
+            vid[kk] = (int)(S.vb[orow][src] + rank);
           }
-          // exact volume in half-voxel units relative to the padded-box centre
-          const long long ox = 2LL * x + er.ox0, oy = 2LL * er.y + er.oy0, oz = 2LL * er.z + er.oz0;
-          vsum = ox * bc->nsum[0] + oy * bc->nsum[1] + oz * bc->nsum[2] + bc->tsum;
+          if (tid < tcap) {
+            tri[3 * tid] = vid[0];
+            tri[3 * tid + 1] = vid[1];
+            tri[3 * tid + 2] = vid[2];
+          } else {
+            err |= DEV_ERR_TCAP;
+          }
         }
-        // |vsum| of one cube < 5e6, so a warp's sum fits in 32 bits
-        const unsigned int same_roi = __match_any_sync(0xffffffffu, roi);
-        const int vs = __reduce_add_sync(same_roi, (int)vsum);
-        if (roi >= 0 && lane == __ffs(same_roi) - 1 && vs)
-          atomicAdd((unsigned long long*)&out[roi].vsum, (unsigned long long)(long long)vs);
-        const long long key = roi >= 0 ? (long long)roi * 256 + cs : -1;
-        const unsigned int same_case = __match_any_sync(0xffffffffu, key);
-        if (roi >= 0 && lane == __ffs(same_case) - 1) atomicAdd(&case_hist[key], (unsigned long long)__popc(same_case));
-        trun += ttot;
+        // exact volume in half-voxel units relative to the padded-box centre
+        const Roi& r = rois[roi];
+        const long long ox = 2LL * x - (r.nx - 1), oy = 2LL * S.y[src] - (r.ny - 1),
+                        oz = 2LL * S.z[src] - (r.nz - 1);
+        vsum = ox * bc->nsum[0] + oy * bc->nsum[1] + oz * bc->nsum[2] + bc->tsum;
       }
+      __syncwarp();  // every lane has read the carries
+      if (on && lane == seglast) S.tcar[src] += tin - seg0;
       __syncwarp();
+      // |vsum| of one cube < 5e6, so a warp's sum fits in 32 bits; cubes of
+      // the tagged ROI are counted in the warp, others (a ROI boundary inside
+      // the warp's words) go straight to global memory
+      const unsigned int same_roi = __match_any_sync(0xffffffffu, roi);
+      const int vs = __reduce_add_sync(same_roi, (int)vsum);
+      if (roi >= 0 && lane == __ffs(same_roi) - 1 && vs) {
+        if (roi == tag) vacc += vs;
+        else atomicAdd((unsigned long long*)&out[roi].vsum, (unsigned long long)(long long)vs);
+      }
+      const long long key = roi >= 0 ? (long long)roi * 256 + cs : -1;
+      const unsigned int same_case = __match_any_sync(0xffffffffu, key);
+      if (roi >= 0 && lane == __ffs(same_case) - 1) {
+        if (roi == tag) hist[cs] += (unsigned int)__popc(same_case);
+        else atomicAdd(&case_hist[key], (unsigned long long)__popc(same_case));
+      }
     }
+    __syncwarp();
   }
+  flush();
   if (err) atomicOr(&tot->status, err);
 }
 
@@ -1041,6 +1130,8 @@ rad_status mesh_count(const MeshBatch& b, MeshScratch& s, MeshTotals* tot, RoiOu
   RAD_TRY(s.bits.reserve(sizeof(uint32_t) * b.words));
   RAD_TRY(s.counts.reserve(sizeof(int4) * b.rows));
   RAD_TRY(s.wpre.reserve(sizeof(int) * b.wpre));
+  RAD_TRY(s.tpre.reserve(sizeof(int) * b.wpre));
+  RAD_TRY(s.wlist.reserve(sizeof(int2) * b.wpre));
   RAD_TRY(s.prefix.reserve(sizeof(long long) * 4 * b.rows));
   RAD_TRY(s.chunk.reserve(sizeof(long long) * 4 * nchunks));
   RAD_TRY(s.hist.reserve(sizeof(unsigned long long) * 256 * b.n));
@@ -1056,8 +1147,8 @@ rad_status mesh_count(const MeshBatch& b, MeshScratch& s, MeshTotals* tot, RoiOu
     RAD_LAUNCH("mc_pack_u8", k_pack<false>, pack_blocks, 256, 0, st, b.rois, b.n, b.words, s.bits.as<uint32_t>());
   const long long warps_needed = (b.rows + (32 / b.L) - 1) / (32 / b.L);
   const int rblocks = (int)std::max<long long>(1, std::min<long long>((warps_needed + 7) / 8, (long long)sms * 8));
-  RAD_LAUNCH("mc_count", k_count, rblocks, 256, 0, st, s.bits.as<uint32_t>(), b.rois, b.n, b.rows, b.L, b.Wc,
-             s.counts.as<int4>(), s.wpre.as<int>());
+  RAD_LAUNCH("mc_count", k_count, rblocks, kCountThreads, 0, st, s.bits.as<uint32_t>(), b.rois, b.n, b.rows, b.L, b.Wc,
+             s.counts.as<int4>(), s.wpre.as<int>(), s.tpre.as<int>(), s.wlist.as<int2>(), b.wpre, tot);
   RAD_LAUNCH("mc_scan_chunks", k_scan_chunks, (int)nchunks, 256, 0, st, s.counts.as<int4>(), b.rows,
              s.prefix.as<long long>(), s.chunk.as<long long>());
   RAD_LAUNCH("mc_scan_top", k_scan_top, 1, 1024, 0, st, s.chunk.as<long long>(), (int)nchunks, tot);
@@ -1084,12 +1175,11 @@ rad_status mesh_emit(const MeshBatch& b, MeshScratch& s, MeshTotals* tot, RoiOut
                (const BinCase*)nullptr, tri, ccap, tcap, tot, out, s.hist.as<unsigned long long>(),
                s.partial.as<double>());
   } else {
-    const long long ewarps = (b.rows + (32 / b.L) - 1) / (32 / b.L);
-    const int eblocks =
-        (int)std::max<long long>(1, std::min<long long>((ewarps + kEmitWarps - 1) / kEmitWarps, (long long)sms * 16));
-    RAD_LAUNCH("mc_emit", k_emit, eblocks, kEmitThreads, 0, st, s.bits.as<uint32_t>(), b.rois, b.n, b.rows, b.L, b.Wc,
-               s.counts.as<int4>(), s.wpre.as<int>(), s.prefix.as<long long>(), s.chunk.as<long long>(),
-               s.bintab.as<BinCase>(), idx2, tri, vcap, tcap, tot, out, s.hist.as<unsigned long long>());
+    const int eblocks = sms * kEmitBlocksPerSM;  // persistent: the list length is known on the device only
+    RAD_LAUNCH("mc_emit", k_emit, eblocks, kEmitThreads, 0, st, s.bits.as<uint32_t>(), b.rois, b.n,
+               s.wlist.as<int2>(), b.wpre, s.wpre.as<int>(), s.tpre.as<int>(), s.prefix.as<long long>(),
+               s.chunk.as<long long>(), s.bintab.as<BinCase>(), idx2, tri, vcap, tcap, tot, out,
+               s.hist.as<unsigned long long>());
     RAD_LAUNCH("mc_mask_totals", k_mask_totals, std::min(b.n, sms * 8), 256, 0, st, b.rois, b.n,
                s.bintab.as<BinCase>(), s.hist.as<unsigned long long>(), out);
   }

@@ -91,6 +91,7 @@ struct RoiOut {
 
 struct MeshTotals {  // batch-wide counts and status of one marching-cubes pass
   long long nv, nt, nvox, na;
+  long long nwords;        // words with surface (binary masks: the emit kernel's work list)
   unsigned int status;
   unsigned int done_ctas;  // last-CTA ticket of the soft cube kernel
 };
@@ -109,6 +110,8 @@ struct MeshScratch {
   DevBuf bits;    // packed inside bits of every ROI
   DevBuf counts;  // int4 per row: vertices, triangles, inside voxels, active cubes
   DevBuf wpre;    // int per (row, word): row-local vertex prefix
+  DevBuf tpre;    // int per (row, word): row-local triangle prefix
+  DevBuf wlist;   // int2 per word with surface: (global row, word)
   DevBuf prefix;  // int64 x 4 per row: chunk-local exclusive prefixes
   DevBuf chunk;   // int64 x 4 per scan chunk: chunk offsets
   DevBuf cubes;   // int4 per active cube: x, global row, case, first triangle id

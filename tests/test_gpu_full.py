@@ -50,6 +50,24 @@ def test_blob_512_cubed():
     assert got["n_vertices"] > 1000000
 
 
+def test_batch_8_blobs_512_cubed():
+    """The large batched configuration: 8 masks of 512^3 (about 1e6 vertices
+    each) in one batch, replayed as a graph; every mask against the oracle
+    (its full mesh counts, volume and area; diameters from exact shortlists)."""
+    masks = synth.blobs_512(1, count=8)
+    devs = [torch.from_numpy(m).cuda() for m, _ in masks]
+    b = rad.Batch(devs, [sp for _, sp in masks])
+    first = b.run()
+    again = b.run()  # graph replay
+    for (mask, sp), got, got2 in zip(masks, first, again):
+        ref, _ = oracle.features(mask, sp, "hull")
+        assert_features(got, ref)
+        assert got2 == got
+        assert got["n_vertices"] > 500000
+    del b, devs
+    torch.cuda.empty_cache()
+
+
 def test_soft_160():
     prob, sp = synth.soft_160(0)
     dev = torch.from_numpy(prob).cuda()
