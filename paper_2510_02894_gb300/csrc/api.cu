@@ -180,6 +180,30 @@ void graph_release(CaptureSink& k) {
   k.stats.clear();
 }
 
+int resident_ctas(const void* kernel, int threads, size_t smem) {
+  struct Key {
+    const void* k;
+    int threads, dev;
+    size_t smem;
+    int n;
+  };
+  static std::mutex mu;
+  static std::vector<Key> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> g(mu);
+  for (const Key& e : cache)
+    if (e.k == kernel && e.threads == threads && e.dev == dev && e.smem == smem) return e.n;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    n = 1;
+  }
+  n = std::max(n, 1);
+  cache.push_back(Key{kernel, threads, dev, smem, n});
+  return n;
+}
+
 int num_sms() {
   static int cached[64] = {0};
   int dev = 0;
@@ -237,6 +261,7 @@ struct ResultBlock {  // device; copied to pinned host memory after every pass
 // Features of every ROI from the mesh and diameter results (one thread per ROI).
 __global__ void k_assemble(const Roi* __restrict__ rois, const RoiOut* __restrict__ ro,
                            const DiamOut* __restrict__ dout, int n, int have_diam, rad_features_t* __restrict__ f) {
+  pdl_enter();
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const Roi& r = rois[i];
     const RoiOut& o = ro[i];

@@ -174,6 +174,7 @@ __device__ __forceinline__ int roi_of_vertex(const RoiOut* ro, int n, long long 
 __global__ void k_hist(const int16_t* __restrict__ idx2, const long long* __restrict__ nv_dev,
                        const RoiDiam* __restrict__ rd, const RoiOut* __restrict__ ro, Params p,
                        int* __restrict__ hist) {
+  pdl_enter();
   const long long n = min(*nv_dev, p.nv_cap);
   const int lane = threadIdx.x & 31;
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -204,6 +205,7 @@ __global__ void k_scatter(const int16_t* __restrict__ idx2, const double* __rest
                           const RoiOut* __restrict__ ro, Params p, const long long* __restrict__ offs,
                           const long long* __restrict__ parts, int* __restrict__ cursor,
                           float4* __restrict__ sorted) {
+  pdl_enter();
   const long long n = min(*nv_dev, p.nv_cap);
   const int lane = threadIdx.x & 31;
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -249,6 +251,7 @@ __global__ void k_scatter(const int16_t* __restrict__ idx2, const double* __rest
 constexpr int kScanBlock = 1024;
 __global__ void k_xscan_part(const int* __restrict__ in, long long n, long long* __restrict__ out,
                              long long* __restrict__ part) {
+  pdl_enter();
   __shared__ long long ws[32];
   const long long i = blockIdx.x * (long long)kScanBlock + threadIdx.x;
   long long v = i < n ? in[i] : 0;
@@ -270,6 +273,7 @@ __global__ void k_xscan_part(const int* __restrict__ in, long long n, long long*
 }
 
 __global__ void k_xscan_top(long long* __restrict__ part, int nparts) {
+  pdl_enter();
   __shared__ long long ws[32];
   long long carry = 0;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -325,6 +329,7 @@ __device__ __forceinline__ long long chunks_upto(long long m) {
 __global__ void k_setup(const RoiDiam* __restrict__ rd, Params p, const long long* __restrict__ offs,
                         const long long* __restrict__ parts, Problem* __restrict__ probs, Tile* __restrict__ tiles,
                         int* __restrict__ chunk0, ProblemState* __restrict__ ps, Counters* __restrict__ cnt) {
+  pdl_enter();
   const int lane = threadIdx.x & 31;
   const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -428,6 +433,7 @@ __global__ void k_setup(const RoiDiam* __restrict__ rd, Params p, const long lon
 // T(F) of every problem from its seeded F (FP64, one thread per problem).
 __global__ void k_thresh(const RoiDiam* __restrict__ rd, const Problem* __restrict__ probs, Params p,
                          const Counters* __restrict__ cnt, ProblemState* __restrict__ ps) {
+  pdl_enter();
   const int np = (int)min((long long)cnt->n_problems, p.max_problems);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x)
     ps[i].T = __float_as_uint(threshold(__uint_as_float(ps[i].F), rd[probs[i].roi]));
@@ -436,6 +442,7 @@ __global__ void k_thresh(const RoiDiam* __restrict__ rd, const Problem* __restri
 // One warp per tile: bounding box of its FP32 positions and its first vertex.
 __global__ void k_tile_box(const float4* __restrict__ sorted, const Tile* __restrict__ tiles, Params p,
                            const Counters* __restrict__ cnt, float4* __restrict__ box, float4* __restrict__ rep) {
+  pdl_enter();
   const int nt = (int)min((long long)(cnt->alloc & 0xffffffffull), p.max_tiles);
   const int lane = threadIdx.x & 31;
   const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
@@ -535,6 +542,7 @@ __device__ __forceinline__ void seed_flush(float m, int problem, ProblemState* p
 __global__ void k_seed(const float4* __restrict__ sorted, const float4* __restrict__ rep, Params p,
                        const Tile* __restrict__ tiles, const int* __restrict__ chunk0, const Counters* __restrict__ cnt,
                        ProblemState* __restrict__ ps) {
+  pdl_enter();
   const unsigned long long alloc = cnt->alloc;
   const int nt = (int)min((long long)(alloc & 0xffffffffull), p.max_tiles);
   const long long K = min((long long)(alloc >> 32), (long long)INT_MAX);
@@ -548,8 +556,10 @@ __global__ void k_seed(const float4* __restrict__ sorted, const float4* __restri
   float m = 0.0f;
   for (; w.k < w.kend; ++w.k) {
     if (w.k >= w.next0 && w.a + 1 < nt) {  // warp-uniform
-      seed_flush(m, ta.problem, ps);
-      m = 0.0f;
+      if (nx.t.problem != ta.problem) {  // one flush per problem
+        seed_flush(m, ta.problem, ps);
+        m = 0.0f;
+      }
       ++w.a;
       ta = nx.t;
       ra = nx.v0;
@@ -574,6 +584,7 @@ __global__ void k_seed(const float4* __restrict__ sorted, const float4* __restri
 __global__ void k_cull(const Tile* __restrict__ tiles, const float4* __restrict__ box, Params p,
                        const int* __restrict__ chunk0, Counters* __restrict__ cnt, const ProblemState* __restrict__ ps,
                        WorkItem* __restrict__ work) {
+  pdl_enter();
   const unsigned long long alloc = cnt->alloc;
   const int nt = (int)min((long long)(alloc & 0xffffffffull), p.max_tiles);
   const long long K = min((long long)(alloc >> 32), (long long)INT_MAX);
@@ -677,6 +688,7 @@ template <int TS, int NT>
 __global__ void __launch_bounds__(NT) k_pairs(const float4* __restrict__ sorted, const WorkItem* __restrict__ work,
                                               Params p, const RoiDiam* __restrict__ rd, Counters* __restrict__ cnt,
                                               ProblemState* __restrict__ ps, float* __restrict__ slicemax) {
+  pdl_enter();
   constexpr int RA = TS / 32;  // A entries per lane, and B slices per tile pair
   constexpr int NWARP = NT / 32;
   __shared__ __align__(16) float4 sA[NWARP][2][TS];
@@ -758,6 +770,7 @@ __global__ void __launch_bounds__(NT) k_pairs(const float4* __restrict__ sorted,
 template <int TS>
 __global__ void k_cand_list(const WorkItem* __restrict__ work, const float* __restrict__ slicemax, Params p,
                             Counters* __restrict__ cnt, const ProblemState* __restrict__ ps, int* __restrict__ hits) {
+  pdl_enter();
   constexpr int RA = TS / 32;
   const long long nslices = min(cnt->n_work, p.work_cap) * RA;
   const int lane = threadIdx.x & 31;
@@ -785,6 +798,7 @@ template <int TS>
 __global__ void k_cand(const float4* __restrict__ sorted, const WorkItem* __restrict__ work,
                        const int* __restrict__ hits, Params p, Counters* __restrict__ cnt,
                        const ProblemState* __restrict__ ps, Cand* __restrict__ cand) {
+  pdl_enter();
   constexpr int RA = TS / 32;
   const long long nh = cnt->n_hits;
   const int lane = threadIdx.x & 31;
@@ -840,6 +854,7 @@ __global__ void k_confirm(const float4* __restrict__ sorted, const int16_t* __re
                           const double* __restrict__ vt, Params p, const RoiDiam* __restrict__ rd,
                           const Counters* __restrict__ cnt, const Cand* __restrict__ cand,
                           DiamOut* __restrict__ out) {
+  pdl_enter();
   const long long nc = min(cnt->n_cand, p.cand_cap);
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nc; c += (long long)gridDim.x * blockDim.x) {
     const Cand k = cand[c];
@@ -859,6 +874,7 @@ __global__ void k_tiebreak(const float4* __restrict__ sorted, const int16_t* __r
                            const double* __restrict__ vt, Params p, const RoiDiam* __restrict__ rd,
                            const RoiOut* __restrict__ ro, const Counters* __restrict__ cnt,
                            const Cand* __restrict__ cand, DiamOut* __restrict__ out, DiamStats* __restrict__ stats) {
+  pdl_enter();
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     stats->problems = cnt->n_problems;
     stats->tiles = (long long)(cnt->alloc & 0xffffffffull);
@@ -889,6 +905,7 @@ __global__ void k_tiebreak(const float4* __restrict__ sorted, const int16_t* __r
 }
 
 __global__ void k_diam_init(DiamOut* __restrict__ out, int n) {
+  pdl_enter();
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
     for (int q = 0; q < 4; ++q) {
       out[i].d2[q] = 0ull;
@@ -922,9 +939,12 @@ rad_status launch_pairs(const float4* sorted, const WorkItem* work, const Params
   auto kp = k_pairs<TS, NT>;
   auto kl = k_cand_list<TS>;
   auto kc = k_cand<TS>;
-  RAD_LAUNCH("diam_pairs_fp32", kp, ctas, NT, 0, st, sorted, work, p, rd, cnt, ps, slicemax);
-  RAD_LAUNCH("diam_cand_list", kl, num_sms() * 4, 256, 0, st, work, slicemax, p, cnt, ps, hits);
-  RAD_LAUNCH("diam_pairs_cand", kc, num_sms() * 4, 256, 0, st, sorted, work, hits, p, cnt, ps, cand);
+  // at most one full wave: the items are dealt out to the grid's warps
+  const int pgrid = std::min(ctas, wave_grid(kp, NT, 1LL << 30));
+  RAD_LAUNCH("diam_pairs_fp32", kp, pgrid, NT, 0, st, sorted, work, p, rd, cnt, ps, slicemax);
+  RAD_LAUNCH("diam_cand_list", kl, wave_grid(kl, 256, num_sms() * 4), 256, 0, st, work, slicemax, p, cnt, ps, hits);
+  RAD_LAUNCH("diam_pairs_cand", kc, wave_grid(kc, 256, num_sms() * 4), 256, 0, st, sorted, work, hits, p, cnt, ps,
+             cand);
   return RAD_OK;
 }
 
@@ -1038,16 +1058,18 @@ rad_status diam_run(int n, const RoiDiam* rd, const RoiOut* ro, const long long*
   RAD_CUDA(cudaMemsetAsync(cursor, 0, sizeof(int) * K1, st));
   RAD_CUDA(cudaMemsetAsync(cnt, 0, sizeof(Counters), st));
   RAD_LAUNCH("diam_init", k_diam_init, std::max(1, std::min((n + 255) / 256, sms * 4)), 256, 0, st, out, n);
-  const int vblocks = (int)std::min<long long>((nv + 255) / 256, (long long)sms * 8);
-  RAD_LAUNCH("diam_hist", k_hist, vblocks, 256, 0, st, idx2, nv_dev, rd, ro, p, hist);
+  RAD_LAUNCH("diam_hist", k_hist, wave_grid(k_hist, 256, (nv + 255) / 256), 256, 0, st, idx2, nv_dev, rd, ro, p, hist);
   RAD_LAUNCH("diam_scan_part", k_xscan_part, (int)nparts, kScanBlock, 0, st, hist, K1, offs, parts);
   RAD_LAUNCH("diam_scan_top", k_xscan_top, 1, 1024, 0, st, parts, (int)nparts);
-  RAD_LAUNCH("diam_scatter", k_scatter, vblocks, 256, 0, st, idx2, vt, nv_dev, rd, ro, p, offs, parts, cursor, sorted);
-  RAD_LAUNCH("diam_setup", k_setup, sms * 4, 256, 0, st, rd, p, offs, parts, probs, tiles, chunk0, ps, cnt);
-  RAD_LAUNCH("diam_tile_box", k_tile_box, sms * 8, 256, 0, st, sorted, tiles, p, cnt, box, rep);
-  RAD_LAUNCH("diam_seed", k_seed, sms * 8, 256, 0, st, sorted, rep, p, tiles, chunk0, cnt, ps);
+  RAD_LAUNCH("diam_scatter", k_scatter, wave_grid(k_scatter, 256, (nv + 255) / 256), 256, 0, st, idx2, vt, nv_dev, rd,
+             ro, p, offs, parts, cursor, sorted);
+  RAD_LAUNCH("diam_setup", k_setup, wave_grid(k_setup, 256, (n + nplanes + 255) / 256 + 1), 256, 0, st, rd, p, offs,
+             parts, probs, tiles, chunk0, ps, cnt);
+  RAD_LAUNCH("diam_tile_box", k_tile_box, wave_grid(k_tile_box, 256, 1LL << 30), 256, 0, st, sorted, tiles, p, cnt, box,
+             rep);
+  RAD_LAUNCH("diam_seed", k_seed, wave_grid(k_seed, 256, 1LL << 30), 256, 0, st, sorted, rep, p, tiles, chunk0, cnt, ps);
   RAD_LAUNCH("diam_thresh", k_thresh, sms * 2, 256, 0, st, rd, probs, p, cnt, ps);
-  RAD_LAUNCH("diam_cull", k_cull, sms * 8, 256, 0, st, tiles, box, p, chunk0, cnt, ps, work);
+  RAD_LAUNCH("diam_cull", k_cull, wave_grid(k_cull, 256, 1LL << 30), 256, 0, st, tiles, box, p, chunk0, cnt, ps, work);
   const int ctas = sms * tu.ctas_per_sm;
   if (tu.tile == 64) {
     if (tu.threads == 64) RAD_TRY((launch_pairs<64, 64>(sorted, work, p, rd, cnt, ps, slicemax, hits, cand, ctas, st)));
@@ -1080,6 +1102,7 @@ __device__ __forceinline__ void take_best(BestD& b, double d2, int i, int j) {
 __global__ void __launch_bounds__(kPlainTile) k_plain(const int16_t* __restrict__ idx2, const double* __restrict__ vt,
                                                       int n, double sx, double sy, double sz,
                                                       BestD* __restrict__ part) {
+  pdl_enter();
   __shared__ double su[3][kPlainTile];
   __shared__ int sq[3][kPlainTile];
   __shared__ BestD sred[4][kPlainTile / 32];
@@ -1148,6 +1171,7 @@ __global__ void __launch_bounds__(kPlainTile) k_plain(const int16_t* __restrict_
 }
 
 __global__ void k_plain_final(const BestD* __restrict__ part, int nparts, DiamResult* __restrict__ out) {
+  pdl_enter();
   if (threadIdx.x < 4) {
     const int q = threadIdx.x;
     BestD r;

@@ -94,6 +94,7 @@ __device__ __forceinline__ uint32_t nz4(uint32_t v) {
 // One thread per bitset word of the whole batch (padding rows included).
 template <bool SOFT>
 __global__ void k_pack(const Roi* __restrict__ rois, int n, long long total, uint32_t* __restrict__ bits) {
+  pdl_enter();
   for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
        id += (long long)gridDim.x * blockDim.x) {
     const Roi& r = rois[n == 1 ? 0 : roi_of_word(rois, n, id)];
@@ -212,6 +213,7 @@ constexpr int kCountThreads = 256;
 __global__ void __launch_bounds__(kCountThreads) k_count(const uint32_t* __restrict__ bits, const Roi* __restrict__ rois, int n, long long total_rows,
                         int L, int Wc, int4* __restrict__ counts, int* __restrict__ wpre, int* __restrict__ tpre,
                         int2* __restrict__ wlist, long long wlist_cap, MeshTotals* __restrict__ tot) {
+  pdl_enter();
   const int lane = threadIdx.x & 31, sub = lane % L, gpw = 32 / L;
   const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -289,6 +291,7 @@ __global__ void __launch_bounds__(kCountThreads) k_count(const uint32_t* __restr
 
 __global__ void k_scan_chunks(const int4* __restrict__ counts, long long R, long long* __restrict__ prefix,
                               long long* __restrict__ chunk) {
+  pdl_enter();
   __shared__ long long sw[4][8];
   const long long beg = (long long)blockIdx.x * kScanChunk;
   constexpr int per = kScanChunk / 256;
@@ -326,6 +329,7 @@ __global__ void k_scan_chunks(const int4* __restrict__ counts, long long R, long
 }
 
 __global__ void k_scan_top(long long* __restrict__ chunk, int nchunks, MeshTotals* __restrict__ tot) {
+  pdl_enter();
   __shared__ long long sw[4][32];
   long long carry[4] = {0, 0, 0, 0};
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -371,6 +375,7 @@ __device__ __forceinline__ long long row_base(const long long* prefix, const lon
 __global__ void k_roi_ranges(const Roi* __restrict__ rois, int n, const long long* __restrict__ prefix,
                              const long long* __restrict__ chunk, const MeshTotals* __restrict__ tot,
                              RoiOut* __restrict__ out) {
+  pdl_enter();
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const Roi& r = rois[i];
     const bool last = i == n - 1;
@@ -430,6 +435,7 @@ __device__ int select_candidate(int loop, const double (*w)[3], const double* sp
 // with A, B, C the local doubled positions (integers 0..2), and area2 = sum of
 // |cof(H) ((B - A) x (C - A))| with H = diag(s / 2).
 __global__ void k_binary_table(const double* __restrict__ spacings, BinCase* __restrict__ tabs) {
+  pdl_enter();
   const int cs = threadIdx.x;
   const double sx = spacings[3 * blockIdx.x], sy = spacings[3 * blockIdx.x + 1], sz = spacings[3 * blockIdx.x + 2];
   BinCase* tab = tabs + 256 * blockIdx.x;
@@ -495,6 +501,7 @@ __global__ void k_rows(const uint32_t* __restrict__ bits, const Roi* __restrict_
                        const long long* __restrict__ prefix, const long long* __restrict__ chunk,
                        int16_t* __restrict__ idx2, double* __restrict__ vt, int4* __restrict__ cubes, long long vcap,
                        long long ccap, MeshTotals* __restrict__ tot) {
+  pdl_enter();
   const int lane = threadIdx.x & 31, sub = lane % L, gpw = 32 / L;
   const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -645,6 +652,7 @@ __global__ void __launch_bounds__(kCubeThreads) k_cubes(const uint32_t* __restri
                                                         MeshTotals* __restrict__ tot, RoiOut* __restrict__ out,
                                                         unsigned long long* __restrict__ case_hist,
                                                         double* __restrict__ partial) {
+  pdl_enter();
   const long long ncubes = min(tot->na, ccap);
   long long vsum = 0;
   double acc_v6 = 0.0, acc_a2 = 0.0;
@@ -833,6 +841,7 @@ __global__ void __launch_bounds__(kEmitThreads, kEmitBlocksPerSM)
            const long long* __restrict__ prefix, const long long* __restrict__ chunk, const BinCase* __restrict__ tab,
            int16_t* __restrict__ idx2, int32_t* __restrict__ tri, long long vcap, long long tcap,
            MeshTotals* __restrict__ tot, RoiOut* __restrict__ out, unsigned long long* __restrict__ case_hist) {
+  pdl_enter();
   __shared__ EmitShared sh[kEmitWarps];
   __shared__ unsigned int s_hist[kEmitWarps][256];  // case counts of the warp's current ROI
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -1084,6 +1093,7 @@ __global__ void __launch_bounds__(kEmitThreads, kEmitBlocksPerSM)
 //   6V = det(diag(s / 2)) * vsum,  2A = sum over cases of count * area2 of the case.
 __global__ void k_mask_totals(const Roi* __restrict__ rois, int n, const BinCase* __restrict__ tab,
                               const unsigned long long* __restrict__ case_hist, RoiOut* __restrict__ out) {
+  pdl_enter();
   __shared__ double s[256];
   for (int i = blockIdx.x; i < n; i += gridDim.x) {
     const Roi& r = rois[i];
@@ -1140,13 +1150,13 @@ rad_status mesh_count(const MeshBatch& b, MeshScratch& s, MeshTotals* tot, RoiOu
   RAD_CUDA(cudaMemsetAsync(out, 0, sizeof(RoiOut) * b.n, st));
   RAD_CUDA(cudaMemsetAsync(s.hist.p, 0, sizeof(unsigned long long) * 256 * b.n, st));
   const int sms = num_sms();
-  const int pack_blocks = (int)std::max<long long>(1, std::min<long long>((b.words + 255) / 256, (long long)sms * 16));
+  const int pack_blocks = wave_grid(k_pack<false>, 256, (b.words + 255) / 256);
   if (b.soft)
     RAD_LAUNCH("mc_pack_f32", k_pack<true>, pack_blocks, 256, 0, st, b.rois, b.n, b.words, s.bits.as<uint32_t>());
   else
     RAD_LAUNCH("mc_pack_u8", k_pack<false>, pack_blocks, 256, 0, st, b.rois, b.n, b.words, s.bits.as<uint32_t>());
   const long long warps_needed = (b.rows + (32 / b.L) - 1) / (32 / b.L);
-  const int rblocks = (int)std::max<long long>(1, std::min<long long>((warps_needed + 7) / 8, (long long)sms * 8));
+  const int rblocks = wave_grid(k_count, kCountThreads, (warps_needed + 7) / 8);
   RAD_LAUNCH("mc_count", k_count, rblocks, kCountThreads, 0, st, s.bits.as<uint32_t>(), b.rois, b.n, b.rows, b.L, b.Wc,
              s.counts.as<int4>(), s.wpre.as<int>(), s.tpre.as<int>(), s.wlist.as<int2>(), b.wpre, tot);
   RAD_LAUNCH("mc_scan_chunks", k_scan_chunks, (int)nchunks, 256, 0, st, s.counts.as<int4>(), b.rows,

@@ -47,6 +47,7 @@ __device__ __forceinline__ void na_take(NaBest& b, double d2, int i, int j) {
 __global__ void __launch_bounds__(kNaTile) k_na_rows(const int16_t* __restrict__ idx2, const double* __restrict__ vt,
                                                      int n, double sx, double sy, double sz,
                                                      NaBest* __restrict__ slots) {
+  pdl_enter();
   __shared__ double su[3][kNaTile];
   __shared__ int sq[3][kNaTile];
   __shared__ NaBest sred[4][kNaTile / 32];
@@ -108,6 +109,7 @@ __global__ void __launch_bounds__(kNaTile) k_na_rows(const int16_t* __restrict__
 
 __global__ void k_na_final(const NaBest* __restrict__ slots, int tiles, double* __restrict__ d2_out,
                            int32_t* __restrict__ pairs_out) {
+  pdl_enter();
   if (threadIdx.x < 4) {
     const int q = threadIdx.x;
     NaBest r;

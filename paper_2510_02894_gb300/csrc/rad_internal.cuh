@@ -1,6 +1,9 @@
 // Internal declarations shared by the CUDA translation units of librad.
 #pragma once
 #include <cuda_runtime.h>
+
+#include <algorithm>
+#include <utility>
 #include <stdint.h>
 
 #include <string>
@@ -32,18 +35,57 @@ rad_status cuda_fail(cudaError_t e, const char* what, const char* file, int line
 void launch_begin(const char* name, cudaStream_t s, void** token);
 void launch_end(void* token, cudaStream_t s);
 
-#define RAD_LAUNCH(name, kernel, grid, block, smem, stream, ...)     \
-  do {                                                               \
-    void* _tok = nullptr;                                            \
-    ::rad::launch_begin(name, stream, &_tok);                        \
-    kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);      \
-    cudaError_t _le = cudaGetLastError();                            \
-    ::rad::launch_end(_tok, stream);                                 \
-    if (_le != cudaSuccess) return ::rad::cuda_fail(_le, name, __FILE__, __LINE__); \
+// Kernels after the first of a pass are launched with programmatic stream
+// serialization (unless per-kernel events are on): their CTAs are scheduled
+// while the previous kernel drains and wait in pdl_enter() until it has
+// completed and its writes are visible, which hides the launch gap between
+// dependent kernels (also inside captured graphs).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_kernel(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, bool pdl,
+                          Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = pdl ? at : nullptr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
+}
+
+#define RAD_LAUNCH(name, kernel, grid, block, smem, stream, ...)                                   \
+  do {                                                                                             \
+    void* _tok = nullptr;                                                                          \
+    ::rad::launch_begin(name, stream, &_tok);                                                      \
+    cudaError_t _le = ::rad::launch_kernel(kernel, dim3(grid), dim3(block), (size_t)(smem), (stream), \
+                                           _tok == nullptr, __VA_ARGS__);                          \
+    if (_le == cudaSuccess) _le = cudaGetLastError();                                              \
+    ::rad::launch_end(_tok, stream);                                                               \
+    if (_le != cudaSuccess) return ::rad::cuda_fail(_le, name, __FILE__, __LINE__);                \
   } while (0)
+
+// First statement of every kernel: wait for the previous kernel in the stream
+// (a no-op without a programmatic dependency), then let the next one be
+// scheduled.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
 
 int num_sms();
 bool profiling_on();
+// CTAs of a kernel that are resident on one SM at once (cached per kernel,
+// block size and device; at least 1).
+int resident_ctas(const void* kernel, int threads, size_t smem);
+// One full wave of a persistent (grid-stride) kernel, at most `needed` CTAs.
+template <typename K>
+int wave_grid(K kernel, int threads, long long needed, size_t smem = 0) {
+  const long long wave = (long long)num_sms() * resident_ctas((const void*)kernel, threads, smem);
+  return (int)std::max<long long>(1, std::min<long long>(needed, wave));
+}
 long long alloc_epoch();           // bumps whenever a library buffer is reallocated
 
 // ---- device buffers ----------------------------------------------------------

@@ -44,6 +44,7 @@ __global__ void k_soft_tri_grad(const int16_t* __restrict__ idx2, const double* 
                                 const int32_t* __restrict__ tri, const long long* __restrict__ nt_dev,
                                 long long tcap, MeshDims d, double sx, double sy, double sz, double gA, double gV,
                                 double* __restrict__ gvtx) {
+  pdl_enter();
   const long long nt = min(*nt_dev, tcap);
   const double sp[3] = {sx, sy, sz};
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nt; t += (long long)gridDim.x * blockDim.x) {
@@ -89,6 +90,7 @@ __global__ void k_soft_tri_grad(const int16_t* __restrict__ idx2, const double* 
 
 __global__ void k_soft_d3_grad(const int16_t* __restrict__ idx2, const double* __restrict__ vt, int i, int j,
                                MeshDims d, double sx, double sy, double sz, double gD, double* __restrict__ gvtx) {
+  pdl_enter();
   if (threadIdx.x != 0 || blockIdx.x != 0 || i < 0 || j < 0 || gD == 0.0) return;
   const double sp[3] = {sx, sy, sz};
   double pi[3], pj[3], df[3];
@@ -111,6 +113,7 @@ __device__ __forceinline__ double voxel(const float* p, const MeshDims& d, int x
 __global__ void k_soft_scatter(const int16_t* __restrict__ idx2, const float* __restrict__ prob,
                                const long long* __restrict__ nv_dev, long long vcap, MeshDims d, double sx, double sy,
                                double sz, const double* __restrict__ gvtx, double* __restrict__ grad) {
+  pdl_enter();
   const long long nv = min(*nv_dev, vcap);
   const double sp[3] = {sx, sy, sz};
   for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nv; v += (long long)gridDim.x * blockDim.x) {
