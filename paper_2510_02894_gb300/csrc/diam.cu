@@ -28,15 +28,23 @@
 //   4. The candidates are re-evaluated in FP64 with the pinned formula: the
 //      largest d2 per ROI and category, then the smallest (i, j) attaining it.
 //
-// FP32 error bound (per pair, binary or soft; u = 2^-24, positions a relative
-// to the grid centre, R = the grid's half extent in mm):
-//   P_k = fl32(a_k),  dx = fl(P_i - P_j),  f = fma(dz,dz, fma(dy,dy, dx*dx))
-//   |f - d2| <= 5.1u d2 + 4.1u |R| sqrt(d2) + 4.1u^2 |R|^2.
-// T(F) inverts this bound (with every coefficient doubled), so every pair
-// attaining the FP64 maximum has f >= T(F) for any F not above the largest
-// f; the culling bound uses the same monotone FP32 operations on box
-// distances, so it bounds f from above without any epsilon.  T only grows, so
-// a pair culled or left out against an earlier T is also below the final one.
+// FP32 error bounds (per pair, binary or soft; u = 2^-24, positions a relative
+// to the grid centre, R = the grid's half diagonal in mm, d2 the FP64 value):
+//   P = fl32(a), and once per entry n = fl(fl(P_x P_x + P_y P_y) + P_z P_z).
+//   Pair kernels (expansion form, 4 FP32 operations per pair):
+//     g = fma(-2P_ix, P_jx, fma(-2P_iy, P_jy, fma(-2P_iz, P_jz, fl(n_i + n_j))))
+//     |g - d2| <= 4.1u R sqrt(d2) + 20.2u R^2
+//     (the norms carry gamma_3 |P|^2, their sum u (n_i + n_j), the fma chain
+//     gamma_3 (|s| + 2 |P_i| |P_j|); the FP32 positions 4u R sqrt(d2) + 4u^2 R^2)
+//   Seed and box bounds (difference form):
+//     dx = fl(P_i - P_j), f = fma(dz,dz, fma(dy,dy, dx*dx))
+//     |f - d2| <= 5.1u d2 + 4.1u R sqrt(d2) + 4.1u^2 R^2.
+// T(F) inverts the larger coefficient of each term (every coefficient
+// doubled), so every pair attaining the FP64 maximum has g >= T(F) and
+// f >= T(F) for any F not above the largest g or f of any pair; the culling
+// bound uses the difference form's monotone FP32 operations on box distances,
+// so it bounds f from above without any epsilon.  T only grows, so a pair
+// culled or left out against an earlier T is also below the final one.
 #include <float.h>
 #include <limits.h>
 #include <math.h>
@@ -104,6 +112,18 @@ struct Params {
   long long work_cap, cand_cap, max_problems, max_tiles;
   long long nv_cap;   // vertex pool capacity: device counts are clamped to it
 };
+
+// Expansion form: a2 = (-2 P_i, n_i), b = (P_j, n_j).
+__device__ __forceinline__ float pair_g(float4 a2, float4 b) {
+  float g = __fadd_rn(a2.w, b.w);
+  g = __fmaf_rn(a2.z, b.z, g);
+  g = __fmaf_rn(a2.y, b.y, g);
+  return __fmaf_rn(a2.x, b.x, g);
+}
+
+__device__ __forceinline__ float4 expand_a(float4 a) {
+  return make_float4(__fmul_rn(-2.0f, a.x), __fmul_rn(-2.0f, a.y), __fmul_rn(-2.0f, a.z), a.w);
+}
 
 __device__ __forceinline__ float pair_f(float4 a, float4 b) {
   const float dx = __fsub_rn(a.x, b.x), dy = __fsub_rn(a.y, b.y), dz = __fsub_rn(a.z, b.z);
@@ -204,7 +224,7 @@ __global__ void k_scatter(const int16_t* __restrict__ idx2, const double* __rest
                           const long long* __restrict__ nv_dev, const RoiDiam* __restrict__ rd,
                           const RoiOut* __restrict__ ro, Params p, const long long* __restrict__ offs,
                           const long long* __restrict__ parts, int* __restrict__ cursor,
-                          float4* __restrict__ sorted) {
+                          float4* __restrict__ sorted, int* __restrict__ ids) {
   pdl_enter();
   const long long n = min(*nv_dev, p.nv_cap);
   const int lane = threadIdx.x & 31;
@@ -220,8 +240,9 @@ __global__ void k_scatter(const int16_t* __restrict__ idx2, const double* __rest
       const RoiDiam& r = rd[roi];
       double u[3];
       vertex_u(idx2, vt, v, u);
-      e = make_float4(__double2float_rn((u[0] - r.cx) * r.sx), __double2float_rn((u[1] - r.cy) * r.sy),
-                      __double2float_rn((u[2] - r.cz) * r.sz), __int_as_float((int)v));
+      const float px = __double2float_rn((u[0] - r.cx) * r.sx), py = __double2float_rn((u[1] - r.cy) * r.sy),
+                  pz = __double2float_rn((u[2] - r.cz) * r.sz);
+      e = make_float4(px, py, pz, __fadd_rn(__fadd_rn(__fmul_rn(px, px), __fmul_rn(py, py)), __fmul_rn(pz, pz)));
     }
     const RoiDiam& r = rd[roi];
     long long key[4];
@@ -241,8 +262,11 @@ __global__ void k_scatter(const int16_t* __restrict__ idx2, const double* __rest
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int b = __shfl_sync(0xffffffffu, base[k], __ffs(peers[k]) - 1);
-      if (key[k] >= 0)
-        sorted[key_offset(offs, parts, key[k]) + b + __popc(peers[k] & ((1u << lane) - 1u))] = e;
+      if (key[k] >= 0) {
+        const long long slot = key_offset(offs, parts, key[k]) + b + __popc(peers[k] & ((1u << lane) - 1u));
+        sorted[slot] = e;
+        ids[slot] = (int)v;
+      }
     }
   }
 }
@@ -725,7 +749,7 @@ __global__ void __launch_bounds__(NT) k_pairs(const float4* __restrict__ sorted,
     if (!(w_cur.ub < T) && 32 * s < w_cur.blen) {
       float4 a[RA];
 #pragma unroll
-      for (int r = 0; r < RA; ++r) a[r] = sA[wid][buf][lane + 32 * r];
+      for (int r = 0; r < RA; ++r) a[r] = expand_a(sA[wid][buf][lane + 32 * r]);
       float mx[RA];
 #pragma unroll
       for (int r = 0; r < RA; ++r) mx[r] = 0.0f;
@@ -734,16 +758,16 @@ __global__ void __launch_bounds__(NT) k_pairs(const float4* __restrict__ sorted,
       for (int j = 0; j < 32; ++j) {
         const float4 b = sb[j];
 #pragma unroll
-        for (int r = 0; r < RA; ++r) mx[r] = fmaxf(mx[r], pair_f(a[r], b));
+        for (int r = 0; r < RA; ++r) mx[r] = fmaxf(mx[r], pair_g(a[r], b));
       }
       m = mx[0];
 #pragma unroll
       for (int r = 1; r < RA; ++r) m = fmaxf(m, mx[r]);
       for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
       if (lane == 0) {
-        if (m > F) {
-          const unsigned int old = atomicMax(&ps[w_cur.problem].F, __float_as_uint(m));
-          if (__float_as_uint(m) > old) atomicMax(&ps[w_cur.problem].T, __float_as_uint(threshold(m, rd[w_cur.roi])));
+        if (m > F) {  // fire and forget: T(F) is monotone, so the largest m wins both maxima
+          atomicMax(&ps[w_cur.problem].F, __float_as_uint(m));
+          atomicMax(&ps[w_cur.problem].T, __float_as_uint(threshold(m, rd[w_cur.roi])));
         }
         n_items += s == 0;
         n_pairs += (unsigned long long)w_cur.alen * (unsigned long long)min(32, w_cur.blen - 32 * s);
@@ -812,7 +836,7 @@ __global__ void k_cand(const float4* __restrict__ sorted, const WorkItem* __rest
     const bool same = w.abeg == w.bbeg;
     float4 a[RA];
 #pragma unroll
-    for (int r = 0; r < RA; ++r) a[r] = sorted[w.abeg + min(lane + 32 * r, w.alen - 1)];
+    for (int r = 0; r < RA; ++r) a[r] = expand_a(sorted[w.abeg + min(lane + 32 * r, w.alen - 1)]);
     const float4 bl = sorted[w.bbeg + min(jb + lane, w.blen - 1)];
     const int nj = min(32, w.blen - jb);
     for (int jj = 0; jj < nj; ++jj) {
@@ -820,12 +844,12 @@ __global__ void k_cand(const float4* __restrict__ sorted, const WorkItem* __rest
       b.x = __shfl_sync(0xffffffffu, bl.x, jj);
       b.y = __shfl_sync(0xffffffffu, bl.y, jj);
       b.z = __shfl_sync(0xffffffffu, bl.z, jj);
-      b.w = 0.0f;
+      b.w = __shfl_sync(0xffffffffu, bl.w, jj);
       const int j = jb + jj;
 #pragma unroll
       for (int r = 0; r < RA; ++r) {
         const int ia = lane + 32 * r;
-        const bool c = ia < w.alen && (!same || ia < j) && pair_f(a[r], b) >= T;
+        const bool c = ia < w.alen && (!same || ia < j) && pair_g(a[r], b) >= T;
         const unsigned int cm = __ballot_sync(0xffffffffu, c);
         if (cm == 0) continue;
         long long base = 0;
@@ -850,7 +874,7 @@ __global__ void k_cand(const float4* __restrict__ sorted, const WorkItem* __rest
 
 // Largest pinned FP64 d2 per ROI and category.  Every pair attaining it is a
 // candidate of its problem, so the maximum over candidates is the maximum.
-__global__ void k_confirm(const float4* __restrict__ sorted, const int16_t* __restrict__ idx2,
+__global__ void k_confirm(const int* __restrict__ ids, const int16_t* __restrict__ idx2,
                           const double* __restrict__ vt, Params p, const RoiDiam* __restrict__ rd,
                           const Counters* __restrict__ cnt, const Cand* __restrict__ cand,
                           DiamOut* __restrict__ out) {
@@ -859,7 +883,7 @@ __global__ void k_confirm(const float4* __restrict__ sorted, const int16_t* __re
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nc; c += (long long)gridDim.x * blockDim.x) {
     const Cand k = cand[c];
     const RoiDiam& r = rd[k.roi];
-    const int i = __float_as_int(sorted[k.ea].w), j = __float_as_int(sorted[k.eb].w);
+    const int i = ids[k.ea], j = ids[k.eb];
     double ui[3], uj[3];
     vertex_u(idx2, vt, i, ui);
     vertex_u(idx2, vt, j, uj);
@@ -870,7 +894,7 @@ __global__ void k_confirm(const float4* __restrict__ sorted, const int16_t* __re
 
 // Candidates attaining their ROI's maximum in their category take the
 // smallest (i, j) (ids local to the ROI).  Block 0 also copies the counters.
-__global__ void k_tiebreak(const float4* __restrict__ sorted, const int16_t* __restrict__ idx2,
+__global__ void k_tiebreak(const int* __restrict__ ids, const int16_t* __restrict__ idx2,
                            const double* __restrict__ vt, Params p, const RoiDiam* __restrict__ rd,
                            const RoiOut* __restrict__ ro, const Counters* __restrict__ cnt,
                            const Cand* __restrict__ cand, DiamOut* __restrict__ out, DiamStats* __restrict__ stats) {
@@ -889,7 +913,7 @@ __global__ void k_tiebreak(const float4* __restrict__ sorted, const int16_t* __r
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nc; c += (long long)gridDim.x * blockDim.x) {
     const Cand k = cand[c];
     const RoiDiam& r = rd[k.roi];
-    int i = __float_as_int(sorted[k.ea].w), j = __float_as_int(sorted[k.eb].w);
+    int i = ids[k.ea], j = ids[k.eb];
     double ui[3], uj[3];
     vertex_u(idx2, vt, i, ui);
     vertex_u(idx2, vt, j, uj);
@@ -989,9 +1013,10 @@ void plan_diam(const std::vector<Roi>& rois, bool soft, std::vector<RoiDiam>& rd
       const double r = 0.5 * (nn[k] + 1) * sp[k];
       R2 += r * r;
     }
+    // the larger coefficient of the two FP32 forms, doubled
     p.alpha = 2.0 * 5.1 * u + 1e-14;
     p.beta = 2.0 * 4.1 * u * sqrt(R2);
-    p.gamma = 2.0 * 4.1 * u * u * R2;
+    p.gamma = 2.0 * std::max(20.2 * u * R2, 4.1 * u * u * R2);
   }
 }
 
@@ -1023,6 +1048,7 @@ rad_status diam_run(int n, const RoiDiam* rd, const RoiOut* ro, const long long*
   add(sizeof(long long) * K1);       // offsets
   add(sizeof(long long) * (nparts + 1));
   add(sizeof(float4) * nsorted);
+  add(sizeof(int) * nsorted);  // vertex id of every sorted entry
   add(sizeof(Problem) * p.max_problems);
   add(sizeof(Tile) * p.max_tiles);
   add(sizeof(int) * p.max_tiles);    // chunk0
@@ -1041,6 +1067,7 @@ rad_status diam_run(int n, const RoiDiam* rd, const RoiOut* ro, const long long*
   long long* offs = carve<long long>(cur, K1);
   long long* parts = carve<long long>(cur, nparts + 1);
   float4* sorted = carve<float4>(cur, nsorted);
+  int* ids = carve<int>(cur, nsorted);
   Problem* probs = carve<Problem>(cur, p.max_problems);
   Tile* tiles = carve<Tile>(cur, p.max_tiles);
   int* chunk0 = carve<int>(cur, p.max_tiles);
@@ -1062,7 +1089,7 @@ rad_status diam_run(int n, const RoiDiam* rd, const RoiOut* ro, const long long*
   RAD_LAUNCH("diam_scan_part", k_xscan_part, (int)nparts, kScanBlock, 0, st, hist, K1, offs, parts);
   RAD_LAUNCH("diam_scan_top", k_xscan_top, 1, 1024, 0, st, parts, (int)nparts);
   RAD_LAUNCH("diam_scatter", k_scatter, wave_grid(k_scatter, 256, (nv + 255) / 256), 256, 0, st, idx2, vt, nv_dev, rd,
-             ro, p, offs, parts, cursor, sorted);
+             ro, p, offs, parts, cursor, sorted, ids);
   RAD_LAUNCH("diam_setup", k_setup, wave_grid(k_setup, 256, (n + nplanes + 255) / 256 + 1), 256, 0, st, rd, p, offs,
              parts, probs, tiles, chunk0, ps, cnt);
   RAD_LAUNCH("diam_tile_box", k_tile_box, wave_grid(k_tile_box, 256, 1LL << 30), 256, 0, st, sorted, tiles, p, cnt, box,
@@ -1082,8 +1109,8 @@ rad_status diam_run(int n, const RoiDiam* rd, const RoiOut* ro, const long long*
     if (tu.threads == 64) RAD_TRY((launch_pairs<256, 64>(sorted, work, p, rd, cnt, ps, slicemax, hits, cand, ctas, st)));
     else RAD_TRY((launch_pairs<256, 128>(sorted, work, p, rd, cnt, ps, slicemax, hits, cand, ctas, st)));
   }
-  RAD_LAUNCH("diam_confirm", k_confirm, sms, 256, 0, st, sorted, idx2, vt, p, rd, cnt, cand, out);
-  RAD_LAUNCH("diam_tiebreak", k_tiebreak, sms, 256, 0, st, sorted, idx2, vt, p, rd, ro, cnt, cand, out, stats);
+  RAD_LAUNCH("diam_confirm", k_confirm, sms, 256, 0, st, ids, idx2, vt, p, rd, cnt, cand, out);
+  RAD_LAUNCH("diam_tiebreak", k_tiebreak, sms, 256, 0, st, ids, idx2, vt, p, rd, ro, cnt, cand, out, stats);
   return RAD_OK;
 }
 
