@@ -257,7 +257,10 @@ __global__ void __launch_bounds__(kCountThreads) k_count(const uint32_t* __restr
         tw += MC_CASE_NTRI[cube_case(v.a, v.as, v.b, v.bs, v.c, v.cs, v.e, v.es, __ffs(act) - 1)];
       const int incl = group_incl(cnt, sub, L), tincl = group_incl(tw, sub, L);
       const bool live = it.valid && w < W;
-      if (live) {
+      // words with surface go to the emit list; only their prefixes are ever
+      // read (a cube's edge is owned by a word with a crossing, i.e. listed)
+      const bool surf = live && ((v.ex | v.ey | v.ez | v.act) != 0u || (w == 0 && (a0 || case_m1)));
+      if (surf) {
         wpre[wbase + w] = carry + incl - cnt;
         tpre[wbase + w] = tcarry + tincl - tw;
       }
@@ -266,8 +269,6 @@ __global__ void __launch_bounds__(kCountThreads) k_count(const uint32_t* __restr
       if (y >= 0 && z >= 0) nvox += __popc(v.a);
       na += __popc(v.act);
       nt += tw;
-      // words with surface go to the emit list
-      const bool surf = live && ((v.ex | v.ey | v.ez | v.act) != 0u || (w == 0 && (a0 || case_m1)));
       const unsigned int sm = __ballot_sync(0xffffffffu, surf);
       if (sm) {
         if (surf) lb[lbn + __popc(sm & ((1u << lane) - 1u))] = make_int2((int)(it.g), w);
