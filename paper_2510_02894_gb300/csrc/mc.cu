@@ -1118,9 +1118,13 @@ __global__ void k_mask_totals(const Roi* __restrict__ rois, int n, const BinCase
   }
 }
 
+// Lanes per row: several words per lane, so the per-row work (ROI lookup,
+// row addresses, scans) is shared by more words -- four for narrow rows (crop
+// batches), two for wide ones (the emit list then keeps fewer rows per warp).
 int group_lanes(int W) {
+  const int per = W <= 8 ? 4 : 2;
   int L = 1;
-  while (L < W && L < 32) L <<= 1;
+  while (per * L < W && L < 32) L <<= 1;
   return L;
 }
 
