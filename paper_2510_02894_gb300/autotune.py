@@ -52,12 +52,16 @@ def _timer_cuda():
     return time_ms
 
 
-def tune(run, label, reps=5, cache_path=DEFAULT_CACHE, time_ms=None, set_tuning=None, get_tuning=None):
+def tune(run, label, reps=5, cache_path=DEFAULT_CACHE, time_ms=None, set_tuning=None, get_tuning=None,
+         margin=0.01):
     """Staged search; returns (best config dict, list of (config, ms)).
 
     run: callable doing one whole pass of the workload (e.g. a rad_extract or
     rad_batch_run).  time_ms / set_tuning / get_tuning default to CUDA events
-    and the library; tests substitute fakes."""
+    and the library; tests substitute fakes.  A candidate replaces the best
+    only when it is faster by `margin` (relative), and the winner is timed
+    again against the starting configuration with twice the repetitions, so
+    timing noise does not move the configuration."""
     time_ms = time_ms or _timer_cuda()
     set_tuning = set_tuning or rad.set_tuning
     get_tuning = get_tuning or rad.get_tuning
@@ -75,6 +79,9 @@ def tune(run, label, reps=5, cache_path=DEFAULT_CACHE, time_ms=None, set_tuning=
         seen[key] = ms
         return ms
 
+    def better(ms, ref):
+        return ms < ref * (1.0 - margin)
+
     best = dict(start)
     best_ms = trial(best)
     for cs in CELL_SHIFTS:
@@ -82,22 +89,31 @@ def tune(run, label, reps=5, cache_path=DEFAULT_CACHE, time_ms=None, set_tuning=
             continue
         cfg = dict(best, cell_shift=cs)
         ms = trial(cfg)
-        if ms < best_ms:
+        if better(ms, best_ms):
             best, best_ms = cfg, ms
     for tile, threads in SHAPES:
         if (tile, threads) == (best["tile"], best["threads"]):
             continue
         cfg = dict(best, tile=tile, threads=threads)
         ms = trial(cfg)
-        if ms < best_ms:
+        if better(ms, best_ms):
             best, best_ms = cfg, ms
     for c in CTAS_PER_SM:
         if c == best["ctas_per_sm"]:
             continue
         cfg = dict(best, ctas_per_sm=c)
         ms = trial(cfg)
-        if ms < best_ms:
+        if better(ms, best_ms):
             best, best_ms = cfg, ms
+    if best != start:  # confirm against the start with more repetitions
+        set_tuning(**start)
+        ms_start = time_ms(run, 2 * reps)
+        set_tuning(**best)
+        ms_best = time_ms(run, 2 * reps)
+        if not better(ms_best, ms_start):
+            best, best_ms = dict(start), ms_start
+        else:
+            best_ms = ms_best
     set_tuning(**best)
     if cache_path:
         store(label, best, best_ms, cache_path)

@@ -216,7 +216,7 @@ __global__ void k_hist(const int16_t* __restrict__ idx2, const long long* __rest
   }
 }
 
-__device__ __forceinline__ long long key_offset(const long long* offs, const long long* parts, long long key);
+__device__ __forceinline__ long long key_offset(const long long* offs, const long long* parts, long long key);  // below
 
 // The four slot reservations of a warp are issued back to back, so one
 // round trip covers all of them.
@@ -271,16 +271,31 @@ __global__ void k_scatter(const int16_t* __restrict__ idx2, const double* __rest
   }
 }
 
-// Generic exclusive scan of int counts to long long offsets (2 kernels).
-constexpr int kScanBlock = 1024;
-__global__ void k_xscan_part(const int* __restrict__ in, long long n, long long* __restrict__ out,
-                             long long* __restrict__ part) {
+// Exclusive scan of the key counts to global offsets, one kernel with a
+// decoupled look-back over chunks of kScanBlock keys (4 per thread).
+constexpr int kScanBlock = 4096;
+constexpr int kScanThreads = 1024;
+__global__ void __launch_bounds__(kScanThreads) k_xscan(const int* __restrict__ in, long long n, int nchunks,
+                                                        long long* __restrict__ out, ScanTile<1>* __restrict__ tiles,
+                                                        unsigned int* __restrict__ tick,
+                                                        unsigned int* __restrict__ status) {
   pdl_enter();
   __shared__ long long ws[32];
-  const long long i = blockIdx.x * (long long)kScanBlock + threadIdx.x;
-  long long v = i < n ? in[i] : 0;
+  __shared__ long long s_ex;
+  __shared__ int s_c;
+  if (threadIdx.x == 0) s_c = (int)atomicAdd(tick, 1u);
+  __syncthreads();
+  const int c = s_c;
+  const long long i0 = (long long)c * kScanBlock + 4 * threadIdx.x;
+  long long v[4];
+  long long own = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    v[k] = i0 + k < n ? in[i0 + k] : 0;
+    own += v[k];
+  }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  long long inc = v;
+  long long inc = own;
   for (int off = 1; off < 32; off <<= 1) {
     const long long o = __shfl_up_sync(0xffffffffu, inc, off);
     if (lane >= off) inc += o;
@@ -288,43 +303,35 @@ __global__ void k_xscan_part(const int* __restrict__ in, long long n, long long*
   if (lane == 31) ws[wid] = inc;
   __syncthreads();
   long long wb = 0, tot = 0;
-  for (int k = 0; k < kScanBlock / 32; ++k) {
+  for (int k = 0; k < kScanThreads / 32; ++k) {
     if (k < wid) wb += ws[k];
     tot += ws[k];
   }
-  if (i < n) out[i] = wb + inc - v;
-  if (threadIdx.x == 0) part[blockIdx.x] = tot;
-}
-
-__global__ void k_xscan_top(long long* __restrict__ part, int nparts) {
-  pdl_enter();
-  __shared__ long long ws[32];
-  long long carry = 0;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int base = 0; base < nparts; base += blockDim.x) {
-    const int i = base + threadIdx.x;
-    const long long v = i < nparts ? part[i] : 0;
-    long long inc = v;
-    for (int off = 1; off < 32; off <<= 1) {
-      const long long o = __shfl_up_sync(0xffffffffu, inc, off);
-      if (lane >= off) inc += o;
+  if (threadIdx.x == 0) scan_publish(&tiles[c], &tot, c == 0 ? 2ull : 1ull);
+  if (wid == 0) {
+    long long e = 0;
+    if (c > 0) {
+      scan_lookback(tiles, c, &e, status);
+      if (lane == 0) {
+        const long long incl = e + tot;
+        scan_publish(&tiles[c], &incl, 2ull);
+      }
     }
-    if (lane == 31) ws[wid] = inc;
-    __syncthreads();
-    long long wb = 0, tot = 0;
-    for (int k = 0; k < nw; ++k) {
-      if (k < wid) wb += ws[k];
-      tot += ws[k];
-    }
-    if (i < nparts) part[i] = carry + wb + inc - v;
-    carry += tot;
-    __syncthreads();
+    if (lane == 0) s_ex = e;
+  }
+  __syncthreads();
+  long long x = s_ex + wb + inc - own;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (i0 + k < n) out[i0 + k] = x;
+    x += v[k];
   }
 }
 
-// Offset of a key: block-local exclusive prefix + the scanned block total.
+// Global offset of a key.
 __device__ __forceinline__ long long key_offset(const long long* offs, const long long* parts, long long key) {
-  return offs[key] + parts[key / kScanBlock];
+  (void)parts;
+  return offs[key];
 }
 
 // ---- 2. problems and tiles --------------------------------------------------------
@@ -1046,7 +1053,7 @@ rad_status diam_run(int n, const RoiDiam* rd, const RoiOut* ro, const long long*
   add(sizeof(int) * K1);             // hist
   add(sizeof(int) * K1);             // cursor
   add(sizeof(long long) * K1);       // offsets
-  add(sizeof(long long) * (nparts + 1));
+  add(sizeof(ScanTile<1>) * nparts + 16);  // look-back state of the key scan and its ticket
   add(sizeof(float4) * nsorted);
   add(sizeof(int) * nsorted);  // vertex id of every sorted entry
   add(sizeof(Problem) * p.max_problems);
@@ -1065,7 +1072,10 @@ rad_status diam_run(int n, const RoiDiam* rd, const RoiOut* ro, const long long*
   int* hist = carve<int>(cur, K1);
   int* cursor = carve<int>(cur, K1);
   long long* offs = carve<long long>(cur, K1);
-  long long* parts = carve<long long>(cur, nparts + 1);
+  char* scan_state = carve<char>(cur, sizeof(ScanTile<1>) * nparts + 16);
+  ScanTile<1>* stiles = reinterpret_cast<ScanTile<1>*>(scan_state);
+  unsigned int* stick = reinterpret_cast<unsigned int*>(scan_state + sizeof(ScanTile<1>) * nparts);
+  const long long* parts = nullptr;
   float4* sorted = carve<float4>(cur, nsorted);
   int* ids = carve<int>(cur, nsorted);
   Problem* probs = carve<Problem>(cur, p.max_problems);
@@ -1086,8 +1096,9 @@ rad_status diam_run(int n, const RoiDiam* rd, const RoiOut* ro, const long long*
   RAD_CUDA(cudaMemsetAsync(cnt, 0, sizeof(Counters), st));
   RAD_LAUNCH("diam_init", k_diam_init, std::max(1, std::min((n + 255) / 256, sms * 4)), 256, 0, st, out, n);
   RAD_LAUNCH("diam_hist", k_hist, wave_grid(k_hist, 256, (nv + 255) / 256), 256, 0, st, idx2, nv_dev, rd, ro, p, hist);
-  RAD_LAUNCH("diam_scan_part", k_xscan_part, (int)nparts, kScanBlock, 0, st, hist, K1, offs, parts);
-  RAD_LAUNCH("diam_scan_top", k_xscan_top, 1, 1024, 0, st, parts, (int)nparts);
+  RAD_CUDA(cudaMemsetAsync(scan_state, 0, sizeof(ScanTile<1>) * nparts + 16, st));
+  RAD_LAUNCH("diam_scan", k_xscan, (int)nparts, kScanThreads, 0, st, hist, K1, (int)nparts, offs, stiles, stick,
+             &cnt->status);
   RAD_LAUNCH("diam_scatter", k_scatter, wave_grid(k_scatter, 256, (nv + 255) / 256), 256, 0, st, idx2, vt, nv_dev, rd,
              ro, p, offs, parts, cursor, sorted, ids);
   RAD_LAUNCH("diam_setup", k_setup, wave_grid(k_setup, 256, (n + nplanes + 255) / 256 + 1), 256, 0, st, rd, p, offs,

@@ -287,21 +287,31 @@ __global__ void __launch_bounds__(kCountThreads) k_count(const uint32_t* __restr
 }
 
 // ---- scan of row counts -------------------------------------------------------------
-// prefix[row] = chunk-local exclusive prefixes of (vertices, triangles, cubes, voxels);
-// chunk[c] = totals of chunk c, turned into chunk offsets by k_scan_top.
+// One kernel, decoupled look-back over chunks of kScanChunk rows: prefix[4 r + q]
+// = global exclusive prefix of (vertices, triangles, active cubes, inside
+// voxels) at row r over the whole batch; the last chunk writes the totals and
+// the last block to finish derives every ROI's id ranges.
 
-__global__ void k_scan_chunks(const int4* __restrict__ counts, long long R, long long* __restrict__ prefix,
-                              long long* __restrict__ chunk) {
+__global__ void k_scan_rows(const int4* __restrict__ counts, long long R, int nchunks, long long* __restrict__ prefix,
+                            ScanTile<4>* __restrict__ tiles, unsigned int* __restrict__ tick,
+                            MeshTotals* __restrict__ tot, const Roi* __restrict__ rois, int n,
+                            RoiOut* __restrict__ out) {
   pdl_enter();
   __shared__ long long sw[4][8];
-  const long long beg = (long long)blockIdx.x * kScanChunk;
+  __shared__ long long s_ex[4];
+  __shared__ int s_c;
+  __shared__ bool s_last;
+  if (threadIdx.x == 0) s_c = (int)atomicAdd(&tick[0], 1u);
+  __syncthreads();
+  const int c = s_c;
+  const long long beg = (long long)c * kScanChunk;
   constexpr int per = kScanChunk / 256;
   long long own[4] = {0, 0, 0, 0};
-  int4 c[per];
+  int4 cv[per];
   for (int i = 0; i < per; ++i) {
     const long long r = beg + threadIdx.x * per + i;
-    c[i] = r < R ? counts[r] : make_int4(0, 0, 0, 0);
-    own[0] += c[i].x; own[1] += c[i].y; own[2] += c[i].w; own[3] += c[i].z;
+    cv[i] = r < R ? counts[r] : make_int4(0, 0, 0, 0);
+    own[0] += cv[i].x; own[1] += cv[i].y; own[2] += cv[i].w; own[3] += cv[i].z;
   }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   long long inc[4] = {own[0], own[1], own[2], own[3]};
@@ -313,85 +323,72 @@ __global__ void k_scan_chunks(const int4* __restrict__ counts, long long R, long
   if (lane == 31)
     for (int q = 0; q < 4; ++q) sw[q][wid] = inc[q];
   __syncthreads();
-  long long ex[4];
+  long long ex[4], agg[4];
   for (int q = 0; q < 4; ++q) {
-    long long wb = 0;
-    for (int k = 0; k < wid; ++k) wb += sw[q][k];
+    long long wb = 0, tb = 0;
+    for (int k = 0; k < 8; ++k) {
+      if (k < wid) wb += sw[q][k];
+      tb += sw[q][k];
+    }
     ex[q] = wb + inc[q] - own[q];
+    agg[q] = tb;
   }
+  if (threadIdx.x == 0) scan_publish(&tiles[c], agg, c == 0 ? 2ull : 1ull);
+  if (wid == 0) {
+    long long e[4] = {0, 0, 0, 0};
+    if (c > 0) {
+      scan_lookback(tiles, c, e, &tot->status);
+      if (lane == 0) {
+        long long incl[4];
+        for (int q = 0; q < 4; ++q) incl[q] = e[q] + agg[q];
+        scan_publish(&tiles[c], incl, 2ull);
+      }
+    }
+    if (lane == 0)
+      for (int q = 0; q < 4; ++q) s_ex[q] = e[q];
+  }
+  __syncthreads();
+  for (int q = 0; q < 4; ++q) ex[q] += s_ex[q];
   for (int i = 0; i < per; ++i) {
     const long long r = beg + threadIdx.x * per + i;
     if (r < R)
       for (int q = 0; q < 4; ++q) prefix[4 * r + q] = ex[q];
-    ex[0] += c[i].x; ex[1] += c[i].y; ex[2] += c[i].w; ex[3] += c[i].z;
+    ex[0] += cv[i].x; ex[1] += cv[i].y; ex[2] += cv[i].w; ex[3] += cv[i].z;
   }
-  if (threadIdx.x == 255)
-    for (int q = 0; q < 4; ++q) chunk[4 * blockIdx.x + q] = ex[q];
-}
-
-__global__ void k_scan_top(long long* __restrict__ chunk, int nchunks, MeshTotals* __restrict__ tot) {
-  pdl_enter();
-  __shared__ long long sw[4][32];
-  long long carry[4] = {0, 0, 0, 0};
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int base = 0; base < nchunks; base += blockDim.x) {
-    const int c = base + threadIdx.x;
-    long long v[4] = {0, 0, 0, 0};
-    if (c < nchunks)
-      for (int q = 0; q < 4; ++q) v[q] = chunk[4 * c + q];
-    long long inc[4] = {v[0], v[1], v[2], v[3]};
-    for (int off = 1; off < 32; off <<= 1)
-      for (int q = 0; q < 4; ++q) {
-        const long long o = __shfl_up_sync(0xffffffffu, inc[q], off);
-        if (lane >= off) inc[q] += o;
-      }
-    if (lane == 31)
-      for (int q = 0; q < 4; ++q) sw[q][wid] = inc[q];
-    __syncthreads();
-    for (int q = 0; q < 4; ++q) {
-      long long wb = 0, bt = 0;
-      for (int k = 0; k < nw; ++k) {
-        if (k < wid) wb += sw[q][k];
-        bt += sw[q][k];
-      }
-      if (c < nchunks) chunk[4 * c + q] = carry[q] + wb + inc[q] - v[q];
-      carry[q] += bt;
-    }
-    __syncthreads();
+  if (c == nchunks - 1 && threadIdx.x == 0) {
+    tot->nv = s_ex[0] + agg[0];
+    tot->nt = s_ex[1] + agg[1];
+    tot->na = s_ex[2] + agg[2];
+    tot->nvox = s_ex[3] + agg[3];
   }
-  if (threadIdx.x == 0) {
-    tot->nv = carry[0];
-    tot->nt = carry[1];
-    tot->na = carry[2];
-    tot->nvox = carry[3];
-  }
-}
-
-// q: 0 vertices, 1 triangles, 2 active cubes, 3 inside voxels
-__device__ __forceinline__ long long row_base(const long long* prefix, const long long* chunk, long long r, int q) {
-  return prefix[4 * r + q] + chunk[4 * (r / kScanChunk) + q];
-}
-
-// Per-ROI ranges of the batch's vertex, triangle and cube ids (one thread per ROI).
-__global__ void k_roi_ranges(const Roi* __restrict__ rois, int n, const long long* __restrict__ prefix,
-                             const long long* __restrict__ chunk, const MeshTotals* __restrict__ tot,
-                             RoiOut* __restrict__ out) {
-  pdl_enter();
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  // the last block to finish: id ranges of every ROI
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&tick[1], 1u) == (unsigned int)nchunks - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const Roi& r = rois[i];
     const bool last = i == n - 1;
     const long long e = r.row0 + r.R;
     RoiOut o = out[i];
-    o.v0 = row_base(prefix, chunk, r.row0, 0);
-    o.t0 = row_base(prefix, chunk, r.row0, 1);
-    o.c0 = row_base(prefix, chunk, r.row0, 2);
-    const long long x0 = row_base(prefix, chunk, r.row0, 3);
-    o.nv = (last ? tot->nv : row_base(prefix, chunk, e, 0)) - o.v0;
-    o.nt = (last ? tot->nt : row_base(prefix, chunk, e, 1)) - o.t0;
-    o.na = (last ? tot->na : row_base(prefix, chunk, e, 2)) - o.c0;
-    o.nvox = (last ? tot->nvox : row_base(prefix, chunk, e, 3)) - x0;
+    o.v0 = __ldcg(&prefix[4 * r.row0]);
+    o.t0 = __ldcg(&prefix[4 * r.row0 + 1]);
+    o.c0 = __ldcg(&prefix[4 * r.row0 + 2]);
+    const long long x0 = __ldcg(&prefix[4 * r.row0 + 3]);
+    o.nv = (last ? __ldcg(&tot->nv) : __ldcg(&prefix[4 * e])) - o.v0;
+    o.nt = (last ? __ldcg(&tot->nt) : __ldcg(&prefix[4 * e + 1])) - o.t0;
+    o.na = (last ? __ldcg(&tot->na) : __ldcg(&prefix[4 * e + 2])) - o.c0;
+    o.nvox = (last ? __ldcg(&tot->nvox) : __ldcg(&prefix[4 * e + 3])) - x0;
     out[i] = o;
   }
+}
+
+// q: 0 vertices, 1 triangles, 2 active cubes, 3 inside voxels (global exclusive prefixes)
+__device__ __forceinline__ long long row_base(const long long* prefix, const long long* chunk, long long r, int q) {
+  (void)chunk;
+  return prefix[4 * r + q];
 }
 
 // ---- triangulation choice -----------------------------------------------------------
@@ -794,30 +791,32 @@ __global__ void __launch_bounds__(kCubeThreads) k_cubes(const uint32_t* __restri
 }
 
 // ---- binary masks: vertices and triangles of the words with surface ----------------
-// One lane per listed word (any order: the row bases and the row-local word
-// prefixes fix every id).  Each lane loads its word's cube rows and the
-// crossing masks and vertex prefixes of the four owner rows (y, z), (y+1, z),
-// (y, z+1), (y+1, z+1) into shared memory (one array per quantity, so lanes
-// hit distinct banks), plus the bit-0 crossings and prefixes of the next word
-// for cubes at bit 31.  The warp then lists the crossing positions and the
-// active cubes of its 32 words and works through each list 32 entries at a
-// time, every lane taking one entry, so a word with a long run of surface is
-// shared by the whole warp.  A vertex id is its row base + word prefix + rank
-// in the word; a cube's triangle ids are its word's base + the triangles of
-// the word's earlier cubes (a prefix over the cube's run in the list plus a
-// per-word carry between rounds).
+// Warps take chunks of 32 listed words from a ticket (any order: the row bases
+// and the row-local word prefixes fix every id), one word per lane.  Each lane
+// loads its word's cube rows and the crossing masks and vertex prefixes of the
+// four owner rows (y, z), (y+1, z), (y, z+1), (y+1, z+1) into shared memory
+// (one array per quantity, so lanes hit distinct banks), plus the bit-0
+// crossings and prefixes of the next word for cubes at bit 31.  The warp then
+// lists the crossing positions and the active cubes of its 32 words and works
+// through each list 32 entries at a time, every lane taking one entry, so a
+// word with a long run of surface is shared by the whole warp.  A vertex id is
+// its row base + word prefix + rank in the word.  A cube's twelve edge ids
+// come branch-free from the owner rows' prefixes at x and x + 1; its triangle
+// ids are its word's base + the triangles of the word's earlier cubes (a
+// prefix over the cube's run in the list plus a per-word carry between rounds).
 constexpr int kEmitThreads = 128;
 constexpr int kEmitWarps = kEmitThreads / 32;
-constexpr int kEmitBlocksPerSM = 6;  // 35 KB of shared memory per block
-constexpr int kListCap = 32 * 33;  // 32 words x (32 bits + the x = -1 entry)
+constexpr int kEmitBlocksPerSM = 5;  // 39 KB of shared memory per block
+constexpr int kListCap = 32 * 33;   // 32 words x (32 bits + the x = -1 entry)
 
 struct __align__(16) EmitShared {
   uint32_t cw[8][32];  // per lane: rows (y,z) (y+1,z) (y,z+1) (y+1,z+1) at x and x + 1: a, as, b, bs, c, cs, e, es
   int4 own[4][32];     // per owner row, per lane: ex, ey, ez, row-local vertex prefix of the word
   int onx[4][32];      // per owner row: next word's prefix << 2 | ey bit 0 << 1 | ex bit 0
-  long long vb[4][32]; // first vertex id of the owner rows
+  int vb[4][32];       // first vertex id of the owner rows
   long long tb[32];    // first triangle id of the word's cubes
   int y[32], z[32], wd[32], roi[32], tab[32], tcar[32];
+  int vid[12][32];     // edge vertex ids of the cube each lane is working on
   unsigned short list[kListCap];
 };
 
@@ -846,11 +845,10 @@ __global__ void __launch_bounds__(kEmitThreads, kEmitBlocksPerSM)
   __shared__ EmitShared sh[kEmitWarps];
   __shared__ unsigned int s_hist[kEmitWarps][256];  // case counts of the warp's current ROI
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   EmitShared& S = sh[wid];
   unsigned int* hist = s_hist[wid];
   const long long nlist = min(tot->nwords, wlist_cap);
+  const long long nchunk = (nlist + 31) / 32;
   unsigned int err = 0;
   // volume sum and case counts of one ROI (tag) stay in the warp until the ROI changes
   int tag = -1;
@@ -871,8 +869,12 @@ __global__ void __launch_bounds__(kEmitThreads, kEmitBlocksPerSM)
     vacc = 0;
     __syncwarp();
   };
-  for (long long k0 = warp * 32; k0 < nlist; k0 += nwarps * 32) {
-    const long long k = k0 + lane;
+  while (true) {
+    unsigned long long ch = 0;
+    if (lane == 0) ch = atomicAdd(&tot->emit_ticket, 1ull);
+    ch = __shfl_sync(0xffffffffu, ch, 0);
+    if ((long long)ch >= nchunk) break;  // warp-uniform
+    const long long k = (long long)ch * 32 + lane;
     const bool valid = k < nlist;
     uint32_t u = 0, act = 0;
     bool m1v = false;
@@ -915,10 +917,10 @@ __global__ void __launch_bounds__(kEmitThreads, kEmitBlocksPerSM)
                (int)((((en2 ^ hn) & 1u) << 1) | ((en2 ^ (en2 >> 1)) & 1u));
         }
         S.onx[0][lane] = o0; S.onx[1][lane] = o1; S.onx[2][lane] = o2; S.onx[3][lane] = o3;
-        S.vb[0][lane] = row_base(prefix, chunk, g, 0);
-        S.vb[1][lane] = oky ? row_base(prefix, chunk, g + 1, 0) : 0;
-        S.vb[2][lane] = okz ? row_base(prefix, chunk, g + r.ny + 1, 0) : 0;
-        S.vb[3][lane] = oky && okz ? row_base(prefix, chunk, g + r.ny + 2, 0) : 0;
+        S.vb[0][lane] = (int)row_base(prefix, chunk, g, 0);
+        S.vb[1][lane] = oky ? (int)row_base(prefix, chunk, g + 1, 0) : 0;
+        S.vb[2][lane] = okz ? (int)row_base(prefix, chunk, g + r.ny + 1, 0) : 0;
+        S.vb[3][lane] = oky && okz ? (int)row_base(prefix, chunk, g + r.ny + 2, 0) : 0;
         S.tb[lane] = row_base(prefix, chunk, g, 1) + (w == 0 ? 0 : tpre[wrow + w]);
         u = (a ^ as) | (a ^ b) | (a ^ c);
         act = (a | as | b | bs | c | cs | e | es) & ~(a & as & b & bs & c & cs & e & es);
@@ -929,7 +931,6 @@ __global__ void __launch_bounds__(kEmitThreads, kEmitBlocksPerSM)
       S.cw[4][lane] = c; S.cw[5][lane] = cs; S.cw[6][lane] = e; S.cw[7][lane] = es;
       S.y[lane] = y; S.z[lane] = z; S.wd[lane] = w; S.roi[lane] = roi; S.tab[lane] = r.tab; S.tcar[lane] = 0;
     }
-
     {
       const int t0 = __shfl_sync(0xffffffffu, S.roi[0], 0);  // lane 0's entry is always valid
       if (t0 != tag) {
@@ -1010,6 +1011,39 @@ __global__ void __launch_bounds__(kEmitThreads, kEmitBlocksPerSM)
         roi = S.roi[src];
         bc = &tab[S.tab[src] * 256 + cs];
         ntri = bc->ntri;
+        // owner-row prefixes and crossings at x (cx = 0) and x + 1 (cx = 1)
+        int p0[4], p1[4];
+        unsigned int x0[4], y0[4], x1[4], y1[4];
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const int4 ow = S.own[kk][src];
+          const uint32_t ex = (uint32_t)ow.x, ey = (uint32_t)ow.y, ez = (uint32_t)ow.z;
+          if (bit == 32) {  // x = -1: the row's first vertex; x + 1 = 0: bit 0 of word 0
+            p0[kk] = 0; x0[kk] = 0u; y0[kk] = 0u;
+            p1[kk] = ow.w; x1[kk] = ex & 1u; y1[kk] = ey & 1u;
+          } else {
+            const uint32_t low = (1u << bit) - 1u;
+            p0[kk] = ow.w + __popc(ex & low) + __popc(ey & low) + __popc(ez & low);
+            x0[kk] = (ex >> bit) & 1u; y0[kk] = (ey >> bit) & 1u;
+            if (bit == 31) {
+              const int nx = S.onx[kk][src];
+              p1[kk] = nx >> 2; x1[kk] = (unsigned int)(nx & 1); y1[kk] = (unsigned int)((nx >> 1) & 1);
+            } else {
+              p1[kk] = p0[kk] + (int)(x0[kk] + y0[kk] + ((ez >> bit) & 1u));
+              x1[kk] = (ex >> (bit + 1)) & 1u; y1[kk] = (ey >> (bit + 1)) & 1u;
+            }
+          }
+        }
+#pragma unroll
+        for (int ed = 0; ed < 12; ++ed) {
+          const int corner = (int)((kEdgeCorner >> (3 * ed)) & 7ull), ax = (int)((kEdgeAxis >> (2 * ed)) & 3u);
+          const int kk = ((corner >> 1) & 1) + 2 * (corner >> 2);
+          const bool hi = corner & 1;
+          int rank = hi ? p1[kk] : p0[kk];
+          if (ax >= 1) rank += (int)(hi ? x1[kk] : x0[kk]);
+          if (ax >= 2) rank += (int)(hi ? y1[kk] : y0[kk]);
+          S.vid[ed][lane] = S.vb[kk][src] + rank;
+        }
       }
       // triangle ids: the word's base + its triangles already written + the
       // triangles of the word's earlier cubes in this round (runs of equal src)
@@ -1020,47 +1054,22 @@ __global__ void __launch_bounds__(kEmitThreads, kEmitBlocksPerSM)
       const int seglast = 31 - __clz(peers);
       long long vsum = 0;
       if (on) {
-        const int w = S.wd[src];
-        const int x = bit == 32 ? -1 : 32 * w + bit;
         const unsigned long long t4 = bc->tri4;
         long long tid = S.tb[src] + S.tcar[src] + (tex - seg0);
         for (int t = 0; t < ntri; ++t, ++tid) {
-          int vid[3];
-#pragma unroll
-          for (int kk = 0; kk < 3; ++kk) {
-            const int ed = (int)((t4 >> (12 * t + 4 * kk)) & 15ull);
-            const int corner = (int)((kEdgeCorner >> (3 * ed)) & 7ull), ax = (int)((kEdgeAxis >> (2 * ed)) & 3u);
-            const int orow = ((corner >> 1) & 1) + 2 * (corner >> 2);
-            const int xo = x + (corner & 1);
-            int rank = 0;  // owner x = -1: the row's first vertex
-            if (xo >= 0) {
-              if ((xo >> 5) == w) {
-                const int4 ow = S.own[orow][src];
-                const int bo = xo & 31;
-                const uint32_t low = (1u << bo) - 1u;
-                rank = ow.w + __popc((uint32_t)ow.x & low) + __popc((uint32_t)ow.y & low) +
-                       __popc((uint32_t)ow.z & low);
-                if (ax >= 1) rank += ((uint32_t)ow.x >> bo) & 1u;
-                if (ax >= 2) rank += ((uint32_t)ow.y >> bo) & 1u;
-              } else {  // bit 0 of the next word
-                const int on2 = S.onx[orow][src];
-                rank = on2 >> 2;
-                if (ax >= 1) rank += on2 & 1;
-                if (ax >= 2) rank += (on2 >> 1) & 1;
-              }
-            }
-            vid[kk] = (int)(S.vb[orow][src] + rank);
-          }
+          const int e0 = (int)((t4 >> (12 * t)) & 15ull), e1 = (int)((t4 >> (12 * t + 4)) & 15ull),
+                    e2 = (int)((t4 >> (12 * t + 8)) & 15ull);
           if (tid < tcap) {
-            tri[3 * tid] = vid[0];
-            tri[3 * tid + 1] = vid[1];
-            tri[3 * tid + 2] = vid[2];
+            tri[3 * tid] = S.vid[e0][lane];
+            tri[3 * tid + 1] = S.vid[e1][lane];
+            tri[3 * tid + 2] = S.vid[e2][lane];
           } else {
             err |= DEV_ERR_TCAP;
           }
         }
         // exact volume in half-voxel units relative to the padded-box centre
         const Roi& r = rois[roi];
+        const int x = bit == 32 ? -1 : 32 * S.wd[src] + bit;
         const long long ox = 2LL * x - (r.nx - 1), oy = 2LL * S.y[src] - (r.ny - 1),
                         oz = 2LL * S.z[src] - (r.nz - 1);
         vsum = ox * bc->nsum[0] + oy * bc->nsum[1] + oz * bc->nsum[2] + bc->tsum;
@@ -1148,7 +1157,8 @@ rad_status mesh_count(const MeshBatch& b, MeshScratch& s, MeshTotals* tot, RoiOu
   RAD_TRY(s.tpre.reserve(sizeof(int) * b.wpre));
   RAD_TRY(s.wlist.reserve(sizeof(int2) * b.wpre));
   RAD_TRY(s.prefix.reserve(sizeof(long long) * 4 * b.rows));
-  RAD_TRY(s.chunk.reserve(sizeof(long long) * 4 * nchunks));
+  const size_t tiles_bytes = sizeof(ScanTile<4>) * nchunks, scan_bytes = tiles_bytes + 2 * sizeof(unsigned int);
+  RAD_TRY(s.chunk.reserve(scan_bytes));  // look-back state of the row scan and its two tickets
   RAD_TRY(s.hist.reserve(sizeof(unsigned long long) * 256 * b.n));
   RAD_TRY(s.partial.reserve(sizeof(double) * 2 * num_sms() * kCubeBlocksPerSM));
   RAD_CUDA(cudaMemsetAsync(tot, 0, sizeof(MeshTotals), st));
@@ -1164,11 +1174,10 @@ rad_status mesh_count(const MeshBatch& b, MeshScratch& s, MeshTotals* tot, RoiOu
   const int rblocks = wave_grid(k_count, kCountThreads, (warps_needed + 7) / 8);
   RAD_LAUNCH("mc_count", k_count, rblocks, kCountThreads, 0, st, s.bits.as<uint32_t>(), b.rois, b.n, b.rows, b.L, b.Wc,
              s.counts.as<int4>(), s.wpre.as<int>(), s.tpre.as<int>(), s.wlist.as<int2>(), b.wpre, tot);
-  RAD_LAUNCH("mc_scan_chunks", k_scan_chunks, (int)nchunks, 256, 0, st, s.counts.as<int4>(), b.rows,
-             s.prefix.as<long long>(), s.chunk.as<long long>());
-  RAD_LAUNCH("mc_scan_top", k_scan_top, 1, 1024, 0, st, s.chunk.as<long long>(), (int)nchunks, tot);
-  RAD_LAUNCH("mc_roi_ranges", k_roi_ranges, (b.n + 255) / 256, 256, 0, st, b.rois, b.n, s.prefix.as<long long>(),
-             s.chunk.as<long long>(), tot, out);
+  RAD_CUDA(cudaMemsetAsync(s.chunk.p, 0, scan_bytes, st));
+  RAD_LAUNCH("mc_scan_rows", k_scan_rows, (int)nchunks, 256, 0, st, s.counts.as<int4>(), b.rows, (int)nchunks,
+             s.prefix.as<long long>(), s.chunk.as<ScanTile<4>>(), (unsigned int*)(s.chunk.as<char>() + tiles_bytes),
+             tot, b.rois, b.n, out);
   return RAD_OK;
 }
 

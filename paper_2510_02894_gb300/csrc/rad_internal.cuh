@@ -67,6 +67,59 @@ cudaError_t launch_kernel(void (*k)(KArgs...), dim3 grid, dim3 block, size_t sme
     if (_le != cudaSuccess) return ::rad::cuda_fail(_le, name, __FILE__, __LINE__);                \
   } while (0)
 
+// ---- single-pass scans (decoupled look-back) ------------------------------------
+// Chunk c of a scan publishes its aggregate (flag 1) as soon as it has it and
+// its inclusive prefix (flag 2) once it has looked back over its predecessors.
+// Each quantity is one 64-bit word, flag << 62 | value, written and read whole,
+// so no fence is needed between a value and its flag.  Chunks take their index
+// from a ticket, so every chunk a block waits for is already running and
+// publishes without waiting itself; only aggregates are waited for.  Every
+// wait is bounded: after kScanSpinLimit polls the chunk is counted as zero and
+// DEV_ERR_TIMEOUT is raised (the result is then reported as an error by the
+// host, never used).
+template <int Q>
+struct __align__(16) ScanTile {
+  unsigned long long w[Q];
+};
+
+constexpr unsigned int kScanSpinLimit = 1u << 20;
+constexpr unsigned long long kScanValue = (1ull << 62) - 1ull;
+
+// One thread: publish values (flag 1: aggregate, flag 2: inclusive prefix).
+template <int Q>
+__device__ __forceinline__ void scan_publish(ScanTile<Q>* t, const long long* v, unsigned long long flag) {
+  for (int q = 0; q < Q; ++q)
+    *(volatile unsigned long long*)&t->w[q] = (flag << 62) | ((unsigned long long)v[q] & kScanValue);
+}
+
+// One full warp: the exclusive prefix of chunk c > 0 (the same in every lane).
+template <int Q>
+__device__ void scan_lookback(ScanTile<Q>* tiles, int c, long long* excl, unsigned int* status) {
+  const int lane = threadIdx.x & 31;
+  for (int q = 0; q < Q; ++q) {
+    excl[q] = 0;
+    for (int p = c - 1; p >= 0; p -= 32) {
+      const int k = p - lane;  // lane l looks at chunk p - l
+      unsigned long long x = 0;
+      if (k >= 0) {
+        x = *(volatile unsigned long long*)&tiles[k].w[q];
+        for (unsigned int n = 0; (x >> 62) == 0 && n < kScanSpinLimit; ++n) {
+          __nanosleep(32);
+          x = *(volatile unsigned long long*)&tiles[k].w[q];
+        }
+        if ((x >> 62) == 0) atomicOr(status, 1u << 4);  // DEV_ERR_TIMEOUT
+      }
+      // the nearest predecessor with an inclusive prefix ends the look-back
+      const unsigned int incl = __ballot_sync(0xffffffffu, k >= 0 && (x >> 62) == 2);
+      const int stop = incl ? __ffs(incl) - 1 : 31;
+      long long v = (k >= 0 && lane <= stop) ? (long long)(x & kScanValue) : 0;
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+      excl[q] += v;
+      if (incl) break;  // chunk 0 publishes its inclusive prefix at once, so this always ends
+    }
+  }
+}
+
 // First statement of every kernel: wait for the previous kernel in the stream
 // (a no-op without a programmatic dependency), then let the next one be
 // scheduled.
@@ -110,6 +163,7 @@ enum : uint32_t {
   DEV_ERR_INTERNAL = 1u << 5, // consistency check failed
   DEV_ERR_PROBCAP = 1u << 6,  // problem/tile list too small
 };
+static_assert(DEV_ERR_TIMEOUT == (1u << 4), "scan_lookback raises this bit");
 
 // ---- marching cubes -----------------------------------------------------------
 // One region of interest of a batch (host-computed, uploaded as a table).
@@ -134,6 +188,7 @@ struct RoiOut {
 struct MeshTotals {  // batch-wide counts and status of one marching-cubes pass
   long long nv, nt, nvox, na;
   long long nwords;        // words with surface (binary masks: the emit kernel's work list)
+  unsigned long long emit_ticket;  // next chunk of the word list
   unsigned int status;
   unsigned int done_ctas;  // last-CTA ticket of the soft cube kernel
 };
