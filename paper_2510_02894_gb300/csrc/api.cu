@@ -417,7 +417,6 @@ static rad_status enqueue_mesh(Work& w, cudaStream_t st, bool count) {
 
 static rad_status enqueue_shape(Work& w, cudaStream_t st) {
   ResultBlock* dr = w.dres();
-  RAD_CUDA(cudaMemsetAsync(&dr->stats, 0, sizeof(DiamStats), st));
   RAD_TRY(diam_run(w.mb.n, w.rd_dev.as<RoiDiam>(), w.dro(), &dr->tot.nv, w.vcap, w.nkeys, w.nplanes, !w.soft,
                    w.idx2.as<int16_t>(), w.soft ? w.vt.as<double>() : nullptr, w.ds, w.dout.as<DiamOut>(),
                    &dr->stats, st));
@@ -596,6 +595,13 @@ rad_status check_geometry(const int64_t dims[3], const double spacing[3]) {
       set_error("spacing[%d] = %g must be finite and > 0", k, spacing[k]);
       return RAD_ERR_INVALID_ARG;
     }
+  }
+  // the packed grid of one mask is indexed with 32-bit arithmetic
+  const long long words = (dims[1] + 3) * (dims[2] + 3) * ((dims[0] + 31) / 32);
+  if (words >= (1LL << 31)) {
+    set_error("mask of %lld x %lld x %lld voxels is too large (%lld packed words >= 2^31)", (long long)dims[0],
+              (long long)dims[1], (long long)dims[2], words);
+    return RAD_ERR_INVALID_ARG;
   }
   return RAD_OK;
 }

@@ -935,8 +935,9 @@ __global__ void k_tiebreak(const int* __restrict__ ids, const int16_t* __restric
   }
 }
 
-__global__ void k_diam_init(DiamOut* __restrict__ out, int n) {
+__global__ void k_diam_init(DiamOut* __restrict__ out, int n, ZeroSet zs) {
   pdl_enter();
+  zero_ranges(zs);  // counters, statistics, key histogram and cursors, scan state
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
     for (int q = 0; q < 4; ++q) {
       out[i].d2[q] = 0ull;
@@ -1091,12 +1092,14 @@ rad_status diam_run(int n, const RoiDiam* rd, const RoiOut* ro, const long long*
   Cand* cand = carve<Cand>(cur, p.cand_cap);
 
   const int sms = num_sms();
-  RAD_CUDA(cudaMemsetAsync(hist, 0, sizeof(int) * K1, st));
-  RAD_CUDA(cudaMemsetAsync(cursor, 0, sizeof(int) * K1, st));
-  RAD_CUDA(cudaMemsetAsync(cnt, 0, sizeof(Counters), st));
-  RAD_LAUNCH("diam_init", k_diam_init, std::max(1, std::min((n + 255) / 256, sms * 4)), 256, 0, st, out, n);
+  ZeroSet zs{};
+  zero_add(zs, hist, sizeof(int) * K1);      // carved in 256-byte units: whole words stay inside
+  zero_add(zs, cursor, sizeof(int) * K1);
+  zero_add(zs, cnt, sizeof(Counters));
+  zero_add(zs, scan_state, sizeof(ScanTile<1>) * nparts + 16);
+  zero_add(zs, stats, sizeof(DiamStats));
+  RAD_LAUNCH("diam_init", k_diam_init, wave_grid(k_diam_init, 256, (K1 + 255) / 256), 256, 0, st, out, n, zs);
   RAD_LAUNCH("diam_hist", k_hist, wave_grid(k_hist, 256, (nv + 255) / 256), 256, 0, st, idx2, nv_dev, rd, ro, p, hist);
-  RAD_CUDA(cudaMemsetAsync(scan_state, 0, sizeof(ScanTile<1>) * nparts + 16, st));
   RAD_LAUNCH("diam_scan", k_xscan, (int)nparts, kScanThreads, 0, st, hist, K1, (int)nparts, offs, stiles, stick,
              &cnt->status);
   RAD_LAUNCH("diam_scatter", k_scatter, wave_grid(k_scatter, 256, (nv + 255) / 256), 256, 0, st, idx2, vt, nv_dev, rd,

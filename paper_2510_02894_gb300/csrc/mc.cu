@@ -93,15 +93,20 @@ __device__ __forceinline__ uint32_t nz4(uint32_t v) {
 
 // One thread per bitset word of the whole batch (padding rows included).
 template <bool SOFT>
-__global__ void k_pack(const Roi* __restrict__ rois, int n, long long total, uint32_t* __restrict__ bits) {
+__global__ void k_pack(const Roi* __restrict__ rois, int n, long long total, uint32_t* __restrict__ bits,
+                       ZeroSet zs) {
   pdl_enter();
+  zero_ranges(zs);  // the pass's counters, per-ROI results and scan state
   for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
        id += (long long)gridDim.x * blockDim.x) {
     const Roi& r = rois[n == 1 ? 0 : roi_of_word(rois, n, id)];
-    const long long local = id - r.word0;
-    const int w = (int)(local % r.W);
-    const long long br = local / r.W;
-    const int y = (int)(br % r.BY) - 1, z = (int)(br / r.BY) - 1;
+    // one ROI's words number BY * BZ * W < 2^31 (checked on the host), so the
+    // index arithmetic is 32-bit
+    const unsigned int local = (unsigned int)(id - r.word0);
+    const unsigned int br = local / (unsigned int)r.W;
+    const int w = (int)(local - br * (unsigned int)r.W);
+    const unsigned int zz = br / (unsigned int)r.BY;
+    const int y = (int)(br - zz * (unsigned int)r.BY) - 1, z = (int)zz - 1;
     uint32_t word = 0;
     if (y >= 0 && y < r.ny && z >= 0 && z < r.nz) {
       const int x0 = w * 32;
@@ -1161,20 +1166,21 @@ rad_status mesh_count(const MeshBatch& b, MeshScratch& s, MeshTotals* tot, RoiOu
   RAD_TRY(s.chunk.reserve(scan_bytes));  // look-back state of the row scan and its two tickets
   RAD_TRY(s.hist.reserve(sizeof(unsigned long long) * 256 * b.n));
   RAD_TRY(s.partial.reserve(sizeof(double) * 2 * num_sms() * kCubeBlocksPerSM));
-  RAD_CUDA(cudaMemsetAsync(tot, 0, sizeof(MeshTotals), st));
-  RAD_CUDA(cudaMemsetAsync(out, 0, sizeof(RoiOut) * b.n, st));
-  RAD_CUDA(cudaMemsetAsync(s.hist.p, 0, sizeof(unsigned long long) * 256 * b.n, st));
+  ZeroSet zs{};
+  zero_add(zs, tot, sizeof(MeshTotals));
+  zero_add(zs, out, sizeof(RoiOut) * b.n);
+  zero_add(zs, s.hist.p, sizeof(unsigned long long) * 256 * b.n);
+  zero_add(zs, s.chunk.p, scan_bytes);
   const int sms = num_sms();
   const int pack_blocks = wave_grid(k_pack<false>, 256, (b.words + 255) / 256);
   if (b.soft)
-    RAD_LAUNCH("mc_pack_f32", k_pack<true>, pack_blocks, 256, 0, st, b.rois, b.n, b.words, s.bits.as<uint32_t>());
+    RAD_LAUNCH("mc_pack_f32", k_pack<true>, pack_blocks, 256, 0, st, b.rois, b.n, b.words, s.bits.as<uint32_t>(), zs);
   else
-    RAD_LAUNCH("mc_pack_u8", k_pack<false>, pack_blocks, 256, 0, st, b.rois, b.n, b.words, s.bits.as<uint32_t>());
+    RAD_LAUNCH("mc_pack_u8", k_pack<false>, pack_blocks, 256, 0, st, b.rois, b.n, b.words, s.bits.as<uint32_t>(), zs);
   const long long warps_needed = (b.rows + (32 / b.L) - 1) / (32 / b.L);
   const int rblocks = wave_grid(k_count, kCountThreads, (warps_needed + 7) / 8);
   RAD_LAUNCH("mc_count", k_count, rblocks, kCountThreads, 0, st, s.bits.as<uint32_t>(), b.rois, b.n, b.rows, b.L, b.Wc,
              s.counts.as<int4>(), s.wpre.as<int>(), s.tpre.as<int>(), s.wlist.as<int2>(), b.wpre, tot);
-  RAD_CUDA(cudaMemsetAsync(s.chunk.p, 0, scan_bytes, st));
   RAD_LAUNCH("mc_scan_rows", k_scan_rows, (int)nchunks, 256, 0, st, s.counts.as<int4>(), b.rows, (int)nchunks,
              s.prefix.as<long long>(), s.chunk.as<ScanTile<4>>(), (unsigned int*)(s.chunk.as<char>() + tiles_bytes),
              tot, b.rois, b.n, out);

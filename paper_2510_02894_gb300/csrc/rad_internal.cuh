@@ -120,6 +120,28 @@ __device__ void scan_lookback(ScanTile<Q>* tiles, int c, long long* excl, unsign
   }
 }
 
+// Byte ranges that the first kernel of a stage zeroes (instead of memset
+// nodes between kernels): 8-byte aligned, lengths rounded up to whole words
+// inside their allocations.
+struct ZeroSet {
+  unsigned long long* p[6];
+  long long words[6];
+  int count;
+};
+
+inline void zero_add(ZeroSet& z, void* p, size_t bytes) {
+  z.p[z.count] = static_cast<unsigned long long*>(p);
+  z.words[z.count] = (long long)((bytes + 7) / 8);
+  ++z.count;
+}
+
+__device__ __forceinline__ void zero_ranges(const ZeroSet& z) {
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long nth = (long long)gridDim.x * blockDim.x;
+  for (int k = 0; k < z.count; ++k)
+    for (long long i = tid; i < z.words[k]; i += nth) z.p[k][i] = 0ull;
+}
+
 // First statement of every kernel: wait for the previous kernel in the stream
 // (a no-op without a programmatic dependency), then let the next one be
 // scheduled.
