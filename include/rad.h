@@ -180,6 +180,18 @@ rad_status rad_soft_backward(const float* prob_dev, const int64_t dims[3], const
                              const double gout[3], const int32_t argmax[2], double* grad_dev, rad_workspace_t** ws,
                              void* stream);
 
+/* ---- failure detection check -------------------------------------------- */
+
+/* Every device-side wait of the library (the look-back of its single-pass
+ * scans) is bounded: after about 2^20 polls it gives up, sets a status bit
+ * and the kernel returns, so a stuck wait becomes RAD_ERR_TIMEOUT on the host
+ * instead of a hung GPU.  This call exercises that path on purpose: one warp
+ * waits for a scan chunk that nothing ever publishes.  It returns
+ * RAD_ERR_TIMEOUT (the expected outcome, after well under a second) with the
+ * CUDA context still usable, or RAD_ERR_INTERNAL if the wait did not report.
+ * Synchronises `stream`. */
+rad_status rad_check_bounded_wait(void* stream);
+
 /* ---- diameters without device allocation --------------------------------- */
 
 /* The paper has no counterpart of this entry point; it exists for callers

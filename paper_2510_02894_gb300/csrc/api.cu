@@ -258,6 +258,14 @@ struct ResultBlock {  // device; copied to pinned host memory after every pass
   DiamStats stats;
 };
 
+// One warp looks back from chunk 1 at chunk 0, which never publishes: the
+// bounded wait gives up and raises DEV_ERR_TIMEOUT.
+__global__ void k_wait_probe(ScanTile<1>* tiles, unsigned int* status) {
+  pdl_enter();
+  long long e = 0;
+  scan_lookback(tiles, 1, &e, status);
+}
+
 // Features of every ROI from the mesh and diameter results (one thread per ROI).
 __global__ void k_assemble(const Roi* __restrict__ rois, const RoiOut* __restrict__ ro,
                            const DiamOut* __restrict__ dout, int n, int have_diam, rad_features_t* __restrict__ f) {
@@ -874,6 +882,25 @@ rad_status rad_soft_backward(const float* prob_dev, const int64_t dims[3], const
                        grad_dev, st));
   RAD_CUDA(cudaStreamSynchronize(st));
   return RAD_OK;
+}
+
+rad_status rad_check_bounded_wait(void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  DevBuf buf;
+  RAD_TRY(buf.reserve(sizeof(ScanTile<1>) * 2 + 16));
+  RAD_CUDA(cudaMemsetAsync(buf.p, 0, sizeof(ScanTile<1>) * 2 + 16, st));
+  unsigned int* status = reinterpret_cast<unsigned int*>(buf.as<char>() + sizeof(ScanTile<1>) * 2);
+  RAD_LAUNCH("wait_probe", rad::k_wait_probe, 1, 32, 0, st, buf.as<ScanTile<1>>(), status);
+  unsigned int h = 0;
+  RAD_CUDA(cudaMemcpyAsync(&h, status, sizeof(h), cudaMemcpyDeviceToHost, st));
+  RAD_CUDA(cudaStreamSynchronize(st));
+  buf.release();
+  if (h & DEV_ERR_TIMEOUT) {
+    set_error("bounded device wait gave up as expected (status 0x%x)", h);
+    return RAD_ERR_TIMEOUT;
+  }
+  set_error("bounded device wait did not report a timeout (status 0x%x)", h);
+  return RAD_ERR_INTERNAL;
 }
 
 rad_status rad_set_tuning(const rad_tuning_t* set, rad_tuning_t* get) {

@@ -71,7 +71,7 @@ EXPORTS = ("rad_mesh", "rad_soft_mesh", "rad_shape", "rad_shape_plain_fp64", "ra
            "rad_workspace_free", "rad_mesh_free", "rad_mesh_copy", "rad_set_tuning", "rad_profile_enable",
            "rad_profile_read", "rad_profile_reset", "rad_launch_count", "rad_status_str", "rad_last_error",
            "rad_last_call_stats", "rad_soft_forward", "rad_soft_backward", "rad_batch_create", "rad_batch_run",
-           "rad_batch_destroy")
+           "rad_batch_destroy", "rad_check_bounded_wait")
 
 
 def lib():
@@ -123,6 +123,8 @@ def lib():
         L.rad_batch_destroy.restype = None
         L.rad_last_error.argtypes = []
         L.rad_last_error.restype = ctypes.c_char_p
+        L.rad_check_bounded_wait.argtypes = [P]
+        L.rad_check_bounded_wait.restype = I
         _lib = L
     return _lib
 
@@ -301,6 +303,12 @@ class Batch:
         if _lib is not None and getattr(self, "h", None) is not None and self.h.value:
             _lib.rad_batch_destroy(self.h)
             self.h = ctypes.c_void_p(None)
+
+
+def check_bounded_wait(stream=None):
+    """Run the library's bounded device wait on a flag that nothing sets;
+    returns the status code (RAD_ERR_TIMEOUT = 4 is the expected outcome)."""
+    return int(lib().rad_check_bounded_wait(_stream(stream)))
 
 
 def set_tuning(tile=None, threads=None, ctas_per_sm=None, cell_shift=None):

@@ -202,3 +202,15 @@ def test_kernel_timing_inside_replayed_graph():
     assert prof["diam_pairs_fp32"]["launches"] == 3 and prof["diam_pairs_fp32"]["total_ms"] > 0
     assert per_call == sum(v["launches"] for v in prof.values()) / 3
     torch.zeros(8, device="cuda").sum().item()  # no CUDA error left behind
+
+
+def test_bounded_wait_reports_timeout_and_context_survives():
+    """A device wait on a flag that nothing sets gives up, is reported as
+    RAD_ERR_TIMEOUT, and the context keeps working afterwards."""
+    import time
+    t0 = time.perf_counter()
+    assert rad.check_bounded_wait() == 4  # RAD_ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 30.0
+    m = synth.ellipsoid_32(3)
+    ref, _ = oracle.features(*m)
+    assert_features(rad.extract(torch.from_numpy(m[0]).cuda(), m[1], rad.Workspace()), ref)
