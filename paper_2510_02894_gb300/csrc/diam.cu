@@ -121,6 +121,27 @@ __device__ __forceinline__ float pair_g(float4 a2, float4 b) {
   return __fmaf_rn(a2.x, b.x, g);
 }
 
+// Packed pairs of FP32 values (Blackwell f32x2 arithmetic, round to nearest
+// per element: the same results as the scalar operations).
+__device__ __forceinline__ unsigned long long pk2(float lo, float hi) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void unpk2(unsigned long long v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long add2(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b, unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
 __device__ __forceinline__ float4 expand_a(float4 a) {
   return make_float4(__fmul_rn(-2.0f, a.x), __fmul_rn(-2.0f, a.y), __fmul_rn(-2.0f, a.z), a.w);
 }
@@ -724,6 +745,7 @@ __global__ void __launch_bounds__(NT) k_pairs(const float4* __restrict__ sorted,
   constexpr int NWARP = NT / 32;
   __shared__ __align__(16) float4 sA[NWARP][2][TS];
   __shared__ __align__(16) float4 sB[NWARP][2][32];
+  __shared__ __align__(16) ulonglong2 sB2[NWARP][2][32];  // the current B, duplicated: (x,x | y,y) and (z,z | n,n)
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const long long nws = min(cnt->n_work, p.work_cap) * RA;
   const long long W = (long long)gridDim.x * NWARP;
@@ -754,19 +776,43 @@ __global__ void __launch_bounds__(NT) k_pairs(const float4* __restrict__ sorted,
     const int s = (int)(t_cur % RA);
     float m = -1.0f;
     if (!(w_cur.ub < T) && 32 * s < w_cur.blen) {
-      float4 a[RA];
+      // A entries r and r + 1 packed per coordinate; every lane duplicates its
+      // own B entry once, so one f32x2 add and three f32x2 FMAs give two pairs
+      // (the same operations, in the same order, as pair_g)
+      unsigned long long ax[RA / 2], ay[RA / 2], az[RA / 2], an[RA / 2];
 #pragma unroll
-      for (int r = 0; r < RA; ++r) a[r] = expand_a(sA[wid][buf][lane + 32 * r]);
+      for (int r = 0; r < RA; r += 2) {
+        const float4 a0 = expand_a(sA[wid][buf][lane + 32 * r]), a1 = expand_a(sA[wid][buf][lane + 32 * (r + 1)]);
+        ax[r / 2] = pk2(a0.x, a1.x); ay[r / 2] = pk2(a0.y, a1.y);
+        az[r / 2] = pk2(a0.z, a1.z); an[r / 2] = pk2(a0.w, a1.w);
+      }
+      {
+        const float4 b = sB[wid][buf][lane];
+        sB2[wid][0][lane] = make_ulonglong2(pk2(b.x, b.x), pk2(b.y, b.y));
+        sB2[wid][1][lane] = make_ulonglong2(pk2(b.z, b.z), pk2(b.w, b.w));
+      }
+      __syncwarp();
       float mx[RA];
 #pragma unroll
       for (int r = 0; r < RA; ++r) mx[r] = 0.0f;
-      const float4* sb = sB[wid][buf];
+      const ulonglong2* bxy = sB2[wid][0];
+      const ulonglong2* bzn = sB2[wid][1];
 #pragma unroll 8
       for (int j = 0; j < 32; ++j) {
-        const float4 b = sb[j];
+        const ulonglong2 p0 = bxy[j], p1 = bzn[j];
 #pragma unroll
-        for (int r = 0; r < RA; ++r) mx[r] = fmaxf(mx[r], pair_g(a[r], b));
+        for (int h = 0; h < RA / 2; ++h) {
+          unsigned long long g = add2(an[h], p1.y);
+          g = fma2(az[h], p1.x, g);
+          g = fma2(ay[h], p0.y, g);
+          g = fma2(ax[h], p0.x, g);
+          float g0, g1;
+          unpk2(g, g0, g1);
+          mx[2 * h] = fmaxf(mx[2 * h], g0);
+          mx[2 * h + 1] = fmaxf(mx[2 * h + 1], g1);
+        }
       }
+      __syncwarp();  // the duplicated B is read before the next item's staging
       m = mx[0];
 #pragma unroll
       for (int r = 1; r < RA; ++r) m = fmaxf(m, mx[r]);
