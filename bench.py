@@ -46,6 +46,25 @@ def load_peaks():
     return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def load_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu table, or None
+    when the table has no row for it or the kernel's source file changed since
+    the counters were taken (its sha256 no longer matches)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "dram_traffic_ct512.md")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        cells = [c.strip() for c in line.strip().strip("|").split("|")]
+        if len(cells) != 6 or cells[0] != kernel:
+            continue
+        src = os.path.join(ROOT, cells[2])
+        if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != cells[3]:
+            return None
+        return int(cells[4]) + int(cells[5])
+    return None
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -326,12 +345,12 @@ def main():
     if bound == "hbm":
         ach = amount / (per_launch_ms / 1e3) / 1e9
         roof.update({"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                     "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": peak_kind,
+                     "frac": ach / peaks["hbm_gbs"], "traffic": load_traffic(dom), "peak_source": peak_kind,
                      "algorithmic_bytes": amount})
     elif bound == "alu":
         ach = amount / (per_launch_ms / 1e3) / 1e12
         roof.update({"bound": "alu", "achieved": ach, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
-                     "frac": ach / fp32_peak_tflops, "traffic": None,
+                     "frac": ach / fp32_peak_tflops, "traffic": load_traffic(dom),
                      "peak_source": f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
                      "algorithmic_flops": amount})
     else:
