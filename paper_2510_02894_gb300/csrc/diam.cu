@@ -45,6 +45,7 @@
 // bound uses the difference form's monotone FP32 operations on box distances,
 // so it bounds f from above without any epsilon.  T only grows, so a pair
 // culled or left out against an earlier T is also below the final one.
+#include <atomic>
 #include <float.h>
 #include <limits.h>
 #include <math.h>
@@ -717,68 +718,112 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// One warp item: tile A and the 32-entry slice s of tile B of a work item,
-// into the warp's own shared-memory buffers.  Entries past a tile's length
-// repeat its last vertex (a real vertex, so maxima are unaffected).
+// B slices per warp unit: a unit is tile A of a work item against G
+// consecutive 32-entry slices of its tile B.  Two slices share the staging
+// and expansion of A; more would leave each warp too few units for a rising
+// T to cull the later ones (T is read when a unit is staged and again before
+// each slice).
 template <int TS>
-__device__ __forceinline__ void stage_slice(float4* sA, float4* sB, const float4* sorted, const WorkItem& w, int s) {
+__host__ __device__ constexpr int pair_slices() {
+  return 2;
+}
+
+// Dynamic shared memory of the pair kernel, per warp: tile A and the unit's
+// B slices, double buffered, plus two duplicated B slices (32 B an entry).
+template <int TS, int NT>
+constexpr size_t pair_smem_bytes() {
+  return (size_t)(NT / 32) * (2 * TS * sizeof(float4) + 2 * 32 * pair_slices<TS>() * sizeof(float4) +
+                              2 * 2 * 32 * sizeof(ulonglong2));
+}
+
+// One warp unit: tile A and the B slices s0 .. s0 + G - 1 of a work item into
+// the warp's own shared-memory buffers.  Entries past a tile's length repeat
+// its last vertex (a real vertex, so maxima are unaffected); slices wholly
+// past it are not copied.
+template <int TS, int G>
+__device__ __forceinline__ void stage_unit(float4* sA, float4* sB, const float4* sorted, const WorkItem& w, int s0) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int r = 0; r < TS / 32; ++r) cp_async16(&sA[lane + 32 * r], &sorted[w.abeg + min(lane + 32 * r, w.alen - 1)]);
-  cp_async16(&sB[lane], &sorted[w.bbeg + min(32 * s + lane, w.blen - 1)]);
+#pragma unroll
+  for (int g = 0; g < G; ++g)
+    if (32 * (s0 + g) < w.blen) cp_async16(&sB[32 * g + lane], &sorted[w.bbeg + min(32 * (s0 + g) + lane, w.blen - 1)]);
 }
 
-// Every warp works on its own over (tile pair, 32-entry B slice) warp items
-// g, g + W, g + 2W, ... (g its global warp index, W the number of warps; the
-// warps of one CTA take the slices of the same tile pair, which share tile A
-// in L1).  It stages the next item with cp.async while it evaluates the
-// current one (no block barrier anywhere), skips an item whose bound is below
-// the current T, and otherwise stores the slice maximum (lane l holds the A
-// entries l, l + 32, ...) and raises F (and T) when it beats F.
-// slicemax[warp item] < 0 marks a skipped or empty slice.
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+  float d;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+
+// Every warp works on its own over units u, u + W, u + 2W, ... (u its global
+// warp index, W the number of warps; the warps of a CTA take neighbouring
+// units, so tiles shared between them come from L1).  It stages the next
+// unit with cp.async while it evaluates the current one (no block barrier
+// anywhere) and skips a unit whose bound is below the current T.  Otherwise
+// it expands tile A once (lane l holds the A entries l, l + 32, ...), works
+// through the unit's B slices (T is read again before each, so a unit stops
+// once T passes its bound), stores each slice maximum, and raises F (and T)
+// when the unit's maximum beats F.  slicemax[slice] < 0 marks a skipped or
+// empty slice.
 template <int TS, int NT>
 __global__ void __launch_bounds__(NT) k_pairs(const float4* __restrict__ sorted, const WorkItem* __restrict__ work,
                                               Params p, const RoiDiam* __restrict__ rd, Counters* __restrict__ cnt,
                                               ProblemState* __restrict__ ps, float* __restrict__ slicemax) {
   pdl_enter();
   constexpr int RA = TS / 32;  // A entries per lane, and B slices per tile pair
+  constexpr int G = pair_slices<TS>();
+  constexpr int UPI = RA / G;  // units per work item
   constexpr int NWARP = NT / 32;
-  __shared__ __align__(16) float4 sA[NWARP][2][TS];
-  __shared__ __align__(16) float4 sB[NWARP][2][32];
-  __shared__ __align__(16) ulonglong2 sB2[NWARP][2][32];  // the current B, duplicated: (x,x | y,y) and (z,z | n,n)
+  static_assert(RA % G == 0 && RA % 2 == 0, "slices per unit");
+  extern __shared__ __align__(16) unsigned char pair_smem[];
+  float4(*sA)[2][TS] = reinterpret_cast<float4(*)[2][TS]>(pair_smem);
+  float4(*sB)[2][32 * G] = reinterpret_cast<float4(*)[2][32 * G]>(pair_smem + NWARP * 2 * TS * sizeof(float4));
+  // one slice's B, duplicated: (x,x | y,y), (z,z | n,n)
+  ulonglong2(*sB2)[2][2][32] = reinterpret_cast<ulonglong2(*)[2][2][32]>(
+      pair_smem + NWARP * 2 * (TS + 32 * G) * sizeof(float4));
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const long long nws = min(cnt->n_work, p.work_cap) * RA;
+  const long long nunits = min(cnt->n_work, p.work_cap) * UPI;
   const long long W = (long long)gridDim.x * NWARP;
   long long t_cur = (long long)blockIdx.x * NWARP + wid;
-  if (t_cur >= nws) return;  // warp-uniform
-  WorkItem w_cur = work[t_cur / RA];
-  stage_slice<TS>(sA[wid][0], sB[wid][0], sorted, w_cur, (int)(t_cur % RA));
+  if (t_cur >= nunits) return;  // warp-uniform
+  WorkItem w_cur = work[t_cur / UPI];
+  stage_unit<TS, G>(sA[wid][0], sB[wid][0], sorted, w_cur, (int)(t_cur % UPI) * G);
   cp_async_commit();
   unsigned long long ft_cur = *(volatile unsigned long long*)&ps[w_cur.problem];
   long long t_nxt = t_cur + W;
-  WorkItem w_nxt = t_nxt < nws ? work[t_nxt / RA] : w_cur;
+  WorkItem w_nxt = t_nxt < nunits ? work[t_nxt / UPI] : w_cur;
   int buf = 0;
   unsigned long long n_items = 0, n_pairs = 0;
+  // duplicate B entry `lane` of slice g into sB2[d]
+  auto dup = [&](int g, int d) {
+    const float4 b = sB[wid][buf][32 * g + lane];
+    sB2[wid][d][0][lane] = make_ulonglong2(pk2(b.x, b.x), pk2(b.y, b.y));
+    sB2[wid][d][1][lane] = make_ulonglong2(pk2(b.z, b.z), pk2(b.w, b.w));
+  };
   while (true) {
-    const bool has_next = t_nxt < nws;
+    const bool has_next = t_nxt < nunits;
     __syncwarp();  // every lane is done with the other buffer
     unsigned long long ft_nxt = ft_cur;
     if (has_next) {
-      stage_slice<TS>(sA[wid][buf ^ 1], sB[wid][buf ^ 1], sorted, w_nxt, (int)(t_nxt % RA));
+      stage_unit<TS, G>(sA[wid][buf ^ 1], sB[wid][buf ^ 1], sorted, w_nxt, (int)(t_nxt % UPI) * G);
       ft_nxt = *(volatile unsigned long long*)&ps[w_nxt.problem];
     }
     cp_async_commit();
     const long long t_nn = t_nxt + W;
-    const WorkItem w_nn = t_nn < nws ? work[t_nn / RA] : w_nxt;
-    cp_async_wait<1>();  // this lane's copies of the current item have landed
+    const WorkItem w_nn = t_nn < nunits ? work[t_nn / UPI] : w_nxt;
+    cp_async_wait<1>();  // this lane's copies of the current unit have landed
     __syncwarp();        // ... and every lane's
     const float F = __uint_as_float((unsigned int)ft_cur), T = __uint_as_float((unsigned int)(ft_cur >> 32));
-    const int s = (int)(t_cur % RA);
-    float m = -1.0f;
-    if (!(w_cur.ub < T) && 32 * s < w_cur.blen) {
-      // A entries r and r + 1 packed per coordinate; every lane duplicates its
-      // own B entry once, so one f32x2 add and three f32x2 FMAs give two pairs
-      // (the same operations, in the same order, as pair_g)
+    const long long item = t_cur / UPI;
+    const int s0 = (int)(t_cur % UPI) * G;
+    const int ns = min(G, (w_cur.blen + 31) / 32 - s0);  // non-empty slices of the unit
+    float um = -1.0f;
+    int ne = 0;  // slices evaluated
+    if (!(w_cur.ub < T) && ns > 0) {
+      // A entries r and r + 1 packed per coordinate; B duplicated, so one f32x2
+      // add and three f32x2 FMAs give two pairs (the same operations, in the
+      // same order, as pair_g)
       unsigned long long ax[RA / 2], ay[RA / 2], az[RA / 2], an[RA / 2];
 #pragma unroll
       for (int r = 0; r < RA; r += 2) {
@@ -786,47 +831,56 @@ __global__ void __launch_bounds__(NT) k_pairs(const float4* __restrict__ sorted,
         ax[r / 2] = pk2(a0.x, a1.x); ay[r / 2] = pk2(a0.y, a1.y);
         az[r / 2] = pk2(a0.z, a1.z); an[r / 2] = pk2(a0.w, a1.w);
       }
-      {
-        const float4 b = sB[wid][buf][lane];
-        sB2[wid][0][lane] = make_ulonglong2(pk2(b.x, b.x), pk2(b.y, b.y));
-        sB2[wid][1][lane] = make_ulonglong2(pk2(b.z, b.z), pk2(b.w, b.w));
-      }
+      dup(0, 0);
       __syncwarp();
-      float mx[RA];
+#pragma unroll 1
+      for (int g = 0; g < ns; ++g) {
+        // T for the next slice, read now and used after this slice's loop
+        const unsigned int tn = g + 1 < ns ? *(volatile unsigned int*)&ps[w_cur.problem].T : 0u;
+        if (g + 1 < ns) dup(g + 1, (g + 1) & 1);  // read only after the barrier below
+        const ulonglong2* bxy = sB2[wid][g & 1][0];
+        const ulonglong2* bzn = sB2[wid][g & 1][1];
+        float mx[RA];
 #pragma unroll
-      for (int r = 0; r < RA; ++r) mx[r] = 0.0f;
-      const ulonglong2* bxy = sB2[wid][0];
-      const ulonglong2* bzn = sB2[wid][1];
-#pragma unroll 8
-      for (int j = 0; j < 32; ++j) {
-        const ulonglong2 p0 = bxy[j], p1 = bzn[j];
+        for (int r = 0; r < RA; ++r) mx[r] = 0.0f;
+#pragma unroll 4
+        for (int j = 0; j < 32; j += 2) {
+          const ulonglong2 p0 = bxy[j], p1 = bzn[j], q0 = bxy[j + 1], q1 = bzn[j + 1];
 #pragma unroll
-        for (int h = 0; h < RA / 2; ++h) {
-          unsigned long long g = add2(an[h], p1.y);
-          g = fma2(az[h], p1.x, g);
-          g = fma2(ay[h], p0.y, g);
-          g = fma2(ax[h], p0.x, g);
-          float g0, g1;
-          unpk2(g, g0, g1);
-          mx[2 * h] = fmaxf(mx[2 * h], g0);
-          mx[2 * h + 1] = fmaxf(mx[2 * h + 1], g1);
+          for (int h = 0; h < RA / 2; ++h) {
+            unsigned long long g0 = add2(an[h], p1.y), g1 = add2(an[h], q1.y);
+            g0 = fma2(az[h], p1.x, g0); g1 = fma2(az[h], q1.x, g1);
+            g0 = fma2(ay[h], p0.y, g0); g1 = fma2(ay[h], q0.y, g1);
+            g0 = fma2(ax[h], p0.x, g0); g1 = fma2(ax[h], q0.x, g1);
+            float g00, g01, g10, g11;
+            unpk2(g0, g00, g01);
+            unpk2(g1, g10, g11);
+            mx[2 * h] = max3f(mx[2 * h], g00, g10);
+            mx[2 * h + 1] = max3f(mx[2 * h + 1], g01, g11);
+          }
         }
+        __syncwarp();  // slice g is read, slice g + 1's duplicate is visible
+        float m = mx[0];
+#pragma unroll
+        for (int r = 1; r < RA; ++r) m = fmaxf(m, mx[r]);
+        for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+        if (lane == 0) {
+          slicemax[item * RA + s0 + g] = m;
+          n_pairs += (unsigned long long)w_cur.alen * (unsigned long long)min(32, w_cur.blen - 32 * (s0 + g));
+        }
+        um = fmaxf(um, m);
+        ne = g + 1;
+        if (w_cur.ub < __uint_as_float(tn)) break;  // T has passed the bound: skip the unit's other slices
       }
-      __syncwarp();  // the duplicated B is read before the next item's staging
-      m = mx[0];
-#pragma unroll
-      for (int r = 1; r < RA; ++r) m = fmaxf(m, mx[r]);
-      for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
       if (lane == 0) {
-        if (m > F) {  // fire and forget: T(F) is monotone, so the largest m wins both maxima
-          atomicMax(&ps[w_cur.problem].F, __float_as_uint(m));
-          atomicMax(&ps[w_cur.problem].T, __float_as_uint(threshold(m, rd[w_cur.roi])));
+        if (um > F) {  // fire and forget: T(F) is monotone, so the largest maximum wins both
+          atomicMax(&ps[w_cur.problem].F, __float_as_uint(um));
+          atomicMax(&ps[w_cur.problem].T, __float_as_uint(threshold(um, rd[w_cur.roi])));
         }
-        n_items += s == 0;
-        n_pairs += (unsigned long long)w_cur.alen * (unsigned long long)min(32, w_cur.blen - 32 * s);
+        n_items += s0 == 0;
       }
     }
-    if (lane == 0) slicemax[t_cur] = m;
+    if (lane < G && lane >= ne) slicemax[item * RA + s0 + lane] = -1.0f;
     if (!has_next) break;
     t_cur = t_nxt;
     w_cur = w_nxt;
@@ -1017,9 +1071,20 @@ rad_status launch_pairs(const float4* sorted, const WorkItem* work, const Params
   auto kp = k_pairs<TS, NT>;
   auto kl = k_cand_list<TS>;
   auto kc = k_cand<TS>;
-  // at most one full wave: the items are dealt out to the grid's warps
-  const int pgrid = std::min(ctas, wave_grid(kp, NT, 1LL << 30));
-  RAD_LAUNCH("diam_pairs_fp32", kp, pgrid, NT, 0, st, sorted, work, p, rd, cnt, ps, slicemax);
+  constexpr size_t smem = pair_smem_bytes<TS, NT>();
+  {  // once per device; the first pass of a workspace runs eagerly, before any capture
+    static std::atomic<unsigned long long> done{0};
+    int dev = 0;
+    RAD_CUDA(cudaGetDevice(&dev));
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (!(done.load() & bit)) {
+      RAD_CUDA(cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      done.fetch_or(bit);
+    }
+  }
+  // at most one full wave: the units are dealt out to the grid's warps
+  const int pgrid = std::min(ctas, wave_grid(kp, NT, 1LL << 30, smem));
+  RAD_LAUNCH("diam_pairs_fp32", kp, pgrid, NT, smem, st, sorted, work, p, rd, cnt, ps, slicemax);
   RAD_LAUNCH("diam_cand_list", kl, wave_grid(kl, 256, num_sms() * 4), 256, 0, st, work, slicemax, p, cnt, ps, hits);
   RAD_LAUNCH("diam_pairs_cand", kc, wave_grid(kc, 256, num_sms() * 4), 256, 0, st, sorted, work, hits, p, cnt, ps,
              cand);
