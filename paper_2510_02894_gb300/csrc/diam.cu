@@ -67,7 +67,10 @@ struct Problem {
   int beg, len;
   int tile_beg;  // first tile
   int roi;
-  int q;  // result slot: 0 3D, 1 Slice, 2 Column, 3 Row
+  int q;   // result slot: 0 3D, 1 Slice, 2 Column, 3 Row
+  int nt;  // tiles
+  int pad;
+  long long chunk_end;  // one past the last seed/cull chunk of its rows; -1: past 2^31 chunks
 };
 
 struct __align__(16) Tile {
@@ -357,12 +360,15 @@ __device__ __forceinline__ long long key_offset(const long long* offs, const lon
 }
 
 // ---- 2. problems and tiles --------------------------------------------------------
-// One warp per candidate problem: the 3D problem of every ROI (items 0..n-1)
+// One lane per candidate problem: the 3D problem of every ROI (items 0..n-1)
 // and every plane of every ROI (items n..).  A problem with >= 2 vertices
 // takes a slot, and -- in one 64-bit atomic, so both ranges follow the same
 // order -- a contiguous run of tiles and of seed/cull chunks (the order of
 // problems does not affect any result).  Row i of a problem with nt tiles
-// scans tiles i..nt-1 in ceil((nt - i) / kChunk) chunks.
+// scans tiles i..nt-1 in ceil((nt - i) / kChunk) chunks.  The setup writes
+// each tile's problem slot only (into chunk0); the tile kernel, one warp per
+// tile, builds the tile record and its first chunk from the problem, so a
+// problem with thousands of tiles is not written by one warp.
 __device__ __forceinline__ int roi_of_plane(const RoiDiam* rd, int n, long long g) {
   int lo = 0, hi = n - 1;
   while (lo < hi) {
@@ -380,16 +386,17 @@ __device__ __forceinline__ long long chunks_upto(long long m) {
 }
 
 __global__ void k_setup(const RoiDiam* __restrict__ rd, Params p, const long long* __restrict__ offs,
-                        const long long* __restrict__ parts, Problem* __restrict__ probs, Tile* __restrict__ tiles,
-                        int* __restrict__ chunk0, ProblemState* __restrict__ ps, Counters* __restrict__ cnt) {
+                        const long long* __restrict__ parts, Problem* __restrict__ probs, int* __restrict__ chunk0,
+                        ProblemState* __restrict__ ps, Counters* __restrict__ cnt) {
   pdl_enter();
   const int lane = threadIdx.x & 31;
   const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   const long long items = p.n + p.nplanes;
-  for (long long base = warp * 32; base < items; base += nwarps * 32) {
-    // one lane per candidate problem
-    const long long it = base + lane;
+  for (long long r0 = 0; r0 < items; r0 += nwarps * 32) {
+    // one lane per candidate problem, dealt with a stride of the warp count,
+    // so the ROIs' 3D problems (the largest) go to different warps
+    const long long it = r0 + lane * nwarps + warp;
     int roi = 0, axis = -1;
     long long beg = 0, len = 0;
     if (it < items) {
@@ -437,7 +444,9 @@ __global__ void k_setup(const RoiDiam* __restrict__ rd, Params p, const long lon
     }
     slot0 = __shfl_sync(0xffffffffu, slot0, 0);
     old0 = __shfl_sync(0xffffffffu, old0, 0);
-    if (use) atomicAdd((unsigned long long*)&cnt->n_pairs, (unsigned long long)nt * (nt + 1) / 2);
+    unsigned long long tp = use ? (unsigned long long)nt * (nt + 1) / 2 : 0ull;
+    for (int off = 16; off > 0; off >>= 1) tp += __shfl_xor_sync(0xffffffffu, tp, off);
+    if (lane == 0) atomicAdd((unsigned long long*)&cnt->n_pairs, tp);
     const int slot = slot0 + __popc(um & ((1u << lane) - 1u));
     const unsigned long long old = old0 + (inc - add);
     const long long tb = (long long)(old & 0xffffffffull);
@@ -451,34 +460,21 @@ __global__ void k_setup(const RoiDiam* __restrict__ rd, Params p, const long lon
     if (ok) {
       Problem pr;
       pr.axis = axis; pr.beg = (int)beg; pr.len = (int)len; pr.tile_beg = (int)tb; pr.roi = roi; pr.q = q;
+      pr.nt = nt; pr.pad = 0;
+      pr.chunk_end = ovf ? -1 : cb + S;
       probs[slot] = pr;
       ProblemState z;
       z.F = 0u; z.T = 0u;
       ps[slot] = z;
     }
-    // the warp writes the tiles of each accepted problem together
+    // the warp marks the tiles of each accepted problem with its slot
     unsigned int wm = __ballot_sync(0xffffffffu, ok);
     while (wm) {
       const int src = __ffs(wm) - 1;
       wm &= wm - 1;
       const int s_slot = __shfl_sync(0xffffffffu, slot, src), s_nt = __shfl_sync(0xffffffffu, nt, src);
-      const int s_roi = __shfl_sync(0xffffffffu, roi, src), s_q = __shfl_sync(0xffffffffu, q, src);
-      const long long s_tb = __shfl_sync(0xffffffffu, tb, src), s_cb = __shfl_sync(0xffffffffu, cb, src);
-      const long long s_beg = __shfl_sync(0xffffffffu, beg, src), s_len = __shfl_sync(0xffffffffu, len, src);
-      const long long s_S = __shfl_sync(0xffffffffu, S, src);
-      const bool s_ovf = __shfl_sync(0xffffffffu, (int)ovf, src) != 0;
-      for (int t = lane; t < s_nt; t += 32) {
-        Tile tl;
-        tl.problem = s_slot;
-        tl.beg = (int)s_beg + t * p.TS;
-        tl.len = min(p.TS, (int)s_len - t * p.TS);
-        tl.tile_end = (int)s_tb + s_nt;
-        tl.roi = s_roi;
-        tl.q = s_q;
-        tl.pad0 = tl.pad1 = 0;
-        tiles[s_tb + t] = tl;
-        chunk0[s_tb + t] = s_ovf ? INT_MAX : (int)(s_cb + s_S - chunks_upto(s_nt - t));
-      }
+      const long long s_tb = __shfl_sync(0xffffffffu, tb, src);
+      for (int t = lane; t < s_nt; t += 32) chunk0[s_tb + t] = s_slot;
     }
   }
 }
@@ -492,16 +488,36 @@ __global__ void k_thresh(const RoiDiam* __restrict__ rd, const Problem* __restri
     ps[i].T = __float_as_uint(threshold(__uint_as_float(ps[i].F), rd[probs[i].roi]));
 }
 
-// One warp per tile: bounding box of its FP32 positions and its first vertex.
-__global__ void k_tile_box(const float4* __restrict__ sorted, const Tile* __restrict__ tiles, Params p,
-                           const Counters* __restrict__ cnt, float4* __restrict__ box, float4* __restrict__ rep) {
+// One warp per tile: its record and first seed/cull chunk, the bounding box
+// of its FP32 positions, and its first vertex.
+__global__ void k_tile_box(const float4* __restrict__ sorted, const Problem* __restrict__ probs, Params p,
+                           const Counters* __restrict__ cnt, Tile* __restrict__ tiles, int* __restrict__ chunk0,
+                           float4* __restrict__ box, float4* __restrict__ rep) {
   pdl_enter();
   const int nt = (int)min((long long)(cnt->alloc & 0xffffffffull), p.max_tiles);
+  const int np = (int)min((long long)cnt->n_problems, p.max_problems);
   const int lane = threadIdx.x & 31;
   const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   for (long long ti = warp; ti < nt; ti += nwarps) {
-    const Tile tl = tiles[ti];
+    const int slot = chunk0[ti];  // the problem's slot, from the setup
+    if ((unsigned int)slot >= (unsigned int)np) continue;  // warp-uniform; not reached (tiles never outrun problems)
+    const Problem pr = probs[slot];
+    const int t = (int)ti - pr.tile_beg;  // tile within its problem
+    if (t < 0 || t >= pr.nt) continue;    // warp-uniform; as above
+    Tile tl;
+    tl.problem = slot;
+    tl.beg = pr.beg + t * p.TS;
+    tl.len = min(p.TS, pr.len - t * p.TS);
+    tl.tile_end = pr.tile_beg + pr.nt;
+    tl.roi = pr.roi;
+    tl.q = pr.q;
+    tl.pad0 = tl.pad1 = 0;
+    __syncwarp();  // every lane has read the slot before lane 0 replaces it
+    if (lane == 0) {
+      tiles[ti] = tl;
+      chunk0[ti] = pr.chunk_end < 0 ? INT_MAX : (int)(pr.chunk_end - chunks_upto(pr.nt - t));
+    }
     float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
     for (int i = lane; i < tl.len; i += 32) {
       const float4 v = sorted[tl.beg + i];
@@ -1216,9 +1232,9 @@ rad_status diam_run(int n, const RoiDiam* rd, const RoiOut* ro, const long long*
   RAD_LAUNCH("diam_scatter", k_scatter, wave_grid(k_scatter, 256, (nv + 255) / 256), 256, 0, st, idx2, vt, nv_dev, rd,
              ro, p, offs, parts, cursor, sorted, ids);
   RAD_LAUNCH("diam_setup", k_setup, wave_grid(k_setup, 256, (n + nplanes + 255) / 256 + 1), 256, 0, st, rd, p, offs,
-             parts, probs, tiles, chunk0, ps, cnt);
-  RAD_LAUNCH("diam_tile_box", k_tile_box, wave_grid(k_tile_box, 256, 1LL << 30), 256, 0, st, sorted, tiles, p, cnt, box,
-             rep);
+             parts, probs, chunk0, ps, cnt);
+  RAD_LAUNCH("diam_tile_box", k_tile_box, wave_grid(k_tile_box, 256, 1LL << 30), 256, 0, st, sorted, probs, p, cnt,
+             tiles, chunk0, box, rep);
   RAD_LAUNCH("diam_seed", k_seed, wave_grid(k_seed, 256, 1LL << 30), 256, 0, st, sorted, rep, p, tiles, chunk0, cnt, ps);
   RAD_LAUNCH("diam_thresh", k_thresh, sms * 2, 256, 0, st, rd, probs, p, cnt, ps);
   RAD_LAUNCH("diam_cull", k_cull, wave_grid(k_cull, 256, 1LL << 30), 256, 0, st, tiles, box, p, chunk0, cnt, ps, work);
