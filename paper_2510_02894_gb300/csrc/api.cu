@@ -315,7 +315,7 @@ struct Work {
   std::vector<RoiDiam> rd, up_rd;
   std::vector<double> tab_sp;         // spacings of the uploaded case tables
   MeshBatch mb;
-  long long nkeys = 0, nplanes = 0;
+  long long nkeys = 0, nplanes = 0, ntab = 0;
   bool soft = false;
   // CUDA graph of the whole pass, valid for the ROI table it was captured with
   cudaStream_t cap_stream = nullptr;
@@ -379,7 +379,7 @@ static rad_status prepare(Work& w, int n, const void* const* data, const int64_t
     }
   }
   plan_batch(dims, data, tab.data(), sp, n, soft, w.rois, w.mb);
-  plan_diam(w.rois, soft, w.rd, w.nkeys, w.nplanes);
+  plan_diam(w.rois, soft, w.rd, w.nkeys, w.ntab, w.nplanes);
   w.soft = soft;
   RAD_TRY(w.rois_dev.reserve(sizeof(Roi) * n));
   RAD_TRY(w.rd_dev.reserve(sizeof(RoiDiam) * n));
@@ -425,8 +425,8 @@ static rad_status enqueue_mesh(Work& w, cudaStream_t st, bool count) {
 
 static rad_status enqueue_shape(Work& w, cudaStream_t st) {
   ResultBlock* dr = w.dres();
-  RAD_TRY(diam_run(w.mb.n, w.rd_dev.as<RoiDiam>(), w.dro(), &dr->tot.nv, w.vcap, w.nkeys, w.nplanes, !w.soft,
-                   w.idx2.as<int16_t>(), w.soft ? w.vt.as<double>() : nullptr, w.ds, w.dout.as<DiamOut>(),
+  RAD_TRY(diam_run(w.mb.n, w.rd_dev.as<RoiDiam>(), w.dro(), &dr->tot.nv, w.vcap, w.nkeys, w.nplanes, w.ntab,
+                   !w.soft, w.idx2.as<int16_t>(), w.soft ? w.vt.as<double>() : nullptr, w.ds, w.dout.as<DiamOut>(),
                    &dr->stats, st));
   return RAD_OK;
 }

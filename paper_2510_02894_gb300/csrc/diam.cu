@@ -248,7 +248,7 @@ __device__ __forceinline__ long long key_offset(const long long* offs, const lon
 __global__ void k_scatter(const int16_t* __restrict__ idx2, const double* __restrict__ vt,
                           const long long* __restrict__ nv_dev, const RoiDiam* __restrict__ rd,
                           const RoiOut* __restrict__ ro, Params p, const long long* __restrict__ offs,
-                          const long long* __restrict__ parts, int* __restrict__ cursor,
+                          const long long* __restrict__ parts, int* __restrict__ cursor, const float* __restrict__ ctab,
                           float4* __restrict__ sorted, int* __restrict__ ids) {
   pdl_enter();
   const long long n = min(*nv_dev, p.nv_cap);
@@ -263,10 +263,19 @@ __global__ void k_scatter(const int16_t* __restrict__ idx2, const double* __rest
       vertex_q(idx2, v, q);
       roi = p.n == 1 ? 0 : roi_of_vertex(ro, p.n, v);
       const RoiDiam& r = rd[roi];
-      double u[3];
-      vertex_u(idx2, vt, v, u);
-      const float px = __double2float_rn((u[0] - r.cx) * r.sx), py = __double2float_rn((u[1] - r.cy) * r.sy),
-                  pz = __double2float_rn((u[2] - r.cz) * r.sz);
+      float px, py, pz;
+      if (vt == nullptr) {  // mask: every coordinate is a doubled grid index, looked up
+        const float* tx = ctab + r.tab0;
+        const float* ty = tx + 2 * r.nx + 3;
+        const float* tz = ty + 2 * r.ny + 3;
+        px = tx[q[0] + 2]; py = ty[q[1] + 2]; pz = tz[q[2] + 2];
+      } else {
+        double u[3];
+        vertex_u(idx2, vt, v, u);
+        px = __double2float_rn((u[0] - r.cx) * r.sx);
+        py = __double2float_rn((u[1] - r.cy) * r.sy);
+        pz = __double2float_rn((u[2] - r.cz) * r.sz);
+      }
       e = make_float4(px, py, pz, __fadd_rn(__fadd_rn(__fmul_rn(px, px), __fmul_rn(py, py)), __fmul_rn(pz, pz)));
     }
     const RoiDiam& r = rd[roi];
@@ -1051,7 +1060,8 @@ __global__ void k_tiebreak(const int* __restrict__ ids, const int16_t* __restric
   }
 }
 
-__global__ void k_diam_init(DiamOut* __restrict__ out, int n, ZeroSet zs) {
+__global__ void k_diam_init(DiamOut* __restrict__ out, int n, ZeroSet zs, const RoiDiam* __restrict__ rd,
+                            float* __restrict__ ctab, long long ntab) {
   pdl_enter();
   zero_ranges(zs);  // counters, statistics, key histogram and cursors, scan state
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
@@ -1059,6 +1069,27 @@ __global__ void k_diam_init(DiamOut* __restrict__ out, int n, ZeroSet zs) {
       out[i].d2[q] = 0ull;
       out[i].pair[q] = ~0ull;
     }
+  // FP32 coordinate tables of the masks: the entry of doubled coordinate q
+  // holds fl32((q / 2 - c) * s), the value the sorted entries carry
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < ntab;
+       e += (long long)gridDim.x * blockDim.x) {
+    int lo = 0, hi = n - 1;  // last ROI whose tables start at or before e
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (rd[mid].tab0 <= e) lo = mid;
+      else hi = mid - 1;
+    }
+    const RoiDiam& r = rd[lo];
+    const long long l = e - r.tab0;
+    const long long lx = 2LL * r.nx + 3, ly = 2LL * r.ny + 3;
+    double c, sp;
+    long long q;
+    if (l < lx) { q = l - 2; c = r.cx; sp = r.sx; }
+    else if (l < lx + ly) { q = l - lx - 2; c = r.cy; sp = r.sy; }
+    else { q = l - lx - ly - 2; c = r.cz; sp = r.sz; }
+    const double u = 0.5 * (double)q;
+    ctab[e] = __double2float_rn((u - c) * sp);
+  }
 }
 
 struct BestD {
@@ -1109,12 +1140,19 @@ rad_status launch_pairs(const float4* sorted, const WorkItem* work, const Params
 
 }  // namespace
 
+// Entries of a mask ROI's FP32 coordinate tables: doubled coordinates
+// q = -2 .. 2n (the vertices use -2 .. 2n - 1) per axis, x then y then z.
+static long long coord_table_len(int nx, int ny, int nz) {
+  return (2LL * nx + 3) + (2LL * ny + 3) + (2LL * nz + 3);
+}
+
 // Host-side per-ROI parameters of the diameter problems.
-void plan_diam(const std::vector<Roi>& rois, bool soft, std::vector<RoiDiam>& rd, long long& nkeys,
+void plan_diam(const std::vector<Roi>& rois, bool soft, std::vector<RoiDiam>& rd, long long& nkeys, long long& ntab,
                long long& nplanes) {
   const rad_tuning_t& tu = tuning();
   rd.resize(rois.size());
   nkeys = 0;
+  ntab = 0;
   nplanes = 0;
   const double u = ldexp(1.0, -24);
   for (size_t i = 0; i < rois.size(); ++i) {
@@ -1137,6 +1175,8 @@ void plan_diam(const std::vector<Roi>& rois, bool soft, std::vector<RoiDiam>& rd
     p.K = p.S2 + (p.planes ? (2LL * g.nx + 1) * p.PY * p.PZ : 0);
     p.key0 = nkeys;
     p.plane0 = nplanes;
+    p.tab0 = soft ? -1 : ntab;
+    if (!soft) ntab += coord_table_len(g.nx, g.ny, g.nz);
     nkeys += p.K;
     nplanes += p.planes ? (2LL * g.nx + 1) + (2LL * g.ny + 1) + (2LL * g.nz + 1) : 0;
     p.sx = g.sx; p.sy = g.sy; p.sz = g.sz;
@@ -1156,8 +1196,8 @@ void plan_diam(const std::vector<Roi>& rois, bool soft, std::vector<RoiDiam>& rd
 }
 
 rad_status diam_run(int n, const RoiDiam* rd, const RoiOut* ro, const long long* nv_dev, long long nv_cap,
-                    long long nkeys, long long nplanes, bool planes, const int16_t* idx2, const double* vt,
-                    DiamScratch& s, DiamOut* out, DiamStats* stats, cudaStream_t st) {
+                    long long nkeys, long long nplanes, long long ntab, bool planes, const int16_t* idx2,
+                    const double* vt, DiamScratch& s, DiamOut* out, DiamStats* stats, cudaStream_t st) {
   const rad_tuning_t& tu = tuning();
   Params p;
   p.n = n;
@@ -1195,6 +1235,7 @@ rad_status diam_run(int n, const RoiDiam* rd, const RoiOut* ro, const long long*
   add(sizeof(float) * 8 * p.work_cap);  // slice maxima (up to 8 slices per item)
   add(sizeof(int) * 8 * p.work_cap);    // slices to rescan
   add(sizeof(Cand) * p.cand_cap);
+  add(sizeof(float) * std::max<long long>(ntab, 1));  // coordinate tables (masks)
   RAD_TRY(s.misc.reserve(bytes));
   char* cur = s.misc.as<char>();
   int* hist = carve<int>(cur, K1);
@@ -1217,6 +1258,7 @@ rad_status diam_run(int n, const RoiDiam* rd, const RoiOut* ro, const long long*
   float* slicemax = carve<float>(cur, 8 * p.work_cap);
   int* hits = carve<int>(cur, 8 * p.work_cap);
   Cand* cand = carve<Cand>(cur, p.cand_cap);
+  float* ctab = carve<float>(cur, std::max<long long>(ntab, 1));
 
   const int sms = num_sms();
   ZeroSet zs{};
@@ -1225,12 +1267,13 @@ rad_status diam_run(int n, const RoiDiam* rd, const RoiOut* ro, const long long*
   zero_add(zs, cnt, sizeof(Counters));
   zero_add(zs, scan_state, sizeof(ScanTile<1>) * nparts + 16);
   zero_add(zs, stats, sizeof(DiamStats));
-  RAD_LAUNCH("diam_init", k_diam_init, wave_grid(k_diam_init, 256, (K1 + 255) / 256), 256, 0, st, out, n, zs);
+  RAD_LAUNCH("diam_init", k_diam_init, wave_grid(k_diam_init, 256, (std::max(K1, ntab) + 255) / 256), 256, 0, st, out,
+             n, zs, rd, ctab, planes ? ntab : 0);
   RAD_LAUNCH("diam_hist", k_hist, wave_grid(k_hist, 256, (nv + 255) / 256), 256, 0, st, idx2, nv_dev, rd, ro, p, hist);
   RAD_LAUNCH("diam_scan", k_xscan, (int)nparts, kScanThreads, 0, st, hist, K1, (int)nparts, offs, stiles, stick,
              &cnt->status);
   RAD_LAUNCH("diam_scatter", k_scatter, wave_grid(k_scatter, 256, (nv + 255) / 256), 256, 0, st, idx2, vt, nv_dev, rd,
-             ro, p, offs, parts, cursor, sorted, ids);
+             ro, p, offs, parts, cursor, ctab, sorted, ids);
   RAD_LAUNCH("diam_setup", k_setup, wave_grid(k_setup, 256, (n + nplanes + 255) / 256 + 1), 256, 0, st, rd, p, offs,
              parts, probs, chunk0, ps, cnt);
   RAD_LAUNCH("diam_tile_box", k_tile_box, wave_grid(k_tile_box, 256, 1LL << 30), 256, 0, st, sorted, probs, p, cnt,

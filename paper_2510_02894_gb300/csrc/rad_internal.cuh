@@ -265,6 +265,7 @@ struct RoiDiam {
   long long key0;                 // first sort key of the ROI
   long long C3, S0, S1, S2, K;    // key blocks (relative): 3D cells, Slice, Column, Row; total
   long long plane0;               // first plane of the ROI in the batch
+  long long tab0;                 // masks: first entry of the ROI's FP32 coordinate tables; -1: none
   double sx, sy, sz;
   double cx, cy, cz;              // centre (index units)
   double alpha, beta, gamma;      // FP32 error-bound coefficients
@@ -293,11 +294,11 @@ struct MeshDims {  // size of one grid
 };
 inline MeshDims make_dims(const int64_t dims[3]) { return MeshDims{(int)dims[0], (int)dims[1], (int)dims[2]}; }
 
-void plan_diam(const std::vector<Roi>& rois, bool soft, std::vector<RoiDiam>& rd, long long& nkeys,
+void plan_diam(const std::vector<Roi>& rois, bool soft, std::vector<RoiDiam>& rd, long long& nkeys, long long& ntab,
                long long& nplanes);
 rad_status diam_run(int n, const RoiDiam* rd, const RoiOut* ro, const long long* nv_dev, long long nv_cap,
-                    long long nkeys, long long nplanes, bool planes, const int16_t* idx2, const double* vt,
-                    DiamScratch& s, DiamOut* out, DiamStats* stats, cudaStream_t st);
+                    long long nkeys, long long nplanes, long long ntab, bool planes, const int16_t* idx2,
+                    const double* vt, DiamScratch& s, DiamOut* out, DiamStats* stats, cudaStream_t st);
 rad_status diam_plain_fp64(const int16_t* idx2, const double* vt, long long nv, const MeshDims& d, const double sp[3],
                            DiamScratch& s, DiamResult* out_dev, cudaStream_t st);
 
