@@ -124,9 +124,12 @@ typedef struct rad_workspace rad_workspace_t;
 rad_status rad_extract(const uint8_t* mask_dev, const int64_t dims[3], const double spacing[3], rad_features_t* out,
                        rad_workspace_t** ws, void* stream);
 
-/* Whole path for one HOST mask: the mask is copied to the device inside the
- * call (pinned host memory gives full bandwidth), the features are copied
- * back.  Same workspace rules as rad_extract. */
+/* Whole path for one HOST mask; the features are copied back.  A pinned
+ * (page-locked, device-mapped) mask is read in place by the first kernel
+ * over the host link, with no staging copy; the graph is replayed while the
+ * mask's address stays the same.  A pageable mask is copied to a device
+ * buffer inside the call first.  Either way the mask has been read when the
+ * call returns.  Same workspace rules as rad_extract. */
 rad_status rad_extract_host(const uint8_t* mask_host, const int64_t dims[3], const double spacing[3],
                             rad_features_t* out, rad_workspace_t** ws, void* stream);
 

@@ -793,6 +793,15 @@ rad_status rad_extract_host(const uint8_t* mask_host, const int64_t dims[3], con
   if (!out || !ws || !mask_host) { set_error("mask_host, out and ws must be non-NULL"); return RAD_ERR_INVALID_ARG; }
   rad_workspace_t* w = ensure_ws(ws);
   const size_t bytes = (size_t)dims[0] * dims[1] * dims[2];
+  // Pinned host memory is mapped into the device's address space: the
+  // bit-packing kernel then reads the mask in place over the host link (one
+  // pass, no staging copy).  Pageable memory is copied to a device buffer.
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, mask_host) == cudaSuccess && a.type == cudaMemoryTypeHost &&
+      a.devicePointer != nullptr)
+    return extract_impl(static_cast<const uint8_t*>(a.devicePointer), dims, spacing, out, w, (cudaStream_t)stream,
+                        (long long)bytes);
+  cudaGetLastError();  // pageable memory may report an error here
   RAD_TRY(w->work.mask.reserve(bytes));
   RAD_CUDA(cudaMemcpyAsync(w->work.mask.p, mask_host, bytes, cudaMemcpyHostToDevice, (cudaStream_t)stream));
   return extract_impl(w->work.mask.as<uint8_t>(), dims, spacing, out, w, (cudaStream_t)stream, (long long)bytes);

@@ -241,8 +241,9 @@ def extract(mask, spacing, ws, stream=None):
 
 
 def extract_host(mask_ptr, shape_zyx, spacing, ws, stream=None):
-    """Whole path for a HOST mask given by address (pinned memory gives full
-    copy bandwidth) and shape [nz, ny, nx]."""
+    """Whole path for a HOST mask given by address and shape [nz, ny, nx].
+    Pinned memory is read in place by the device; pageable memory is copied
+    inside the call."""
     dims, sp = _geometry(shape_zyx, spacing)
     f = Features()
     _check(lib().rad_extract_host(ctypes.c_void_p(int(mask_ptr)), dims, sp, ctypes.byref(f), ctypes.byref(ws.h),

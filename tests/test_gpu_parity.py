@@ -126,6 +126,16 @@ def test_extract_paths_agree():
     host = torch.from_numpy(m).pin_memory()
     ws2 = rad.Workspace()
     assert_features(rad.extract_host(host.data_ptr(), m.shape, sp, ws2), ref)
+    # pageable host memory goes through a device copy
+    ws3 = rad.Workspace()
+    assert_features(rad.extract_host(m.ctypes.data, m.shape, sp, ws3), ref)
+    # pinned memory is read in place at every call, graph replays included:
+    # new contents in the same buffer give the new features
+    for seed in (4, 5, 3):
+        mk, spk = synth.ellipsoid_32(seed)
+        refk, _ = oracle.features(mk, spk)
+        host.copy_(torch.from_numpy(mk))
+        assert_features(rad.extract_host(host.data_ptr(), mk.shape, spk, ws2), refk)
     # a different mask through the same workspace (pools grow as needed)
     rng = np.random.default_rng(9)
     m2 = (synth._noise_blob(rng, (30, 40, 50), 2.0) > 0.5).astype(np.uint8)
