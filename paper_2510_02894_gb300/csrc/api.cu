@@ -317,6 +317,10 @@ struct Work {
   MeshBatch mb;
   long long nkeys = 0, nplanes = 0, ntab = 0;
   bool soft = false;
+  // side branch of a pass: the diameter stage's initialisation runs beside
+  // the mesh, the masks' per-ROI totals beside the diameters
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_init = nullptr, ev_tot = nullptr;
   // CUDA graph of the whole pass, valid for the ROI table it was captured with
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t gexec = nullptr;
@@ -334,6 +338,9 @@ struct Work {
   ~Work() {
     drop_graph();
     if (cap_stream) cudaStreamDestroy(cap_stream);
+    if (side) cudaStreamDestroy(side);
+    for (cudaEvent_t e : {ev_fork, ev_init, ev_tot})
+      if (e) cudaEventDestroy(e);
     for (DevBuf* b : {&ms.bits, &ms.counts, &ms.wpre, &ms.tpre, &ms.wlist, &ms.prefix, &ms.chunk, &ms.cubes, &ms.hist, &ms.partial,
                       &ms.bintab, &ms.tabsp, &ds.misc, &ds.plain_part, &result, &ro, &dout, &feats, &rois_dev,
                       &rd_dev, &idx2, &vt, &tri, &mask, &gvtx, &plain})
@@ -440,10 +447,33 @@ static rad_status enqueue_finish(Work& w, bool have_diam, cudaStream_t st) {
   return RAD_OK;
 }
 
-// One whole pass (mesh, diameters, features to pinned host memory).
+// One whole pass (mesh, diameters, features to pinned host memory).  The
+// diameter stage's initialisation depends on nothing from the mesh, and the
+// masks' per-ROI totals feed only the final assembly: both run on a side
+// branch (two branches of one graph when captured).
 static rad_status enqueue_pass(Work& w, cudaStream_t st) {
-  RAD_TRY(enqueue_mesh(w, st, true));
-  RAD_TRY(enqueue_shape(w, st));
+  if (!w.side) RAD_CUDA(cudaStreamCreateWithFlags(&w.side, cudaStreamNonBlocking));
+  for (cudaEvent_t* e : {&w.ev_fork, &w.ev_init, &w.ev_tot})
+    if (!*e) RAD_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+  ResultBlock* dr = w.dres();
+  RAD_CUDA(cudaEventRecord(w.ev_fork, st));
+  RAD_CUDA(cudaStreamWaitEvent(w.side, w.ev_fork, 0));
+  RAD_TRY(diam_run(w.mb.n, w.rd_dev.as<RoiDiam>(), w.dro(), &dr->tot.nv, w.vcap, w.nkeys, w.nplanes, w.ntab,
+                   !w.soft, w.idx2.as<int16_t>(), w.soft ? w.vt.as<double>() : nullptr, w.ds, w.dout.as<DiamOut>(),
+                   &dr->stats, w.side, 1));
+  RAD_CUDA(cudaEventRecord(w.ev_init, w.side));
+  RAD_TRY(mesh_count(w.mb, w.ms, &dr->tot, w.dro(), st));
+  RAD_TRY(mesh_emit(w.mb, w.ms, &dr->tot, w.dro(), w.idx2.as<int16_t>(), w.soft ? w.vt.as<double>() : nullptr,
+                    w.tri.as<int32_t>(), w.vcap, w.tcap, st, false));
+  RAD_CUDA(cudaEventRecord(w.ev_fork, st));
+  RAD_CUDA(cudaStreamWaitEvent(w.side, w.ev_fork, 0));
+  RAD_TRY(mesh_totals(w.mb, w.ms, w.dro(), w.side));
+  RAD_CUDA(cudaEventRecord(w.ev_tot, w.side));
+  RAD_CUDA(cudaStreamWaitEvent(st, w.ev_init, 0));
+  RAD_TRY(diam_run(w.mb.n, w.rd_dev.as<RoiDiam>(), w.dro(), &dr->tot.nv, w.vcap, w.nkeys, w.nplanes, w.ntab,
+                   !w.soft, w.idx2.as<int16_t>(), w.soft ? w.vt.as<double>() : nullptr, w.ds, w.dout.as<DiamOut>(),
+                   &dr->stats, st, 2));
+  RAD_CUDA(cudaStreamWaitEvent(st, w.ev_tot, 0));
   return enqueue_finish(w, true, st);
 }
 

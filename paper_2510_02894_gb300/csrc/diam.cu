@@ -1197,7 +1197,7 @@ void plan_diam(const std::vector<Roi>& rois, bool soft, std::vector<RoiDiam>& rd
 
 rad_status diam_run(int n, const RoiDiam* rd, const RoiOut* ro, const long long* nv_dev, long long nv_cap,
                     long long nkeys, long long nplanes, long long ntab, bool planes, const int16_t* idx2,
-                    const double* vt, DiamScratch& s, DiamOut* out, DiamStats* stats, cudaStream_t st) {
+                    const double* vt, DiamScratch& s, DiamOut* out, DiamStats* stats, cudaStream_t st, int which) {
   const rad_tuning_t& tu = tuning();
   Params p;
   p.n = n;
@@ -1267,8 +1267,14 @@ rad_status diam_run(int n, const RoiDiam* rd, const RoiOut* ro, const long long*
   zero_add(zs, cnt, sizeof(Counters));
   zero_add(zs, scan_state, sizeof(ScanTile<1>) * nparts + 16);
   zero_add(zs, stats, sizeof(DiamStats));
-  RAD_LAUNCH("diam_init", k_diam_init, wave_grid(k_diam_init, 256, (std::max(K1, ntab) + 255) / 256), 256, 0, st, out,
-             n, zs, rd, ctab, planes ? ntab : 0);
+  if (which & 1) {
+    // on its own (a graph branch beside the mesh) it needs few CTAs: a few MB zeroed
+    const long long init_ctas = (std::max(K1, ntab) + 255) / 256;
+    RAD_LAUNCH("diam_init", k_diam_init,
+               wave_grid(k_diam_init, 256, which == 1 ? std::min<long long>(init_ctas, sms) : init_ctas), 256, 0, st,
+               out, n, zs, rd, ctab, planes ? ntab : 0);
+  }
+  if (!(which & 2)) return RAD_OK;
   RAD_LAUNCH("diam_hist", k_hist, wave_grid(k_hist, 256, (nv + 255) / 256), 256, 0, st, idx2, nv_dev, rd, ro, p, hist);
   RAD_LAUNCH("diam_scan", k_xscan, (int)nparts, kScanThreads, 0, st, hist, K1, (int)nparts, offs, stiles, stick,
              &cnt->status);

@@ -1188,7 +1188,7 @@ rad_status mesh_count(const MeshBatch& b, MeshScratch& s, MeshTotals* tot, RoiOu
 }
 
 rad_status mesh_emit(const MeshBatch& b, MeshScratch& s, MeshTotals* tot, RoiOut* out, int16_t* idx2, double* vt,
-                     int32_t* tri, long long vcap, long long tcap, cudaStream_t st) {
+                     int32_t* tri, long long vcap, long long tcap, cudaStream_t st, bool totals) {
   // every active cube has at least one triangle: the cube list fits in tcap
   const long long ccap = std::max<long long>(tcap, 1);
   if (b.soft) RAD_TRY(s.cubes.reserve(sizeof(int4) * ccap));
@@ -1210,9 +1210,15 @@ rad_status mesh_emit(const MeshBatch& b, MeshScratch& s, MeshTotals* tot, RoiOut
                s.wlist.as<int2>(), b.wpre, s.wpre.as<int>(), s.tpre.as<int>(), s.prefix.as<long long>(),
                s.chunk.as<long long>(), s.bintab.as<BinCase>(), idx2, tri, vcap, tcap, tot, out,
                s.hist.as<unsigned long long>());
-    RAD_LAUNCH("mc_mask_totals", k_mask_totals, std::min(b.n, sms * 8), 256, 0, st, b.rois, b.n,
-               s.bintab.as<BinCase>(), s.hist.as<unsigned long long>(), out);
+    if (totals) RAD_TRY(mesh_totals(b, s, out, st));
   }
+  return RAD_OK;
+}
+
+rad_status mesh_totals(const MeshBatch& b, MeshScratch& s, RoiOut* out, cudaStream_t st) {
+  if (b.soft) return RAD_OK;  // the soft cube kernel finishes its own totals
+  RAD_LAUNCH("mc_mask_totals", k_mask_totals, std::min(b.n, num_sms() * 8), 256, 0, st, b.rois, b.n,
+             s.bintab.as<BinCase>(), s.hist.as<unsigned long long>(), out);
   return RAD_OK;
 }
 

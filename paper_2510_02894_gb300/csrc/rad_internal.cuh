@@ -247,8 +247,11 @@ rad_status mesh_tables(const double* spacings_host, int n_tabs, MeshScratch& s, 
 // Phase 1: pack + count + scan; batch totals in *tot, per-ROI id ranges in out[].
 rad_status mesh_count(const MeshBatch& b, MeshScratch& s, MeshTotals* tot, RoiOut* out, cudaStream_t st);
 // Phase 2: vertices / triangles (up to the capacities) and per-ROI 6V, 2A.
+// With totals = false a mask's per-ROI 6V and 2A are left to mesh_totals
+// (on any stream ordered after this one).
 rad_status mesh_emit(const MeshBatch& b, MeshScratch& s, MeshTotals* tot, RoiOut* out, int16_t* idx2, double* vt,
-                     int32_t* tri, long long vcap, long long tcap, cudaStream_t st);
+                     int32_t* tri, long long vcap, long long tcap, cudaStream_t st, bool totals = true);
+rad_status mesh_totals(const MeshBatch& b, MeshScratch& s, RoiOut* out, cudaStream_t st);
 
 // ---- diameters ----------------------------------------------------------------
 struct DiamScratch {
@@ -296,9 +299,13 @@ inline MeshDims make_dims(const int64_t dims[3]) { return MeshDims{(int)dims[0],
 
 void plan_diam(const std::vector<Roi>& rois, bool soft, std::vector<RoiDiam>& rd, long long& nkeys, long long& ntab,
                long long& nplanes);
+// which: 1 = the stage's initialisation only (zeroing, per-ROI results,
+// coordinate tables; needs nothing from the mesh), 2 = everything after it,
+// 3 = both.  Both calls of a split run see the same scratch layout.
 rad_status diam_run(int n, const RoiDiam* rd, const RoiOut* ro, const long long* nv_dev, long long nv_cap,
                     long long nkeys, long long nplanes, long long ntab, bool planes, const int16_t* idx2,
-                    const double* vt, DiamScratch& s, DiamOut* out, DiamStats* stats, cudaStream_t st);
+                    const double* vt, DiamScratch& s, DiamOut* out, DiamStats* stats, cudaStream_t st,
+                    int which = 3);
 rad_status diam_plain_fp64(const int16_t* idx2, const double* vt, long long nv, const MeshDims& d, const double sp[3],
                            DiamScratch& s, DiamResult* out_dev, cudaStream_t st);
 
