@@ -450,8 +450,14 @@ static rad_status enqueue_finish(Work& w, bool have_diam, cudaStream_t st) {
 // One whole pass (mesh, diameters, features to pinned host memory).  The
 // diameter stage's initialisation depends on nothing from the mesh, and the
 // masks' per-ROI totals feed only the final assembly: both run on a side
-// branch (two branches of one graph when captured).
+// branch (two branches of one graph when captured).  With per-kernel
+// profiling on, the pass stays on one stream so every kernel is timed alone.
 static rad_status enqueue_pass(Work& w, cudaStream_t st) {
+  if (profiling_on()) {
+    RAD_TRY(enqueue_mesh(w, st, true));
+    RAD_TRY(enqueue_shape(w, st));
+    return enqueue_finish(w, true, st);
+  }
   if (!w.side) RAD_CUDA(cudaStreamCreateWithFlags(&w.side, cudaStreamNonBlocking));
   for (cudaEvent_t* e : {&w.ev_fork, &w.ev_init, &w.ev_tot})
     if (!*e) RAD_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
