@@ -262,6 +262,7 @@ def main():
     N, T = feats["n_vertices"], feats["n_triangles"]
     pairs = N * (N - 1) / 2
     tuned = {}
+    tuning_default = rad.get_tuning()  # each workload's search starts from the library default
     if not args.no_autotune:  # pick tile / block shapes on this workload (a second or so)
         cache = os.path.join(tempfile.gettempdir(), "rad_bench_tuning.json")
         cfg, table = autotune.tune(lambda: rad.extract(dev, sp, ws), autotune.bucket(1, N), cache_path=cache)
@@ -389,6 +390,7 @@ def main():
         devs = [torch.from_numpy(c).cuda() for c, _ in crops]
         b = rad.Batch(devs, [s for _, s in crops])
         if not args.no_autotune:
+            rad.set_tuning(**tuning_default)
             nb = sum(f["n_vertices"] for f in b.run())
             cache = os.path.join(tempfile.gettempdir(), "rad_bench_tuning.json")
             cfg, table = autotune.tune(b.run, autotune.bucket(len(devs), nb), cache_path=cache)

@@ -10,21 +10,24 @@
 //   1. Every vertex gets four keys -- a spatial cell (3D problem) and its
 //      Slice (z), Column (y) and Row (x) plane -- and one counting sort lays
 //      the vertices out as float4 (x, y, z in FP32, centred and scaled; w =
-//      vertex id).  The 3D problem is the whole cell-sorted range; every plane
-//      with two or more vertices is its own problem.
+//      the FP32 squared norm), with the vertex ids in a parallel array.  A
+//      mask's FP32 coordinates come from per-ROI tables indexed by the doubled
+//      grid coordinate.  The 3D problem is the whole cell-sorted range; every
+//      plane with two or more vertices is its own problem.
 //   2. Each problem is cut into tiles of TS vertices with bounding boxes and
 //      a representative vertex.  The upper triangle of a problem's tile pairs
 //      is walked as (tile row, 128-column chunk) items spread evenly over all
 //      warps: the representative pairs seed the running maximum F, then the
 //      tile pairs whose farthest-corner bound reaches T(F) form the work list.
-//   3. The surviving tile pairs are split into (tile pair, 32-entry B slice)
-//      warp items.  Every warp takes items from a ticket and evaluates them in
-//      FP32 from its own shared-memory buffers (the next item is staged with
-//      cp.async while the current one is evaluated, no block barriers); it
-//      re-culls against the current F, keeps the slice maximum and raises F
-//      with one atomic when it beats F.  Slices whose maximum reaches the
-//      final T(F) are rescanned and their pairs with f >= T(F) become
-//      candidates.
+//   3. The surviving tile pairs are split into (tile pair, two 32-entry B
+//      slices) warp units, dealt statically over all warps.  Every warp
+//      evaluates its units in FP32 (f32x2, two A entries per lane and
+//      coordinate) from its own shared-memory buffers (the next unit is
+//      staged with cp.async while the current one is evaluated, no block
+//      barriers); it re-culls against the current T before every slice,
+//      keeps each slice maximum and raises F with one atomic when it beats F.
+//      Slices whose maximum reaches the final T(F) are rescanned and their
+//      pairs with f >= T(F) become candidates.
 //   4. The candidates are re-evaluated in FP64 with the pinned formula: the
 //      largest d2 per ROI and category, then the smallest (i, j) attaining it.
 //
@@ -241,14 +244,13 @@ __global__ void k_hist(const int16_t* __restrict__ idx2, const long long* __rest
   }
 }
 
-__device__ __forceinline__ long long key_offset(const long long* offs, const long long* parts, long long key);  // below
 
 // The four slot reservations of a warp are issued back to back, so one
 // round trip covers all of them.
 __global__ void k_scatter(const int16_t* __restrict__ idx2, const double* __restrict__ vt,
                           const long long* __restrict__ nv_dev, const RoiDiam* __restrict__ rd,
                           const RoiOut* __restrict__ ro, Params p, const long long* __restrict__ offs,
-                          const long long* __restrict__ parts, int* __restrict__ cursor, const float* __restrict__ ctab,
+                          int* __restrict__ cursor, const float* __restrict__ ctab,
                           float4* __restrict__ sorted, int* __restrict__ ids) {
   pdl_enter();
   const long long n = min(*nv_dev, p.nv_cap);
@@ -297,7 +299,7 @@ __global__ void k_scatter(const int16_t* __restrict__ idx2, const double* __rest
     for (int k = 0; k < 4; ++k) {
       const int b = __shfl_sync(0xffffffffu, base[k], __ffs(peers[k]) - 1);
       if (key[k] >= 0) {
-        const long long slot = key_offset(offs, parts, key[k]) + b + __popc(peers[k] & ((1u << lane) - 1u));
+        const long long slot = offs[key[k]] + b + __popc(peers[k] & ((1u << lane) - 1u));
         sorted[slot] = e;
         ids[slot] = (int)v;
       }
@@ -362,11 +364,6 @@ __global__ void __launch_bounds__(kScanThreads) k_xscan(const int* __restrict__ 
   }
 }
 
-// Global offset of a key.
-__device__ __forceinline__ long long key_offset(const long long* offs, const long long* parts, long long key) {
-  (void)parts;
-  return offs[key];
-}
 
 // ---- 2. problems and tiles --------------------------------------------------------
 // One lane per candidate problem: the 3D problem of every ROI (items 0..n-1)
@@ -395,7 +392,7 @@ __device__ __forceinline__ long long chunks_upto(long long m) {
 }
 
 __global__ void k_setup(const RoiDiam* __restrict__ rd, Params p, const long long* __restrict__ offs,
-                        const long long* __restrict__ parts, Problem* __restrict__ probs, int* __restrict__ chunk0,
+                        Problem* __restrict__ probs, int* __restrict__ chunk0,
                         ProblemState* __restrict__ ps, Counters* __restrict__ cnt) {
   pdl_enter();
   const int lane = threadIdx.x & 31;
@@ -429,8 +426,8 @@ __global__ void k_setup(const RoiDiam* __restrict__ rd, Params p, const long lon
           axis = 0; k0 = r.key0 + r.S2 + (l - nz2 - ny2) * r.PY * r.PZ; k1 = k0 + (long long)r.PY * r.PZ;
         }
       }
-      beg = key_offset(offs, parts, k0);
-      len = key_offset(offs, parts, k1) - beg;
+      beg = offs[k0];
+      len = offs[k1] - beg;
     }
     const bool use = len >= 2;
     const unsigned int um = __ballot_sync(0xffffffffu, use);
@@ -949,20 +946,42 @@ __global__ void k_cand_list(const WorkItem* __restrict__ work, const float* __re
 
 // Candidates: one warp per listed slice rescans it (A entries in registers,
 // the 32 B entries one per lane, broadcast by shuffles) and lists its pairs
-// with f >= T.
+// with f >= T.  A warp stages its candidates in shared memory and reserves
+// list slots 33..64 at a time, so the list counter sees few atomics.
+constexpr int kCandThreads = 256;
 template <int TS>
-__global__ void k_cand(const float4* __restrict__ sorted, const WorkItem* __restrict__ work,
-                       const int* __restrict__ hits, Params p, Counters* __restrict__ cnt,
-                       const ProblemState* __restrict__ ps, Cand* __restrict__ cand) {
+__global__ void __launch_bounds__(kCandThreads) k_cand(const float4* __restrict__ sorted,
+                                                       const WorkItem* __restrict__ work, const int* __restrict__ hits,
+                                                       Params p, Counters* __restrict__ cnt,
+                                                       const ProblemState* __restrict__ ps, Cand* __restrict__ cand) {
   pdl_enter();
   constexpr int RA = TS / 32;
   const long long nh = cnt->n_hits;
   const int lane = threadIdx.x & 31;
+  __shared__ Cand s_cb[kCandThreads / 32][64];
+  Cand* cb = s_cb[threadIdx.x >> 5];
+  int cbn = 0;  // staged candidates (warp-uniform)
+  auto cflush = [&]() {
+    __syncwarp();
+    long long base = 0;
+    if (lane == 0) base = (long long)atomicAdd((unsigned long long*)&cnt->n_cand, (unsigned long long)cbn);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    for (int i = lane; i < cbn; i += 32) {
+      if (base + i < p.cand_cap) cand[base + i] = cb[i];
+      else atomicOr(&cnt->status, DEV_ERR_CANDCAP);
+    }
+    __syncwarp();
+    cbn = 0;
+  };
   const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  // the next hit's slice and work item are loaded while the current one is rescanned
+  int sl_nxt = warp < nh ? hits[warp] : 0;
+  WorkItem w_nxt;
+  if (warp < nh) w_nxt = work[sl_nxt / RA];
   for (long long h = warp; h < nh; h += nwarps) {
-    const int sl = hits[h];
-    const WorkItem w = work[sl / RA];
+    const int sl = sl_nxt;
+    const WorkItem w = w_nxt;
     const float T = __uint_as_float(ps[w.problem].T);
     const int jb = (sl % RA) * 32;
     const bool same = w.abeg == w.bbeg;
@@ -970,6 +989,10 @@ __global__ void k_cand(const float4* __restrict__ sorted, const WorkItem* __rest
 #pragma unroll
     for (int r = 0; r < RA; ++r) a[r] = expand_a(sorted[w.abeg + min(lane + 32 * r, w.alen - 1)]);
     const float4 bl = sorted[w.bbeg + min(jb + lane, w.blen - 1)];
+    if (h + nwarps < nh) {
+      sl_nxt = hits[h + nwarps];
+      w_nxt = work[sl_nxt / RA];
+    }
     const int nj = min(32, w.blen - jb);
     for (int jj = 0; jj < nj; ++jj) {
       float4 b;
@@ -983,23 +1006,18 @@ __global__ void k_cand(const float4* __restrict__ sorted, const WorkItem* __rest
         const int ia = lane + 32 * r;
         const bool c = ia < w.alen && (!same || ia < j) && pair_g(a[r], b) >= T;
         const unsigned int cm = __ballot_sync(0xffffffffu, c);
-        if (cm == 0) continue;
-        long long base = 0;
-        if (lane == 0) base = (long long)atomicAdd((unsigned long long*)&cnt->n_cand, (unsigned long long)__popc(cm));
-        base = __shfl_sync(0xffffffffu, base, 0);
+        if (cm == 0) continue;  // warp-uniform
         if (c) {
-          const long long slot = base + __popc(cm & ((1u << lane) - 1u));
-          if (slot < p.cand_cap) {
-            Cand k;
-            k.ea = w.abeg + ia; k.eb = w.bbeg + j; k.roi = w.roi; k.q = w.q;
-            cand[slot] = k;
-          } else {
-            atomicOr(&cnt->status, DEV_ERR_CANDCAP);
-          }
+          Cand k;
+          k.ea = w.abeg + ia; k.eb = w.bbeg + j; k.roi = w.roi; k.q = w.q;
+          cb[cbn + __popc(cm & ((1u << lane) - 1u))] = k;
         }
+        cbn += __popc(cm);
+        if (cbn > 32) cflush();
       }
     }
   }
+  if (cbn) cflush();
 }
 
 // ---- 5. FP64 confirmation -------------------------------------------------------------
@@ -1133,8 +1151,8 @@ rad_status launch_pairs(const float4* sorted, const WorkItem* work, const Params
   const int pgrid = std::min(ctas, wave_grid(kp, NT, 1LL << 30, smem));
   RAD_LAUNCH("diam_pairs_fp32", kp, pgrid, NT, smem, st, sorted, work, p, rd, cnt, ps, slicemax);
   RAD_LAUNCH("diam_cand_list", kl, wave_grid(kl, 256, num_sms() * 4), 256, 0, st, work, slicemax, p, cnt, ps, hits);
-  RAD_LAUNCH("diam_pairs_cand", kc, wave_grid(kc, 256, num_sms() * 4), 256, 0, st, sorted, work, hits, p, cnt, ps,
-             cand);
+  RAD_LAUNCH("diam_pairs_cand", kc, wave_grid(kc, kCandThreads, num_sms() * 4), kCandThreads, 0, st, sorted, work,
+             hits, p, cnt, ps, cand);
   return RAD_OK;
 }
 
@@ -1244,7 +1262,6 @@ rad_status diam_run(int n, const RoiDiam* rd, const RoiOut* ro, const long long*
   char* scan_state = carve<char>(cur, sizeof(ScanTile<1>) * nparts + 16);
   ScanTile<1>* stiles = reinterpret_cast<ScanTile<1>*>(scan_state);
   unsigned int* stick = reinterpret_cast<unsigned int*>(scan_state + sizeof(ScanTile<1>) * nparts);
-  const long long* parts = nullptr;
   float4* sorted = carve<float4>(cur, nsorted);
   int* ids = carve<int>(cur, nsorted);
   Problem* probs = carve<Problem>(cur, p.max_problems);
@@ -1279,9 +1296,9 @@ rad_status diam_run(int n, const RoiDiam* rd, const RoiOut* ro, const long long*
   RAD_LAUNCH("diam_scan", k_xscan, (int)nparts, kScanThreads, 0, st, hist, K1, (int)nparts, offs, stiles, stick,
              &cnt->status);
   RAD_LAUNCH("diam_scatter", k_scatter, wave_grid(k_scatter, 256, (nv + 255) / 256), 256, 0, st, idx2, vt, nv_dev, rd,
-             ro, p, offs, parts, cursor, ctab, sorted, ids);
+             ro, p, offs, cursor, ctab, sorted, ids);
   RAD_LAUNCH("diam_setup", k_setup, wave_grid(k_setup, 256, (n + nplanes + 255) / 256 + 1), 256, 0, st, rd, p, offs,
-             parts, probs, chunk0, ps, cnt);
+             probs, chunk0, ps, cnt);
   RAD_LAUNCH("diam_tile_box", k_tile_box, wave_grid(k_tile_box, 256, 1LL << 30), 256, 0, st, sorted, probs, p, cnt,
              tiles, chunk0, box, rep);
   RAD_LAUNCH("diam_seed", k_seed, wave_grid(k_seed, 256, 1LL << 30), 256, 0, st, sorted, rep, p, tiles, chunk0, cnt, ps);

@@ -13,22 +13,26 @@
 //            and packed to one bit per voxel (32 voxels per word) with zero
 //            rows around it; the packed grid is 1/8 of the input and stays in
 //            L2 for the passes below.
-//   k_count  one group of lanes per x-row (y, z): crossing-edge bits by XOR of
-//            neighbouring rows, counted with popc; active cubes by OR/AND of
-//            the four rows of a cube row; per-row vertex, triangle, voxel and
-//            active-cube counts, and per-word vertex prefixes.
-//   k_scan_* chunked exclusive scan of the row counts over the whole batch:
-//            vertex and triangle ids follow the canonical (z, y, x, axis)
-//            order inside each ROI, ROIs one after the other.
-//   k_rows   per row: the row's vertices (ids = row base + popc ranks) and a
-//            compact list of its active cubes with their first triangle id.
-//   k_cubes  one thread per active cube: vertex ids of its crossing edges, its
-//            triangles, and the volume and area sums.  For a mask the volume
-//            is an exact int64 sum in half-voxel units
-//            (6V = det(diag(s/2)) * sum A.(B x C)) and the area comes from a
-//            per-case table and a per-ROI, per-case histogram, so both are
-//            deterministic; a soft map (one ROI) sums FP64 per triangle with
-//            a fixed-order reduction.
+//   k_count  one group of lanes per x-row (y, z), two or four words per
+//            lane: crossing-edge bits by XOR of neighbouring rows, counted
+//            with popc; active cubes by OR/AND of the four rows of a cube
+//            row; per-row vertex, triangle, voxel and active-cube counts,
+//            row-local word prefixes (written only for words with surface)
+//            and the list of words with surface.
+//   k_scan_rows  single-pass exclusive scan of the row counts over the whole
+//            batch (decoupled look-back, bounded waits): vertex and triangle
+//            ids follow the canonical (z, y, x, axis) order inside each ROI,
+//            ROIs one after the other.
+//   k_emit   masks: warps take 32 listed words at a time; a word's vertices
+//            get ids = row base + word prefix + popc rank, its active cubes
+//            their twelve edge ids and triangles (a per-case table), the
+//            exact int64 volume in half-voxel units
+//            (6V = det(diag(s/2)) * sum A.(B x C)) and a per-ROI, per-case
+//            histogram from which k_mask_totals takes the area, so both are
+//            deterministic.
+//   k_rows, k_cubes  soft maps (one ROI): per row its interpolated vertices
+//            and a compact list of active cubes, then one thread per cube for
+//            its triangles and FP64 volume and area, summed in a fixed order.
 #include <stdio.h>
 
 #include <algorithm>
@@ -391,8 +395,7 @@ __global__ void k_scan_rows(const int4* __restrict__ counts, long long R, int nc
 }
 
 // q: 0 vertices, 1 triangles, 2 active cubes, 3 inside voxels (global exclusive prefixes)
-__device__ __forceinline__ long long row_base(const long long* prefix, const long long* chunk, long long r, int q) {
-  (void)chunk;
+__device__ __forceinline__ long long row_base(const long long* prefix, long long r, int q) {
   return prefix[4 * r + q];
 }
 
@@ -501,8 +504,7 @@ __device__ __forceinline__ double crossing_t(double v0, double v1) {
 template <bool SOFT>
 __global__ void k_rows(const uint32_t* __restrict__ bits, const Roi* __restrict__ rois, int n, long long total_rows,
                        int L, int Wc, const int4* __restrict__ counts, const int* __restrict__ wpre,
-                       const long long* __restrict__ prefix, const long long* __restrict__ chunk,
-                       int16_t* __restrict__ idx2, double* __restrict__ vt, int4* __restrict__ cubes, long long vcap,
+                       const long long* __restrict__ prefix, int16_t* __restrict__ idx2, double* __restrict__ vt, int4* __restrict__ cubes, long long vcap,
                        long long ccap, MeshTotals* __restrict__ tot) {
   pdl_enter();
   const int lane = threadIdx.x & 31, sub = lane % L, gpw = 32 / L;
@@ -521,9 +523,9 @@ __global__ void k_rows(const uint32_t* __restrict__ bits, const Roi* __restrict_
     const uint32_t* R10 = brow(bits, r, y + 1, z);
     const uint32_t* R01 = brow(bits, r, y, z + 1);
     const uint32_t* R11 = brow(bits, r, y + 1, z + 1);
-    const long long vb = it.valid ? row_base(prefix, chunk, it.g, 0) : 0;
-    const long long tb = it.valid ? row_base(prefix, chunk, it.g, 1) : 0;
-    const long long cb = it.valid ? row_base(prefix, chunk, it.g, 2) : 0;
+    const long long vb = it.valid ? row_base(prefix, it.g, 0) : 0;
+    const long long tb = it.valid ? row_base(prefix, it.g, 1) : 0;
+    const long long cb = it.valid ? row_base(prefix, it.g, 2) : 0;
     const uint32_t a0 = ldw(R00, 0, W) & 1u, b0 = ldw(R10, 0, W) & 1u, c0 = ldw(R01, 0, W) & 1u,
                    e0 = ldw(R11, 0, W) & 1u;
     const int case_m1 = (int)((a0 << 1) | (b0 << 3) | (c0 << 5) | (e0 << 7));
@@ -605,11 +607,10 @@ struct OwnerWord {
 };
 
 __device__ __forceinline__ OwnerWord owner_word(const uint32_t* bits, const Roi& r, const int* wpre,
-                                                const long long* prefix, const long long* chunk, int xo, int yo,
-                                                int zo) {
+                                                const long long* prefix, int xo, int yo, int zo) {
   OwnerWord o;
   const long long g = r.row0 + (long long)(zo + 1) * (r.ny + 1) + (yo + 1);
-  o.base = row_base(prefix, chunk, g, 0);
+  o.base = row_base(prefix, g, 0);
   if (xo < 0) {
     o.pre = 0; o.ex = o.ey = o.ez = 0u;
     return o;
@@ -649,7 +650,6 @@ template <bool SOFT>
 __global__ void __launch_bounds__(kCubeThreads) k_cubes(const uint32_t* __restrict__ bits, const Roi* __restrict__ rois,
                                                         int n, const int* __restrict__ wpre,
                                                         const long long* __restrict__ prefix,
-                                                        const long long* __restrict__ chunk,
                                                         const int4* __restrict__ cubes, const BinCase* __restrict__ tab,
                                                         int32_t* __restrict__ tri, long long ccap, long long tcap,
                                                         MeshTotals* __restrict__ tot, RoiOut* __restrict__ out,
@@ -690,7 +690,7 @@ __global__ void __launch_bounds__(kCubeThreads) k_cubes(const uint32_t* __restri
         const int slot = cz * 4 + cy * 2 + cx;
         const int g[3] = {x + cx, y + cy, z + cz};
         if (!((have >> slot) & 1u)) {
-          ow[slot] = owner_word(bits, r, wpre, prefix, chunk, g[0], g[1], g[2]);
+          ow[slot] = owner_word(bits, r, wpre, prefix, g[0], g[1], g[2]);
           have |= 1u << slot;
         }
         vid[e] = (int)(ow[slot].base + owner_rank(ow[slot], g[0], a));
@@ -843,7 +843,7 @@ constexpr unsigned int kEdgeAxis = (0u << 0) | (1u << 2) | (2u << 4) | (1u << 6)
 __global__ void __launch_bounds__(kEmitThreads, kEmitBlocksPerSM)
     k_emit(const uint32_t* __restrict__ bits, const Roi* __restrict__ rois, int n, const int2* __restrict__ wlist,
            long long wlist_cap, const int* __restrict__ wpre, const int* __restrict__ tpre,
-           const long long* __restrict__ prefix, const long long* __restrict__ chunk, const BinCase* __restrict__ tab,
+           const long long* __restrict__ prefix, const BinCase* __restrict__ tab,
            int16_t* __restrict__ idx2, int32_t* __restrict__ tri, long long vcap, long long tcap,
            MeshTotals* __restrict__ tot, RoiOut* __restrict__ out, unsigned long long* __restrict__ case_hist) {
   pdl_enter();
@@ -922,11 +922,11 @@ __global__ void __launch_bounds__(kEmitThreads, kEmitBlocksPerSM)
                (int)((((en2 ^ hn) & 1u) << 1) | ((en2 ^ (en2 >> 1)) & 1u));
         }
         S.onx[0][lane] = o0; S.onx[1][lane] = o1; S.onx[2][lane] = o2; S.onx[3][lane] = o3;
-        S.vb[0][lane] = (int)row_base(prefix, chunk, g, 0);
-        S.vb[1][lane] = oky ? (int)row_base(prefix, chunk, g + 1, 0) : 0;
-        S.vb[2][lane] = okz ? (int)row_base(prefix, chunk, g + r.ny + 1, 0) : 0;
-        S.vb[3][lane] = oky && okz ? (int)row_base(prefix, chunk, g + r.ny + 2, 0) : 0;
-        S.tb[lane] = row_base(prefix, chunk, g, 1) + (w == 0 ? 0 : tpre[wrow + w]);
+        S.vb[0][lane] = (int)row_base(prefix, g, 0);
+        S.vb[1][lane] = oky ? (int)row_base(prefix, g + 1, 0) : 0;
+        S.vb[2][lane] = okz ? (int)row_base(prefix, g + r.ny + 1, 0) : 0;
+        S.vb[3][lane] = oky && okz ? (int)row_base(prefix, g + r.ny + 2, 0) : 0;
+        S.tb[lane] = row_base(prefix, g, 1) + (w == 0 ? 0 : tpre[wrow + w]);
         u = (a ^ as) | (a ^ b) | (a ^ c);
         act = (a | as | b | bs | c | cs | e | es) & ~(a & as & b & bs & c & cs & e & es);
         m1v = w == 0 && (a & 1u);
@@ -1198,17 +1198,17 @@ rad_status mesh_emit(const MeshBatch& b, MeshScratch& s, MeshTotals* tot, RoiOut
   const int cblocks = sms * kCubeBlocksPerSM;
   if (b.soft) {
     RAD_LAUNCH("mc_rows_soft", k_rows<true>, rblocks, 256, 0, st, s.bits.as<uint32_t>(), b.rois, b.n, b.rows, b.L,
-               b.Wc, s.counts.as<int4>(), s.wpre.as<int>(), s.prefix.as<long long>(), s.chunk.as<long long>(), idx2,
+               b.Wc, s.counts.as<int4>(), s.wpre.as<int>(), s.prefix.as<long long>(), idx2,
                vt, s.cubes.as<int4>(), vcap, ccap, tot);
     RAD_LAUNCH("mc_cubes_soft", k_cubes<true>, cblocks, kCubeThreads, 0, st, s.bits.as<uint32_t>(), b.rois, b.n,
-               s.wpre.as<int>(), s.prefix.as<long long>(), s.chunk.as<long long>(), s.cubes.as<int4>(),
+               s.wpre.as<int>(), s.prefix.as<long long>(), s.cubes.as<int4>(),
                (const BinCase*)nullptr, tri, ccap, tcap, tot, out, s.hist.as<unsigned long long>(),
                s.partial.as<double>());
   } else {
     const int eblocks = sms * kEmitBlocksPerSM;  // persistent: the list length is known on the device only
     RAD_LAUNCH("mc_emit", k_emit, eblocks, kEmitThreads, 0, st, s.bits.as<uint32_t>(), b.rois, b.n,
                s.wlist.as<int2>(), b.wpre, s.wpre.as<int>(), s.tpre.as<int>(), s.prefix.as<long long>(),
-               s.chunk.as<long long>(), s.bintab.as<BinCase>(), idx2, tri, vcap, tcap, tot, out,
+               s.bintab.as<BinCase>(), idx2, tri, vcap, tcap, tot, out,
                s.hist.as<unsigned long long>());
     if (totals) RAD_TRY(mesh_totals(b, s, out, st));
   }
