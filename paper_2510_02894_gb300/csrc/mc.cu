@@ -101,9 +101,22 @@ __global__ void k_pack(const Roi* __restrict__ rois, int n, long long total, uin
                        ZeroSet zs) {
   pdl_enter();
   zero_ranges(zs);  // the pass's counters, per-ROI results and scan state
-  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
-       id += (long long)gridDim.x * blockDim.x) {
-    const Roi& r = rois[n == 1 ? 0 : roi_of_word(rois, n, id)];
+  // every block takes one contiguous range of words, so a thread's words
+  // only move forward and its ROI is found by one search and then stepped
+  const long long per = ((total + gridDim.x - 1) / gridDim.x + blockDim.x - 1) / blockDim.x * blockDim.x;
+  const long long beg = (long long)blockIdx.x * per, end = min(total, beg + per);
+  int ri = 0;
+  long long next0 = LLONG_MAX;  // first word of ROI ri + 1
+  if (n > 1 && beg + threadIdx.x < end) {
+    ri = roi_of_word(rois, n, beg + threadIdx.x);
+    next0 = ri + 1 < n ? rois[ri + 1].word0 : LLONG_MAX;
+  }
+  for (long long id = beg + threadIdx.x; id < end; id += blockDim.x) {
+    while (id >= next0) {  // at most a few ROIs per step (ROIs hold whole padded grids)
+      ++ri;
+      next0 = ri + 1 < n ? rois[ri + 1].word0 : LLONG_MAX;
+    }
+    const Roi& r = rois[ri];
     // one ROI's words number BY * BZ * W < 2^31 (checked on the host), so the
     // index arithmetic is 32-bit
     const unsigned int local = (unsigned int)(id - r.word0);
@@ -126,7 +139,32 @@ __global__ void k_pack(const Roi* __restrict__ rois, int n, long long total, uin
           const uint4 a = __ldg(reinterpret_cast<const uint4*>(row + x0));
           word = nz4(a.x) | (nz4(a.y) << 4) | (nz4(a.z) << 8) | (nz4(a.w) << 12);
         } else {
-          for (int i = 0; i < cnt; ++i) word |= (uint32_t)(row[x0 + i] != 0) << i;
+          // any alignment: the one to three 16-byte blocks holding bytes
+          // x0 .. x0 + cnt - 1, realigned by funnel shifts (bytes of the
+          // neighbouring rows in them are shifted or masked out); blocks that
+          // would reach outside the mask buffer take the byte loop
+          const uintptr_t a = reinterpret_cast<uintptr_t>(row + x0);
+          const int off = (int)(a & 15u);
+          const uint4* blk = reinterpret_cast<const uint4*>(a - (uintptr_t)off);
+          const int nblk = (off + cnt + 15) >> 4;
+          const uint8_t* base = (const uint8_t*)r.data;
+          const uint8_t* end = base + (long long)r.nx * r.ny * r.nz;
+          if ((const uint8_t*)blk >= base && (const uint8_t*)(blk + nblk) <= end) {
+            const uint4 c0 = __ldg(blk);
+            const uint4 c1 = nblk > 1 ? __ldg(blk + 1) : make_uint4(0u, 0u, 0u, 0u);
+            const uint4 c2 = nblk > 2 ? __ldg(blk + 2) : make_uint4(0u, 0u, 0u, 0u);
+            const uint32_t wv[12] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w, c2.x, c2.y, c2.z, c2.w};
+            const int j0 = off >> 2, sh = (off & 3) * 8;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+              const uint32_t lo = j0 == 0 ? wv[k] : (j0 == 1 ? wv[k + 1] : (j0 == 2 ? wv[k + 2] : wv[k + 3]));
+              const uint32_t hi = j0 == 0 ? wv[k + 1] : (j0 == 1 ? wv[k + 2] : (j0 == 2 ? wv[k + 3] : wv[k + 4]));
+              word |= nz4(__funnelshift_r(lo, hi, sh)) << (4 * k);
+            }
+            if (cnt < 32) word &= (1u << cnt) - 1u;
+          } else {
+            for (int i = 0; i < cnt; ++i) word |= (uint32_t)(row[x0 + i] != 0) << i;
+          }
         }
       } else {
         const float* row = (const float*)r.data + ((long long)z * r.ny + y) * r.nx;
