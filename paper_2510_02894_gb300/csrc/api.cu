@@ -253,7 +253,7 @@ const rad_tuning_t& tuning() { return g_tuning; }
 
 // ---- per-workspace state --------------------------------------------------------------
 
-struct ResultBlock {  // device; copied to pinned host memory after every pass
+struct ResultBlock {  // device; copied to pinned host memory after every pass (8-byte aligned POD)
   MeshTotals tot;
   DiamStats stats;
 };
@@ -266,10 +266,18 @@ __global__ void k_wait_probe(ScanTile<1>* tiles, unsigned int* status) {
   scan_lookback(tiles, 1, &e, status);
 }
 
-// Features of every ROI from the mesh and diameter results (one thread per ROI).
+// Features of every ROI from the mesh and diameter results (one thread per
+// ROI), written straight into the caller-visible pinned host buffer (mapped
+// into the device's address space), and the pass's result block copied to
+// its pinned host copy by the first threads: no copy nodes after the pass.
 __global__ void k_assemble(const Roi* __restrict__ rois, const RoiOut* __restrict__ ro,
-                           const DiamOut* __restrict__ dout, int n, int have_diam, rad_features_t* __restrict__ f) {
+                           const DiamOut* __restrict__ dout, int n, int have_diam, rad_features_t* __restrict__ f,
+                           const ResultBlock* __restrict__ res, ResultBlock* __restrict__ res_host) {
   pdl_enter();
+  static_assert(sizeof(ResultBlock) % 8 == 0, "result block copied in 8-byte words");
+  if (blockIdx.x == 0)
+    for (int k = threadIdx.x; k < (int)(sizeof(ResultBlock) / 8); k += blockDim.x)
+      reinterpret_cast<unsigned long long*>(res_host)[k] = reinterpret_cast<const unsigned long long*>(res)[k];
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const Roi& r = rois[i];
     const RoiOut& o = ro[i];
@@ -300,11 +308,11 @@ struct Work {
   MeshScratch ms;
   DiamScratch ds;
   DevBuf result;            // ResultBlock
-  DevBuf ro, dout, feats;   // per ROI: RoiOut, DiamOut, rad_features_t
+  DevBuf ro, dout;          // per ROI: RoiOut, DiamOut
   DevBuf rois_dev, rd_dev;  // per ROI: Roi, RoiDiam
   DevBuf idx2, vt, tri;
   long long vcap = 0, tcap = 0;
-  ResultBlock* host = nullptr;       // pinned copies
+  ResultBlock* host = nullptr;       // pinned copies, written by the assembly kernel
   rad_features_t* hfeats = nullptr;
   int hfeats_cap = 0;
   DevBuf mask;  // device copy of a host mask (rad_extract_host)
@@ -342,7 +350,7 @@ struct Work {
     for (cudaEvent_t e : {ev_fork, ev_init, ev_tot})
       if (e) cudaEventDestroy(e);
     for (DevBuf* b : {&ms.bits, &ms.counts, &ms.wpre, &ms.tpre, &ms.wlist, &ms.prefix, &ms.chunk, &ms.cubes, &ms.hist, &ms.partial,
-                      &ms.bintab, &ms.tabsp, &ds.misc, &ds.plain_part, &result, &ro, &dout, &feats, &rois_dev,
+                      &ms.bintab, &ms.tabsp, &ds.misc, &ds.plain_part, &result, &ro, &dout, &rois_dev,
                       &rd_dev, &idx2, &vt, &tri, &mask, &gvtx, &plain})
       b->release();
     if (host) cudaFreeHost(host);
@@ -368,7 +376,6 @@ static rad_status prepare(Work& w, int n, const void* const* data, const int64_t
   RAD_TRY(w.result.reserve(sizeof(ResultBlock)));
   RAD_TRY(w.ro.reserve(sizeof(RoiOut) * n));
   RAD_TRY(w.dout.reserve(sizeof(DiamOut) * n));
-  RAD_TRY(w.feats.reserve(sizeof(rad_features_t) * n));
   // case tables: one per distinct spacing (binary masks)
   std::vector<int> tab(n, 0);
   std::vector<double> tsp;
@@ -441,9 +448,7 @@ static rad_status enqueue_shape(Work& w, cudaStream_t st) {
 static rad_status enqueue_finish(Work& w, bool have_diam, cudaStream_t st) {
   const int n = w.mb.n;
   RAD_LAUNCH("assemble", k_assemble, std::max(1, (n + 127) / 128), 128, 0, st, w.mb.rois, w.dro(),
-             w.dout.as<DiamOut>(), n, have_diam ? 1 : 0, w.feats.as<rad_features_t>());
-  RAD_CUDA(cudaMemcpyAsync(w.host, w.dres(), sizeof(ResultBlock), cudaMemcpyDeviceToHost, st));
-  RAD_CUDA(cudaMemcpyAsync(w.hfeats, w.feats.p, sizeof(rad_features_t) * n, cudaMemcpyDeviceToHost, st));
+             w.dout.as<DiamOut>(), n, have_diam ? 1 : 0, w.hfeats, w.dres(), w.host);
   return RAD_OK;
 }
 
