@@ -34,11 +34,14 @@
 // FP32 error bounds (per pair, binary or soft; u = 2^-24, positions a relative
 // to the grid centre, R = the grid's half diagonal in mm, d2 the FP64 value):
 //   P = fl32(a), and once per entry n = fl(fl(P_x P_x + P_y P_y) + P_z P_z).
-//   Pair kernels (expansion form, 4 FP32 operations per pair):
-//     g = fma(-2P_ix, P_jx, fma(-2P_iy, P_jy, fma(-2P_iz, P_jz, fl(n_i + n_j))))
+//   Pair kernels (expansion form, 3 FP32 operations per pair, n_i added once
+//   per maximum):
+//     h = fma(-2P_ix, P_jx, fma(-2P_iy, P_jy, fma(-2P_iz, P_jz, n_j)))
+//     g = fl(n_i + h)
 //     |g - d2| <= 4.1u R sqrt(d2) + 20.2u R^2
-//     (the norms carry gamma_3 |P|^2, their sum u (n_i + n_j), the fma chain
-//     gamma_3 (|s| + 2 |P_i| |P_j|); the FP32 positions 4u R sqrt(d2) + 4u^2 R^2)
+//     (the norms carry 2 gamma_3 R^2, the fma chain gamma_3 (|n_j| + 2 |P_i|
+//     |P_j|) <= 3 gamma_3 R^2, the final add u |g| <= 4u R^2: about 19.1u R^2;
+//     the FP32 positions 4u R sqrt(d2) + 4u^2 R^2)
 //   Seed and box bounds (difference form):
 //     dx = fl(P_i - P_j), f = fma(dz,dz, fma(dy,dy, dx*dx))
 //     |f - d2| <= 5.1u d2 + 4.1u R sqrt(d2) + 4.1u^2 R^2.
@@ -120,13 +123,15 @@ struct Params {
   long long nv_cap;   // vertex pool capacity: device counts are clamped to it
 };
 
-// Expansion form: a2 = (-2 P_i, n_i), b = (P_j, n_j).
-__device__ __forceinline__ float pair_g(float4 a2, float4 b) {
-  float g = __fadd_rn(a2.w, b.w);
-  g = __fmaf_rn(a2.z, b.z, g);
-  g = __fmaf_rn(a2.y, b.y, g);
-  return __fmaf_rn(a2.x, b.x, g);
+// Expansion form: a2 = (-2 P_i, n_i), b = (P_j, n_j).  The FMA chain starts
+// from n_j and n_i is added last, so a maximum over many b needs that add
+// only once (rounding to nearest is monotone: max fl(n_i + h) = fl(n_i + max h)).
+__device__ __forceinline__ float pair_h(float4 a2, float4 b) {
+  float h = __fmaf_rn(a2.z, b.z, b.w);
+  h = __fmaf_rn(a2.y, b.y, h);
+  return __fmaf_rn(a2.x, b.x, h);
 }
+__device__ __forceinline__ float pair_g(float4 a2, float4 b) { return __fadd_rn(a2.w, pair_h(a2, b)); }
 
 // Packed pairs of FP32 values (Blackwell f32x2 arithmetic, round to nearest
 // per element: the same results as the scalar operations).
@@ -843,9 +848,9 @@ __global__ void __launch_bounds__(NT) k_pairs(const float4* __restrict__ sorted,
     float um = -1.0f;
     int ne = 0;  // slices evaluated
     if (!(w_cur.ub < T) && ns > 0) {
-      // A entries r and r + 1 packed per coordinate; B duplicated, so one f32x2
-      // add and three f32x2 FMAs give two pairs (the same operations, in the
-      // same order, as pair_g)
+      // A entries r and r + 1 packed per coordinate; B duplicated, so three
+      // f32x2 FMAs give two pairs (the same operations, in the same order, as
+      // pair_h; pair_g's final add of n_a is applied once per slice maximum)
       unsigned long long ax[RA / 2], ay[RA / 2], az[RA / 2], an[RA / 2];
 #pragma unroll
       for (int r = 0; r < RA; r += 2) {
@@ -862,16 +867,17 @@ __global__ void __launch_bounds__(NT) k_pairs(const float4* __restrict__ sorted,
         if (g + 1 < ns) dup(g + 1, (g + 1) & 1);  // read only after the barrier below
         const ulonglong2* bxy = sB2[wid][g & 1][0];
         const ulonglong2* bzn = sB2[wid][g & 1][1];
+        // h = fma(-2a_x, b_x, fma(-2a_y, b_y, fma(-2a_z, b_z, n_b))) per pair,
+        // its maximum over the slice per A entry, and n_a added once at the end
         float mx[RA];
 #pragma unroll
-        for (int r = 0; r < RA; ++r) mx[r] = 0.0f;
+        for (int r = 0; r < RA; ++r) mx[r] = -FLT_MAX;
 #pragma unroll 4
         for (int j = 0; j < 32; j += 2) {
           const ulonglong2 p0 = bxy[j], p1 = bzn[j], q0 = bxy[j + 1], q1 = bzn[j + 1];
 #pragma unroll
           for (int h = 0; h < RA / 2; ++h) {
-            unsigned long long g0 = add2(an[h], p1.y), g1 = add2(an[h], q1.y);
-            g0 = fma2(az[h], p1.x, g0); g1 = fma2(az[h], q1.x, g1);
+            unsigned long long g0 = fma2(az[h], p1.x, p1.y), g1 = fma2(az[h], q1.x, q1.y);
             g0 = fma2(ay[h], p0.y, g0); g1 = fma2(ay[h], q0.y, g1);
             g0 = fma2(ax[h], p0.x, g0); g1 = fma2(ax[h], q0.x, g1);
             float g00, g01, g10, g11;
@@ -882,9 +888,13 @@ __global__ void __launch_bounds__(NT) k_pairs(const float4* __restrict__ sorted,
           }
         }
         __syncwarp();  // slice g is read, slice g + 1's duplicate is visible
-        float m = mx[0];
+        float m = 0.0f;  // f is never below 0 in exact arithmetic; a rounded value below counts as 0
 #pragma unroll
-        for (int r = 1; r < RA; ++r) m = fmaxf(m, mx[r]);
+        for (int h = 0; h < RA / 2; ++h) {
+          float g0, g1;
+          unpk2(add2(an[h], pk2(mx[2 * h], mx[2 * h + 1])), g0, g1);
+          m = max3f(m, g0, g1);
+        }
         for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
         if (lane == 0) {
           slicemax[item * RA + s0 + g] = m;
