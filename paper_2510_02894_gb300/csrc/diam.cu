@@ -618,8 +618,10 @@ __device__ __forceinline__ void seed_flush(float m, int problem, ProblemState* p
 
 // Seed: the pairs of tile representatives (first vertices) in every tile
 // pair of a problem, plus each tile's first-last pair, are actual vertex
-// pairs, so their largest f is a valid starting F.
-__global__ void k_seed(const float4* __restrict__ sorted, const float4* __restrict__ rep, Params p,
+// pairs, so their largest f is a valid starting F.  Five blocks per SM
+// (48 registers): more resident warps for this latency-bound walk measured
+// faster than four or six.
+__global__ void __launch_bounds__(256, 5) k_seed(const float4* __restrict__ sorted, const float4* __restrict__ rep, Params p,
                        const Tile* __restrict__ tiles, const int* __restrict__ chunk0, const Counters* __restrict__ cnt,
                        ProblemState* __restrict__ ps) {
   pdl_enter();
