@@ -241,9 +241,13 @@ def all_diameters(u, spacing, method="auto"):
     """[(d2, i, j)] for 3D, Slice, Column, Row.
 
     method "brute": one all-pairs pass; "fast": pruned 3D + grouped planes;
-    "hull": convex-hull shortlists + pinned brute force (very large sets).
-    All give the same results (checked against the brute force in the
-    oracle tests); "auto" picks by size."""
+    "hull": convex-hull shortlists + pinned brute force (very large sets);
+    "auto" picks by size.  The brute force is pinned by explicit numpy scans
+    and closed forms (tests/test_oracle_pins.py); "fast" is compared with it
+    bit for bit in test_fast_diameters_match_bruteforce (same file), and
+    "hull" in tests/test_oracle_hull.py (3D and every plane family, on boxes,
+    slabs, lines, single voxels, hollow boxes, spheres, ellipsoids and batch
+    crops)."""
     n = u.shape[0]
     if method == "brute" or (method == "auto" and n <= 20000):
         return diameters_bruteforce(u, spacing)
