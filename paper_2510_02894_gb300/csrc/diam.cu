@@ -193,6 +193,13 @@ __device__ __forceinline__ void vertex_q(const int16_t* idx2, long long v, int q
 
 __device__ __forceinline__ int slot_of_axis(int axis) { return axis < 0 ? 0 : (axis == 2 ? 1 : (axis == 1 ? 2 : 3)); }
 
+// Running maximum F and threshold T are shared by a family: (ROI, result
+// slot).  A family's result is the maximum over all of its problems (the 3D
+// problem, or every plane of one orientation), so a tile pair of one plane
+// whose bound is below the largest value found in ANY plane of its family
+// cannot change the result and is culled.
+__device__ __forceinline__ int fam_of(int roi, int q) { return 4 * roi + q; }
+
 // ---- 1. keys, histogram, scatter ------------------------------------------------
 // kind 0: 3D cell (z, y, x order); kinds 1..3: (plane, 2D cell) for Slice
 // (equal z), Column (equal y) and Row (equal x), all offset by the ROI's
@@ -397,8 +404,7 @@ __device__ __forceinline__ long long chunks_upto(long long m) {
 }
 
 __global__ void k_setup(const RoiDiam* __restrict__ rd, Params p, const long long* __restrict__ offs,
-                        Problem* __restrict__ probs, int* __restrict__ chunk0,
-                        ProblemState* __restrict__ ps, Counters* __restrict__ cnt) {
+                        Problem* __restrict__ probs, int* __restrict__ chunk0, Counters* __restrict__ cnt) {
   pdl_enter();
   const int lane = threadIdx.x & 31;
   const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
@@ -474,9 +480,6 @@ __global__ void k_setup(const RoiDiam* __restrict__ rd, Params p, const long lon
       pr.nt = nt; pr.pad = 0;
       pr.chunk_end = ovf ? -1 : cb + S;
       probs[slot] = pr;
-      ProblemState z;
-      z.F = 0u; z.T = 0u;
-      ps[slot] = z;
     }
     // the warp marks the tiles of each accepted problem with its slot
     unsigned int wm = __ballot_sync(0xffffffffu, ok);
@@ -490,13 +493,11 @@ __global__ void k_setup(const RoiDiam* __restrict__ rd, Params p, const long lon
   }
 }
 
-// T(F) of every problem from its seeded F (FP64, one thread per problem).
-__global__ void k_thresh(const RoiDiam* __restrict__ rd, const Problem* __restrict__ probs, Params p,
-                         const Counters* __restrict__ cnt, ProblemState* __restrict__ ps) {
+// T(F) of every family from its seeded F (FP64, one thread per family).
+__global__ void k_thresh(const RoiDiam* __restrict__ rd, Params p, ProblemState* __restrict__ ps) {
   pdl_enter();
-  const int np = (int)min((long long)cnt->n_problems, p.max_problems);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x)
-    ps[i].T = __float_as_uint(threshold(__uint_as_float(ps[i].F), rd[probs[i].roi]));
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 4 * p.n; i += gridDim.x * blockDim.x)
+    ps[i].T = __float_as_uint(threshold(__uint_as_float(ps[i].F), rd[i >> 2]));
 }
 
 // One warp per tile: its record and first seed/cull chunk, the bounding box
@@ -611,9 +612,9 @@ __device__ __forceinline__ void row_ahead(RowAhead& r, const Tile* tiles, const 
   }
 }
 
-__device__ __forceinline__ void seed_flush(float m, int problem, ProblemState* ps) {
+__device__ __forceinline__ void seed_flush(float m, int fam, ProblemState* ps) {
   for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
-  if ((threadIdx.x & 31) == 0 && m > 0.0f) atomicMax(&ps[problem].F, __float_as_uint(m));
+  if ((threadIdx.x & 31) == 0 && m > 0.0f) atomicMax(&ps[fam].F, __float_as_uint(m));
 }
 
 // Seed: the pairs of tile representatives (first vertices) in every tile
@@ -638,8 +639,8 @@ __global__ void __launch_bounds__(256, 5) k_seed(const float4* __restrict__ sort
   float m = 0.0f;
   for (; w.k < w.kend; ++w.k) {
     if (w.k >= w.next0 && w.a + 1 < nt) {  // warp-uniform
-      if (nx.t.problem != ta.problem) {  // one flush per problem
-        seed_flush(m, ta.problem, ps);
+      if (fam_of(nx.t.roi, nx.t.q) != fam_of(ta.roi, ta.q)) {  // one flush per family
+        seed_flush(m, fam_of(ta.roi, ta.q), ps);
         m = 0.0f;
       }
       ++w.a;
@@ -658,7 +659,7 @@ __global__ void __launch_bounds__(256, 5) k_seed(const float4* __restrict__ sort
       if (b < ta.tile_end) m = fmaxf(m, pair_f(ra, rep[b]));
     }
   }
-  seed_flush(m, ta.problem, ps);
+  seed_flush(m, fam_of(ta.roi, ta.q), ps);
 }
 
 // Cull: every tile pair (a, b >= a) of a problem whose box bound reaches
@@ -678,8 +679,8 @@ __global__ void __launch_bounds__(256, 4) k_cull(const Tile* __restrict__ tiles,
   if (!walk_begin(w, chunk0, nt, K)) return;
   Tile ta = tiles[w.a];
   float4 alo = box[2 * w.a], ahi = box[2 * w.a + 1];
-  int problem = ta.problem;
-  float T = __uint_as_float(ps[problem].T);
+  int fam = fam_of(ta.roi, ta.q);
+  float T = __uint_as_float(ps[fam].T);
   RowAhead nx;
   row_ahead(nx, tiles, box, 2, chunk0, nt, w.a);
   for (; w.k < w.kend; ++w.k) {
@@ -691,9 +692,9 @@ __global__ void __launch_bounds__(256, 4) k_cull(const Tile* __restrict__ tiles,
       w.c0 = w.next0;
       w.next0 = nx.next1;
       row_ahead(nx, tiles, box, 2, chunk0, nt, w.a);
-      if (ta.problem != problem) {
-        problem = ta.problem;
-        T = __uint_as_float(ps[problem].T);
+      if (fam_of(ta.roi, ta.q) != fam) {
+        fam = fam_of(ta.roi, ta.q);
+        T = __uint_as_float(ps[fam].T);
       }
     }
     const long long b0 = w.a + (w.k - w.c0) * kChunk;
@@ -821,7 +822,7 @@ __global__ void __launch_bounds__(NT) k_pairs(const float4* __restrict__ sorted,
   WorkItem w_cur = work[t_cur / UPI];
   stage_unit<TS, G>(sA[wid][0], sB[wid][0], sorted, w_cur, (int)(t_cur % UPI) * G);
   cp_async_commit();
-  unsigned long long ft_cur = *(volatile unsigned long long*)&ps[w_cur.problem];
+  unsigned long long ft_cur = *(volatile unsigned long long*)&ps[fam_of(w_cur.roi, w_cur.q)];
   long long t_nxt = t_cur + W;
   WorkItem w_nxt = t_nxt < nunits ? work[t_nxt / UPI] : w_cur;
   int buf = 0;
@@ -838,7 +839,7 @@ __global__ void __launch_bounds__(NT) k_pairs(const float4* __restrict__ sorted,
     unsigned long long ft_nxt = ft_cur;
     if (has_next) {
       stage_unit<TS, G>(sA[wid][buf ^ 1], sB[wid][buf ^ 1], sorted, w_nxt, (int)(t_nxt % UPI) * G);
-      ft_nxt = *(volatile unsigned long long*)&ps[w_nxt.problem];
+      ft_nxt = *(volatile unsigned long long*)&ps[fam_of(w_nxt.roi, w_nxt.q)];
     }
     cp_async_commit();
     const long long t_nn = t_nxt + W;
@@ -867,7 +868,7 @@ __global__ void __launch_bounds__(NT) k_pairs(const float4* __restrict__ sorted,
 #pragma unroll 1
       for (int g = 0; g < ns; ++g) {
         // T for the next slice, read now and used after this slice's loop
-        const unsigned int tn = g + 1 < ns ? *(volatile unsigned int*)&ps[w_cur.problem].T : 0u;
+        const unsigned int tn = g + 1 < ns ? *(volatile unsigned int*)&ps[fam_of(w_cur.roi, w_cur.q)].T : 0u;
         if (g + 1 < ns) dup(g + 1, (g + 1) & 1);  // read only after the barrier below
         const ulonglong2* bxy = sB2[wid][g & 1][0];
         const ulonglong2* bzn = sB2[wid][g & 1][1];
@@ -910,8 +911,8 @@ __global__ void __launch_bounds__(NT) k_pairs(const float4* __restrict__ sorted,
       }
       if (lane == 0) {
         if (um > F) {  // fire and forget: T(F) is monotone, so the largest maximum wins both
-          atomicMax(&ps[w_cur.problem].F, __float_as_uint(um));
-          atomicMax(&ps[w_cur.problem].T, __float_as_uint(threshold(um, rd[w_cur.roi])));
+          atomicMax(&ps[fam_of(w_cur.roi, w_cur.q)].F, __float_as_uint(um));
+          atomicMax(&ps[fam_of(w_cur.roi, w_cur.q)].T, __float_as_uint(threshold(um, rd[w_cur.roi])));
         }
         n_items += s0 == 0;
       }
@@ -947,7 +948,10 @@ __global__ void k_cand_list(const WorkItem* __restrict__ work, const float* __re
     bool hit = false;
     if (sl < nslices) {
       const float m = slicemax[sl];
-      if (m >= 0.0f) hit = m >= __uint_as_float(ps[work[sl / RA].problem].T);
+      if (m >= 0.0f) {
+        const WorkItem& w = work[sl / RA];
+        hit = m >= __uint_as_float(ps[fam_of(w.roi, w.q)].T);
+      }
     }
     const unsigned int hm = __ballot_sync(0xffffffffu, hit);
     if (hm == 0) continue;
@@ -996,7 +1000,7 @@ __global__ void __launch_bounds__(kCandThreads) k_cand(const float4* __restrict_
   for (long long h = warp; h < nh; h += nwarps) {
     const int sl = sl_nxt;
     const WorkItem w = w_nxt;
-    const float T = __uint_as_float(ps[w.problem].T);
+    const float T = __uint_as_float(ps[fam_of(w.roi, w.q)].T);
     const int jb = (sl % RA) * 32;
     const bool same = w.abeg == w.bbeg;
     float4 a[RA];
@@ -1261,7 +1265,7 @@ rad_status diam_run(int n, const RoiDiam* rd, const RoiOut* ro, const long long*
   add(sizeof(int) * p.max_tiles);    // chunk0
   add(sizeof(float4) * 2 * p.max_tiles);
   add(sizeof(float4) * p.max_tiles);
-  add(sizeof(ProblemState) * p.max_problems);
+  add(sizeof(ProblemState) * 4 * n);
   add(sizeof(Counters));
   add(sizeof(WorkItem) * p.work_cap);
   add(sizeof(float) * 8 * p.work_cap);  // slice maxima (up to 8 slices per item)
@@ -1283,7 +1287,7 @@ rad_status diam_run(int n, const RoiDiam* rd, const RoiOut* ro, const long long*
   int* chunk0 = carve<int>(cur, p.max_tiles);
   float4* box = carve<float4>(cur, 2 * p.max_tiles);
   float4* rep = carve<float4>(cur, p.max_tiles);
-  ProblemState* ps = carve<ProblemState>(cur, p.max_problems);
+  ProblemState* ps = carve<ProblemState>(cur, 4 * n);
   Counters* cnt = carve<Counters>(cur, 1);
   WorkItem* work = carve<WorkItem>(cur, p.work_cap);
   float* slicemax = carve<float>(cur, 8 * p.work_cap);
@@ -1298,6 +1302,7 @@ rad_status diam_run(int n, const RoiDiam* rd, const RoiOut* ro, const long long*
   zero_add(zs, cnt, sizeof(Counters));
   zero_add(zs, scan_state, sizeof(ScanTile<1>) * nparts + 16);
   zero_add(zs, stats, sizeof(DiamStats));
+  zero_add(zs, ps, sizeof(ProblemState) * 4 * n);  // F = T = 0 for every family
   if (which & 1) {
     // on its own (a graph branch beside the mesh) it needs few CTAs: a few MB zeroed
     const long long init_ctas = (std::max(K1, ntab) + 255) / 256;
@@ -1312,11 +1317,11 @@ rad_status diam_run(int n, const RoiDiam* rd, const RoiOut* ro, const long long*
   RAD_LAUNCH("diam_scatter", k_scatter, wave_grid(k_scatter, 256, (nv + 255) / 256), 256, 0, st, idx2, vt, nv_dev, rd,
              ro, p, offs, cursor, ctab, sorted, ids);
   RAD_LAUNCH("diam_setup", k_setup, wave_grid(k_setup, 256, (n + nplanes + 255) / 256 + 1), 256, 0, st, rd, p, offs,
-             probs, chunk0, ps, cnt);
+             probs, chunk0, cnt);
   RAD_LAUNCH("diam_tile_box", k_tile_box, wave_grid(k_tile_box, 256, 1LL << 30), 256, 0, st, sorted, probs, p, cnt,
              tiles, chunk0, box, rep);
   RAD_LAUNCH("diam_seed", k_seed, wave_grid(k_seed, 256, 1LL << 30), 256, 0, st, sorted, rep, p, tiles, chunk0, cnt, ps);
-  RAD_LAUNCH("diam_thresh", k_thresh, sms * 2, 256, 0, st, rd, probs, p, cnt, ps);
+  RAD_LAUNCH("diam_thresh", k_thresh, std::max(1, std::min(sms * 2, (4 * n + 255) / 256)), 256, 0, st, rd, p, ps);
   RAD_LAUNCH("diam_cull", k_cull, wave_grid(k_cull, 256, 1LL << 30), 256, 0, st, tiles, box, p, chunk0, cnt, ps, work);
   const int ctas = sms * tu.ctas_per_sm;
   if (tu.tile == 64) {
