@@ -253,6 +253,7 @@ typedef struct {
   int64_t items_evaluated;         /* tile pairs evaluated in FP32 (after re-culling) */
   int64_t pairs_evaluated;         /* vertex pairs evaluated in FP32 */
   int64_t candidates;              /* pairs re-evaluated in FP64 */
+  int64_t coarse_pairs;            /* coarse tile pairs refined (problems of 512+ tiles are walked at two levels) */
 } rad_call_stats_t;
 rad_status rad_last_call_stats(rad_call_stats_t* out);
 

@@ -563,6 +563,7 @@ static void record_stats(const ResultBlock& r, long long h2d, long long d2h, boo
   g_stats.items_evaluated = r.stats.items_evaluated;
   g_stats.pairs_evaluated = r.stats.pairs_evaluated;
   g_stats.candidates = r.stats.candidates;
+  g_stats.coarse_pairs = r.stats.coarse_pairs;
 }
 
 // Whole pass on the prepared batch.  Capacities come from the previous call

@@ -67,6 +67,11 @@ namespace rad {
 namespace {
 
 constexpr int kChunk = 128;  // tile columns per seed / cull item (4 per lane)
+// Problems of kBigTiles or more tiles are walked at two levels: coarse tiles
+// of kCoarse tiles are seeded and culled first, then only the tile pairs
+// inside surviving coarse pairs are tested (one warp per coarse pair).
+constexpr int kCoarse = 32;
+constexpr int kBigTiles = 512;
 
 struct Problem {
   int axis;  // -1: 3D, 0: Row (equal x), 1: Column (equal y), 2: Slice (equal z)
@@ -75,16 +80,24 @@ struct Problem {
   int roi;
   int q;   // result slot: 0 3D, 1 Slice, 2 Column, 3 Row
   int nt;  // tiles
-  int pad;
+  int fine;  // -1: walked as is; -2: tiles only (walked through its coarse problem, the next slot);
+             // >= 0: coarse problem, first tile of its fine problem (the previous slot)
   long long chunk_end;  // one past the last seed/cull chunk of its rows; -1: past 2^31 chunks
 };
 
 struct __align__(16) Tile {
   int problem, beg, len, tile_end;  // tile_end: one past the problem's last tile
-  int roi, q, pad0, pad1;           // ROI and result slot of the problem
+  int roi, q;                       // ROI and result slot of the problem
+  int fine0, nfine;                 // coarse tiles: first fine tile and how many (else 0, 0)
 };
 
 // A surviving tile pair: both vertex ranges, its box bound and its result slot.
+// A coarse tile pair that survived culling: its fine tile ranges.
+struct RefineItem {
+  int fa, na, fb, nb;
+  int problem, roi, q, same;  // problem: the fine problem's slot; same: a coarse tile with itself
+};
+
 struct WorkItem {
   int problem, roi;
   int abeg, alen, bbeg, blen;
@@ -103,7 +116,7 @@ struct __align__(8) ProblemState {  // read as one 64-bit word by the pair kerne
 
 struct Counters {
   int n_problems;
-  unsigned int pad1;
+  unsigned int alloc_fine;   // tiles of fine problems (their own region after the walked tiles)
   unsigned long long alloc;  // (seed/cull chunks << 32) + tiles, one atomic per problem
   long long n_pairs;         // tile pairs (upper triangles)
   long long n_work;
@@ -111,7 +124,8 @@ struct Counters {
   long long n_hits;  // slices to rescan for candidates
   unsigned long long items_evaluated, pairs_evaluated;
   unsigned int status;
-  unsigned int pad;
+  unsigned int n_refine;     // surviving coarse tile pairs
+  unsigned int seed_done, pad2;  // last-block ticket of the seed
 };
 
 // Batch-wide parameters of one run.
@@ -120,7 +134,9 @@ struct Params {
   int TS;
   long long nplanes;  // planes of all ROIs
   long long work_cap, cand_cap, max_problems, max_tiles;
+  long long max_fine, refine_cap;  // tiles of fine problems (their region after max_tiles); coarse pairs
   long long nv_cap;   // vertex pool capacity: device counts are clamped to it
+  long long sweep_min;  // ROIs with at least this many vertices get the farthest-point seed
 };
 
 // Expansion form: a2 = (-2 P_i, n_i), b = (P_j, n_j).  The FMA chain starts
@@ -229,23 +245,113 @@ __device__ __forceinline__ int roi_of_vertex(const RoiOut* ro, int n, long long 
   return lo;
 }
 
-// Warp-aggregated: lanes with equal keys (consecutive vertices share cells and
-// planes) make one atomic.
-__global__ void k_hist(const int16_t* __restrict__ idx2, const long long* __restrict__ nv_dev,
-                       const RoiDiam* __restrict__ rd, const RoiOut* __restrict__ ro, Params p,
-                       int* __restrict__ hist) {
+// FP32 position of vertex v relative to its ROI's centre, scaled by the
+// spacing: a mask's coordinates come from the ROI's tables (indexed by the
+// doubled grid coordinate), a soft map's from its FP64 position.
+__device__ __forceinline__ float3 vert_pos(const int16_t* idx2, const double* vt, const float* ctab, const RoiDiam& r,
+                                           long long v) {
+  if (vt == nullptr) {
+    const float* tx = ctab + r.tab0;
+    const float* ty = tx + 2 * r.nx + 3;
+    const float* tz = ty + 2 * r.ny + 3;
+    return make_float3(tx[idx2[3 * v] + 2], ty[idx2[3 * v + 1] + 2], tz[idx2[3 * v + 2] + 2]);
+  }
+  double u[3];
+  vertex_u(idx2, vt, v, u);
+  return make_float3(__double2float_rn((u[0] - r.cx) * r.sx), __double2float_rn((u[1] - r.cy) * r.sy),
+                     __double2float_rn((u[2] - r.cz) * r.sz));
+}
+
+__device__ __forceinline__ float pair_f3(float3 a, float3 b) {
+  return pair_f(make_float4(a.x, a.y, a.z, 0.f), make_float4(b.x, b.y, b.z, 0.f));
+}
+
+// Farthest-point sweep of the 3D seed, accumulated per thread: the largest
+// (f bits << 32 | ROI-local vertex) of the thread's vertices, for its current
+// ROI.  f is the distance of an actual vertex pair, so it is a valid seed of
+// the ROI's 3D family F; the argmax is kept when a slot array is given.
+struct SweepAcc {
+  int roi = -1;
+  unsigned long long key = 0ull;
+};
+
+__device__ __forceinline__ void sweep_global(int roi, unsigned long long key, unsigned long long* slot,
+                                             ProblemState* ps) {
+  if (roi < 0 || key == 0ull) return;
+  if (slot) atomicMax(&slot[roi], key);
+  atomicMax(&ps[fam_of(roi, 0)].F, (unsigned int)(key >> 32));
+}
+
+// One step, called by every lane of the warp.  A single mask accumulates in
+// the thread (one ROI; the block reduces at the end); a batch reduces the
+// lanes of each ROI in the warp at once and makes one atomic per ROI.
+__device__ __forceinline__ void sweep_step(SweepAcc& a, bool multi, bool valid, int roi, float f, unsigned int local,
+                                           unsigned long long* slot, ProblemState* ps) {
+  const unsigned long long k = valid ? ((unsigned long long)__float_as_uint(f) << 32) | local : 0ull;  // f >= 0
+  if (!multi) {
+    a.roi = 0;
+    a.key = k > a.key ? k : a.key;
+    return;
+  }
+  const int lane = threadIdx.x & 31;
+  const unsigned int peers = __match_any_sync(0xffffffffu, valid ? roi : -1);
+  const unsigned int hi = __reduce_max_sync(peers, (unsigned int)(k >> 32));
+  const unsigned int lo = __reduce_max_sync(peers, (unsigned int)(k >> 32) == hi ? (unsigned int)k : 0u);
+  if (valid && lane == __ffs(peers) - 1) sweep_global(roi, ((unsigned long long)hi << 32) | lo, slot, ps);
+}
+
+// End of the kernel (every thread of the block): lanes of one ROI reduce in
+// the warp; warps whose ROI is the block's (all of them for a single mask)
+// reduce in shared memory, so a block makes one atomic per value.
+__device__ __forceinline__ void sweep_finish(const SweepAcc& a, int block_roi, unsigned long long* s_key,
+                                             unsigned long long* slot, ProblemState* ps) {
+  if (a.roi < 0 && block_roi < 0) return;  // block-uniform: a batch, or a block without vertices
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) *s_key = 0ull;
+  __syncthreads();
+  const unsigned int peers = __match_any_sync(0xffffffffu, a.roi);
+  const unsigned int hi = __reduce_max_sync(peers, (unsigned int)(a.key >> 32));
+  const unsigned int lo = __reduce_max_sync(peers, (unsigned int)(a.key >> 32) == hi ? (unsigned int)a.key : 0u);
+  const unsigned long long k = ((unsigned long long)hi << 32) | lo;
+  if (lane == __ffs(peers) - 1 && a.roi >= 0) {
+    if (a.roi == block_roi) atomicMax(s_key, k);
+    else sweep_global(a.roi, k, slot, ps);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) sweep_global(block_roi, *s_key, slot, ps);
+}
+
+// Key histogram, warp-aggregated: lanes with equal keys (consecutive vertices
+// share cells and planes) make one atomic.  Also the first sweep of the 3D
+// seed: the vertex farthest from each ROI's first vertex.
+__global__ void k_hist(const int16_t* __restrict__ idx2, const double* __restrict__ vt,
+                       const long long* __restrict__ nv_dev, const RoiDiam* __restrict__ rd,
+                       const RoiOut* __restrict__ ro, Params p, const float* __restrict__ ctab,
+                       int* __restrict__ hist, unsigned long long* __restrict__ sweep, ProblemState* __restrict__ ps) {
   pdl_enter();
+  __shared__ unsigned long long s_key;
   const long long n = min(*nv_dev, p.nv_cap);
   const int lane = threadIdx.x & 31;
   const long long stride = (long long)gridDim.x * blockDim.x;
+  SweepAcc acc;
   for (long long v0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) - lane; v0 < n; v0 += stride) {
     const long long v = v0 + lane;
     int q[3] = {0, 0, 0};
     int roi = 0;
+    float f = 0.0f;
+    unsigned int local = 0;
+    bool sw = false;
     if (v < n) {
       vertex_q(idx2, v, q);
       roi = p.n == 1 ? 0 : roi_of_vertex(ro, p.n, v);
+      sw = ro[roi].nv >= p.sweep_min;
+      if (sw) {
+        const long long first = ro[roi].v0;
+        f = pair_f3(vert_pos(idx2, vt, ctab, rd[roi], first), vert_pos(idx2, vt, ctab, rd[roi], v));
+        local = (unsigned int)(v - first);
+      }
     }
+    if (__any_sync(0xffffffffu, sw)) sweep_step(acc, p.n > 1, sw, roi, f, local, sweep, ps);
     const RoiDiam& r = rd[roi];
     for (int k = 0; k < 4; ++k) {
       const bool use = v < n && (k == 0 || r.planes);
@@ -254,17 +360,23 @@ __global__ void k_hist(const int16_t* __restrict__ idx2, const long long* __rest
       if (key >= 0 && lane == __ffs(peers) - 1) atomicAdd(&hist[key], __popc(peers));
     }
   }
+  sweep_finish(acc, p.n == 1 && blockIdx.x * (long long)blockDim.x < n ? 0 : -1, &s_key, sweep, ps);
 }
 
 
 // The four slot reservations of a warp are issued back to back, so one
 // round trip covers all of them.
+// The second sweep of the 3D seed rides along: each vertex's f to the vertex
+// the first sweep found raises the ROI's 3D F.
 __global__ void k_scatter(const int16_t* __restrict__ idx2, const double* __restrict__ vt,
                           const long long* __restrict__ nv_dev, const RoiDiam* __restrict__ rd,
                           const RoiOut* __restrict__ ro, Params p, const long long* __restrict__ offs,
                           int* __restrict__ cursor, const float* __restrict__ ctab,
-                          float4* __restrict__ sorted, int* __restrict__ ids) {
+                          float4* __restrict__ sorted, int* __restrict__ ids,
+                          const unsigned long long* __restrict__ sweep, ProblemState* __restrict__ ps) {
   pdl_enter();
+  __shared__ unsigned long long s_key;
+  SweepAcc acc;
   const long long n = min(*nv_dev, p.nv_cap);
   const int lane = threadIdx.x & 31;
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -273,25 +385,18 @@ __global__ void k_scatter(const int16_t* __restrict__ idx2, const double* __rest
     int q[3] = {0, 0, 0};
     int roi = 0;
     float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
+    float f2 = 0.0f;
+    bool sw = false;
     if (v < n) {
       vertex_q(idx2, v, q);
       roi = p.n == 1 ? 0 : roi_of_vertex(ro, p.n, v);
       const RoiDiam& r = rd[roi];
-      float px, py, pz;
-      if (vt == nullptr) {  // mask: every coordinate is a doubled grid index, looked up
-        const float* tx = ctab + r.tab0;
-        const float* ty = tx + 2 * r.nx + 3;
-        const float* tz = ty + 2 * r.ny + 3;
-        px = tx[q[0] + 2]; py = ty[q[1] + 2]; pz = tz[q[2] + 2];
-      } else {
-        double u[3];
-        vertex_u(idx2, vt, v, u);
-        px = __double2float_rn((u[0] - r.cx) * r.sx);
-        py = __double2float_rn((u[1] - r.cy) * r.sy);
-        pz = __double2float_rn((u[2] - r.cz) * r.sz);
-      }
-      e = make_float4(px, py, pz, __fadd_rn(__fadd_rn(__fmul_rn(px, px), __fmul_rn(py, py)), __fmul_rn(pz, pz)));
+      const float3 P = vert_pos(idx2, vt, ctab, r, v);
+      e = make_float4(P.x, P.y, P.z, __fadd_rn(__fadd_rn(__fmul_rn(P.x, P.x), __fmul_rn(P.y, P.y)), __fmul_rn(P.z, P.z)));
+      sw = ro[roi].nv >= p.sweep_min;
+      if (sw) f2 = pair_f3(vert_pos(idx2, vt, ctab, r, ro[roi].v0 + (long long)(sweep[roi] & 0xffffffffull)), P);
     }
+    if (__any_sync(0xffffffffu, sw)) sweep_step(acc, p.n > 1, sw, roi, f2, 0u, nullptr, ps);
     const RoiDiam& r = rd[roi];
     long long key[4];
     unsigned int peers[4];
@@ -317,6 +422,7 @@ __global__ void k_scatter(const int16_t* __restrict__ idx2, const double* __rest
       }
     }
   }
+  sweep_finish(acc, p.n == 1 && blockIdx.x * (long long)blockDim.x < n ? 0 : -1, &s_key, nullptr, ps);
 }
 
 // Exclusive scan of the key counts to global offsets, one kernel with a
@@ -443,98 +549,98 @@ __global__ void k_setup(const RoiDiam* __restrict__ rd, Params p, const long lon
     const bool use = len >= 2;
     const unsigned int um = __ballot_sync(0xffffffffu, use);
     if (um == 0) continue;  // warp-uniform
-    // warp-aggregated allocation of slots, tiles and chunks
-    const int nt = use ? (int)((len + p.TS - 1) / p.TS) : 0;
+    // warp-aggregated allocation of slots, walked tiles and chunks, and fine
+    // tiles.  A problem of kBigTiles tiles or more takes two slots: its fine
+    // problem (tiles in the fine region, never walked) and its coarse problem
+    // (walked, one tile per kCoarse fine tiles).
+    const int ntf = use ? (int)((len + p.TS - 1) / p.TS) : 0;
+    const bool big = ntf >= kBigTiles;
+    const int nt = big ? (ntf + kCoarse - 1) / kCoarse : ntf;  // walked tiles
+    const int nslot = use ? (big ? 2 : 1) : 0;
+    const int nfin = big ? ntf : 0;
     const long long S = use ? chunks_upto(nt) : 0;
     const unsigned long long add = use ? ((unsigned long long)S << 32) + (unsigned long long)nt : 0ull;
     unsigned long long inc = add;
+    int sinc = nslot, finc = nfin;
     for (int off = 1; off < 32; off <<= 1) {
       const unsigned long long o = __shfl_up_sync(0xffffffffu, inc, off);
-      if (lane >= off) inc += o;
+      const int os = __shfl_up_sync(0xffffffffu, sinc, off), of = __shfl_up_sync(0xffffffffu, finc, off);
+      if (lane >= off) { inc += o; sinc += os; finc += of; }
     }
     const unsigned long long total = __shfl_sync(0xffffffffu, inc, 31);
+    const int stotal = __shfl_sync(0xffffffffu, sinc, 31), ftotal = __shfl_sync(0xffffffffu, finc, 31);
     int slot0 = 0;
+    unsigned int fine0 = 0;
     unsigned long long old0 = 0;
     if (lane == 0) {
-      slot0 = atomicAdd(&cnt->n_problems, __popc(um));
+      slot0 = atomicAdd(&cnt->n_problems, stotal);
       old0 = atomicAdd(&cnt->alloc, total);
+      if (ftotal) fine0 = atomicAdd(&cnt->alloc_fine, (unsigned int)ftotal);
     }
     slot0 = __shfl_sync(0xffffffffu, slot0, 0);
     old0 = __shfl_sync(0xffffffffu, old0, 0);
+    fine0 = __shfl_sync(0xffffffffu, fine0, 0);
     unsigned long long tp = use ? (unsigned long long)nt * (nt + 1) / 2 : 0ull;
     for (int off = 16; off > 0; off >>= 1) tp += __shfl_xor_sync(0xffffffffu, tp, off);
     if (lane == 0) atomicAdd((unsigned long long*)&cnt->n_pairs, tp);
-    const int slot = slot0 + __popc(um & ((1u << lane) - 1u));
+    const int slot = slot0 + sinc - nslot;
+    const long long fb = (long long)fine0 + finc - nfin;  // first fine tile (region offset)
     const unsigned long long old = old0 + (inc - add);
     const long long tb = (long long)(old & 0xffffffffull);
     const long long cb = (long long)(old >> 32);
-    const bool ok = use && slot < p.max_problems && tb + nt <= p.max_tiles;
+    const bool ok = use && slot + nslot <= p.max_problems && tb + nt <= p.max_tiles && fb + nfin <= p.max_fine;
     // more than 2^31 chunks in one batch (about 740k tiles in one problem):
     // reported, and the chunk walk stays inside the tile array
     const bool ovf = ok && cb + S > (long long)INT_MAX;
     if ((use && !ok) || ovf) atomicOr(&cnt->status, DEV_ERR_PROBCAP);
     const int q = slot_of_axis(axis);
+    const int wslot = big ? slot + 1 : slot;  // slot of the walked problem
     if (ok) {
       Problem pr;
       pr.axis = axis; pr.beg = (int)beg; pr.len = (int)len; pr.tile_beg = (int)tb; pr.roi = roi; pr.q = q;
-      pr.nt = nt; pr.pad = 0;
+      pr.nt = nt; pr.fine = -1;
       pr.chunk_end = ovf ? -1 : cb + S;
-      probs[slot] = pr;
+      if (big) {
+        Problem f = pr;
+        f.tile_beg = (int)(p.max_tiles + fb);
+        f.nt = ntf;
+        f.fine = -2;
+        f.chunk_end = 0;
+        probs[slot] = f;
+        pr.fine = f.tile_beg;
+      }
+      probs[wslot] = pr;
     }
     // the warp marks the tiles of each accepted problem with its slot
     unsigned int wm = __ballot_sync(0xffffffffu, ok);
     while (wm) {
       const int src = __ffs(wm) - 1;
       wm &= wm - 1;
-      const int s_slot = __shfl_sync(0xffffffffu, slot, src), s_nt = __shfl_sync(0xffffffffu, nt, src);
+      const int s_slot = __shfl_sync(0xffffffffu, wslot, src), s_nt = __shfl_sync(0xffffffffu, nt, src);
       const long long s_tb = __shfl_sync(0xffffffffu, tb, src);
       for (int t = lane; t < s_nt; t += 32) chunk0[s_tb + t] = s_slot;
+      const int s_nf = __shfl_sync(0xffffffffu, nfin, src);
+      const long long s_fb = __shfl_sync(0xffffffffu, fb, src);
+      for (int t = lane; t < s_nf; t += 32) chunk0[p.max_tiles + s_fb + t] = s_slot - 1;
     }
   }
 }
 
-// T(F) of every family from its seeded F (FP64, one thread per family).
-__global__ void k_thresh(const RoiDiam* __restrict__ rd, Params p, ProblemState* __restrict__ ps) {
-  pdl_enter();
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 4 * p.n; i += gridDim.x * blockDim.x)
-    ps[i].T = __float_as_uint(threshold(__uint_as_float(ps[i].F), rd[i >> 2]));
-}
-
-// One warp per tile: its record and first seed/cull chunk, the bounding box
-// of its FP32 positions, and its first vertex.
-__global__ void k_tile_box(const float4* __restrict__ sorted, const Problem* __restrict__ probs, Params p,
-                           const Counters* __restrict__ cnt, Tile* __restrict__ tiles, int* __restrict__ chunk0,
-                           float4* __restrict__ box, float4* __restrict__ rep) {
-  pdl_enter();
-  const int nt = (int)min((long long)(cnt->alloc & 0xffffffffull), p.max_tiles);
-  const int np = (int)min((long long)cnt->n_problems, p.max_problems);
+// The box of every coarse tile as the union of its fine tiles' boxes (one
+// warp per walked tile, grid-stride).
+__device__ __noinline__ void coarse_boxes(const Tile* __restrict__ tiles, int nt, float4* __restrict__ box) {
   const int lane = threadIdx.x & 31;
   const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   for (long long ti = warp; ti < nt; ti += nwarps) {
-    const int slot = chunk0[ti];  // the problem's slot, from the setup
-    if ((unsigned int)slot >= (unsigned int)np) continue;  // warp-uniform; not reached (tiles never outrun problems)
-    const Problem pr = probs[slot];
-    const int t = (int)ti - pr.tile_beg;  // tile within its problem
-    if (t < 0 || t >= pr.nt) continue;    // warp-uniform; as above
-    Tile tl;
-    tl.problem = slot;
-    tl.beg = pr.beg + t * p.TS;
-    tl.len = min(p.TS, pr.len - t * p.TS);
-    tl.tile_end = pr.tile_beg + pr.nt;
-    tl.roi = pr.roi;
-    tl.q = pr.q;
-    tl.pad0 = tl.pad1 = 0;
-    __syncwarp();  // every lane has read the slot before lane 0 replaces it
-    if (lane == 0) {
-      tiles[ti] = tl;
-      chunk0[ti] = pr.chunk_end < 0 ? INT_MAX : (int)(pr.chunk_end - chunks_upto(pr.nt - t));
-    }
+    const int nf = tiles[ti].nfine;
+    if (nf == 0) continue;  // warp-uniform
+    const int f0 = tiles[ti].fine0;
     float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
-    for (int i = lane; i < tl.len; i += 32) {
-      const float4 v = sorted[tl.beg + i];
-      lo[0] = fminf(lo[0], v.x); lo[1] = fminf(lo[1], v.y); lo[2] = fminf(lo[2], v.z);
-      hi[0] = fmaxf(hi[0], v.x); hi[1] = fmaxf(hi[1], v.y); hi[2] = fmaxf(hi[2], v.z);
+    if (lane < nf) {
+      const float4 l4 = box[2 * (f0 + lane)], h4 = box[2 * (f0 + lane) + 1];
+      lo[0] = l4.x; lo[1] = l4.y; lo[2] = l4.z;
+      hi[0] = h4.x; hi[1] = h4.y; hi[2] = h4.z;
     }
     for (int off = 16; off > 0; off >>= 1)
       for (int k = 0; k < 3; ++k) {
@@ -544,7 +650,62 @@ __global__ void k_tile_box(const float4* __restrict__ sorted, const Problem* __r
     if (lane == 0) {
       box[2 * ti] = make_float4(lo[0], lo[1], lo[2], 0.f);
       box[2 * ti + 1] = make_float4(hi[0], hi[1], hi[2], 0.f);
+    }
+  }
+}
+
+// One warp per tile (walked tiles, then the fine region): its record and
+// first seed/cull chunk, the bounding box of its FP32 positions (coarse
+// tiles: later, from their fine tiles), and its first vertex.
+__global__ void k_tile_box(const float4* __restrict__ sorted, const Problem* __restrict__ probs, Params p,
+                           const Counters* __restrict__ cnt, Tile* __restrict__ tiles, int* __restrict__ chunk0,
+                           float4* __restrict__ box, float4* __restrict__ rep) {
+  pdl_enter();
+  const int nt = (int)min((long long)(cnt->alloc & 0xffffffffull), p.max_tiles);
+  const int nf = (int)min((long long)cnt->alloc_fine, p.max_fine);
+  const int np = (int)min((long long)cnt->n_problems, p.max_problems);
+  const int lane = threadIdx.x & 31;
+  const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long k = warp; k < (long long)nt + nf; k += nwarps) {
+    const long long ti = k < nt ? k : p.max_tiles + (k - nt);
+    const int slot = chunk0[ti];  // the problem's slot, from the setup
+    if ((unsigned int)slot >= (unsigned int)np) continue;  // warp-uniform; not reached (tiles never outrun problems)
+    const Problem pr = probs[slot];
+    const int t = (int)(ti - pr.tile_beg);  // tile within its problem
+    if (t < 0 || t >= pr.nt) continue;      // warp-uniform; as above
+    const bool coarse = pr.fine >= 0;
+    const int span = coarse ? kCoarse * p.TS : p.TS;
+    Tile tl;
+    tl.problem = slot;
+    tl.beg = pr.beg + t * span;
+    tl.len = min(span, pr.len - t * span);
+    tl.tile_end = pr.tile_beg + pr.nt;
+    tl.roi = pr.roi;
+    tl.q = pr.q;
+    tl.fine0 = coarse ? pr.fine + t * kCoarse : 0;
+    tl.nfine = coarse ? min(kCoarse, (pr.len + p.TS - 1) / p.TS - t * kCoarse) : 0;
+    __syncwarp();  // every lane has read the slot before lane 0 replaces it
+    if (lane == 0) {
+      tiles[ti] = tl;
+      if (k < nt) chunk0[ti] = pr.chunk_end < 0 ? INT_MAX : (int)(pr.chunk_end - chunks_upto(pr.nt - t));
       rep[ti] = sorted[tl.beg];
+    }
+    if (coarse) continue;  // warp-uniform
+    float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+    for (int i = lane; i < tl.len; i += 32) {
+      const float4 v = sorted[tl.beg + i];
+      lo[0] = fminf(lo[0], v.x); lo[1] = fminf(lo[1], v.y); lo[2] = fminf(lo[2], v.z);
+      hi[0] = fmaxf(hi[0], v.x); hi[1] = fmaxf(hi[1], v.y); hi[2] = fmaxf(hi[2], v.z);
+    }
+    for (int off = 16; off > 0; off >>= 1)
+      for (int k2 = 0; k2 < 3; ++k2) {
+        lo[k2] = fminf(lo[k2], __shfl_xor_sync(0xffffffffu, lo[k2], off));
+        hi[k2] = fmaxf(hi[k2], __shfl_xor_sync(0xffffffffu, hi[k2], off));
+      }
+    if (lane == 0) {
+      box[2 * ti] = make_float4(lo[0], lo[1], lo[2], 0.f);
+      box[2 * ti + 1] = make_float4(hi[0], hi[1], hi[2], 0.f);
     }
   }
 }
@@ -619,56 +780,100 @@ __device__ __forceinline__ void seed_flush(float m, int fam, ProblemState* ps) {
 
 // Seed: the pairs of tile representatives (first vertices) in every tile
 // pair of a problem, plus each tile's first-last pair, are actual vertex
-// pairs, so their largest f is a valid starting F.  Five blocks per SM
-// (48 registers): more resident warps for this latency-bound walk measured
+// pairs, so their largest f is a valid starting F.  Before walking, the
+// blocks form the coarse tiles' boxes; the block that finishes last turns
+// every family's F into T(F) for the cull.  Five blocks per SM (48
+// registers): more resident warps for this latency-bound walk measured
 // faster than four or six.
 __global__ void __launch_bounds__(256, 5) k_seed(const float4* __restrict__ sorted, const float4* __restrict__ rep, Params p,
-                       const Tile* __restrict__ tiles, const int* __restrict__ chunk0, const Counters* __restrict__ cnt,
-                       ProblemState* __restrict__ ps) {
+                       const Tile* __restrict__ tiles, const int* __restrict__ chunk0, Counters* __restrict__ cnt,
+                       ProblemState* __restrict__ ps, const RoiDiam* __restrict__ rd, float4* __restrict__ box) {
   pdl_enter();
+  __shared__ bool s_last;
   const unsigned long long alloc = cnt->alloc;
   const int nt = (int)min((long long)(alloc & 0xffffffffull), p.max_tiles);
   const long long K = min((long long)(alloc >> 32), (long long)INT_MAX);
   const int lane = threadIdx.x & 31;
+  if (cnt->alloc_fine) coarse_boxes(tiles, nt, box);  // only when some problem is walked at two levels
   ChunkWalk w;
-  if (!walk_begin(w, chunk0, nt, K)) return;
-  Tile ta = tiles[w.a];
-  float4 ra = rep[w.a];
-  RowAhead nx;
-  row_ahead(nx, tiles, rep, 1, chunk0, nt, w.a);
-  float m = 0.0f;
-  for (; w.k < w.kend; ++w.k) {
-    if (w.k >= w.next0 && w.a + 1 < nt) {  // warp-uniform
-      if (fam_of(nx.t.roi, nx.t.q) != fam_of(ta.roi, ta.q)) {  // one flush per family
-        seed_flush(m, fam_of(ta.roi, ta.q), ps);
-        m = 0.0f;
+  if (walk_begin(w, chunk0, nt, K)) {  // warp-uniform
+    Tile ta = tiles[w.a];
+    float4 ra = rep[w.a];
+    RowAhead nx;
+    row_ahead(nx, tiles, rep, 1, chunk0, nt, w.a);
+    float m = 0.0f;
+    for (; w.k < w.kend; ++w.k) {
+      if (w.k >= w.next0 && w.a + 1 < nt) {  // warp-uniform
+        if (fam_of(nx.t.roi, nx.t.q) != fam_of(ta.roi, ta.q)) {  // one flush per family
+          seed_flush(m, fam_of(ta.roi, ta.q), ps);
+          m = 0.0f;
+        }
+        ++w.a;
+        ta = nx.t;
+        ra = nx.v0;
+        w.c0 = w.next0;
+        w.next0 = nx.next1;
+        row_ahead(nx, tiles, rep, 1, chunk0, nt, w.a);
       }
-      ++w.a;
-      ta = nx.t;
-      ra = nx.v0;
-      w.c0 = w.next0;
-      w.next0 = nx.next1;
-      row_ahead(nx, tiles, rep, 1, chunk0, nt, w.a);
-    }
-    const long long c = w.k - w.c0;
-    const long long b0 = w.a + c * kChunk;
-    if (c == 0 && lane == 0) m = fmaxf(m, pair_f(ra, sorted[ta.beg + ta.len - 1]));
+      const long long c = w.k - w.c0;
+      const long long b0 = w.a + c * kChunk;
+      if (c == 0 && lane == 0) m = fmaxf(m, pair_f(ra, sorted[ta.beg + ta.len - 1]));
 #pragma unroll
-    for (int u = 0; u < kChunk / 32; ++u) {
-      const long long b = b0 + 32 * u + lane;
-      if (b < ta.tile_end) m = fmaxf(m, pair_f(ra, rep[b]));
+      for (int u = 0; u < kChunk / 32; ++u) {
+        const long long b = b0 + 32 * u + lane;
+        if (b < ta.tile_end) m = fmaxf(m, pair_f(ra, rep[b]));
+      }
     }
+    seed_flush(m, fam_of(ta.roi, ta.q), ps);
   }
-  seed_flush(m, fam_of(ta.roi, ta.q), ps);
+  // the block that finishes last turns every family's F into T(F)
+  __threadfence();  // this thread's seeds are visible before the block takes its ticket
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&cnt->seed_done, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  for (int i = threadIdx.x; i < 4 * p.n; i += blockDim.x)
+    ps[i].T = __float_as_uint(threshold(__uint_as_float(__ldcg(&ps[i].F)), rd[i >> 2]));
 }
 
 // Cull: every tile pair (a, b >= a) of a problem whose box bound reaches
 // T(F) goes to the work list, with both vertex ranges and the bound.  Four
 // blocks per SM (64 registers): more resident warps for this latency-bound
 // walk measured faster than the uncapped 76 registers, small spill included.
+// The surviving pairs of one coarse row's chunk (bit l of m[u]: column
+// b0 + 32 u + l) go to the refine list.
+__device__ __noinline__ void cull_coarse(const Tile* __restrict__ tiles, const Params& p, Counters* __restrict__ cnt,
+                                         RefineItem* __restrict__ refine, const Tile& ta, long long b0, int a,
+                                         const unsigned int* m) {
+  constexpr int U = kChunk / 32;
+  const int lane = threadIdx.x & 31;
+  int total = 0;
+  for (int u = 0; u < U; ++u) total += __popc(m[u]);
+  long long rbase = 0;
+  if (lane == 0) rbase = (long long)atomicAdd(&cnt->n_refine, (unsigned int)total);
+  rbase = __shfl_sync(0xffffffffu, rbase, 0);
+  for (int u = 0; u < U; ++u) {
+    if ((m[u] >> lane) & 1u) {
+      const long long slot = rbase + __popc(m[u] & ((1u << lane) - 1u));
+      const long long b = b0 + 32 * u + lane;
+      if (slot < p.refine_cap) {
+        const Tile tb = tiles[b];
+        RefineItem ri;
+        ri.fa = ta.fine0; ri.na = ta.nfine; ri.fb = tb.fine0; ri.nb = tb.nfine;
+        ri.problem = ta.problem - 1; ri.roi = ta.roi; ri.q = ta.q; ri.same = b == a;
+        refine[slot] = ri;
+      } else {
+        atomicOr(&cnt->status, DEV_ERR_WORKCAP);
+      }
+    }
+    rbase += __popc(m[u]);
+  }
+}
+
 __global__ void __launch_bounds__(256, 4) k_cull(const Tile* __restrict__ tiles, const float4* __restrict__ box, Params p,
                        const int* __restrict__ chunk0, Counters* __restrict__ cnt, const ProblemState* __restrict__ ps,
-                       WorkItem* __restrict__ work) {
+                       WorkItem* __restrict__ work, RefineItem* __restrict__ refine) {
   pdl_enter();
   const unsigned long long alloc = cnt->alloc;
   const int nt = (int)min((long long)(alloc & 0xffffffffull), p.max_tiles);
@@ -715,6 +920,10 @@ __global__ void __launch_bounds__(256, 4) k_cull(const Tile* __restrict__ tiles,
       total += __popc(m[u]);
     }
     if (total == 0) continue;  // warp-uniform
+    if (ta.nfine > 0) {  // a coarse row: its surviving pairs are refined by the next kernel
+      cull_coarse(tiles, p, cnt, refine, ta, b0, w.a, m);
+      continue;
+    }
     long long base = 0;
     if (lane == 0) base = (long long)atomicAdd((unsigned long long*)&cnt->n_work, (unsigned long long)total);
     base = __shfl_sync(0xffffffffu, base, 0);
@@ -734,6 +943,74 @@ __global__ void __launch_bounds__(256, 4) k_cull(const Tile* __restrict__ tiles,
         }
       }
       base += __popc(m[u]);
+    }
+  }
+}
+
+// Refinement of the surviving coarse tile pairs, one warp per pair: lane l
+// holds the boxes of fine tile l of both coarse tiles in registers, and the
+// warp tests each fine tile of the first (broadcast by shuffles) against the
+// lanes' fine tiles of the second (only b >= a within one coarse tile).
+// Surviving fine pairs go to the work list.
+__global__ void k_refine(const Tile* __restrict__ tiles, const float4* __restrict__ box, Params p,
+                         Counters* __restrict__ cnt, const ProblemState* __restrict__ ps,
+                         const RefineItem* __restrict__ refine, WorkItem* __restrict__ work) {
+  pdl_enter();
+  const long long nr = min((long long)cnt->n_refine, p.refine_cap);
+  const int lane = threadIdx.x & 31;
+  const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long k = warp; k < nr; k += nwarps) {
+    const RefineItem ri = refine[k];
+    const float T = __uint_as_float(ps[fam_of(ri.roi, ri.q)].T);
+    const bool ha = lane < ri.na, hb = lane < ri.nb;
+    const int a_own = ri.fa + lane, b = ri.fb + lane;
+    float4 alo = make_float4(0.f, 0.f, 0.f, 0.f), ahi = alo, blo = alo, bhi = alo;
+    int bbeg = 0, blen = 0;
+    if (ha) {
+      alo = box[2 * a_own];
+      ahi = box[2 * a_own + 1];
+    }
+    if (hb) {
+      blo = box[2 * b];
+      bhi = box[2 * b + 1];
+      bbeg = tiles[b].beg;
+      blen = tiles[b].len;
+    }
+    unsigned int am = 0u;  // fine tiles of the first coarse tile whose pair with this lane's tile survives
+    for (int ia = 0; ia < ri.na; ++ia) {  // warp-uniform
+      const float4 l4 = make_float4(__shfl_sync(0xffffffffu, alo.x, ia), __shfl_sync(0xffffffffu, alo.y, ia),
+                                    __shfl_sync(0xffffffffu, alo.z, ia), 0.f);
+      const float4 h4 = make_float4(__shfl_sync(0xffffffffu, ahi.x, ia), __shfl_sync(0xffffffffu, ahi.y, ia),
+                                    __shfl_sync(0xffffffffu, ahi.z, ia), 0.f);
+      if (hb && (!ri.same || lane >= ia)) {
+        if (box_ub(l4, h4, blo, bhi) >= T) am |= 1u << ia;
+      }
+    }
+    const int mine = __popc(am);
+    int incl = mine;
+    for (int off = 1; off < 32; off <<= 1) {
+      const int o = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += o;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total == 0) continue;  // warp-uniform
+    long long base = 0;
+    if (lane == 0) base = (long long)atomicAdd((unsigned long long*)&cnt->n_work, (unsigned long long)total);
+    base = __shfl_sync(0xffffffffu, base, 0) + (incl - mine);
+    for (unsigned int mm = am; mm; mm &= mm - 1, ++base) {
+      const int ia = __ffs(mm) - 1;
+      if (base < p.work_cap) {
+        const int a = ri.fa + ia;
+        const Tile ta = tiles[a];
+        WorkItem it;
+        it.problem = ri.problem; it.roi = ri.roi; it.q = ri.q;
+        it.abeg = ta.beg; it.alen = ta.len; it.bbeg = bbeg; it.blen = blen;
+        it.ub = box_ub(box[2 * a], box[2 * a + 1], blo, bhi);
+        work[base] = it;
+      } else {
+        atomicOr(&cnt->status, DEV_ERR_WORKCAP);
+      }
     }
   }
 }
@@ -1069,12 +1346,13 @@ __global__ void k_tiebreak(const int* __restrict__ ids, const int16_t* __restric
   pdl_enter();
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     stats->problems = cnt->n_problems;
-    stats->tiles = (long long)(cnt->alloc & 0xffffffffull);
+    stats->tiles = (long long)(cnt->alloc & 0xffffffffull) + (long long)cnt->alloc_fine;
     stats->tile_pairs = cnt->n_pairs;
     stats->work_items = cnt->n_work;
     stats->items_evaluated = (long long)cnt->items_evaluated;
     stats->pairs_evaluated = (long long)cnt->pairs_evaluated;
     stats->candidates = cnt->n_cand;
+    stats->coarse_pairs = cnt->n_refine;
     stats->status |= cnt->status;
   }
   const long long nc = min(cnt->n_cand, p.cand_cap);
@@ -1241,13 +1519,17 @@ rad_status diam_run(int n, const RoiDiam* rd, const RoiOut* ro, const long long*
   p.nplanes = nplanes;
   const long long nv = std::max<long long>(nv_cap, 2);
   p.nv_cap = nv_cap;
+  p.sweep_min = (long long)kBigTiles * p.TS;  // the ROIs whose 3D problem is walked at two levels
   const long long nsorted = nv * (planes ? 4 : 1);
-  p.max_problems = n + nplanes + 1;
+  p.max_problems = 2 * (n + nplanes) + 2;  // a problem walked at two levels takes two slots
   p.max_tiles = nsorted / p.TS + p.max_problems + 1;
+  p.max_fine = nsorted / p.TS + p.max_problems + 1;
   if (s.work_cap == 0) s.work_cap = 1 << 20;
   if (s.cand_cap == 0) s.cand_cap = 1 << 20;
   p.work_cap = s.work_cap;
   p.cand_cap = s.cand_cap;
+  p.refine_cap = std::max<long long>(4096, s.work_cap / 8);  // grows with the work list
+  const long long ntiles = p.max_tiles + p.max_fine;
 
   // scratch layout (hist/offsets carry one extra entry: offs[K] = total)
   const long long K1 = nkeys + 1;
@@ -1261,11 +1543,12 @@ rad_status diam_run(int n, const RoiDiam* rd, const RoiOut* ro, const long long*
   add(sizeof(float4) * nsorted);
   add(sizeof(int) * nsorted);  // vertex id of every sorted entry
   add(sizeof(Problem) * p.max_problems);
-  add(sizeof(Tile) * p.max_tiles);
-  add(sizeof(int) * p.max_tiles);    // chunk0
-  add(sizeof(float4) * 2 * p.max_tiles);
-  add(sizeof(float4) * p.max_tiles);
-  add(sizeof(ProblemState) * 4 * n);
+  add(sizeof(Tile) * ntiles);
+  add(sizeof(int) * ntiles);    // chunk0
+  add(sizeof(float4) * 2 * ntiles);
+  add(sizeof(float4) * ntiles);
+  add(sizeof(ProblemState) * 4 * n + sizeof(unsigned long long) * n);  // family states, sweep slots
+  add(sizeof(RefineItem) * p.refine_cap);
   add(sizeof(Counters));
   add(sizeof(WorkItem) * p.work_cap);
   add(sizeof(float) * 8 * p.work_cap);  // slice maxima (up to 8 slices per item)
@@ -1283,11 +1566,15 @@ rad_status diam_run(int n, const RoiDiam* rd, const RoiOut* ro, const long long*
   float4* sorted = carve<float4>(cur, nsorted);
   int* ids = carve<int>(cur, nsorted);
   Problem* probs = carve<Problem>(cur, p.max_problems);
-  Tile* tiles = carve<Tile>(cur, p.max_tiles);
-  int* chunk0 = carve<int>(cur, p.max_tiles);
-  float4* box = carve<float4>(cur, 2 * p.max_tiles);
-  float4* rep = carve<float4>(cur, p.max_tiles);
-  ProblemState* ps = carve<ProblemState>(cur, 4 * n);
+  Tile* tiles = carve<Tile>(cur, ntiles);
+  int* chunk0 = carve<int>(cur, ntiles);
+  float4* box = carve<float4>(cur, 2 * ntiles);
+  float4* rep = carve<float4>(cur, ntiles);
+  const size_t fam_bytes = sizeof(ProblemState) * 4 * n + sizeof(unsigned long long) * n;
+  char* fam_state = carve<char>(cur, fam_bytes);
+  ProblemState* ps = reinterpret_cast<ProblemState*>(fam_state);
+  unsigned long long* sweep = reinterpret_cast<unsigned long long*>(fam_state + sizeof(ProblemState) * 4 * n);
+  RefineItem* refine = carve<RefineItem>(cur, p.refine_cap);
   Counters* cnt = carve<Counters>(cur, 1);
   WorkItem* work = carve<WorkItem>(cur, p.work_cap);
   float* slicemax = carve<float>(cur, 8 * p.work_cap);
@@ -1302,7 +1589,7 @@ rad_status diam_run(int n, const RoiDiam* rd, const RoiOut* ro, const long long*
   zero_add(zs, cnt, sizeof(Counters));
   zero_add(zs, scan_state, sizeof(ScanTile<1>) * nparts + 16);
   zero_add(zs, stats, sizeof(DiamStats));
-  zero_add(zs, ps, sizeof(ProblemState) * 4 * n);  // F = T = 0 for every family
+  zero_add(zs, fam_state, fam_bytes);  // F = T = 0 for every family; sweep slots
   if (which & 1) {
     // on its own (a graph branch beside the mesh) it needs few CTAs: a few MB zeroed
     const long long init_ctas = (std::max(K1, ntab) + 255) / 256;
@@ -1311,18 +1598,22 @@ rad_status diam_run(int n, const RoiDiam* rd, const RoiOut* ro, const long long*
                out, n, zs, rd, ctab, planes ? ntab : 0);
   }
   if (!(which & 2)) return RAD_OK;
-  RAD_LAUNCH("diam_hist", k_hist, wave_grid(k_hist, 256, (nv + 255) / 256), 256, 0, st, idx2, nv_dev, rd, ro, p, hist);
+  RAD_LAUNCH("diam_hist", k_hist, wave_grid(k_hist, 256, (nv + 255) / 256), 256, 0, st, idx2, vt, nv_dev, rd, ro, p,
+             ctab, hist, sweep, ps);
   RAD_LAUNCH("diam_scan", k_xscan, (int)nparts, kScanThreads, 0, st, hist, K1, (int)nparts, offs, stiles, stick,
              &cnt->status);
   RAD_LAUNCH("diam_scatter", k_scatter, wave_grid(k_scatter, 256, (nv + 255) / 256), 256, 0, st, idx2, vt, nv_dev, rd,
-             ro, p, offs, cursor, ctab, sorted, ids);
+             ro, p, offs, cursor, ctab, sorted, ids, sweep, ps);
   RAD_LAUNCH("diam_setup", k_setup, wave_grid(k_setup, 256, (n + nplanes + 255) / 256 + 1), 256, 0, st, rd, p, offs,
              probs, chunk0, cnt);
   RAD_LAUNCH("diam_tile_box", k_tile_box, wave_grid(k_tile_box, 256, 1LL << 30), 256, 0, st, sorted, probs, p, cnt,
              tiles, chunk0, box, rep);
-  RAD_LAUNCH("diam_seed", k_seed, wave_grid(k_seed, 256, 1LL << 30), 256, 0, st, sorted, rep, p, tiles, chunk0, cnt, ps);
-  RAD_LAUNCH("diam_thresh", k_thresh, std::max(1, std::min(sms * 2, (4 * n + 255) / 256)), 256, 0, st, rd, p, ps);
-  RAD_LAUNCH("diam_cull", k_cull, wave_grid(k_cull, 256, 1LL << 30), 256, 0, st, tiles, box, p, chunk0, cnt, ps, work);
+  RAD_LAUNCH("diam_seed", k_seed, wave_grid(k_seed, 256, 1LL << 30), 256, 0, st, sorted, rep, p, tiles, chunk0, cnt, ps,
+             rd, box);
+  RAD_LAUNCH("diam_cull", k_cull, wave_grid(k_cull, 256, 1LL << 30), 256, 0, st, tiles, box, p, chunk0, cnt, ps, work,
+             refine);
+  RAD_LAUNCH("diam_refine", k_refine, wave_grid(k_refine, 256, std::max<long long>(1, p.refine_cap / 8)), 256, 0, st,
+             tiles, box, p, cnt, ps, refine, work);
   const int ctas = sms * tu.ctas_per_sm;
   if (tu.tile == 64) {
     if (tu.threads == 64) RAD_TRY((launch_pairs<64, 64>(sorted, work, p, rd, cnt, ps, slicemax, hits, cand, ctas, st)));

@@ -283,7 +283,7 @@ struct DiamOut {
 
 struct DiamStats {
   long long problems, tiles, tile_pairs, work_items, items_evaluated, pairs_evaluated, candidates;
-  unsigned int status, pad;
+  unsigned int status, coarse_pairs;
 };
 
 // Result of the plain FP64 kernel (one mask).

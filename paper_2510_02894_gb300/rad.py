@@ -59,7 +59,8 @@ class Tuning(ctypes.Structure):
 
 class CallStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("h2d_bytes", "d2h_bytes", "problems", "tiles", "tile_pairs",
-                                               "work_items", "items_evaluated", "pairs_evaluated", "candidates")]
+                                               "work_items", "items_evaluated", "pairs_evaluated", "candidates",
+                                               "coarse_pairs")]
 
 
 class KernelStat(ctypes.Structure):
