@@ -284,7 +284,63 @@ def features(data, spacing, method="auto"):
         "argmax_row": diam[3][1:],
         "d2": [d[0] for d in diam],
     }
+    out.update(derived_features(m.volume, m.area, data, sp))
     return out, m
+
+
+DERIVED_NAMES = ("Sphericity", "SurfaceVolumeRatio", "Compactness1", "Compactness2", "SphericalDisproportion",
+                 "MajorAxisLength", "MinorAxisLength", "LeastAxisLength", "Elongation", "Flatness")
+
+
+def derived_features(volume, area, mask, spacing):
+    """The rest of the Shape class (paper Sec. 2 names the Shape class the
+    method accelerates), written from the standard definitions in plain FP64:
+
+      Sphericity             = (36 pi V^2)^(1/3) / A
+      SurfaceVolumeRatio     = A / V
+      Compactness1           = V / (sqrt(pi) A^(3/2))
+      Compactness2           = 36 pi V^2 / A^3
+      SphericalDisproportion = A / (36 pi V^2)^(1/3)
+
+    with V the mesh volume and A the surface area, and, from the eigenvalues
+    l1 >= l2 >= l3 of the covariance (1/N normalisation) of the physical
+    coordinates of the N inside voxel centres,
+
+      Major/Minor/LeastAxisLength = 4 sqrt(l1), 4 sqrt(l2), 4 sqrt(l3)
+      Elongation = sqrt(l2 / l1),  Flatness = sqrt(l3 / l1).
+
+    Readings: a feature with a zero denominator is 0; eigenvalues below 0
+    (rounding) count as 0."""
+    V, A = float(volume), float(area)
+    out = {}
+    k = (36.0 * np.pi * V * V) ** (1.0 / 3.0)
+    out["Sphericity"] = k / A if A > 0 else 0.0
+    out["SurfaceVolumeRatio"] = A / V if V > 0 else 0.0
+    out["Compactness1"] = V / (np.sqrt(np.pi) * A ** 1.5) if A > 0 else 0.0
+    out["Compactness2"] = 36.0 * np.pi * V * V / A ** 3 if A > 0 else 0.0
+    out["SphericalDisproportion"] = A / k if k > 0 else 0.0
+    lam = covariance_eigenvalues(mask, spacing)
+    l1, l2, l3 = (max(float(x), 0.0) for x in lam)
+    out["MajorAxisLength"] = 4.0 * np.sqrt(l1)
+    out["MinorAxisLength"] = 4.0 * np.sqrt(l2)
+    out["LeastAxisLength"] = 4.0 * np.sqrt(l3)
+    out["Elongation"] = float(np.sqrt(l2 / l1)) if l1 > 0 else 0.0
+    out["Flatness"] = float(np.sqrt(l3 / l1)) if l1 > 0 else 0.0
+    return out
+
+
+def covariance_eigenvalues(mask, spacing):
+    """Eigenvalues (descending) of sum (p - m)(p - m)^T / N over the inside
+    voxel centres p = (x sx, y sy, z sz) of a [nz][ny][nx] mask, m their mean."""
+    arr = np.asarray(mask)
+    inside = arr > 0.5 if arr.dtype.kind == "f" else arr != 0
+    zyx = np.argwhere(inside)
+    if zyx.shape[0] == 0:
+        return np.zeros(3)
+    P = zyx[:, ::-1].astype(np.float64) * np.asarray(spacing, np.float64)
+    D = P - P.mean(axis=0)
+    C = D.T @ D / P.shape[0]
+    return np.sort(np.linalg.eigvalsh(C))[::-1]
 
 
 def soft_grad(mesh, gA, gV, gD, argmax3d=(-1, -1)):
