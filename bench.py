@@ -47,22 +47,21 @@ def load_peaks():
 
 
 def load_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu table, or None
-    when the table has no row for it or the kernel's source file changed since
-    the counters were taken (its sha256 no longer matches)."""
+    """DRAM bytes per launch of `kernel` (dram__bytes_read.sum + write.sum) from
+    the committed ncu table profiles/dram_traffic.json, or None when the table
+    has no entry for it or the kernel's source file changed since the counters
+    were taken (its sha256 no longer matches)."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "dram_traffic_ct512.md")
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
     if not os.path.exists(path):
         return None
-    for line in open(path):
-        cells = [c.strip() for c in line.strip().strip("|").split("|")]
-        if len(cells) != 6 or cells[0] != kernel:
-            continue
-        src = os.path.join(ROOT, cells[2])
-        if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != cells[3]:
-            return None
-        return int(cells[4]) + int(cells[5])
-    return None
+    entry = json.load(open(path)).get("kernels", {}).get(kernel)
+    if not entry:
+        return None
+    src = os.path.join(ROOT, entry["source"])
+    if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != entry["sha256_16"]:
+        return None
+    return int(entry["dram_bytes_read"]) + int(entry["dram_bytes_write"])
 
 
 class ClockSampler:
@@ -155,25 +154,185 @@ def job_throughput(units_per_rank, ms_max, world):
 def kernel_work(name, ctx):
     """Algorithmic work of one launch of `name`: ("hbm", bytes) or ("alu", FP32 flops).
 
-    Bytes count what the kernel must move at least once (its inputs read, its
-    outputs written); flops count the evaluated vertex pairs of the FP32
-    filter at 8 flops each."""
-    nvox, words4, N, T, R, na = (ctx[k] for k in ("nvox", "bitset_bytes", "N", "T", "rows", "cubes"))
-    W = ctx["words_per_row"]
+    Bytes count what the kernel must move at least once: the mask read and the
+    bitset written (pack), the bitset read and the per-row counts written
+    (count), the vertex and triangle output of the surface (emit: 18 B per
+    vertex and 12 B per triangle), the vertices read and the sorted entries
+    written (diameter sort).  Flops count the evaluated vertex pairs of the
+    FP32 filter at 8 flops each."""
+    nvox, words4, N, T, R = (ctx[k] for k in ("nvox", "bitset_bytes", "N", "T", "rows"))
     table = {
-        "mc_pack_u8": nvox + words4,                    # mask in, bitset out
-        "mc_count": words4 + 16 * R + 4 * R * W,        # bitset in, row counts + word prefixes out
-        "mc_emit": words4 + 4 * R * W + 32 * R + 6 * N + 12 * T,  # bitset, word prefixes, row bases in;
-                                                                    # vertices and triangles out
-        "mc_scan_chunks": 16 * R + 32 * R,              # row counts in, row prefixes out
-        "diam_hist": 6 * N,                             # vertices in
-        "diam_scatter": 6 * N + 4 * 16 * N,             # vertices in, sorted entries out
+        "mc_pack_u8": nvox + words4,
+        "mc_count": words4 + 16 * R,
+        "mc_emit": 18 * N + 12 * T,
+        "diam_hist": 6 * N,
+        "diam_scatter": 6 * N + 4 * 20 * N,
     }
     if name == "diam_pairs_fp32":
         return "alu", FLOPS_PER_PAIR * ctx["pairs_evaluated"]
     if name in table:
         return "hbm", table[name]
     return None, None
+
+
+MESH_KERNELS = ("mc_pack_u8", "mc_count", "mc_scan_rows", "mc_emit")
+
+
+def mesh_stage_roofline(kernels, ctx, peak_gbs, steps):
+    """The marching-cubes stage as a whole: mask in, vertices and triangles out
+    (nvox + 18 N + 12 T bytes) over the summed per-kernel times of its kernels."""
+    ms = sum(kernels[k]["total_ms"] for k in MESH_KERNELS if k in kernels) / steps
+    if ms <= 0:
+        return None
+    b = ctx["nvox"] + 18 * ctx["N"] + 12 * ctx["T"]
+    gbs = b / (ms / 1e3) / 1e9
+    return {"kernels": list(MESH_KERNELS), "ms": ms, "algorithmic_bytes": b, "achieved": gbs, "peak": peak_gbs,
+            "unit": "GB/s", "frac": gbs / peak_gbs}
+
+
+def timed(fn, steps, stream, flush):
+    """Device milliseconds of fn() per call (CUDA events on `stream`, L2 flushed
+    before each call) and host microseconds per call (wall clock)."""
+    import torch
+    dev_ms, host_us = [], []
+    for _ in range(steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        host_us.append((time.perf_counter() - t0) * 1e6)
+        dev_ms.append(e0.elapsed_time(e1))
+    return statistics.median(dev_ms), statistics.median(host_us)
+
+
+def bench_c1(args, stream, flush):
+    """Per-ROI latency of a 32^3 ellipsoid through rad_extract (the pass
+    replayed as one CUDA graph; results read back to the host every call)."""
+    import torch
+    from paper_2510_02894_gb300 import rad, synth
+    m, sp = synth.ellipsoid_32(0)
+    dev = torch.from_numpy(m).cuda()
+    ws_new = rad.Workspace()
+    t0 = time.perf_counter()
+    rad.extract(dev, sp, ws_new)  # first call of a new workspace: allocation, tables from the cache
+    first_us = (time.perf_counter() - t0) * 1e6
+    ws = rad.Workspace()
+    for _ in range(max(args.warmup, 3)):
+        f = rad.extract(dev, sp, ws)
+    launches0 = rad.launch_count()
+    dms, hus = timed(lambda: rad.extract(dev, sp, ws), max(args.steps, 50), stream, flush)
+    return {"workload": "ellipsoid_32: 32^3 uint8, semi-axes (10,7,5), spacing (1,1,1), seed 0",
+            "n_vertices": f["n_vertices"], "latency_us": hus, "device_us": dms * 1e3,
+            "first_call_new_workspace_us": first_us, "rois_per_s": 1e6 / hus,
+            "gpu_launches_per_call": (rad.launch_count() - launches0) / max(args.steps, 50),
+            "timing": "median of calls; host wall clock from the call to the features on the host"}
+
+
+def bench_c4(args, stream, flush, peak_gbs):
+    """Soft 160^3 map: rad_soft_forward + rad_soft_backward per step."""
+    import torch
+    from paper_2510_02894_gb300 import rad, synth
+    prob_np, sp = synth.soft_160(0)
+    prob = torch.from_numpy(prob_np).cuda()
+    grad = torch.empty(prob.shape, dtype=torch.float64, device="cuda")
+    ws = rad.Workspace()
+    gout = (1.0, 1.0, 1.0)
+    box = {}
+
+    def fwd():
+        box["f"] = rad.soft_forward(prob, sp, ws)
+
+    def bwd():
+        rad.soft_backward(prob, sp, gout, box["f"][1], grad, ws)
+
+    def both():
+        fwd()
+        bwd()
+    for _ in range(max(args.warmup, 3)):
+        both()
+    steps = max(args.steps, 10)
+    f_ms, _ = timed(fwd, steps, stream, flush)
+    b_ms, _ = timed(bwd, steps, stream, flush)
+    t_ms, t_us = timed(both, steps, stream, flush)
+    nvox = prob.numel()
+    algo = nvox * (4 + 4 + 8)  # forward reads 4 B/voxel; backward reads 4 B and writes the FP64 gradient
+    gbs = algo / (t_ms / 1e3) / 1e9
+    return {"workload": "soft_160: 160^3 float32 sigmoid(4 G_3(sd)) of a rotated ellipsoid, seed 0",
+            "forward_ms": f_ms, "backward_ms": b_ms, "fwd_bwd_ms": t_ms, "fwd_bwd_host_us": t_us,
+            "algorithmic_bytes": algo, "achieved_gbs": gbs, "hbm_frac": gbs / peak_gbs,
+            "bytes_note": "4 B/voxel read (forward) + 4 B/voxel read + 8 B/voxel FP64 gradient written (backward)"}
+
+
+def bench_c5(args, stream, flush):
+    """8 x 512^3 blobs as one batch (one set of launches, replayed as one CUDA graph)."""
+    import torch
+    from paper_2510_02894_gb300 import rad, synth
+    blobs = synth.blobs_512(0)
+    devs = [torch.from_numpy(m).cuda() for m, _ in blobs]
+    sps = [s for _, s in blobs]
+    del blobs
+    b = rad.Batch(devs, sps)
+    feats = None
+    for _ in range(max(args.warmup, 3)):
+        feats = b.run()
+    steps = max(min(args.steps, 10), 3)
+    ms, _ = timed(b.run, steps, stream, flush)
+    st = rad.last_call_stats()
+    pairs = sum(f["n_vertices"] * (f["n_vertices"] - 1) / 2 for f in feats)
+    out = {"workload": "blobs_512x8: 8 x 512^3 uint8 smoothed-noise blobs, ~40% filled, spacing (0.6,0.6,1.2), "
+                       "seed 0", "rois": len(devs), "ms": ms, "rois_per_s": len(devs) / (ms / 1e3),
+           "vertex_pairs_per_s": pairs / (ms / 1e3), "n_vertices": [f["n_vertices"] for f in feats],
+           "pairs_evaluated_fp32": st["pairs_evaluated"], "voxels": int(sum(d.numel() for d in devs))}
+    del b, devs
+    torch.cuda.empty_cache()
+    return out
+
+
+def ablation_ct(m, ref, keys, stream):
+    """The FP64 accumulation variants (rad_shape_fp64_variant 1-6) on one mesh:
+    milliseconds per call and whether the results equal the FP32-filter engine's."""
+    import torch
+    from paper_2510_02894_gb300 import rad
+    out = {}
+    for name, v in rad.FP64_VARIANTS.items():
+        rad.shape_fp64_variant(m, v)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        f = rad.shape_fp64_variant(m, v)
+        e1.record(stream)
+        e1.synchronize()
+        out[name] = {"ms": e0.elapsed_time(e1), "identical": all(f[k] == ref[k] for k in keys)}
+    return out
+
+
+def ablation_batch(crops, stream):
+    """The same variants over the 256 crops, one mesh per crop (meshes built
+    first, outside the timing): total milliseconds per variant."""
+    import torch
+    from paper_2510_02894_gb300 import rad
+    meshes = [rad.mesh(torch.from_numpy(c).cuda(), sp) for c, sp in crops]
+    keys = ("Maximum3DDiameter", "argmax3d", "Maximum2DDiameterSlice", "argmax_slice")
+    base = [rad.shape(mm) for mm in meshes]
+    out = {}
+    for name, v in rad.FP64_VARIANTS.items():
+        for mm in meshes[:4]:
+            rad.shape_fp64_variant(mm, v)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = [rad.shape_fp64_variant(mm, v) for mm in meshes]
+        e1.record(stream)
+        e1.synchronize()
+        same = all(r[k] == b[k] for r, b in zip(res, base) for k in keys)
+        out[name] = {"ms": e0.elapsed_time(e1), "identical": bool(same)}
+    return out
 
 
 def oracle_sample(mask, sp, n_slices, m_pairs_vertices):
@@ -216,11 +375,12 @@ def run_reference(args):
     value = statistics.mean(vals)
     sample = (f"per step: oracle mesh of 16 central of 256 z-slices (time scaled x16) + brute-force pairs of "
               f"{m} vertices ({m * (m - 1) // 2} pairs), extrapolated to N={N} ({pairs:.3e} pairs)")
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+    line = {"impl": "reference", "extrapolated": True, "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_vertices": N},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                             "extrapolated": True},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -236,6 +396,9 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-configs", action="store_true", help="skip the 32^3, soft 160^3 and 8 x 512^3 lines")
+    ap.add_argument("--ablation", action="store_true",
+                    help="also time the FP64 accumulation variants on the CT mesh and the 256 crops")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -377,11 +540,25 @@ def main():
         e1.record(stream)
         e1.synchronize()
         fms = e0.elapsed_time(e1)
-        same = all(fp[k] == ff[k] for k in ("Maximum3DDiameter", "Maximum2DDiameterSlice", "Maximum2DDiameterColumn",
-                                            "Maximum2DDiameterRow", "argmax3d", "argmax_slice", "argmax_column",
-                                            "argmax_row"))
+        keys = ("Maximum3DDiameter", "Maximum2DDiameterSlice", "Maximum2DDiameterColumn", "Maximum2DDiameterRow",
+                "argmax3d", "argmax_slice", "argmax_column", "argmax_row")
+        for _ in range(3):
+            rad.shape_fp64_variant(m, rad.FP64_CULLED)
+        e0.record(stream)
+        fc = rad.shape_fp64_variant(m, rad.FP64_CULLED)
+        e1.record(stream)
+        e1.synchronize()
+        cms = e0.elapsed_time(e1)
+        cstats = rad.last_call_stats()
+        same = all(fp[k] == ff[k] and fc[k] == ff[k] for k in keys)
         plain = {"ms": pms, "pairs_per_s": pairs / (pms / 1e3), "fp32_filter_shape_ms": fms,
-                 "speedup_vs_plain": pms / fms, "identical_results": bool(same)}
+                 "culled_fp64_shape_ms": cms, "culled_fp64_pairs_evaluated": cstats["pairs_evaluated"],
+                 "speedup_vs_plain": pms / fms, "fp32_filter_speedup_vs_culled_fp64": cms / fms,
+                 "identical_results": bool(same),
+                 "note": "plain = all pairs in FP64; culled_fp64 = the same tile walk and culling as the FP32 "
+                         "filter, every surviving pair in FP64; shape timings from a built mesh (rad_shape)"}
+        if args.ablation:
+            plain["ablation"] = ablation_ct(m, ff, keys, stream)
 
     # ---- batched crops: 256 ROIs in one set of launches (one CUDA graph) -----------
     batch = None
@@ -430,14 +607,23 @@ def main():
                  "mode": "rad_batch_run: one launch per stage over all 256 ROIs, replayed as one CUDA graph",
                  "pairs_evaluated_fp32": bs["pairs_evaluated"], "tuning": rad.get_tuning(),
                  "diam_stats": bs, "kernels": batch_kernels}
+        if args.ablation:
+            batch["ablation"] = ablation_batch(crops, stream)
         rad.set_tuning(**tuning_main)
+
+    # ---- the other workloads: 32^3 latency, soft 160^3 forward + adjoint, 8 x 512^3 batch ----
+    configs = {}
+    if not args.no_configs:
+        configs["c1"] = bench_c1(args, stream, flush)
+        configs["c4"] = bench_c4(args, stream, flush, peaks["hbm_gbs"])
+        configs["c5"] = bench_c5(args, stream, flush)
 
     # ---- CPU baseline: the oracle on a bounded sample --------------------------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t_mesh, rate, cores, m = oracle_sample(mask, sp, 16, 60000)
         full_s = t_mesh + pairs / rate
-        cpu = {"value": pairs / full_s, "unit": UNIT, "cores": cores, "kind": "oracle",
+        cpu = {"value": pairs / full_s, "unit": UNIT, "cores": cores, "kind": "oracle", "extrapolated": True,
                "sample": (f"oracle mesh of 16 central of 256 z-slices (time x16) + FP64 brute-force pairs of {m} "
                           f"vertices, extrapolated to all {pairs:.3e} pairs (mesh {t_mesh:.2f} s, "
                           f"{rate:.3e} pairs/s)")}
@@ -450,10 +636,11 @@ def main():
                            "pairs_evaluated_fp32": d["pairs_evaluated"], "l2": "flushed between steps (256 MB write)",
                            "parallelism": f"replicas x{world}", "diam_stats": stats, "tuning": tuning_main,
                            "autotune": tuned},
-                "roofline": roof, "kernels": kernel_table, "ms_per_step_with_kernel_events": statistics.mean(prof_ms),
+                "roofline": roof, "mesh_stage": mesh_stage_roofline(kernels, d, peaks["hbm_gbs"], args.steps),
+                "kernels": kernel_table, "ms_per_step_with_kernel_events": statistics.mean(prof_ms),
                 "e2e": {"value": job_throughput(pairs, e2e, world), "unit": UNIT, "ms_per_step": e2e,
                         "h2d_bytes_per_step": hstats["h2d_bytes"], "d2h_bytes_per_step": hstats["d2h_bytes"]},
-                "plain_fp64": plain, "batched": batch, "cpu_baseline": cpu, "clocks": clk,
+                "plain_fp64": plain, "batched": batch, "configs": configs, "cpu_baseline": cpu, "clocks": clk,
                 "gpu_launches": launches, "gpu_launches_per_step": launches / args.steps}
         print(json.dumps(line))
     if world > 1:

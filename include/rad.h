@@ -52,7 +52,17 @@ typedef enum {
   RAD_ERR_INTERNAL = 6     /* a device-side consistency check failed */
 } rad_status;
 
-/* Features of one mask (names as in PyRadiomics' Shape class). */
+/* Features of one mask (names as in PyRadiomics' Shape class).
+ * The derived features follow the standard Shape-class definitions, with V =
+ * MeshVolume and A = SurfaceArea:
+ *   Sphericity = (36 pi V^2)^(1/3) / A, SurfaceVolumeRatio = A / V,
+ *   Compactness1 = V / (sqrt(pi) A^(3/2)), Compactness2 = 36 pi V^2 / A^3,
+ *   SphericalDisproportion = A / (36 pi V^2)^(1/3);
+ * and, from the eigenvalues l1 >= l2 >= l3 of the covariance (1/N) of the
+ * physical coordinates of the N inside voxel centres:
+ *   Major/Minor/LeastAxisLength = 4 sqrt(l1), 4 sqrt(l2), 4 sqrt(l3),
+ *   Elongation = sqrt(l2 / l1), Flatness = sqrt(l3 / l1).
+ * A feature with a zero denominator is 0. */
 typedef struct {
   double MeshVolume, SurfaceArea, VoxelVolume;
   double Maximum3DDiameter, Maximum2DDiameterSlice, Maximum2DDiameterColumn, Maximum2DDiameterRow;
@@ -60,6 +70,8 @@ typedef struct {
   int32_t argmax3d[2], argmax_slice[2], argmax_column[2], argmax_row[2];
   int32_t status; /* rad_status of this mask (batched calls) */
   int32_t _pad;
+  double Sphericity, SurfaceVolumeRatio, Compactness1, Compactness2, SphericalDisproportion;
+  double MajorAxisLength, MinorAxisLength, LeastAxisLength, Elongation, Flatness;
 } rad_features_t;
 
 /* A mesh on the device.  Zero-initialise before the first rad_mesh(); the
@@ -114,6 +126,40 @@ rad_status rad_shape(const rad_mesh_t* mesh, rad_features_t* out, void* stream);
  * strip of pairs, no culling, no FP32 filter): the comparison kernel.
  * Writes all features of the mesh to *out.  Synchronises `stream`. */
 rad_status rad_shape_plain_fp64(const rad_mesh_t* mesh, rad_features_t* out, void* stream);
+
+/* Accumulation patterns of the FP64 diameter search (Sec. 3, "Optimization
+ * research and results", optimisation steps (1)-(5), Fig. 3), plus the
+ * culled search of rad_shape with FP64 in place of the FP32 filter:
+ *   RAD_FP64_EQUAL_LOAD     (1) equal runs of pairs per thread, vertices read
+ *                               from global memory, every improvement pushed
+ *                               to the global result by an atomic;
+ *   RAD_FP64_BLOCK_ATOMICS  (2) as (1), improvements kept per block in shared
+ *                               memory, one global atomic per block;
+ *   RAD_FP64_SHARED_2D      (3) tile pairs per block, the partner tile staged
+ *                               in shared memory as a [vertex][xyz] array,
+ *                               block result in shared memory as in (2);
+ *   RAD_FP64_THREAD_LOCAL   (4) as (3) with per-thread maxima in registers,
+ *                               merged once per block;
+ *   RAD_FP64_PLAIN_1D       (5) per-coordinate 1D shared arrays, per-thread
+ *                               maxima, one partial per block and a final
+ *                               pass: the kernel of rad_shape_plain_fp64;
+ *   RAD_FP64_CULLED             the tile walk and bounding-box culling of
+ *                               rad_shape, every surviving pair evaluated in
+ *                               FP64 (no FP32 filter, no candidate list).
+ * Every variant returns the exact FP64 maxima with the smallest (i, j) on
+ * ties, identical to rad_shape.  Any other value gives RAD_ERR_INVALID_ARG. */
+enum {
+  RAD_FP64_EQUAL_LOAD = 1,
+  RAD_FP64_BLOCK_ATOMICS = 2,
+  RAD_FP64_SHARED_2D = 3,
+  RAD_FP64_THREAD_LOCAL = 4,
+  RAD_FP64_PLAIN_1D = 5,
+  RAD_FP64_CULLED = 6
+};
+
+/* Diameters of `mesh` by one of the variants above; all features of the
+ * mesh to *out (host).  Synchronises `stream`. */
+rad_status rad_shape_fp64_variant(const rad_mesh_t* mesh, int variant, rad_features_t* out, void* stream);
 
 /* Whole path for one device mask: mesh + shape with library-owned buffers
  * kept in `ws` between calls (one host synchronisation per call, none

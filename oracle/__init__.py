@@ -333,14 +333,29 @@ def covariance_eigenvalues(mask, spacing):
     """Eigenvalues (descending) of sum (p - m)(p - m)^T / N over the inside
     voxel centres p = (x sx, y sy, z sz) of a [nz][ny][nx] mask, m their mean."""
     arr = np.asarray(mask)
-    inside = arr > 0.5 if arr.dtype.kind == "f" else arr != 0
-    zyx = np.argwhere(inside)
-    if zyx.shape[0] == 0:
+    sp = np.asarray(spacing, np.float64)
+    slab = 16  # z-slices per step: large masks stay within memory
+
+    def points(z0):
+        part = arr[z0:z0 + slab]
+        inside = part > 0.5 if arr.dtype.kind == "f" else part != 0
+        zyx = np.argwhere(inside)
+        zyx[:, 0] += z0
+        return zyx[:, ::-1].astype(np.float64) * sp
+
+    n, total = 0, np.zeros(3)
+    for z0 in range(0, arr.shape[0], slab):  # first pass: the mean
+        P = points(z0)
+        n += P.shape[0]
+        total += P.sum(axis=0)
+    if n == 0:
         return np.zeros(3)
-    P = zyx[:, ::-1].astype(np.float64) * np.asarray(spacing, np.float64)
-    D = P - P.mean(axis=0)
-    C = D.T @ D / P.shape[0]
-    return np.sort(np.linalg.eigvalsh(C))[::-1]
+    mean = total / n
+    C = np.zeros((3, 3))
+    for z0 in range(0, arr.shape[0], slab):  # second pass: sum of (p - m)(p - m)^T
+        D = points(z0) - mean
+        C += D.T @ D
+    return np.sort(np.linalg.eigvalsh(C / n))[::-1]
 
 
 def soft_grad(mesh, gA, gV, gD, argmax3d=(-1, -1)):

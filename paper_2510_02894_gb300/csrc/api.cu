@@ -270,9 +270,9 @@ __global__ void k_wait_probe(ScanTile<1>* tiles, unsigned int* status) {
 // ROI), written straight into the caller-visible pinned host buffer (mapped
 // into the device's address space), and the pass's result block copied to
 // its pinned host copy by the first threads: no copy nodes after the pass.
-__global__ void k_assemble(const Roi* __restrict__ rois, const RoiOut* __restrict__ ro,
-                           const DiamOut* __restrict__ dout, int n, int have_diam, rad_features_t* __restrict__ f,
-                           const ResultBlock* __restrict__ res, ResultBlock* __restrict__ res_host) {
+__global__ void k_assemble(const Roi* rois, const RoiOut* ro,
+                           const DiamOut* dout, int n, int have_diam, rad_features_t* f,
+                           const ResultBlock* res, ResultBlock* res_host) {
   pdl_enter();
   static_assert(sizeof(ResultBlock) % 8 == 0, "result block copied in 8-byte words");
   if (blockIdx.x == 0)
@@ -300,6 +300,10 @@ __global__ void k_assemble(const Roi* __restrict__ rois, const RoiOut* __restric
     }
     x.status = 0;
     x._pad = 0;
+    double* dv[10] = {&x.Sphericity, &x.SurfaceVolumeRatio, &x.Compactness1, &x.Compactness2,
+                      &x.SphericalDisproportion, &x.MajorAxisLength, &x.MinorAxisLength, &x.LeastAxisLength,
+                      &x.Elongation, &x.Flatness};
+    for (int k = 0; k < 10; ++k) *dv[k] = o.has_derived ? o.derived[k] : 0.0;
     f[i] = x;
   }
 }
@@ -328,7 +332,7 @@ struct Work {
   // side branch of a pass: the diameter stage's initialisation runs beside
   // the mesh, the masks' per-ROI totals beside the diameters
   cudaStream_t side = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_init = nullptr, ev_tot = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_init = nullptr, ev_tot = nullptr, ev_cnt = nullptr;
   // CUDA graph of the whole pass, valid for the ROI table it was captured with
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t gexec = nullptr;
@@ -347,7 +351,7 @@ struct Work {
     drop_graph();
     if (cap_stream) cudaStreamDestroy(cap_stream);
     if (side) cudaStreamDestroy(side);
-    for (cudaEvent_t e : {ev_fork, ev_init, ev_tot})
+    for (cudaEvent_t e : {ev_fork, ev_init, ev_tot, ev_cnt})
       if (e) cudaEventDestroy(e);
     for (DevBuf* b : {&ms.bits, &ms.counts, &ms.wpre, &ms.tpre, &ms.wlist, &ms.prefix, &ms.chunk, &ms.cubes, &ms.hist, &ms.partial,
                       &ms.bintab, &ms.tabsp, &ds.misc, &ds.plain_part, &result, &ro, &dout, &rois_dev,
@@ -433,6 +437,7 @@ static rad_status size_pools(Work& w, cudaStream_t st) {
 static rad_status enqueue_mesh(Work& w, cudaStream_t st, bool count) {
   ResultBlock* dr = w.dres();
   if (count) RAD_TRY(mesh_count(w.mb, w.ms, &dr->tot, w.dro(), st));
+  RAD_TRY(mesh_moments(w.mb, w.ms, &dr->tot, w.dro(), st));
   return mesh_emit(w.mb, w.ms, &dr->tot, w.dro(), w.idx2.as<int16_t>(), w.soft ? w.vt.as<double>() : nullptr,
                    w.tri.as<int32_t>(), w.vcap, w.tcap, st);
 }
@@ -454,8 +459,8 @@ static rad_status enqueue_finish(Work& w, bool have_diam, cudaStream_t st) {
 
 // One whole pass (mesh, diameters, features to pinned host memory).  The
 // diameter stage's initialisation depends on nothing from the mesh, and the
-// masks' per-ROI totals feed only the final assembly: both run on a side
-// branch (two branches of one graph when captured).  With per-kernel
+// voxel moments and the masks' per-ROI totals feed only the final assembly:
+// they run on a side branch (two branches of one graph when captured).  With per-kernel
 // profiling on, the pass stays on one stream so every kernel is timed alone.
 static rad_status enqueue_pass(Work& w, cudaStream_t st) {
   if (profiling_on()) {
@@ -464,7 +469,7 @@ static rad_status enqueue_pass(Work& w, cudaStream_t st) {
     return enqueue_finish(w, true, st);
   }
   if (!w.side) RAD_CUDA(cudaStreamCreateWithFlags(&w.side, cudaStreamNonBlocking));
-  for (cudaEvent_t* e : {&w.ev_fork, &w.ev_init, &w.ev_tot})
+  for (cudaEvent_t* e : {&w.ev_fork, &w.ev_init, &w.ev_tot, &w.ev_cnt})
     if (!*e) RAD_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
   ResultBlock* dr = w.dres();
   RAD_CUDA(cudaEventRecord(w.ev_fork, st));
@@ -474,6 +479,10 @@ static rad_status enqueue_pass(Work& w, cudaStream_t st) {
                    &dr->stats, w.side, 1));
   RAD_CUDA(cudaEventRecord(w.ev_init, w.side));
   RAD_TRY(mesh_count(w.mb, w.ms, &dr->tot, w.dro(), st));
+  // the voxel moments need only the packed bits: beside the emit pass
+  RAD_CUDA(cudaEventRecord(w.ev_cnt, st));
+  RAD_CUDA(cudaStreamWaitEvent(w.side, w.ev_cnt, 0));
+  RAD_TRY(mesh_moments(w.mb, w.ms, &dr->tot, w.dro(), w.side));
   RAD_TRY(mesh_emit(w.mb, w.ms, &dr->tot, w.dro(), w.idx2.as<int16_t>(), w.soft ? w.vt.as<double>() : nullptr,
                     w.tri.as<int32_t>(), w.vcap, w.tcap, st, false));
   RAD_CUDA(cudaEventRecord(w.ev_fork, st));
@@ -719,15 +728,18 @@ rad_status check_mesh(const rad_mesh_t* mesh) {
   return RAD_OK;
 }
 
-// Diameters of the mesh held by `w` (built by build_mesh on the same Work).
-rad_status shape_of_mesh(const rad_mesh_t* mesh, Work& w, bool plain, rad_features_t* out, cudaStream_t st) {
+// Diameters of the mesh held by `w` (built by build_mesh on the same Work):
+// variant 0 is the FP32-filter engine, RAD_FP64_EQUAL_LOAD ..
+// RAD_FP64_PLAIN_1D the all-pairs FP64 kernels, RAD_FP64_CULLED the engine
+// with FP64 pair evaluation.
+rad_status shape_of_mesh(const rad_mesh_t* mesh, Work& w, int variant, rad_features_t* out, cudaStream_t st) {
   for (int attempt = 0; attempt < 4; ++attempt) {
-    if (plain) {
+    if (variant >= RAD_FP64_EQUAL_LOAD && variant <= RAD_FP64_PLAIN_1D) {
       RAD_TRY(w.plain.reserve(sizeof(DiamResult)));
       RAD_TRY(enqueue_finish(w, false, st));
       if (mesh->n_vertices >= 2)
-        RAD_TRY(diam_plain_fp64(mesh->vtx_idx2, mesh->vtx_t, mesh->n_vertices, make_dims(mesh->dims), mesh->spacing,
-                                w.ds, w.plain.as<DiamResult>(), st));
+        RAD_TRY(diam_fp64_variant(variant, mesh->vtx_idx2, mesh->vtx_t, mesh->n_vertices, make_dims(mesh->dims),
+                                  mesh->spacing, w.ds, w.plain.as<DiamResult>(), st));
       DiamResult pr;
       memset(&pr, 0, sizeof(pr));
       if (mesh->n_vertices >= 2)
@@ -746,7 +758,10 @@ rad_status shape_of_mesh(const rad_mesh_t* mesh, Work& w, bool plain, rad_featur
       record_stats(*w.host, 0, (long long)sizeof(DiamResult), false);
       return RAD_OK;
     }
-    RAD_TRY(enqueue_shape(w, st));
+    w.ds.fp64_pairs = variant == RAD_FP64_CULLED;
+    const rad_status es = enqueue_shape(w, st);
+    w.ds.fp64_pairs = false;
+    RAD_TRY(es);
     RAD_TRY(enqueue_finish(w, true, st));
     RAD_CUDA(cudaStreamSynchronize(st));
     const unsigned int s = w.host->stats.status;
@@ -783,13 +798,23 @@ rad_status rad_soft_mesh(const float* prob_dev, const int64_t dims[3], const dou
 rad_status rad_shape(const rad_mesh_t* mesh, rad_features_t* out, void* stream) {
   RAD_TRY(check_mesh(mesh));
   if (!out) { set_error("out is NULL"); return RAD_ERR_INVALID_ARG; }
-  return shape_of_mesh(mesh, *static_cast<Work*>(mesh->_priv), false, out, (cudaStream_t)stream);
+  return shape_of_mesh(mesh, *static_cast<Work*>(mesh->_priv), 0, out, (cudaStream_t)stream);
 }
 
 rad_status rad_shape_plain_fp64(const rad_mesh_t* mesh, rad_features_t* out, void* stream) {
   RAD_TRY(check_mesh(mesh));
   if (!out) { set_error("out is NULL"); return RAD_ERR_INVALID_ARG; }
-  return shape_of_mesh(mesh, *static_cast<Work*>(mesh->_priv), true, out, (cudaStream_t)stream);
+  return shape_of_mesh(mesh, *static_cast<Work*>(mesh->_priv), RAD_FP64_PLAIN_1D, out, (cudaStream_t)stream);
+}
+
+rad_status rad_shape_fp64_variant(const rad_mesh_t* mesh, int variant, rad_features_t* out, void* stream) {
+  RAD_TRY(check_mesh(mesh));
+  if (!out) { set_error("out is NULL"); return RAD_ERR_INVALID_ARG; }
+  if (variant < RAD_FP64_EQUAL_LOAD || variant > RAD_FP64_CULLED) {
+    set_error("unknown FP64 diameter variant");
+    return RAD_ERR_INVALID_ARG;
+  }
+  return shape_of_mesh(mesh, *static_cast<Work*>(mesh->_priv), variant, out, (cudaStream_t)stream);
 }
 
 rad_status rad_mesh_copy(const rad_mesh_t* mesh, int16_t* idx2, double* t, int32_t* tri, void* stream) {

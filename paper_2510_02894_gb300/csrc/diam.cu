@@ -324,10 +324,10 @@ __device__ __forceinline__ void sweep_finish(const SweepAcc& a, int block_roi, u
 // Key histogram, warp-aggregated: lanes with equal keys (consecutive vertices
 // share cells and planes) make one atomic.  Also the first sweep of the 3D
 // seed: the vertex farthest from each ROI's first vertex.
-__global__ void k_hist(const int16_t* __restrict__ idx2, const double* __restrict__ vt,
-                       const long long* __restrict__ nv_dev, const RoiDiam* __restrict__ rd,
-                       const RoiOut* __restrict__ ro, Params p, const float* __restrict__ ctab,
-                       int* __restrict__ hist, unsigned long long* __restrict__ sweep, ProblemState* __restrict__ ps) {
+__global__ void k_hist(const int16_t* idx2, const double* vt,
+                       const long long* nv_dev, const RoiDiam* rd,
+                       const RoiOut* ro, Params p, const float* ctab,
+                       int* hist, unsigned long long* sweep, ProblemState* ps) {
   pdl_enter();
   __shared__ unsigned long long s_key;
   const long long n = min(*nv_dev, p.nv_cap);
@@ -368,12 +368,12 @@ __global__ void k_hist(const int16_t* __restrict__ idx2, const double* __restric
 // round trip covers all of them.
 // The second sweep of the 3D seed rides along: each vertex's f to the vertex
 // the first sweep found raises the ROI's 3D F.
-__global__ void k_scatter(const int16_t* __restrict__ idx2, const double* __restrict__ vt,
-                          const long long* __restrict__ nv_dev, const RoiDiam* __restrict__ rd,
-                          const RoiOut* __restrict__ ro, Params p, const long long* __restrict__ offs,
-                          int* __restrict__ cursor, const float* __restrict__ ctab,
-                          float4* __restrict__ sorted, int* __restrict__ ids,
-                          const unsigned long long* __restrict__ sweep, ProblemState* __restrict__ ps) {
+__global__ void k_scatter(const int16_t* idx2, const double* vt,
+                          const long long* nv_dev, const RoiDiam* rd,
+                          const RoiOut* ro, Params p, const long long* offs,
+                          int* cursor, const float* ctab,
+                          float4* sorted, int* ids,
+                          const unsigned long long* sweep, ProblemState* ps) {
   pdl_enter();
   __shared__ unsigned long long s_key;
   SweepAcc acc;
@@ -429,10 +429,10 @@ __global__ void k_scatter(const int16_t* __restrict__ idx2, const double* __rest
 // decoupled look-back over chunks of kScanBlock keys (4 per thread).
 constexpr int kScanBlock = 4096;
 constexpr int kScanThreads = 1024;
-__global__ void __launch_bounds__(kScanThreads) k_xscan(const int* __restrict__ in, long long n, int nchunks,
-                                                        long long* __restrict__ out, ScanTile<1>* __restrict__ tiles,
-                                                        unsigned int* __restrict__ tick,
-                                                        unsigned int* __restrict__ status) {
+__global__ void __launch_bounds__(kScanThreads) k_xscan(const int* in, long long n, int nchunks,
+                                                        long long* out, ScanTile<1>* tiles,
+                                                        unsigned int* tick,
+                                                        unsigned int* status) {
   pdl_enter();
   __shared__ long long ws[32];
   __shared__ long long s_ex;
@@ -509,8 +509,8 @@ __device__ __forceinline__ long long chunks_upto(long long m) {
   return kChunk * q * (q + 1) / 2 + r * (q + 1);
 }
 
-__global__ void k_setup(const RoiDiam* __restrict__ rd, Params p, const long long* __restrict__ offs,
-                        Problem* __restrict__ probs, int* __restrict__ chunk0, Counters* __restrict__ cnt) {
+__global__ void k_setup(const RoiDiam* rd, Params p, const long long* offs,
+                        Problem* probs, int* chunk0, Counters* cnt) {
   pdl_enter();
   const int lane = threadIdx.x & 31;
   const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
@@ -628,7 +628,7 @@ __global__ void k_setup(const RoiDiam* __restrict__ rd, Params p, const long lon
 
 // The box of every coarse tile as the union of its fine tiles' boxes (one
 // warp per walked tile, grid-stride).
-__device__ __noinline__ void coarse_boxes(const Tile* __restrict__ tiles, int nt, float4* __restrict__ box) {
+__device__ __noinline__ void coarse_boxes(const Tile* tiles, int nt, float4* box) {
   const int lane = threadIdx.x & 31;
   const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -657,9 +657,9 @@ __device__ __noinline__ void coarse_boxes(const Tile* __restrict__ tiles, int nt
 // One warp per tile (walked tiles, then the fine region): its record and
 // first seed/cull chunk, the bounding box of its FP32 positions (coarse
 // tiles: later, from their fine tiles), and its first vertex.
-__global__ void k_tile_box(const float4* __restrict__ sorted, const Problem* __restrict__ probs, Params p,
-                           const Counters* __restrict__ cnt, Tile* __restrict__ tiles, int* __restrict__ chunk0,
-                           float4* __restrict__ box, float4* __restrict__ rep) {
+__global__ void k_tile_box(const float4* sorted, const Problem* probs, Params p,
+                           const Counters* cnt, Tile* tiles, int* chunk0,
+                           float4* box, float4* rep) {
   pdl_enter();
   const int nt = (int)min((long long)(cnt->alloc & 0xffffffffull), p.max_tiles);
   const int nf = (int)min((long long)cnt->alloc_fine, p.max_fine);
@@ -785,9 +785,9 @@ __device__ __forceinline__ void seed_flush(float m, int fam, ProblemState* ps) {
 // every family's F into T(F) for the cull.  Five blocks per SM (48
 // registers): more resident warps for this latency-bound walk measured
 // faster than four or six.
-__global__ void __launch_bounds__(256, 5) k_seed(const float4* __restrict__ sorted, const float4* __restrict__ rep, Params p,
-                       const Tile* __restrict__ tiles, const int* __restrict__ chunk0, Counters* __restrict__ cnt,
-                       ProblemState* __restrict__ ps, const RoiDiam* __restrict__ rd, float4* __restrict__ box) {
+__global__ void __launch_bounds__(256, 5) k_seed(const float4* sorted, const float4* rep, Params p,
+                       const Tile* tiles, const int* chunk0, Counters* cnt,
+                       ProblemState* ps, const RoiDiam* rd, float4* box) {
   pdl_enter();
   __shared__ bool s_last;
   const unsigned long long alloc = cnt->alloc;
@@ -843,8 +843,8 @@ __global__ void __launch_bounds__(256, 5) k_seed(const float4* __restrict__ sort
 // walk measured faster than the uncapped 76 registers, small spill included.
 // The surviving pairs of one coarse row's chunk (bit l of m[u]: column
 // b0 + 32 u + l) go to the refine list.
-__device__ __noinline__ void cull_coarse(const Tile* __restrict__ tiles, const Params& p, Counters* __restrict__ cnt,
-                                         RefineItem* __restrict__ refine, const Tile& ta, long long b0, int a,
+__device__ __noinline__ void cull_coarse(const Tile* tiles, const Params& p, Counters* cnt,
+                                         RefineItem* refine, const Tile& ta, long long b0, int a,
                                          const unsigned int* m) {
   constexpr int U = kChunk / 32;
   const int lane = threadIdx.x & 31;
@@ -871,9 +871,9 @@ __device__ __noinline__ void cull_coarse(const Tile* __restrict__ tiles, const P
   }
 }
 
-__global__ void __launch_bounds__(256, 4) k_cull(const Tile* __restrict__ tiles, const float4* __restrict__ box, Params p,
-                       const int* __restrict__ chunk0, Counters* __restrict__ cnt, const ProblemState* __restrict__ ps,
-                       WorkItem* __restrict__ work, RefineItem* __restrict__ refine) {
+__global__ void __launch_bounds__(256, 4) k_cull(const Tile* tiles, const float4* box, Params p,
+                       const int* chunk0, Counters* cnt, const ProblemState* ps,
+                       WorkItem* work, RefineItem* refine) {
   pdl_enter();
   const unsigned long long alloc = cnt->alloc;
   const int nt = (int)min((long long)(alloc & 0xffffffffull), p.max_tiles);
@@ -952,9 +952,9 @@ __global__ void __launch_bounds__(256, 4) k_cull(const Tile* __restrict__ tiles,
 // warp tests each fine tile of the first (broadcast by shuffles) against the
 // lanes' fine tiles of the second (only b >= a within one coarse tile).
 // Surviving fine pairs go to the work list.
-__global__ void k_refine(const Tile* __restrict__ tiles, const float4* __restrict__ box, Params p,
-                         Counters* __restrict__ cnt, const ProblemState* __restrict__ ps,
-                         const RefineItem* __restrict__ refine, WorkItem* __restrict__ work) {
+__global__ void k_refine(const Tile* tiles, const float4* box, Params p,
+                         Counters* cnt, const ProblemState* ps,
+                         const RefineItem* refine, WorkItem* work) {
   pdl_enter();
   const long long nr = min((long long)cnt->n_refine, p.refine_cap);
   const int lane = threadIdx.x & 31;
@@ -1076,9 +1076,9 @@ __device__ __forceinline__ float max3f(float a, float b, float c) {
 // when the unit's maximum beats F.  slicemax[slice] < 0 marks a skipped or
 // empty slice.
 template <int TS, int NT>
-__global__ void __launch_bounds__(NT) k_pairs(const float4* __restrict__ sorted, const WorkItem* __restrict__ work,
-                                              Params p, const RoiDiam* __restrict__ rd, Counters* __restrict__ cnt,
-                                              ProblemState* __restrict__ ps, float* __restrict__ slicemax) {
+__global__ void __launch_bounds__(NT) k_pairs(const float4* sorted, const WorkItem* work,
+                                              Params p, const RoiDiam* rd, Counters* cnt,
+                                              ProblemState* ps, float* slicemax) {
   pdl_enter();
   constexpr int RA = TS / 32;  // A entries per lane, and B slices per tile pair
   constexpr int G = pair_slices<TS>();
@@ -1213,8 +1213,8 @@ __global__ void __launch_bounds__(NT) k_pairs(const float4* __restrict__ sorted,
 // Slices whose maximum reaches their problem's final T, listed compactly
 // (one lane per slice).
 template <int TS>
-__global__ void k_cand_list(const WorkItem* __restrict__ work, const float* __restrict__ slicemax, Params p,
-                            Counters* __restrict__ cnt, const ProblemState* __restrict__ ps, int* __restrict__ hits) {
+__global__ void k_cand_list(const WorkItem* work, const float* slicemax, Params p,
+                            Counters* cnt, const ProblemState* ps, int* hits) {
   pdl_enter();
   constexpr int RA = TS / 32;
   const long long nslices = min(cnt->n_work, p.work_cap) * RA;
@@ -1245,10 +1245,10 @@ __global__ void k_cand_list(const WorkItem* __restrict__ work, const float* __re
 // list slots 33..64 at a time, so the list counter sees few atomics.
 constexpr int kCandThreads = 256;
 template <int TS>
-__global__ void __launch_bounds__(kCandThreads) k_cand(const float4* __restrict__ sorted,
-                                                       const WorkItem* __restrict__ work, const int* __restrict__ hits,
-                                                       Params p, Counters* __restrict__ cnt,
-                                                       const ProblemState* __restrict__ ps, Cand* __restrict__ cand) {
+__global__ void __launch_bounds__(kCandThreads) k_cand(const float4* sorted,
+                                                       const WorkItem* work, const int* hits,
+                                                       Params p, Counters* cnt,
+                                                       const ProblemState* ps, Cand* cand) {
   pdl_enter();
   constexpr int RA = TS / 32;
   const long long nh = cnt->n_hits;
@@ -1315,14 +1315,119 @@ __global__ void __launch_bounds__(kCandThreads) k_cand(const float4* __restrict_
   if (cbn) cflush();
 }
 
+// ---- FP64 in place of the FP32 filter (the culled FP64 variant) ---------------------
+
+// Every pair of every surviving work item in FP64 with the pinned formula:
+// one warp per work item (re-culled against the current T first), the A
+// entries' positions in registers (lane l holds entries l, l + 32, ...), the
+// B entries staged 32 at a time in the warp's shared memory.  Each lane keeps
+// its best (d2, i, j) key; the warp's best goes to the family's 128-bit key
+// with one atomic and raises F to d2 rounded down (a value no larger than the
+// FP64 maximum, so T(F) stays below every pair that attains it).
+constexpr int kP64Threads = 256;
+template <int TS>
+__global__ void __launch_bounds__(kP64Threads) k_pairs64(const int* ids, const int16_t* idx2, const double* vt,
+                                                         const WorkItem* work, Params p, const RoiDiam* rd,
+                                                         const RoiOut* ro, Counters* cnt, ProblemState* ps,
+                                                         Key128* keys) {
+  pdl_enter();
+  constexpr int RA = TS / 32;
+  __shared__ double s_u[kP64Threads / 32][3][32];
+  __shared__ int s_id[kP64Threads / 32][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const long long nitems = min(cnt->n_work, p.work_cap);
+  const long long nwarps = (long long)gridDim.x * (kP64Threads / 32);
+  unsigned long long n_items = 0, n_pairs = 0;
+  for (long long it = (long long)blockIdx.x * (kP64Threads / 32) + wid; it < nitems; it += nwarps) {
+    const WorkItem w = work[it];
+    const int fam = fam_of(w.roi, w.q);
+    if (w.ub < __uint_as_float(*(volatile unsigned int*)&ps[fam].T)) continue;  // warp-uniform
+    const long long v0 = ro[w.roi].v0;
+    const RoiDiam& r = rd[w.roi];
+    const bool same = w.abeg == w.bbeg;
+    double ua[RA][3];
+    int ia[RA];
+#pragma unroll
+    for (int k = 0; k < RA; ++k) {
+      const int e = lane + 32 * k;
+      ia[k] = -1;
+      if (e < w.alen) {
+        const int id = ids[w.abeg + e];
+        vertex_u(idx2, vt, id, ua[k]);
+        ia[k] = id - (int)v0;
+      }
+    }
+    Key128 best{0ull, 0ull};
+    for (int jb = 0; jb < w.blen; jb += 32) {
+      __syncwarp();
+      if (jb + lane < w.blen) {
+        const int id = ids[w.bbeg + jb + lane];
+        double u[3];
+        vertex_u(idx2, vt, id, u);
+        s_u[wid][0][lane] = u[0];
+        s_u[wid][1][lane] = u[1];
+        s_u[wid][2][lane] = u[2];
+        s_id[wid][lane] = id - (int)v0;
+      }
+      __syncwarp();
+      const int nj = min(32, w.blen - jb);
+      for (int jj = 0; jj < nj; ++jj) {
+        const double bx = s_u[wid][0][jj], by = s_u[wid][1][jj], bz = s_u[wid][2][jj];
+        const int jid = s_id[wid][jj];
+#pragma unroll
+        for (int k = 0; k < RA; ++k) {
+          if (ia[k] < 0 || (same && lane + 32 * k >= jb + jj)) continue;
+          const double d2 = pin_d2(ua[k][0], ua[k][1], ua[k][2], bx, by, bz, r.sx, r.sy, r.sz);
+          const Key128 key = make_key(d2, min(ia[k], jid), max(ia[k], jid));
+          if (key_gt(key, best)) best = key;
+        }
+      }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      Key128 o;
+      o.lo = __shfl_xor_sync(0xffffffffu, best.lo, off);
+      o.hi = __shfl_xor_sync(0xffffffffu, best.hi, off);
+      if (key_gt(o, best)) best = o;
+    }
+    if (lane == 0) {
+      ++n_items;
+      n_pairs += same ? (unsigned long long)w.alen * (w.alen - 1) / 2 : (unsigned long long)w.alen * w.blen;
+      if (best.hi | best.lo) {
+        atomic_max_key(&keys[fam], best);
+        const float Fn = __double2float_rd(__longlong_as_double((long long)best.hi));
+        if (Fn > __uint_as_float(*(volatile unsigned int*)&ps[fam].F)) {
+          atomicMax(&ps[fam].F, __float_as_uint(Fn));
+          atomicMax(&ps[fam].T, __float_as_uint(threshold(Fn, r)));
+        }
+      }
+    }
+  }
+  if (lane == 0 && n_pairs) {
+    atomicAdd(&cnt->items_evaluated, n_items);
+    atomicAdd(&cnt->pairs_evaluated, n_pairs);
+  }
+}
+
+// The families' keys into the per-ROI results (d2 bits and (i << 32 | j)).
+__global__ void k_keys_out(const Key128* keys, int n, DiamOut* out) {
+  pdl_enter();
+  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < 4 * n; f += gridDim.x * blockDim.x) {
+    const Key128 k = keys[f];
+    if (k.hi | k.lo) {
+      out[f >> 2].d2[f & 3] = k.hi;
+      out[f >> 2].pair[f & 3] = ~k.lo;
+    }
+  }
+}
+
 // ---- 5. FP64 confirmation -------------------------------------------------------------
 
 // Largest pinned FP64 d2 per ROI and category.  Every pair attaining it is a
 // candidate of its problem, so the maximum over candidates is the maximum.
-__global__ void k_confirm(const int* __restrict__ ids, const int16_t* __restrict__ idx2,
-                          const double* __restrict__ vt, Params p, const RoiDiam* __restrict__ rd,
-                          const Counters* __restrict__ cnt, const Cand* __restrict__ cand,
-                          DiamOut* __restrict__ out) {
+__global__ void k_confirm(const int* ids, const int16_t* idx2,
+                          const double* vt, Params p, const RoiDiam* rd,
+                          const Counters* cnt, const Cand* cand,
+                          DiamOut* out) {
   pdl_enter();
   const long long nc = min(cnt->n_cand, p.cand_cap);
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nc; c += (long long)gridDim.x * blockDim.x) {
@@ -1339,10 +1444,10 @@ __global__ void k_confirm(const int* __restrict__ ids, const int16_t* __restrict
 
 // Candidates attaining their ROI's maximum in their category take the
 // smallest (i, j) (ids local to the ROI).  Block 0 also copies the counters.
-__global__ void k_tiebreak(const int* __restrict__ ids, const int16_t* __restrict__ idx2,
-                           const double* __restrict__ vt, Params p, const RoiDiam* __restrict__ rd,
-                           const RoiOut* __restrict__ ro, const Counters* __restrict__ cnt,
-                           const Cand* __restrict__ cand, DiamOut* __restrict__ out, DiamStats* __restrict__ stats) {
+__global__ void k_tiebreak(const int* ids, const int16_t* idx2,
+                           const double* vt, Params p, const RoiDiam* rd,
+                           const RoiOut* ro, const Counters* cnt,
+                           const Cand* cand, DiamOut* out, DiamStats* stats) {
   pdl_enter();
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     stats->problems = cnt->n_problems;
@@ -1374,8 +1479,8 @@ __global__ void k_tiebreak(const int* __restrict__ ids, const int16_t* __restric
   }
 }
 
-__global__ void k_diam_init(DiamOut* __restrict__ out, int n, ZeroSet zs, const RoiDiam* __restrict__ rd,
-                            float* __restrict__ ctab, long long ntab) {
+__global__ void k_diam_init(DiamOut* out, int n, ZeroSet zs, const RoiDiam* rd,
+                            float* ctab, long long ntab) {
   pdl_enter();
   zero_ranges(zs);  // counters, statistics, key histogram and cursors, scan state
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
@@ -1555,6 +1660,7 @@ rad_status diam_run(int n, const RoiDiam* rd, const RoiOut* ro, const long long*
   add(sizeof(int) * 8 * p.work_cap);    // slices to rescan
   add(sizeof(Cand) * p.cand_cap);
   add(sizeof(float) * std::max<long long>(ntab, 1));  // coordinate tables (masks)
+  add(sizeof(Key128) * 4 * n);  // family maxima of the FP64 pair kernel
   RAD_TRY(s.misc.reserve(bytes));
   char* cur = s.misc.as<char>();
   int* hist = carve<int>(cur, K1);
@@ -1581,6 +1687,7 @@ rad_status diam_run(int n, const RoiDiam* rd, const RoiOut* ro, const long long*
   int* hits = carve<int>(cur, 8 * p.work_cap);
   Cand* cand = carve<Cand>(cur, p.cand_cap);
   float* ctab = carve<float>(cur, std::max<long long>(ntab, 1));
+  Key128* keys = carve<Key128>(cur, 4 * n);
 
   const int sms = num_sms();
   ZeroSet zs{};
@@ -1590,6 +1697,7 @@ rad_status diam_run(int n, const RoiDiam* rd, const RoiOut* ro, const long long*
   zero_add(zs, scan_state, sizeof(ScanTile<1>) * nparts + 16);
   zero_add(zs, stats, sizeof(DiamStats));
   zero_add(zs, fam_state, fam_bytes);  // F = T = 0 for every family; sweep slots
+  if (s.fp64_pairs) zero_add(zs, keys, sizeof(Key128) * 4 * n);
   if (which & 1) {
     // on its own (a graph branch beside the mesh) it needs few CTAs: a few MB zeroed
     const long long init_ctas = (std::max(K1, ntab) + 255) / 256;
@@ -1615,6 +1723,21 @@ rad_status diam_run(int n, const RoiDiam* rd, const RoiOut* ro, const long long*
   RAD_LAUNCH("diam_refine", k_refine, wave_grid(k_refine, 256, std::max<long long>(1, p.refine_cap / 8)), 256, 0, st,
              tiles, box, p, cnt, ps, refine, work);
   const int ctas = sms * tu.ctas_per_sm;
+  if (s.fp64_pairs) {  // every surviving pair in FP64: no filter, no candidates
+    if (tu.tile == 64) {
+      RAD_LAUNCH("diam_pairs_fp64", k_pairs64<64>, wave_grid(k_pairs64<64>, kP64Threads, 1LL << 30), kP64Threads, 0, st,
+                 ids, idx2, vt, work, p, rd, ro, cnt, ps, keys);
+    } else if (tu.tile == 128) {
+      RAD_LAUNCH("diam_pairs_fp64", k_pairs64<128>, wave_grid(k_pairs64<128>, kP64Threads, 1LL << 30), kP64Threads, 0,
+                 st, ids, idx2, vt, work, p, rd, ro, cnt, ps, keys);
+    } else {
+      RAD_LAUNCH("diam_pairs_fp64", k_pairs64<256>, wave_grid(k_pairs64<256>, kP64Threads, 1LL << 30), kP64Threads, 0,
+                 st, ids, idx2, vt, work, p, rd, ro, cnt, ps, keys);
+    }
+    RAD_LAUNCH("diam_keys_out", k_keys_out, std::max(1, std::min(sms, (4 * n + 255) / 256)), 256, 0, st, keys, n, out);
+    RAD_LAUNCH("diam_tiebreak", k_tiebreak, 1, 32, 0, st, ids, idx2, vt, p, rd, ro, cnt, cand, out, stats);  // statistics
+    return RAD_OK;
+  }
   if (tu.tile == 64) {
     if (tu.threads == 64) RAD_TRY((launch_pairs<64, 64>(sorted, work, p, rd, cnt, ps, slicemax, hits, cand, ctas, st)));
     else RAD_TRY((launch_pairs<64, 128>(sorted, work, p, rd, cnt, ps, slicemax, hits, cand, ctas, st)));
@@ -1643,9 +1766,9 @@ __device__ __forceinline__ void take_best(BestD& b, double d2, int i, int j) {
 
 // Persistent grid over the upper-triangular tile pairs; each CTA keeps its
 // running (d2, i, j) for 3D, Slice, Column, Row and writes them to scratch.
-__global__ void __launch_bounds__(kPlainTile) k_plain(const int16_t* __restrict__ idx2, const double* __restrict__ vt,
+__global__ void __launch_bounds__(kPlainTile) k_plain(const int16_t* idx2, const double* vt,
                                                       int n, double sx, double sy, double sz,
-                                                      BestD* __restrict__ part) {
+                                                      BestD* part) {
   pdl_enter();
   __shared__ double su[3][kPlainTile];
   __shared__ int sq[3][kPlainTile];
@@ -1714,7 +1837,7 @@ __global__ void __launch_bounds__(kPlainTile) k_plain(const int16_t* __restrict_
   }
 }
 
-__global__ void k_plain_final(const BestD* __restrict__ part, int nparts, DiamResult* __restrict__ out) {
+__global__ void k_plain_final(const BestD* part, int nparts, DiamResult* out) {
   pdl_enter();
   if (threadIdx.x < 4) {
     const int q = threadIdx.x;

@@ -33,6 +33,9 @@
 //   k_rows, k_cubes  soft maps (one ROI): per row its interpolated vertices
 //            and a compact list of active cubes, then one thread per cube for
 //            its triangles and FP64 volume and area, summed in a fixed order.
+#include <array>
+#include <map>
+#include <mutex>
 #include <stdio.h>
 
 #include <algorithm>
@@ -44,6 +47,83 @@
 namespace rad {
 
 namespace {
+
+// Eigenvalues (descending) of a symmetric 3x3 matrix by cyclic Jacobi
+// rotations in FP64: each rotation zeroes one off-diagonal element, and the
+// sweeps stop once the off-diagonal part is negligible against the diagonal.
+// (A closed form through the characteristic cubic loses about half the digits
+// of a nearly repeated eigenvalue, which the square roots of the axis lengths
+// then expose; rotations keep every eigenvalue within a few ulps of |A|.)
+// One division, one square root and one reciprocal square root per rotation.
+__device__ void sym3_eigenvalues(double a[3][3], double lam[3]) {
+  for (int sweep = 0; sweep < 16; ++sweep) {
+    const double off = a[0][1] * a[0][1] + a[0][2] * a[0][2] + a[1][2] * a[1][2];
+    const double diag = a[0][0] * a[0][0] + a[1][1] * a[1][1] + a[2][2] * a[2][2];
+    if (off <= 1e-34 * diag) break;
+    for (int p = 0; p < 2; ++p)
+      for (int q = p + 1; q < 3; ++q) {
+        const double apq = a[p][q];
+        if (apq == 0.0) continue;
+        // t = tan of the rotation angle, the smaller root of t^2 + 2 theta t - 1 = 0
+        const double theta = 0.5 * (a[q][q] - a[p][p]);
+        const double h = sqrt(theta * theta + apq * apq);
+        const double t = apq / (fabs(theta) + h) * (theta >= 0.0 ? 1.0 : -1.0);
+        const double c = rsqrt(t * t + 1.0), s = t * c;
+        a[p][p] -= t * apq;
+        a[q][q] += t * apq;
+        a[p][q] = a[q][p] = 0.0;
+        const int r = 3 - p - q;
+        const double arp = a[r][p], arq = a[r][q];
+        a[r][p] = a[p][r] = c * arp - s * arq;
+        a[r][q] = a[q][r] = s * arp + c * arq;
+      }
+  }
+  lam[0] = a[0][0]; lam[1] = a[1][1]; lam[2] = a[2][2];
+  for (int i = 0; i < 2; ++i)
+    for (int j = i + 1; j < 3; ++j)
+      if (lam[j] > lam[i]) { const double t = lam[i]; lam[i] = lam[j]; lam[j] = t; }
+}
+
+// Closed-form Shape features into d[0..4] (Sphericity, SurfaceVolumeRatio,
+// Compactness1, Compactness2, SphericalDisproportion) from the mesh volume V
+// and area A; a zero denominator gives 0.
+__device__ void closed_form_features(double V, double A, double* d) {
+  const double pi = 3.14159265358979323846;
+  const double k = cbrt(36.0 * pi * V * V);
+  d[0] = A > 0.0 ? k / A : 0.0;
+  d[1] = V > 0.0 ? A / V : 0.0;
+  d[2] = A > 0.0 ? V / (sqrt(pi) * A * sqrt(A)) : 0.0;
+  d[3] = A > 0.0 ? 36.0 * pi * V * V / (A * A * A) : 0.0;
+  d[4] = k > 0.0 ? A / k : 0.0;
+}
+
+// Principal axes into d[5..9] (Major/Minor/LeastAxisLength, Elongation,
+// Flatness) from the eigenvalues of the inside voxels' coordinate covariance
+// (1/N normalisation).  The covariance numerators N sum(ab) - sum(a) sum(b)
+// are formed exactly in 128-bit integers from the exact moments, so each
+// entry is rounded once.  Eigenvalues below 0 (rounding) count as 0; with a
+// zero major eigenvalue the ratios are 0.
+__device__ void principal_axes(long long N, const unsigned long long* mom, double sx, double sy, double sz,
+                               double* d) {
+  double lam[3] = {0.0, 0.0, 0.0};
+  if (N > 0) {
+    const double sp[3] = {sx, sy, sz};
+    const int ia[6] = {0, 1, 2, 0, 0, 1}, ib[6] = {0, 1, 2, 1, 2, 2};  // xx yy zz xy xz yz
+    double c[3][3];
+    for (int e = 0; e < 6; ++e) {
+      const __int128 num = (__int128)N * (__int128)mom[3 + e] - (__int128)mom[ia[e]] * (__int128)mom[ib[e]];
+      const double v = (double)num / ((double)N * (double)N) * sp[ia[e]] * sp[ib[e]];
+      c[ia[e]][ib[e]] = c[ib[e]][ia[e]] = v;
+    }
+    sym3_eigenvalues(c, lam);
+  }
+  for (int k = 0; k < 3; ++k) lam[k] = lam[k] > 0.0 ? lam[k] : 0.0;
+  d[5] = 4.0 * sqrt(lam[0]);
+  d[6] = 4.0 * sqrt(lam[1]);
+  d[7] = 4.0 * sqrt(lam[2]);
+  d[8] = lam[0] > 0.0 ? sqrt(lam[1] / lam[0]) : 0.0;
+  d[9] = lam[0] > 0.0 ? sqrt(lam[2] / lam[0]) : 0.0;
+}
 
 constexpr int kScanChunk = 2048;  // rows per scan chunk (256 threads x 8)
 constexpr int kCubeBlocksPerSM = 2;
@@ -97,7 +177,7 @@ __device__ __forceinline__ uint32_t nz4(uint32_t v) {
 
 // One thread per bitset word of the whole batch (padding rows included).
 template <bool SOFT>
-__global__ void k_pack(const Roi* __restrict__ rois, int n, long long total, uint32_t* __restrict__ bits,
+__global__ void k_pack(const Roi* rois, int n, long long total, uint32_t* bits,
                        ZeroSet zs) {
   pdl_enter();
   zero_ranges(zs);  // the pass's counters, per-ROI results and scan state
@@ -257,9 +337,9 @@ __device__ __forceinline__ RowItem row_item(const Roi* rois, int n, long long to
 // and every word with crossings or active cubes (word 0 also for the x = -1
 // vertex and cube) is appended to wlist (any order: the prefixes fix the ids).
 constexpr int kCountThreads = 256;
-__global__ void __launch_bounds__(kCountThreads) k_count(const uint32_t* __restrict__ bits, const Roi* __restrict__ rois, int n, long long total_rows,
-                        int L, int Wc, int4* __restrict__ counts, int* __restrict__ wpre, int* __restrict__ tpre,
-                        int2* __restrict__ wlist, long long wlist_cap, MeshTotals* __restrict__ tot) {
+__global__ void __launch_bounds__(kCountThreads) k_count(const uint32_t* bits, const Roi* rois, int n, long long total_rows,
+                        int L, int Wc, int4* counts, int* wpre, int* tpre,
+                        int2* wlist, long long wlist_cap, MeshTotals* tot) {
   pdl_enter();
   const int lane = threadIdx.x & 31, sub = lane % L, gpw = 32 / L;
   const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
@@ -339,10 +419,10 @@ __global__ void __launch_bounds__(kCountThreads) k_count(const uint32_t* __restr
 // voxels) at row r over the whole batch; the last chunk writes the totals and
 // the last block to finish derives every ROI's id ranges.
 
-__global__ void k_scan_rows(const int4* __restrict__ counts, long long R, int nchunks, long long* __restrict__ prefix,
-                            ScanTile<4>* __restrict__ tiles, unsigned int* __restrict__ tick,
-                            MeshTotals* __restrict__ tot, const Roi* __restrict__ rois, int n,
-                            RoiOut* __restrict__ out) {
+__global__ void k_scan_rows(const int4* counts, long long R, int nchunks, long long* prefix,
+                            ScanTile<4>* tiles, unsigned int* tick,
+                            MeshTotals* tot, const Roi* rois, int n,
+                            RoiOut* out) {
   pdl_enter();
   __shared__ long long sw[4][8];
   __shared__ long long s_ex[4];
@@ -478,7 +558,7 @@ __device__ int select_candidate(int loop, const double (*w)[3], const double* sp
 //   tsum = sum of A . (B x C),
 // with A, B, C the local doubled positions (integers 0..2), and area2 = sum of
 // |cof(H) ((B - A) x (C - A))| with H = diag(s / 2).
-__global__ void k_binary_table(const double* __restrict__ spacings, BinCase* __restrict__ tabs) {
+__global__ void k_binary_table(const double* spacings, BinCase* tabs) {
   pdl_enter();
   const int cs = threadIdx.x;
   const double sx = spacings[3 * blockIdx.x], sy = spacings[3 * blockIdx.x + 1], sz = spacings[3 * blockIdx.x + 2];
@@ -540,10 +620,10 @@ __device__ __forceinline__ double crossing_t(double v0, double v1) {
 // ---- rows: vertices and the active-cube list --------------------------------------------
 
 template <bool SOFT>
-__global__ void k_rows(const uint32_t* __restrict__ bits, const Roi* __restrict__ rois, int n, long long total_rows,
-                       int L, int Wc, const int4* __restrict__ counts, const int* __restrict__ wpre,
-                       const long long* __restrict__ prefix, int16_t* __restrict__ idx2, double* __restrict__ vt, int4* __restrict__ cubes, long long vcap,
-                       long long ccap, MeshTotals* __restrict__ tot) {
+__global__ void k_rows(const uint32_t* bits, const Roi* rois, int n, long long total_rows,
+                       int L, int Wc, const int4* counts, const int* wpre,
+                       const long long* prefix, int16_t* idx2, double* vt, int4* cubes, long long vcap,
+                       long long ccap, MeshTotals* tot) {
   pdl_enter();
   const int lane = threadIdx.x & 31, sub = lane % L, gpw = 32 / L;
   const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
@@ -685,14 +765,14 @@ __device__ __forceinline__ int edge_axis(int e) {
 }
 
 template <bool SOFT>
-__global__ void __launch_bounds__(kCubeThreads) k_cubes(const uint32_t* __restrict__ bits, const Roi* __restrict__ rois,
-                                                        int n, const int* __restrict__ wpre,
-                                                        const long long* __restrict__ prefix,
-                                                        const int4* __restrict__ cubes, const BinCase* __restrict__ tab,
-                                                        int32_t* __restrict__ tri, long long ccap, long long tcap,
-                                                        MeshTotals* __restrict__ tot, RoiOut* __restrict__ out,
-                                                        unsigned long long* __restrict__ case_hist,
-                                                        double* __restrict__ partial) {
+__global__ void __launch_bounds__(kCubeThreads) k_cubes(const uint32_t* bits, const Roi* rois,
+                                                        int n, const int* wpre,
+                                                        const long long* prefix,
+                                                        const int4* cubes, const BinCase* tab,
+                                                        int32_t* tri, long long ccap, long long tcap,
+                                                        MeshTotals* tot, RoiOut* out,
+                                                        unsigned long long* case_hist,
+                                                        double* partial) {
   pdl_enter();
   const long long ncubes = min(tot->na, ccap);
   long long vsum = 0;
@@ -829,6 +909,8 @@ __global__ void __launch_bounds__(kCubeThreads) k_cubes(const uint32_t* __restri
     }
     out[0].vol6 = v;
     out[0].area2 = a;
+    closed_form_features(v / 6.0, a * 0.5, out[0].derived);
+    out[0].has_derived = 1;
     tot->done_ctas = 0;
   }
 }
@@ -879,11 +961,11 @@ constexpr unsigned int kEdgeAxis = (0u << 0) | (1u << 2) | (2u << 4) | (1u << 6)
                                    (2u << 12) | (2u << 14) | (0u << 16) | (1u << 18) | (1u << 20) | (0u << 22);
 
 __global__ void __launch_bounds__(kEmitThreads, kEmitBlocksPerSM)
-    k_emit(const uint32_t* __restrict__ bits, const Roi* __restrict__ rois, int n, const int2* __restrict__ wlist,
-           long long wlist_cap, const int* __restrict__ wpre, const int* __restrict__ tpre,
-           const long long* __restrict__ prefix, const BinCase* __restrict__ tab,
-           int16_t* __restrict__ idx2, int32_t* __restrict__ tri, long long vcap, long long tcap,
-           MeshTotals* __restrict__ tot, RoiOut* __restrict__ out, unsigned long long* __restrict__ case_hist) {
+    k_emit(const uint32_t* bits, const Roi* rois, int n, const int2* wlist,
+           long long wlist_cap, const int* wpre, const int* tpre,
+           const long long* prefix, const BinCase* tab,
+           int16_t* idx2, int32_t* tri, long long vcap, long long tcap,
+           MeshTotals* tot, RoiOut* out, unsigned long long* case_hist) {
   pdl_enter();
   __shared__ EmitShared sh[kEmitWarps];
   __shared__ unsigned int s_hist[kEmitWarps][256];  // case counts of the warp's current ROI
@@ -1144,8 +1226,8 @@ __global__ void __launch_bounds__(kEmitThreads, kEmitBlocksPerSM)
 
 // Mask volume and area per ROI (one block per ROI, fixed order):
 //   6V = det(diag(s / 2)) * vsum,  2A = sum over cases of count * area2 of the case.
-__global__ void k_mask_totals(const Roi* __restrict__ rois, int n, const BinCase* __restrict__ tab,
-                              const unsigned long long* __restrict__ case_hist, RoiOut* __restrict__ out) {
+__global__ void k_mask_totals(const Roi* rois, int n, const BinCase* tab,
+                              const unsigned long long* case_hist, RoiOut* out) {
   pdl_enter();
   __shared__ double s[256];
   for (int i = blockIdx.x; i < n; i += gridDim.x) {
@@ -1163,10 +1245,115 @@ __global__ void k_mask_totals(const Roi* __restrict__ rois, int n, const BinCase
     }
     if (threadIdx.x == 0) {
       const double h3 = (0.5 * r.sx) * (0.5 * r.sy) * (0.5 * r.sz);
-      out[i].vol6 = (double)out[i].vsum * h3;
+      const double vol6 = (double)out[i].vsum * h3;
+      out[i].vol6 = vol6;
       out[i].area2 = s[0];
+      closed_form_features(vol6 / 6.0, s[0] * 0.5, out[i].derived);
+      out[i].has_derived = 1;
     }
     __syncthreads();
+  }
+}
+
+// ---- voxel-coordinate moments -------------------------------------------------------
+// Exact integer moments of the inside voxels' index coordinates per ROI (for
+// the principal axes of the Shape class): every bitset word contributes
+// through popcounts of its bit-index planes (sum of set bit positions b and of
+// b^2), combined with the word's x0 = 32 w and its row (y, z).  One thread
+// per word over contiguous per-block ranges (like the packing pass); a
+// thread's sums stay in registers while its ROI is the same, a block adds its
+// own ROI's sums with one atomic per moment.
+// Exact index-coordinate moments of the inside voxels, one thread per voxel
+// row (y, z) of a ROI: the row's count c, sum x and sum x^2 come from the
+// packed words (popcounts against the bit-position planes), and the row adds
+// c, y c, z c, ... to the ROI's nine sums.  Warps whose rows share one ROI
+// reduce by shuffles first; a block's first ROI collects in shared memory.
+__global__ void k_moments(const uint32_t* bits, const Roi* rois, int n, long long rows, RoiOut* out,
+                          MeshTotals* tot) {
+  pdl_enter();
+  __shared__ unsigned long long s_m[9];
+  __shared__ bool s_last;
+  if (threadIdx.x < 9) s_m[threadIdx.x] = 0ull;
+  const long long blk0 = (long long)blockIdx.x * blockDim.x;
+  const int block_roi = blk0 < rows ? (n == 1 ? 0 : roi_of_row(rois, n, blk0)) : -1;
+  __syncthreads();
+  for (long long base = blk0; base < rows; base += (long long)gridDim.x * blockDim.x) {
+    const long long g = base + threadIdx.x;
+    unsigned long long m[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) m[k] = 0ull;
+    int ri = -1;
+    if (g < rows) {
+      ri = n == 1 ? 0 : roi_of_row(rois, n, g);
+      const Roi& r = rois[ri];
+      const long long local = g - r.row0;
+      const unsigned long long zz = (unsigned long long)(local / (r.ny + 1));
+      const unsigned long long yy = (unsigned long long)(local - (long long)zz * (r.ny + 1));
+      if (yy < (unsigned long long)r.ny && zz < (unsigned long long)r.nz) {
+        const uint32_t* row = bits + r.word0 + ((long long)(zz + 1) * r.BY + (long long)(yy + 1)) * r.W;
+        const uint32_t M[5] = {0xAAAAAAAAu, 0xCCCCCCCCu, 0xF0F0F0F0u, 0xFF00FF00u, 0xFFFF0000u};
+        unsigned long long c = 0, sx = 0, sxx = 0;
+        for (int w = 0; w < r.W; ++w) {
+          const uint32_t B = __ldcg(row + w);
+          if (B == 0u) continue;
+          unsigned int cw, sb, sbb;
+          if (B == 0xFFFFFFFFu) {
+            cw = 32; sb = 496; sbb = 10416;  // sums of b and b^2 over b = 0 .. 31
+          } else {
+            cw = __popc(B); sb = 0; sbb = 0;
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {  // b = sum_k 2^k [bit k of b]
+              const unsigned int pk = __popc(B & M[k]);
+              sb += pk << k;
+              sbb += pk << (2 * k);
+#pragma unroll
+              for (int l = k + 1; l < 5; ++l) sbb += __popc(B & M[k] & M[l]) << (k + l + 1);
+            }
+          }
+          const unsigned long long x0 = 32ull * (unsigned long long)w;
+          c += cw;
+          sx += x0 * cw + sb;
+          sxx += x0 * (x0 * cw + 2ull * sb) + sbb;
+        }
+        m[0] = sx; m[1] = yy * c; m[2] = zz * c;
+        m[3] = sxx; m[4] = yy * yy * c; m[5] = zz * zz * c;
+        m[6] = yy * sx; m[7] = zz * sx; m[8] = yy * zz * c;
+      }
+    }
+    const int r0 = __shfl_sync(0xffffffffu, ri, 0);
+    const bool uniform = __all_sync(0xffffffffu, ri == r0 || ri < 0);
+    if (uniform) {
+      for (int k = 0; k < 9; ++k) {
+        unsigned long long v = m[k];
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        m[k] = v;
+      }
+      if ((threadIdx.x & 31) == 0 && r0 >= 0) {
+        for (int k = 0; k < 9; ++k)
+          if (m[k]) {
+            if (r0 == block_roi) atomicAdd(&s_m[k], m[k]);
+            else atomicAdd(&out[r0].mom[k], m[k]);
+          }
+      }
+    } else if (ri >= 0) {  // a warp across a ROI boundary (batches)
+      for (int k = 0; k < 9; ++k)
+        if (m[k]) atomicAdd(&out[ri].mom[k], m[k]);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 9 && block_roi >= 0 && s_m[threadIdx.x]) atomicAdd(&out[block_roi].mom[threadIdx.x], s_m[threadIdx.x]);
+  // the block that finishes last: principal axes of every ROI (FP64, one
+  // thread per ROI; beside the emit pass, off the critical path)
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&tot->mom_done, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    unsigned long long mom[9];
+    for (int k = 0; k < 9; ++k) mom[k] = __ldcg(&out[i].mom[k]);
+    principal_axes(__ldcg(&out[i].nvox), mom, rois[i].sx, rois[i].sy, rois[i].sz, out[i].derived);
   }
 }
 
@@ -1184,11 +1371,49 @@ int group_lanes(int W) {
 
 // ---- host ---------------------------------------------------------------------------
 
+namespace {
+// Case tables built so far, per (device, spacing), for the life of the
+// process: a new workspace or batch with a known spacing copies its table
+// instead of rebuilding it.  The buffers are never freed (one 256-case table
+// per distinct spacing); a device reset invalidates them.
+struct TableCache {
+  std::mutex mu;
+  std::map<std::array<double, 4>, const BinCase*> tabs;  // key: device, sx, sy, sz
+};
+TableCache& table_cache() {
+  static TableCache* c = new TableCache;  // never destroyed: no teardown order issues at exit
+  return *c;
+}
+}  // namespace
+
 rad_status mesh_tables(const double* spacings_host, int n_tabs, MeshScratch& s, cudaStream_t st) {
   RAD_TRY(s.bintab.reserve(sizeof(BinCase) * 256 * std::max(n_tabs, 1)));
   RAD_TRY(s.tabsp.reserve(sizeof(double) * 3 * std::max(n_tabs, 1)));
-  RAD_CUDA(cudaMemcpyAsync(s.tabsp.p, spacings_host, sizeof(double) * 3 * n_tabs, cudaMemcpyHostToDevice, st));
-  RAD_LAUNCH("mc_binary_table", k_binary_table, n_tabs, 256, 0, st, s.tabsp.as<double>(), s.bintab.as<BinCase>());
+  int dev = 0;
+  RAD_CUDA(cudaGetDevice(&dev));
+  TableCache& tc = table_cache();
+  std::lock_guard<std::mutex> lock(tc.mu);
+  auto key = [&](int k) {
+    return std::array<double, 4>{(double)dev, spacings_host[3 * k], spacings_host[3 * k + 1], spacings_host[3 * k + 2]};
+  };
+  std::vector<double> miss;
+  std::vector<int> miss_k;
+  for (int k = 0; k < n_tabs; ++k)
+    if (!tc.tabs.count(key(k))) {
+      miss.insert(miss.end(), {spacings_host[3 * k], spacings_host[3 * k + 1], spacings_host[3 * k + 2]});
+      miss_k.push_back(k);
+    }
+  if (!miss_k.empty()) {  // build the new ones in one launch, and finish before publishing them
+    BinCase* fresh = nullptr;
+    RAD_CUDA(cudaMalloc(&fresh, sizeof(BinCase) * 256 * miss_k.size()));
+    RAD_CUDA(cudaMemcpyAsync(s.tabsp.p, miss.data(), sizeof(double) * miss.size(), cudaMemcpyHostToDevice, st));
+    RAD_LAUNCH("mc_binary_table", k_binary_table, (int)miss_k.size(), 256, 0, st, s.tabsp.as<double>(), fresh);
+    RAD_CUDA(cudaStreamSynchronize(st));
+    for (size_t m = 0; m < miss_k.size(); ++m) tc.tabs[key(miss_k[m])] = fresh + 256 * m;
+  }
+  for (int k = 0; k < n_tabs; ++k)
+    RAD_CUDA(cudaMemcpyAsync(s.bintab.as<BinCase>() + 256 * k, tc.tabs[key(k)], sizeof(BinCase) * 256,
+                             cudaMemcpyDeviceToDevice, st));
   return RAD_OK;
 }
 
@@ -1250,6 +1475,12 @@ rad_status mesh_emit(const MeshBatch& b, MeshScratch& s, MeshTotals* tot, RoiOut
                s.hist.as<unsigned long long>());
     if (totals) RAD_TRY(mesh_totals(b, s, out, st));
   }
+  return RAD_OK;
+}
+
+rad_status mesh_moments(const MeshBatch& b, MeshScratch& s, MeshTotals* tot, RoiOut* out, cudaStream_t st) {
+  RAD_LAUNCH("mc_moments", k_moments, wave_grid(k_moments, 256, (b.rows + 255) / 256), 256, 0, st,
+             s.bits.as<uint32_t>(), b.rois, b.n, b.rows, out, tot);
   return RAD_OK;
 }
 

@@ -44,9 +44,9 @@ __device__ __forceinline__ void na_take(NaBest& b, double d2, int i, int j) {
   if (na_better(d2, i, j, b)) { b.d2 = d2; b.i = i; b.j = j; }
 }
 
-__global__ void __launch_bounds__(kNaTile) k_na_rows(const int16_t* __restrict__ idx2, const double* __restrict__ vt,
+__global__ void __launch_bounds__(kNaTile) k_na_rows(const int16_t* idx2, const double* vt,
                                                      int n, double sx, double sy, double sz,
-                                                     NaBest* __restrict__ slots) {
+                                                     NaBest* slots) {
   pdl_enter();
   __shared__ double su[3][kNaTile];
   __shared__ int sq[3][kNaTile];
@@ -107,8 +107,8 @@ __global__ void __launch_bounds__(kNaTile) k_na_rows(const int16_t* __restrict__
   }
 }
 
-__global__ void k_na_final(const NaBest* __restrict__ slots, int tiles, double* __restrict__ d2_out,
-                           int32_t* __restrict__ pairs_out) {
+__global__ void k_na_final(const NaBest* slots, int tiles, double* d2_out,
+                           int32_t* pairs_out) {
   pdl_enter();
   if (threadIdx.x < 4) {
     const int q = threadIdx.x;

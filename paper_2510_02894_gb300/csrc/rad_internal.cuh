@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <utility>
 #include <stdint.h>
+#include <stdlib.h>
 
 #include <string>
 #include <vector>
@@ -124,12 +125,14 @@ __device__ void scan_lookback(ScanTile<Q>* tiles, int c, long long* excl, unsign
 // nodes between kernels): 8-byte aligned, lengths rounded up to whole words
 // inside their allocations.
 struct ZeroSet {
-  unsigned long long* p[6];
-  long long words[6];
+  static constexpr int kMax = 8;
+  unsigned long long* p[kMax];
+  long long words[kMax];
   int count;
 };
 
 inline void zero_add(ZeroSet& z, void* p, size_t bytes) {
+  if (z.count >= ZeroSet::kMax) abort();  // a fixed list: more ranges is a bug of the caller
   z.p[z.count] = static_cast<unsigned long long*>(p);
   z.words[z.count] = (long long)((bytes + 7) / 8);
   ++z.count;
@@ -144,7 +147,12 @@ __device__ __forceinline__ void zero_ranges(const ZeroSet& z) {
 
 // First statement of every kernel: wait for the previous kernel in the stream
 // (a no-op without a programmatic dependency), then let the next one be
-// scheduled.
+// scheduled.  No kernel parameter of this library is declared restrict:
+// with restrict-qualified parameters the compiler may treat loads of data
+// that an earlier kernel of the pass writes as invariant (read-only cache
+// loads, free to move above griddepcontrol.wait), and under programmatic
+// dependent launch such loads were measured to return data from before the
+// earlier kernel's writes.
 __device__ __forceinline__ void pdl_enter() {
   asm volatile("griddepcontrol.wait;\n" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
@@ -205,7 +213,15 @@ struct RoiOut {
   long long v0, nv, t0, nt, c0, na, nvox;  // id ranges of vertices, triangles, cubes; inside voxels
   long long vsum;                          // exact sum of A.(B x C) in half-voxel units (masks)
   double vol6, area2;                      // 6 V and 2 A
+  // exact moments of the inside voxels' index coordinates:
+  // sum x, y, z, xx, yy, zz, xy, xz, yz
+  unsigned long long mom[9];
+  // derived Shape features (rad_features_t order, Sphericity .. Flatness),
+  // valid when has_derived (masks: computed beside the diameter stage)
+  double derived[10];
+  long long has_derived;
 };
+
 
 struct MeshTotals {  // batch-wide counts and status of one marching-cubes pass
   long long nv, nt, nvox, na;
@@ -213,6 +229,8 @@ struct MeshTotals {  // batch-wide counts and status of one marching-cubes pass
   unsigned long long emit_ticket;  // next chunk of the word list
   unsigned int status;
   unsigned int done_ctas;  // last-CTA ticket of the soft cube kernel
+  unsigned int mom_done;   // last-CTA ticket of the moments kernel
+  unsigned int pad;
 };
 
 // Host view of a batch.
@@ -252,12 +270,17 @@ rad_status mesh_count(const MeshBatch& b, MeshScratch& s, MeshTotals* tot, RoiOu
 rad_status mesh_emit(const MeshBatch& b, MeshScratch& s, MeshTotals* tot, RoiOut* out, int16_t* idx2, double* vt,
                      int32_t* tri, long long vcap, long long tcap, cudaStream_t st, bool totals = true);
 rad_status mesh_totals(const MeshBatch& b, MeshScratch& s, RoiOut* out, cudaStream_t st);
+// Exact coordinate moments of every ROI's inside voxels from the packed bits,
+// and from them the principal axes (after mesh_count; on any stream ordered
+// after it).
+rad_status mesh_moments(const MeshBatch& b, MeshScratch& s, MeshTotals* tot, RoiOut* out, cudaStream_t st);
 
 // ---- diameters ----------------------------------------------------------------
 struct DiamScratch {
   DevBuf misc;        // sort, problems, tiles, work list, candidates (carved per run)
   DevBuf plain_part;  // per-CTA partial results of the plain FP64 kernel
   long long work_cap = 0, cand_cap = 0;
+  bool fp64_pairs = false;  // evaluate the surviving tile pairs in FP64 (no FP32 filter)
 };
 
 // Per-ROI parameters of the diameter problems (host-computed, uploaded).
@@ -308,6 +331,10 @@ rad_status diam_run(int n, const RoiDiam* rd, const RoiOut* ro, const long long*
                     int which = 3);
 rad_status diam_plain_fp64(const int16_t* idx2, const double* vt, long long nv, const MeshDims& d, const double sp[3],
                            DiamScratch& s, DiamResult* out_dev, cudaStream_t st);
+// FP64 all-pairs diameters by one of the accumulation variants
+// RAD_FP64_EQUAL_LOAD .. RAD_FP64_PLAIN_1D (one mesh; results as diam_plain_fp64).
+rad_status diam_fp64_variant(int variant, const int16_t* idx2, const double* vt, long long nv, const MeshDims& d,
+                             const double sp[3], DiamScratch& s, DiamResult* out_dev, cudaStream_t st);
 
 const rad_tuning_t& tuning();
 
@@ -349,6 +376,55 @@ __device__ __forceinline__ double pin_d2(double uix, double uiy, double uiz, dou
   double dz = __dmul_rn(__dsub_rn(uiz, ujz), sz);
   double r = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
   return __dadd_rn(r, __dmul_rn(dz, dz));
+}
+
+// A (d2, i, j) maximum as one 128-bit key: high word the bits of d2
+// (non-negative doubles order like their bit patterns), low word
+// ~(i << 32 | j), so the larger key has the larger d2, then the smaller
+// (i, j).  Zero means "no pair yet".
+struct __align__(16) Key128 {
+  unsigned long long lo, hi;
+};
+
+__device__ __forceinline__ bool key_gt(const Key128& a, const Key128& b) {
+  return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo);
+}
+
+__device__ __forceinline__ Key128 make_key(double d2, int i, int j) {
+  Key128 k;
+  k.hi = (unsigned long long)__double_as_longlong(d2);
+  k.lo = ~(((unsigned long long)(unsigned int)i << 32) | (unsigned int)j);
+  return k;
+}
+
+// 128-bit compare-and-swap on a 16-byte aligned generic address (global or
+// shared); returns the value found there.
+__device__ __forceinline__ Key128 cas128(Key128* p, const Key128& cmp, const Key128& val) {
+  Key128 r;
+  asm volatile(
+      "{\n\t.reg .b128 d, c, v;\n\t"
+      "mov.b128 c, {%2, %3};\n\t"
+      "mov.b128 v, {%4, %5};\n\t"
+      "atom.cas.b128 d, [%6], c, v;\n\t"
+      "mov.b128 {%0, %1}, d;\n\t}"
+      : "=l"(r.lo), "=l"(r.hi)
+      : "l"(cmp.lo), "l"(cmp.hi), "l"(val.lo), "l"(val.hi), "l"(p)
+      : "memory");
+  return r;
+}
+
+// Raise *p to at least v; returns the larger of v and what *p held.  The
+// first guess may be a torn read: the compare-and-swap validates it.
+__device__ __forceinline__ Key128 atomic_max_key(Key128* p, const Key128& v) {
+  Key128 cur;
+  cur.lo = *(volatile unsigned long long*)&p->lo;
+  cur.hi = *(volatile unsigned long long*)&p->hi;
+  while (key_gt(v, cur)) {
+    const Key128 prev = cas128(p, cur, v);
+    if (prev.lo == cur.lo && prev.hi == cur.hi) return v;
+    cur = prev;
+  }
+  return cur;
 }
 
 // Index-space position of a vertex from its doubled coordinates and t.

@@ -40,10 +40,10 @@ __device__ __forceinline__ void cross3(const double* a, const double* b, double*
   o[2] = a[0] * b[1] - a[1] * b[0];
 }
 
-__global__ void k_soft_tri_grad(const int16_t* __restrict__ idx2, const double* __restrict__ vt,
-                                const int32_t* __restrict__ tri, const long long* __restrict__ nt_dev,
+__global__ void k_soft_tri_grad(const int16_t* idx2, const double* vt,
+                                const int32_t* tri, const long long* nt_dev,
                                 long long tcap, MeshDims d, double sx, double sy, double sz, double gA, double gV,
-                                double* __restrict__ gvtx) {
+                                double* gvtx) {
   pdl_enter();
   const long long nt = min(*nt_dev, tcap);
   const double sp[3] = {sx, sy, sz};
@@ -88,8 +88,8 @@ __global__ void k_soft_tri_grad(const int16_t* __restrict__ idx2, const double* 
   }
 }
 
-__global__ void k_soft_d3_grad(const int16_t* __restrict__ idx2, const double* __restrict__ vt, int i, int j,
-                               MeshDims d, double sx, double sy, double sz, double gD, double* __restrict__ gvtx) {
+__global__ void k_soft_d3_grad(const int16_t* idx2, const double* vt, int i, int j,
+                               MeshDims d, double sx, double sy, double sz, double gD, double* gvtx) {
   pdl_enter();
   if (threadIdx.x != 0 || blockIdx.x != 0 || i < 0 || j < 0 || gD == 0.0) return;
   const double sp[3] = {sx, sy, sz};
@@ -110,9 +110,9 @@ __device__ __forceinline__ double voxel(const float* p, const MeshDims& d, int x
   return (double)__ldg(p + ((long long)z * d.ny + y) * d.nx + x);
 }
 
-__global__ void k_soft_scatter(const int16_t* __restrict__ idx2, const float* __restrict__ prob,
-                               const long long* __restrict__ nv_dev, long long vcap, MeshDims d, double sx, double sy,
-                               double sz, const double* __restrict__ gvtx, double* __restrict__ grad) {
+__global__ void k_soft_scatter(const int16_t* idx2, const float* prob,
+                               const long long* nv_dev, long long vcap, MeshDims d, double sx, double sy,
+                               double sz, const double* gvtx, double* grad) {
   pdl_enter();
   const long long nv = min(*nv_dev, vcap);
   const double sp[3] = {sx, sy, sz};

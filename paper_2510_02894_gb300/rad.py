@@ -24,6 +24,10 @@ class RadError(RuntimeError):
         self.status = status
 
 
+DERIVED = ("Sphericity", "SurfaceVolumeRatio", "Compactness1", "Compactness2", "SphericalDisproportion",
+           "MajorAxisLength", "MinorAxisLength", "LeastAxisLength", "Elongation", "Flatness")
+
+
 class Features(ctypes.Structure):
     _fields_ = [("MeshVolume", ctypes.c_double), ("SurfaceArea", ctypes.c_double), ("VoxelVolume", ctypes.c_double),
                 ("Maximum3DDiameter", ctypes.c_double), ("Maximum2DDiameterSlice", ctypes.c_double),
@@ -31,7 +35,8 @@ class Features(ctypes.Structure):
                 ("n_vertices", ctypes.c_int64), ("n_triangles", ctypes.c_int64), ("n_voxels", ctypes.c_int64),
                 ("argmax3d", ctypes.c_int32 * 2), ("argmax_slice", ctypes.c_int32 * 2),
                 ("argmax_column", ctypes.c_int32 * 2), ("argmax_row", ctypes.c_int32 * 2),
-                ("status", ctypes.c_int32), ("_pad", ctypes.c_int32)]
+                ("status", ctypes.c_int32), ("_pad", ctypes.c_int32)] + \
+        [(n, ctypes.c_double) for n in DERIVED]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k in ("MeshVolume", "SurfaceArea", "VoxelVolume", "Maximum3DDiameter",
@@ -41,6 +46,8 @@ class Features(ctypes.Structure):
             a = getattr(self, k)
             d[k] = (int(a[0]), int(a[1]))
         d["status"] = int(self.status)
+        for k in DERIVED:
+            d[k] = getattr(self, k)
         return d
 
 
@@ -68,7 +75,8 @@ class KernelStat(ctypes.Structure):
 
 
 _lib = None
-EXPORTS = ("rad_mesh", "rad_soft_mesh", "rad_shape", "rad_shape_plain_fp64", "rad_extract", "rad_extract_host",
+EXPORTS = ("rad_mesh", "rad_soft_mesh", "rad_shape", "rad_shape_plain_fp64", "rad_shape_fp64_variant", "rad_extract",
+           "rad_extract_host",
            "rad_workspace_free", "rad_mesh_free", "rad_mesh_copy", "rad_set_tuning", "rad_profile_enable",
            "rad_profile_read", "rad_profile_reset", "rad_launch_count", "rad_status_str", "rad_last_error",
            "rad_last_call_stats", "rad_soft_forward", "rad_soft_backward", "rad_batch_create", "rad_batch_run",
@@ -89,6 +97,8 @@ def lib():
         for name in ("rad_shape", "rad_shape_plain_fp64"):
             getattr(L, name).argtypes = [ctypes.POINTER(MeshT), ctypes.POINTER(Features), P]
             getattr(L, name).restype = I
+        L.rad_shape_fp64_variant.argtypes = [ctypes.POINTER(MeshT), I, ctypes.POINTER(Features), P]
+        L.rad_shape_fp64_variant.restype = I
         for name in ("rad_extract", "rad_extract_host"):
             getattr(L, name).argtypes = [P, P, P, ctypes.POINTER(Features), ctypes.POINTER(P), P]
             getattr(L, name).restype = I
@@ -216,6 +226,18 @@ def shape(m, stream=None):
 def shape_plain_fp64(m, stream=None):
     f = Features()
     _check(lib().rad_shape_plain_fp64(ctypes.byref(m.m), ctypes.byref(f), _stream(stream)))
+    return f.as_dict()
+
+
+# FP64 diameter variants of rad_shape_fp64_variant (rad.h)
+FP64_EQUAL_LOAD, FP64_BLOCK_ATOMICS, FP64_SHARED_2D, FP64_THREAD_LOCAL, FP64_PLAIN_1D, FP64_CULLED = 1, 2, 3, 4, 5, 6
+FP64_VARIANTS = {"equal_load": FP64_EQUAL_LOAD, "block_atomics": FP64_BLOCK_ATOMICS, "shared_2d": FP64_SHARED_2D,
+                 "thread_local": FP64_THREAD_LOCAL, "plain_1d": FP64_PLAIN_1D, "culled_fp64": FP64_CULLED}
+
+
+def shape_fp64_variant(m, variant, stream=None):
+    f = Features()
+    _check(lib().rad_shape_fp64_variant(ctypes.byref(m.m), int(variant), ctypes.byref(f), _stream(stream)))
     return f.as_dict()
 
 

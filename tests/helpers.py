@@ -33,3 +33,23 @@ def assert_features(got, ref, planes=True, rel=REL_TOL):
         assert got[k] == ref[k], (k, got[k], ref[k])
     for k in args:
         assert tuple(got[k]) == tuple(ref[k]), (k, got[k], ref[k])
+    assert_derived(got, ref, rel)
+
+
+CLOSED_FORM = ("Sphericity", "SurfaceVolumeRatio", "Compactness1", "Compactness2", "SphericalDisproportion")
+AXES = ("MajorAxisLength", "MinorAxisLength", "LeastAxisLength")
+
+
+def assert_derived(got, ref, rel=REL_TOL):
+    """Derived Shape features: closed forms in V and A within rel; principal
+    axes from the covariance eigenvalues within rel of the major axis (small
+    eigenvalues carry rounding relative to the largest)."""
+    if "Sphericity" not in ref or "Sphericity" not in got:
+        return
+    for k in CLOSED_FORM:
+        assert abs(got[k] - ref[k]) <= rel * max(abs(ref[k]), 1e-300), (k, got[k], ref[k])
+    major = ref["MajorAxisLength"]
+    for k in AXES:
+        assert abs(got[k] - ref[k]) <= rel * max(abs(ref[k]), 1e-300) + 1e-6 * major, (k, got[k], ref[k])
+    for k in ("Elongation", "Flatness"):
+        assert abs(got[k] - ref[k]) <= 1e-6, (k, got[k], ref[k])
