@@ -41,6 +41,7 @@ def _load():
         lib.orc_diameter3d_pruned.argtypes = [P, I64, P, P, P, P, P]
         lib.orc_diameter2d_grouped.argtypes = [P, I64, P, ctypes.c_int, P, P, P]
         lib.orc_soft_grad.argtypes = [P, D, D, D, I64, I64, P]
+        lib.orc_soft_grad4.argtypes = [P, D, D, P, P, P]
         lib.orc_subset_max.argtypes = [P, P, I64, P, P, P, P]
         lib.orc_pair_d2.restype = D
         lib.orc_pair_d2.argtypes = [P, I64, I64, P]
@@ -364,6 +365,19 @@ def soft_grad(mesh, gA, gV, gD, argmax3d=(-1, -1)):
     nx, ny, nz = mesh.dims
     grad = np.zeros((nz, ny, nx), np.float64)
     lib.orc_soft_grad(mesh._h, float(gA), float(gV), float(gD), int(argmax3d[0]), int(argmax3d[1]), _ptr(grad))
+    return grad
+
+
+def soft_grad_planes(mesh, gA, gV, gD4, pairs4):
+    """Analytic FP64 gradient of gA*A + gV*V + sum_q gD4[q]*D_q w.r.t. every
+    voxel, D_q the 3D, Slice, Column and Row diameters with their argmax
+    pairs pairs4[q] (each pair held fixed: the 3D term's formula per pair)."""
+    lib = _load()
+    nx, ny, nz = mesh.dims
+    grad = np.zeros((nz, ny, nx), np.float64)
+    g = np.array([float(x) for x in gD4], np.float64)
+    pr = np.array([int(v) for pq in pairs4 for v in pq], np.int64)
+    lib.orc_soft_grad4(mesh._h, float(gA), float(gV), _ptr(g), _ptr(pr), _ptr(grad))
     return grad
 
 

@@ -891,7 +891,19 @@ static void cross3(const double a[3], const double b[3], double o[3]) {
   o[2] = a[0] * b[1] - a[1] * b[0];
 }
 
+/* The same with the planar diameters too: gD[q] and the argmax pair
+ * (pairs[2q], pairs[2q + 1]) for q = 0 (3D), 1 (Slice), 2 (Column), 3 (Row).
+ * Each diameter term is the 3D term's formula on its own pair (the pair, and
+ * so the plane, held fixed). */
+int orc_soft_grad4(const orc_mesh* m, double gA, double gV, const double gD[4], const int64_t pairs[8], double* grad);
+
 int orc_soft_grad(const orc_mesh* m, double gA, double gV, double gD, int64_t i3, int64_t j3, double* grad) {
+  const double g4[4] = {gD, 0.0, 0.0, 0.0};
+  const int64_t p4[8] = {i3, j3, -1, -1, -1, -1, -1, -1};
+  return orc_soft_grad4(m, gA, gV, g4, p4, grad);
+}
+
+int orc_soft_grad4(const orc_mesh* m, double gA, double gV, const double gD[4], const int64_t pairs[8], double* grad) {
   int64_t nvox = m->dims[0] * m->dims[1] * m->dims[2];
   memset(grad, 0, sizeof(double) * (size_t)nvox);
   double* gp = (double*)calloc((size_t)(m->nv ? m->nv : 1) * 3, sizeof(double));
@@ -929,7 +941,9 @@ int orc_soft_grad(const orc_mesh* m, double gA, double gV, double gD, int64_t i3
       gp[3 * ic + k] += gV * vab[k] / 6.0;
     }
   }
-  if (i3 >= 0 && j3 >= 0 && gD != 0.0) {
+  for (int q = 0; q < 4; ++q) {
+    const int64_t i3 = pairs[2 * q], j3 = pairs[2 * q + 1];
+    if (i3 < 0 || j3 < 0 || gD[q] == 0.0) continue;
     double pi[3], pj[3], d[3];
     vpos_rel(m, i3, pi);
     vpos_rel(m, j3, pj);
@@ -937,8 +951,8 @@ int orc_soft_grad(const orc_mesh* m, double gA, double gV, double gD, int64_t i3
     double D = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
     if (D > 0.0)
       for (int k = 0; k < 3; ++k) {
-        gp[3 * i3 + k] += gD * d[k] / D;
-        gp[3 * j3 + k] -= gD * d[k] / D;
+        gp[3 * i3 + k] += gD[q] * d[k] / D;
+        gp[3 * j3 + k] -= gD[q] * d[k] / D;
       }
   }
   for (int64_t v = 0; v < m->nv; ++v) {

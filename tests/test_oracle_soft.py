@@ -116,3 +116,54 @@ def test_soft_gradient_finite_differences(seed):
         vp = vals.copy(); vp[z, y, x] += h
         Lp, _, _ = _loss(vp, sp, w)
         assert Lp == L0
+
+
+def _loss4(vals, sp, w):
+    f, m = oracle.features(vals, sp)
+    D = ("Maximum3DDiameter", "Maximum2DDiameterSlice", "Maximum2DDiameterColumn", "Maximum2DDiameterRow")
+    return w[0] * f["SurfaceArea"] + w[1] * f["MeshVolume"] + sum(w[2 + q] * f[D[q]] for q in range(4)), f, m
+
+
+ARGS4 = ("argmax3d", "argmax_slice", "argmax_column", "argmax_row")
+
+
+@pytest.mark.parametrize("seed", [0, 3])
+def test_soft_planar_gradient_finite_differences(seed):
+    """The planar-diameter terms of the gradient (each argmax pair held
+    fixed) against central differences of the oracle's FP64 forward pass, on
+    band voxels whose perturbation keeps the mesh and all four argmax pairs."""
+    vals, sp = synth.soft_160(seed, n=30)
+    vals = vals.astype(np.float64)
+    rng = np.random.default_rng(200 + seed)
+    w = (0.4, -0.2, 0.0, 1.3, -0.9, 0.7)  # A, V, D3, Slice, Column, Row
+    L0, f0, m0 = _loss4(vals, sp, w)
+    pairs = [f0[k] for k in ARGS4]
+    g = oracle.soft_grad_planes(m0, w[0], w[1], w[2:], pairs)
+    # the planar argmax vertices carry a gradient of their own
+    gp = oracle.soft_grad_planes(m0, 0.0, 0.0, (0.0, 1.0, 1.0, 1.0), pairs)
+    assert np.count_nonzero(gp) >= 4
+    band = np.argwhere(gp != 0.0)
+    h = 1e-4
+    checked = 0
+    for idx in rng.permutation(len(band)):
+        z, y, x = band[idx]
+        vp = vals.copy(); vp[z, y, x] += h
+        vm = vals.copy(); vm[z, y, x] -= h
+        Lp, fp, mp = _loss4(vp, sp, w)
+        Lm, fm, mm = _loss4(vm, sp, w)
+        if not (np.array_equal(mp.tri, m0.tri) and np.array_equal(mm.tri, m0.tri)):
+            continue
+        if any(fp[k] != f0[k] or fm[k] != f0[k] for k in ARGS4):
+            continue
+        fd = (Lp - Lm) / (2 * h)
+        assert fd == pytest.approx(g[z, y, x], rel=1e-5, abs=1e-7), (z, y, x)
+        checked += 1
+    assert checked >= 4
+
+
+def test_soft_grad_planes_reduces_to_3d_term():
+    vals, sp = synth.soft_160(1, n=24)
+    f, m = oracle.features(vals, sp)
+    a = oracle.soft_grad(m, 0.3, 0.6, 1.7, f["argmax3d"])
+    b = oracle.soft_grad_planes(m, 0.3, 0.6, (1.7, 0.0, 0.0, 0.0), [f[k] for k in ARGS4])
+    assert np.array_equal(a, b)
