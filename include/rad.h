@@ -229,6 +229,68 @@ rad_status rad_soft_backward(const float* prob_dev, const int64_t dims[3], const
                              const double gout[3], const int32_t argmax[2], double* grad_dev, rad_workspace_t** ws,
                              void* stream);
 
+/* All features of a soft map in *out (host), as rad_shape gives them for
+ * its mesh: SurfaceArea, MeshVolume, VoxelVolume (voxels above 0.5), the
+ * maximum 3D diameter and the planar diameters with their argmax pairs, and
+ * the derived Shape features.  A plane of a soft mesh is the set of vertices
+ * whose coordinate on that axis is exactly the same FP64 value (on a grid
+ * plane, or off it where interpolated vertices of several edges coincide).
+ * Synchronises `stream`. */
+rad_status rad_soft_features(const float* prob_dev, const int64_t dims[3], const double spacing[3],
+                             rad_features_t* out, rad_workspace_t** ws, void* stream);
+
+/* Adjoint with the planar diameters: grad_dev (device, nx*ny*nz doubles,
+ * overwritten) receives the gradient of
+ *   gout[0] A + gout[1] V + gout[2] D3 + gout[3] DSlice + gout[4] DColumn + gout[5] DRow
+ * with the argmax pairs (argmax[2q], argmax[2q+1]) of the 3D, Slice, Column
+ * and Row diameters from rad_soft_features (-1, -1 leaves a term out).  Each
+ * pair is held fixed, a planar pair with its plane; otherwise as
+ * rad_soft_backward.  Synchronises `stream`. */
+rad_status rad_soft_backward_planes(const float* prob_dev, const int64_t dims[3], const double spacing[3],
+                                    const double gout[6], const int32_t argmax[8], double* grad_dev,
+                                    rad_workspace_t** ws, void* stream);
+
+/* Batches of soft maps: n maps (device float32 maps probs_dev[i] of size
+ * dims[3i..3i+2] with spacing spacing[3i..3i+2]) through one set of launches
+ * for the meshes, one for the diameters and one for the adjoint.
+ * rad_soft_batch_forward writes out[0..n-1] (host) like rad_soft_features;
+ * rad_soft_batch_backward writes each grads_dev[i] (device, overwritten) like
+ * rad_soft_backward_planes, with weights gout[6i..6i+5] and argmax pairs
+ * argmax[8i..8i+7].  n >= 1; any NULL pointer, bad size or spacing, or argmax
+ * pair outside its map's mesh gives RAD_ERR_INVALID_ARG before any launch.
+ * Synchronise `stream`. */
+rad_status rad_soft_batch_forward(int n, const float* const* probs_dev, const int64_t* dims, const double* spacing,
+                                  rad_features_t* out, rad_workspace_t** ws, void* stream);
+rad_status rad_soft_batch_backward(int n, const float* const* probs_dev, const int64_t* dims, const double* spacing,
+                                   const double* gout, const int32_t* argmax, double* const* grads_dev,
+                                   rad_workspace_t** ws, void* stream);
+
+/* ---- preprocessing: crop to the ROI and resample ------------------------------- */
+
+/* Crop a device uint8 mask [nz][ny][nx] to the bounding box of its ROI
+ * voxels and optionally resample it by nearest neighbour: the preprocessing
+ * the paper names as open work that could move to the GPU (Sec. 3,
+ * "Discussion of the results").  Definitions:
+ *   ROI voxel   value == label (0 <= label <= 255), or value != 0 (label < 0);
+ *   box         per axis the smallest and largest ROI index, widened by pad
+ *               voxels per side and clamped to the grid: lo_k, m_k voxels;
+ *   resample    (new_spacing non-NULL, every entry > 0) n'_k =
+ *               floor((m_k - 1) s_k / s'_k) + 1 output voxels, output voxel i
+ *               taking input voxel lo_k + min(m_k - 1, floor(i s'_k / s_k + 1/2))
+ *               (FP64, left to right); without it the box itself (n'_k = m_k);
+ *   output      1 where the sampled voxel is an ROI voxel, else 0.
+ * Writes out_dims (n'_x, n'_y, n'_z), box_lo (the input index of output
+ * voxel 0) and out_spacing (host) always; writes the output voxels to out_dev
+ * (device, [n'_z][n'_y][n'_x] uint8, caller-owned) when out_capacity bytes
+ * suffice, else returns RAD_ERR_CAPACITY having written nothing there (call
+ * with out_capacity 0 to ask for the size).  A mask without ROI voxels gives
+ * out_dims (0, 0, 0) and RAD_OK.  Scratch lives in *ws (NULL on first use).
+ * Synchronises `stream`. */
+rad_status rad_crop_resample(const uint8_t* mask_dev, const int64_t dims[3], const double spacing[3], int label,
+                             int pad, const double new_spacing[3], uint8_t* out_dev, int64_t out_capacity,
+                             int64_t out_dims[3], int64_t box_lo[3], double out_spacing[3], rad_workspace_t** ws,
+                             void* stream);
+
 /* ---- failure detection check -------------------------------------------- */
 
 /* Every device-side wait of the library (the look-back of its single-pass

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <atomic>
 #include <mutex>
 #include <string>
@@ -322,6 +323,8 @@ struct Work {
   DevBuf mask;  // device copy of a host mask (rad_extract_host)
   DevBuf gvtx;  // per-vertex position gradients (soft adjoint)
   DevBuf plain; // result of the plain FP64 kernel
+  DevBuf soft_maps;  // SoftMap table of a soft adjoint batch
+  DevBuf prep;       // crop/resample: box reduction, its result and the index maps
   // plan of the current batch
   std::vector<Roi> rois, up_rois;     // planned / last uploaded
   std::vector<RoiDiam> rd, up_rd;
@@ -355,7 +358,7 @@ struct Work {
       if (e) cudaEventDestroy(e);
     for (DevBuf* b : {&ms.bits, &ms.counts, &ms.wpre, &ms.tpre, &ms.wlist, &ms.prefix, &ms.chunk, &ms.cubes, &ms.hist, &ms.partial,
                       &ms.bintab, &ms.tabsp, &ds.misc, &ds.plain_part, &result, &ro, &dout, &rois_dev,
-                      &rd_dev, &idx2, &vt, &tri, &mask, &gvtx, &plain})
+                      &rd_dev, &idx2, &vt, &tri, &mask, &gvtx, &plain, &soft_maps, &prep})
       b->release();
     if (host) cudaFreeHost(host);
     if (hfeats) cudaFreeHost(hfeats);
@@ -445,7 +448,7 @@ static rad_status enqueue_mesh(Work& w, cudaStream_t st, bool count) {
 static rad_status enqueue_shape(Work& w, cudaStream_t st) {
   ResultBlock* dr = w.dres();
   RAD_TRY(diam_run(w.mb.n, w.rd_dev.as<RoiDiam>(), w.dro(), &dr->tot.nv, w.vcap, w.nkeys, w.nplanes, w.ntab,
-                   !w.soft, w.idx2.as<int16_t>(), w.soft ? w.vt.as<double>() : nullptr, w.ds, w.dout.as<DiamOut>(),
+                   true, w.idx2.as<int16_t>(), w.soft ? w.vt.as<double>() : nullptr, w.ds, w.dout.as<DiamOut>(),
                    &dr->stats, st));
   return RAD_OK;
 }
@@ -475,7 +478,7 @@ static rad_status enqueue_pass(Work& w, cudaStream_t st) {
   RAD_CUDA(cudaEventRecord(w.ev_fork, st));
   RAD_CUDA(cudaStreamWaitEvent(w.side, w.ev_fork, 0));
   RAD_TRY(diam_run(w.mb.n, w.rd_dev.as<RoiDiam>(), w.dro(), &dr->tot.nv, w.vcap, w.nkeys, w.nplanes, w.ntab,
-                   !w.soft, w.idx2.as<int16_t>(), w.soft ? w.vt.as<double>() : nullptr, w.ds, w.dout.as<DiamOut>(),
+                   true, w.idx2.as<int16_t>(), w.soft ? w.vt.as<double>() : nullptr, w.ds, w.dout.as<DiamOut>(),
                    &dr->stats, w.side, 1));
   RAD_CUDA(cudaEventRecord(w.ev_init, w.side));
   RAD_TRY(mesh_count(w.mb, w.ms, &dr->tot, w.dro(), st));
@@ -491,7 +494,7 @@ static rad_status enqueue_pass(Work& w, cudaStream_t st) {
   RAD_CUDA(cudaEventRecord(w.ev_tot, w.side));
   RAD_CUDA(cudaStreamWaitEvent(st, w.ev_init, 0));
   RAD_TRY(diam_run(w.mb.n, w.rd_dev.as<RoiDiam>(), w.dro(), &dr->tot.nv, w.vcap, w.nkeys, w.nplanes, w.ntab,
-                   !w.soft, w.idx2.as<int16_t>(), w.soft ? w.vt.as<double>() : nullptr, w.ds, w.dout.as<DiamOut>(),
+                   true, w.idx2.as<int16_t>(), w.soft ? w.vt.as<double>() : nullptr, w.ds, w.dout.as<DiamOut>(),
                    &dr->stats, st, 2));
   RAD_CUDA(cudaStreamWaitEvent(st, w.ev_tot, 0));
   return enqueue_finish(w, true, st);
@@ -913,16 +916,96 @@ rad_status rad_batch_run(rad_batch_t* b, rad_features_t* out, void* stream) {
 
 void rad_batch_destroy(rad_batch_t* b) { delete b; }
 
+}  // extern "C"
+
+namespace {
+
+rad_status check_soft_args(int n, const float* const* probs, const int64_t* dims, const double* spacing) {
+  if (n < 1 || !probs || !dims || !spacing) {
+    set_error("n must be >= 1 and probs, dims, spacing non-NULL");
+    return RAD_ERR_INVALID_ARG;
+  }
+  for (int i = 0; i < n; ++i) {
+    RAD_TRY(check_geometry(dims + 3 * i, spacing + 3 * i));
+    RAD_TRY(check_device_ptr(probs[i], "prob_dev"));
+  }
+  return RAD_OK;
+}
+
+// Features of n soft maps: one set of launches for the meshes, one for the
+// diameters (the work and candidate lists grow and the diameters rerun when
+// they overflow).
+rad_status soft_features_impl(Work& w, int n, const float* const* probs, const int64_t* dims, const double* sp,
+                              rad_features_t* out, cudaStream_t st) {
+  std::vector<const void*> ptrs(probs, probs + n);
+  RAD_TRY(prepare(w, n, ptrs.data(), dims, sp, true, st));
+  RAD_TRY(run_mesh_only(w, st, nullptr));
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    RAD_TRY(enqueue_shape(w, st));
+    RAD_TRY(enqueue_finish(w, true, st));
+    RAD_CUDA(cudaStreamSynchronize(st));
+    const unsigned int s = w.host->stats.status;
+    if (s & DEV_ERR_WORKCAP) { w.ds.work_cap *= 4; continue; }
+    if (s & DEV_ERR_CANDCAP) { w.ds.cand_cap *= 4; continue; }
+    RAD_TRY(status_from_dev(s));
+    memcpy(out, w.hfeats, sizeof(rad_features_t) * n);
+    record_stats(*w.host, 0, (long long)(sizeof(ResultBlock) + sizeof(rad_features_t) * n), true);
+    return RAD_OK;
+  }
+  return status_from_dev(w.host->stats.status);
+}
+
+// Gradients of n soft maps (meshes recomputed, then one set of adjoint launches).
+rad_status soft_backward_impl(Work& w, int n, const float* const* probs, const int64_t* dims, const double* sp,
+                              const double* gout, const int32_t* argmax, double* const* grads, cudaStream_t st) {
+  std::vector<const void*> ptrs(probs, probs + n);
+  RAD_TRY(prepare(w, n, ptrs.data(), dims, sp, true, st));
+  RAD_TRY(run_mesh_only(w, st, nullptr));
+  std::vector<RoiOut> ro(n);
+  RAD_CUDA(cudaMemcpyAsync(ro.data(), w.dro(), sizeof(RoiOut) * n, cudaMemcpyDeviceToHost, st));
+  RAD_CUDA(cudaStreamSynchronize(st));
+  std::vector<SoftMap> maps(n);
+  long long vox = 0;
+  for (int i = 0; i < n; ++i) {
+    SoftMap& m = maps[i];
+    m.prob = probs[i];
+    m.grad = grads[i];
+    m.nx = (int)dims[3 * i]; m.ny = (int)dims[3 * i + 1]; m.nz = (int)dims[3 * i + 2]; m.pad = 0;
+    m.sx = sp[3 * i]; m.sy = sp[3 * i + 1]; m.sz = sp[3 * i + 2];
+    for (int k = 0; k < 6; ++k) m.gout[k] = gout[6 * i + k];
+    const long long nv = ro[i].nv;
+    for (int q = 0; q < 4; ++q) {
+      const int a = argmax[8 * i + 2 * q], b = argmax[8 * i + 2 * q + 1];
+      if ((a >= 0 || b >= 0) && (a < 0 || b < 0 || a >= nv || b >= nv || a == b)) {
+        set_error("argmax pair (%d, %d) is not a vertex pair of map %d's mesh (%lld vertices)", a, b, i, nv);
+        return RAD_ERR_INVALID_ARG;
+      }
+      m.pair[2 * q] = a;
+      m.pair[2 * q + 1] = b;
+    }
+    m.vox0 = vox;
+    vox += (long long)m.nx * m.ny * m.nz;
+  }
+  RAD_TRY(w.soft_maps.reserve(sizeof(SoftMap) * n));
+  RAD_CUDA(cudaMemcpyAsync(w.soft_maps.p, maps.data(), sizeof(SoftMap) * n, cudaMemcpyHostToDevice, st));
+  RAD_TRY(w.gvtx.reserve(sizeof(double) * 3 * std::max<long long>(w.vcap, 1)));
+  ResultBlock* dr = w.dres();
+  RAD_TRY(soft_adjoint(w.idx2.as<int16_t>(), w.vt.as<double>(), w.tri.as<int32_t>(), &dr->tot.nv, &dr->tot.nt, w.vcap,
+                       w.tcap, w.dro(), w.soft_maps.as<SoftMap>(), n, vox, w.gvtx.as<double>(), st));
+  RAD_CUDA(cudaStreamSynchronize(st));  // the host table may go once the copy has run
+  return RAD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 rad_status rad_soft_forward(const float* prob_dev, const int64_t dims[3], const double spacing[3], double out[3],
                             int32_t argmax[2], rad_workspace_t** ws, void* stream) {
-  RAD_TRY(check_geometry(dims, spacing));
   if (!out || !argmax || !ws) { set_error("out, argmax and ws must be non-NULL"); return RAD_ERR_INVALID_ARG; }
-  RAD_TRY(check_device_ptr(prob_dev, "prob_dev"));
-  rad_workspace_t* w = ensure_ws(ws);
-  cudaStream_t st = (cudaStream_t)stream;
-  RAD_TRY(build_mesh(prob_dev, true, dims, spacing, w->work, &w->mesh, st));
+  RAD_TRY(check_soft_args(1, &prob_dev, dims, spacing));
   rad_features_t f;
-  RAD_TRY(shape_of_mesh(&w->mesh, w->work, false, &f, st));
+  RAD_TRY(soft_features_impl(ensure_ws(ws)->work, 1, &prob_dev, dims, spacing, &f, (cudaStream_t)stream));
   out[0] = f.SurfaceArea;
   out[1] = f.MeshVolume;
   out[2] = f.Maximum3DDiameter;
@@ -931,33 +1014,92 @@ rad_status rad_soft_forward(const float* prob_dev, const int64_t dims[3], const 
   return RAD_OK;
 }
 
+rad_status rad_soft_features(const float* prob_dev, const int64_t dims[3], const double spacing[3],
+                             rad_features_t* out, rad_workspace_t** ws, void* stream) {
+  if (!out || !ws) { set_error("out and ws must be non-NULL"); return RAD_ERR_INVALID_ARG; }
+  RAD_TRY(check_soft_args(1, &prob_dev, dims, spacing));
+  return soft_features_impl(ensure_ws(ws)->work, 1, &prob_dev, dims, spacing, out, (cudaStream_t)stream);
+}
+
+rad_status rad_soft_batch_forward(int n, const float* const* probs_dev, const int64_t* dims, const double* spacing,
+                                  rad_features_t* out, rad_workspace_t** ws, void* stream) {
+  if (!out || !ws) { set_error("out and ws must be non-NULL"); return RAD_ERR_INVALID_ARG; }
+  RAD_TRY(check_soft_args(n, probs_dev, dims, spacing));
+  return soft_features_impl(ensure_ws(ws)->work, n, probs_dev, dims, spacing, out, (cudaStream_t)stream);
+}
+
 rad_status rad_soft_backward(const float* prob_dev, const int64_t dims[3], const double spacing[3],
                              const double gout[3], const int32_t argmax[2], double* grad_dev, rad_workspace_t** ws,
                              void* stream) {
-  RAD_TRY(check_geometry(dims, spacing));
   if (!gout || !argmax || !ws) { set_error("gout, argmax and ws must be non-NULL"); return RAD_ERR_INVALID_ARG; }
-  RAD_TRY(check_device_ptr(prob_dev, "prob_dev"));
+  RAD_TRY(check_soft_args(1, &prob_dev, dims, spacing));
   RAD_TRY(check_device_ptr(grad_dev, "grad_dev"));
-  rad_workspace_t* w = ensure_ws(ws);
-  Work& wk = w->work;
-  cudaStream_t st = (cudaStream_t)stream;
-  // recompute the mesh instead of keeping it from the forward pass
-  RAD_TRY(build_mesh(prob_dev, true, dims, spacing, wk, &w->mesh, st));
-  const long long nv = w->mesh.n_vertices;
-  if ((argmax[0] >= 0 || argmax[1] >= 0) &&
-      (argmax[0] < 0 || argmax[1] < 0 || argmax[0] >= nv || argmax[1] >= nv || argmax[0] == argmax[1])) {
-    set_error("argmax pair (%d, %d) is not a vertex pair of this map's mesh (%lld vertices)", argmax[0], argmax[1],
-              nv);
+  const double g6[6] = {gout[0], gout[1], gout[2], 0.0, 0.0, 0.0};
+  const int32_t a8[8] = {argmax[0], argmax[1], -1, -1, -1, -1, -1, -1};
+  return soft_backward_impl(ensure_ws(ws)->work, 1, &prob_dev, dims, spacing, g6, a8, &grad_dev, (cudaStream_t)stream);
+}
+
+rad_status rad_soft_backward_planes(const float* prob_dev, const int64_t dims[3], const double spacing[3],
+                                    const double gout[6], const int32_t argmax[8], double* grad_dev,
+                                    rad_workspace_t** ws, void* stream) {
+  if (!gout || !argmax || !ws) { set_error("gout, argmax and ws must be non-NULL"); return RAD_ERR_INVALID_ARG; }
+  RAD_TRY(check_soft_args(1, &prob_dev, dims, spacing));
+  RAD_TRY(check_device_ptr(grad_dev, "grad_dev"));
+  return soft_backward_impl(ensure_ws(ws)->work, 1, &prob_dev, dims, spacing, gout, argmax, &grad_dev,
+                            (cudaStream_t)stream);
+}
+
+rad_status rad_soft_batch_backward(int n, const float* const* probs_dev, const int64_t* dims, const double* spacing,
+                                   const double* gout, const int32_t* argmax, double* const* grads_dev,
+                                   rad_workspace_t** ws, void* stream) {
+  if (!gout || !argmax || !grads_dev || !ws) {
+    set_error("gout, argmax, grads_dev and ws must be non-NULL");
     return RAD_ERR_INVALID_ARG;
   }
-  RAD_TRY(wk.gvtx.reserve(sizeof(double) * 3 * std::max<long long>(wk.vcap, 1)));
-  const MeshDims d = make_dims(dims);
-  ResultBlock* dr = wk.dres();
-  RAD_TRY(soft_adjoint(wk.idx2.as<int16_t>(), wk.vt.as<double>(), wk.tri.as<int32_t>(), &dr->tot.nv, &dr->tot.nt,
-                       wk.vcap, wk.tcap, prob_dev, d, spacing, gout, argmax[0], argmax[1], wk.gvtx.as<double>(),
-                       grad_dev, st));
-  RAD_CUDA(cudaStreamSynchronize(st));
-  return RAD_OK;
+  RAD_TRY(check_soft_args(n, probs_dev, dims, spacing));
+  for (int i = 0; i < n; ++i) RAD_TRY(check_device_ptr(grads_dev[i], "grads_dev"));
+  return soft_backward_impl(ensure_ws(ws)->work, n, probs_dev, dims, spacing, gout, argmax, grads_dev,
+                            (cudaStream_t)stream);
+}
+
+rad_status rad_crop_resample(const uint8_t* mask_dev, const int64_t dims[3], const double spacing[3], int label,
+                             int pad, const double new_spacing[3], uint8_t* out_dev, int64_t out_capacity,
+                             int64_t out_dims[3], int64_t box_lo[3], double out_spacing[3], rad_workspace_t** ws,
+                             void* stream) {
+  RAD_TRY(check_geometry(dims, spacing));
+  if (!out_dims || !box_lo || !out_spacing || !ws) {
+    set_error("out_dims, box_lo, out_spacing and ws must be non-NULL");
+    return RAD_ERR_INVALID_ARG;
+  }
+  if (label > 255 || pad < 0 || out_capacity < 0) {
+    set_error("label must be < 256 (negative: any non-zero value), pad and out_capacity >= 0");
+    return RAD_ERR_INVALID_ARG;
+  }
+  if (new_spacing)
+    for (int k = 0; k < 3; ++k)
+      if (!(new_spacing[k] > 0.0) || !std::isfinite(new_spacing[k])) {
+        set_error("new_spacing must be positive and finite");
+        return RAD_ERR_INVALID_ARG;
+      }
+  RAD_TRY(check_device_ptr(mask_dev, "mask_dev"));
+  cudaStream_t st = (cudaStream_t)stream;
+  Work& w = ensure_ws(ws)->work;
+  PrepInfo info;
+  RAD_TRY(prep_bbox(mask_dev, dims, spacing, label, pad, new_spacing, w.prep, &info, st));
+  for (int k = 0; k < 3; ++k) {
+    out_dims[k] = info.nout[k];
+    box_lo[k] = info.lo[k];
+    out_spacing[k] = new_spacing ? new_spacing[k] : spacing[k];
+  }
+  record_stats(ResultBlock{}, 0, (long long)sizeof(PrepInfo), false);
+  if (info.empty) return RAD_OK;
+  const long long need = info.nout[0] * info.nout[1] * info.nout[2];
+  if (need > out_capacity || !out_dev) {
+    set_error("output needs %lld bytes, capacity %lld", need, (long long)out_capacity);
+    return RAD_ERR_CAPACITY;
+  }
+  RAD_TRY(check_device_ptr(out_dev, "out_dev"));
+  return prep_gather(mask_dev, dims, spacing, label, new_spacing, info, w.prep, out_dev, st);
 }
 
 rad_status rad_check_bounded_wait(void* stream) {

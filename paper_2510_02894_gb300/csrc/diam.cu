@@ -125,7 +125,8 @@ struct Counters {
   unsigned long long items_evaluated, pairs_evaluated;
   unsigned int status;
   unsigned int n_refine;     // surviving coarse tile pairs
-  unsigned int seed_done, pad2;  // last-block ticket of the seed
+  unsigned int seed_done;  // last-block ticket of the seed
+  unsigned int n_groups;   // planes of a soft map off the grid planes (groups of equal coordinate)
 };
 
 // Batch-wide parameters of one run.
@@ -137,6 +138,26 @@ struct Params {
   long long max_fine, refine_cap;  // tiles of fine problems (their region after max_tiles); coarse pairs
   long long nv_cap;   // vertex pool capacity: device counts are clamped to it
   long long sweep_min;  // ROIs with at least this many vertices get the farthest-point seed
+};
+
+// Planes of soft maps.  A soft vertex lies on a grid edge: on the edge's
+// axis its coordinate is g + t.  Where that value is an integer the vertex
+// lies on a grid plane, and it joins that plane's problem like a mask vertex.
+// Otherwise its plane (the vertices whose coordinate on that axis is exactly
+// the same FP64 value, as the definition of the planar diameters asks) is
+// found through a hash table keyed by (ROI, axis, value bits): every group of
+// two or more vertices becomes one problem with a key of its own after all
+// ROIs' keys; vertices alone on their value go to one spare key that no
+// problem covers.
+struct FracState {
+  Key128* hkey = nullptr;  // (value bits, (ROI << 2 | axis) + 1); zero: empty slot
+  int* hcnt = nullptr;     // vertices per slot
+  int* hgid = nullptr;     // group of a slot with two or more vertices
+  int* vslot = nullptr;    // slot of each vertex, -1: on a grid plane
+  int* gra = nullptr;      // (ROI << 2 | axis) of each group
+  long long hmask = 0;     // table size - 1 (a power of two at least twice the vertex capacity)
+  long long fbase = 0;     // key of group 0
+  long long gcap = 0;      // group keys (the spare key is fbase + gcap)
 };
 
 // Expansion form: a2 = (-2 P_i, n_i), b = (P_j, n_j).  The FMA chain starts
@@ -234,6 +255,24 @@ __device__ __forceinline__ long long key_of(const RoiDiam& p, const int q[3], in
   return p.key0 + p.S2 + (long long)x1 * p.PY * p.PZ + (long long)pz * p.PY + py;
 }
 
+// Plane key (kinds 1..3) of vertex v: a mask vertex, or a soft vertex off
+// its edge's axis, by key_of; a soft vertex on a grid plane by key_of with
+// its exact doubled coordinate; otherwise its group's key (see FracState).
+__device__ __forceinline__ long long plane_key(const RoiDiam& r, const int q[3], int kind, long long v,
+                                               const double* vt, const FracState& fs) {
+  const int a = 3 - kind;  // Slice: z, Column: y, Row: x
+  if (vt == nullptr || !(q[a] & 1)) return key_of(r, q, kind);
+  const double u = __dadd_rn((double)((q[a] - 1) >> 1), vt[v]);
+  if (u == floor(u)) {
+    int qq[3] = {q[0], q[1], q[2]};
+    qq[a] = 2 * (int)u;
+    return key_of(r, qq, kind);
+  }
+  const int h = fs.vslot[v];
+  if (h >= 0 && fs.hcnt[h] >= 2) return fs.fbase + fs.hgid[h];
+  return fs.fbase + fs.gcap;
+}
+
 // ROI of a global vertex id (last ROI whose first vertex is <= v).
 __device__ __forceinline__ int roi_of_vertex(const RoiOut* ro, int n, long long v) {
   int lo = 0, hi = n - 1;
@@ -321,13 +360,74 @@ __device__ __forceinline__ void sweep_finish(const SweepAcc& a, int block_roi, u
   if (threadIdx.x == 0) sweep_global(block_roi, *s_key, slot, ps);
 }
 
+// fmix64, the finalizer of MurmurHash3 (Appleby): a 64-bit mixing function.
+__device__ __forceinline__ unsigned long long mix64(unsigned long long x) {
+  x ^= x >> 33;
+  x *= 0xff51afd7ed558ccdull;
+  x ^= x >> 33;
+  x *= 0xc4ceb9fe1a85ec53ull;
+  x ^= x >> 33;
+  return x;
+}
+
+// Soft maps: every vertex whose coordinate on its edge's axis is not an
+// integer enters the hash table (open addressing, linear probing, slots
+// claimed by a 128-bit compare-and-swap) and counts itself in its slot.
+__global__ void k_frac_insert(const int16_t* idx2, const double* vt, const long long* nv_dev, const RoiOut* ro,
+                              Params p, FracState fs, Counters* cnt) {
+  pdl_enter();
+  const long long n = min(*nv_dev, p.nv_cap);
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
+    int q[3];
+    vertex_q(idx2, v, q);
+    const int a = (q[0] & 1) ? 0 : ((q[1] & 1) ? 1 : 2);
+    const double u = __dadd_rn((double)((q[a] - 1) >> 1), vt[v]);
+    int slot = -1;
+    if (u != floor(u)) {
+      const int roi = p.n == 1 ? 0 : roi_of_vertex(ro, p.n, v);
+      Key128 key;
+      key.lo = (unsigned long long)__double_as_longlong(u);
+      key.hi = (((unsigned long long)roi << 2) | (unsigned long long)a) + 1ull;
+      long long h = (long long)(mix64(key.lo ^ mix64(key.hi)) & (unsigned long long)fs.hmask);
+      for (long long probe = 0; probe <= fs.hmask; ++probe) {
+        const Key128 old = cas128(&fs.hkey[h], Key128{0ull, 0ull}, key);
+        if ((old.lo == 0ull && old.hi == 0ull) || (old.lo == key.lo && old.hi == key.hi)) {
+          slot = (int)h;
+          break;
+        }
+        h = (h + 1) & fs.hmask;
+      }
+      if (slot >= 0) atomicAdd(&fs.hcnt[slot], 1);
+      else atomicOr(&cnt->status, DEV_ERR_PROBCAP);  // a full table: not reached at twice the vertex capacity
+    }
+    fs.vslot[v] = slot;
+  }
+}
+
+// Every slot with two or more vertices becomes a group (a planar problem).
+__global__ void k_frac_assign(FracState fs, Counters* cnt) {
+  pdl_enter();
+  for (long long h = blockIdx.x * (long long)blockDim.x + threadIdx.x; h <= fs.hmask;
+       h += (long long)gridDim.x * blockDim.x) {
+    if (fs.hcnt[h] < 2) continue;
+    const unsigned int g = atomicAdd(&cnt->n_groups, 1u);
+    if ((long long)g < fs.gcap) {
+      fs.hgid[h] = (int)g;
+      fs.gra[g] = (int)(fs.hkey[h].hi - 1ull);
+    } else {
+      fs.hgid[h] = (int)fs.gcap;  // the spare key; reported
+      atomicOr(&cnt->status, DEV_ERR_PROBCAP);
+    }
+  }
+}
+
 // Key histogram, warp-aggregated: lanes with equal keys (consecutive vertices
 // share cells and planes) make one atomic.  Also the first sweep of the 3D
 // seed: the vertex farthest from each ROI's first vertex.
 __global__ void k_hist(const int16_t* idx2, const double* vt,
                        const long long* nv_dev, const RoiDiam* rd,
                        const RoiOut* ro, Params p, const float* ctab,
-                       int* hist, unsigned long long* sweep, ProblemState* ps) {
+                       int* hist, unsigned long long* sweep, ProblemState* ps, FracState fs) {
   pdl_enter();
   __shared__ unsigned long long s_key;
   const long long n = min(*nv_dev, p.nv_cap);
@@ -355,7 +455,7 @@ __global__ void k_hist(const int16_t* idx2, const double* vt,
     const RoiDiam& r = rd[roi];
     for (int k = 0; k < 4; ++k) {
       const bool use = v < n && (k == 0 || r.planes);
-      const long long key = use ? key_of(r, q, k) : -1;
+      const long long key = use ? (k == 0 ? key_of(r, q, 0) : plane_key(r, q, k, v, vt, fs)) : -1;
       const unsigned int peers = __match_any_sync(0xffffffffu, key);
       if (key >= 0 && lane == __ffs(peers) - 1) atomicAdd(&hist[key], __popc(peers));
     }
@@ -373,7 +473,7 @@ __global__ void k_scatter(const int16_t* idx2, const double* vt,
                           const RoiOut* ro, Params p, const long long* offs,
                           int* cursor, const float* ctab,
                           float4* sorted, int* ids,
-                          const unsigned long long* sweep, ProblemState* ps) {
+                          const unsigned long long* sweep, ProblemState* ps, FracState fs) {
   pdl_enter();
   __shared__ unsigned long long s_key;
   SweepAcc acc;
@@ -404,7 +504,7 @@ __global__ void k_scatter(const int16_t* idx2, const double* vt,
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const bool use = v < n && (k == 0 || r.planes);
-      key[k] = use ? key_of(r, q, k) : -1;
+      key[k] = use ? (k == 0 ? key_of(r, q, 0) : plane_key(r, q, k, v, vt, fs)) : -1;
       peers[k] = __match_any_sync(0xffffffffu, key[k]);
     }
 #pragma unroll
@@ -510,12 +610,13 @@ __device__ __forceinline__ long long chunks_upto(long long m) {
 }
 
 __global__ void k_setup(const RoiDiam* rd, Params p, const long long* offs,
-                        Problem* probs, int* chunk0, Counters* cnt) {
+                        Problem* probs, int* chunk0, Counters* cnt, FracState fs) {
   pdl_enter();
   const int lane = threadIdx.x & 31;
   const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  const long long items = p.n + p.nplanes;
+  const long long items = p.n + p.nplanes + (fs.hkey ? fs.gcap : 0);
+  const long long ngroups = fs.hkey ? min((long long)cnt->n_groups, fs.gcap) : 0;
   for (long long r0 = 0; r0 < items; r0 += nwarps * 32) {
     // one lane per candidate problem, dealt with a stride of the warp count,
     // so the ROIs' 3D problems (the largest) go to different warps
@@ -529,6 +630,15 @@ __global__ void k_setup(const RoiDiam* rd, Params p, const long long* offs,
         const RoiDiam& r = rd[roi];
         k0 = r.key0;
         k1 = r.key0 + r.C3;
+      } else if (it >= p.n + p.nplanes) {  // a soft map's plane off the grid planes
+        const long long g = it - p.n - p.nplanes;
+        k0 = k1 = 0;
+        if (g < ngroups) {
+          roi = fs.gra[g] >> 2;
+          axis = fs.gra[g] & 3;
+          k0 = fs.fbase + g;
+          k1 = k0 + 1;
+        }
       } else {
         const long long g = it - p.n;
         roi = roi_of_plane(rd, p.n, g);
@@ -1578,7 +1688,7 @@ void plan_diam(const std::vector<Roi>& rois, bool soft, std::vector<RoiDiam>& rd
     const Roi& g = rois[i];
     RoiDiam& p = rd[i];
     p.nx = g.nx; p.ny = g.ny; p.nz = g.nz;
-    p.planes = soft ? 0 : 1;
+    p.planes = 1;  // masks and soft maps: the planar diameters too
     p.cell_shift = tu.cell_shift;
     p.CX = ((2 * g.nx) >> p.cell_shift) + 1;
     p.CY = ((2 * g.ny) >> p.cell_shift) + 1;
@@ -1626,7 +1736,20 @@ rad_status diam_run(int n, const RoiDiam* rd, const RoiOut* ro, const long long*
   p.nv_cap = nv_cap;
   p.sweep_min = (long long)kBigTiles * p.TS;  // the ROIs whose 3D problem is walked at two levels
   const long long nsorted = nv * (planes ? 4 : 1);
-  p.max_problems = 2 * (n + nplanes) + 2;  // a problem walked at two levels takes two slots
+  // soft maps with planes: groups of vertices off the grid planes (two or
+  // more vertices each), one key per group after all ROIs' keys, and a spare
+  FracState fs;
+  const bool frac = planes && vt != nullptr;
+  long long hsize = 0;
+  if (frac) {
+    fs.gcap = nv / 2 + 1;
+    fs.fbase = nkeys;
+    hsize = 16;  // 16 keys fill one 256-byte carve unit: the counts follow the keys directly
+    while (hsize < 2 * nv) hsize <<= 1;
+    fs.hmask = hsize - 1;
+  }
+  const long long nkeys_all = nkeys + (frac ? fs.gcap + 1 : 0);
+  p.max_problems = 2 * (n + nplanes + (frac ? fs.gcap : 0)) + 2;  // a problem walked at two levels takes two slots
   p.max_tiles = nsorted / p.TS + p.max_problems + 1;
   p.max_fine = nsorted / p.TS + p.max_problems + 1;
   if (s.work_cap == 0) s.work_cap = 1 << 20;
@@ -1637,7 +1760,7 @@ rad_status diam_run(int n, const RoiDiam* rd, const RoiOut* ro, const long long*
   const long long ntiles = p.max_tiles + p.max_fine;
 
   // scratch layout (hist/offsets carry one extra entry: offs[K] = total)
-  const long long K1 = nkeys + 1;
+  const long long K1 = nkeys_all + 1;
   const long long nparts = (K1 + kScanBlock - 1) / kScanBlock;
   size_t bytes = 0;
   auto add = [&](size_t m) { bytes += (m + 255) & ~size_t(255); };
@@ -1661,6 +1784,13 @@ rad_status diam_run(int n, const RoiDiam* rd, const RoiOut* ro, const long long*
   add(sizeof(Cand) * p.cand_cap);
   add(sizeof(float) * std::max<long long>(ntab, 1));  // coordinate tables (masks)
   add(sizeof(Key128) * 4 * n);  // family maxima of the FP64 pair kernel
+  if (frac) {
+    add(sizeof(Key128) * hsize);  // hash keys, then counts: one zeroed range
+    add(sizeof(int) * hsize);
+    add(sizeof(int) * hsize);     // group of a slot
+    add(sizeof(int) * nv);        // slot of a vertex
+    add(sizeof(int) * fs.gcap);   // (ROI, axis) of a group
+  }
   RAD_TRY(s.misc.reserve(bytes));
   char* cur = s.misc.as<char>();
   int* hist = carve<int>(cur, K1);
@@ -1688,6 +1818,13 @@ rad_status diam_run(int n, const RoiDiam* rd, const RoiOut* ro, const long long*
   Cand* cand = carve<Cand>(cur, p.cand_cap);
   float* ctab = carve<float>(cur, std::max<long long>(ntab, 1));
   Key128* keys = carve<Key128>(cur, 4 * n);
+  if (frac) {
+    fs.hkey = carve<Key128>(cur, hsize);
+    fs.hcnt = carve<int>(cur, hsize);
+    fs.hgid = carve<int>(cur, hsize);
+    fs.vslot = carve<int>(cur, nv);
+    fs.gra = carve<int>(cur, fs.gcap);
+  }
 
   const int sms = num_sms();
   ZeroSet zs{};
@@ -1698,6 +1835,7 @@ rad_status diam_run(int n, const RoiDiam* rd, const RoiOut* ro, const long long*
   zero_add(zs, stats, sizeof(DiamStats));
   zero_add(zs, fam_state, fam_bytes);  // F = T = 0 for every family; sweep slots
   if (s.fp64_pairs) zero_add(zs, keys, sizeof(Key128) * 4 * n);
+  if (frac) zero_add(zs, fs.hkey, (sizeof(Key128) + sizeof(int)) * hsize);  // keys and counts (adjacent)
   if (which & 1) {
     // on its own (a graph branch beside the mesh) it needs few CTAs: a few MB zeroed
     const long long init_ctas = (std::max(K1, ntab) + 255) / 256;
@@ -1706,14 +1844,20 @@ rad_status diam_run(int n, const RoiDiam* rd, const RoiOut* ro, const long long*
                out, n, zs, rd, ctab, planes ? ntab : 0);
   }
   if (!(which & 2)) return RAD_OK;
+  if (frac) {
+    RAD_LAUNCH("diam_frac_insert", k_frac_insert, wave_grid(k_frac_insert, 256, (nv + 255) / 256), 256, 0, st, idx2,
+               vt, nv_dev, ro, p, fs, cnt);
+    RAD_LAUNCH("diam_frac_assign", k_frac_assign, wave_grid(k_frac_assign, 256, (hsize + 255) / 256), 256, 0, st, fs,
+               cnt);
+  }
   RAD_LAUNCH("diam_hist", k_hist, wave_grid(k_hist, 256, (nv + 255) / 256), 256, 0, st, idx2, vt, nv_dev, rd, ro, p,
-             ctab, hist, sweep, ps);
+             ctab, hist, sweep, ps, fs);
   RAD_LAUNCH("diam_scan", k_xscan, (int)nparts, kScanThreads, 0, st, hist, K1, (int)nparts, offs, stiles, stick,
              &cnt->status);
   RAD_LAUNCH("diam_scatter", k_scatter, wave_grid(k_scatter, 256, (nv + 255) / 256), 256, 0, st, idx2, vt, nv_dev, rd,
-             ro, p, offs, cursor, ctab, sorted, ids, sweep, ps);
-  RAD_LAUNCH("diam_setup", k_setup, wave_grid(k_setup, 256, (n + nplanes + 255) / 256 + 1), 256, 0, st, rd, p, offs,
-             probs, chunk0, cnt);
+             ro, p, offs, cursor, ctab, sorted, ids, sweep, ps, fs);
+  RAD_LAUNCH("diam_setup", k_setup, wave_grid(k_setup, 256, (n + nplanes + (frac ? fs.gcap : 0) + 255) / 256 + 1), 256,
+             0, st, rd, p, offs, probs, chunk0, cnt, fs);
   RAD_LAUNCH("diam_tile_box", k_tile_box, wave_grid(k_tile_box, 256, 1LL << 30), 256, 0, st, sorted, probs, p, cnt,
              tiles, chunk0, box, rep);
   RAD_LAUNCH("diam_seed", k_seed, wave_grid(k_seed, 256, 1LL << 30), 256, 0, st, sorted, rep, p, tiles, chunk0, cnt, ps,

@@ -865,6 +865,26 @@ __global__ void __launch_bounds__(kCubeThreads) k_cubes(const uint32_t* bits, co
         vsum = ox * bc.nsum[0] + oy * bc.nsum[1] + oz * bc.nsum[2] + bc.tsum;
       }
     }
+    if (SOFT && n > 1) {
+      // a batch of soft maps: per-ROI sums by FP64 atomics (one per warp
+      // when its lanes share the ROI), the closed forms at the end
+      const unsigned int same_roi = __match_any_sync(0xffffffffu, valid ? roi : -1);
+      if (same_roi == 0xffffffffu) {
+        for (int off = 16; off > 0; off >>= 1) {
+          acc_v6 += __shfl_xor_sync(0xffffffffu, acc_v6, off);
+          acc_a2 += __shfl_xor_sync(0xffffffffu, acc_a2, off);
+        }
+        if (lane == 0 && valid) {
+          atomicAdd(&out[roi].vol6, acc_v6);
+          atomicAdd(&out[roi].area2, acc_a2);
+        }
+      } else if (valid) {
+        atomicAdd(&out[roi].vol6, acc_v6);
+        atomicAdd(&out[roi].area2, acc_a2);
+      }
+      acc_v6 = 0.0;
+      acc_a2 = 0.0;
+    }
     if (!SOFT) {
       // lanes of one ROI add their volume sums with one atomic; lanes of one
       // (ROI, case) add their count with one atomic
@@ -881,6 +901,22 @@ __global__ void __launch_bounds__(kCubeThreads) k_cubes(const uint32_t* bits, co
   }
   if (err) atomicOr(&tot->status, err);
   if (!SOFT) return;
+  __shared__ bool last;
+  if (n > 1) {  // the last CTA: closed forms of every map of the batch
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&tot->done_ctas, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      closed_form_features(__ldcg(&out[i].vol6) / 6.0, __ldcg(&out[i].area2) * 0.5, out[i].derived);
+      out[i].has_derived = 1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) tot->done_ctas = 0;
+    return;
+  }
   // soft map (one ROI): fixed-order block reduction, then the last CTA finishes
   const int wid = threadIdx.x >> 5;
   for (int off = 16; off > 0; off >>= 1) {
@@ -888,7 +924,6 @@ __global__ void __launch_bounds__(kCubeThreads) k_cubes(const uint32_t* bits, co
     acc_a2 += __shfl_xor_sync(0xffffffffu, acc_a2, off);
   }
   __shared__ double s_v6[kCubeThreads / 32], s_a2[kCubeThreads / 32];
-  __shared__ bool last;
   if (lane == 0) { s_v6[wid] = acc_v6; s_a2[wid] = acc_a2; }
   __syncthreads();
   if (threadIdx.x == 0) {

@@ -339,10 +339,38 @@ rad_status diam_fp64_variant(int variant, const int16_t* idx2, const double* vt,
 const rad_tuning_t& tuning();
 
 // Adjoint of the soft-map features (grad: dense FP64, nx*ny*nz; gvtx: 3 x vcap).
+// One map of a soft adjoint batch (device table): its map and gradient
+// (dense [nz][ny][nx] float64, caller-owned), size, spacing, the weights
+// (A, V, D3, Slice, Column, Row) and the four argmax pairs (ROI-local vertex
+// ids, -1: term left out), and its first voxel in the batch's voxel count.
+struct SoftMap {
+  const float* prob;
+  double* grad;
+  int nx, ny, nz, pad;
+  double sx, sy, sz;
+  double gout[6];
+  int pair[8];
+  long long vox0;
+};
+
+// Preprocessing (prep.cu): the ROI's box, widened and clamped (lo, m voxels
+// per axis), and the output size; empty when the mask has no ROI voxel.
+struct PrepInfo {
+  long long lo[3], m[3], nout[3];
+  int empty, pad;
+};
+// Box and output size of a crop/resample into *info_host (synchronises st).
+rad_status prep_bbox(const uint8_t* mask, const int64_t dims[3], const double sp[3], int label, int pad,
+                     const double* new_sp, DevBuf& scratch, PrepInfo* info_host, cudaStream_t st);
+// The output voxels into out (info_host from prep_bbox on the same scratch; synchronises st).
+rad_status prep_gather(const uint8_t* mask, const int64_t dims[3], const double sp[3], int label,
+                       const double* new_sp, const PrepInfo& info_host, DevBuf& scratch, uint8_t* out,
+                       cudaStream_t st);
+
+// Gradients of a batch of soft maps whose meshes are in the pools (see soft.cu).
 rad_status soft_adjoint(const int16_t* idx2, const double* vt, const int32_t* tri, const long long* nv_dev,
-                        const long long* nt_dev, long long vcap, long long tcap, const float* prob, const MeshDims& d,
-                        const double sp[3], const double gout[3], int ai, int aj, double* gvtx, double* grad,
-                        cudaStream_t st);
+                        const long long* nt_dev, long long vcap, long long tcap, const RoiOut* ro, const SoftMap* maps,
+                        int n, long long total_vox, double* gvtx, cudaStream_t st);
 
 }  // namespace rad
 

@@ -80,7 +80,8 @@ EXPORTS = ("rad_mesh", "rad_soft_mesh", "rad_shape", "rad_shape_plain_fp64", "ra
            "rad_workspace_free", "rad_mesh_free", "rad_mesh_copy", "rad_set_tuning", "rad_profile_enable",
            "rad_profile_read", "rad_profile_reset", "rad_launch_count", "rad_status_str", "rad_last_error",
            "rad_last_call_stats", "rad_soft_forward", "rad_soft_backward", "rad_batch_create", "rad_batch_run",
-           "rad_batch_destroy", "rad_check_bounded_wait")
+           "rad_batch_destroy", "rad_check_bounded_wait", "rad_soft_features", "rad_soft_backward_planes",
+           "rad_soft_batch_forward", "rad_soft_batch_backward", "rad_crop_resample")
 
 
 def lib():
@@ -126,6 +127,16 @@ def lib():
         L.rad_soft_forward.restype = I
         L.rad_soft_backward.argtypes = [P, P, P, P, P, P, ctypes.POINTER(P), P]
         L.rad_soft_backward.restype = I
+        L.rad_soft_features.argtypes = [P, P, P, ctypes.POINTER(Features), ctypes.POINTER(P), P]
+        L.rad_soft_features.restype = I
+        L.rad_soft_backward_planes.argtypes = [P, P, P, P, P, P, ctypes.POINTER(P), P]
+        L.rad_soft_backward_planes.restype = I
+        L.rad_soft_batch_forward.argtypes = [I, P, P, P, P, ctypes.POINTER(P), P]
+        L.rad_soft_batch_forward.restype = I
+        L.rad_soft_batch_backward.argtypes = [I, P, P, P, P, P, P, ctypes.POINTER(P), P]
+        L.rad_soft_batch_backward.restype = I
+        L.rad_crop_resample.argtypes = [P, P, P, I, I, P, P, ctypes.c_int64, P, P, P, ctypes.POINTER(P), P]
+        L.rad_crop_resample.restype = I
         L.rad_batch_create.argtypes = [I, P, P, P, ctypes.POINTER(P), P]
         L.rad_batch_create.restype = I
         L.rad_batch_run.argtypes = [P, ctypes.POINTER(Features), P]
@@ -298,6 +309,111 @@ def soft_backward(prob, spacing, gout, argmax, grad, ws, stream=None):
     am = (ctypes.c_int32 * 2)(int(argmax[0]), int(argmax[1]))
     _check(lib().rad_soft_backward(ctypes.c_void_p(prob.data_ptr()), dims, sp, g, am,
                                    ctypes.c_void_p(grad.data_ptr()), ctypes.byref(ws.h), _stream(stream)))
+
+
+ARGMAX_KEYS = ("argmax3d", "argmax_slice", "argmax_column", "argmax_row")
+
+
+def soft_features(prob, spacing, ws, stream=None):
+    """All features (dict) of a CUDA float32 probability map, planar
+    diameters and their argmax pairs included."""
+    _device_tensor(prob, "torch.float32")
+    dims, sp = _geometry(prob.shape, spacing)
+    f = Features()
+    _check(lib().rad_soft_features(ctypes.c_void_p(prob.data_ptr()), dims, sp, ctypes.byref(f), ctypes.byref(ws.h),
+                                   _stream(stream)))
+    return f.as_dict()
+
+
+def _pairs8(feats_or_pairs):
+    if isinstance(feats_or_pairs, dict):
+        return [int(v) for k in ARGMAX_KEYS for v in feats_or_pairs[k]]
+    return [int(v) for pq in feats_or_pairs for v in pq]
+
+
+def soft_backward_planes(prob, spacing, gout6, argmax, grad, ws, stream=None):
+    """grad (CUDA float64, prob's shape) = d(gout6 . (A, V, D3, DSlice,
+    DColumn, DRow)) / d prob; argmax: the features dict of soft_features or
+    four (i, j) pairs."""
+    _device_tensor(prob, "torch.float32")
+    _device_tensor(grad, "torch.float64")
+    if tuple(grad.shape) != tuple(prob.shape):
+        raise ValueError("grad must have prob's shape")
+    dims, sp = _geometry(prob.shape, spacing)
+    g = (ctypes.c_double * 6)(*(float(v) for v in gout6))
+    am = (ctypes.c_int32 * 8)(*_pairs8(argmax))
+    _check(lib().rad_soft_backward_planes(ctypes.c_void_p(prob.data_ptr()), dims, sp, g, am,
+                                          ctypes.c_void_p(grad.data_ptr()), ctypes.byref(ws.h), _stream(stream)))
+
+
+def _batch_geometry(probs, spacings):
+    n = len(probs)
+    if n < 1 or len(spacings) != n:
+        raise ValueError("need one spacing per map and at least one map")
+    for p in probs:
+        _device_tensor(p, "torch.float32")
+    dims = (ctypes.c_int64 * (3 * n))(*[int(d) for p in probs for d in (p.shape[2], p.shape[1], p.shape[0])])
+    sp = (ctypes.c_double * (3 * n))(*[float(v) for s in spacings for v in s])
+    ptrs = (ctypes.c_void_p * n)(*[p.data_ptr() for p in probs])
+    return n, ptrs, dims, sp
+
+
+def soft_batch_forward(probs, spacings, ws, stream=None):
+    """Features (list of dicts) of several soft maps in one set of launches."""
+    n, ptrs, dims, sp = _batch_geometry(probs, spacings)
+    out = (Features * n)()
+    _check(lib().rad_soft_batch_forward(n, ptrs, dims, sp, out, ctypes.byref(ws.h), _stream(stream)))
+    return [out[i].as_dict() for i in range(n)]
+
+
+def soft_batch_backward(probs, spacings, gouts, argmaxes, grads, ws, stream=None):
+    """Gradients of several soft maps in one set of launches: gouts[i] the six
+    weights and argmaxes[i] the features dict (or four pairs) of map i."""
+    n, ptrs, dims, sp = _batch_geometry(probs, spacings)
+    if len(grads) != n or len(gouts) != n or len(argmaxes) != n:
+        raise ValueError("one gradient, weight set and argmax set per map")
+    for p, g in zip(probs, grads):
+        _device_tensor(g, "torch.float64")
+        if tuple(g.shape) != tuple(p.shape):
+            raise ValueError("each grad must have its map's shape")
+    g6 = (ctypes.c_double * (6 * n))(*[float(v) for go in gouts for v in go])
+    a8 = (ctypes.c_int32 * (8 * n))(*[v for am in argmaxes for v in _pairs8(am)])
+    gp = (ctypes.c_void_p * n)(*[g.data_ptr() for g in grads])
+    _check(lib().rad_soft_batch_backward(n, ptrs, dims, sp, g6, a8, gp, ctypes.byref(ws.h), _stream(stream)))
+
+
+STATUS_CAPACITY = 3
+
+
+def crop_resample(mask, spacing, ws, label=None, pad=0, new_spacing=None, out=None, stream=None):
+    """Crop a CUDA uint8 mask to its ROI's bounding box (label None: any
+    non-zero value) widened by `pad`, optionally resampled to new_spacing by
+    nearest neighbour.  Returns (out tensor [nz'][ny'][nx'] uint8 on the
+    mask's device, box_lo (x, y, z), out_spacing); `out` may be a preallocated
+    CUDA uint8 tensor with enough elements."""
+    import torch
+    _device_tensor(mask, "torch.uint8")
+    dims, sp = _geometry(mask.shape, spacing)
+    nsp = (ctypes.c_double * 3)(*new_spacing) if new_spacing is not None else None
+    od = (ctypes.c_int64 * 3)()
+    lo = (ctypes.c_int64 * 3)()
+    osp = (ctypes.c_double * 3)()
+    lab = -1 if label is None else int(label)
+    L = lib()
+    cap = 0 if out is None else out.numel()
+    ptr = None if out is None else ctypes.c_void_p(out.data_ptr())
+    st = L.rad_crop_resample(ctypes.c_void_p(mask.data_ptr()), dims, sp, lab, int(pad), nsp, ptr, cap, od, lo, osp,
+                             ctypes.byref(ws.h), _stream(stream))
+    if st == STATUS_CAPACITY and out is None:
+        out = torch.empty(int(od[0]) * int(od[1]) * int(od[2]), dtype=torch.uint8, device=mask.device)
+        st = L.rad_crop_resample(ctypes.c_void_p(mask.data_ptr()), dims, sp, lab, int(pad), nsp,
+                                 ctypes.c_void_p(out.data_ptr()), out.numel(), od, lo, osp, ctypes.byref(ws.h),
+                                 _stream(stream))
+    _check(st)
+    n = int(od[0]) * int(od[1]) * int(od[2])
+    res = (out if out is not None else torch.empty(0, dtype=torch.uint8, device=mask.device))
+    res = res.reshape(-1)[:n].reshape(int(od[2]), int(od[1]), int(od[0]))
+    return res, (int(lo[0]), int(lo[1]), int(lo[2])), (osp[0], osp[1], osp[2])
 
 
 class Batch:
