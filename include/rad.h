@@ -311,8 +311,8 @@ rad_status rad_check_bounded_wait(void* stream);
  * the implicit synchronisation of cudaMalloc/cudaFree).  It computes the
  * same diameters as rad_shape_plain_fp64 (plain FP64 all pairs, same pinned
  * formula and tie-break) and allocates nothing: its only scratch is a static
- * device array of 256 KB built into the library, which every GPU that loads
- * the library keeps until the process exits.
+ * device array of 256 KB built into the library, resident on a device from
+ * the library module's load there until that device's context is destroyed.
  *   idx2_dev   device, n_vertices x 3 int16 doubled index coordinates
  *   t_dev      device, n_vertices doubles (soft meshes) or NULL (masks)
  *   n_vertices 0 .. 1048576 (4096 tiles of 256 vertices); larger counts are
@@ -321,9 +321,11 @@ rad_status rad_check_bounded_wait(void* stream);
  *   pairs_dev  device, 8 int32 out: (i, j) of each, (-1, -1) if no pair
  * Asynchronous on `stream` (nothing is copied to the host).  The first call
  * on a device looks up the device address of the static array with that
- * device current; make that first call before any stream capture.  All calls
- * share the one array: calls that overlap on the GPU (other streams or
- * threads) race and must be serialised by the caller. */
+ * device current and caches it for the process: a device reset
+ * (cudaDeviceReset) or another teardown of the device's primary context
+ * invalidates that address, so no call may follow one.  All calls share the
+ * one array: calls that overlap on the GPU (other streams or threads) race
+ * and must be serialised by the caller. */
 rad_status rad_diameters_plain_fp64_noalloc(const int16_t* idx2_dev, const double* t_dev, int64_t n_vertices,
                                             const double spacing[3], double* d2_dev, int32_t* pairs_dev,
                                             void* stream);

@@ -324,6 +324,8 @@ struct Work {
   DevBuf gvtx;  // per-vertex position gradients (soft adjoint)
   DevBuf plain; // result of the plain FP64 kernel
   DevBuf soft_maps;  // SoftMap table of a soft adjoint batch
+  std::vector<SoftMap> soft_maps_host;  // its host copy (the source of the upload)
+  std::vector<Roi> prev_rois;           // map table of the previous soft forward call
   DevBuf prep;       // crop/resample: box reduction, its result and the index maps
   // plan of the current batch
   std::vector<Roi> rois, up_rois;     // planned / last uploaded
@@ -932,39 +934,31 @@ rad_status check_soft_args(int n, const float* const* probs, const int64_t* dims
   return RAD_OK;
 }
 
-// Features of n soft maps: one set of launches for the meshes, one for the
-// diameters (the work and candidate lists grow and the diameters rerun when
-// they overflow).
+// Features of n soft maps: one pass (meshes, diameters, features), replayed
+// as a CUDA graph when the same maps come again (the graph is captured on the
+// second call with an unchanged map table, so a stream of new maps, as in
+// training, never pays for captures it cannot reuse).
 rad_status soft_features_impl(Work& w, int n, const float* const* probs, const int64_t* dims, const double* sp,
                               rad_features_t* out, cudaStream_t st) {
   std::vector<const void*> ptrs(probs, probs + n);
   RAD_TRY(prepare(w, n, ptrs.data(), dims, sp, true, st));
-  RAD_TRY(run_mesh_only(w, st, nullptr));
-  for (int attempt = 0; attempt < 4; ++attempt) {
-    RAD_TRY(enqueue_shape(w, st));
-    RAD_TRY(enqueue_finish(w, true, st));
-    RAD_CUDA(cudaStreamSynchronize(st));
-    const unsigned int s = w.host->stats.status;
-    if (s & DEV_ERR_WORKCAP) { w.ds.work_cap *= 4; continue; }
-    if (s & DEV_ERR_CANDCAP) { w.ds.cand_cap *= 4; continue; }
-    RAD_TRY(status_from_dev(s));
-    memcpy(out, w.hfeats, sizeof(rad_features_t) * n);
-    record_stats(*w.host, 0, (long long)(sizeof(ResultBlock) + sizeof(rad_features_t) * n), true);
-    return RAD_OK;
-  }
-  return status_from_dev(w.host->stats.status);
+  const bool repeat = w.prev_rois.size() == w.rois.size() &&
+                      same_bytes(w.prev_rois.data(), w.rois.data(), sizeof(Roi) * w.rois.size());
+  w.prev_rois = w.rois;
+  RAD_TRY(run_pass(w, st, repeat, 0));
+  memcpy(out, w.hfeats, sizeof(rad_features_t) * n);
+  return RAD_OK;
 }
 
-// Gradients of n soft maps (meshes recomputed, then one set of adjoint launches).
+// Gradients of n soft maps: the meshes are recomputed and the adjoint runs
+// right behind them, with one host synchronisation (pool sizes and argmax
+// pairs are checked on the device; a pool overflow repeats the call's work).
 rad_status soft_backward_impl(Work& w, int n, const float* const* probs, const int64_t* dims, const double* sp,
                               const double* gout, const int32_t* argmax, double* const* grads, cudaStream_t st) {
   std::vector<const void*> ptrs(probs, probs + n);
   RAD_TRY(prepare(w, n, ptrs.data(), dims, sp, true, st));
-  RAD_TRY(run_mesh_only(w, st, nullptr));
-  std::vector<RoiOut> ro(n);
-  RAD_CUDA(cudaMemcpyAsync(ro.data(), w.dro(), sizeof(RoiOut) * n, cudaMemcpyDeviceToHost, st));
-  RAD_CUDA(cudaStreamSynchronize(st));
-  std::vector<SoftMap> maps(n);
+  std::vector<SoftMap>& maps = w.soft_maps_host;
+  maps.resize(n);
   long long vox = 0;
   for (int i = 0; i < n; ++i) {
     SoftMap& m = maps[i];
@@ -973,27 +967,37 @@ rad_status soft_backward_impl(Work& w, int n, const float* const* probs, const i
     m.nx = (int)dims[3 * i]; m.ny = (int)dims[3 * i + 1]; m.nz = (int)dims[3 * i + 2]; m.pad = 0;
     m.sx = sp[3 * i]; m.sy = sp[3 * i + 1]; m.sz = sp[3 * i + 2];
     for (int k = 0; k < 6; ++k) m.gout[k] = gout[6 * i + k];
-    const long long nv = ro[i].nv;
-    for (int q = 0; q < 4; ++q) {
-      const int a = argmax[8 * i + 2 * q], b = argmax[8 * i + 2 * q + 1];
-      if ((a >= 0 || b >= 0) && (a < 0 || b < 0 || a >= nv || b >= nv || a == b)) {
-        set_error("argmax pair (%d, %d) is not a vertex pair of map %d's mesh (%lld vertices)", a, b, i, nv);
-        return RAD_ERR_INVALID_ARG;
-      }
-      m.pair[2 * q] = a;
-      m.pair[2 * q + 1] = b;
-    }
+    for (int k = 0; k < 8; ++k) m.pair[k] = argmax[8 * i + k];
     m.vox0 = vox;
     vox += (long long)m.nx * m.ny * m.nz;
   }
   RAD_TRY(w.soft_maps.reserve(sizeof(SoftMap) * n));
-  RAD_CUDA(cudaMemcpyAsync(w.soft_maps.p, maps.data(), sizeof(SoftMap) * n, cudaMemcpyHostToDevice, st));
-  RAD_TRY(w.gvtx.reserve(sizeof(double) * 3 * std::max<long long>(w.vcap, 1)));
+  if (w.vcap == 0) RAD_TRY(size_pools(w, st));
   ResultBlock* dr = w.dres();
-  RAD_TRY(soft_adjoint(w.idx2.as<int16_t>(), w.vt.as<double>(), w.tri.as<int32_t>(), &dr->tot.nv, &dr->tot.nt, w.vcap,
-                       w.tcap, w.dro(), w.soft_maps.as<SoftMap>(), n, vox, w.gvtx.as<double>(), st));
-  RAD_CUDA(cudaStreamSynchronize(st));  // the host table may go once the copy has run
-  return RAD_OK;
+  for (int attempt = 0; attempt < 3; ++attempt) {
+    RAD_TRY(w.gvtx.reserve(sizeof(double) * 3 * std::max<long long>(w.vcap, 1)));
+    RAD_CUDA(cudaMemcpyAsync(w.soft_maps.p, maps.data(), sizeof(SoftMap) * n, cudaMemcpyHostToDevice, st));
+    RAD_TRY(mesh_count(w.mb, w.ms, &dr->tot, w.dro(), st));
+    RAD_TRY(mesh_emit(w.mb, w.ms, &dr->tot, w.dro(), w.idx2.as<int16_t>(), w.vt.as<double>(), w.tri.as<int32_t>(),
+                      w.vcap, w.tcap, st));
+    RAD_TRY(soft_adjoint(w.idx2.as<int16_t>(), w.vt.as<double>(), w.tri.as<int32_t>(), &dr->tot.nv, &dr->tot.nt,
+                         w.vcap, w.tcap, w.dro(), w.soft_maps.as<SoftMap>(), n, vox, w.gvtx.as<double>(),
+                         &dr->tot.status, st));
+    RAD_CUDA(cudaMemcpyAsync(w.host, dr, sizeof(ResultBlock), cudaMemcpyDeviceToHost, st));
+    RAD_CUDA(cudaStreamSynchronize(st));
+    const MeshTotals& t = w.host->tot;
+    if (t.nv > w.vcap || t.nt > w.tcap || (t.status & (DEV_ERR_VCAP | DEV_ERR_TCAP))) {
+      RAD_TRY(size_pools(w, st));
+      continue;
+    }
+    if (t.status & DEV_ERR_PAIR) {
+      set_error("an argmax pair is not a vertex pair of its map's mesh");
+      return RAD_ERR_INVALID_ARG;
+    }
+    record_stats(*w.host, 0, (long long)sizeof(ResultBlock), false);
+    return status_from_dev(t.status);
+  }
+  return status_from_dev(w.host->tot.status);
 }
 
 }  // namespace

@@ -6,13 +6,16 @@
 // must not trigger the implicit synchronisation of cudaMalloc/cudaFree.
 // rad_diameters_plain_fp64_noalloc serves them: the caller passes the
 // vertices and the output buffers, and the only scratch this entry point
-// uses is a file-scope static device array that the library image carries
-// (every GPU that loads the library holds it until the process exits).
+// uses is a file-scope static device array that the library image carries:
+// it is resident on a device from the library module's load there until that
+// device's context is destroyed.
 //
-// The kernel is a variant of the plain FP64 all-pairs diameter kernel: one
-// CTA per 256-vertex tile row i scans the tiles j >= i and writes its best
-// (d2, i, j) for 3D, Slice, Column and Row into slot i of the static array; a
-// second kernel reduces the slots in fixed order into the caller's outputs.
+// The kernel is a variant of the plain FP64 all-pairs diameter kernel: CTA c
+// scans the 256-vertex tile rows c and T - 1 - c (T tile rows; row i holds
+// the tiles j >= i), so every CTA covers about T + 1 tiles, and writes its
+// best (d2, i, j) for 3D, Slice, Column and Row into slot c of the static
+// array; a second kernel reduces the slots in fixed order into the caller's
+// outputs.
 #include <mutex>
 
 #include "rad_internal.cuh"
@@ -44,17 +47,10 @@ __device__ __forceinline__ void na_take(NaBest& b, double d2, int i, int j) {
   if (na_better(d2, i, j, b)) { b.d2 = d2; b.i = i; b.j = j; }
 }
 
-__global__ void __launch_bounds__(kNaTile) k_na_rows(const int16_t* idx2, const double* vt,
-                                                     int n, double sx, double sy, double sz,
-                                                     NaBest* slots) {
-  pdl_enter();
-  __shared__ double su[3][kNaTile];
-  __shared__ int sq[3][kNaTile];
-  __shared__ NaBest sred[4][kNaTile / 32];
-  const int nt = (n + kNaTile - 1) / kNaTile;
-  const int ti = blockIdx.x;
-  NaBest b[4];
-  for (int q = 0; q < 4; ++q) { b[q].d2 = 0.0; b[q].i = -1; b[q].j = -1; }
+// Tile row ti (tiles ti .. nt - 1) into the thread's maxima b; every thread
+// of the block calls it (it synchronises the block).
+__device__ void na_row(const int16_t* idx2, const double* vt, int n, int nt, int ti, double sx, double sy,
+                       double sz, double (*su)[kNaTile], int (*sq)[kNaTile], NaBest b[4]) {
   const int i = ti * kNaTile + threadIdx.x;
   double ui[3] = {0.0, 0.0, 0.0};
   int qi[3] = {0, 0, 0};
@@ -86,6 +82,21 @@ __global__ void __launch_bounds__(kNaTile) k_na_rows(const int16_t* idx2, const 
       if (same_x) na_take(b[3], d2, i, j);
     }
   }
+}
+
+__global__ void __launch_bounds__(kNaTile) k_na_rows(const int16_t* idx2, const double* vt,
+                                                     int n, double sx, double sy, double sz,
+                                                     NaBest* slots) {
+  pdl_enter();
+  __shared__ double su[3][kNaTile];
+  __shared__ int sq[3][kNaTile];
+  __shared__ NaBest sred[4][kNaTile / 32];
+  const int nt = (n + kNaTile - 1) / kNaTile;
+  const int c = blockIdx.x;
+  NaBest b[4];
+  for (int q = 0; q < 4; ++q) { b[q].d2 = 0.0; b[q].i = -1; b[q].j = -1; }
+  na_row(idx2, vt, n, nt, c, sx, sy, sz, su, sq, b);
+  if (nt - 1 - c > c) na_row(idx2, vt, n, nt, nt - 1 - c, sx, sy, sz, su, sq, b);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int q = 0; q < 4; ++q) {
     for (int off = 16; off > 0; off >>= 1) {
@@ -103,7 +114,7 @@ __global__ void __launch_bounds__(kNaTile) k_na_rows(const int16_t* idx2, const 
     NaBest r = sred[q][0];
     for (int w = 1; w < kNaTile / 32; ++w)
       if (na_better(sred[q][w].d2, sred[q][w].i, sred[q][w].j, r)) r = sred[q][w];
-    slots[4 * ti + q] = r;
+    slots[4 * c + q] = r;
   }
 }
 
@@ -123,7 +134,9 @@ __global__ void k_na_final(const NaBest* slots, int tiles, double* d2_out,
 }
 
 // Device address of the static scratch, looked up once per device (with that
-// device current) and cached.
+// device current) and cached for the life of the process: a device reset
+// (cudaDeviceReset) or any teardown of the device's primary context
+// invalidates it, so the library must not be used across one.
 std::mutex g_na_mu;
 NaBest* g_na_ptr[64] = {nullptr};
 
@@ -172,9 +185,10 @@ extern "C" rad_status rad_diameters_plain_fp64_noalloc(const int16_t* idx2_dev, 
   cudaStream_t st = (cudaStream_t)stream;
   const int n = (int)n_vertices;
   const int tiles = (n + kNaTile - 1) / kNaTile;
-  if (tiles > 0)
-    RAD_LAUNCH("noalloc_plain_fp64_rows", k_na_rows, tiles, kNaTile, 0, st, idx2_dev, t_dev, n, spacing[0], spacing[1],
+  const int ctas = (tiles + 1) / 2;  // rows c and tiles - 1 - c per CTA
+  if (ctas > 0)
+    RAD_LAUNCH("noalloc_plain_fp64_rows", k_na_rows, ctas, kNaTile, 0, st, idx2_dev, t_dev, n, spacing[0], spacing[1],
                spacing[2], slots);
-  RAD_LAUNCH("noalloc_plain_fp64_final", k_na_final, 1, 32, 0, st, slots, tiles, d2_dev, pairs_dev);
+  RAD_LAUNCH("noalloc_plain_fp64_final", k_na_final, 1, 32, 0, st, slots, ctas, d2_dev, pairs_dev);
   return RAD_OK;
 }

@@ -192,6 +192,7 @@ enum : uint32_t {
   DEV_ERR_TIMEOUT = 1u << 4,  // a bounded wait gave up
   DEV_ERR_INTERNAL = 1u << 5, // consistency check failed
   DEV_ERR_PROBCAP = 1u << 6,  // problem/tile list too small
+  DEV_ERR_PAIR = 1u << 7,     // an argmax pair passed to the soft adjoint is not a vertex pair of its mesh
 };
 static_assert(DEV_ERR_TIMEOUT == (1u << 4), "scan_lookback raises this bit");
 
@@ -370,7 +371,7 @@ rad_status prep_gather(const uint8_t* mask, const int64_t dims[3], const double 
 // Gradients of a batch of soft maps whose meshes are in the pools (see soft.cu).
 rad_status soft_adjoint(const int16_t* idx2, const double* vt, const int32_t* tri, const long long* nv_dev,
                         const long long* nt_dev, long long vcap, long long tcap, const RoiOut* ro, const SoftMap* maps,
-                        int n, long long total_vox, double* gvtx, cudaStream_t st);
+                        int n, long long total_vox, double* gvtx, unsigned int* status, cudaStream_t st);
 
 }  // namespace rad
 

@@ -106,8 +106,10 @@ __global__ void k_soft_tri_grad(const int16_t* idx2, const double* vt, const int
 }
 
 // One thread per (map, diameter): the argmax pair's two position gradients.
+// A pair that is not a vertex pair of its map's mesh (one side negative, out
+// of range or both equal) raises DEV_ERR_PAIR and adds nothing.
 __global__ void k_soft_pair_grad(const int16_t* idx2, const double* vt, const RoiOut* ro, const SoftMap* maps, int n,
-                                 double* gvtx) {
+                                 double* gvtx, unsigned int* status) {
   pdl_enter();
   const int it = blockIdx.x * blockDim.x + threadIdx.x;
   if (it >= 4 * n) return;
@@ -115,7 +117,13 @@ __global__ void k_soft_pair_grad(const int16_t* idx2, const double* vt, const Ro
   const int q = it & 3;
   const double gD = m.gout[2 + q];
   const int il = m.pair[2 * q], jl = m.pair[2 * q + 1];
-  if (il < 0 || jl < 0 || gD == 0.0) return;
+  if (il < 0 && jl < 0) return;
+  const long long nv = ro[it >> 2].nv;
+  if (il < 0 || jl < 0 || il >= nv || jl >= nv || il == jl) {
+    atomicOr(status, DEV_ERR_PAIR);
+    return;
+  }
+  if (gD == 0.0) return;
   const long long v0 = ro[it >> 2].v0, i = v0 + il, j = v0 + jl;
   const MeshDims d = dims_of(m);
   const double sp[3] = {m.sx, m.sy, m.sz};
@@ -183,13 +191,14 @@ __global__ void k_soft_scatter(const int16_t* idx2, const long long* nv_dev, lon
 
 rad_status soft_adjoint(const int16_t* idx2, const double* vt, const int32_t* tri, const long long* nv_dev,
                         const long long* nt_dev, long long vcap, long long tcap, const RoiOut* ro, const SoftMap* maps,
-                        int n, long long total_vox, double* gvtx, cudaStream_t st) {
+                        int n, long long total_vox, double* gvtx, unsigned int* status, cudaStream_t st) {
   const int sms = num_sms();
   RAD_CUDA(cudaMemsetAsync(gvtx, 0, sizeof(double) * 3 * std::max<long long>(vcap, 1), st));
   RAD_LAUNCH("soft_zero", k_soft_zero, wave_grid(k_soft_zero, 256, (total_vox + 255) / 256), 256, 0, st, maps, n,
              total_vox);
   RAD_LAUNCH("soft_tri_grad", k_soft_tri_grad, sms * 8, 256, 0, st, idx2, vt, tri, nt_dev, tcap, ro, maps, n, gvtx);
-  RAD_LAUNCH("soft_pair_grad", k_soft_pair_grad, (4 * n + 127) / 128, 128, 0, st, idx2, vt, ro, maps, n, gvtx);
+  RAD_LAUNCH("soft_pair_grad", k_soft_pair_grad, (4 * n + 127) / 128, 128, 0, st, idx2, vt, ro, maps, n, gvtx,
+             status);
   RAD_LAUNCH("soft_scatter", k_soft_scatter, sms * 8, 256, 0, st, idx2, nv_dev, vcap, ro, maps, n, gvtx);
   return RAD_OK;
 }

@@ -1,8 +1,10 @@
 """rad_diameters_plain_fp64_noalloc: the entry point for callers that cannot
 call cudaMalloc (for example when a framework owns the whole device memory
 budget, or when allocation after start-up is forbidden).  It must give the
-same diameters and argmax pairs as rad_shape_plain_fp64, call after call,
-while using only the library's static scratch array.
+oracle's diameters and argmax pairs (and so rad_shape_plain_fp64's), call
+after call, with no pair at 0 or 1 vertices, while allocating no device
+memory: after a first call, device memory in use is unchanged by further
+calls.
 
 Kept in a file that pytest collects last, so that a failure here comes after
 every other test has run."""
@@ -11,6 +13,7 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 from paper_2510_02894_gb300 import synth
 
 torch = pytest.importorskip("torch")
@@ -55,9 +58,36 @@ def test_noalloc_matches_plain_entry_point_twice():
     for mask, sp in cases:
         m = rad.mesh(torch.from_numpy(mask).cuda(), sp)
         ref = rad.shape_plain_fp64(m)
+        oref, _ = oracle.features(mask, sp)
+        for k in KEYS + ARGS:
+            assert (tuple(ref[k]) if k in ARGS else ref[k]) == (tuple(oref[k]) if k in ARGS else oref[k]), k
         for _ in range(2):  # the static scratch keeps the previous call's contents
             d2, pairs = _call(fn, m, sp)
-            _check(ref, d2, pairs)
+            _check(oref, d2, pairs)
+
+
+def test_noalloc_no_pair_and_no_allocation():
+    rad, fn = _entry()
+    mask, sp = synth.ellipsoid_32(5)
+    m = rad.mesh(torch.from_numpy(mask).cuda(), sp)
+    _call(fn, m, sp)  # first call: the scratch address is looked up
+    d2 = torch.full((4,), -1.0, dtype=torch.float64, device="cuda")
+    pairs = torch.full((8,), -7, dtype=torch.int32, device="cuda")
+    sp3 = (ctypes.c_double * 3)(*sp)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    for nv in (0, 1, m.n_vertices):
+        st = fn(ctypes.c_void_p(m.m.vtx_idx2), None, nv, sp3, ctypes.c_void_p(d2.data_ptr()),
+                ctypes.c_void_p(pairs.data_ptr()), stream)
+        assert st == 0
+        torch.cuda.synchronize()
+        if nv < 2:  # no pair: 0 and (-1, -1)
+            assert d2.cpu().tolist() == [0.0] * 4 and pairs.cpu().tolist() == [-1] * 8
+    # nothing allocated on the device by the calls (driver view and torch's allocator)
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.cuda.memory_allocated() == alloc0
 
 
 def test_noalloc_soft_mesh_and_limits():
