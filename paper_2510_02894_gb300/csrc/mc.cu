@@ -521,30 +521,43 @@ __device__ __forceinline__ long long row_base(const long long* prefix, long long
 // Among a loop's admissible candidates (stored in ascending lexicographic order
 // of their canonical triple lists): minimum area score, then maximum volume,
 // then the first in list order.  Pinned FP64 arithmetic, so the same choice
-// as any other implementation of the rule.
+// as any other implementation of the rule.  Volumes are computed only when
+// the scores leave a tie (they decide nothing otherwise).
 __device__ int select_candidate(int loop, const double (*w)[3], const double* sp) {
   const int k = MC_LOOP_K[loop], nt = k - 2;
   const int cb = MC_LOOP_CAND_BEGIN[loop], ce = MC_LOOP_CAND_BEGIN[loop + 1];
   if (ce - cb == 1) return cb;
-  double sc[MC_MAX_CAND], vv[MC_MAX_CAND];
+  double sc[MC_MAX_CAND];
   double smin = 0.0;
   for (int c = cb; c < ce; ++c) {
     const int tb = MC_CAND_TRI_BEGIN[c];
-    double s = 0.0, v = 0.0;
+    double s = 0.0;
     for (int t = 0; t < nt; ++t) {
       const unsigned char* tr = &MC_CAND_TRIPLES[3 * (tb + t)];
       s = __dadd_rn(s, pin_tri_r(w[tr[0]], w[tr[1]], w[tr[2]]));
-      v = __dadd_rn(v, pin_vol6(w[tr[0]], w[tr[1]], w[tr[2]]));
     }
     sc[c - cb] = s;
-    vv[c - cb] = v;
     if (c == cb || s < smin) smin = s;
   }
   const double slim = __dadd_rn(smin, __dmul_rn(smin, 1e-12));
+  int tied = 0, only = cb;
+  for (int c = 0; c < ce - cb; ++c)
+    if (sc[c] <= slim) { ++tied; only = cb + c; }
+  if (tied == 1) return only;
+  double vv[MC_MAX_CAND];
   double vmax = 0.0;
   bool have = false;
-  for (int c = 0; c < ce - cb; ++c)
-    if (sc[c] <= slim && (!have || vv[c] > vmax)) { vmax = vv[c]; have = true; }
+  for (int c = 0; c < ce - cb; ++c) {
+    if (!(sc[c] <= slim)) continue;
+    const int tb = MC_CAND_TRI_BEGIN[cb + c];
+    double v = 0.0;
+    for (int t = 0; t < nt; ++t) {
+      const unsigned char* tr = &MC_CAND_TRIPLES[3 * (tb + t)];
+      v = __dadd_rn(v, pin_vol6(w[tr[0]], w[tr[1]], w[tr[2]]));
+    }
+    vv[c] = v;
+    if (!have || v > vmax) { vmax = v; have = true; }
+  }
   const double vlim = __dsub_rn(vmax, __dmul_rn(__dmul_rn(__dmul_rn(sp[0], sp[1]), sp[2]), 1e-9));
   for (int c = 0; c < ce - cb; ++c)
     if (sc[c] <= slim && vv[c] >= vlim) return cb + c;
@@ -780,8 +793,12 @@ __global__ void __launch_bounds__(kCubeThreads) k_cubes(const uint32_t* bits, co
   unsigned int err = 0;
   const int lane = threadIdx.x & 31;
   const long long stride = (long long)gridDim.x * blockDim.x;
-  // warp-uniform loop: lanes past the end take part in the aggregation below
-  for (long long k0 = blockIdx.x * (long long)blockDim.x + threadIdx.x - lane; k0 < ncubes; k0 += stride) {
+  // warp-uniform loop: lanes past the end take part in the aggregation below.
+  // Consecutive 32-cube groups go to consecutive blocks (the warps are
+  // interleaved over the grid), so a short cube list still spreads over every
+  // SM's FP64 units instead of filling the first blocks only.
+  const long long gw = (long long)(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+  for (long long k0 = gw * 32; k0 < ncubes; k0 += stride) {
     const long long k = k0 + lane;
     const bool valid = k < ncubes;
     const int4 cu = valid ? cubes[k] : make_int4(0, 0, 0, 0);
