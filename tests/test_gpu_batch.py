@@ -16,8 +16,9 @@ if torch.cuda.is_available():
     from paper_2510_02894_gb300 import rad
 
 
-def test_batch_matches_oracle_per_roi():
-    crops = synth.batch_256(2, n=64)
+@pytest.mark.parametrize("seed,n", [(2, 64), (0, 256)])  # seed 0, 256: the benchmark's crops
+def test_batch_matches_oracle_per_roi(seed, n):
+    crops = synth.batch_256(seed, n=n)
     masks = [torch.from_numpy(m).cuda() for m, _ in crops]
     b = rad.Batch(masks, [s for _, s in crops])
     refs = [oracle.features(m, s)[0] for m, s in crops]
