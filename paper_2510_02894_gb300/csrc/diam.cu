@@ -1858,13 +1858,22 @@ rad_status diam_run(int n, const RoiDiam* rd, const RoiOut* ro, const long long*
              ro, p, offs, cursor, ctab, sorted, ids, sweep, ps, fs);
   RAD_LAUNCH("diam_setup", k_setup, wave_grid(k_setup, 256, (n + nplanes + (frac ? fs.gcap : 0) + 255) / 256 + 1), 256,
              0, st, rd, p, offs, probs, chunk0, cnt, fs);
-  RAD_LAUNCH("diam_tile_box", k_tile_box, wave_grid(k_tile_box, 256, 1LL << 30), 256, 0, st, sorted, probs, p, cnt,
+  // grids no larger than the host-side bounds of their work (small ROIs then
+  // launch a few blocks instead of a full wave): one warp per tile; (tile row,
+  // chunk) items are at most tiles x chunks per row; coarse pairs exist only
+  // when one problem can reach kBigTiles tiles
+  const long long tile_blocks = (p.max_tiles + p.max_fine + 7) / 8;
+  const long long walk_items = p.max_tiles * ((p.max_tiles + kChunk - 1) / kChunk);
+  const long long walk_blocks = (walk_items + 7) / 8;
+  const bool can_coarse = nsorted >= (long long)kBigTiles * p.TS;
+  RAD_LAUNCH("diam_tile_box", k_tile_box, wave_grid(k_tile_box, 256, tile_blocks), 256, 0, st, sorted, probs, p, cnt,
              tiles, chunk0, box, rep);
-  RAD_LAUNCH("diam_seed", k_seed, wave_grid(k_seed, 256, 1LL << 30), 256, 0, st, sorted, rep, p, tiles, chunk0, cnt, ps,
+  RAD_LAUNCH("diam_seed", k_seed, wave_grid(k_seed, 256, walk_blocks), 256, 0, st, sorted, rep, p, tiles, chunk0, cnt, ps,
              rd, box);
-  RAD_LAUNCH("diam_cull", k_cull, wave_grid(k_cull, 256, 1LL << 30), 256, 0, st, tiles, box, p, chunk0, cnt, ps, work,
+  RAD_LAUNCH("diam_cull", k_cull, wave_grid(k_cull, 256, walk_blocks), 256, 0, st, tiles, box, p, chunk0, cnt, ps, work,
              refine);
-  RAD_LAUNCH("diam_refine", k_refine, wave_grid(k_refine, 256, std::max<long long>(1, p.refine_cap / 8)), 256, 0, st,
+  RAD_LAUNCH("diam_refine", k_refine, wave_grid(k_refine, 256, can_coarse ? std::max<long long>(1, p.refine_cap / 8) : 1),
+             256, 0, st,
              tiles, box, p, cnt, ps, refine, work);
   const int ctas = sms * tu.ctas_per_sm;
   if (s.fp64_pairs) {  // every surviving pair in FP64: no filter, no candidates

@@ -1510,7 +1510,8 @@ rad_status mesh_emit(const MeshBatch& b, MeshScratch& s, MeshTotals* tot, RoiOut
   const int sms = num_sms();
   const long long warps_needed = (b.rows + (32 / b.L) - 1) / (32 / b.L);
   const int rblocks = (int)std::max<long long>(1, std::min<long long>((warps_needed + 7) / 8, (long long)sms * 8));
-  const int cblocks = sms * kCubeBlocksPerSM;
+  // no more blocks than the cube capacity needs (a small map launches a few)
+  const int cblocks = (int)std::min<long long>((long long)sms * kCubeBlocksPerSM, (ccap + kCubeThreads - 1) / kCubeThreads);
   if (b.soft) {
     RAD_LAUNCH("mc_rows_soft", k_rows<true>, rblocks, 256, 0, st, s.bits.as<uint32_t>(), b.rois, b.n, b.rows, b.L,
                b.Wc, s.counts.as<int4>(), s.wpre.as<int>(), s.prefix.as<long long>(), idx2,
@@ -1520,7 +1521,10 @@ rad_status mesh_emit(const MeshBatch& b, MeshScratch& s, MeshTotals* tot, RoiOut
                (const BinCase*)nullptr, tri, ccap, tcap, tot, out, s.hist.as<unsigned long long>(),
                s.partial.as<double>());
   } else {
-    const int eblocks = sms * kEmitBlocksPerSM;  // persistent: the list length is known on the device only
+    // persistent: the list length is known on the device only; the words of
+    // all rows bound it (a small mask launches a few blocks)
+    const int eblocks = (int)std::max<long long>(
+        1, std::min<long long>((long long)sms * kEmitBlocksPerSM, (b.wpre + 32 * kEmitWarps - 1) / (32 * kEmitWarps)));
     RAD_LAUNCH("mc_emit", k_emit, eblocks, kEmitThreads, 0, st, s.bits.as<uint32_t>(), b.rois, b.n,
                s.wlist.as<int2>(), b.wpre, s.wpre.as<int>(), s.tpre.as<int>(), s.prefix.as<long long>(),
                s.bintab.as<BinCase>(), idx2, tri, vcap, tcap, tot, out,
