@@ -37,6 +37,14 @@ def test_ct_512x512x256():
     mask, sp = synth.ct_512(0)
     got = check_full(mask, sp)
     assert got["n_vertices"] > 100000
+    # from a pinned host buffer (the slab-pipelined pass): the same features
+    host = torch.from_numpy(mask).pin_memory()
+    ws = rad.Workspace()
+    for _ in range(2):
+        h = rad.extract_host(host.data_ptr(), mask.shape, sp, ws)
+        for k in got:
+            if k not in ("status",):
+                assert h[k] == got[k], k
 
 
 def test_batch_crops():
