@@ -37,7 +37,7 @@ def test_ct_512x512x256():
     mask, sp = synth.ct_512(0)
     got = check_full(mask, sp)
     assert got["n_vertices"] > 100000
-    # from a pinned host buffer (the slab-pipelined pass): the same features
+    # from a pinned host buffer, read in place over the host link: the same features
     host = torch.from_numpy(mask).pin_memory()
     ws = rad.Workspace()
     for _ in range(2):

@@ -141,9 +141,7 @@ def test_extract_paths_agree():
     m2 = (synth._noise_blob(rng, (30, 40, 50), 2.0) > 0.5).astype(np.uint8)
     ref2, _ = oracle.features(m2, (0.5, 0.5, 1.0))
     assert_features(rad.extract(torch.from_numpy(m2).cuda(), (0.5, 0.5, 1.0), ws), ref2)
-    # a pinned mask is meshed in z-slabs (read over the host link while the
-    # slabs already read are counted and emitted): slab sizes that leave some
-    # slabs without rows of their own, and rows of odd widths
+    # pinned masks of odd sizes and row widths, read in place at every call
     for shape in ((16, 9, 7), (17, 33, 40), (64, 20, 90)):
         mk = (synth._noise_blob(rng, shape, 1.5) > 0.5).astype(np.uint8)
         refk, _ = oracle.features(mk, (0.7, 0.9, 1.3))
