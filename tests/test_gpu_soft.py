@@ -229,3 +229,29 @@ def test_soft_batch_rejects_bad_arguments():
         rad.soft_batch_backward([p], [(1.0, 1.0, 1.0)], [W6], [bad], [g], ws)
     with pytest.raises(ValueError):
         rad.soft_batch_forward([], [], ws)
+
+
+def test_autograd_planes_and_batch():
+    """The six-feature autograd functions (one map, and a batch of maps)
+    against the oracle's forward values and analytic gradients."""
+    from paper_2510_02894_gb300.soft import SIX, soft_batch_features, soft_shape_features6
+    w = torch.tensor([0.3, -0.4, 1.1, 0.9, -0.6, 0.5], dtype=torch.float64, device="cuda")
+    maps = [synth.soft_160(20, n=28), synth.soft_160(21, n=36)]
+    # one map
+    prob, sp = maps[0]
+    t = torch.from_numpy(prob).cuda().requires_grad_(True)
+    f6 = soft_shape_features6(t, sp)
+    (f6 * w).sum().backward()
+    ref, om = oracle.features(prob, sp)
+    assert [f6[k].item() for k in range(6)][2:] == [ref[k] for k in SIX[2:]]
+    gr = oracle.soft_grad_planes(om, 0.3, -0.4, (1.1, 0.9, -0.6, 0.5), [ref[k] for k in rad.ARGMAX_KEYS])
+    assert np.allclose(t.grad.double().cpu().numpy(), gr, rtol=1e-6, atol=1e-9 * np.abs(gr).max())
+    # a batch of two
+    ts = [torch.from_numpy(p).cuda().requires_grad_(True) for p, _ in maps]
+    fb = soft_batch_features(ts, [s for _, s in maps])
+    (fb * w).sum().backward()
+    for tk, (p, s), row in zip(ts, maps, fb):
+        ref, om = oracle.features(p, s)
+        assert [row[k].item() for k in range(2, 6)] == [ref[k] for k in SIX[2:]]
+        gr = oracle.soft_grad_planes(om, 0.3, -0.4, (1.1, 0.9, -0.6, 0.5), [ref[k] for k in rad.ARGMAX_KEYS])
+        assert np.allclose(tk.grad.double().cpu().numpy(), gr, rtol=1e-6, atol=1e-9 * np.abs(gr).max())
