@@ -1510,8 +1510,11 @@ rad_status mesh_emit(const MeshBatch& b, MeshScratch& s, MeshTotals* tot, RoiOut
   const int sms = num_sms();
   const long long warps_needed = (b.rows + (32 / b.L) - 1) / (32 / b.L);
   const int rblocks = (int)std::max<long long>(1, std::min<long long>((warps_needed + 7) / 8, (long long)sms * 8));
-  // no more blocks than the cube capacity needs (a small map launches a few)
-  const int cblocks = (int)std::min<long long>((long long)sms * kCubeBlocksPerSM, (ccap + kCubeThreads - 1) / kCubeThreads);
+  // a whole number of blocks per SM: the 32-cube groups are dealt round-robin
+  // over the blocks, so every SM gets the same number of groups (the FP64
+  // pipes bound this kernel; a grid that is not a multiple of the SM count
+  // leaves some SMs with twice the work of others)
+  const int cblocks = sms * kCubeBlocksPerSM;
   if (b.soft) {
     RAD_LAUNCH("mc_rows_soft", k_rows<true>, rblocks, 256, 0, st, s.bits.as<uint32_t>(), b.rois, b.n, b.rows, b.L,
                b.Wc, s.counts.as<int4>(), s.wpre.as<int>(), s.prefix.as<long long>(), idx2,
