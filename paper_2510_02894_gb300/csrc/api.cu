@@ -1086,6 +1086,10 @@ rad_status rad_crop_resample(const uint8_t* mask_dev, const int64_t dims[3], con
         return RAD_ERR_INVALID_ARG;
       }
   RAD_TRY(check_device_ptr(mask_dev, "mask_dev"));
+  if ((dims[0] + 15) / 16 * dims[1] * dims[2] >= (1ll << 31)) {
+    set_error("mask too large for one call (%lld 16-voxel chunks)", (long long)((dims[0] + 15) / 16 * dims[1] * dims[2]));
+    return RAD_ERR_INVALID_ARG;
+  }
   cudaStream_t st = (cudaStream_t)stream;
   Work& w = ensure_ws(ws)->work;
   PrepInfo info;
@@ -1098,6 +1102,10 @@ rad_status rad_crop_resample(const uint8_t* mask_dev, const int64_t dims[3], con
   record_stats(ResultBlock{}, 0, (long long)sizeof(PrepInfo), false);
   if (info.empty) return RAD_OK;
   const long long need = info.nout[0] * info.nout[1] * info.nout[2];
+  if ((info.nout[0] + 3) / 4 * info.nout[1] * info.nout[2] >= (1ll << 31)) {
+    set_error("output of %lld voxels is too large for one call", need);
+    return RAD_ERR_INVALID_ARG;
+  }
   if (need > out_capacity || !out_dev) {
     set_error("output needs %lld bytes, capacity %lld", need, (long long)out_capacity);
     return RAD_ERR_CAPACITY;

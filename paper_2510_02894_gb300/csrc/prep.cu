@@ -25,6 +25,17 @@ __device__ __forceinline__ bool roi_byte(unsigned int b, int label) {
   return label < 0 ? b != 0u : b == (unsigned int)label;
 }
 
+// The four bytes of v that are ROI voxels as 4 bits (byte k -> bit k), all
+// four tested at once: a non-zero test (label < 0), or a zero test of v XOR
+// the label replicated into every byte.
+__device__ __forceinline__ uint32_t roi4(uint32_t v, int label) {
+  const uint32_t x = label < 0 ? v : v ^ (0x01010101u * (uint32_t)label);
+  uint32_t t = (x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu;  // bit 7 of a byte set iff the byte of x is non-zero
+  t = (t | x) & 0x80808080u;
+  if (label >= 0) t ^= 0x80808080u;               // equal to the label: x's byte is zero
+  return (((t >> 7) * 0x00204081u) >> 21) & 0xFu;
+}
+
 // Lowest and highest set bit positions of a 16-bit mask (mask != 0).
 __device__ __forceinline__ void bit_range(unsigned int m, int& lo, int& hi) {
   lo = __ffs(m) - 1;
@@ -38,20 +49,19 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep_bbox(const uint8_t* mask,
                                                             double tx, double ty, double tz, int resample, int* box,
                                                             PrepInfo* info, unsigned int* ticket) {
   pdl_enter();
-  const int cpr = vec16 ? nx / 16 : (nx + 15) / 16;  // 16-voxel chunks per row
-  const long long total = (long long)cpr * ny * nz;
+  // 16-voxel chunks; the host keeps their count below 2^31, so the index
+  // arithmetic is 32-bit
+  const unsigned int cpr = vec16 ? nx / 16 : (nx + 15) / 16;
+  const unsigned int total = cpr * (unsigned int)ny * (unsigned int)nz;
   int bmin[3] = {INT_MAX, INT_MAX, INT_MAX}, bmax[3] = {-1, -1, -1};
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < total;
-       c += (long long)gridDim.x * blockDim.x) {
-    const long long row = c / cpr;
+  for (unsigned int c = blockIdx.x * blockDim.x + threadIdx.x; c < total; c += gridDim.x * blockDim.x) {
+    const unsigned int row = c / cpr;
     const int x0 = (int)(c - row * cpr) * 16;
-    const uint8_t* p = mask + row * nx + x0;
+    const uint8_t* p = mask + (long long)row * nx + x0;
     unsigned int m = 0u;
     if (vec16) {
       const uint4 v = __ldg(reinterpret_cast<const uint4*>(p));
-      const unsigned int w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-      for (int k = 0; k < 16; ++k) m |= (unsigned int)roi_byte((w[k >> 2] >> (8 * (k & 3))) & 0xffu, label) << k;
+      m = roi4(v.x, label) | (roi4(v.y, label) << 4) | (roi4(v.z, label) << 8) | (roi4(v.w, label) << 12);
     } else {
       const int nb = min(16, nx - x0);
       for (int k = 0; k < nb; ++k) m |= (unsigned int)roi_byte(__ldg(p + k), label) << k;
@@ -59,13 +69,14 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep_bbox(const uint8_t* mask,
     if (m == 0u) continue;
     int lo, hi;
     bit_range(m, lo, hi);
-    const int y = (int)(row % ny), z = (int)(row / ny);
+    const unsigned int z = row / (unsigned int)ny;
+    const int y = (int)(row - z * (unsigned int)ny);
     bmin[0] = min(bmin[0], x0 + lo);
     bmax[0] = max(bmax[0], x0 + hi);
     bmin[1] = min(bmin[1], y);
     bmax[1] = max(bmax[1], y);
-    bmin[2] = min(bmin[2], z);
-    bmax[2] = max(bmax[2], z);
+    bmin[2] = min(bmin[2], (int)z);
+    bmax[2] = max(bmax[2], (int)z);
   }
   // warp, then block, then one atomic per value and block
   __shared__ int s_min[3][kPrepThreads / 32], s_max[3][kPrepThreads / 32];
@@ -141,18 +152,18 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep_gather(const uint8_t* mas
   const PrepInfo r = *info;
   const long long ox = r.nout[0], oy = r.nout[1], oz = r.nout[2];
   const long long q = (ox + 3) / 4;  // quads per output row
-  const long long total = q * oy * oz;
+  const long long total = q * oy * oz;  // below 2^31 (checked on the host): 32-bit index arithmetic below
   const int* mx = maps;
   const int* my = maps + ox;
   const int* mz = my + oy;
   const bool aligned = (ox & 3) == 0 && ((uintptr_t)out & 3) == 0;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long row = e / q;
-    const long long x0 = (e - row * q) * 4;
-    const long long y = row % oy, z = row / oy;
+  const unsigned int q32 = (unsigned int)q, oy32 = (unsigned int)oy, tot32 = (unsigned int)total;
+  for (unsigned int e = blockIdx.x * blockDim.x + threadIdx.x; e < tot32; e += gridDim.x * blockDim.x) {
+    const unsigned int row = e / q32;
+    const long long x0 = (long long)(e - row * q32) * 4;
+    const unsigned int z = row / oy32, y = row - z * oy32;
     const uint8_t* src = mask + ((long long)__ldg(&mz[z]) * ny + __ldg(&my[y])) * nx;
-    uint8_t* dst = out + row * ox + x0;
+    uint8_t* dst = out + (long long)row * ox + x0;
     const int nb = (int)min(4ll, ox - x0);
     unsigned int v = 0u;
     for (int k = 0; k < nb; ++k) v |= (unsigned int)roi_byte(__ldg(src + __ldg(&mx[x0 + k])), label) << (8 * k);
