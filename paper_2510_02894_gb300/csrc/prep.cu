@@ -10,10 +10,10 @@
 //               voxel i samples lo_k + min(m_k - 1, floor(i s'_k / s_k + 1/2))
 //   output      1 where the sampled voxel is an ROI voxel, else 0
 //
-// Three kernels: a bounding-box reduction over the mask (HBM-bound, 16 bytes
-// per load where rows allow it; its last block derives the box and the
-// output size), the three per-axis index maps, and a gather that writes the
-// output four voxels per thread.
+// Three kernels: a bounding-box reduction over the mask (16 bytes per load
+// where rows allow it, four bytes tested per instruction; its last block
+// derives the box and the output size), the three per-axis index maps, and a
+// gather that writes sixteen output voxels per thread.
 #include <limits.h>
 
 #include "rad_internal.cuh"
@@ -144,33 +144,43 @@ __global__ void k_prep_maps(const PrepInfo* info, double sx, double sy, double s
   }
 }
 
-// Output voxels, four consecutive x per thread (one 32-bit store where the
-// output row allows it).
+// Output voxels, sixteen consecutive bytes of the flat output per thread,
+// whatever the row length: the first byte's (x, y, z) from one division, then
+// x stepped (and the row advanced at its end); one 16-byte store when the
+// output is 16-byte aligned and the run is whole.
 __global__ void __launch_bounds__(kPrepThreads) k_prep_gather(const uint8_t* mask, int nx, int ny, int label,
                                                               const PrepInfo* info, const int* maps, uint8_t* out) {
   pdl_enter();
   const PrepInfo r = *info;
   const long long ox = r.nout[0], oy = r.nout[1], oz = r.nout[2];
-  const long long q = (ox + 3) / 4;  // quads per output row
-  const long long total = q * oy * oz;  // below 2^31 (checked on the host): 32-bit index arithmetic below
+  const long long total = ox * oy * oz;  // with the runs below 2^31 x 16 (checked on the host)
+  const unsigned int runs = (unsigned int)((total + 15) / 16);
   const int* mx = maps;
   const int* my = maps + ox;
   const int* mz = my + oy;
-  const bool aligned = (ox & 3) == 0 && ((uintptr_t)out & 3) == 0;
-  const unsigned int q32 = (unsigned int)q, oy32 = (unsigned int)oy, tot32 = (unsigned int)total;
-  for (unsigned int e = blockIdx.x * blockDim.x + threadIdx.x; e < tot32; e += gridDim.x * blockDim.x) {
-    const unsigned int row = e / q32;
-    const long long x0 = (long long)(e - row * q32) * 4;
-    const unsigned int z = row / oy32, y = row - z * oy32;
+  const bool aligned = ((uintptr_t)out & 15) == 0;
+  const unsigned int ox32 = (unsigned int)ox, oy32 = (unsigned int)oy;
+  for (unsigned int e = blockIdx.x * blockDim.x + threadIdx.x; e < runs; e += gridDim.x * blockDim.x) {
+    const long long f0 = (long long)e * 16;
+    unsigned int row = (unsigned int)(f0 / ox32);
+    unsigned int x = (unsigned int)(f0 - (long long)row * ox32);
+    unsigned int z = row / oy32, y = row - z * oy32;
     const uint8_t* src = mask + ((long long)__ldg(&mz[z]) * ny + __ldg(&my[y])) * nx;
-    uint8_t* dst = out + (long long)row * ox + x0;
-    const int nb = (int)min(4ll, ox - x0);
-    unsigned int v = 0u;
-    for (int k = 0; k < nb; ++k) v |= (unsigned int)roi_byte(__ldg(src + __ldg(&mx[x0 + k])), label) << (8 * k);
-    if (aligned) {
-      *reinterpret_cast<unsigned int*>(dst) = v;
+    const int nb = (int)min(16ll, total - f0);
+    uint32_t w[4] = {0u, 0u, 0u, 0u};
+    for (int k = 0; k < nb; ++k) {
+      w[k >> 2] |= (uint32_t)roi_byte(__ldg(src + __ldg(&mx[x])), label) << (8 * (k & 3));
+      if (++x == ox32 && k + 1 < nb) {  // next output row
+        x = 0;
+        if (++y == oy32) { y = 0; ++z; }
+        src = mask + ((long long)__ldg(&mz[z]) * ny + __ldg(&my[y])) * nx;
+      }
+    }
+    uint8_t* dst = out + f0;
+    if (aligned && nb == 16) {
+      *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
     } else {
-      for (int k = 0; k < nb; ++k) dst[k] = (uint8_t)((v >> (8 * k)) & 0xffu);
+      for (int k = 0; k < nb; ++k) dst[k] = (uint8_t)((w[k >> 2] >> (8 * (k & 3))) & 0xffu);
     }
   }
 }
@@ -216,9 +226,9 @@ rad_status prep_gather(const uint8_t* mask, const int64_t dims[3], const double 
   const double t[3] = {new_sp ? new_sp[0] : sp[0], new_sp ? new_sp[1] : sp[1], new_sp ? new_sp[2] : sp[2]};
   RAD_LAUNCH("prep_maps", k_prep_maps, wave_grid(k_prep_maps, 256, (nmap + 255) / 256), 256, 0, st, info, sp[0],
              sp[1], sp[2], t[0], t[1], t[2], new_sp ? 1 : 0, maps);
-  const long long quads = (info_host.nout[0] + 3) / 4 * info_host.nout[1] * info_host.nout[2];
+  const long long runs = (info_host.nout[0] * info_host.nout[1] * info_host.nout[2] + 15) / 16;
   RAD_LAUNCH("prep_gather", k_prep_gather,
-             wave_grid(k_prep_gather, kPrepThreads, (quads + kPrepThreads - 1) / kPrepThreads), kPrepThreads, 0, st,
+             wave_grid(k_prep_gather, kPrepThreads, (runs + kPrepThreads - 1) / kPrepThreads), kPrepThreads, 0, st,
              mask, (int)dims[0], (int)dims[1], label, info, maps, out);
   RAD_CUDA(cudaStreamSynchronize(st));  // a host copy of the box result may have been the source above
   return RAD_OK;
