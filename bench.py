@@ -415,7 +415,9 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--no-configs", action="store_true", help="skip the 32^3, soft 160^3 and 8 x 512^3 lines")
+    ap.add_argument("--no-configs", action="store_true", help="skip the 32^3, soft 160^3, 8 x 512^3 and crop lines")
+    ap.add_argument("--configs", default="c1,c4,c5,preprocess",
+                    help="which of those lines to run (comma-separated subset of c1,c4,c5,preprocess)")
     ap.add_argument("--ablation", action="store_true",
                     help="also time the FP64 accumulation variants on the CT mesh and the 256 crops")
     args = ap.parse_args()
@@ -633,10 +635,15 @@ def main():
     # ---- the other workloads: 32^3 latency, soft 160^3 forward + adjoint, 8 x 512^3 batch ----
     configs = {}
     if not args.no_configs:
-        configs["c1"] = bench_c1(args, stream, flush)
-        configs["c4"] = bench_c4(args, stream, flush, peaks["hbm_gbs"])
-        configs["c5"] = bench_c5(args, stream, flush)
-        configs["preprocess"] = bench_prep(args, stream, flush, peaks["hbm_gbs"], dev, sp)
+        want = set(c.strip() for c in args.configs.split(","))
+        if "c1" in want:
+            configs["c1"] = bench_c1(args, stream, flush)
+        if "c4" in want:
+            configs["c4"] = bench_c4(args, stream, flush, peaks["hbm_gbs"])
+        if "c5" in want:
+            configs["c5"] = bench_c5(args, stream, flush)
+        if "preprocess" in want:
+            configs["preprocess"] = bench_prep(args, stream, flush, peaks["hbm_gbs"], dev, sp)
 
     # ---- CPU baseline: the oracle on a bounded sample --------------------------------
     cpu = None
