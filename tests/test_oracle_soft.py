@@ -167,3 +167,49 @@ def test_soft_grad_planes_reduces_to_3d_term():
     a = oracle.soft_grad(m, 0.3, 0.6, 1.7, f["argmax3d"])
     b = oracle.soft_grad_planes(m, 0.3, 0.6, (1.7, 0.0, 0.0, 0.0), [f[k] for k in ARGS4])
     assert np.array_equal(a, b)
+
+
+def _numpy_planar(u, sp, axis):
+    """Max pinned d2 over the pairs with exactly equal coordinate on `axis`,
+    smallest (i, j) on ties: an explicit numpy scan, independent of the C code."""
+    best = (0.0, -1, -1)
+    n = u.shape[0]
+    s = np.asarray(sp, np.float64)
+    for i in range(n - 1):
+        j = np.arange(i + 1, n)
+        j = j[u[j, axis] == u[i, axis]]
+        if j.size == 0:
+            continue
+        d = (u[i] - u[j]) * s
+        d2 = (d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2]
+        k = int(np.argmax(d2))  # first maximum: the smallest j for this i
+        if d2[k] > best[0] or best[1] < 0:
+            best = (float(d2[k]), i, int(j[k]))
+    return best
+
+
+@pytest.mark.parametrize("case", ["layered", "soft20"])
+def test_soft_planes_by_exact_coordinate(case):
+    """Planar diameters of soft meshes: planes are sets of exactly equal FP64
+    coordinates, on the grid planes or off them (vertices of edges along the
+    axis whose interpolated coordinates coincide)."""
+    if case == "layered":
+        n = 14
+        vals = np.zeros((n, n, n), np.float32)
+        z = np.arange(n)
+        prof = (0.95 - 0.05 * np.abs(z - n / 2.0)).astype(np.float32)
+        vals[:, 2:n - 2, 3:n - 4] = prof[:, None, None]
+        vals[n // 2, 4:7, 5:8] = 0.5
+        sp = (1.0, 1.0, 1.0)
+    else:
+        vals, sp = synth.soft_160(9, n=20)
+    m = oracle.OracleMesh(vals, sp)
+    ref = oracle.diameters_bruteforce(m.u, sp)
+    for q, ax in ((1, 2), (2, 1), (3, 0)):
+        want = _numpy_planar(m.u, sp, ax)
+        assert ref[q] == want, (case, ax, ref[q], want)
+        assert oracle.diameter2d(m.u, sp, ax) == want
+    if case == "layered":  # off-grid planes of many vertices exist
+        zc = m.u[:, 2]
+        frac = zc[zc != np.floor(zc)]
+        assert np.unique(frac, return_counts=True)[1].max() >= 8
