@@ -457,6 +457,13 @@ def main():
     # ---- timed region: device-resident inputs ------------------------------------
     clocks = ClockSampler(local)
     clocks.start()
+    # the timed steps last a few ms, shorter than nvidia-smi's sampling period:
+    # the same steps run untimed for about a second inside the sampling window
+    # first, so the samples see the clocks under this load
+    t_end = time.perf_counter() + 1.0
+    while time.perf_counter() < t_end:
+        flush.zero_()
+        rad.extract(dev, sp, ws)
     launches0 = rad.launch_count()
     barrier(world)
     torch.cuda.synchronize()
