@@ -127,6 +127,7 @@ struct Counters {
   unsigned int n_refine;     // surviving coarse tile pairs
   unsigned int seed_done;  // last-block ticket of the seed
   unsigned int n_groups;   // planes of a soft map off the grid planes (groups of equal coordinate)
+  unsigned int confirm_done, pad3;  // last-block ticket of the FP64 confirmation
 };
 
 // Batch-wide parameters of one run.
@@ -1532,44 +1533,31 @@ __global__ void k_keys_out(const Key128* keys, int n, DiamOut* out) {
 
 // ---- 5. FP64 confirmation -------------------------------------------------------------
 
-// Largest pinned FP64 d2 per ROI and category.  Every pair attaining it is a
-// candidate of its problem, so the maximum over candidates is the maximum.
-__global__ void k_confirm(const int* ids, const int16_t* idx2,
-                          const double* vt, Params p, const RoiDiam* rd,
-                          const Counters* cnt, const Cand* cand,
-                          DiamOut* out) {
-  pdl_enter();
-  const long long nc = min(cnt->n_cand, p.cand_cap);
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nc; c += (long long)gridDim.x * blockDim.x) {
-    const Cand k = cand[c];
-    const RoiDiam& r = rd[k.roi];
-    const int i = ids[k.ea], j = ids[k.eb];
-    double ui[3], uj[3];
-    vertex_u(idx2, vt, i, ui);
-    vertex_u(idx2, vt, j, uj);
-    const double d2 = pin_d2(ui[0], ui[1], ui[2], uj[0], uj[1], uj[2], r.sx, r.sy, r.sz);
-    atomicMax(&out[k.roi].d2[k.q], (unsigned long long)__double_as_longlong(d2));
-  }
+// The FP64 confirmation: every candidate's pinned FP64 d2 and its pair (ids
+// local to the ROI, i < j) as one 128-bit key, raised into its (ROI,
+// category) family with a compare-and-swap: the largest d2, then the
+// smallest (i, j).  Every pair attaining the maximum is a candidate of its
+// problem, so the family's key is the FP64 maximum with its tie-break.  The
+// block that finishes last writes the keys into the per-ROI results and
+// copies the counters.
+__device__ void copy_stats(Counters* cnt, DiamStats* stats) {
+  stats->problems = cnt->n_problems;
+  stats->tiles = (long long)(cnt->alloc & 0xffffffffull) + (long long)cnt->alloc_fine;
+  stats->tile_pairs = cnt->n_pairs;
+  stats->work_items = cnt->n_work;
+  stats->items_evaluated = (long long)cnt->items_evaluated;
+  stats->pairs_evaluated = (long long)cnt->pairs_evaluated;
+  stats->candidates = cnt->n_cand;
+  stats->coarse_pairs = cnt->n_refine;
+  stats->status |= cnt->status;
 }
 
-// Candidates attaining their ROI's maximum in their category take the
-// smallest (i, j) (ids local to the ROI).  Block 0 also copies the counters.
-__global__ void k_tiebreak(const int* ids, const int16_t* idx2,
-                           const double* vt, Params p, const RoiDiam* rd,
-                           const RoiOut* ro, const Counters* cnt,
-                           const Cand* cand, DiamOut* out, DiamStats* stats) {
+__global__ void k_confirm(const int* ids, const int16_t* idx2,
+                          const double* vt, Params p, const RoiDiam* rd,
+                          const RoiOut* ro, Counters* cnt, const Cand* cand,
+                          Key128* keys, DiamOut* out, DiamStats* stats) {
   pdl_enter();
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    stats->problems = cnt->n_problems;
-    stats->tiles = (long long)(cnt->alloc & 0xffffffffull) + (long long)cnt->alloc_fine;
-    stats->tile_pairs = cnt->n_pairs;
-    stats->work_items = cnt->n_work;
-    stats->items_evaluated = (long long)cnt->items_evaluated;
-    stats->pairs_evaluated = (long long)cnt->pairs_evaluated;
-    stats->candidates = cnt->n_cand;
-    stats->coarse_pairs = cnt->n_refine;
-    stats->status |= cnt->status;
-  }
+  __shared__ bool s_last;
   const long long nc = min(cnt->n_cand, p.cand_cap);
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nc; c += (long long)gridDim.x * blockDim.x) {
     const Cand k = cand[c];
@@ -1579,14 +1567,33 @@ __global__ void k_tiebreak(const int* ids, const int16_t* idx2,
     vertex_u(idx2, vt, i, ui);
     vertex_u(idx2, vt, j, uj);
     const double d2 = pin_d2(ui[0], ui[1], ui[2], uj[0], uj[1], uj[2], r.sx, r.sy, r.sz);
-    if ((unsigned long long)__double_as_longlong(d2) == __ldcg(&out[k.roi].d2[k.q])) {
-      const long long v0 = ro[k.roi].v0;
-      i -= (int)v0;
-      j -= (int)v0;
-      if (i > j) { const int t = i; i = j; j = t; }
-      atomicMin(&out[k.roi].pair[k.q], ((unsigned long long)(unsigned int)i << 32) | (unsigned int)j);
+    const int v0 = (int)ro[k.roi].v0;
+    i -= v0;
+    j -= v0;
+    atomic_max_key(&keys[fam_of(k.roi, k.q)], make_key(d2, min(i, j), max(i, j)));
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&cnt->confirm_done, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  for (int f = threadIdx.x; f < 4 * p.n; f += blockDim.x) {
+    Key128 k;
+    k.lo = __ldcg(&keys[f].lo);
+    k.hi = __ldcg(&keys[f].hi);
+    if (k.hi | k.lo) {
+      out[f >> 2].d2[f & 3] = k.hi;
+      out[f >> 2].pair[f & 3] = ~k.lo;
     }
   }
+  if (threadIdx.x == 0) copy_stats(cnt, stats);
+}
+
+// Statistics only (the culled FP64 mode has no candidates).
+__global__ void k_stats(Counters* cnt, DiamStats* stats) {
+  pdl_enter();
+  if (threadIdx.x == 0 && blockIdx.x == 0) copy_stats(cnt, stats);
 }
 
 __global__ void k_diam_init(DiamOut* out, int n, ZeroSet zs, const RoiDiam* rd,
@@ -1834,7 +1841,7 @@ rad_status diam_run(int n, const RoiDiam* rd, const RoiOut* ro, const long long*
   zero_add(zs, scan_state, sizeof(ScanTile<1>) * nparts + 16);
   zero_add(zs, stats, sizeof(DiamStats));
   zero_add(zs, fam_state, fam_bytes);  // F = T = 0 for every family; sweep slots
-  if (s.fp64_pairs) zero_add(zs, keys, sizeof(Key128) * 4 * n);
+  zero_add(zs, keys, sizeof(Key128) * 4 * n);  // family keys of the FP64 confirmation (or FP64 pair mode)
   if (frac) zero_add(zs, fs.hkey, (sizeof(Key128) + sizeof(int)) * hsize);  // keys and counts (adjacent)
   if (which & 1) {
     // on its own (a graph branch beside the mesh) it needs few CTAs: a few MB zeroed
@@ -1888,7 +1895,7 @@ rad_status diam_run(int n, const RoiDiam* rd, const RoiOut* ro, const long long*
                  st, ids, idx2, vt, work, p, rd, ro, cnt, ps, keys);
     }
     RAD_LAUNCH("diam_keys_out", k_keys_out, std::max(1, std::min(sms, (4 * n + 255) / 256)), 256, 0, st, keys, n, out);
-    RAD_LAUNCH("diam_tiebreak", k_tiebreak, 1, 32, 0, st, ids, idx2, vt, p, rd, ro, cnt, cand, out, stats);  // statistics
+    RAD_LAUNCH("diam_stats", k_stats, 1, 32, 0, st, cnt, stats);
     return RAD_OK;
   }
   if (tu.tile == 64) {
@@ -1902,8 +1909,7 @@ rad_status diam_run(int n, const RoiDiam* rd, const RoiOut* ro, const long long*
     if (tu.threads == 64) RAD_TRY((launch_pairs<256, 64>(sorted, work, p, rd, cnt, ps, slicemax, hits, cand, ctas, st)));
     else RAD_TRY((launch_pairs<256, 128>(sorted, work, p, rd, cnt, ps, slicemax, hits, cand, ctas, st)));
   }
-  RAD_LAUNCH("diam_confirm", k_confirm, sms, 256, 0, st, ids, idx2, vt, p, rd, cnt, cand, out);
-  RAD_LAUNCH("diam_tiebreak", k_tiebreak, sms, 256, 0, st, ids, idx2, vt, p, rd, ro, cnt, cand, out, stats);
+  RAD_LAUNCH("diam_confirm", k_confirm, sms, 256, 0, st, ids, idx2, vt, p, rd, ro, cnt, cand, keys, out, stats);
   return RAD_OK;
 }
 
