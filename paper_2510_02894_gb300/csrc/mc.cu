@@ -983,7 +983,7 @@ __global__ void __launch_bounds__(kCubeThreads) k_cubes(const uint32_t* bits, co
 // prefix over the cube's run in the list plus a per-word carry between rounds).
 constexpr int kEmitThreads = 128;
 constexpr int kEmitWarps = kEmitThreads / 32;
-constexpr int kEmitBlocksPerSM = 5;  // 39 KB of shared memory per block
+constexpr int kEmitBlocksPerSM = 6;  // 36.3 KB of shared memory per block
 constexpr int kListCap = 32 * 33;   // 32 words x (32 bits + the x = -1 entry)
 
 struct __align__(16) EmitShared {
@@ -1020,24 +1020,27 @@ __global__ void __launch_bounds__(kEmitThreads, kEmitBlocksPerSM)
            MeshTotals* tot, RoiOut* out, unsigned long long* case_hist) {
   pdl_enter();
   __shared__ EmitShared sh[kEmitWarps];
-  __shared__ unsigned int s_hist[kEmitWarps][256];  // case counts of the warp's current ROI
+  // case counts of the warp's current ROI, 16 bits each: they are flushed
+  // before the cubes counted since the last flush could pass 65,535
+  __shared__ unsigned short s_hist[kEmitWarps][256];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   EmitShared& S = sh[wid];
-  unsigned int* hist = s_hist[wid];
+  unsigned short* hist = s_hist[wid];
+  unsigned int since = 0;  // cubes of the tagged ROI offered to the counts since the last flush
   const long long nlist = min(tot->nwords, wlist_cap);
   const long long nchunk = (nlist + 31) / 32;
   unsigned int err = 0;
   // volume sum and case counts of one ROI (tag) stay in the warp until the ROI changes
   int tag = -1;
   long long vacc = 0;
-  for (int c = lane; c < 256; c += 32) hist[c] = 0u;
+  for (int c = lane; c < 256; c += 32) hist[c] = 0;
   auto flush = [&]() {
     __syncwarp();
     if (tag >= 0) {
       for (int c = lane; c < 256; c += 32) {
         const unsigned int h = hist[c];
         if (h) atomicAdd(&case_hist[(long long)tag * 256 + c], (unsigned long long)h);
-        hist[c] = 0u;
+        hist[c] = 0;
       }
       long long v = vacc;  // the leader of the tagged run differs between rounds
       for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
@@ -1113,6 +1116,7 @@ __global__ void __launch_bounds__(kEmitThreads, kEmitBlocksPerSM)
       if (t0 != tag) {
         flush();
         tag = t0;
+        since = 0;
       }
     }
 
@@ -1163,6 +1167,11 @@ __global__ void __launch_bounds__(kEmitThreads, kEmitBlocksPerSM)
     const int cin = warp_incl(cc, lane);
     const int ctot = __shfl_sync(0xffffffffu, cin, 31);
     if (ctot == 0) continue;  // warp-uniform
+    if (since + (unsigned int)ctot > 65535u) {  // no count can pass 16 bits
+      flush();
+      since = 0;
+    }
+    since += (unsigned int)ctot;
     {
       int o = cin - cc;
       if (case_m1) S.list[o++] = (unsigned short)((lane << 6) | 32);
@@ -1266,7 +1275,7 @@ __global__ void __launch_bounds__(kEmitThreads, kEmitBlocksPerSM)
       const long long key = roi >= 0 ? (long long)roi * 256 + cs : -1;
       const unsigned int same_case = __match_any_sync(0xffffffffu, key);
       if (roi >= 0 && lane == __ffs(same_case) - 1) {
-        if (roi == tag) hist[cs] += (unsigned int)__popc(same_case);
+        if (roi == tag) hist[cs] = (unsigned short)(hist[cs] + __popc(same_case));
         else atomicAdd(&case_hist[key], (unsigned long long)__popc(same_case));
       }
     }

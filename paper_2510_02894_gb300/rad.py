@@ -264,25 +264,27 @@ class Workspace:
             self.h = ctypes.c_void_p(None)
 
 
-def extract(mask, spacing, ws, stream=None):
-    """Whole path (mesh + all features) for a CUDA uint8 mask."""
+def extract(mask, spacing, ws, stream=None, out=None):
+    """Whole path (mesh + all features) for a CUDA uint8 mask.  Returns a
+    dict, or, when `out` (a Features) is given, fills it and returns it (the
+    rad_features_t the call wrote, no conversion)."""
     _device_tensor(mask, "torch.uint8")
     dims, sp = _geometry(mask.shape, spacing)
-    f = Features()
+    f = Features() if out is None else out
     _check(lib().rad_extract(ctypes.c_void_p(mask.data_ptr()), dims, sp, ctypes.byref(f), ctypes.byref(ws.h),
                              _stream(stream)))
-    return f.as_dict()
+    return f.as_dict() if out is None else f
 
 
-def extract_host(mask_ptr, shape_zyx, spacing, ws, stream=None):
+def extract_host(mask_ptr, shape_zyx, spacing, ws, stream=None, out=None):
     """Whole path for a HOST mask given by address and shape [nz, ny, nx].
     Pinned memory is read in place by the device; pageable memory is copied
-    inside the call."""
+    inside the call.  `out` as in extract()."""
     dims, sp = _geometry(shape_zyx, spacing)
-    f = Features()
+    f = Features() if out is None else out
     _check(lib().rad_extract_host(ctypes.c_void_p(int(mask_ptr)), dims, sp, ctypes.byref(f), ctypes.byref(ws.h),
                                   _stream(stream)))
-    return f.as_dict()
+    return f.as_dict() if out is None else f
 
 
 def soft_forward(prob, spacing, ws, stream=None):
@@ -434,10 +436,18 @@ class Batch:
         _check(lib().rad_batch_create(n, ptrs, dims, sp, ctypes.byref(self.h), _stream(stream)))
         self.n = n
 
-    def run(self, stream=None):
-        out = (Features * self.n)()
-        _check(lib().rad_batch_run(self.h, out, _stream(stream)))
-        return [f.as_dict() for f in out]
+    def features_buffer(self):
+        """A rad_features_t array for run(out=...)."""
+        return (Features * self.n)()
+
+    def run(self, stream=None, out=None):
+        """Features of every ROI: a list of dicts, or, when `out` (from
+        features_buffer()) is given, that array filled by the call."""
+        buf = (Features * self.n)() if out is None else out
+        if len(buf) != self.n:
+            raise ValueError("out must hold one rad_features_t per ROI")
+        _check(lib().rad_batch_run(self.h, buf, _stream(stream)))
+        return [f.as_dict() for f in buf] if out is None else buf
 
     def __del__(self):
         if _lib is not None and getattr(self, "h", None) is not None and self.h.value:

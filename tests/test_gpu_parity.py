@@ -123,9 +123,13 @@ def test_extract_paths_agree():
     dev = torch.from_numpy(m).cuda()
     for _ in range(3):  # the workspace is reused
         assert_features(rad.extract(dev, sp, ws), ref)
+    f = rad.Features()  # the rad_features_t form, filled in place
+    assert rad.extract(dev, sp, ws, out=f) is f
+    assert_features(f.as_dict(), ref)
     host = torch.from_numpy(m).pin_memory()
     ws2 = rad.Workspace()
     assert_features(rad.extract_host(host.data_ptr(), m.shape, sp, ws2), ref)
+    assert_features(rad.extract_host(host.data_ptr(), m.shape, sp, ws2, out=rad.Features()).as_dict(), ref)
     # pageable host memory goes through a device copy
     ws3 = rad.Workspace()
     assert_features(rad.extract_host(m.ctypes.data, m.shape, sp, ws3), ref)
