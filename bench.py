@@ -550,6 +550,23 @@ def main():
                      "algorithmic_flops": amount})
     else:
         roof.update({"bound": None, "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None})
+    # ---- measured multiply-add peaks (outside every timed region) -------------------
+    probe = {"fp32_tflops": rad.peak_probe(rad.PROBE_FP32), "fp32x2_tflops": rad.peak_probe(rad.PROBE_FP32X2),
+             "fp64_tflops": rad.peak_probe(rad.PROBE_FP64),
+             "how": "rad_peak_probe: one wave of 256-thread blocks, 8 independent multiply-add chains per thread "
+                    "in registers, second of two launches timed with CUDA events; 2 flops per fma"}
+    fp32_measured = max(probe["fp32_tflops"], probe["fp32x2_tflops"])
+    fp32_filter = None
+    if kernels.get("diam_pairs_fp32", {}).get("launches"):
+        kp = kernels["diam_pairs_fp32"]
+        p_ms = kp["total_ms"] / kp["launches"]
+        p_ach = d["pairs_evaluated"] * FLOPS_PER_PAIR / (p_ms / 1e3) / 1e12
+        fp32_filter = {"kernel": "diam_pairs_fp32", "launch_ms": p_ms, "pairs_evaluated": d["pairs_evaluated"],
+                       "flops_per_pair": FLOPS_PER_PAIR, "achieved_tflops": p_ach,
+                       "frac_of_derived": p_ach / fp32_peak_tflops, "derived_tflops": fp32_peak_tflops,
+                       "frac_of_measured": p_ach / fp32_measured, "measured_tflops": fp32_measured}
+    if roof.get("bound") == "alu":
+        roof["peak_measured"] = fp32_measured
     kernel_table = {k: {"launches_per_step": v["launches"] / args.steps, "ms_per_step": v["total_ms"] / args.steps,
                         "share": v["total_ms"] / total_ms} for k, v in sorted(kernels.items(),
                                                                               key=lambda kv: -kv[1]["total_ms"])}
@@ -586,6 +603,8 @@ def main():
                  "culled_fp64_shape_ms": cms, "culled_fp64_pairs_evaluated": cstats["pairs_evaluated"],
                  "speedup_vs_plain": pms / fms, "fp32_filter_speedup_vs_culled_fp64": cms / fms,
                  "identical_results": bool(same),
+                 "fp64_flops_per_pair": 11, "fp64_tflops": pairs / (pms / 1e3) * 11 / 1e12,
+                 "fp64_frac_of_measured": pairs / (pms / 1e3) * 11 / 1e12 / probe["fp64_tflops"],
                  "note": "plain = all pairs in FP64; culled_fp64 = the same tile walk and culling as the FP32 "
                          "filter, every surviving pair in FP64; shape timings from a built mesh (rad_shape)"}
         if args.ablation:
@@ -680,6 +699,7 @@ def main():
                            "parallelism": f"replicas x{world}", "diam_stats": stats, "tuning": tuning_main,
                            "autotune": tuned},
                 "roofline": roof, "mesh_stage": mesh_stage_roofline(kernels, d, peaks["hbm_gbs"], args.steps),
+                "fp32_filter": fp32_filter, "peaks_probe": probe,
                 "kernels": kernel_table, "ms_per_step_with_kernel_events": statistics.mean(prof_ms),
                 "e2e": {"value": job_throughput(pairs, e2e, world), "unit": UNIT, "ms_per_step": e2e,
                         "h2d_bytes_per_step": hstats["h2d_bytes"], "d2h_bytes_per_step": hstats["d2h_bytes"]},

@@ -291,6 +291,26 @@ rad_status rad_crop_resample(const uint8_t* mask_dev, const int64_t dims[3], con
                              int64_t out_dims[3], int64_t box_lo[3], double out_spacing[3], rad_workspace_t** ws,
                              void* stream);
 
+/* ---- measured arithmetic peaks -------------------------------------------- */
+
+/* Kinds of rad_peak_probe. */
+enum { RAD_PROBE_FP32 = 0, RAD_PROBE_FP32X2 = 1, RAD_PROBE_FP64 = 2 };
+
+/* The arithmetic rate of this GPU, for the roofline of ALU-bound kernels
+ * (the FP32 filter of the diameters, Sec. 2, is bound by FP32 arithmetic; the
+ * plain all-pairs kernels by FP64).  One full wave of blocks runs eight
+ * independent multiply-add chains per thread in registers, with no memory
+ * traffic; the second of two identical launches is timed with CUDA events
+ * on `stream` (a few ms each for FP32, about 10 ms for FP64).
+ *   kind    RAD_PROBE_FP32 (scalar FP32 fma), RAD_PROBE_FP32X2 (packed f32x2
+ *           fma, two lanes per instruction) or RAD_PROBE_FP64 (FP64 fma)
+ *   tflops  host pointer; receives the rate in TFLOP/s, 2 flops per
+ *           multiply-add (4 per packed one)
+ * Unknown kind or NULL tflops: RAD_ERR_INVALID_ARG, nothing launched.  Uses a
+ * 16-byte device buffer of its own (allocated and freed by the call).
+ * Synchronises `stream`. */
+rad_status rad_peak_probe(int kind, double* tflops, void* stream);
+
 /* ---- failure detection check -------------------------------------------- */
 
 /* Every device-side wait of the library (the look-back of its single-pass

@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "librad.so")
 INCLUDE = os.path.join(ROOT, "include")
-SOURCES = ["mc.cu", "diam.cu", "api.cu", "noalloc.cu", "soft.cu", "ablation.cu", "prep.cu"]
+SOURCES = ["mc.cu", "diam.cu", "api.cu", "noalloc.cu", "soft.cu", "ablation.cu", "prep.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -81,7 +81,7 @@ EXPORTS = ("rad_mesh", "rad_soft_mesh", "rad_shape", "rad_shape_plain_fp64", "ra
            "rad_profile_read", "rad_profile_reset", "rad_launch_count", "rad_status_str", "rad_last_error",
            "rad_last_call_stats", "rad_soft_forward", "rad_soft_backward", "rad_batch_create", "rad_batch_run",
            "rad_batch_destroy", "rad_check_bounded_wait", "rad_soft_features", "rad_soft_backward_planes",
-           "rad_soft_batch_forward", "rad_soft_batch_backward", "rad_crop_resample")
+           "rad_soft_batch_forward", "rad_soft_batch_backward", "rad_crop_resample", "rad_peak_probe")
 
 
 def lib():
@@ -147,6 +147,8 @@ def lib():
         L.rad_last_error.restype = ctypes.c_char_p
         L.rad_check_bounded_wait.argtypes = [P]
         L.rad_check_bounded_wait.restype = I
+        L.rad_peak_probe.argtypes = [I, ctypes.POINTER(ctypes.c_double), P]
+        L.rad_peak_probe.restype = I
         _lib = L
     return _lib
 
@@ -459,6 +461,17 @@ def check_bounded_wait(stream=None):
     """Run the library's bounded device wait on a flag that nothing sets;
     returns the status code (RAD_ERR_TIMEOUT = 4 is the expected outcome)."""
     return int(lib().rad_check_bounded_wait(_stream(stream)))
+
+
+PROBE_FP32, PROBE_FP32X2, PROBE_FP64 = 0, 1, 2
+
+
+def peak_probe(kind, stream=None):
+    """Measured multiply-add rate of this GPU in TFLOP/s (rad_peak_probe):
+    PROBE_FP32 scalar FP32, PROBE_FP32X2 packed f32x2, PROBE_FP64 FP64."""
+    out = ctypes.c_double(0.0)
+    _check(lib().rad_peak_probe(int(kind), ctypes.byref(out), _stream(stream)))
+    return out.value
 
 
 def set_tuning(tile=None, threads=None, ctas_per_sm=None, cell_shift=None):

@@ -236,3 +236,24 @@ def test_bounded_wait_reports_timeout_and_context_survives():
     m = synth.ellipsoid_32(3)
     ref, _ = oracle.features(*m)
     assert_features(rad.extract(torch.from_numpy(m[0]).cuda(), m[1], rad.Workspace()), ref)
+
+
+def test_peak_probe_rates_and_arguments():
+    """The measured multiply-add rates (the ALU roofline's denominators) are
+    finite and within the range this part can reach: scalar FP32 below the
+    152 SMs x 128 lanes x 2 flops x 2.07 GHz = 80.6 TFLOP/s the units allow
+    (5 % margin), FP64 below FP32.  A bad kind or a NULL output is
+    rejected before any launch."""
+    import ctypes
+    fp32 = rad.peak_probe(rad.PROBE_FP32)
+    fp32x2 = rad.peak_probe(rad.PROBE_FP32X2)
+    fp64 = rad.peak_probe(rad.PROBE_FP64)
+    props = torch.cuda.get_device_properties(0)
+    ceiling = props.multi_processor_count * 128 * 2 * 2.07e9 / 1e12 * 1.05
+    assert 1.0 < fp32 < ceiling, (fp32, ceiling)
+    assert 1.0 < fp32x2 < 2.0 * ceiling, (fp32x2, ceiling)  # in case packed issue doubles the lane rate
+    assert 0.0 < fp64 < fp32
+    out = ctypes.c_double(0.0)
+    assert rad.lib().rad_peak_probe(7, ctypes.byref(out), None) == 1  # RAD_ERR_INVALID_ARG
+    assert rad.lib().rad_peak_probe(rad.PROBE_FP32, None, None) == 1
+    torch.zeros(8, device="cuda").sum().item()  # no CUDA error left behind
