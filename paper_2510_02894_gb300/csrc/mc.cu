@@ -376,8 +376,15 @@ __global__ void __launch_bounds__(kCountThreads) k_count(const uint32_t* bits, c
     int na = (sub == 0 && case_m1) ? 1 : 0;
     int nvox = 0;
     const long long wbase = r.wpre0 + (it.g - r.row0) * (long long)W;
-    for (int w = sub; w < Wc; w += L) {
+    for (int w = sub; w < Wc; w += L) {  // the same trip count on every lane (Wc is a multiple of L)
       const WordView v = word_view(R00, R10, R01, R11, w, W);
+      // no crossing, no active cube and no x = -1 entry in any of the warp's
+      // words: nothing to count, scan or list, only the inside voxels
+      const bool quiet = (v.ex | v.ey | v.ez | v.act) == 0u && !(w == 0 && (a0 || case_m1));
+      if (__all_sync(0xffffffffu, quiet)) {
+        if (y >= 0 && z >= 0) nvox += __popc(v.a);
+        continue;
+      }
       const int cnt = __popc(v.ex) + __popc(v.ey) + __popc(v.ez);
       int tw = 0;
       for (uint32_t act = v.act; act; act &= act - 1)
