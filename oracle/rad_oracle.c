@@ -252,8 +252,9 @@ static int get_triangulations(int k, tri_list_t** out) {
 /*   e1 = B - A, e2 = C - A; n = e1 x e2 (each component as a*b - c*d)   */
 /*   r = sqrt((n_x^2 + n_y^2) + n_z^2)                                  */
 /*   score = sum of r over the triangles in ascending canonical order.  */
-/* Ties are broken by the lexicographically smallest sorted list of     */
-/* canonical triples.                                                   */
+/* Area ties go to the larger enclosed volume (tri_vol6), and remaining */
+/* ties to the lexicographically smallest sorted list of canonical      */
+/* triples (choose_triangulation).                                      */
 /* ------------------------------------------------------------------ */
 
 static void canon_triple(int a, int b, int c, int out[3]) {
