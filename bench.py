@@ -190,6 +190,21 @@ def mesh_stage_roofline(kernels, ctx, peak_gbs, steps):
             "unit": "GB/s", "frac": gbs / peak_gbs}
 
 
+def fp32_filter_entry(kernels, pairs_evaluated, derived_tflops, measured_tflops):
+    """The FP32 filter's rate per launch (evaluated pairs x 8 flops over the
+    pair kernel's mean launch time) against the derived and the measured
+    FP32 peak; None when the pair kernel did not run."""
+    kp = kernels.get("diam_pairs_fp32")
+    if not kp or not kp.get("launches"):
+        return None
+    p_ms = kp["total_ms"] / kp["launches"]
+    ach = pairs_evaluated * FLOPS_PER_PAIR / (p_ms / 1e3) / 1e12
+    return {"kernel": "diam_pairs_fp32", "launch_ms": p_ms, "pairs_evaluated": pairs_evaluated,
+            "flops_per_pair": FLOPS_PER_PAIR, "achieved_tflops": ach,
+            "frac_of_derived": ach / derived_tflops, "derived_tflops": derived_tflops,
+            "frac_of_measured": ach / measured_tflops, "measured_tflops": measured_tflops}
+
+
 def timed(fn, steps, stream, flush):
     """Device milliseconds of fn() per call (CUDA events on `stream`, L2 flushed
     before each call) and host microseconds per call (wall clock)."""
@@ -556,15 +571,7 @@ def main():
              "how": "rad_peak_probe: one wave of 256-thread blocks, 8 independent multiply-add chains per thread "
                     "in registers, second of two launches timed with CUDA events; 2 flops per fma"}
     fp32_measured = max(probe["fp32_tflops"], probe["fp32x2_tflops"])
-    fp32_filter = None
-    if kernels.get("diam_pairs_fp32", {}).get("launches"):
-        kp = kernels["diam_pairs_fp32"]
-        p_ms = kp["total_ms"] / kp["launches"]
-        p_ach = d["pairs_evaluated"] * FLOPS_PER_PAIR / (p_ms / 1e3) / 1e12
-        fp32_filter = {"kernel": "diam_pairs_fp32", "launch_ms": p_ms, "pairs_evaluated": d["pairs_evaluated"],
-                       "flops_per_pair": FLOPS_PER_PAIR, "achieved_tflops": p_ach,
-                       "frac_of_derived": p_ach / fp32_peak_tflops, "derived_tflops": fp32_peak_tflops,
-                       "frac_of_measured": p_ach / fp32_measured, "measured_tflops": fp32_measured}
+    fp32_filter = fp32_filter_entry(kernels, d["pairs_evaluated"], fp32_peak_tflops, fp32_measured)
     if roof.get("bound") == "alu":
         roof["peak_measured"] = fp32_measured
     kernel_table = {k: {"launches_per_step": v["launches"] / args.steps, "ms_per_step": v["total_ms"] / args.steps,

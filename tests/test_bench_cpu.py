@@ -67,3 +67,16 @@ def test_kernel_work_formulas():
     kernels = {k: {"total_ms": 1.0} for k in bench.MESH_KERNELS}
     r = bench.mesh_stage_roofline(kernels, ctx, 1000.0, steps=2)
     assert r["ms"] == 2.0 and r["algorithmic_bytes"] == 1000 + 180 + 240
+
+
+def test_fp32_filter_entry():
+    """25M pairs x 8 flops in 0.01 ms per launch (two launches, 0.02 ms in
+    all) is 20 TFLOP/s: a quarter of an 80 TFLOP/s peak."""
+    kernels = {"diam_pairs_fp32": {"launches": 2, "total_ms": 0.02}}
+    e = bench.fp32_filter_entry(kernels, 25e6, 80.0, 100.0)
+    assert abs(e["launch_ms"] - 0.01) < 1e-15
+    assert abs(e["achieved_tflops"] - 20.0) < 1e-9
+    assert abs(e["frac_of_derived"] - 0.25) < 1e-12 and abs(e["frac_of_measured"] - 0.2) < 1e-12
+    assert bench.fp32_filter_entry({}, 25e6, 80.0, 100.0) is None
+    assert bench.fp32_filter_entry({"diam_pairs_fp32": {"launches": 0, "total_ms": 0.0}}, 1, 1.0, 1.0) is None
+
