@@ -225,7 +225,7 @@ def timed(fn, steps, stream, flush):
     return statistics.median(dev_ms), statistics.median(host_us)
 
 
-def bench_c1(args, stream, flush):
+def bench_ellipsoid32(args, stream, flush):
     """Per-ROI latency of a 32^3 ellipsoid through rad_extract (the pass
     replayed as one CUDA graph; results read back to the host every call)."""
     import torch
@@ -249,7 +249,7 @@ def bench_c1(args, stream, flush):
             "timing": "median of calls; host wall clock from the call to the features on the host"}
 
 
-def bench_c4(args, stream, flush, peak_gbs):
+def bench_soft160(args, stream, flush, peak_gbs):
     """Soft 160^3 map: rad_soft_forward + rad_soft_backward per step."""
     import torch
     from paper_2510_02894_gb300 import rad, synth
@@ -284,7 +284,7 @@ def bench_c4(args, stream, flush, peak_gbs):
             "bytes_note": "4 B/voxel read (forward) + 4 B/voxel read + 8 B/voxel FP64 gradient written (backward)"}
 
 
-def bench_c5(args, stream, flush):
+def bench_blobs512x8(args, stream, flush):
     """8 x 512^3 blobs as one batch (one set of launches, replayed as one CUDA graph)."""
     import torch
     from paper_2510_02894_gb300 import rad, synth
@@ -433,8 +433,9 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-configs", action="store_true", help="skip the 32^3, soft 160^3, 8 x 512^3 and crop lines")
-    ap.add_argument("--configs", default="c1,c4,c5,preprocess",
-                    help="which of those lines to run (comma-separated subset of c1,c4,c5,preprocess)")
+    ap.add_argument("--configs", default="ellipsoid_32,soft_160,blobs_512x8,preprocess",
+                    help="which of those lines to run (comma-separated subset of "
+                         "ellipsoid_32,soft_160,blobs_512x8,preprocess)")
     ap.add_argument("--ablation", action="store_true",
                     help="also time the FP64 accumulation variants on the CT mesh and the 256 crops")
     args = ap.parse_args()
@@ -678,12 +679,12 @@ def main():
     configs = {}
     if not args.no_configs:
         want = set(c.strip() for c in args.configs.split(","))
-        if "c1" in want:
-            configs["c1"] = bench_c1(args, stream, flush)
-        if "c4" in want:
-            configs["c4"] = bench_c4(args, stream, flush, peaks["hbm_gbs"])
-        if "c5" in want:
-            configs["c5"] = bench_c5(args, stream, flush)
+        if "ellipsoid_32" in want:
+            configs["ellipsoid_32"] = bench_ellipsoid32(args, stream, flush)
+        if "soft_160" in want:
+            configs["soft_160"] = bench_soft160(args, stream, flush, peaks["hbm_gbs"])
+        if "blobs_512x8" in want:
+            configs["blobs_512x8"] = bench_blobs512x8(args, stream, flush)
         if "preprocess" in want:
             configs["preprocess"] = bench_prep(args, stream, flush, peaks["hbm_gbs"], dev, sp)
 
