@@ -269,7 +269,8 @@ class Workspace:
 def extract(mask, spacing, ws, stream=None, out=None):
     """Whole path (mesh + all features) for a CUDA uint8 mask.  Returns a
     dict, or, when `out` (a Features) is given, fills it and returns it (the
-    rad_features_t the call wrote, no conversion)."""
+    rad_features_t the call wrote, no conversion; a later call with the same
+    `out` overwrites it)."""
     _device_tensor(mask, "torch.uint8")
     dims, sp = _geometry(mask.shape, spacing)
     f = Features() if out is None else out
@@ -444,7 +445,8 @@ class Batch:
 
     def run(self, stream=None, out=None):
         """Features of every ROI: a list of dicts, or, when `out` (from
-        features_buffer()) is given, that array filled by the call."""
+        features_buffer()) is given, that array filled by the call (a later
+        call with the same array overwrites it)."""
         buf = (Features * self.n)() if out is None else out
         if len(buf) != self.n:
             raise ValueError("out must hold one rad_features_t per ROI")
