@@ -140,6 +140,36 @@ def test_pair_error_bounds(dims, sp):
         assert worst_g == 0.0 and worst_f == 0.0, (worst_g, worst_f)
 
 
+@pytest.mark.parametrize("dims,sp", [GRIDS[0], GRIDS[2]])
+def test_pair_error_bounds_soft_positions(dims, sp):
+    """Soft maps: a vertex sits at owner + t along its edge with any FP64 t in
+    (0, 1), so positions are not on the half-integer lattice; the same bounds
+    hold (they only use |P| <= R)."""
+    rng = np.random.default_rng(9)
+    R2 = radius2(dims, sp)
+    R = np.sqrt(R2)
+    worst = 0.0
+    for _ in range(800):
+        uu = []
+        for _v in range(2):
+            ax = int(rng.integers(3))
+            u = [float(rng.integers(0, n)) for n in dims]
+            u[ax] = float(rng.integers(-1, dims[ax])) + float(rng.uniform(0.001, 0.999))
+            uu.append(u)
+        if rng.random() < 0.4:  # short pairs
+            uu[1] = [uu[0][k] + float(rng.uniform(-1.5, 1.5)) for k in range(3)]
+        ea, eb = entry(uu[0], dims, sp), entry(uu[1], dims, sp)
+        d2 = exact_d2(uu[0], uu[1], sp)
+        sq = float(d2) ** 0.5
+        eg = abs(float(Fraction(float(g_expansion(ea, eb))) - d2))
+        ef = abs(float(Fraction(float(f_difference(ea, eb))) - d2))
+        bg = 4.1 * U * R * sq + 20.2 * U * R2
+        bf = 5.1 * U * float(d2) + 4.1 * U * R * sq + 4.1 * U * U * R2
+        assert eg <= bg and ef <= bf, (uu, eg, bg, ef, bf)
+        worst = max(worst, eg / bg, ef / bf)
+    assert worst > 0.02
+
+
 @pytest.mark.parametrize("dims,sp", GRIDS[:2])
 def test_threshold_keeps_every_maximal_pair(dims, sp):
     """Small vertex sets with many exact ties at the maximum (points on the
