@@ -207,3 +207,39 @@ def test_threshold_keeps_every_maximal_pair(dims, sp):
         assert T > 0.0
         for p in top:
             assert gs[p] >= T and fs[p] >= T, (trial, p, gs[p], fs[p], T)
+
+
+def box_ub(alo, ahi, blo, bhi):
+    """The culling bound of two boxes of FP32 positions, in the kernels' order:
+    per axis the larger of fl(bhi - alo) and fl(ahi - blo), then
+    fma(mz, mz, fma(my, my, fl(mx mx)))."""
+    m = [max(np.float32(bhi[k] - alo[k]), np.float32(ahi[k] - blo[k])) for k in range(3)]
+    f = np.float32(m[0] * m[0])
+    f = fma32(m[1], m[1], f)
+    return fma32(m[2], m[2], f)
+
+
+@pytest.mark.parametrize("dims,sp", [GRIDS[0], GRIDS[2]])
+def test_box_bound_covers_every_pair_without_epsilon(dims, sp):
+    """Tiles of FP32 positions (near each other, overlapping, far apart): the
+    culling bound of the two tiles' boxes is >= the difference-form f of every
+    pair drawn from them, exactly (monotone FP32 operations)."""
+    rng = np.random.default_rng(3)
+    for trial in range(60):
+        centre = [random_vertex(rng, dims) for _ in range(2)]
+        if trial % 3 == 0:
+            centre[1] = [c + float(rng.uniform(-3, 3)) for c in centre[0]]
+        tiles = []
+        for t in range(2):
+            pts = []
+            for _ in range(8):
+                u = [centre[t][k] + float(rng.uniform(-4, 4)) for k in range(3)]
+                pts.append(entry(u, dims, sp))
+            lo = [min(p[0][k] for p in pts) for k in range(3)]
+            hi = [max(p[0][k] for p in pts) for k in range(3)]
+            tiles.append((pts, lo, hi))
+        (pa, alo, ahi), (pb, blo, bhi) = tiles
+        ub = box_ub(alo, ahi, blo, bhi)
+        for ea in pa:
+            for eb in pb:
+                assert f_difference(ea, eb) <= ub and f_difference(eb, ea) <= ub
