@@ -62,7 +62,7 @@ def test_random_small_masks():
     for it in range(150):
         shape = tuple(int(v) for v in rng.integers(1, 8, size=3))
         m = (rng.random(shape) < rng.uniform(0.2, 0.8)).astype(np.uint8)
-        m[m > 0] = rng.integers(1, 255, size=int(m.sum()), dtype=np.uint8)  # any non-zero value is inside
+        m[m > 0] = rng.integers(1, 256, size=int(m.sum()), dtype=np.uint8)  # any non-zero value (1..255) is inside
         sp = tuple(float(v) for v in rng.choice([0.5, 0.6, 0.7, 0.8, 1.0, 1.2, 2.5, 3.0], size=3))
         run_both(m, sp)
 
